@@ -1,0 +1,209 @@
+"""Pins for the oracle's pressure operator (eq. 1.1a, eq. p_discrete), the
+null-space projection, the preconditioner and preconditioned CG (Section 2.4).
+
+Pins: the tensor's eigenstructure (Section 1.1), the constant-coefficient
+closed form (m = 0), a manufactured solution derived symbolically from
+eq. (1.1a) with sympy, and a dense 8x8 assembly solved by numpy's
+least-squares routine.
+"""
+import numpy as np
+import pytest
+import sympy as sp
+
+import oracle as O
+
+RNG = np.random.default_rng(99)
+
+
+def test_tensor_eigenstructure():
+    """(m (x) m + r I) has eigenvalue r + |m|^2 along m and r along m-perp."""
+    npts = 50
+    m = RNG.standard_normal((2, npts))
+    r = RNG.uniform(0.05, 0.3, npts)
+    q = O.apply_K(m, r, m)
+    assert np.allclose(q, (r + (m ** 2).sum(0)) * m, rtol=1e-14, atol=1e-14)
+    mperp = np.stack([-m[1], m[0]])
+    assert np.allclose(O.apply_K(m, r, mperp), r * mperp, rtol=1e-14, atol=1e-14)
+    m3 = RNG.standard_normal((3, npts))
+    v = np.cross(m3.T, RNG.standard_normal((npts, 3))).T  # orthogonal to m3
+    assert np.allclose(O.apply_K(m3, r, v), r * v, atol=1e-13)
+
+
+@pytest.mark.parametrize("n,L", [((16, 8), (1.0, 2.0)), ((8, 32), (0.5, 1.0))])
+def test_constant_coefficient_operator_closed_form(n, L):
+    """m = 0, r = const: A p = r (-Laplacian) p with symbol r |xi~|^2."""
+    g = O.Grid(n, L)
+    r0 = 0.37
+    m = np.zeros((2,) + g.shape)
+    r = np.full(g.shape, r0)
+    # single mode: A cos(2 pi (k x / Lx + l y / Ly)) = r (2 pi)^2 ((k/Lx)^2 + (l/Ly)^2) cos(...)
+    X, Y = np.meshgrid(np.arange(n[0]) * L[0] / n[0], np.arange(n[1]) * L[1] / n[1])
+    k, l = 3, 2
+    p = np.cos(2 * np.pi * (k * X / L[0] + l * Y / L[1]))
+    lam = r0 * (2 * np.pi) ** 2 * ((k / L[0]) ** 2 + (l / L[1]) ** 2)
+    assert np.allclose(O.apply_A(g, m, r, p), lam * p, atol=1e-11 * lam)
+    # random field versus the same symbol applied with numpy's FFT
+    p = RNG.standard_normal(g.shape)
+    lx = np.arange(n[0]); ly = np.arange(n[1])
+    xix = np.where(lx < n[0] // 2, 2 * np.pi * lx / L[0], np.where(lx == n[0] // 2, 0.0, 2 * np.pi * (lx - n[0]) / L[0]))
+    xiy = np.where(ly < n[1] // 2, 2 * np.pi * ly / L[1], np.where(ly == n[1] // 2, 0.0, 2 * np.pi * (ly - n[1]) / L[1]))
+    sym = r0 * (xix[None, :] ** 2 + xiy[:, None] ** 2)
+    ref = np.fft.ifft2(sym * np.fft.fft2(p)).real
+    assert np.allclose(O.apply_A(g, m, r, p), ref, atol=1e-10)
+
+
+def manufactured(n, L):
+    """p, m, r band-limited trig polynomials; S = -div((m m^T + r I) grad p)
+    computed symbolically from eq. (1.1a)."""
+    x, y = sp.symbols("x y", real=True)
+    Lx, Ly = [sp.nsimplify(v) for v in L]
+    tx, ty = 2 * sp.pi * x / Lx, 2 * sp.pi * y / Ly
+    p = sp.sin(tx) * sp.cos(2 * ty) + sp.Rational(1, 2) * sp.cos(tx + ty)
+    m1 = sp.Rational(3, 10) + sp.Rational(1, 5) * sp.cos(ty)
+    m2 = sp.Rational(2, 5) * sp.sin(tx)
+    r = sp.Rational(1, 10) + sp.Rational(1, 20) * sp.cos(tx)
+    px, py = sp.diff(p, x), sp.diff(p, y)
+    mg = m1 * px + m2 * py
+    q1 = m1 * mg + r * px
+    q2 = m2 * mg + r * py
+    S = -(sp.diff(q1, x) + sp.diff(q2, y))
+    f = sp.lambdify((x, y), (p, m1, m2, r, S), "numpy")
+    X, Y = np.meshgrid(np.arange(n[0]) * L[0] / n[0], np.arange(n[1]) * L[1] / n[1])
+    vals = [np.broadcast_to(np.asarray(v, dtype=float), X.shape).copy() for v in f(X, Y)]
+    P, M1, M2, R, S = vals
+    return P, np.stack([M1, M2]), R, S
+
+
+@pytest.mark.parametrize("n,L", [((16, 16), (1.0, 1.0)), ((16, 32), (1.0, 2.0)),
+                                 ((32, 16), (0.5, 1.0))])
+def test_operator_manufactured_solution(n, L):
+    g = O.Grid(n, L)
+    P, M, R, S = manufactured(n, L)
+    Ap = O.apply_A(g, M, R, P)
+    assert np.abs(Ap - S).max() < 1e-11 * np.abs(S).max()
+
+
+@pytest.mark.parametrize("n,L", [((16, 16), (1.0, 1.0)), ((32, 16), (0.5, 1.0))])
+def test_pcg_recovers_manufactured_pressure(n, L):
+    g = O.Grid(n, L)
+    P, M, R, S = manufactured(n, L)
+    b = O.project(g, S)
+    x, st = O.pcg(g, M, R, b, rtol=1e-13, maxit=500)
+    assert st.rc == O.OK
+    Pp = O.project(g, P)
+    assert np.allclose(Pp, P, atol=1e-14)  # P has no null-mode content
+    assert np.abs(x - Pp).max() < 1e-10 * np.abs(P).max()
+
+
+def assemble(g, m, r):
+    n = g.npts
+    A = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = O.apply_A(g, m, r, e.reshape(g.shape)).ravel()
+    return A
+
+
+def corner_modes(g):
+    ny, nx = g.shape
+    i = np.arange(nx); j = np.arange(ny)
+    out = []
+    for ex in (0, 1):
+        for ey in (0, 1):
+            out.append((((-1.0) ** (ex * i))[None, :] * ((-1.0) ** (ey * j))[:, None]).ravel())
+    return np.array(out)
+
+
+def test_dense_8x8_symmetric_psd_nullspace_and_solve():
+    g = O.Grid((8, 8), (1.0, 1.5))
+    m = RNG.uniform(0, 1, (2,) + g.shape)
+    r = RNG.uniform(0.05, 0.2, g.shape)
+    A = assemble(g, m, r)
+    assert np.abs(A - A.T).max() < 1e-11 * np.abs(A).max()
+    ev = np.linalg.eigvalsh(0.5 * (A + A.T))
+    assert ev.min() > -1e-10 * ev.max()
+    assert (np.abs(ev) < 1e-9 * ev.max()).sum() == 4  # R2: exactly the corner modes
+    C = corner_modes(g)
+    assert np.abs(A @ C.T).max() < 1e-10 * np.abs(A).max()
+    # projection removes exactly the corner-mode components
+    f = RNG.standard_normal(g.shape)
+    Q, _ = np.linalg.qr(C.T)
+    fp_ref = f.ravel() - Q @ (Q.T @ f.ravel())
+    assert np.allclose(O.project(g, f).ravel(), fp_ref, atol=1e-13)
+    # CG versus the minimum-norm least-squares solution
+    S = O.project(g, RNG.standard_normal(g.shape))
+    x_ls = np.linalg.lstsq(A, S.ravel(), rcond=1e-12)[0]
+    x_cg, st = O.pcg(g, m, r, S, rtol=1e-13, maxit=500)
+    assert st.rc == O.OK
+    assert np.abs(x_cg.ravel() - x_ls).max() < 1e-9 * np.abs(x_ls).max()
+
+
+def test_pcg_constant_coefficient_converges_in_one_iteration():
+    g = O.Grid((16, 32), (1.0, 2.0))
+    r0 = 0.2
+    m = np.zeros((2,) + g.shape)
+    r = np.full(g.shape, r0)
+    S = O.project(g, RNG.standard_normal(g.shape))
+    x, st = O.pcg(g, m, r, S, kappa=r0, rtol=1e-12, maxit=10)
+    assert st.rc == O.OK and st.cg_iters == 1
+    # closed form: p^ = S^ / (r |xi~|^2) off the null modes
+    n = g.n
+    lx = np.arange(n[0]); ly = np.arange(n[1])
+    xix = np.where(lx < n[0] // 2, 2 * np.pi * lx / 1.0, np.where(lx == n[0] // 2, 0.0, 2 * np.pi * (lx - n[0]) / 1.0))
+    xiy = np.where(ly < n[1] // 2, 2 * np.pi * ly / 2.0, np.where(ly == n[1] // 2, 0.0, 2 * np.pi * (ly - n[1]) / 2.0))
+    sym = r0 * (xix[None, :] ** 2 + xiy[:, None] ** 2)
+    Sh = np.fft.fft2(S)
+    ph = np.where(sym > 0, Sh / np.where(sym > 0, sym, 1), 0)
+    assert np.allclose(x, np.fft.ifft2(ph).real, atol=1e-12)
+
+
+def test_pcg_iterations_within_condition_bound():
+    """Generalised eigenvalues of (A, kappa L) lie in [min eig K, max eig K]/kappa,
+    so the CG error bound gives it <= ceil(sqrt(cond)/2 * ln(2/rtol))."""
+    g = O.Grid((32, 32))
+    m = RNG.uniform(0, 1, (2,) + g.shape)
+    r = RNG.uniform(0.05, 0.15, g.shape)
+    S = O.project(g, RNG.standard_normal(g.shape))
+    rtol = 1e-10
+    cond = (r + (m ** 2).sum(0)).max() / r.min()
+    # bound on ||e||_A; relative residual picks up at most sqrt(cond(A)) more
+    condA = cond * (2 * np.pi * 16) ** 2 / (2 * np.pi) ** 2
+    bound = int(np.ceil(0.5 * np.sqrt(cond) * np.log(2 * np.sqrt(condA) / rtol)))
+    x, st = O.pcg(g, m, r, S, rtol=rtol, maxit=10000)
+    assert st.rc == O.OK
+    assert st.cg_iters <= bound
+    assert st.true_rel_residual < 10 * rtol
+
+
+def test_pcg_warm_start_at_solution_takes_no_iteration():
+    g = O.Grid((16, 16))
+    m = RNG.uniform(0, 1, (2,) + g.shape)
+    r = np.full(g.shape, 0.1)
+    S = O.project(g, RNG.standard_normal(g.shape))
+    x, st = O.pcg(g, m, r, S, rtol=1e-12)
+    x2, st2 = O.pcg(g, m, r, S, x0=x, rtol=1e-10)
+    assert st2.cg_iters == 0
+    assert np.array_equal(x2, O.project(g, x))
+
+
+def test_pcg_zero_source_gives_zero_pressure():
+    g = O.Grid((8, 8))
+    m = RNG.uniform(0, 1, (2,) + g.shape)
+    r = np.full(g.shape, 0.1)
+    x, st = O.pcg(g, m, r, np.zeros(g.shape), x0=RNG.standard_normal(g.shape))
+    assert st.cg_iters == 0 and np.all(x == 0)
+
+
+def test_preconditioner_inverts_constant_coefficient_operator():
+    g = O.Grid((16, 8), (1.0, 2.0))
+    kappa = 0.7
+    m = np.zeros((2,) + g.shape)
+    r = np.full(g.shape, kappa)
+    p = O.project(g, RNG.standard_normal(g.shape))
+    z = O.precond(g, kappa, O.apply_A(g, m, r, p))
+    assert np.allclose(z, p, atol=1e-12)
+    # null modes map to zero
+    C = corner_modes(g)
+    for c in C:
+        assert np.abs(O.precond(g, kappa, c.reshape(g.shape))).max() < 1e-14
