@@ -1,0 +1,159 @@
+/*
+ * hc.h -- C ABI of the GB300 (sm_103a) implementation of one time step of the
+ * Fourier spectral FFT+CG splitting scheme for the periodic Hu-Cai
+ * network-formation system
+ *
+ *     -div((m (x) m + r I) grad p) = S                              (eq. 1.1a)
+ *     d_t m - D^2 Lap m - c^2 (m . grad p) grad p + |m|^{2(gamma-1)} m = 0   (eq. 1.1b)
+ *
+ * of Aceves-Sanchez, Degond, Merino-Aceituno and Wytrzens (arXiv 2606.06720).
+ * One step is the loop body of Algorithm 1: the FFT+CG pressure solve of
+ * Section 2.4 (eq. p_discrete) from m^k with warm start p^k, then the split
+ * m-update of Section 2.3 -- exact activation (eq. m_activation_discrete),
+ * exact relaxation (eq. m_relaxation_discrete), exact Fourier diffusion
+ * (eq. diffusion_space_discrete).
+ *
+ * Conventions shared by every entry point
+ *   - Grid (Section 2.2): n[a] nodes per axis, periodic end point excluded,
+ *     x_i = i L[a] / n[a].  2D only: dim = 2, n[0] = nx, n[1] = ny, both powers
+ *     of two in [8, 4096]; n[2] must be 1.
+ *   - Field layout: row-major, x fastest.  A scalar field has nx*ny doubles at
+ *     index j*nx + i.  A vector field (m) is component-major: component c of
+ *     point (i, j) at c*nx*ny + j*nx + i, so count = 2*nx*ny.
+ *   - Every host pointer is FP64 whatever the internal precision; it is read
+ *     or written completely before the call returns (the call waits for its
+ *     own copies), so the caller may reuse the buffer right away.
+ *   - Every call returns HC_OK (0) or a negative HC_E* code and never throws.
+ *     A non-HC_OK return from a setter leaves the context's previous value.
+ *   - A context is not thread-safe; calls on one context must not overlap.
+ *   - Device work runs on params.stream (a cudaStream_t, NULL = legacy default
+ *     stream).  Calls that return data to the host synchronise that stream.
+ */
+#ifndef HC_H
+#define HC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HC_OK 0
+#define HC_EINVAL (-1)     /* bad argument: null pointer, size mismatch, unsupported grid, r <= 0 ... */
+#define HC_ENOMEM (-2)     /* device allocation failed or the workspace given is too small */
+#define HC_ECUDA (-3)      /* a CUDA runtime call failed (the context should be destroyed) */
+#define HC_ENOCONV (-4)    /* CG hit its iteration cap; the state was still advanced */
+#define HC_ENONFINITE (-5) /* NaN/Inf in p or m, e.g. the activation exponential overflowed (Remark 2.1) */
+#define HC_ETIMEOUT (-6)   /* a bounded device-side wait gave up */
+#define HC_ENOTSUP (-7)    /* valid request that this build does not implement */
+
+/* Arithmetic of the path. */
+#define HC_FP64_PLAIN 0   /* every kernel in IEEE FP64 */
+#define HC_FP32_REFINED 1 /* FFTs, operator applies and split step in FP32; pressure solve wrapped in
+                             FP64 iterative refinement (FP64 residual, FP64 correction accumulation,
+                             FP64 dot products and null-space projection) */
+
+typedef struct hc_ctx hc_ctx; /* opaque; owns (or borrows) all device memory of one problem */
+
+typedef struct {
+  int dim;      /* 2 */
+  int n[3];     /* nodes per axis (x, y, z) */
+  double L[3];  /* domain lengths, > 0 */
+} hc_grid;
+
+typedef struct {
+  double c, D, gamma, dt; /* activation c, diffusion D, metabolic exponent gamma, time step (Algorithm 1 inputs) */
+  double cg_rtol;         /* stop when ||S - A p||_2 <= cg_rtol ||S||_2, S projected (Section 2.4; default 1e-7 if <= 0) */
+  int cg_maxit;           /* CG iteration cap per solve; in refined mode per inner FP32 solve (default 1000 if <= 0) */
+  int precision;          /* HC_FP64_PLAIN or HC_FP32_REFINED */
+  double kappa;           /* preconditioner constant; <= 0: mean(r) + mean(|m|^2)/2, recomputed every step */
+  double inner_rtol;      /* refined mode: inner FP32 CG stops at this reduction of its own residual (default 1e-4 if <= 0) */
+  int max_sweeps;         /* refined mode: cap on FP64 refinement sweeps per solve (default 10 if <= 0) */
+  int use_graph;          /* 1: each step runs as one CUDA graph with device-side loop control; 0: host loop */
+  void* stream;           /* cudaStream_t the context launches on */
+} hc_params;
+
+typedef struct {
+  int cg_iters;        /* CG iterations of the last step's pressure solve (summed over sweeps) */
+  int refine_sweeps;   /* refined mode: inner solves run; plain mode: 0 */
+  double rel_residual; /* ||S - A p||_2 / ||S||_2 at exit: FP64-evaluated in refined mode, recursive in plain mode */
+  double kappa;        /* preconditioner constant used */
+  int status;          /* HC_OK, HC_ENOCONV or HC_ENONFINITE for that step */
+} hc_step_stats;
+
+/* Bytes of device workspace hc_create needs for this grid and precision. */
+int hc_workspace_size(const hc_grid* grid, const hc_params* params, size_t* bytes);
+
+/* Create a context.  If workspace is non-NULL it must be a device pointer to at
+ * least hc_workspace_size() bytes, 256-byte aligned; the context borrows it
+ * (the caller frees it after hc_destroy).  If NULL the context allocates its
+ * own with cudaMalloc.  Initial state: r = 1, S = 0, m = 0, p = 0.
+ * Errors: HC_EINVAL (grid/params), HC_ENOMEM, HC_ECUDA. */
+int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* workspace,
+              size_t workspace_bytes);
+
+/* Replace the scalar parameters (c, D, gamma, dt, tolerances, kappa, use_graph);
+ * the grid, precision and stream must match the ones given at creation. */
+int hc_set_params(hc_ctx* ctx, const hc_params* params);
+
+/* Background permeability r(x) (eq. 1.1a); count = nx*ny; requires r > 0
+ * everywhere (the paper assumes r >= r0 > 0) and finite, else HC_EINVAL. */
+int hc_set_r(hc_ctx* ctx, const double* r, size_t count);
+
+/* Source/sink field S (eq. 1.1a); count = nx*ny.  Stored after projection onto
+ * the complement of the operator's null space (zero mean and no corner modes:
+ * the solvability condition that the paper states as int S = 0). */
+int hc_set_source(hc_ctx* ctx, const double* S, size_t count);
+
+/* Conductivity m (count = 2*nx*ny, component-major). */
+int hc_set_m(hc_ctx* ctx, const double* m, size_t count);
+
+/* Pressure p used as the CG initial guess of the next step (Section 2.4 uses
+ * p^k; default 0).  Projected like S. */
+int hc_set_p(hc_ctx* ctx, const double* p, size_t count);
+
+/* Run nsteps passes of the loop body of Algorithm 1.  `last` (may be NULL)
+ * receives the stats of the final step.  Returns HC_OK, or the first non-OK
+ * step status (HC_ENOCONV: the steps still ran; HC_ENONFINITE: stopped). */
+int hc_step(hc_ctx* ctx, int nsteps, hc_step_stats* last);
+
+/* Copy the current p (count = nx*ny) or m (count = 2*nx*ny) to host memory. */
+int hc_get_p(hc_ctx* ctx, double* out, size_t count);
+int hc_get_m(hc_ctx* ctx, double* out, size_t count);
+
+/* --- Component entry points (each runs one part of the step on the GPU) --- */
+
+/* Spectral gradient of the current p (Section 2.4 and Algorithm 1 "compute
+ * gradient of p via FFT"): out = (d_x p, d_y p), count = 2*nx*ny. */
+int hc_gradient(hc_ctx* ctx, double* out, size_t count);
+
+/* Apply the discrete pressure operator of eq. (p_discrete) with the current m
+ * and r: out = A f for the field f (count = nx*ny; f is projected first). */
+int hc_apply_operator(hc_ctx* ctx, const double* f, double* out, size_t count);
+
+/* Only Step 2 of Algorithm 1 (activation, relaxation, diffusion) with the
+ * current p and m; m is updated in place on the device. */
+int hc_split_step(hc_ctx* ctx);
+
+/* Forward 2D DFT of a real field (count = nx*ny) in the packed half-spectrum
+ * layout: out has ny*(nx/2) complex values (2*ny*(nx/2) doubles, re/im
+ * interleaved); entry (ky, kx) for 1 <= kx < nx/2 is F[ky][kx] and entry
+ * (ky, 0) is F[ky][0] + i F[ky][nx/2]. */
+int hc_spectrum(hc_ctx* ctx, const double* f, double* out, size_t count);
+
+/* Number of this library's kernel launches issued by the context so far
+ * (graph launches count every kernel node). */
+int hc_launch_count(const hc_ctx* ctx, long long* count);
+
+void hc_destroy(hc_ctx* ctx);
+const char* hc_strerror(int code);
+
+/* Description of the most recent CUDA failure behind an HC_ECUDA on the
+ * calling thread (source line, call, CUDA error name and text); "" if none.
+ * The string is owned by the library and overwritten by the next failure. */
+const char* hc_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

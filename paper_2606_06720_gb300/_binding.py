@@ -1,0 +1,280 @@
+"""ctypes binding of ``include/hc.h``: argument marshalling only.
+
+The module-level functions carry the C names (``hc_create``, ``hc_step`` ...)
+and take/return plain ctypes values.  ``Solver`` wraps one context: it
+allocates the device workspace as a torch tensor, passes torch's current CUDA
+stream, and converts numpy / torch CPU arrays to the FP64 host pointers the
+ABI expects.  Nothing here computes any part of the scheme.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBNAME = os.path.join(HERE, "libhc_gb300.so")
+
+HC_OK, HC_EINVAL, HC_ENOMEM, HC_ECUDA = 0, -1, -2, -3
+HC_ENOCONV, HC_ENONFINITE, HC_ETIMEOUT, HC_ENOTSUP = -4, -5, -6, -7
+HC_FP64_PLAIN, HC_FP32_REFINED = 0, 1
+
+
+class HuCaiError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        detail = ""
+        if code == HC_ECUDA:
+            detail = " [" + lib.hc_last_cuda_error().decode() + "]"
+        super().__init__(f"{what}: {strerror(code)} ({code}){detail}")
+
+
+class hc_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("L", C.c_double * 3)]
+
+
+class hc_params(C.Structure):
+    _fields_ = [("c", C.c_double), ("D", C.c_double), ("gamma", C.c_double), ("dt", C.c_double),
+                ("cg_rtol", C.c_double), ("cg_maxit", C.c_int), ("precision", C.c_int),
+                ("kappa", C.c_double), ("inner_rtol", C.c_double), ("max_sweeps", C.c_int),
+                ("use_graph", C.c_int), ("stream", C.c_void_p)]
+
+
+class hc_step_stats(C.Structure):
+    _fields_ = [("cg_iters", C.c_int), ("refine_sweeps", C.c_int), ("rel_residual", C.c_double),
+                ("kappa", C.c_double), ("status", C.c_int)]
+
+
+def library_path() -> str:
+    return _LIBNAME
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(_LIBNAME):
+        raise ImportError(
+            f"{_LIBNAME} is missing: build it with `python -m paper_2606_06720_gb300.build` "
+            "(or __graft_entry__.build()); there is no CPU fallback")
+    lib = C.CDLL(_LIBNAME)
+    P = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    sig = {
+        "hc_workspace_size": ([C.POINTER(hc_grid), C.POINTER(hc_params), C.POINTER(C.c_size_t)], C.c_int),
+        "hc_create": ([C.POINTER(P), C.POINTER(hc_grid), C.POINTER(hc_params), P, C.c_size_t], C.c_int),
+        "hc_set_params": ([P, C.POINTER(hc_params)], C.c_int),
+        "hc_set_r": ([P, dp, C.c_size_t], C.c_int),
+        "hc_set_source": ([P, dp, C.c_size_t], C.c_int),
+        "hc_set_m": ([P, dp, C.c_size_t], C.c_int),
+        "hc_set_p": ([P, dp, C.c_size_t], C.c_int),
+        "hc_step": ([P, C.c_int, C.POINTER(hc_step_stats)], C.c_int),
+        "hc_get_p": ([P, dp, C.c_size_t], C.c_int),
+        "hc_get_m": ([P, dp, C.c_size_t], C.c_int),
+        "hc_gradient": ([P, dp, C.c_size_t], C.c_int),
+        "hc_apply_operator": ([P, dp, dp, C.c_size_t], C.c_int),
+        "hc_split_step": ([P], C.c_int),
+        "hc_spectrum": ([P, dp, dp, C.c_size_t], C.c_int),
+        "hc_launch_count": ([P, C.POINTER(C.c_longlong)], C.c_int),
+        "hc_destroy": ([P], None),
+        "hc_strerror": ([C.c_int], C.c_char_p),
+        "hc_last_cuda_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+# C-named entry points (thin aliases) ----------------------------------------
+hc_workspace_size = lib.hc_workspace_size
+hc_create = lib.hc_create
+hc_set_params = lib.hc_set_params
+hc_set_r = lib.hc_set_r
+hc_set_source = lib.hc_set_source
+hc_set_m = lib.hc_set_m
+hc_set_p = lib.hc_set_p
+hc_step = lib.hc_step
+hc_get_p = lib.hc_get_p
+hc_get_m = lib.hc_get_m
+hc_gradient = lib.hc_gradient
+hc_apply_operator = lib.hc_apply_operator
+hc_split_step = lib.hc_split_step
+hc_spectrum = lib.hc_spectrum
+hc_launch_count = lib.hc_launch_count
+hc_destroy = lib.hc_destroy
+
+
+def strerror(code: int) -> str:
+    return lib.hc_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str, ok=(HC_OK,)):
+    if rc not in ok:
+        raise HuCaiError(rc, what)
+    return rc
+
+
+@dataclass
+class StepStats:
+    cg_iters: int
+    refine_sweeps: int
+    rel_residual: float
+    kappa: float
+    status: int
+    rc: int
+
+
+def _host_f64(a, count: int, writable: bool = False):
+    """(pointer, keepalive) of a contiguous FP64 host buffer: numpy array or
+    torch CPU tensor (pinned or not)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != count:
+                raise ValueError("expected a contiguous float64 CPU tensor of %d elements" % count)
+            return C.cast(C.c_void_p(a.data_ptr()), C.POINTER(C.c_double)), a
+    except ImportError:
+        pass
+    arr = np.asarray(a)
+    if arr.dtype != np.float64 or not arr.flags["C_CONTIGUOUS"]:
+        if writable:
+            raise ValueError("output buffer must be a contiguous float64 array")
+        arr = np.ascontiguousarray(arr, dtype=np.float64)
+    if arr.size != count:
+        raise ValueError("expected %d elements, got %d" % (count, arr.size))
+    return arr.ctypes.data_as(C.POINTER(C.c_double)), arr
+
+
+class Solver:
+    """One Hu-Cai problem on one GPU.
+
+    ``n = (nx, ny)`` nodes, ``L = (Lx, Ly)``; ``precision`` is ``"fp64"`` (plain)
+    or ``"fp32_refined"``.  Arrays use numpy shapes ``(ny, nx)`` for scalar
+    fields and ``(2, ny, nx)`` for m.
+    """
+
+    def __init__(self, n, L=(1.0, 1.0), *, c: float, D: float, gamma: float, dt: float,
+                 precision: str = "fp32_refined", cg_rtol: float = 1e-8, cg_maxit: int = 1000,
+                 kappa: float = 0.0, inner_rtol: float = 1e-4, max_sweeps: int = 10,
+                 use_graph: bool = True, device: str = "cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.n = (int(n[0]), int(n[1]))
+        self.L = (float(L[0]), float(L[1]))
+        self.npts = self.n[0] * self.n[1]
+        self.shape = (self.n[1], self.n[0])
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.grid = hc_grid(2, (C.c_int * 3)(self.n[0], self.n[1], 1),
+                            (C.c_double * 3)(self.L[0], self.L[1], 1.0))
+        prec = {"fp64": HC_FP64_PLAIN, "fp64_plain": HC_FP64_PLAIN,
+                "fp32_refined": HC_FP32_REFINED}[precision]
+        self.precision = precision
+        self.params = hc_params(c, D, gamma, dt, cg_rtol, int(cg_maxit), prec, kappa, inner_rtol,
+                                int(max_sweeps), int(bool(use_graph)), self.stream.cuda_stream)
+        nbytes = C.c_size_t()
+        _check(hc_workspace_size(C.byref(self.grid), C.byref(self.params), C.byref(nbytes)),
+               "hc_workspace_size")
+        # device memory comes from torch's allocator; the context borrows it
+        self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(hc_create(C.byref(self.ctx), C.byref(self.grid), C.byref(self.params),
+                             C.c_void_p(aligned), nbytes.value), "hc_create")
+
+    # lifecycle -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None) and self.ctx.value:
+            hc_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # parameters and fields ----------------------------------------------
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            if k == "use_graph":
+                v = int(bool(v))
+            setattr(self.params, k, v)
+        _check(hc_set_params(self.ctx, C.byref(self.params)), "hc_set_params")
+
+    def set_r(self, r):
+        p, keep = _host_f64(r, self.npts)
+        _check(hc_set_r(self.ctx, p, self.npts), "hc_set_r")
+
+    def set_source(self, S):
+        p, keep = _host_f64(S, self.npts)
+        _check(hc_set_source(self.ctx, p, self.npts), "hc_set_source")
+
+    def set_m(self, m):
+        p, keep = _host_f64(m, 2 * self.npts)
+        _check(hc_set_m(self.ctx, p, 2 * self.npts), "hc_set_m")
+
+    def set_p(self, p_):
+        p, keep = _host_f64(p_, self.npts)
+        _check(hc_set_p(self.ctx, p, self.npts), "hc_set_p")
+
+    def get_p(self, out=None):
+        out = np.empty(self.shape) if out is None else out
+        p, keep = _host_f64(out, self.npts, writable=True)
+        _check(hc_get_p(self.ctx, p, self.npts), "hc_get_p")
+        return out
+
+    def get_m(self, out=None):
+        out = np.empty((2,) + self.shape) if out is None else out
+        p, keep = _host_f64(out, 2 * self.npts, writable=True)
+        _check(hc_get_m(self.ctx, p, 2 * self.npts), "hc_get_m")
+        return out
+
+    # the step -------------------------------------------------------------
+    def step(self, nsteps: int = 1, allow=(HC_OK, HC_ENOCONV)) -> StepStats:
+        st = hc_step_stats()
+        rc = hc_step(self.ctx, int(nsteps), C.byref(st))
+        _check(rc, "hc_step", ok=allow)
+        return StepStats(st.cg_iters, st.refine_sweeps, st.rel_residual, st.kappa, st.status, rc)
+
+    # components ----------------------------------------------------------
+    def gradient(self):
+        out = np.empty((2,) + self.shape)
+        p, keep = _host_f64(out, 2 * self.npts, writable=True)
+        _check(hc_gradient(self.ctx, p, 2 * self.npts), "hc_gradient")
+        return out
+
+    def apply_operator(self, f):
+        fp, keep = _host_f64(f, self.npts)
+        out = np.empty(self.shape)
+        op, keep2 = _host_f64(out, self.npts, writable=True)
+        _check(hc_apply_operator(self.ctx, fp, op, self.npts), "hc_apply_operator")
+        return out
+
+    def split_step(self):
+        _check(hc_split_step(self.ctx), "hc_split_step")
+
+    def spectrum(self, f):
+        """Packed half spectrum, complex array of shape (ny, nx/2)."""
+        fp, keep = _host_f64(f, self.npts)
+        out = np.empty((self.n[1], self.n[0] // 2), dtype=np.complex128)
+        op = out.view(np.float64).ctypes.data_as(C.POINTER(C.c_double))
+        _check(hc_spectrum(self.ctx, fp, op, self.npts), "hc_spectrum")
+        return out
+
+    def launch_count(self) -> int:
+        v = C.c_longlong()
+        _check(hc_launch_count(self.ctx, C.byref(v)), "hc_launch_count")
+        return v.value

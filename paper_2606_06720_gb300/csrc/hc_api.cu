@@ -1,0 +1,978 @@
+// hc_api.cu -- C ABI and host orchestration of one time step of the Fourier
+// spectral FFT+CG splitting scheme (arXiv 2606.06720, Algorithm 1).
+//
+// The host only sequences kernels and moves the boundary's FP64 arrays.  All
+// arithmetic of the step runs in the kernels of hc_kernels_f32.cu /
+// hc_kernels_f64.cu.  CG loop control is device-side: every iteration kernel
+// returns at once when the solve state says "done", so the host either polls
+// a small state block every few iterations (host loop) or, in graph mode,
+// replays one CUDA graph per step whose CG and refinement loops are
+// conditional WHILE nodes driven by the kernels themselves.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hc.h"
+#include "hc_internal.cuh"
+
+using hc::cx;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kChunk = 4;  // CG iterations launched between host polls (host-loop mode)
+
+struct Layout {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename P>
+  P* take(size_t bytes) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    P* p = base ? reinterpret_cast<P*>(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+bool is_pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+}  // namespace
+
+struct hc_ctx {
+  hc_grid grid;
+  hc_params prm;
+  int nx, ny, H;
+  size_t n;  // points
+  int refined;
+  cudaStream_t stream;
+  bool owns_ws;
+  void* ws;
+  size_t ws_bytes;
+  long long launches;
+  double mean_r;
+
+  // device memory (all inside the workspace)
+  hc::SolveState* st;
+  double* partials;
+  double* stage;            // 2n doubles: FP64 boundary staging
+  cx<double>* p64;          // pressure spectrum
+  cx<double>* b64;          // source spectrum (projected)
+  cx<double>* r64;          // residual (FP64)
+  cx<double>* d64;          // CG direction (plain mode)
+  cx<double>* q64;          // A d (plain mode)
+  cx<double>* G64;          // 2 spectra: gradient / flux / m scratch (FP64)
+  cx<float>* r32;           // refined: inner residual
+  cx<float>* d32;           // refined: inner direction
+  cx<float>* q32;           // refined: A d
+  cx<float>* x32;           // refined: inner solution (correction delta)
+  cx<float>* G32;           // refined: 2 spectra scratch (FP32)
+  void* m[2];               // conductivity components (double or float)
+  void* rf;                 // permeability r (double or float)
+  // tables
+  cx<float>*twx_f, *twy_f;
+  cx<double>*twx_d, *twy_d;
+  float *kxd_f, *kyd_f, *hx_f, *hy_f;
+  double *kxd_d, *kyd_d, *hx_d, *hy_d;
+  hc::Geo<float> gf;
+  hc::Geo<double> gd;
+
+  hc::SolveState* st_host;  // pinned mirror for readback
+  // graph mode: captured on a private stream (capture is illegal on the
+  // legacy default stream), launched on `stream`
+  cudaStream_t cap_stream;
+  cudaGraphExec_t gexec;
+  bool graph_ready;
+  int graph_nodes_fixed, graph_nodes_body, graph_nodes_outer;
+};
+
+namespace {
+
+// exp(-2 pi i m / N) for m < N, with exact octant symmetry.
+void twiddles(int N, std::vector<double>& re, std::vector<double>& im) {
+  re.resize(N);
+  im.resize(N);
+  const double half_pi = 1.57079632679489661923;
+  for (int m = 0; m < N; ++m) {
+    const long long a4 = 4LL * m;
+    const int q = (int)(a4 / N);
+    const long long r = a4 - (long long)q * N;  // angle = (pi/2) (q + r/N)
+    double c, s;
+    if (2 * r <= N) {
+      const double phi = half_pi * (double)r / N;
+      c = std::cos(phi);
+      s = std::sin(phi);
+    } else {
+      const double phi = half_pi * (double)(N - r) / N;
+      c = std::sin(phi);
+      s = std::cos(phi);
+    }
+    double ct, stt;
+    switch (q & 3) {
+      case 0: ct = c; stt = s; break;
+      case 1: ct = -s; stt = c; break;
+      case 2: ct = -c; stt = -s; break;
+      default: ct = s; stt = -c; break;
+    }
+    re[m] = ct;
+    im[m] = -stt;
+  }
+}
+
+// Fourier variable of Section 2.3.3 (Nyquist entry positive).
+double xi(int l, int N, double L) {
+  const double two_pi = 6.28318530717958647692;
+  return (2 * l <= N) ? two_pi * l / L : two_pi * (l - N) / L;
+}
+// First-derivative multiplier, Nyquist entry zero.
+double xid(int l, int N, double L) { return (2 * l == N) ? 0.0 : xi(l, N, L); }
+
+void layout(hc_ctx* c, Layout& L) {
+  const size_t n = c->n;
+  const size_t S64 = (size_t)c->ny * c->H * sizeof(cx<double>);
+  const size_t S32 = (size_t)c->ny * c->H * sizeof(cx<float>);
+  const int max_ctas = (int)std::max<size_t>({(size_t)c->H, (size_t)c->ny, (size_t)1216});
+  c->st = L.take<hc::SolveState>(sizeof(hc::SolveState));
+  c->partials = L.take<double>(sizeof(double) * 4 * max_ctas);
+  c->stage = L.take<double>(sizeof(double) * 2 * n);
+  c->p64 = L.take<cx<double>>(S64);
+  c->b64 = L.take<cx<double>>(S64);
+  c->r64 = L.take<cx<double>>(S64);
+  c->G64 = L.take<cx<double>>(2 * S64);
+  if (!c->refined) {
+    c->d64 = L.take<cx<double>>(S64);
+    c->q64 = L.take<cx<double>>(S64);
+    c->r32 = c->d32 = c->q32 = c->x32 = c->G32 = nullptr;
+    c->m[0] = L.take<double>(sizeof(double) * n);
+    c->m[1] = L.take<double>(sizeof(double) * n);
+    c->rf = L.take<double>(sizeof(double) * n);
+  } else {
+    c->d64 = c->q64 = nullptr;
+    c->r32 = L.take<cx<float>>(S32);
+    c->d32 = L.take<cx<float>>(S32);
+    c->q32 = L.take<cx<float>>(S32);
+    c->x32 = L.take<cx<float>>(S32);
+    c->G32 = L.take<cx<float>>(2 * S32);
+    c->m[0] = L.take<float>(sizeof(float) * n);
+    c->m[1] = L.take<float>(sizeof(float) * n);
+    c->rf = L.take<float>(sizeof(float) * n);
+  }
+  c->twx_f = L.take<cx<float>>(sizeof(cx<float>) * c->nx);
+  c->twy_f = L.take<cx<float>>(sizeof(cx<float>) * c->ny);
+  c->twx_d = L.take<cx<double>>(sizeof(cx<double>) * c->nx);
+  c->twy_d = L.take<cx<double>>(sizeof(cx<double>) * c->ny);
+  c->kxd_f = L.take<float>(sizeof(float) * c->H);
+  c->kyd_f = L.take<float>(sizeof(float) * c->ny);
+  c->hx_f = L.take<float>(sizeof(float) * (c->H + 1));
+  c->hy_f = L.take<float>(sizeof(float) * c->ny);
+  c->kxd_d = L.take<double>(sizeof(double) * c->H);
+  c->kyd_d = L.take<double>(sizeof(double) * c->ny);
+  c->hx_d = L.take<double>(sizeof(double) * (c->H + 1));
+  c->hy_d = L.take<double>(sizeof(double) * c->ny);
+}
+
+int check_grid(const hc_grid* g) {
+  if (!g || g->dim != 2) return HC_EINVAL;
+  if (!is_pow2_in(g->n[0], 8, 4096) || !is_pow2_in(g->n[1], 8, 4096) || g->n[2] != 1)
+    return HC_EINVAL;
+  if (!(g->L[0] > 0) || !(g->L[1] > 0) || !std::isfinite(g->L[0]) || !std::isfinite(g->L[1]))
+    return HC_EINVAL;
+  return HC_OK;
+}
+
+int check_params(const hc_params* p) {
+  if (!p) return HC_EINVAL;
+  if (p->precision != HC_FP64_PLAIN && p->precision != HC_FP32_REFINED) return HC_EINVAL;
+  if (!std::isfinite(p->c) || !std::isfinite(p->D) || !std::isfinite(p->gamma) ||
+      !std::isfinite(p->dt) || p->dt < 0)
+    return HC_EINVAL;
+  return HC_OK;
+}
+
+template <typename T>
+void fill_geo(hc_ctx* c, hc::Geo<T>& g, const cx<T>* twx, const cx<T>* twy, const T* kxd,
+              const T* kyd, const T* hx, const T* hy) {
+  g.nx = c->nx;
+  g.ny = c->ny;
+  g.H = c->H;
+  g.lnx = ilog2(c->nx);
+  g.lny = ilog2(c->ny);
+  g.lH = ilog2(c->H);
+  // column CTA: tc packed columns x ny/8 threads, at most 512 threads
+  int tc = 512 >> (g.lny - 3);
+  if (tc < 1) tc = 1;
+  if (tc > 32) tc = 32;
+  if (tc > c->H) tc = c->H;
+  g.tc = tc;
+  g.ltc = ilog2(tc);
+  // row CTA: rpc rows x nx/8 threads, about 256 threads
+  int rpc = 256 >> (g.lnx - 3);
+  if (rpc < 1) rpc = 1;
+  if (rpc > c->ny) rpc = c->ny;
+  g.rpc = rpc;
+  g.lrpc = ilog2(rpc);
+  g.twx = twx;
+  g.twy = twy;
+  g.kxd = kxd;
+  g.kyd = kyd;
+  g.hx = hx;
+  g.hy = hy;
+  g.partials = c->partials;
+  g.npartials = (int)std::max<size_t>({(size_t)c->H, (size_t)c->ny, (size_t)1216});
+}
+
+// Most recent CUDA failure seen by this library on the calling thread.
+thread_local char g_last_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char* call, int line) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "hc_api.cu:%d %s -> %s (%s)", line, call,
+                cudaGetErrorName(e), cudaGetErrorString(e));
+  return HC_ECUDA;
+}
+
+#define CU(x)                                                   \
+  do {                                                          \
+    cudaError_t e_ = (x);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x, __LINE__);  \
+  } while (0)
+
+int upload_tables(hc_ctx* c) {
+  std::vector<double> re, im;
+  auto put_tw = [&](int N, cx<float>* df, cx<double>* dd) -> int {
+    twiddles(N, re, im);
+    std::vector<cx<float>> hf(N);
+    std::vector<cx<double>> hd(N);
+    for (int m = 0; m < N; ++m) {
+      hf[m].x = (float)re[m];
+      hf[m].y = (float)im[m];
+      hd[m].x = re[m];
+      hd[m].y = im[m];
+    }
+    CU(cudaMemcpy(df, hf.data(), sizeof(cx<float>) * N, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dd, hd.data(), sizeof(cx<double>) * N, cudaMemcpyHostToDevice));
+    return HC_OK;
+  };
+  int rc = put_tw(c->nx, c->twx_f, c->twx_d);
+  if (rc) return rc;
+  rc = put_tw(c->ny, c->twy_f, c->twy_d);
+  if (rc) return rc;
+  std::vector<double> kx(c->H), ky(c->ny);
+  for (int k = 0; k < c->H; ++k) kx[k] = (k == 0) ? 0.0 : xid(k, c->nx, c->grid.L[0]);
+  for (int k = 0; k < c->ny; ++k) ky[k] = xid(k, c->ny, c->grid.L[1]);
+  std::vector<float> kxf(kx.begin(), kx.end()), kyf(ky.begin(), ky.end());
+  CU(cudaMemcpy(c->kxd_d, kx.data(), sizeof(double) * c->H, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->kyd_d, ky.data(), sizeof(double) * c->ny, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->kxd_f, kxf.data(), sizeof(float) * c->H, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->kyd_f, kyf.data(), sizeof(float) * c->ny, cudaMemcpyHostToDevice));
+  return HC_OK;
+}
+
+// Heat factors exp(-D^2 xi^2 dt) per axis (eq. diffusion_space_discrete); the
+// 2D factor is their product.
+int upload_heat(hc_ctx* c) {
+  const double D2dt = c->prm.D * c->prm.D * c->prm.dt;
+  std::vector<double> hx(c->H + 1), hy(c->ny);
+  for (int k = 0; k <= c->H; ++k) {
+    const double x = xi(k, c->nx, c->grid.L[0]);
+    hx[k] = std::exp(-D2dt * x * x);
+  }
+  for (int k = 0; k < c->ny; ++k) {
+    const double y = xi(k, c->ny, c->grid.L[1]);
+    hy[k] = std::exp(-D2dt * y * y);
+  }
+  std::vector<float> hxf(hx.begin(), hx.end()), hyf(hy.begin(), hy.end());
+  CU(cudaMemcpyAsync(c->hx_d, hx.data(), sizeof(double) * (c->H + 1), cudaMemcpyHostToDevice,
+                     c->stream));
+  CU(cudaMemcpyAsync(c->hy_d, hy.data(), sizeof(double) * c->ny, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->hx_f, hxf.data(), sizeof(float) * (c->H + 1), cudaMemcpyHostToDevice,
+                     c->stream));
+  CU(cudaMemcpyAsync(c->hy_f, hyf.data(), sizeof(float) * c->ny, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));  // host vectors die here
+  return HC_OK;
+}
+
+hc::SplitCoef split_coef(const hc_params& p) {
+  hc::SplitCoef s;
+  s.c2dt = p.c * p.c * p.dt;
+  s.gamma = p.gamma;
+  s.dt = p.dt;
+  s.exp_mdt = std::exp(-p.dt);
+  s.gamma_is_one = (p.gamma == 1.0) ? 1 : 0;
+  s.two1mg_dt = 2.0 * (1.0 - p.gamma) * p.dt;
+  s.pow_a = 2.0 * (1.0 - p.gamma);
+  s.pow_b = s.gamma_is_one ? 0.0 : 1.0 / (2.0 * (1.0 - p.gamma));
+  return s;
+}
+
+void apply_defaults(hc_params& p) {
+  if (!(p.cg_rtol > 0)) p.cg_rtol = 1e-7;
+  if (p.cg_maxit <= 0) p.cg_maxit = 1000;
+  if (!(p.inner_rtol > 0)) p.inner_rtol = 1e-4;
+  if (p.max_sweeps <= 0) p.max_sweeps = 10;
+}
+
+int push_config(hc_ctx* c) {
+  hc::SolveConfig cfg;
+  cfg.outer_thresh2_rel = c->prm.cg_rtol * c->prm.cg_rtol;
+  cfg.inner_rtol2 = c->prm.inner_rtol * c->prm.inner_rtol;
+  cfg.user_kappa = c->prm.kappa > 0 ? c->prm.kappa : 0.0;
+  cfg.mean_r = c->mean_r;
+  cfg.maxit = c->prm.cg_maxit;
+  cfg.max_sweeps = c->prm.max_sweeps;
+  cfg.graph_mode = 0;  // set true only while a graph runs
+  cfg.refined = c->refined;
+  hc::set_config(c->st, cfg, c->stream);
+  c->launches += 1;
+  CU(cudaGetLastError());
+  return HC_OK;
+}
+
+// ---------------------------------------------------------------- step pieces
+// r = b - A x0 in FP64 plain mode; initialises the CG state.
+void plain_init(hc_ctx* c) {
+  auto& g = c->gd;
+  cx<double>* Gx = c->G64;
+  cx<double>* Gy = c->G64 + (size_t)c->ny * c->H;
+  hc::col_grad<double, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy, c->st, 0,
+                               c->stream);
+  hc::row_apply<double, double>(g, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1],
+                                (const double*)c->rf, Gx, Gy, nullptr, c->stream);
+  hc::col_div<double>(g, hc::CD_RESID, Gx, Gy, nullptr, c->b64, c->r64, nullptr, nullptr, c->st,
+                      c->stream);
+  c->launches += 3;
+}
+
+void plain_iter(hc_ctx* c) {
+  auto& g = c->gd;
+  cx<double>* Gx = c->G64;
+  cx<double>* Gy = c->G64 + (size_t)c->ny * c->H;
+  hc::col_grad<double, double>(g, hc::CG_DUPDATE, (cx<double>*)nullptr, c->r64, c->d64, nullptr, Gx,
+                               Gy, c->st, 1, c->stream);
+  hc::row_apply<double, double>(g, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1],
+                                (const double*)c->rf, Gx, Gy, c->st, c->stream);
+  hc::col_div<double>(g, hc::CD_CG, Gx, Gy, c->d64, nullptr, c->q64, nullptr, nullptr, c->st,
+                      c->stream);
+  hc::cg_update<double>(g, c->p64, c->r64, c->d64, c->q64, c->st, c->stream);
+  c->launches += 4;
+}
+
+// FP64 residual S - A p64 (after p64 += delta) and inner-CG initialisation.
+void refined_resid(hc_ctx* c) {
+  auto& g = c->gd;
+  cx<double>* Gx = c->G64;
+  cx<double>* Gy = c->G64 + (size_t)c->ny * c->H;
+  hc::col_grad<double, double>(g, hc::CG_ADDDELTA, c->p64, nullptr, nullptr, c->x32, Gx, Gy, c->st,
+                               0, c->stream);
+  hc::row_apply<double, float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1],
+                               (const float*)c->rf, Gx, Gy, nullptr, c->stream);
+  hc::col_div<double>(g, hc::CD_RESID_REFINE, Gx, Gy, nullptr, c->b64, c->r64, c->r32, c->x32,
+                      c->st, c->stream);
+  c->launches += 3;
+}
+
+void refined_iter(hc_ctx* c) {
+  auto& g = c->gf;
+  cx<float>* Gx = c->G32;
+  cx<float>* Gy = c->G32 + (size_t)c->ny * c->H;
+  hc::col_grad<float, float>(g, hc::CG_DUPDATE, (cx<float>*)nullptr, c->r32, c->d32, nullptr, Gx,
+                             Gy, c->st, 1, c->stream);
+  hc::row_apply<float, float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1],
+                              (const float*)c->rf, Gx, Gy, c->st, c->stream);
+  hc::col_div<float>(g, hc::CD_CG, Gx, Gy, c->d32, nullptr, c->q32, nullptr, nullptr, c->st,
+                     c->stream);
+  hc::cg_update<float>(g, c->x32, c->r32, c->d32, c->q32, c->st, c->stream);
+  c->launches += 4;
+}
+
+// Step 2 of Algorithm 1: gradient of the new p, activation + relaxation,
+// diffusion, back to physical m (and sum |m|^2 for the next kappa).
+template <typename T>
+void split_step_t(hc_ctx* c, hc::Geo<T>& g, cx<T>* G) {
+  cx<T>* Gx = G;
+  cx<T>* Gy = G + (size_t)c->ny * c->H;
+  hc::col_grad<T, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy, c->st, 0,
+                          c->stream);
+  hc::row_split<T>(g, Gx, Gy, (const T*)c->m[0], (const T*)c->m[1], Gx, Gy, split_coef(c->prm),
+                   c->st, c->stream);
+  hc::col_heat<T>(g, Gx, Gy, c->stream);
+  hc::row_c2r<T>(g, Gx, Gy, (T*)c->m[0], (T*)c->m[1], c->st, 1, c->stream);
+  c->launches += 4;
+}
+
+void split_step(hc_ctx* c) {
+  if (c->refined)
+    split_step_t<float>(c, c->gf, c->G32);
+  else
+    split_step_t<double>(c, c->gd, c->G64);
+}
+
+int read_state(hc_ctx* c) {
+  CU(cudaMemcpyAsync(c->st_host, c->st, sizeof(hc::SolveState), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+// Launch CG iterations in chunks until the device says done.
+int run_cg_host(hc_ctx* c, bool refined_inner) {
+  for (int guard = 0; guard < 1000000; guard += kChunk) {
+    for (int k = 0; k < kChunk; ++k) {
+      if (refined_inner)
+        refined_iter(c);
+      else
+        plain_iter(c);
+    }
+    CU(cudaGetLastError());
+    int rc = read_state(c);
+    if (rc) return rc;
+    if (c->st_host->done) return HC_OK;
+  }
+  return HC_ETIMEOUT;
+}
+
+int step_host(hc_ctx* c) {
+  hc::step_begin(c->st, (int)c->n, c->stream);
+  c->launches += 1;
+  if (!c->refined) {
+    plain_init(c);
+    int rc = run_cg_host(c, false);
+    if (rc) return rc;
+  } else {
+    for (int sweep = 0;; ++sweep) {
+      refined_resid(c);
+      int rc = read_state(c);
+      if (rc) return rc;
+      if (c->st_host->outer_done) break;
+      rc = run_cg_host(c, true);
+      if (rc) return rc;
+      if (sweep > 1000) return HC_ETIMEOUT;
+    }
+  }
+  split_step(c);
+  hc::step_end(c->st, c->refined, c->stream);
+  c->launches += 1;
+  CU(cudaGetLastError());
+  return HC_OK;
+}
+
+// ---------------------------------------------------------------- graph mode
+// One graph per context: step_begin, [plain: init residual, WHILE(cg) body]
+// or [refined: WHILE(outer){ residual, WHILE(inner) body }], split step,
+// step_end.  Loop conditions are set by the kernels (cudaGraphSetConditional)
+// and default to 0 at every launch, so a loop whose controlling kernel did not
+// run is skipped rather than repeated: step_begin opens the refinement loop,
+// the residual kernels open the CG loop, cg_update keeps it open while the
+// iteration cap and tolerance allow.
+int build_graph_on(hc_ctx* c);
+
+int build_graph(hc_ctx* c) {
+  if (!c->cap_stream) CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  // everything issued before the capture must be complete: the private stream
+  // does not order against the context's stream
+  CU(cudaStreamSynchronize(c->stream));
+  cudaStream_t keep = c->stream;
+  c->stream = c->cap_stream;
+  long long before = c->launches;
+  int rc = build_graph_on(c);
+  c->stream = keep;
+  c->launches = before;  // capture launched nothing
+  if (rc) {
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(c->cap_stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(c->cap_stream, &junk);
+      if (junk) cudaGraphDestroy(junk);
+    }
+    cudaGetLastError();
+  }
+  return rc;
+}
+
+int build_graph_on(hc_ctx* c) {
+  cudaGraph_t graph;
+  CU(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h_inner = 0, h_outer = 0;
+  // capture the straight-line prefix
+  cudaStream_t s = c->stream;
+  CU(cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  hc::step_begin(c->st, (int)c->n, s);
+  c->launches += 1;
+  if (!c->refined) plain_init(c);
+  CU(cudaStreamEndCapture(s, &graph));
+  // the loop node(s), appended after the current sink of the graph
+  auto sink_of = [&](cudaGraph_t gr, cudaGraphNode_t& out) -> int {
+    size_t nn = 0;
+    CU(cudaGraphGetNodes(gr, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CU(cudaGraphGetNodes(gr, nodes.data(), &nn));
+    out = nullptr;
+    for (auto nd : nodes) {
+      size_t nout = 0;
+      CU(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nout));
+      if (nout == 0) out = nd;
+    }
+    return HC_OK;
+  };
+  cudaGraphNode_t tail;
+  if (sink_of(graph, tail)) return HC_ECUDA;
+  cudaGraph_t loop_owner = graph;
+  cudaGraphNode_t loop_node;
+  cudaGraph_t body;
+  if (c->refined) {
+    CU(cudaGraphConditionalHandleCreate(&h_outer, graph, 0, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams op = {};
+    op.type = cudaGraphNodeTypeConditional;
+    op.conditional.handle = h_outer;
+    op.conditional.type = cudaGraphCondTypeWhile;
+    op.conditional.size = 1;
+    CU(cudaGraphAddNode(&loop_node, graph, &tail, nullptr, 1, &op));
+    cudaGraph_t obody = op.conditional.phGraph_out[0];
+    CU(cudaStreamBeginCaptureToGraph(s, obody, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    refined_resid(c);
+    CU(cudaStreamEndCapture(s, &obody));
+    cudaGraphNode_t otail;
+    if (sink_of(obody, otail)) return HC_ECUDA;
+    CU(cudaGraphConditionalHandleCreate(&h_inner, obody, 0, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_inner;
+    ip.conditional.type = cudaGraphCondTypeWhile;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    CU(cudaGraphAddNode(&inode, obody, &otail, nullptr, 1, &ip));
+    body = ip.conditional.phGraph_out[0];
+    loop_owner = graph;
+  } else {
+    CU(cudaGraphConditionalHandleCreate(&h_inner, graph, 0, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_inner;
+    ip.conditional.type = cudaGraphCondTypeWhile;
+    ip.conditional.size = 1;
+    CU(cudaGraphAddNode(&loop_node, graph, &tail, nullptr, 1, &ip));
+    body = ip.conditional.phGraph_out[0];
+  }
+  CU(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  if (c->refined)
+    refined_iter(c);
+  else
+    plain_iter(c);
+  CU(cudaStreamEndCapture(s, &body));
+  // suffix: split step and step end, after the loop node
+  CU(cudaStreamBeginCaptureToGraph(s, loop_owner, &loop_node, nullptr, 1,
+                                   cudaStreamCaptureModeThreadLocal));
+  split_step(c);
+  hc::step_end(c->st, c->refined, s);
+  c->launches += 1;
+  CU(cudaStreamEndCapture(s, &graph));
+  CU(cudaGraphInstantiate(&c->gexec, graph, 0));
+  CU(cudaGraphDestroy(graph));
+  c->graph_nodes_fixed = c->refined ? 1 + 4 + 1 : 1 + 3 + 4 + 1;
+  c->graph_nodes_body = 4;
+  c->graph_nodes_outer = 3;
+  // hand the handles to the kernels
+  CU(cudaMemcpy(&c->st->h_inner, &h_inner, sizeof(h_inner), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(&c->st->h_outer, &h_outer, sizeof(h_outer), cudaMemcpyHostToDevice));
+  c->graph_ready = true;
+  return HC_OK;
+}
+
+int set_graph_mode(hc_ctx* c, int on) {
+  int v = on ? 1 : 0;
+  CU(cudaMemcpyAsync(&c->st->graph_mode, &v, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+int fill_stats(hc_ctx* c, hc_step_stats* out) {
+  const hc::SolveState& h = *c->st_host;
+  if (out) {
+    out->cg_iters = h.total_it;
+    out->refine_sweeps = h.sweeps;
+    const double r2 = c->refined ? h.outer_r2 : h.rnorm2;
+    out->rel_residual = h.outer_b2 > 0 ? std::sqrt(r2 / h.outer_b2) : 0.0;
+    out->kappa = h.kappa;
+    out->status = h.step_status;
+  }
+  return HC_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+
+extern "C" {
+
+const char* hc_strerror(int code) {
+  switch (code) {
+    case HC_OK: return "ok";
+    case HC_EINVAL: return "invalid argument";
+    case HC_ENOMEM: return "out of device memory or workspace too small";
+    case HC_ECUDA: return "CUDA runtime error";
+    case HC_ENOCONV: return "CG did not reach the tolerance within its iteration cap";
+    case HC_ENONFINITE: return "non-finite value in p or m";
+    case HC_ETIMEOUT: return "bounded wait gave up";
+    case HC_ENOTSUP: return "not supported by this build";
+    default: return "unknown error";
+  }
+}
+
+int hc_workspace_size(const hc_grid* grid, const hc_params* params, size_t* bytes) {
+  if (check_grid(grid) || check_params(params) || !bytes) return HC_EINVAL;
+  hc_ctx tmp;
+  std::memset(&tmp, 0, sizeof(tmp));
+  tmp.grid = *grid;
+  tmp.nx = grid->n[0];
+  tmp.ny = grid->n[1];
+  tmp.H = tmp.nx / 2;
+  tmp.n = (size_t)tmp.nx * tmp.ny;
+  tmp.refined = params->precision == HC_FP32_REFINED;
+  Layout L;
+  layout(&tmp, L);
+  *bytes = (L.off + kAlign - 1) / kAlign * kAlign;
+  return HC_OK;
+}
+
+int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* workspace,
+              size_t workspace_bytes) {
+  if (!out) return HC_EINVAL;
+  *out = nullptr;
+  if (check_grid(grid) || check_params(params)) return HC_EINVAL;
+  if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return HC_EINVAL;
+  size_t need = 0;
+  hc_workspace_size(grid, params, &need);
+  if (workspace && workspace_bytes < need) return HC_ENOMEM;
+  hc_ctx* c = new (std::nothrow) hc_ctx;
+  if (!c) return HC_ENOMEM;
+  std::memset(c, 0, sizeof(*c));
+  c->grid = *grid;
+  c->prm = *params;
+  apply_defaults(c->prm);
+  c->nx = grid->n[0];
+  c->ny = grid->n[1];
+  c->H = c->nx / 2;
+  c->n = (size_t)c->nx * c->ny;
+  c->refined = params->precision == HC_FP32_REFINED;
+  c->stream = (cudaStream_t)params->stream;
+  c->mean_r = 1.0;
+  if (workspace) {
+    c->ws = workspace;
+    c->ws_bytes = workspace_bytes;
+    c->owns_ws = false;
+  } else {
+    if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+      delete c;
+      return HC_ENOMEM;
+    }
+    c->ws_bytes = need;
+    c->owns_ws = true;
+  }
+  if (cudaMallocHost(&c->st_host, sizeof(hc::SolveState)) != cudaSuccess) {
+    if (c->owns_ws) cudaFree(c->ws);
+    delete c;
+    return HC_ENOMEM;
+  }
+  Layout L;
+  L.base = static_cast<char*>(c->ws);
+  layout(c, L);
+  fill_geo<float>(c, c->gf, c->twx_f, c->twy_f, c->kxd_f, c->kyd_f, c->hx_f, c->hy_f);
+  fill_geo<double>(c, c->gd, c->twx_d, c->twy_d, c->kxd_d, c->kyd_d, c->hx_d, c->hy_d);
+  hc::set_smem_limits_f32();
+  hc::set_smem_limits_f64();
+  int rc = HC_OK;
+  if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess) rc = HC_ECUDA;
+  if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HC_ECUDA;
+  if (!rc) rc = upload_tables(c);
+  if (!rc) rc = upload_heat(c);
+  // r = 1 everywhere by default
+  if (!rc) {
+    std::vector<double> ones(c->n, 1.0);
+    rc = hc_set_r(c, ones.data(), c->n);
+  }
+  if (!rc) rc = push_config(c);
+  if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HC_ECUDA;
+  if (rc) {
+    hc_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return HC_OK;
+}
+
+void hc_destroy(hc_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  if (c->graph_ready) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->owns_ws && c->ws) cudaFree(c->ws);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  delete c;
+}
+
+int hc_set_params(hc_ctx* c, const hc_params* p) {
+  if (!c || check_params(p)) return HC_EINVAL;
+  if (p->precision != c->prm.precision || p->stream != c->prm.stream) return HC_EINVAL;
+  hc_params np = *p;
+  apply_defaults(np);
+  c->prm = np;
+  int rc = upload_heat(c);
+  if (!rc) rc = push_config(c);
+  if (!rc && c->graph_ready) {
+    // split coefficients are baked into the graph's kernel parameters
+    cudaGraphExecDestroy(c->gexec);
+    c->graph_ready = false;
+  }
+  return rc;
+}
+
+int hc_set_r(hc_ctx* c, const double* r, size_t count) {
+  if (!c || !r || count != c->n) return HC_EINVAL;
+  double s = 0;
+  for (size_t i = 0; i < count; ++i) {
+    if (!(r[i] > 0) || !std::isfinite(r[i])) return HC_EINVAL;
+    s += r[i];
+  }
+  CU(cudaMemcpyAsync(c->stage, r, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+  if (c->refined)
+    hc::convert<float, double>(c->stage, (float*)c->rf, count, c->stream);
+  else
+    hc::convert<double, double>(c->stage, (double*)c->rf, count, c->stream);
+  c->launches += 1;
+  c->mean_r = s / (double)count;
+  int rc = push_config(c);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+// Forward 2D transform of the FP64 field in stage -> projected FP64 spectrum.
+static int forward64(hc_ctx* c, cx<double>* out, hc::SolveState* norm_into) {
+  cx<double>* rows = c->G64;
+  hc::row_r2c<double>(c->gd, c->stage, nullptr, rows, nullptr, c->stream);
+  hc::col_fwd<double>(c->gd, rows, nullptr, out, nullptr, 1, 1, norm_into, c->stream);
+  c->launches += 2;
+  CU(cudaGetLastError());
+  return HC_OK;
+}
+
+int hc_set_source(hc_ctx* c, const double* S, size_t count) {
+  if (!c || !S || count != c->n) return HC_EINVAL;
+  for (size_t i = 0; i < count; ++i)
+    if (!std::isfinite(S[i])) return HC_EINVAL;
+  CU(cudaMemcpyAsync(c->stage, S, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+  int rc = forward64(c, c->b64, c->st);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+int hc_set_p(hc_ctx* c, const double* p, size_t count) {
+  if (!c || !p || count != c->n) return HC_EINVAL;
+  CU(cudaMemcpyAsync(c->stage, p, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+  int rc = forward64(c, c->p64, nullptr);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+int hc_set_m(hc_ctx* c, const double* m, size_t count) {
+  if (!c || !m || count != 2 * c->n) return HC_EINVAL;
+  CU(cudaMemcpyAsync(c->stage, m, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+  if (c->refined) {
+    hc::convert<float, double>(c->stage, (float*)c->m[0], c->n, c->stream);
+    hc::convert<float, double>(c->stage + c->n, (float*)c->m[1], c->n, c->stream);
+    hc::msum<float>(c->gf, (const float*)c->m[0], (const float*)c->m[1], c->st, c->stream);
+  } else {
+    hc::convert<double, double>(c->stage, (double*)c->m[0], c->n, c->stream);
+    hc::convert<double, double>(c->stage + c->n, (double*)c->m[1], c->n, c->stream);
+    hc::msum<double>(c->gd, (const double*)c->m[0], (const double*)c->m[1], c->st, c->stream);
+  }
+  c->launches += 3;
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+int hc_get_m(hc_ctx* c, double* out, size_t count) {
+  if (!c || !out || count != 2 * c->n) return HC_EINVAL;
+  if (c->refined) {
+    hc::convert<double, float>((const float*)c->m[0], c->stage, c->n, c->stream);
+    hc::convert<double, float>((const float*)c->m[1], c->stage + c->n, c->n, c->stream);
+  } else {
+    hc::convert<double, double>((const double*)c->m[0], c->stage, c->n, c->stream);
+    hc::convert<double, double>((const double*)c->m[1], c->stage + c->n, c->n, c->stream);
+  }
+  c->launches += 2;
+  CU(cudaMemcpyAsync(out, c->stage, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+int hc_get_p(hc_ctx* c, double* out, size_t count) {
+  if (!c || !out || count != c->n) return HC_EINVAL;
+  cx<double>* rows = c->G64;
+  hc::col_inv<double>(c->gd, c->p64, rows, 1.0 / (double)c->n, c->stream);
+  hc::row_c2r<double>(c->gd, rows, nullptr, c->stage, nullptr, nullptr, 0, c->stream);
+  c->launches += 2;
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(out, c->stage, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+int hc_step(hc_ctx* c, int nsteps, hc_step_stats* last) {
+  if (!c || nsteps < 0) return HC_EINVAL;
+  if (nsteps == 0) return HC_OK;
+  hc::reset_accum(c->st, c->stream);
+  c->launches += 1;
+  if (c->prm.use_graph) {
+    if (!c->graph_ready) {
+      int rc = build_graph(c);
+      if (rc) return rc;
+    }
+    int rc = set_graph_mode(c, 1);
+    if (rc) return rc;
+    for (int k = 0; k < nsteps; ++k) CU(cudaGraphLaunch(c->gexec, c->stream));
+    rc = read_state(c);
+    int rc2 = set_graph_mode(c, 0);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    const hc::SolveState& h = *c->st_host;
+    // kernels that ran: fixed nodes per step, body per CG iteration, outer body per sweep + 1
+    c->launches += (long long)c->graph_nodes_fixed * nsteps + (long long)c->graph_nodes_body * h.acc_iters;
+    if (c->refined) c->launches += (long long)c->graph_nodes_outer * (h.acc_sweeps + nsteps);
+  } else {
+    for (int k = 0; k < nsteps; ++k) {
+      int rc = step_host(c);
+      if (rc) return rc;
+      rc = read_state(c);
+      if (rc) return rc;
+      if (c->st_host->step_status == HC_ENONFINITE) break;
+    }
+  }
+  int rc = read_state(c);
+  if (rc) return rc;
+  fill_stats(c, last);
+  return c->st_host->first_bad;
+}
+
+int hc_gradient(hc_ctx* c, double* out, size_t count) {
+  if (!c || !out || count != 2 * c->n) return HC_EINVAL;
+  if (c->refined) {
+    cx<float>* Gx = c->G32;
+    cx<float>* Gy = c->G32 + (size_t)c->ny * c->H;
+    hc::col_grad<float, double>(c->gf, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy,
+                                c->st, 0, c->stream);
+    hc::row_c2r<float>(c->gf, Gx, Gy, (float*)Gx, (float*)Gy, nullptr, 0, c->stream);
+    hc::convert<double, float>((const float*)Gx, c->stage, c->n, c->stream);
+    hc::convert<double, float>((const float*)Gy, c->stage + c->n, c->n, c->stream);
+    c->launches += 4;
+  } else {
+    cx<double>* Gx = c->G64;
+    cx<double>* Gy = c->G64 + (size_t)c->ny * c->H;
+    hc::col_grad<double, double>(c->gd, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy,
+                                 c->st, 0, c->stream);
+    hc::row_c2r<double>(c->gd, Gx, Gy, c->stage, c->stage + c->n, nullptr, 0, c->stream);
+    c->launches += 2;
+  }
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(out, c->stage, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+int hc_apply_operator(hc_ctx* c, const double* f, double* out, size_t count) {
+  if (!c || !f || !out || count != c->n) return HC_EINVAL;
+  CU(cudaMemcpyAsync(c->stage, f, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+  if (c->refined) {
+    auto& g = c->gf;
+    cx<float>* Gx = c->G32;
+    cx<float>* Gy = c->G32 + (size_t)c->ny * c->H;
+    float* fp = reinterpret_cast<float*>(c->q32);
+    hc::convert<float, double>(c->stage, fp, c->n, c->stream);
+    hc::row_r2c<float>(g, fp, nullptr, Gx, nullptr, c->stream);
+    hc::col_fwd<float>(g, Gx, nullptr, c->d32, nullptr, 1, 1, nullptr, c->stream);
+    hc::col_grad<float, float>(g, hc::CG_PLAIN, c->d32, nullptr, nullptr, nullptr, Gx, Gy, c->st, 0,
+                               c->stream);
+    hc::row_apply<float, float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1],
+                                (const float*)c->rf, Gx, Gy, nullptr, c->stream);
+    hc::col_div<float>(g, hc::CD_PLAIN, Gx, Gy, nullptr, nullptr, c->q32, nullptr, nullptr, nullptr,
+                       c->stream);
+    hc::col_inv<float>(g, c->q32, Gx, 1.0f / (float)c->n, c->stream);
+    hc::row_c2r<float>(g, Gx, nullptr, fp, nullptr, nullptr, 0, c->stream);
+    hc::convert<double, float>(fp, c->stage, c->n, c->stream);
+    c->launches += 9;
+  } else {
+    auto& g = c->gd;
+    cx<double>* Gx = c->G64;
+    cx<double>* Gy = c->G64 + (size_t)c->ny * c->H;
+    hc::row_r2c<double>(g, c->stage, nullptr, Gx, nullptr, c->stream);
+    hc::col_fwd<double>(g, Gx, nullptr, c->d64, nullptr, 1, 1, nullptr, c->stream);
+    hc::col_grad<double, double>(g, hc::CG_PLAIN, c->d64, nullptr, nullptr, nullptr, Gx, Gy, c->st,
+                                 0, c->stream);
+    hc::row_apply<double, double>(g, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1],
+                                  (const double*)c->rf, Gx, Gy, nullptr, c->stream);
+    hc::col_div<double>(g, hc::CD_PLAIN, Gx, Gy, nullptr, nullptr, c->q64, nullptr, nullptr,
+                        nullptr, c->stream);
+    hc::col_inv<double>(g, c->q64, Gx, 1.0 / (double)c->n, c->stream);
+    hc::row_c2r<double>(g, Gx, nullptr, c->stage, nullptr, nullptr, 0, c->stream);
+    c->launches += 7;
+  }
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(out, c->stage, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+int hc_split_step(hc_ctx* c) {
+  if (!c) return HC_EINVAL;
+  split_step(c);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+int hc_spectrum(hc_ctx* c, const double* f, double* out, size_t count) {
+  if (!c || !f || !out || count != c->n) return HC_EINVAL;
+  CU(cudaMemcpyAsync(c->stage, f, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+  const size_t ns = (size_t)c->ny * c->H;
+  if (c->refined) {
+    auto& g = c->gf;
+    float* fp = reinterpret_cast<float*>(c->q32);
+    hc::convert<float, double>(c->stage, fp, c->n, c->stream);
+    hc::row_r2c<float>(g, fp, nullptr, c->G32, nullptr, c->stream);
+    hc::col_fwd<float>(g, c->G32, nullptr, c->d32, nullptr, 1, 0, nullptr, c->stream);
+    hc::convert<double, float>(reinterpret_cast<const float*>(c->d32), c->stage, 2 * ns, c->stream);
+    c->launches += 4;
+  } else {
+    auto& g = c->gd;
+    hc::row_r2c<double>(g, c->stage, nullptr, c->G64, nullptr, c->stream);
+    hc::col_fwd<double>(g, c->G64, nullptr, reinterpret_cast<cx<double>*>(c->stage), nullptr, 1, 0,
+                        nullptr, c->stream);
+    c->launches += 2;
+  }
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(out, c->stage, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+const char* hc_last_cuda_error(void) { return g_last_error; }
+
+int hc_launch_count(const hc_ctx* c, long long* count) {
+  if (!c || !count) return HC_EINVAL;
+  *count = c->launches;
+  return HC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// hc_internal.cuh -- types shared by the kernel translation units and the host
+// orchestration of the Hu-Cai spectral step (arXiv 2606.06720, Section 2).
+//
+// Spectral layout ("packed half spectrum").  A real nx x ny field f with 2D DFT
+// F[ky][kx] is stored as ny rows of H = nx/2 complex values:
+//   P[ky][kx] = F[ky][kx]                     for 1 <= kx < H,
+//   P[ky][0]  = F[ky][0] + i F[ky][H]         (the two real-in-x columns packed).
+// A row-transformed field (x transformed, y not yet) uses the same packing row
+// by row.  Every spectral vector is the unnormalised DFT; physical fields are
+// row-major with x fastest.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hc {
+
+// Complex value with the size and alignment of float2 / double2, so loads and
+// stores compile to single vector memory instructions.
+template <typename T>
+struct alignas(2 * sizeof(T)) cx {
+  T x, y;
+};
+
+// Device-resident scalar state of one pressure solve (CG and refinement).
+// All reductions that feed it are computed in FP64 by the last CTA of the
+// producing kernel, summing the per-CTA partials in a fixed order.
+struct SolveState {
+  double alpha, beta, rho;   // CG scalars
+  double rnorm2;             // ||r||^2 of the CG recursion (spectral weights)
+  double bnorm2;             // ||b||^2 of the right-hand side of the running CG
+  double thresh2;            // CG stops when rnorm2 <= thresh2
+  double kappa;              // preconditioner constant of this step
+  double mean_r;             // mean of r (set with r)
+  double msum;               // sum |m|^2 of the current m
+  double outer_r2;           // refined: ||S - A p64||^2 at the last FP64 evaluation
+  double outer_b2;           // ||S||^2 (spectral weights)
+  double outer_thresh2;      // refined: (cg_rtol ||S||)^2
+  double inner_rtol2;        // refined: inner reduction factor squared
+  double user_kappa;         // > 0: fixed kappa
+  double outer_rtol2;        // cg_rtol^2
+  int refined;               // 1: FP32 inner CG with FP64 refinement
+  int pad0_;
+  int it;                    // CG iterations of the running solve
+  int maxit;                 // cap
+  int done;                  // running CG finished (converged or capped)
+  int first;                 // next d-update is d = z (no previous direction)
+  int status;                // 0, HC_ENOCONV, HC_ENONFINITE of the running solve
+  int total_it;              // refined: iterations summed over sweeps
+  int sweeps;                // refined: inner solves run in this step
+  int outer_done;            // refined: FP64 residual below the tolerance
+  int max_sweeps;
+  int nonfinite;             // set when the split step produced a non-finite m
+  int step_status;           // status of the last completed step
+  int graph_mode;            // 1: kernels drive the conditional nodes below
+  int first_bad;             // first non-OK step status since the last reset
+  int acc_iters;             // CG iterations summed over the steps since the last reset
+  int acc_sweeps;            // refinement sweeps summed likewise
+  int acc_steps;             // steps completed since the last reset
+  unsigned long long h_inner;  // cudaGraphConditionalHandle of the CG loop
+  unsigned long long h_outer;  // cudaGraphConditionalHandle of the refinement loop
+  unsigned int ticket[8];    // last-CTA tickets, one per reduction site
+};
+
+// Values the host changes between steps (tolerances, caps, r statistics).
+struct SolveConfig {
+  double outer_thresh2_rel;  // cg_rtol^2 (multiplied by ||S||^2 on the device)
+  double inner_rtol2;
+  double user_kappa;
+  double mean_r;
+  int maxit;
+  int max_sweeps;
+  int graph_mode;
+  int refined;
+};
+
+// Reduction sites (ticket indices).
+enum { TK_DIV = 0, TK_UPDATE = 1, TK_RESID = 2, TK_MSUM = 3, TK_PROJ = 4 };
+
+// Geometry and tables for one precision.
+template <typename T>
+struct Geo {
+  int nx, ny, H;             // H = nx/2 packed columns
+  int lnx, lny, lH;          // log2 of the above
+  int tc, ltc;               // packed columns per column-kernel CTA
+  int rpc, lrpc;             // rows per row-kernel CTA
+  const cx<T>* twx;          // exp(-2 pi i m / nx), m < nx
+  const cx<T>* twy;          // exp(-2 pi i m / ny), m < ny
+  const T* kxd;              // first-derivative wavenumbers along x for kx < H (Nyquist reading: 0 at kx = 0 packed)
+  const T* kyd;              // first-derivative wavenumbers along y, ky < ny, 0 at ky = ny/2
+  const T* hx;               // heat factor exp(-D^2 xi_x^2 dt), kx = 0..H (H + 1 entries)
+  const T* hy;               // heat factor exp(-D^2 xi_y^2 dt), ky < ny
+  double* partials;          // per-CTA FP64 partial sums, 4 per CTA
+  int npartials;             // capacity in CTAs
+};
+
+// Split-step coefficients (Section 2.3), precomputed on the host in FP64.
+struct SplitCoef {
+  double c2dt;       // c^2 dt
+  double gamma;
+  double dt;
+  double exp_mdt;    // exp(-dt), the gamma = 1 branch
+  double two1mg_dt;  // 2 (1 - gamma) dt
+  double pow_a;      // 2 (1 - gamma)
+  double pow_b;      // 1 / (2 (1 - gamma))
+  int gamma_is_one;
+};
+
+// Column-kernel modes.
+enum ColGradMode { CG_PLAIN = 0, CG_DUPDATE = 1, CG_ADDDELTA = 2 };
+enum ColDivMode { CD_PLAIN = 0, CD_CG = 1, CD_RESID = 2, CD_RESID_REFINE = 3 };
+
+// ---------------- launchers (defined per precision) ----------------
+// Row pass, forward: physical pair (a, b) -> packed row spectra (A, B). b/B may be null.
+template <typename T>
+void row_r2c(const Geo<T>& g, const T* a, const T* b, cx<T>* A, cx<T>* B, cudaStream_t s);
+// Row pass, inverse: packed row spectra -> physical pair; optional sum(a^2+b^2) into st->msum.
+template <typename T>
+void row_c2r(const Geo<T>& g, const cx<T>* A, const cx<T>* B, T* a, T* b, SolveState* st,
+             int kappa_update, cudaStream_t s);
+// Row pass of the operator apply: C2R(gx, gy) -> q = (m.g) m + r g -> R2C(q).
+template <typename T, typename Tm>
+void row_apply(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const Tm* mx, const Tm* my,
+               const Tm* r, cx<T>* Qx, cx<T>* Qy, const SolveState* st, cudaStream_t s);
+// Row pass of the split step: C2R(grad p) -> activation -> relaxation -> R2C(m).
+template <typename T>
+void row_split(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const T* mx, const T* my,
+               cx<T>* Mx, cx<T>* My, SplitCoef cf, SolveState* st, cudaStream_t s);
+// Column pass, forward FFT along y of nv (1|2) row-transformed fields; optional
+// projection + ||.||^2 of field 0 into st->outer_b2 (project=1).
+template <typename T>
+void col_fwd(const Geo<T>& g, const cx<T>* in0, const cx<T>* in1, cx<T>* out0, cx<T>* out1, int nv,
+             int project, SolveState* st, cudaStream_t s);
+// Column pass, inverse FFT along y of one spectrum, times `scale`.
+template <typename T>
+void col_inv(const Geo<T>& g, const cx<T>* in, cx<T>* out, T scale, cudaStream_t s);
+// Column pass of the gradient: G_x = IFFT_y(i kx P / n), G_y = IFFT_y(i ky P / n).
+//   CG_PLAIN:    P = in (Tin may be double while T is float)
+//   CG_DUPDATE:  d = M^-1 r + beta d (d = M^-1 r when st->first), stored to dio; P = d
+//   CG_ADDDELTA: P = in + delta (FP64 accumulate), stored back to in; P used for the gradient
+template <typename T, typename Tin>
+void col_grad(const Geo<T>& g, int mode, cx<Tin>* in, const cx<T>* rvec, cx<T>* dio,
+              const cx<float>* delta, cx<T>* Gx, cx<T>* Gy, SolveState* st, int check_done,
+              cudaStream_t s);
+// Column pass of the divergence: q = -i (kx FFT_y(Qx) + ky FFT_y(Qy)).
+//   CD_PLAIN:        out = q
+//   CD_CG:           out = q; <d, q> -> alpha = rho / <d,q>
+//   CD_RESID:        out (r) = b - q; ||r||^2, <r, M^-1 r> -> CG initialisation
+//   CD_RESID_REFINE: as CD_RESID in FP64 plus r32 = float(r), delta = 0, and the
+//                    outer convergence test
+template <typename T>
+void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const cx<T>* d,
+             const cx<T>* b, cx<T>* out, cx<float>* r32, cx<float>* delta32, SolveState* st,
+             cudaStream_t s);
+// Column pass of the diffusion: FFT_y, times exp(-D^2 |xi|^2 dt) / n, IFFT_y, in place.
+template <typename T>
+void col_heat(const Geo<T>& g, cx<T>* Mx, cx<T>* My, cudaStream_t s);
+// CG update: x += alpha d, r -= alpha q, then ||r||^2 and <r, M^-1 r> -> beta, stop test.
+template <typename T>
+void cg_update(const Geo<T>& g, cx<T>* x, cx<T>* r, const cx<T>* d, const cx<T>* q, SolveState* st,
+               cudaStream_t s);
+// Elementwise conversions and helpers.
+template <typename To, typename Ti>
+void convert(const Ti* in, To* out, size_t n, cudaStream_t s);
+template <typename T>
+void msum(const Geo<T>& g, const T* mx, const T* my, SolveState* st, cudaStream_t s);
+
+// Opt every kernel of one precision in to the full shared memory per block.
+void set_smem_limits_f32();
+void set_smem_limits_f64();
+// Solve bookkeeping (one thread): configuration, step start (counters, kappa,
+// thresholds), step end (stats and status accumulation), accumulator reset.
+void set_config(SolveState* st, SolveConfig cfg, cudaStream_t s);
+void step_begin(SolveState* st, int npts, cudaStream_t s);
+void step_end(SolveState* st, int refined, cudaStream_t s);
+void reset_accum(SolveState* st, cudaStream_t s);
+
+}  // namespace hc

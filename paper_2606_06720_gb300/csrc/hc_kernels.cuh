@@ -1,0 +1,989 @@
+// hc_kernels.cuh -- sm_103a kernels of one time step of the Fourier spectral
+// scheme for the periodic Hu-Cai system (arXiv 2606.06720, Section 2).
+//
+// A 2D transform is split into a row pass (length nx along the contiguous x
+// axis, one complex FFT per row carrying two real fields as re/im) and a column
+// pass (length ny along y over tiles of TC packed columns).  The passes carry
+// the scheme's pointwise work as fused prologues/epilogues:
+//   column pass "grad": multiply by i xi / n (eq. p_discrete, inner bracket)
+//   row pass "apply":   q = (m.g) m + r g  (eq. 1.1a tensor)
+//   column pass "div":  -i xi . q^        (eq. p_discrete, outer bracket)
+//   row pass "split":   activation + relaxation (eqs. m_activation_discrete,
+//                        m_relaxation_discrete)
+//   column pass "heat": exp(-D^2 |xi|^2 dt) (eq. diffusion_space_discrete)
+//
+// FFT: Stockham autosort, radix-8 passes (radix 4 or 2 for the last pass),
+// every thread holding 8 elements per transform.  Data arrive from and leave
+// for global memory in registers in the "canonical" order: thread j holds
+// elements j + s*N/8, s = 0..7, which is both the input order of the first pass
+// and the output order of the last one, so transforms chain through registers
+// and only the inner passes touch shared memory.  Shared-memory slabs insert
+// one pad element per 8 to break the stride-8 bank conflicts.
+#pragma once
+
+#include "hc_internal.cuh"
+#include "hc.h"
+
+namespace hc {
+
+// ------------------------------------------------------------------ complex
+template <typename T>
+__device__ __forceinline__ cx<T> cmk(T a, T b) {
+  cx<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return cmk<T>(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return cmk<T>(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return cmk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return cmk<T>(a.x * s, a.y * s); }
+// a * (S i), S = +-1
+template <int S, typename T>
+__device__ __forceinline__ cx<T> cmul_si(cx<T> a) {
+  return S > 0 ? cmk<T>(-a.y, a.x) : cmk<T>(a.y, -a.x);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> czero() { return cmk<T>((T)0, (T)0); }
+
+template <typename To, typename Ti>
+__device__ __forceinline__ cx<To> ccast(cx<Ti> a) { return cmk<To>((To)a.x, (To)a.y); }
+
+// Read-only-path load of a complex table entry.
+__device__ __forceinline__ cx<float> ldg(const cx<float>* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return cmk<float>(v.x, v.y);
+}
+__device__ __forceinline__ cx<double> ldg(const cx<double>* p) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return cmk<double>(v.x, v.y);
+}
+
+__device__ __forceinline__ float hc_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double hc_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float hc_pow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double hc_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float hc_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double hc_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ bool hc_finite(float x) { return isfinite(x); }
+__device__ __forceinline__ bool hc_finite(double x) { return isfinite(x); }
+
+// ------------------------------------------------------------------ small DFTs
+// Kernel exp(S 2 pi i n k / R); S = -1 forward, +1 inverse.
+template <int S, typename T>
+__device__ __forceinline__ void dft2(cx<T>& a, cx<T>& b) {
+  cx<T> t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <int S, typename T>
+__device__ __forceinline__ void dft4(cx<T>& a0, cx<T>& a1, cx<T>& a2, cx<T>& a3) {
+  cx<T> t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
+  cx<T> t3 = cmul_si<S>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+template <int S, typename T>
+__device__ __forceinline__ void dft8(cx<T>* v) {
+  cx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  cx<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<S>(e0, e1, e2, e3);
+  dft4<S>(o0, o1, o2, o3);
+  const T h = (T)0.70710678118654752440;  // cos(pi/4)
+  // W8 = (1 + S i)/sqrt(2); W8^2 = S i; W8^3 = (-1 + S i)/sqrt(2)
+  o1 = cmk<T>((o1.x - (T)S * o1.y) * h, (o1.y + (T)S * o1.x) * h);
+  o2 = cmul_si<S>(o2);
+  o3 = cmk<T>((-o3.x - (T)S * o3.y) * h, (-o3.y + (T)S * o3.x) * h);
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+
+__device__ __forceinline__ int padk(int e) { return e + (e >> 3); }
+
+// ------------------------------------------------------------------ FFT core
+// NV transforms of length N = 2^lN (lN >= 3), one per slab, computed by the
+// N/8 threads j = 0..N/8-1 of each transform.  v[q][s] holds element
+// j + s N/8 on entry (input) and on exit (output).  Element e of slab q lives
+// at sl[q][padk(e) * ks].  Every thread of the CTA must call this together.
+// tw[m] = exp(-2 pi i m / N); the inverse uses the conjugates.
+template <int S, int NV, typename T>
+__device__ __forceinline__ void fft_canon(cx<T> (&v)[NV][8], cx<T>* const* sl, int ks, int j,
+                                          int lN, const cx<T>* __restrict__ tw) {
+  const int N8 = 1 << (lN - 3);
+  int lNs = 0;
+  int rem = lN;
+#pragma unroll 1
+  while (true) {
+    if (rem >= 3) {
+      const int k = j & ((1 << lNs) - 1);
+      if (lNs > 0) {
+        const int step = k << (lN - 3 - lNs);  // k * N / (8 Ns)
+#pragma unroll
+        for (int r = 1; r < 8; ++r) {
+          cx<T> w = ldg(&tw[r * step]);
+          if (S > 0) w.y = -w.y;
+#pragma unroll
+          for (int q = 0; q < NV; ++q) v[q][r] = cmul(v[q][r], w);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NV; ++q) dft8<S>(v[q]);
+      if (rem == 3) return;  // last pass: output index j + r N/8 = slot r
+      const int base = ((j >> lNs) << (lNs + 3)) + k;  // Stockham expand(j, Ns, 8)
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int e = base + (r << lNs);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sl[q][padk(e) * ks] = v[q][r];
+      }
+      __syncthreads();
+      lNs += 3;
+      rem -= 3;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int e = j + s * N8;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q][s] = sl[q][padk(e) * ks];
+      }
+    } else if (rem == 2) {
+      // last pass, radix 4: butterflies jj = j + u N/8 (u = 0, 1) read/write
+      // elements jj + r N/4 = slot u + 2 r
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int jj = j + u * N8;
+        const int k = jj & ((1 << lNs) - 1);
+        const int step = k << (lN - 2 - lNs);
+#pragma unroll
+        for (int r = 1; r < 4; ++r) {
+          cx<T> w = ldg(&tw[r * step]);
+          if (S > 0) w.y = -w.y;
+#pragma unroll
+          for (int q = 0; q < NV; ++q) v[q][u + 2 * r] = cmul(v[q][u + 2 * r], w);
+        }
+#pragma unroll
+        for (int q = 0; q < NV; ++q) dft4<S>(v[q][u], v[q][u + 2], v[q][u + 4], v[q][u + 6]);
+      }
+      return;
+    } else {
+      // last pass, radix 2: butterflies jj = j + u N/8 (u = 0..3), slots u, u + 4
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int jj = j + u * N8;
+        const int k = jj & ((1 << lNs) - 1);
+        cx<T> w = ldg(&tw[k << (lN - 1 - lNs)]);
+        if (S > 0) w.y = -w.y;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          v[q][u + 4] = cmul(v[q][u + 4], w);
+          dft2<S>(v[q][u], v[q][u + 4]);
+        }
+      }
+      return;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ reductions
+// Block-reduce K doubles; thread 0 gets the block total.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K]) {
+  __shared__ double red[32 * K];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[warp * K + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0;
+      for (int w = 0; w < nw; ++w) s += red[w * K + k];
+      v[k] = s;
+    }
+  }
+}
+
+// Write this CTA's K partial sums; returns true (in every thread) in the CTA
+// that arrived last, which then holds the grand totals in tot (fixed order:
+// CTA 0, 1, 2, ...), and re-arms the ticket.
+template <int K>
+__device__ __forceinline__ bool last_cta_sum(double (&v)[K], double* partials,
+                                             unsigned int* ticket, double (&tot)[K]) {
+  __shared__ unsigned int s_last;
+  block_sum<K>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[blockIdx.x * 4 + k] = v[k];
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0;
+      for (unsigned int c = 0; c < gridDim.x; ++c) s += __ldcg(&partials[c * 4 + k]);
+      tot[k] = s;
+    }
+    *ticket = 0u;
+  }
+  return true;
+}
+
+// Preconditioner symbol 1 / (kappa |xi~|^2) of the constant-coefficient
+// operator (0 on the null modes).
+template <typename T>
+__device__ __forceinline__ T pinv_sym(const Geo<T>& g, int kx, int ky, T kappa) {
+  const T a = g.kxd[kx], b = g.kyd[ky];
+  const T s2 = a * a + b * b;
+  return s2 > (T)0 ? (T)1 / (kappa * s2) : (T)0;
+}
+
+// ------------------------------------------------------------------ row helpers
+// Element k of Z = A_full + i B_full, the spectrum of the complex row a + i b,
+// from the packed Hermitian half spectra A, B (B may be null: b = 0).
+template <typename T>
+__device__ __forceinline__ cx<T> load_pair_c2r(const cx<T>* __restrict__ A,
+                                               const cx<T>* __restrict__ B, int k, int H) {
+  if (k == 0 || k == H) {
+    cx<T> a = A[0], b = B ? B[0] : czero<T>();
+    return k == 0 ? cmk<T>(a.x, b.x) : cmk<T>(a.y, b.y);
+  }
+  if (k < H) {
+    cx<T> a = A[k], b = B ? B[k] : czero<T>();
+    return cmk<T>(a.x - b.y, a.y + b.x);  // A + i B
+  }
+  cx<T> a = A[2 * H - k], b = B ? B[2 * H - k] : czero<T>();
+  return cmk<T>(a.x + b.y, b.x - a.y);  // conj(A) + i conj(B)
+}
+
+// From the canonical-order spectrum Z of the complex row a + i b, write the
+// packed half spectra of a and b (B may be null).
+template <typename T>
+__device__ __forceinline__ void store_pair_r2c(cx<T> (&v)[1][8], cx<T>* slab, int j, int N, int H,
+                                               cx<T>* __restrict__ A, cx<T>* __restrict__ B) {
+  const int N8 = N >> 3;
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 8; ++s) slab[padk(j + s * N8)] = v[0][s];
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int k = j + s * N8;  // k < H
+    const cx<T> z = slab[padk(k)];
+    cx<T> a, b;
+    if (k == 0) {
+      const cx<T> zh = slab[padk(H)];
+      a = cmk<T>(z.x, zh.x);
+      b = cmk<T>(z.y, zh.y);
+    } else {
+      const cx<T> zc = slab[padk(N - k)];
+      a = cmk<T>((T)0.5 * (z.x + zc.x), (T)0.5 * (z.y - zc.y));
+      b = cmk<T>((T)0.5 * (z.y + zc.y), (T)-0.5 * (z.x - zc.x));
+    }
+    A[k] = a;
+    if (B) B[k] = b;
+  }
+}
+
+// ------------------------------------------------------------------ row kernels
+template <typename T>
+__global__ void __launch_bounds__(512) k_row_r2c(Geo<T> g, const T* __restrict__ a,
+                                                 const T* __restrict__ b, cx<T>* __restrict__ A,
+                                                 cx<T>* __restrict__ B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
+  const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
+  const int y = (blockIdx.x << g.lrpc) + rb;
+  cx<T>* slab = sm + rb * (N + (N >> 3));
+  cx<T>* const sl[1] = {slab};
+  const size_t ro = (size_t)y * N;
+  cx<T> v[1][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = j + s * N8;
+    v[0][s] = cmk<T>(a[ro + x], b ? b[ro + x] : (T)0);
+  }
+  fft_canon<-1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  store_pair_r2c(v, slab, j, N, H, A + (size_t)y * H, B ? B + (size_t)y * H : nullptr);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const cx<T>* B, T* a,
+                                                 T* b, SolveState* st,
+                                                 int kappa_update) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
+  const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
+  const int y = (blockIdx.x << g.lrpc) + rb;
+  cx<T>* slab = sm + rb * (N + (N >> 3));
+  cx<T>* const sl[1] = {slab};
+  const cx<T>* Ar = A + (size_t)y * H;
+  const cx<T>* Br = B ? B + (size_t)y * H : nullptr;
+  cx<T> v[1][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
+  fft_canon<+1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  const size_t ro = (size_t)y * N;
+  double acc[1] = {0.0};
+  bool finite = true;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = j + s * N8;
+    a[ro + x] = v[0][s].x;
+    if (b) b[ro + x] = v[0][s].y;
+    if (kappa_update) {
+      acc[0] += (double)v[0][s].x * (double)v[0][s].x + (double)v[0][s].y * (double)v[0][s].y;
+      finite = finite && hc_finite(v[0][s].x) && hc_finite(v[0][s].y);
+    }
+  }
+  if (kappa_update) {
+    if (!finite) st->nonfinite = 1;
+    double tot[1];
+    if (last_cta_sum<1>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
+      st->msum = tot[0];
+    }
+  }
+}
+
+template <typename T, typename Tm>
+__global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
+                                                   const Tm* __restrict__ mx,
+                                                   const Tm* __restrict__ my,
+                                                   const Tm* __restrict__ rr, cx<T>* Qx, cx<T>* Qy,
+                                                   const SolveState* __restrict__ st) {
+  if (st && st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
+  const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
+  const int y = (blockIdx.x << g.lrpc) + rb;
+  cx<T>* slab = sm + rb * (N + (N >> 3));
+  cx<T>* const sl[1] = {slab};
+  const cx<T>* Ar = Gx + (size_t)y * H;
+  const cx<T>* Br = Gy + (size_t)y * H;
+  cx<T> v[1][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
+  fft_canon<+1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  // v = grad p (gx + i gy) at x = j + s N/8: apply (m (x) m + r I)
+  const size_t ro = (size_t)y * N;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = j + s * N8;
+    const T gx = v[0][s].x, gy = v[0][s].y;
+    const T ax = (T)mx[ro + x], ay = (T)my[ro + x], r = (T)rr[ro + x];
+    const T mg = ax * gx + ay * gy;
+    v[0][s] = cmk<T>(ax * mg + r * gx, ay * mg + r * gy);
+  }
+  fft_canon<-1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  store_pair_r2c(v, slab, j, N, H, Qx + (size_t)y * H, Qy + (size_t)y * H);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_row_split(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
+                                                   const T* __restrict__ mx,
+                                                   const T* __restrict__ my, cx<T>* Mx, cx<T>* My,
+                                                   SplitCoef cf,
+                                                   SolveState* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
+  const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
+  const int y = (blockIdx.x << g.lrpc) + rb;
+  cx<T>* slab = sm + rb * (N + (N >> 3));
+  cx<T>* const sl[1] = {slab};
+  const cx<T>* Ar = Gx + (size_t)y * H;
+  const cx<T>* Br = Gy + (size_t)y * H;
+  cx<T> v[1][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
+  fft_canon<+1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  const size_t ro = (size_t)y * N;
+  const T c2dt = (T)cf.c2dt;
+  bool finite = true;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = j + s * N8;
+    const T gx = v[0][s].x, gy = v[0][s].y;
+    T ax = mx[ro + x], ay = my[ro + x];
+    // Activation, exact solution of dm/dt = c^2 (g g^T) m over dt written as
+    // m + c^2 dt phi1(c^2 |g|^2 dt) (m.g) g with phi1(z) = expm1(z)/z: the
+    // same value as eq. (m_activation_discrete) without forming exp(z) - 1.
+    const T mg = ax * gx + ay * gy;
+    if (mg != (T)0) {
+      const T z = c2dt * (gx * gx + gy * gy);
+      const T coef = z > (T)0 ? c2dt * (hc_expm1(z) / z) : c2dt;
+      const T t = coef * mg;
+      ax += t * gx;
+      ay += t * gy;
+    }
+    // Relaxation, eq. (m_relaxation_discrete).
+    if (cf.gamma_is_one) {
+      ax *= (T)cf.exp_mdt;
+      ay *= (T)cf.exp_mdt;
+    } else {
+      const T n2 = ax * ax + ay * ay;
+      if (n2 > (T)0) {
+        const T nm = hc_sqrt(n2);
+        const T bb = hc_pow(nm, (T)cf.pow_a) - (T)cf.two1mg_dt;
+        const T sc = bb >= (T)0 ? hc_pow(bb, (T)cf.pow_b) / nm : (T)0;
+        ax *= sc;
+        ay *= sc;
+      }
+    }
+    finite = finite && hc_finite(ax) && hc_finite(ay);
+    v[0][s] = cmk<T>(ax, ay);
+  }
+  if (!finite) st->nonfinite = 1;
+  fft_canon<-1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  store_pair_r2c(v, slab, j, N, H, Mx + (size_t)y * H, My + (size_t)y * H);
+}
+
+// ------------------------------------------------------------------ column kernels
+// Thread layout of a column CTA: b = packed column within the tile (fastest),
+// j = FFT thread index; slab q at sm + q * slab_elems + b with stride tc.
+struct ColIdx {
+  int b, j, kx, NY8;
+};
+template <typename T>
+__device__ __forceinline__ ColIdx col_idx(const Geo<T>& g) {
+  ColIdx c;
+  c.b = threadIdx.x & (g.tc - 1);
+  c.j = threadIdx.x >> g.ltc;
+  c.kx = (blockIdx.x << g.ltc) + c.b;
+  c.NY8 = 1 << (g.lny - 3);
+  return c;
+}
+template <typename T>
+__device__ __forceinline__ int slab_elems(const Geo<T>& g) {
+  return (g.ny + (g.ny >> 3)) * g.tc;
+}
+
+template <typename T, typename Tin, int MODE>
+__global__ void __launch_bounds__(512) k_col_grad(Geo<T> g, cx<Tin>* in, const cx<T>* __restrict__ rvec,
+                                                  cx<T>* dio, const cx<float>* __restrict__ delta,
+                                                  cx<T>* __restrict__ Gx, cx<T>* __restrict__ Gy,
+                                                  SolveState* st, int check_done) {
+  if (check_done && st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const ColIdx c = col_idx(g);
+  const int H = g.H;
+  const int se = slab_elems(g);
+  cx<T>* const sl[2] = {sm + c.b, sm + se + c.b};
+  const T invn = (T)(1.0 / ((double)g.nx * (double)g.ny));
+  const T ax = g.kxd[c.kx] * invn;
+  bool first = false, add_delta = false;
+  T beta = 0, kappa = 0;
+  if (MODE == CG_DUPDATE) {
+    first = st->first != 0;
+    beta = (T)st->beta;
+    kappa = (T)st->kappa;
+  }
+  if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
+  cx<T> v[2][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int ky = c.j + s * c.NY8;
+    const size_t idx = (size_t)ky * H + c.kx;
+    cx<T> P;
+    if constexpr (MODE == CG_PLAIN) {
+      P = ccast<T>(in[idx]);
+    } else if constexpr (MODE == CG_DUPDATE) {
+      const T pv = pinv_sym(g, c.kx, ky, kappa);
+      const cx<T> z = cscale(rvec[idx], pv);
+      P = first ? z : cadd(z, cscale(dio[idx], beta));
+      dio[idx] = P;
+    } else {
+      // FP64 correction accumulation p64 += delta (refinement)
+      P = ccast<T>(in[idx]);
+      if (add_delta) {
+        P = cadd(P, ccast<T>(delta[idx]));
+        in[idx] = ccast<Tin>(P);
+      }
+    }
+    const T ay = g.kyd[ky] * invn;
+    v[0][s] = cmk<T>(-ax * P.y, ax * P.x);  // i (kx/n) P
+    v[1][s] = cmk<T>(-ay * P.y, ay * P.x);  // i (ky/n) P
+  }
+  fft_canon<+1, 2>(v, sl, g.tc, c.j, g.lny, g.twy);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const size_t idx = (size_t)(c.j + s * c.NY8) * H + c.kx;
+    Gx[idx] = v[0][s];
+    Gy[idx] = v[1][s];
+  }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restrict__ Qx,
+                                                 const cx<T>* __restrict__ Qy,
+                                                 const cx<T>* __restrict__ d,
+                                                 const cx<T>* __restrict__ bvec,
+                                                 cx<T>* __restrict__ out, cx<float>* __restrict__ r32,
+                                                 cx<float>* __restrict__ delta32, SolveState* st) {
+  if (MODE == CD_CG && st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const ColIdx c = col_idx(g);
+  const int H = g.H;
+  const int se = slab_elems(g);
+  cx<T>* const sl[2] = {sm + c.b, sm + se + c.b};
+  cx<T> v[2][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const size_t idx = (size_t)(c.j + s * c.NY8) * H + c.kx;
+    v[0][s] = Qx[idx];
+    v[1][s] = Qy[idx];
+  }
+  fft_canon<-1, 2>(v, sl, g.tc, c.j, g.lny, g.twy);
+  const T ax = g.kxd[c.kx];
+  const double w = c.kx == 0 ? 1.0 : 2.0;  // Parseval weight of a packed column
+  double acc[3] = {0.0, 0.0, 0.0};
+  T kappa = 0;
+  if (MODE == CD_RESID || MODE == CD_RESID_REFINE) kappa = (T)st->kappa;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int ky = c.j + s * c.NY8;
+    const size_t idx = (size_t)ky * H + c.kx;
+    const T ay = g.kyd[ky];
+    const cx<T> t = cmk<T>(ax * v[0][s].x + ay * v[1][s].x, ax * v[0][s].y + ay * v[1][s].y);
+    const cx<T> q = cmk<T>(t.y, -t.x);  // -i (kx Qx + ky Qy)
+    if constexpr (MODE == CD_PLAIN) {
+      out[idx] = q;
+    } else if constexpr (MODE == CD_CG) {
+      out[idx] = q;
+      const cx<T> dv = d[idx];
+      acc[0] += w * ((double)dv.x * (double)q.x + (double)dv.y * (double)q.y);
+    } else if constexpr (MODE == CD_RESID) {
+      const cx<T> rv = csub(bvec[idx], q);
+      out[idx] = rv;
+      const double r2 = (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
+      acc[0] += w * r2;
+      acc[1] += w * r2 * (double)pinv_sym(g, c.kx, ky, kappa);
+    } else {
+      const cx<T> rv = csub(bvec[idx], q);
+      out[idx] = rv;
+      acc[0] += w * ((double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y);
+      const cx<float> rf = ccast<float>(rv);
+      r32[idx] = rf;
+      delta32[idx] = czero<float>();
+      const double r2f = (double)rf.x * (double)rf.x + (double)rf.y * (double)rf.y;
+      acc[1] += w * r2f;
+      acc[2] += w * r2f * (double)pinv_sym(g, c.kx, ky, kappa);
+    }
+  }
+  if constexpr (MODE == CD_PLAIN) return;
+  double tot[3];
+  if constexpr (MODE == CD_CG) {
+    double a1[1] = {acc[0]}, t1[1];
+    if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0) {
+      const double dq = t1[0];
+      if (dq > 0 && isfinite(dq)) {
+        st->alpha = st->rho / dq;
+      } else {
+        st->alpha = 0;
+        st->done = 1;
+        if (!isfinite(dq)) st->status = HC_ENONFINITE;
+      }
+      st->first = 0;
+    }
+  } else if constexpr (MODE == CD_RESID) {
+    double a2[2] = {acc[0], acc[1]}, t2[2];
+    if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0) {
+      st->rnorm2 = t2[0];
+      st->rho = t2[1];
+      st->it = 0;
+      st->first = 1;
+      st->status = 0;
+      st->done = (t2[0] <= st->thresh2 || st->maxit <= 0) ? 1 : 0;
+      if (!isfinite(t2[0])) {
+        st->status = HC_ENONFINITE;
+        st->done = 1;
+      }
+      if (st->graph_mode) cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
+    }
+  } else {
+    if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot) && threadIdx.x == 0) {
+      st->outer_r2 = tot[0];
+      const bool finite = isfinite(tot[0]);
+      const bool conv = tot[0] <= st->outer_thresh2;
+      st->outer_done = (conv || !finite || st->sweeps >= st->max_sweeps) ? 1 : 0;
+      if (!finite) st->status = HC_ENONFINITE;
+      else if (!conv && st->outer_done) st->status = HC_ENOCONV;
+      else st->status = 0;
+      // inner FP32 CG on A delta = r32 from delta = 0
+      st->bnorm2 = tot[1];
+      st->thresh2 = st->inner_rtol2 * tot[1];
+      st->rnorm2 = tot[1];
+      st->rho = tot[2];
+      st->it = 0;
+      st->first = 1;
+      st->done = (st->outer_done || tot[1] == 0.0) ? 1 : 0;
+      if (!st->outer_done) st->sweeps += 1;
+      if (st->graph_mode) {
+        cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
+        cudaGraphSetConditional(st->h_outer, st->outer_done ? 0u : 1u);
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My) {  // in place
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const ColIdx c = col_idx(g);
+  const int H = g.H, ny = g.ny;
+  const int se = slab_elems(g);
+  cx<T>* const sl[2] = {sm + c.b, sm + se + c.b};
+  cx<T> v[2][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const size_t idx = (size_t)(c.j + s * c.NY8) * H + c.kx;
+    v[0][s] = Mx[idx];
+    v[1][s] = My[idx];
+  }
+  fft_canon<-1, 2>(v, sl, g.tc, c.j, g.lny, g.twy);
+  const T invn = (T)(1.0 / ((double)g.nx * (double)ny));
+  if (blockIdx.x == 0) {
+    // The packed column holds kx = 0 (A) and kx = nx/2 (B) as A + iB; their heat
+    // factors differ, so separate with the ky <-> -ky symmetry:
+    // new = (h0 + hN)/2 P[ky] + (h0 - hN)/2 conj(P[-ky]).
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int e = padk(c.j + s * c.NY8) * g.tc;
+      sl[0][e] = v[0][s];
+      sl[1][e] = v[1][s];
+    }
+    __syncthreads();
+    if (c.b == 0) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int ky = c.j + s * c.NY8;
+        const int kn = (ny - ky) & (ny - 1);
+        const T h0 = g.hx[0] * g.hy[ky] * invn, hN = g.hx[H] * g.hy[ky] * invn;
+        const T hp = (T)0.5 * (h0 + hN), hm = (T)0.5 * (h0 - hN);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const cx<T> pn = sl[q][padk(kn) * g.tc];
+          v[q][s] = cmk<T>(hp * v[q][s].x + hm * pn.x, hp * v[q][s].y - hm * pn.y);
+        }
+      }
+    }
+  }
+  if (c.kx != 0) {
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const T h = g.hx[c.kx] * g.hy[c.j + s * c.NY8] * invn;
+      v[0][s] = cscale(v[0][s], h);
+      v[1][s] = cscale(v[1][s], h);
+    }
+  }
+  fft_canon<+1, 2>(v, sl, g.tc, c.j, g.lny, g.twy);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const size_t idx = (size_t)(c.j + s * c.NY8) * H + c.kx;
+    Mx[idx] = v[0][s];
+    My[idx] = v[1][s];
+  }
+}
+
+template <typename T, int NV>
+__global__ void __launch_bounds__(512) k_col_fwd(Geo<T> g, const cx<T>* __restrict__ in0,
+                                                 const cx<T>* __restrict__ in1, cx<T>* out0,
+                                                 cx<T>* out1, int project, SolveState* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const ColIdx c = col_idx(g);
+  const int H = g.H;
+  const int se = slab_elems(g);
+  cx<T>* const sl[2] = {sm + c.b, sm + se + c.b};
+  cx<T> v[NV][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const size_t idx = (size_t)(c.j + s * c.NY8) * H + c.kx;
+    v[0][s] = in0[idx];
+    if (NV > 1) v[NV - 1][s] = in1[idx];
+  }
+  fft_canon<-1, NV>(v, sl, g.tc, c.j, g.lny, g.twy);
+  double acc[1] = {0.0};
+  const double w = c.kx == 0 ? 1.0 : 2.0;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int ky = c.j + s * c.NY8;
+    const size_t idx = (size_t)ky * H + c.kx;
+    if (project && c.kx == 0 && (ky == 0 || ky == (g.ny >> 1))) v[0][s] = czero<T>();  // corner modes
+    out0[idx] = v[0][s];
+    if (NV > 1) out1[idx] = v[NV - 1][s];
+    acc[0] += w * ((double)v[0][s].x * (double)v[0][s].x + (double)v[0][s].y * (double)v[0][s].y);
+  }
+  if (project && st) {
+    double tot[1];
+    if (last_cta_sum<1>(acc, g.partials, &st->ticket[TK_PROJ], tot) && threadIdx.x == 0)
+      st->outer_b2 = tot[0];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_col_inv(Geo<T> g, const cx<T>* __restrict__ in,
+                                                 cx<T>* __restrict__ out, T scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const ColIdx c = col_idx(g);
+  const int H = g.H;
+  cx<T>* const sl[1] = {sm + c.b};
+  cx<T> v[1][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) v[0][s] = in[(size_t)(c.j + s * c.NY8) * H + c.kx];
+  fft_canon<+1, 1>(v, sl, g.tc, c.j, g.lny, g.twy);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) out[(size_t)(c.j + s * c.NY8) * H + c.kx] = cscale(v[0][s], scale);
+}
+
+// ------------------------------------------------------------------ CG update
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_update(Geo<T> g, cx<T>* __restrict__ x,
+                                                   cx<T>* __restrict__ r,
+                                                   const cx<T>* __restrict__ d,
+                                                   const cx<T>* __restrict__ q, SolveState* st) {
+  if (st->done) {
+    if (st->graph_mode && blockIdx.x == 0 && threadIdx.x == 0)
+      cudaGraphSetConditional(st->h_inner, 0u);
+    return;
+  }
+  const T alpha = (T)st->alpha;
+  const T kappa = (T)st->kappa;
+  const size_t total = (size_t)g.ny * g.H;
+  double acc[2] = {0.0, 0.0};
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i & (size_t)(g.H - 1));
+    const int ky = (int)(i >> g.lH);
+    const cx<T> dv = d[i];
+    const cx<T> xv = x[i], qv = q[i];
+    cx<T> rv = r[i];
+    x[i] = cmk<T>(xv.x + alpha * dv.x, xv.y + alpha * dv.y);
+    rv = cmk<T>(rv.x - alpha * qv.x, rv.y - alpha * qv.y);
+    r[i] = rv;
+    const double w = kx == 0 ? 1.0 : 2.0;
+    const double r2 = w * ((double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y);
+    acc[0] += r2;
+    acc[1] += r2 * (double)pinv_sym(g, kx, ky, kappa);
+  }
+  double tot[2];
+  if (last_cta_sum<2>(acc, g.partials, &st->ticket[TK_UPDATE], tot) && threadIdx.x == 0) {
+    const double rho_new = tot[1];
+    st->rnorm2 = tot[0];
+    st->beta = st->rho > 0 ? rho_new / st->rho : 0.0;
+    st->rho = rho_new;
+    st->it += 1;
+    st->total_it += 1;
+    if (!isfinite(tot[0])) {
+      st->status = HC_ENONFINITE;
+      st->done = 1;
+    } else if (tot[0] <= st->thresh2) {
+      st->done = 1;
+    } else if (st->it >= st->maxit) {
+      st->done = 1;
+      st->status = HC_ENOCONV;
+    }
+    if (st->graph_mode) cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
+  }
+}
+
+// ------------------------------------------------------------------ elementwise
+template <typename To, typename Ti>
+__global__ void k_convert(const Ti* __restrict__ in, To* __restrict__ out, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (To)in[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_msum(Geo<T> g, const T* __restrict__ mx,
+                                              const T* __restrict__ my, SolveState* st) {
+  const size_t n = (size_t)g.nx * g.ny;
+  double acc[1] = {0.0};
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    acc[0] += (double)mx[i] * (double)mx[i] + (double)my[i] * (double)my[i];
+  double tot[1];
+  if (last_cta_sum<1>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
+    st->msum = tot[0];
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+static inline int row_threads(const Geo<T>& g) { return g.rpc << (g.lnx - 3); }
+template <typename T>
+static inline size_t row_smem(const Geo<T>& g) {
+  return (size_t)g.rpc * (g.nx + (g.nx >> 3)) * sizeof(cx<T>);
+}
+template <typename T>
+static inline int col_threads(const Geo<T>& g) { return g.tc << (g.lny - 3); }
+template <typename T>
+static inline size_t col_smem(const Geo<T>& g, int nv) {
+  return (size_t)nv * (g.ny + (g.ny >> 3)) * g.tc * sizeof(cx<T>);
+}
+static inline int upd_blocks(size_t total) {
+  size_t b = (total + 255) / 256;
+  return (int)(b < 1216 ? b : 1216);  // 8 CTAs of 256 threads per SM on 152 SMs
+}
+
+template <typename T>
+void row_r2c(const Geo<T>& g, const T* a, const T* b, cx<T>* A, cx<T>* B, cudaStream_t s) {
+  k_row_r2c<T><<<g.ny >> g.lrpc, row_threads(g), row_smem(g), s>>>(g, a, b, A, B);
+}
+template <typename T>
+void row_c2r(const Geo<T>& g, const cx<T>* A, const cx<T>* B, T* a, T* b, SolveState* st,
+             int kappa_update, cudaStream_t s) {
+  k_row_c2r<T><<<g.ny >> g.lrpc, row_threads(g), row_smem(g), s>>>(g, A, B, a, b, st, kappa_update);
+}
+template <typename T, typename Tm>
+void row_apply(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const Tm* mx, const Tm* my,
+               const Tm* r, cx<T>* Qx, cx<T>* Qy, const SolveState* st, cudaStream_t s) {
+  k_row_apply<T, Tm><<<g.ny >> g.lrpc, row_threads(g), row_smem(g), s>>>(g, Gx, Gy, mx, my, r, Qx,
+                                                                         Qy, st);
+}
+template <typename T>
+void row_split(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const T* mx, const T* my,
+               cx<T>* Mx, cx<T>* My, SplitCoef cf, SolveState* st, cudaStream_t s) {
+  k_row_split<T><<<g.ny >> g.lrpc, row_threads(g), row_smem(g), s>>>(g, Gx, Gy, mx, my, Mx, My, cf,
+                                                                     st);
+}
+template <typename T>
+void col_fwd(const Geo<T>& g, const cx<T>* in0, const cx<T>* in1, cx<T>* out0, cx<T>* out1, int nv,
+             int project, SolveState* st, cudaStream_t s) {
+  if (nv == 1)
+    k_col_fwd<T, 1><<<g.H >> g.ltc, col_threads(g), col_smem(g, 1), s>>>(g, in0, in1, out0, out1,
+                                                                          project, st);
+  else
+    k_col_fwd<T, 2><<<g.H >> g.ltc, col_threads(g), col_smem(g, 2), s>>>(g, in0, in1, out0, out1,
+                                                                          project, st);
+}
+template <typename T>
+void col_inv(const Geo<T>& g, const cx<T>* in, cx<T>* out, T scale, cudaStream_t s) {
+  k_col_inv<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 1), s>>>(g, in, out, scale);
+}
+template <typename T, typename Tin>
+void col_grad(const Geo<T>& g, int mode, cx<Tin>* in, const cx<T>* rvec, cx<T>* dio,
+              const cx<float>* delta, cx<T>* Gx, cx<T>* Gy, SolveState* st, int check_done,
+              cudaStream_t s) {
+  const int nb = g.H >> g.ltc, nt = col_threads(g);
+  const size_t sm = col_smem(g, 2);
+  if (mode == CG_PLAIN)
+    k_col_grad<T, Tin, CG_PLAIN><<<nb, nt, sm, s>>>(g, in, rvec, dio, delta, Gx, Gy, st, check_done);
+  else if (mode == CG_DUPDATE)
+    k_col_grad<T, Tin, CG_DUPDATE><<<nb, nt, sm, s>>>(g, in, rvec, dio, delta, Gx, Gy, st,
+                                                      check_done);
+  else
+    k_col_grad<T, Tin, CG_ADDDELTA><<<nb, nt, sm, s>>>(g, in, rvec, dio, delta, Gx, Gy, st,
+                                                       check_done);
+}
+template <typename T>
+void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const cx<T>* d,
+             const cx<T>* b, cx<T>* out, cx<float>* r32, cx<float>* delta32, SolveState* st,
+             cudaStream_t s) {
+  const int nb = g.H >> g.ltc, nt = col_threads(g);
+  const size_t sm = col_smem(g, 2);
+  switch (mode) {
+    case CD_PLAIN:
+      k_col_div<T, CD_PLAIN><<<nb, nt, sm, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
+      break;
+    case CD_CG:
+      k_col_div<T, CD_CG><<<nb, nt, sm, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
+      break;
+    case CD_RESID:
+      k_col_div<T, CD_RESID><<<nb, nt, sm, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
+      break;
+    default:
+      k_col_div<T, CD_RESID_REFINE><<<nb, nt, sm, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
+      break;
+  }
+}
+template <typename T>
+void col_heat(const Geo<T>& g, cx<T>* Mx, cx<T>* My, cudaStream_t s) {
+  k_col_heat<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 2), s>>>(g, Mx, My);
+}
+template <typename T>
+void cg_update(const Geo<T>& g, cx<T>* x, cx<T>* r, const cx<T>* d, const cx<T>* q, SolveState* st,
+               cudaStream_t s) {
+  k_cg_update<T><<<upd_blocks((size_t)g.ny * g.H), 256, 0, s>>>(g, x, r, d, q, st);
+}
+template <typename To, typename Ti>
+void convert(const Ti* in, To* out, size_t n, cudaStream_t s) {
+  k_convert<To, Ti><<<upd_blocks(n), 256, 0, s>>>(in, out, n);
+}
+template <typename T>
+void msum(const Geo<T>& g, const T* mx, const T* my, SolveState* st, cudaStream_t s) {
+  k_msum<T><<<upd_blocks((size_t)g.nx * g.ny), 256, 0, s>>>(g, mx, my, st);
+}
+
+// Allow a kernel the full opt-in shared memory of the device, less its own
+// static shared memory (the two together may not exceed the opt-in limit).
+template <typename K>
+void allow_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, kernel) != cudaSuccess) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       optin - (int)a.sharedSizeBytes);
+}
+
+template <typename T>
+void set_smem_limits_t() {
+  allow_smem(k_row_r2c<T>);
+  allow_smem(k_row_c2r<T>);
+  allow_smem(k_row_apply<T, T>);
+  allow_smem(k_row_split<T>);
+  allow_smem(k_col_fwd<T, 1>);
+  allow_smem(k_col_fwd<T, 2>);
+  allow_smem(k_col_inv<T>);
+  allow_smem(k_col_heat<T>);
+  allow_smem(k_col_div<T, CD_PLAIN>);
+  allow_smem(k_col_div<T, CD_CG>);
+  allow_smem(k_col_div<T, CD_RESID>);
+  allow_smem(k_col_div<T, CD_RESID_REFINE>);
+}
+template <typename T, typename Tin>
+void set_smem_limits_grad() {
+  allow_smem(k_col_grad<T, Tin, CG_PLAIN>);
+  allow_smem(k_col_grad<T, Tin, CG_DUPDATE>);
+  allow_smem(k_col_grad<T, Tin, CG_ADDDELTA>);
+}
+
+}  // namespace hc

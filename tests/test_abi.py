@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports
+every entry point declared in include/hc.h, and validates arguments on the
+host before touching the GPU.  No kernel runs here."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    path = __graft_entry__._builder().build()
+    return C.CDLL(path)
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "hc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hc_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["hc_create", "hc_set_r", "hc_set_source", "hc_set_m", "hc_set_p", "hc_step",
+                     "hc_get_p", "hc_get_m", "hc_destroy", "hc_strerror"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_workspace_size_without_gpu(lib):
+    from paper_2606_06720_gb300 import _binding as Bd
+    assert Bd.strerror(0) == "ok"
+    assert "invalid" in Bd.strerror(-1)
+    g = Bd.hc_grid(2, (C.c_int * 3)(64, 32, 1), (C.c_double * 3)(1.0, 1.0, 1.0))
+    for prec in (Bd.HC_FP64_PLAIN, Bd.HC_FP32_REFINED):
+        p = Bd.hc_params(10.0, 0.05, 0.75, 1e-3, 1e-10, 100, prec, 0.0, 1e-4, 10, 0, None)
+        nb = C.c_size_t()
+        assert Bd.hc_workspace_size(C.byref(g), C.byref(p), C.byref(nb)) == 0
+        assert nb.value > 64 * 32 * 8 * 6
+
+
+@pytest.mark.parametrize("n", [(12, 8), (4, 8), (8, 8192), (64, 0), (3, 3)])
+def test_invalid_grids_are_rejected_on_the_host(lib, n):
+    from paper_2606_06720_gb300 import _binding as Bd
+    g = Bd.hc_grid(2, (C.c_int * 3)(n[0], n[1], 1), (C.c_double * 3)(1.0, 1.0, 1.0))
+    p = Bd.hc_params(10.0, 0.05, 0.75, 1e-3, 1e-10, 100, 0, 0.0, 1e-4, 10, 0, None)
+    nb = C.c_size_t()
+    assert Bd.hc_workspace_size(C.byref(g), C.byref(p), C.byref(nb)) == Bd.HC_EINVAL
+    ctx = C.c_void_p()
+    assert Bd.hc_create(C.byref(ctx), C.byref(g), C.byref(p), None, 0) == Bd.HC_EINVAL
+    assert not ctx.value
+
+
+def test_invalid_params_are_rejected_on_the_host(lib):
+    from paper_2606_06720_gb300 import _binding as Bd
+    g = Bd.hc_grid(2, (C.c_int * 3)(16, 16, 1), (C.c_double * 3)(1.0, 1.0, 1.0))
+    ctx = C.c_void_p()
+    bad = [Bd.hc_params(10.0, 0.05, 0.75, 1e-3, 1e-10, 100, 7, 0.0, 1e-4, 10, 0, None),
+           Bd.hc_params(float("nan"), 0.05, 0.75, 1e-3, 1e-10, 100, 0, 0.0, 1e-4, 10, 0, None),
+           Bd.hc_params(10.0, 0.05, 0.75, -1.0, 1e-10, 100, 0, 0.0, 1e-4, 10, 0, None)]
+    for p in bad:
+        assert Bd.hc_create(C.byref(ctx), C.byref(g), C.byref(p), None, 0) == Bd.HC_EINVAL
+    # misaligned borrowed workspace
+    p = Bd.hc_params(10.0, 0.05, 0.75, 1e-3, 1e-10, 100, 0, 0.0, 1e-4, 10, 0, None)
+    assert Bd.hc_create(C.byref(ctx), C.byref(g), C.byref(p), C.c_void_p(4097), 1 << 30) == Bd.HC_EINVAL
+    # null context pointers
+    assert Bd.hc_step(None, 1, None) == Bd.HC_EINVAL
+    assert Bd.hc_set_r(None, None, 0) == Bd.HC_EINVAL

@@ -1,0 +1,130 @@
+"""GPU parity of the step's components against the FP64 oracle, through the
+C ABI: the 2D transform (row + column passes), the spectral gradient, the
+pressure operator of eq. (p_discrete), and the split substeps of Section 2.3.
+
+Sizes span several CTAs and both ragged shapes (nx != ny, Lx != Ly), the
+minimum FFT length 8 and the maximum 4096."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_common import hc, packed, rel_l2  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+RNG = np.random.default_rng(2024)
+TOL = {"fp64": 1e-12, "fp32_refined": 2e-6}
+
+SHAPES = [(8, 8), (16, 8), (8, 32), (64, 32), (32, 256), (256, 64), (512, 512), (4096, 8),
+          (8, 4096)]
+
+
+def solver(hc, n, L=(1.0, 1.0), precision="fp64", **kw):
+    args = dict(c=10.0, D=0.05, gamma=0.75, dt=1e-3)
+    args.update(kw)
+    return hc.Solver(n, L, precision=precision, **args)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
+@pytest.mark.parametrize("n", SHAPES + [(2048, 2048)])
+def test_spectrum_matches_oracle_transform(hc, precision, n):
+    g = O.Grid(n)
+    f = RNG.standard_normal(g.shape)
+    with solver(hc, n, precision=precision) as s:
+        P = s.spectrum(f)
+    ref = packed(O.fftn(g, f, -1))
+    assert rel_l2(P, ref) < TOL[precision] * (3 if n[0] * n[1] > 1 << 20 else 1)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
+@pytest.mark.parametrize("n,L", [((64, 32), (1.0, 0.5)), ((8, 8), (1.0, 1.0)),
+                                 ((256, 512), (2.0, 1.0)), ((4096, 8), (1.0, 1.0))])
+def test_gradient_matches_oracle(hc, precision, n, L):
+    g = O.Grid(n, L)
+    p = RNG.standard_normal(g.shape)
+    with solver(hc, n, L, precision=precision) as s:
+        s.set_p(p)
+        grad = s.gradient()
+        p_back = s.get_p()
+    pp = O.project(g, p)
+    assert rel_l2(p_back, pp) < 1e-13  # p is held in FP64 in both modes
+    assert rel_l2(grad, O.gradient(g, pp)) < TOL[precision] * 2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
+@pytest.mark.parametrize("n,L", [((64, 32), (1.0, 0.5)), ((16, 16), (1.0, 1.0)),
+                                 ((512, 256), (1.0, 2.0)), ((8, 4096), (1.0, 1.0)),
+                                 ((2048, 2048), (1.0, 1.0))])
+def test_operator_matches_oracle(hc, precision, n, L):
+    g = O.Grid(n, L)
+    m = RNG.uniform(0, 1, (2,) + g.shape)
+    r = W.smooth_r(n, 1, L)
+    f = RNG.standard_normal(g.shape)
+    with solver(hc, n, L, precision=precision) as s:
+        s.set_m(m)
+        s.set_r(r)
+        Af = s.apply_operator(f)
+    ref = O.apply_A(g, m, r, O.project(g, f))
+    assert rel_l2(Af, ref) < TOL[precision] * 5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
+@pytest.mark.parametrize("gamma", [0.5, 0.75, 1.0, 1.5])
+def test_split_step_matches_oracle(hc, precision, gamma):
+    """Step 2 of Algorithm 1 alone, with p given: activation with grad p,
+    relaxation, diffusion, including points with |m| = 0, b < 0 (extinction)
+    and grad p = 0 (p constant along rows)."""
+    n, L = (128, 64), (1.0, 0.5)
+    g = O.Grid(n, L)
+    X, Y = np.meshgrid(np.arange(n[0]) / n[0], np.arange(n[1]) * 0.5 / n[1])
+    # smooth part plus a little noise: c^2 |grad p|^2 dt stays O(1), the
+    # regime Remark 2.1 asks for (white noise of size 0.1 would push the
+    # activation exponent past FP32 range)
+    p = np.sin(2 * np.pi * X) * np.cos(4 * np.pi * Y) + 0.003 * RNG.standard_normal(g.shape)
+    m = RNG.uniform(-0.5, 0.5, (2,) + g.shape)
+    m[:, 3, :] = 0.0           # |m| = 0
+    m[:, 5, :] = 1e-4          # extinguished by relaxation when gamma < 1
+    c, D, dt = 3.0, 0.05, 2e-3
+    with solver(hc, n, L, precision=precision, c=c, D=D, gamma=gamma, dt=dt) as s:
+        s.set_p(p)
+        s.set_m(m)
+        s.split_step()
+        got = s.get_m()
+    pp = O.project(g, p)
+    mm = m if precision == "fp64" else m.astype(np.float32).astype(np.float64)
+    a = O.activation(mm, O.gradient(g, pp), c, dt)
+    b = O.relaxation(a, gamma, dt)
+    ref = O.diffusion(g, b, D, dt)
+    z = c * c * dt * (O.gradient(g, pp) ** 2).sum(0)
+    assert z.max() < 10 and np.abs(ref).max() < 1e3
+    assert rel_l2(got, ref) < (1e-12 if precision == "fp64" else 2e-6)
+
+
+def test_activation_overflow_is_reported(hc):
+    """Remark 2.1: exp(c^2 |grad p|^2 dt) must stay bounded; an FP32 overflow
+    surfaces as HC_ENONFINITE, not as silent garbage."""
+    n = (32, 32)
+    g = O.Grid(n)
+    X, Y = np.meshgrid(np.arange(32) / 32, np.arange(32) / 32)
+    S = W.minus_mean(np.sin(2 * np.pi * X))
+    with solver(hc, n, precision="fp32_refined", c=1e4, dt=1.0, gamma=1.0) as s:
+        s.set_r(np.full(g.shape, 0.1))
+        s.set_source(S)
+        s.set_m(np.full((2,) + g.shape, 0.3))
+        st = s.step(1, allow=(hc.HC_ENONFINITE,))
+    assert st.rc == hc.HC_ENONFINITE and st.status == hc.HC_ENONFINITE
+
+
+def test_bad_arguments_return_einval(hc):
+    with solver(hc, (16, 16)) as s:
+        import ctypes as C
+        from paper_2606_06720_gb300 import _binding as Bd
+        bad_r = np.full((16, 16), 0.1)
+        bad_r[2, 3] = 0.0
+        with pytest.raises(hc.HuCaiError) as e:
+            s.set_r(bad_r)
+        assert e.value.code == hc.HC_EINVAL
+        buf = np.zeros(10)
+        assert Bd.hc_set_m(s.ctx, buf.ctypes.data_as(C.POINTER(C.c_double)), 10) == hc.HC_EINVAL
+        assert Bd.hc_step(s.ctx, -1, None) == hc.HC_EINVAL
