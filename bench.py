@@ -1,0 +1,474 @@
+#!/usr/bin/env python3
+"""Throughput of one time step of the Fourier spectral FFT+CG splitting scheme
+for the periodic Hu-Cai system (arXiv 2606.06720, Algorithm 1) on GB300.
+
+Workload: the 2048^2 source/sink problem (smooth random r in [0.05, 0.15],
+S = +G(0.3,0.5) - G(0.7,0.5) with sigma 0.05, m0 ~ U[0, 0.5], c = 25,
+D = 0.02, gamma = 0.5, dt = 5e-4), FP32 operator/FFT/split step with the
+pressure solve wrapped in FP64 iterative refinement to a relative residual of
+1e-8.  A "step" is one pass of the loop body of Algorithm 1 (pressure solve +
+activation + relaxation + diffusion).  Metric: Mpoint-steps/s = nx*ny*steps /
+time / 1e6, summed over ranks (each rank runs an independent replica).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead (the reference arm; see cpu_baseline).  `--accuracy` runs the
+equal-accuracy calibration of the plain FP64 path and prints its summary.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoint-steps/s at 2048² FP32-refined vs FP64 plain at equal accuracy; HBM GB/s"
+UNIT = "Mpoint-steps/s"
+N_GRID = 2048
+CG_RTOL_REFINED = 1e-8      # the refined path's pressure tolerance
+FP64_EQUAL_RTOL = 1e-6      # loosest plain-FP64 tolerance reaching m rel. L2 <= 1e-5 at 100 steps
+                            # (calibrated with --accuracy)
+HBM_PEAK_FALLBACK = 6800.0  # GB/s, recipe fallback when MEASURED_PEAKS.json is absent
+FP64_PEAK_TFLOPS = 1.25     # nominal FP64 of GB300 (recipe table); a plain-ALU bound
+
+# Algorithmic bytes moved per launch of each step kernel, in units of n = nx*ny
+# points (F4 = 4n bytes: one FP32 field, physical or packed spectral; F8 = 8n).
+# Each input read once, each output written once; scalars and tables ignored.
+BYTES_PER_POINT = {
+    "fp32_refined": {
+        "cg_grad": 20,     # read r, d; write d, Gx, Gy          5 F4
+        "cg_apply": 28,    # read Gx, Gy, mx, my, r; write Qx, Qy 7 F4
+        "cg_div": 16,      # read Qx, Qy, d; write q              4 F4
+        "cg_update": 24,   # read x, r, d, q; write x, r          6 F4
+        "res_grad": 24,    # read p64; write Gx64, Gy64           3 F8
+        "res_apply": 44,   # read Gx64, Gy64 (2 F8), m, r (3 F4); write 2 F8
+        "res_div": 40,     # read Qx64, Qy64, b64; write r64 (4 F8) + r32, delta (2 F4)
+        "split_grad": 16,  # read p64 (F8); write Gx, Gy (2 F4)
+        "split_row": 24,   # read Gx, Gy, mx, my; write Mx, My    6 F4
+        "split_heat": 16,  # read Mx, My; write Mx, My            4 F4
+        "split_c2r": 16,   # read Mx, My; write mx, my            4 F4
+    },
+    "fp64": {
+        "cg_grad": 40, "cg_apply": 56, "cg_div": 32, "cg_update": 48, "res_grad": 24,
+        "res_apply": 56, "res_div": 32, "split_grad": 24, "split_row": 48, "split_heat": 32,
+        "split_c2r": 32,
+    },
+}
+FP64_KERNELS = {"fp32_refined": {"res_grad", "res_apply", "res_div"},
+                "fp64": set(BYTES_PER_POINT["fp64"])}
+
+
+def fft_flops_per_point(kernel: str, nx: int, ny: int) -> float:
+    """Algorithmic FLOPs per point and launch: 5 N log2 N per complex FFT of
+    length N (the usual FFT count), plus the pointwise algebra."""
+    lx, ly = math.log2(nx), math.log2(ny)
+    col2 = 5.0 * ly            # two length-ny complex FFTs over nx/2 columns
+    row1 = 5.0 * lx            # one length-nx complex FFT per row
+    return {
+        "cg_grad": col2 + 4, "res_grad": col2 + 2, "split_grad": col2 + 2,
+        "cg_apply": 2 * row1 + 9, "res_apply": 2 * row1 + 9,
+        "cg_div": col2 + 6, "res_div": col2 + 10,
+        "cg_update": 10, "split_row": 2 * row1 + 30, "split_heat": 2 * col2 + 3,
+        "split_c2r": row1 + 2,
+    }[kernel]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) taken while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = sorted(float(r[1]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows
+                                                          if r[3].replace(".", "").isdigit())}
+
+
+# ----------------------------------------------------------------- oracle (CPU)
+def oracle_steps(n: int, steps: int, warm: int = 1):
+    """Time `steps` oracle steps of the source/sink workload resampled at n^2,
+    after `warm` untimed steps (so the timed steps are warm-started like the
+    GPU's).  Returns (seconds, threads, cg_iters)."""
+    import numpy as np
+    import oracle as O
+    import workloads as W
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    w = W.source_sink_2d(n)
+    g = O.Grid(w.n, w.L)
+    prm = O.Params(c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, cg_rtol=CG_RTOL_REFINED, cg_maxit=2000)
+    m, p = w.m0.copy(), np.zeros(g.shape)
+    for _ in range(warm):
+        m, p, _ = O.step(g, prm, w.r, w.S, m, p)
+    t0 = time.perf_counter()
+    iters = 0
+    for _ in range(steps):
+        m, p, st = O.step(g, prm, w.r, w.S, m, p)
+        iters += st.cg_iters
+    return time.perf_counter() - t0, threads, iters
+
+
+def workload_config(extra: dict | None = None) -> dict:
+    cfg = {
+        "workload": "source_sink_2048: 2048x2048 periodic unit square, smooth random r in "
+                    "[0.05,0.15] (|k|<=8, seed 0), S=+G(0.3,0.5)-G(0.7,0.5) sigma 0.05 minus mean, "
+                    "m0~U[0,0.5] seed 0, c=25 D=0.02 gamma=0.5 dt=5e-4",
+        "precision": "FP32 FFT/operator/split step + FP64 iterative refinement of the pressure",
+        "cg_rtol": CG_RTOL_REFINED,
+        "grid": [N_GRID, N_GRID],
+        "l2": "inputs larger than L2 (refined working set ~390 MB > 129 MiB L2); no flush",
+        "loop_control": "one CUDA graph per step, CG/refinement loops as conditional WHILE nodes",
+        "parallelism": "replicas (one independent problem per GPU)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args) -> None:
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n = args.ref_n
+    K, Wm = args.steps, args.warmup
+    secs, threads, iters = oracle_steps(n, K, warm=max(Wm, 1))
+    value = n * n * K / secs / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": K, "warmup": Wm, "ms_per_step": secs / K * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"the same workload resampled at {n}x{n}; each timed step is one "
+                                   f"FP64 oracle step (warm-started, cg_rtol {CG_RTOL_REFINED})"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cg_iters_per_step": iters / K,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- accuracy calibration
+def run_accuracy(args) -> None:
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_2606_06720_gb300 as P
+    steps = args.acc_steps
+    w = W.source_sink_2d(N_GRID, steps=steps)
+
+    def run(precision, rtol):
+        with P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision=precision,
+                      cg_rtol=rtol, cg_maxit=5000) as s:
+            s.set_r(w.r)
+            s.set_source(w.S)
+            s.set_m(w.m0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = s.step(steps)
+            dt = time.perf_counter() - t0
+            return s.get_m(), s.get_p(), st, dt
+
+    m_ref, p_ref, st_ref, _ = run("fp64", 1e-13)
+    out = {"steps": steps, "reference": "FP64 plain GPU, cg_rtol 1e-13", "runs": []}
+
+    def err(m):
+        return float(np.linalg.norm(m - m_ref) / np.linalg.norm(m_ref))
+
+    for precision, rtol in [("fp32_refined", CG_RTOL_REFINED), ("fp32_refined", 1e-6),
+                            ("fp64", 1e-5), ("fp64", 1e-6), ("fp64", 1e-7), ("fp64", 1e-8)]:
+        m, p, st, secs = run(precision, rtol)
+        out["runs"].append({"precision": precision, "cg_rtol": rtol, "m_rel_l2": err(m),
+                            "mean_cg_iters": st.total_cg_iters / steps,
+                            "mpoint_steps_per_s": w.npts * steps / secs / 1e6})
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------- GB300 arm
+def run_gb300(args) -> None:
+    import numpy as np
+    import torch
+    import workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__._builder().build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_2606_06720_gb300 as P
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    w = W.source_sink_2d(N_GRID)
+    K, Wm = args.steps, args.warmup
+    s = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp32_refined",
+                 cg_rtol=CG_RTOL_REFINED, cg_maxit=2000, use_graph=not args.host_loop,
+                 device=str(dev))
+    s.set_r(w.r)
+    s.set_source(w.S)
+    s.set_m(w.m0)
+    if args.inner_rtol:
+        s.set_params(inner_rtol=args.inner_rtol)
+    from paper_2606_06720_gb300.autotune import autotune
+    s.step(1)  # realistic buffer contents for the tuner
+    tuning = autotune(s, reps=10) if not args.no_tune else s.get_tuning()
+    s.set_m(w.m0)
+    s.set_p(np.zeros(w.shape))
+    stream = s.stream
+    if Wm > 0:
+        s.step(Wm)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device-resident inputs
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = ("GPU-" + str(props.uuid)) if getattr(props, "uuid", None) else str(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = s.launch_count()
+    with ClockSampler(gpu_id) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        e0.record(stream)
+        st = s.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        barrier()
+    launches = s.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms)
+    npts = w.npts
+    value = world * npts * K / (ms_max / 1e3) / 1e6
+    iters_per_step = st.total_cg_iters / K
+    sweeps_per_step = st.total_sweeps / K
+
+    # ---- per-kernel durations (CUDA events around back-to-back launches, same data)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    counts = {"cg_grad": iters_per_step, "cg_apply": iters_per_step, "cg_div": iters_per_step,
+              "cg_update": iters_per_step, "res_grad": sweeps_per_step + 1,
+              "res_apply": sweeps_per_step + 1, "res_div": sweeps_per_step + 1, "split_grad": 1,
+              "split_row": 1, "split_heat": 1, "split_c2r": 1}
+    kernels = {}
+    bytes_step = 0.0
+    for name, cnt in counts.items():
+        kms = s.time_kernel(name, reps=args.kernel_reps)
+        bpp = BYTES_PER_POINT["fp32_refined"][name]
+        fpp = fft_flops_per_point(name, *w.n)
+        is64 = name in FP64_KERNELS["fp32_refined"]
+        gbs = bpp * npts / (kms / 1e3) / 1e9
+        tfl = fpp * npts / (kms / 1e3) / 1e12
+        kernels[name] = {"ms": kms, "launches_per_step": cnt, "ms_per_step": kms * cnt,
+                         "alg_GBs": gbs, "alg_TFLOPs": tfl,
+                         "bound": "alu" if is64 else "hbm",
+                         "frac": (tfl / FP64_PEAK_TFLOPS) if is64 else (gbs / hbm_peak)}
+        bytes_step += bpp * npts * cnt
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    dk = kernels[dom]
+    if dk["bound"] == "alu":
+        roofline = {"bound": "alu", "kernel": dom, "achieved": dk["alg_TFLOPs"],
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": dk["frac"],
+                    "traffic": None, "peak_source": "nominal FP64 (recipe table)"}
+    else:
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["alg_GBs"], "peak": hbm_peak,
+                    "unit": "GB/s", "frac": dk["frac"], "traffic": None,
+                    "peak_source": hbm_src}
+    share = dk["ms_per_step"] / (ms / K)
+    roofline["share_of_step"] = share
+
+    # ---- e2e through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ke = max(5, K // 10)
+        hm = torch.empty(2 * npts, dtype=torch.float64, pin_memory=True)
+        hp = torch.empty(npts, dtype=torch.float64, pin_memory=True)
+        s.get_m(out=hm)
+        s.get_p(out=hp)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            s.set_m(hm)
+            s.set_p(hp)
+            s.step(1)
+            s.get_m(out=hm)
+            s.get_p(out=hp)
+        torch.cuda.synchronize()
+        secs = max_over_ranks(time.perf_counter() - t0)
+        barrier()
+        e2e = {"value": world * npts * Ke / secs / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * npts * 8, "d2h_bytes_per_step": 3 * npts * 8,
+               "steps": Ke, "path": "hc_set_m + hc_set_p (pinned host FP64) -> hc_step(1) -> "
+                                    "hc_get_m + hc_get_p (pinned host FP64)"}
+
+    # ---- plain FP64 path at equal accuracy
+    fp64 = None
+    if not args.no_fp64:
+        K64 = max(3, K // 20)
+        s64 = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp64",
+                       cg_rtol=FP64_EQUAL_RTOL, cg_maxit=5000, use_graph=True, device=str(dev))
+        s64.set_r(w.r)
+        s64.set_source(w.S)
+        s64.set_m(w.m0)
+        s64.step(1)
+        if not args.no_tune:
+            autotune(s64, reps=3)
+        s64.set_m(w.m0)
+        s64.set_p(np.zeros(w.shape))
+        s64.step(max(Wm, 3))
+        barrier()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(s64.stream)
+        st64 = s64.step(K64)
+        a1.record(s64.stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(a0.elapsed_time(a1))
+        k64 = {}
+        for name in ("cg_apply", "cg_div", "cg_grad"):
+            kms = s64.time_kernel(name, reps=max(3, args.kernel_reps // 5))
+            k64[name] = {"ms": kms, "alg_TFLOPs": fft_flops_per_point(name, *w.n) * npts / (kms / 1e3) / 1e12}
+        s64.close()
+        v64 = world * npts * K64 / (ms64 / 1e3) / 1e6
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / K64, "steps": K64,
+                "cg_rtol": FP64_EQUAL_RTOL, "cg_iters_per_step": st64.total_cg_iters / K64,
+                "kernels": k64, "speedup_of_refined": value / v64}
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        secs, threads, it = oracle_steps(N_GRID, 1, warm=1)
+        cpu = {"value": npts / secs / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"one warm-started FP64 oracle step of the same 2048x2048 workload "
+                         f"(after one untimed step), cg_rtol {CG_RTOL_REFINED}, {it} CG iterations"}
+
+    closed_inner = s.params.inner_rtol
+    s.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config({"tuning": tuning, "inner_rtol": closed_inner}),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "hbm_gbs": bytes_step * K / (ms / 1e3) / 1e9,
+            "cg_iters_per_step": iters_per_step, "refine_sweeps_per_step": sweeps_per_step,
+            "cg_iterations_per_s": world * iters_per_step * K / (ms_max / 1e3),
+            "rel_residual_last_step": st.rel_residual,
+            "fp64_plain": fp64, "kernels": kernels,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--ref-n", type=int, default=512, help="reference arm: oracle sample grid")
+    ap.add_argument("--kernel-reps", type=int, default=30)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--inner-rtol", type=float, default=0.0,
+                    help="inner FP32 CG reduction factor (0: library default)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="host-driven CG loop instead of graphs (ncu cannot profile kernel "
+                         "nodes of graphs with conditional nodes)")
+    ap.add_argument("--accuracy", action="store_true", help="equal-accuracy calibration")
+    ap.add_argument("--acc-steps", type=int, default=100)
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("need --steps >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.accuracy:
+        run_accuracy(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -79,6 +79,8 @@ typedef struct {
   double rel_residual; /* ||S - A p||_2 / ||S||_2 at exit: FP64-evaluated in refined mode, recursive in plain mode */
   double kappa;        /* preconditioner constant used */
   int status;          /* HC_OK, HC_ENOCONV or HC_ENONFINITE for that step */
+  long long total_cg_iters; /* CG iterations summed over all steps of the hc_step call */
+  long long total_sweeps;   /* refinement sweeps summed likewise */
 } hc_step_stats;
 
 /* Bytes of device workspace hc_create needs for this grid and precision. */
@@ -140,6 +142,48 @@ int hc_split_step(hc_ctx* ctx);
  * interleaved); entry (ky, kx) for 1 <= kx < nx/2 is F[ky][kx] and entry
  * (ky, 0) is F[ky][0] + i F[ky][nx/2]. */
 int hc_spectrum(hc_ctx* ctx, const double* f, double* out, size_t count);
+
+/* Launch shapes of the FFT passes, per arithmetic precision ([0] FP32
+ * kernels, [1] FP64 kernels).  col_tile: packed columns per column-pass CTA
+ * (power of two, col_tile*ny/8 <= 512 threads, col_tile <= nx/2, <= 32);
+ * row_rows: rows per row-pass CTA (power of two, row_rows*nx/8 <= 512,
+ * row_rows <= ny).  Results do not depend on them beyond the order of
+ * floating-point sums. */
+typedef struct {
+  int col_tile[2];
+  int row_rows[2];
+} hc_tuning;
+
+int hc_get_tuning(const hc_ctx* ctx, hc_tuning* out);
+/* HC_EINVAL if a value breaks the limits above or needs more shared memory
+ * than a CTA may have. */
+int hc_set_tuning(hc_ctx* ctx, const hc_tuning* in);
+
+/* Kernels of one step, as timed by hc_time_kernel.  The CG_* kernels are the
+ * CG iteration (FP32 inner CG in refined mode, FP64 CG in plain mode); RES_*
+ * the FP64 residual evaluation (refined: p64 += delta then S - A p64; plain:
+ * the initial residual); SPLIT_* Step 2 of Algorithm 1. */
+enum {
+  HC_K_CG_GRAD = 0,    /* column pass: d-update, i xi d / n, inverse FFT_y */
+  HC_K_CG_APPLY = 1,   /* row pass: C2R, (m m^T + r I) g, R2C */
+  HC_K_CG_DIV = 2,     /* column pass: FFT_y, -i xi . q, <d, A d> */
+  HC_K_CG_UPDATE = 3,  /* x += alpha d, r -= alpha A d, <r, M^-1 r> */
+  HC_K_RES_GRAD = 4,
+  HC_K_RES_APPLY = 5,
+  HC_K_RES_DIV = 6,
+  HC_K_SPLIT_GRAD = 7, /* column pass: gradient of the new p */
+  HC_K_SPLIT_ROW = 8,  /* row pass: C2R, activation, relaxation, R2C */
+  HC_K_SPLIT_HEAT = 9, /* column pass: FFT_y, heat factor, IFFT_y */
+  HC_K_SPLIT_C2R = 10, /* row pass: C2R to physical m, sum |m|^2 */
+  HC_K_COUNT = 11
+};
+
+/* Launch one step kernel `reps` times back to back on the context's current
+ * buffers, between two CUDA events on the context's stream, and return the
+ * mean milliseconds per launch.  Outputs go to scratch buffers and a scratch
+ * solve state, so the state of the problem (m, p, S, r) is left as it was;
+ * the scratch contents are undefined afterwards.  For measurement only. */
+int hc_time_kernel(hc_ctx* ctx, int kernel, int reps, double* ms_per_launch);
 
 /* Number of this library's kernel launches issued by the context so far
  * (graph launches count every kernel node). */

@@ -42,9 +42,14 @@ class hc_params(C.Structure):
                 ("use_graph", C.c_int), ("stream", C.c_void_p)]
 
 
+class hc_tuning(C.Structure):
+    _fields_ = [("col_tile", C.c_int * 2), ("row_rows", C.c_int * 2)]
+
+
 class hc_step_stats(C.Structure):
     _fields_ = [("cg_iters", C.c_int), ("refine_sweeps", C.c_int), ("rel_residual", C.c_double),
-                ("kappa", C.c_double), ("status", C.c_int)]
+                ("kappa", C.c_double), ("status", C.c_int), ("total_cg_iters", C.c_longlong),
+                ("total_sweeps", C.c_longlong)]
 
 
 def library_path() -> str:
@@ -78,6 +83,9 @@ def _load() -> C.CDLL:
         "hc_destroy": ([P], None),
         "hc_strerror": ([C.c_int], C.c_char_p),
         "hc_last_cuda_error": ([], C.c_char_p),
+        "hc_time_kernel": ([P, C.c_int, C.c_int, dp], C.c_int),
+        "hc_get_tuning": ([P, C.POINTER(hc_tuning)], C.c_int),
+        "hc_set_tuning": ([P, C.POINTER(hc_tuning)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -105,6 +113,13 @@ hc_split_step = lib.hc_split_step
 hc_spectrum = lib.hc_spectrum
 hc_launch_count = lib.hc_launch_count
 hc_destroy = lib.hc_destroy
+hc_time_kernel = lib.hc_time_kernel
+hc_get_tuning = lib.hc_get_tuning
+hc_set_tuning = lib.hc_set_tuning
+
+# kernel ids of hc_time_kernel (include/hc.h)
+KERNELS = ["cg_grad", "cg_apply", "cg_div", "cg_update", "res_grad", "res_apply", "res_div",
+           "split_grad", "split_row", "split_heat", "split_c2r"]
 
 
 def strerror(code: int) -> str:
@@ -125,6 +140,8 @@ class StepStats:
     kappa: float
     status: int
     rc: int
+    total_cg_iters: int = 0
+    total_sweeps: int = 0
 
 
 def _host_f64(a, count: int, writable: bool = False):
@@ -247,7 +264,8 @@ class Solver:
         st = hc_step_stats()
         rc = hc_step(self.ctx, int(nsteps), C.byref(st))
         _check(rc, "hc_step", ok=allow)
-        return StepStats(st.cg_iters, st.refine_sweeps, st.rel_residual, st.kappa, st.status, rc)
+        return StepStats(st.cg_iters, st.refine_sweeps, st.rel_residual, st.kappa, st.status, rc,
+                         st.total_cg_iters, st.total_sweeps)
 
     # components ----------------------------------------------------------
     def gradient(self):
@@ -273,6 +291,22 @@ class Solver:
         op = out.view(np.float64).ctypes.data_as(C.POINTER(C.c_double))
         _check(hc_spectrum(self.ctx, fp, op, self.npts), "hc_spectrum")
         return out
+
+    def time_kernel(self, name: str, reps: int = 20) -> float:
+        """Mean milliseconds per launch of one step kernel (see hc_time_kernel)."""
+        ms = C.c_double()
+        _check(hc_time_kernel(self.ctx, KERNELS.index(name), int(reps), C.byref(ms)),
+               "hc_time_kernel")
+        return ms.value
+
+    def get_tuning(self) -> dict:
+        t = hc_tuning()
+        _check(hc_get_tuning(self.ctx, C.byref(t)), "hc_get_tuning")
+        return {"col_tile": list(t.col_tile), "row_rows": list(t.row_rows)}
+
+    def set_tuning(self, col_tile, row_rows):
+        t = hc_tuning((C.c_int * 2)(*col_tile), (C.c_int * 2)(*row_rows))
+        _check(hc_set_tuning(self.ctx, C.byref(t)), "hc_set_tuning")
 
     def launch_count(self) -> int:
         v = C.c_longlong()

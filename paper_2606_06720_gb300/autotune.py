@@ -1,0 +1,103 @@
+"""Launch-shape autotuner of the FFT passes.
+
+For a Solver it measures, with ``hc_time_kernel`` on the solver's own data,
+every admissible column-tile width and rows-per-CTA count of the FP32 and
+FP64 kernel families and keeps the fastest.  Results are cached on disk per
+(GPU name, grid, precision) so later processes reuse them; the cache lives in
+``$HC_TUNING_CACHE`` or ``~/.cache/hucai_gb300/tuning.json``.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+# kernels that share each launch-shape knob, per precision mode
+_FAMILIES = {
+    "fp32_refined": {
+        ("col_tile", 0): ["cg_grad", "cg_div", "split_grad", "split_heat"],
+        ("row_rows", 0): ["cg_apply", "split_row", "split_c2r"],
+        ("col_tile", 1): ["res_grad", "res_div"],
+        ("row_rows", 1): ["res_apply"],
+    },
+    "fp64": {
+        ("col_tile", 1): ["cg_grad", "cg_div", "split_grad", "split_heat", "res_grad"],
+        ("row_rows", 1): ["cg_apply", "split_row", "split_c2r", "res_apply"],
+    },
+}
+
+
+def _cache_path() -> str:
+    return os.environ.get("HC_TUNING_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "hucai_gb300", "tuning.json"))
+
+
+def _key(solver) -> str:
+    import torch
+    name = torch.cuda.get_device_name(solver.device)
+    return f"{name}|{solver.n[0]}x{solver.n[1]}|{solver.precision}"
+
+
+def _candidates(solver, knob: str):
+    nx, ny = solver.n
+    out = []
+    v = 1
+    while v <= 32:
+        if knob == "col_tile":
+            ok = v <= nx // 2 and v * (ny // 8) <= 512
+        else:
+            ok = v <= ny and v * (nx // 8) <= 512
+        if ok:
+            out.append(v)
+        v *= 2
+    return out
+
+
+def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = False) -> dict:
+    """Pick the fastest launch shapes for this solver; returns the tuning."""
+    path = _cache_path()
+    key = _key(solver)
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except Exception:
+            cache = {}
+    if use_cache and key in cache:
+        t = cache[key]
+        try:
+            solver.set_tuning(t["col_tile"], t["row_rows"])
+            return solver.get_tuning()
+        except Exception:
+            pass
+    prec = "fp64" if solver.precision.startswith("fp64") else "fp32_refined"
+    best = solver.get_tuning()
+    report = {}
+    for (knob, idx), kernels in _FAMILIES[prec].items():
+        times = {}
+        for v in _candidates(solver, knob):
+            trial = {"col_tile": list(best["col_tile"]), "row_rows": list(best["row_rows"])}
+            trial[knob][idx] = v
+            try:
+                solver.set_tuning(trial["col_tile"], trial["row_rows"])
+            except Exception:
+                continue
+            times[v] = sum(solver.time_kernel(k, reps) for k in kernels)
+        if times:
+            v = min(times, key=times.get)
+            best[knob][idx] = v
+            report[f"{knob}[{idx}]"] = {str(k): round(t * 1e3, 2) for k, t in times.items()}
+    solver.set_tuning(best["col_tile"], best["row_rows"])
+    if verbose:
+        print(json.dumps({"autotune": key, "us": report, "best": best}))
+    if use_cache:
+        cache[key] = best
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + f".{os.getpid()}.tmp"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    return best

@@ -63,6 +63,7 @@ struct hc_ctx {
 
   // device memory (all inside the workspace)
   hc::SolveState* st;
+  hc::SolveState* st_time;  // scratch state for hc_time_kernel (never drives a loop)
   double* partials;
   double* stage;            // 2n doubles: FP64 boundary staging
   cx<double>* p64;          // pressure spectrum
@@ -142,6 +143,7 @@ void layout(hc_ctx* c, Layout& L) {
   const size_t S32 = (size_t)c->ny * c->H * sizeof(cx<float>);
   const int max_ctas = (int)std::max<size_t>({(size_t)c->H, (size_t)c->ny, (size_t)1216});
   c->st = L.take<hc::SolveState>(sizeof(hc::SolveState));
+  c->st_time = L.take<hc::SolveState>(sizeof(hc::SolveState));
   c->partials = L.take<double>(sizeof(double) * 4 * max_ctas);
   c->stage = L.take<double>(sizeof(double) * 2 * n);
   c->p64 = L.take<cx<double>>(S64);
@@ -602,6 +604,8 @@ int fill_stats(hc_ctx* c, hc_step_stats* out) {
     out->rel_residual = h.outer_b2 > 0 ? std::sqrt(r2 / h.outer_b2) : 0.0;
     out->kappa = h.kappa;
     out->status = h.step_status;
+    out->total_cg_iters = h.acc_iters;
+    out->total_sweeps = h.acc_sweeps;
   }
   return HC_OK;
 }
@@ -968,6 +972,184 @@ int hc_spectrum(hc_ctx* c, const double* f, double* out, size_t count) {
 }
 
 const char* hc_last_cuda_error(void) { return g_last_error; }
+
+int hc_get_tuning(const hc_ctx* c, hc_tuning* t) {
+  if (!c || !t) return HC_EINVAL;
+  t->col_tile[0] = c->gf.tc;
+  t->col_tile[1] = c->gd.tc;
+  t->row_rows[0] = c->gf.rpc;
+  t->row_rows[1] = c->gd.rpc;
+  return HC_OK;
+}
+
+int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
+  if (!c || !t) return HC_EINVAL;
+  int dev = 0, optin = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int lnx = ilog2(c->nx), lny = ilog2(c->ny);
+  for (int p = 0; p < 2; ++p) {
+    const int tc = t->col_tile[p], rpc = t->row_rows[p];
+    const size_t esz = p == 0 ? sizeof(cx<float>) : sizeof(cx<double>);
+    if (tc < 1 || (tc & (tc - 1)) || tc > 32 || tc > c->H || (tc << (lny - 3)) > 512) return HC_EINVAL;
+    if (rpc < 1 || (rpc & (rpc - 1)) || rpc > c->ny || (rpc << (lnx - 3)) > 512) return HC_EINVAL;
+    const size_t col_sm = 2 * (size_t)(c->ny + (c->ny >> 3)) * tc * esz + 1024;
+    const size_t row_sm = (size_t)rpc * c->nx * esz + 1024;
+    if (col_sm > (size_t)optin || row_sm > (size_t)optin) return HC_EINVAL;
+  }
+  c->gf.tc = t->col_tile[0];
+  c->gf.ltc = ilog2(t->col_tile[0]);
+  c->gd.tc = t->col_tile[1];
+  c->gd.ltc = ilog2(t->col_tile[1]);
+  c->gf.rpc = t->row_rows[0];
+  c->gf.lrpc = ilog2(t->row_rows[0]);
+  c->gd.rpc = t->row_rows[1];
+  c->gd.lrpc = ilog2(t->row_rows[1]);
+  if (c->graph_ready) {  // launch shapes are baked into the graph
+    cudaGraphExecDestroy(c->gexec);
+    c->graph_ready = false;
+  }
+  return HC_OK;
+}
+
+int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
+  if (!c || !ms_per_launch || reps < 1 || kernel < 0 || kernel >= HC_K_COUNT) return HC_EINVAL;
+  // scratch state: loop open, nothing converges, zero step lengths so the
+  // repeated launches leave their inputs unchanged
+  hc::SolveState init;
+  CU(cudaMemcpyAsync(&init, c->st, sizeof(init), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  init.done = 0;
+  init.first = 1;
+  init.alpha = 0;
+  init.beta = 0;
+  init.maxit = 0x7fffffff;
+  init.thresh2 = -1.0;
+  init.outer_thresh2 = -1.0;
+  init.max_sweeps = 0x7fffffff;
+  init.graph_mode = 0;
+  for (int k = 0; k < 8; ++k) init.ticket[k] = 0;
+  CU(cudaMemcpyAsync(c->st_time, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
+  hc::SolveState* ts = c->st_time;
+  const size_t ns = (size_t)c->ny * c->H;
+  auto launch = [&]() {
+    if (c->refined) {
+      auto& g = c->gf;
+      auto& gd = c->gd;
+      cx<float>*Gx = c->G32, *Gy = c->G32 + ns;
+      cx<double>*Gx64 = c->G64, *Gy64 = c->G64 + ns;
+      switch (kernel) {
+        case HC_K_CG_GRAD:
+          hc::col_grad<float, float>(g, hc::CG_DUPDATE, (cx<float>*)nullptr, c->r32, c->d32, nullptr,
+                                     Gx, Gy, ts, 1, c->stream);
+          break;
+        case HC_K_CG_APPLY:
+          hc::row_apply<float, float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1],
+                                      (const float*)c->rf, c->q32, c->x32, ts, c->stream);
+          break;
+        case HC_K_CG_DIV:
+          hc::col_div<float>(g, hc::CD_CG, Gx, Gy, c->d32, nullptr, c->q32, nullptr, nullptr, ts,
+                             c->stream);
+          break;
+        case HC_K_CG_UPDATE:
+          hc::cg_update<float>(g, c->x32, c->r32, c->d32, c->q32, ts, c->stream);
+          break;
+        case HC_K_RES_GRAD:
+          hc::col_grad<double, double>(gd, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx64,
+                                       Gy64, ts, 0, c->stream);
+          break;
+        case HC_K_RES_APPLY:
+          hc::row_apply<double, float>(gd, Gx64, Gy64, (const float*)c->m[0], (const float*)c->m[1],
+                                       (const float*)c->rf, c->r64, (cx<double>*)c->stage,
+                                       nullptr, c->stream);
+          break;
+        case HC_K_RES_DIV:
+          hc::col_div<double>(gd, hc::CD_RESID_REFINE, Gx64, Gy64, nullptr, c->b64, c->r64, c->d32,
+                              c->q32, ts, c->stream);
+          break;
+        case HC_K_SPLIT_GRAD:
+          hc::col_grad<float, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy, ts,
+                                      0, c->stream);
+          break;
+        case HC_K_SPLIT_ROW:
+          hc::row_split<float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1], c->q32, c->x32,
+                               split_coef(c->prm), ts, c->stream);
+          break;
+        case HC_K_SPLIT_HEAT:
+          hc::col_heat<float>(g, Gx, Gy, c->stream);
+          break;
+        default:
+          hc::row_c2r<float>(g, Gx, Gy, (float*)c->q32, (float*)c->x32, ts, 1, c->stream);
+          break;
+      }
+    } else {
+      auto& g = c->gd;
+      cx<double>*Gx = c->G64, *Gy = c->G64 + ns;
+      double* sx = c->stage;
+      double* sy = c->stage + c->n;
+      switch (kernel) {
+        case HC_K_CG_GRAD:
+          hc::col_grad<double, double>(g, hc::CG_DUPDATE, (cx<double>*)nullptr, c->r64, c->d64,
+                                       nullptr, Gx, Gy, ts, 1, c->stream);
+          break;
+        case HC_K_CG_APPLY:
+          hc::row_apply<double, double>(g, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1],
+                                        (const double*)c->rf, c->q64, (cx<double>*)c->stage, ts,
+                                        c->stream);
+          break;
+        case HC_K_CG_DIV:
+          hc::col_div<double>(g, hc::CD_CG, Gx, Gy, c->d64, nullptr, c->q64, nullptr, nullptr, ts,
+                              c->stream);
+          break;
+        case HC_K_CG_UPDATE:
+          hc::cg_update<double>(g, (cx<double>*)c->stage, c->r64, c->d64,
+                                c->q64, ts, c->stream);
+          break;
+        case HC_K_RES_GRAD:
+        case HC_K_SPLIT_GRAD:
+          hc::col_grad<double, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy, ts,
+                                       0, c->stream);
+          break;
+        case HC_K_RES_APPLY:
+          hc::row_apply<double, double>(g, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1],
+                                        (const double*)c->rf, c->q64, (cx<double>*)c->stage, nullptr,
+                                        c->stream);
+          break;
+        case HC_K_RES_DIV:
+          hc::col_div<double>(g, hc::CD_RESID, Gx, Gy, nullptr, c->b64, c->q64, nullptr, nullptr, ts,
+                              c->stream);
+          break;
+        case HC_K_SPLIT_ROW:
+          hc::row_split<double>(g, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1], c->q64,
+                                (cx<double>*)c->stage, split_coef(c->prm), ts, c->stream);
+          break;
+        case HC_K_SPLIT_HEAT:
+          hc::col_heat<double>(g, Gx, Gy, c->stream);
+          break;
+        default:
+          hc::row_c2r<double>(g, Gx, Gy, sx, sy, ts, 1, c->stream);
+          break;
+      }
+    }
+  };
+  launch();  // warm-up
+  CU(cudaGetLastError());
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, c->stream));
+  for (int k = 0; k < reps; ++k) launch();
+  CU(cudaEventRecord(e1, c->stream));
+  CU(cudaEventSynchronize(e1));
+  float ms = 0;
+  CU(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CU(cudaGetLastError());
+  c->launches += reps + 1;
+  *ms_per_launch = (double)ms / reps;
+  return HC_OK;
+}
 
 int hc_launch_count(const hc_ctx* c, long long* count) {
   if (!c || !count) return HC_EINVAL;

@@ -116,13 +116,36 @@ __device__ __forceinline__ void dft8(cx<T>* v) {
 
 __device__ __forceinline__ int padk(int e) { return e + (e >> 3); }
 
+// Row slabs (one transform per slab, stride 1) use an XOR swizzle inside
+// aligned blocks instead of padding.  Shared memory serves a warp's 8-byte
+// accesses in 16-lane phases and 16-byte accesses in 8-lane phases; the
+// swizzles below make every Stockham access pattern of a radix-8 pass
+// (writes to 8j + r, 64(j/8) + j%8 + 8r, ...; canonical reads j + sN/8)
+// touch distinct banks within a phase, and they need no extra space.
+template <typename T>
+__device__ __forceinline__ int rswz(int e);
+template <>
+__device__ __forceinline__ int rswz<float>(int e) {
+  const int k = e >> 4;
+  return e ^ ((k & 7) | ((k & 4) << 1));
+}
+template <>
+__device__ __forceinline__ int rswz<double>(int e) {
+  return e ^ ((e >> 3) & 7);
+}
+// Slot of element e: swizzled row slab (SWZ) or padded column slab with stride ks.
+template <typename T, bool SWZ>
+__device__ __forceinline__ int slot(int e, int ks) {
+  return SWZ ? rswz<T>(e) : padk(e) * ks;
+}
+
 // ------------------------------------------------------------------ FFT core
 // NV transforms of length N = 2^lN (lN >= 3), one per slab, computed by the
 // N/8 threads j = 0..N/8-1 of each transform.  v[q][s] holds element
 // j + s N/8 on entry (input) and on exit (output).  Element e of slab q lives
 // at sl[q][padk(e) * ks].  Every thread of the CTA must call this together.
 // tw[m] = exp(-2 pi i m / N); the inverse uses the conjugates.
-template <int S, int NV, typename T>
+template <int S, int NV, bool SWZ = false, typename T>
 __device__ __forceinline__ void fft_canon(cx<T> (&v)[NV][8], cx<T>* const* sl, int ks, int j,
                                           int lN, const cx<T>* __restrict__ tw) {
   const int N8 = 1 << (lN - 3);
@@ -151,7 +174,7 @@ __device__ __forceinline__ void fft_canon(cx<T> (&v)[NV][8], cx<T>* const* sl, i
       for (int r = 0; r < 8; ++r) {
         const int e = base + (r << lNs);
 #pragma unroll
-        for (int q = 0; q < NV; ++q) sl[q][padk(e) * ks] = v[q][r];
+        for (int q = 0; q < NV; ++q) sl[q][slot<T, SWZ>(e, ks)] = v[q][r];
       }
       __syncthreads();
       lNs += 3;
@@ -160,7 +183,7 @@ __device__ __forceinline__ void fft_canon(cx<T> (&v)[NV][8], cx<T>* const* sl, i
       for (int s = 0; s < 8; ++s) {
         const int e = j + s * N8;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) v[q][s] = sl[q][padk(e) * ks];
+        for (int q = 0; q < NV; ++q) v[q][s] = sl[q][slot<T, SWZ>(e, ks)];
       }
     } else if (rem == 2) {
       // last pass, radix 4: butterflies jj = j + u N/8 (u = 0, 1) read/write
@@ -244,17 +267,51 @@ __device__ __forceinline__ bool last_cta_sum(double (&v)[K], double* partials,
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
+  // every thread of the last CTA sums a fixed strided subset of the partials,
+  // then a fixed-order block reduction: deterministic for a given grid
+  double w[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) w[k] = 0.0;
+  for (unsigned int c = threadIdx.x; c < gridDim.x; c += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] += __ldcg(&partials[c * 4 + k]);
+  block_sum<K>(w);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = 0;
-      for (unsigned int c = 0; c < gridDim.x; ++c) s += __ldcg(&partials[c * 4 + k]);
-      tot[k] = s;
-    }
+    for (int k = 0; k < K; ++k) tot[k] = w[k];
     *ticket = 0u;
   }
   return true;
 }
+
+// Per-thread dot-product accumulator.  FP64 data: plain FP64.  FP32 data: an
+// unevaluated pair of floats (double-float): each product is split exactly
+// into p + e with an FMA and added with Knuth's TwoSum, so the per-thread sum
+// keeps about 48 significant bits while running on the FP32 pipes (GB300's
+// FP64 rate is 1/58 of its FP32 rate).  Threads' sums are then promoted to
+// FP64 for the block and grid reductions.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_prod(double x, double y) { s = fma(x, y, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add_prod(float x, float y) {
+    const float p = x * y;
+    const float e = fmaf(x, y, -p);  // x*y - p exactly
+    const float t = hi + p;
+    const float bp = t - hi;
+    const float err = (hi - (t - bp)) + (p - bp);  // hi + p - t exactly
+    hi = t;
+    lo += err + e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 // Preconditioner symbol 1 / (kappa |xi~|^2) of the constant-coefficient
 // operator (0 on the null modes).
@@ -291,19 +348,19 @@ __device__ __forceinline__ void store_pair_r2c(cx<T> (&v)[1][8], cx<T>* slab, in
   const int N8 = N >> 3;
   __syncthreads();
 #pragma unroll
-  for (int s = 0; s < 8; ++s) slab[padk(j + s * N8)] = v[0][s];
+  for (int s = 0; s < 8; ++s) slab[rswz<T>(j + s * N8)] = v[0][s];
   __syncthreads();
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int k = j + s * N8;  // k < H
-    const cx<T> z = slab[padk(k)];
+    const cx<T> z = slab[rswz<T>(k)];
     cx<T> a, b;
     if (k == 0) {
-      const cx<T> zh = slab[padk(H)];
+      const cx<T> zh = slab[rswz<T>(H)];
       a = cmk<T>(z.x, zh.x);
       b = cmk<T>(z.y, zh.y);
     } else {
-      const cx<T> zc = slab[padk(N - k)];
+      const cx<T> zc = slab[rswz<T>(N - k)];
       a = cmk<T>((T)0.5 * (z.x + zc.x), (T)0.5 * (z.y - zc.y));
       b = cmk<T>((T)0.5 * (z.y + zc.y), (T)-0.5 * (z.x - zc.x));
     }
@@ -322,7 +379,7 @@ __global__ void __launch_bounds__(512) k_row_r2c(Geo<T> g, const T* __restrict__
   const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
   const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
   const int y = (blockIdx.x << g.lrpc) + rb;
-  cx<T>* slab = sm + rb * (N + (N >> 3));
+  cx<T>* slab = sm + rb * N;
   cx<T>* const sl[1] = {slab};
   const size_t ro = (size_t)y * N;
   cx<T> v[1][8];
@@ -331,7 +388,7 @@ __global__ void __launch_bounds__(512) k_row_r2c(Geo<T> g, const T* __restrict__
     const int x = j + s * N8;
     v[0][s] = cmk<T>(a[ro + x], b ? b[ro + x] : (T)0);
   }
-  fft_canon<-1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  fft_canon<-1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   store_pair_r2c(v, slab, j, N, H, A + (size_t)y * H, B ? B + (size_t)y * H : nullptr);
 }
 
@@ -344,16 +401,16 @@ __global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const
   const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
   const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
   const int y = (blockIdx.x << g.lrpc) + rb;
-  cx<T>* slab = sm + rb * (N + (N >> 3));
+  cx<T>* slab = sm + rb * N;
   cx<T>* const sl[1] = {slab};
   const cx<T>* Ar = A + (size_t)y * H;
   const cx<T>* Br = B ? B + (size_t)y * H : nullptr;
   cx<T> v[1][8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
-  fft_canon<+1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   const size_t ro = (size_t)y * N;
-  double acc[1] = {0.0};
+  DotAcc<T> m2;
   bool finite = true;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
@@ -361,11 +418,13 @@ __global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const
     a[ro + x] = v[0][s].x;
     if (b) b[ro + x] = v[0][s].y;
     if (kappa_update) {
-      acc[0] += (double)v[0][s].x * (double)v[0][s].x + (double)v[0][s].y * (double)v[0][s].y;
+      m2.add_prod(v[0][s].x, v[0][s].x);
+      m2.add_prod(v[0][s].y, v[0][s].y);
       finite = finite && hc_finite(v[0][s].x) && hc_finite(v[0][s].y);
     }
   }
   if (kappa_update) {
+    double acc[1] = {m2.value()};
     if (!finite) st->nonfinite = 1;
     double tot[1];
     if (last_cta_sum<1>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
@@ -386,14 +445,14 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
   const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
   const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
   const int y = (blockIdx.x << g.lrpc) + rb;
-  cx<T>* slab = sm + rb * (N + (N >> 3));
+  cx<T>* slab = sm + rb * N;
   cx<T>* const sl[1] = {slab};
   const cx<T>* Ar = Gx + (size_t)y * H;
   const cx<T>* Br = Gy + (size_t)y * H;
   cx<T> v[1][8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
-  fft_canon<+1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   // v = grad p (gx + i gy) at x = j + s N/8: apply (m (x) m + r I)
   const size_t ro = (size_t)y * N;
 #pragma unroll
@@ -404,7 +463,7 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
     const T mg = ax * gx + ay * gy;
     v[0][s] = cmk<T>(ax * mg + r * gx, ay * mg + r * gy);
   }
-  fft_canon<-1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  fft_canon<-1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   store_pair_r2c(v, slab, j, N, H, Qx + (size_t)y * H, Qy + (size_t)y * H);
 }
 
@@ -419,14 +478,14 @@ __global__ void __launch_bounds__(512) k_row_split(Geo<T> g, const cx<T>* Gx, co
   const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
   const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
   const int y = (blockIdx.x << g.lrpc) + rb;
-  cx<T>* slab = sm + rb * (N + (N >> 3));
+  cx<T>* slab = sm + rb * N;
   cx<T>* const sl[1] = {slab};
   const cx<T>* Ar = Gx + (size_t)y * H;
   const cx<T>* Br = Gy + (size_t)y * H;
   cx<T> v[1][8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
-  fft_canon<+1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   const size_t ro = (size_t)y * N;
   const T c2dt = (T)cf.c2dt;
   bool finite = true;
@@ -464,7 +523,7 @@ __global__ void __launch_bounds__(512) k_row_split(Geo<T> g, const cx<T>* Gx, co
     v[0][s] = cmk<T>(ax, ay);
   }
   if (!finite) st->nonfinite = 1;
-  fft_canon<-1, 1>(v, sl, 1, j, g.lnx, g.twx);
+  fft_canon<-1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   store_pair_r2c(v, slab, j, N, H, Mx + (size_t)y * H, My + (size_t)y * H);
 }
 
@@ -569,6 +628,7 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
   const T ax = g.kxd[c.kx];
   const double w = c.kx == 0 ? 1.0 : 2.0;  // Parseval weight of a packed column
   double acc[3] = {0.0, 0.0, 0.0};
+  DotAcc<T> dq;
   T kappa = 0;
   if (MODE == CD_RESID || MODE == CD_RESID_REFINE) kappa = (T)st->kappa;
 #pragma unroll
@@ -583,7 +643,9 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
     } else if constexpr (MODE == CD_CG) {
       out[idx] = q;
       const cx<T> dv = d[idx];
-      acc[0] += w * ((double)dv.x * (double)q.x + (double)dv.y * (double)q.y);
+      const T wt = (T)w;  // 1 or 2: exact
+      dq.add_prod(wt * dv.x, q.x);
+      dq.add_prod(wt * dv.y, q.y);
     } else if constexpr (MODE == CD_RESID) {
       const cx<T> rv = csub(bvec[idx], q);
       out[idx] = rv;
@@ -605,7 +667,7 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
   if constexpr (MODE == CD_PLAIN) return;
   double tot[3];
   if constexpr (MODE == CD_CG) {
-    double a1[1] = {acc[0]}, t1[1];
+    double a1[1] = {dq.value()}, t1[1];
     if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0) {
       const double dq = t1[0];
       if (dq > 0 && isfinite(dq)) {
@@ -785,7 +847,7 @@ __global__ void __launch_bounds__(256) k_cg_update(Geo<T> g, cx<T>* __restrict__
   const T alpha = (T)st->alpha;
   const T kappa = (T)st->kappa;
   const size_t total = (size_t)g.ny * g.H;
-  double acc[2] = {0.0, 0.0};
+  DotAcc<T> rr, rz;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
     const int kx = (int)(i & (size_t)(g.H - 1));
@@ -796,11 +858,14 @@ __global__ void __launch_bounds__(256) k_cg_update(Geo<T> g, cx<T>* __restrict__
     x[i] = cmk<T>(xv.x + alpha * dv.x, xv.y + alpha * dv.y);
     rv = cmk<T>(rv.x - alpha * qv.x, rv.y - alpha * qv.y);
     r[i] = rv;
-    const double w = kx == 0 ? 1.0 : 2.0;
-    const double r2 = w * ((double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y);
-    acc[0] += r2;
-    acc[1] += r2 * (double)pinv_sym(g, kx, ky, kappa);
+    const T wt = kx == 0 ? (T)1 : (T)2;
+    const T wp = wt * pinv_sym(g, kx, ky, kappa);  // weight times preconditioner symbol
+    rr.add_prod(wt * rv.x, rv.x);
+    rr.add_prod(wt * rv.y, rv.y);
+    rz.add_prod(wp * rv.x, rv.x);
+    rz.add_prod(wp * rv.y, rv.y);
   }
+  double acc[2] = {rr.value(), rz.value()};
   double tot[2];
   if (last_cta_sum<2>(acc, g.partials, &st->ticket[TK_UPDATE], tot) && threadIdx.x == 0) {
     const double rho_new = tot[1];
@@ -834,10 +899,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_msum(Geo<T> g, const T* __restrict__ mx,
                                               const T* __restrict__ my, SolveState* st) {
   const size_t n = (size_t)g.nx * g.ny;
-  double acc[1] = {0.0};
+  DotAcc<T> m2;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    acc[0] += (double)mx[i] * (double)mx[i] + (double)my[i] * (double)my[i];
+       i += (size_t)gridDim.x * blockDim.x) {
+    m2.add_prod(mx[i], mx[i]);
+    m2.add_prod(my[i], my[i]);
+  }
+  double acc[1] = {m2.value()};
   double tot[1];
   if (last_cta_sum<1>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
     st->msum = tot[0];
@@ -849,7 +917,7 @@ template <typename T>
 static inline int row_threads(const Geo<T>& g) { return g.rpc << (g.lnx - 3); }
 template <typename T>
 static inline size_t row_smem(const Geo<T>& g) {
-  return (size_t)g.rpc * (g.nx + (g.nx >> 3)) * sizeof(cx<T>);
+  return (size_t)g.rpc * g.nx * sizeof(cx<T>);
 }
 template <typename T>
 static inline int col_threads(const Geo<T>& g) { return g.tc << (g.lny - 3); }
@@ -859,7 +927,7 @@ static inline size_t col_smem(const Geo<T>& g, int nv) {
 }
 static inline int upd_blocks(size_t total) {
   size_t b = (total + 255) / 256;
-  return (int)(b < 1216 ? b : 1216);  // 8 CTAs of 256 threads per SM on 152 SMs
+  return (int)(b < 608 ? b : 608);  // 4 CTAs of 256 threads per SM on 152 SMs
 }
 
 template <typename T>

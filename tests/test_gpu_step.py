@@ -131,8 +131,9 @@ def test_headline_2048_one_step(hc, precision, tol):
         st = s.step(1)
         assert st.status == 0 and st.rel_residual <= 1e-8
         em, ep = rel_l2(s.get_m(), m_ref), rel_l2(s.get_p(), p_ref)
-    # p is only determined to the CG tolerance: compare within it
-    assert em <= tol and ep <= max(tol, 1e-6), (em, ep)
+    # FP64: the same iteration as the oracle, so p agrees to rounding; refined:
+    # p is determined to the CG tolerance only
+    assert em <= tol and ep <= (tol if precision == "fp64" else 1e-6), (em, ep)
 
 
 @pytest.mark.parametrize("case", ["zero_source", "zero_m", "gamma_one", "gamma_gt_one", "no_activation",
@@ -188,3 +189,39 @@ def test_launch_count_and_workspace_borrowing(hc):
         assert after - before >= 2 * (6 + 3 * (st.refine_sweeps + 1))
         # the workspace is a torch tensor: the library allocated nothing itself
         assert s.workspace.is_cuda and s.workspace.numel() > 0
+
+
+def test_tuning_changes_only_summation_order(hc):
+    """Launch shapes (column tile width, rows per CTA) regroup the same
+    arithmetic: results agree to rounding, invalid shapes are rejected."""
+    w = W.source_sink_2d(256, steps=2)
+    outs = []
+    with make_solver(hc, w, "fp64") as s:
+        base = s.get_tuning()
+        for col, row in [((1, 1), (1, 1)), ((4, 2), (2, 1)), ((8, 4), (1, 2))]:
+            s.set_tuning(list(col), list(row))
+            s.set_m(w.m0)
+            s.set_p(np.zeros(w.shape))
+            st = s.step(2)
+            outs.append((s.get_m(), s.get_p()))
+        for bad in [((3, 1), (1, 1)), ((64, 1), (1, 1)), ((1, 1), (1, 1024)), ((1, 0), (1, 1))]:
+            with pytest.raises(hc.HuCaiError):
+                s.set_tuning(list(bad[0]), list(bad[1]))
+        assert s.get_tuning()["col_tile"] == [8, 4]
+    for m, p in outs[1:]:
+        assert rel_l2(m, outs[0][0]) < 1e-12 and rel_l2(p, outs[0][1]) < 1e-11
+
+
+def test_autotuner_picks_admissible_shapes(hc, tmp_path, monkeypatch):
+    from paper_2606_06720_gb300.autotune import autotune
+    monkeypatch.setenv("HC_TUNING_CACHE", str(tmp_path / "tune.json"))
+    w = W.source_sink_2d(512, steps=1)
+    with make_solver(hc, w, "fp32_refined") as s:
+        s.step(1)
+        t = autotune(s, reps=3)
+        assert t == s.get_tuning()
+        assert (tmp_path / "tune.json").exists()
+        t2 = autotune(s, reps=3)  # from the cache
+        assert t2 == t
+        st = s.step(1)
+        assert st.status == 0 and st.rel_residual <= 1e-8
