@@ -189,6 +189,32 @@ int hc_time_kernel(hc_ctx* ctx, int kernel, int reps, double* ms_per_launch);
  * (graph launches count every kernel node). */
 int hc_launch_count(const hc_ctx* ctx, long long* count);
 
+/* --- Transform without device allocation (the paper has no counterpart) --- */
+
+#define HC_NOALLOC_MAX_POINTS 65536 /* nx*ny limit of hc_spectrum_noalloc */
+
+/* The forward 2D transform of hc_spectrum for callers that cannot allocate
+ * device memory: for example a plugin inside a host framework that reserves the
+ * whole GPU for its own pool allocator, or a loop where cudaMalloc's implicit
+ * device synchronisation is not acceptable.  No context is needed.
+ *   f:      device pointer, nx*ny FP64 values, row-major with x fastest.
+ *   out:    device pointer receiving ny*(nx/2) complex FP64 values (re/im
+ *           interleaved) in the packed layout of hc_spectrum.
+ *   nx, ny: powers of two in [8, 4096] with nx*ny <= HC_NOALLOC_MAX_POINTS;
+ *           anything else (or a null pointer) returns HC_EINVAL.
+ *   stream: cudaStream_t (NULL: legacy default stream); the call only enqueues
+ *           work on it and returns.  CUDA failures return HC_ECUDA.
+ * Scratch lives in one fixed 640 KiB static device array of the library
+ * (present on every GPU the process uses, until the process exits); the call
+ * allocates nothing and calls no allocating routine.  All calls share that
+ * array; each call rewrites it completely before reading it, so nothing from
+ * an earlier call is reused, but calls whose GPU work overlaps (other streams
+ * or threads at the same time) race on it and must be serialised by the
+ * caller.  The first call on each device does a one-time set-up (it looks up
+ * the array's device address and raises the kernels' shared-memory limit):
+ * make that first call before any stream capture. */
+int hc_spectrum_noalloc(const double* f, double* out, int nx, int ny, void* stream);
+
 void hc_destroy(hc_ctx* ctx);
 const char* hc_strerror(int code);
 

@@ -86,6 +86,7 @@ def _load() -> C.CDLL:
         "hc_time_kernel": ([P, C.c_int, C.c_int, dp], C.c_int),
         "hc_get_tuning": ([P, C.POINTER(hc_tuning)], C.c_int),
         "hc_set_tuning": ([P, C.POINTER(hc_tuning)], C.c_int),
+        "hc_spectrum_noalloc": ([P, P, C.c_int, C.c_int, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -116,6 +117,7 @@ hc_destroy = lib.hc_destroy
 hc_time_kernel = lib.hc_time_kernel
 hc_get_tuning = lib.hc_get_tuning
 hc_set_tuning = lib.hc_set_tuning
+hc_spectrum_noalloc = lib.hc_spectrum_noalloc
 
 # kernel ids of hc_time_kernel (include/hc.h)
 KERNELS = ["cg_grad", "cg_apply", "cg_div", "cg_update", "res_grad", "res_apply", "res_div",
