@@ -31,7 +31,7 @@ METRIC = "Mpoint-steps/s at 2048² FP32-refined vs FP64 plain at equal accuracy;
 UNIT = "Mpoint-steps/s"
 N_GRID = 2048
 CG_RTOL_REFINED = 1e-8      # the refined path's pressure tolerance
-FP64_EQUAL_RTOL = 1e-6      # loosest plain-FP64 tolerance reaching m rel. L2 <= 1e-5 at 100 steps
+FP64_EQUAL_RTOL = 1e-4      # loosest plain-FP64 tolerance reaching m rel. L2 <= 1e-5 at 100 steps
                             # (calibrated with --accuracy)
 HBM_PEAK_FALLBACK = 6800.0  # GB/s, recipe fallback when MEASURED_PEAKS.json is absent
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 of GB300 (recipe table); a plain-ALU bound
@@ -235,8 +235,8 @@ def run_accuracy(args) -> None:
     def err(m):
         return float(np.linalg.norm(m - m_ref) / np.linalg.norm(m_ref))
 
-    for precision, rtol in [("fp32_refined", CG_RTOL_REFINED), ("fp32_refined", 1e-6),
-                            ("fp64", 1e-5), ("fp64", 1e-6), ("fp64", 1e-7), ("fp64", 1e-8)]:
+    for precision, rtol in [("fp32_refined", CG_RTOL_REFINED), ("fp32_refined_df", CG_RTOL_REFINED),
+                            ("fp64", 1e-3), ("fp64", 1e-4), ("fp64", 1e-5), ("fp64", 1e-6)]:
         m, p, st, secs = run(precision, rtol)
         out["runs"].append({"precision": precision, "cg_rtol": rtol, "m_rel_l2": err(m),
                             "mean_cg_iters": st.total_cg_iters / steps,
@@ -285,7 +285,8 @@ def run_gb300(args) -> None:
         s.set_params(inner_rtol=args.inner_rtol)
     from paper_2606_06720_gb300.autotune import autotune
     s.step(1)  # realistic buffer contents for the tuner
-    tuning = autotune(s, reps=10) if not args.no_tune else s.get_tuning()
+    tune_report = {}
+    tuning = autotune(s, reps=10, report=tune_report) if not args.no_tune else s.get_tuning()
     s.set_m(w.m0)
     s.set_p(np.zeros(w.shape))
     stream = s.stream
@@ -377,6 +378,46 @@ def run_gb300(args) -> None:
                "steps": Ke, "path": "hc_set_m + hc_set_p (pinned host FP64) -> hc_step(1) -> "
                                     "hc_get_m + hc_get_p (pinned host FP64)"}
 
+    # ---- the same refined path with the refinement in double-float (FP32 pipes)
+    dfv = None
+    if not args.no_df:
+        sdf = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt,
+                       precision="fp32_refined_df", cg_rtol=CG_RTOL_REFINED, cg_maxit=2000,
+                       use_graph=not args.host_loop, device=str(dev))
+        sdf.set_r(w.r)
+        sdf.set_source(w.S)
+        sdf.set_m(w.m0)
+        sdf.step(1)
+        if not args.no_tune:
+            autotune(sdf, reps=10)
+        sdf.set_m(w.m0)
+        sdf.set_p(np.zeros(w.shape))
+        sdf.step(Wm)
+        Kd = max(10, K // 3)
+        barrier()
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(sdf.stream)
+        std = sdf.step(Kd)
+        b1.record(sdf.stream)
+        torch.cuda.synchronize()
+        msd = max_over_ranks(b0.elapsed_time(b1))
+        kdf = {}
+        for name in ("res_grad", "res_apply", "res_div"):
+            kms = sdf.time_kernel(name, reps=args.kernel_reps)
+            kdf[name] = {"ms": kms,
+                         "alg_TFLOPs": fft_flops_per_point(name, *w.n) * npts / (kms / 1e3) / 1e12,
+                         "alg_GBs": BYTES_PER_POINT["fp32_refined"][name] * npts / (kms / 1e3) / 1e9}
+        sdf.close()
+        dfv = {"value": world * npts * Kd / (msd / 1e3) / 1e6, "unit": UNIT,
+               "ms_per_step": msd / Kd, "steps": Kd,
+               "cg_iters_per_step": std.total_cg_iters / Kd,
+               "refine_sweeps_per_step": std.total_sweeps / Kd,
+               "rel_residual_last_step": std.rel_residual,
+               "refinement_arithmetic": "double-float (48-bit significand) on the FP32 pipes",
+               "kernels": kdf}
+
     # ---- plain FP64 path at equal accuracy
     fp64 = None
     if not args.no_fp64:
@@ -426,14 +467,15 @@ def run_gb300(args) -> None:
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config({"tuning": tuning, "inner_rtol": closed_inner}),
+            "config": workload_config({"tuning": tuning, "inner_rtol": closed_inner,
+                                       "tuning_us": tune_report.get("us")}),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
             "hbm_gbs": bytes_step * K / (ms / 1e3) / 1e9,
             "cg_iters_per_step": iters_per_step, "refine_sweeps_per_step": sweeps_per_step,
             "cg_iterations_per_s": world * iters_per_step * K / (ms_max / 1e3),
             "rel_residual_last_step": st.rel_residual,
-            "fp64_plain": fp64, "kernels": kernels,
+            "fp64_plain": fp64, "refined_df": dfv, "kernels": kernels,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -451,6 +493,7 @@ def main() -> None:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-df", action="store_true", help="skip the double-float refinement leg")
     ap.add_argument("--inner-rtol", type=float, default=0.0,
                     help="inner FP32 CG reduction factor (0: library default)")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")

@@ -52,6 +52,10 @@ extern "C" {
 #define HC_FP32_REFINED 1 /* FFTs, operator applies and split step in FP32; pressure solve wrapped in
                              FP64 iterative refinement (FP64 residual, FP64 correction accumulation,
                              FP64 dot products and null-space projection) */
+#define HC_FP32_REFINED_DF 2 /* as HC_FP32_REFINED, with the refinement's FP64-class arithmetic
+                                (residual, correction accumulation, state p and S) carried in
+                                double-float pairs on the FP32 pipes: 48-bit significands instead
+                                of 53, for GB300's low FP64 issue rate */
 
 typedef struct hc_ctx hc_ctx; /* opaque; owns (or borrows) all device memory of one problem */
 
@@ -147,11 +151,14 @@ int hc_spectrum(hc_ctx* ctx, const double* f, double* out, size_t count);
  * kernels, [1] FP64 kernels).  col_tile: packed columns per column-pass CTA
  * (power of two, col_tile*ny/8 <= 512 threads, col_tile <= nx/2, <= 32);
  * row_rows: rows per row-pass CTA (power of two, row_rows*nx/8 <= 512,
- * row_rows <= ny).  Results do not depend on them beyond the order of
- * floating-point sums. */
+ * row_rows <= ny), col_pipe (see below).  Results do not depend on them
+ * beyond the order of floating-point sums. */
 typedef struct {
   int col_tile[2];
   int row_rows[2];
+  int col_pipe[2]; /* 1: the CG/residual/heat column passes run persistent, prefetching the next
+                      tile with cp.async while transforming the current one; needs
+                      col_tile * (8 bytes FP32 | 16 bytes FP64) to be a multiple of 16 */
 } hc_tuning;
 
 int hc_get_tuning(const hc_ctx* ctx, hc_tuning* out);

@@ -19,7 +19,7 @@ _LIBNAME = os.path.join(HERE, "libhc_gb300.so")
 
 HC_OK, HC_EINVAL, HC_ENOMEM, HC_ECUDA = 0, -1, -2, -3
 HC_ENOCONV, HC_ENONFINITE, HC_ETIMEOUT, HC_ENOTSUP = -4, -5, -6, -7
-HC_FP64_PLAIN, HC_FP32_REFINED = 0, 1
+HC_FP64_PLAIN, HC_FP32_REFINED, HC_FP32_REFINED_DF = 0, 1, 2
 
 
 class HuCaiError(RuntimeError):
@@ -43,7 +43,7 @@ class hc_params(C.Structure):
 
 
 class hc_tuning(C.Structure):
-    _fields_ = [("col_tile", C.c_int * 2), ("row_rows", C.c_int * 2)]
+    _fields_ = [("col_tile", C.c_int * 2), ("row_rows", C.c_int * 2), ("col_pipe", C.c_int * 2)]
 
 
 class hc_step_stats(C.Structure):
@@ -170,8 +170,9 @@ def _host_f64(a, count: int, writable: bool = False):
 class Solver:
     """One Hu-Cai problem on one GPU.
 
-    ``n = (nx, ny)`` nodes, ``L = (Lx, Ly)``; ``precision`` is ``"fp64"`` (plain)
-    or ``"fp32_refined"``.  Arrays use numpy shapes ``(ny, nx)`` for scalar
+    ``n = (nx, ny)`` nodes, ``L = (Lx, Ly)``; ``precision`` is ``"fp64"`` (plain),
+    ``"fp32_refined"`` (FP64 refinement) or ``"fp32_refined_df"`` (refinement in
+    double-float on the FP32 pipes).  Arrays use numpy shapes ``(ny, nx)`` for scalar
     fields and ``(2, ny, nx)`` for m.
     """
 
@@ -191,7 +192,7 @@ class Solver:
         self.grid = hc_grid(2, (C.c_int * 3)(self.n[0], self.n[1], 1),
                             (C.c_double * 3)(self.L[0], self.L[1], 1.0))
         prec = {"fp64": HC_FP64_PLAIN, "fp64_plain": HC_FP64_PLAIN,
-                "fp32_refined": HC_FP32_REFINED}[precision]
+                "fp32_refined": HC_FP32_REFINED, "fp32_refined_df": HC_FP32_REFINED_DF}[precision]
         self.precision = precision
         self.params = hc_params(c, D, gamma, dt, cg_rtol, int(cg_maxit), prec, kappa, inner_rtol,
                                 int(max_sweeps), int(bool(use_graph)), self.stream.cuda_stream)
@@ -304,10 +305,14 @@ class Solver:
     def get_tuning(self) -> dict:
         t = hc_tuning()
         _check(hc_get_tuning(self.ctx, C.byref(t)), "hc_get_tuning")
-        return {"col_tile": list(t.col_tile), "row_rows": list(t.row_rows)}
+        return {"col_tile": list(t.col_tile), "row_rows": list(t.row_rows),
+                "col_pipe": list(t.col_pipe)}
 
-    def set_tuning(self, col_tile, row_rows):
-        t = hc_tuning((C.c_int * 2)(*col_tile), (C.c_int * 2)(*row_rows))
+    def set_tuning(self, col_tile, row_rows, col_pipe=None):
+        if col_pipe is None:
+            col_pipe = self.get_tuning()["col_pipe"]
+        t = hc_tuning((C.c_int * 2)(*col_tile), (C.c_int * 2)(*row_rows),
+                      (C.c_int * 2)(*col_pipe))
         _check(hc_set_tuning(self.ctx, C.byref(t)), "hc_set_tuning")
 
     def launch_count(self) -> int:

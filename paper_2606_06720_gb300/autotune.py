@@ -52,10 +52,16 @@ def _candidates(solver, knob: str):
     return out
 
 
-def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = False) -> dict:
-    """Pick the fastest launch shapes for this solver; returns the tuning."""
+def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = False,
+             report: dict | None = None) -> dict:
+    """Pick the fastest launch shapes for this solver and apply them; returns
+    the tuning.  If `report` is a dict it receives the cache key and the
+    measured microseconds per candidate (empty when the cache answered)."""
     path = _cache_path()
     key = _key(solver)
+    if report is not None:
+        report["key"] = key
+        report["us"] = {}
     cache = {}
     if use_cache and os.path.exists(path):
         try:
@@ -66,30 +72,41 @@ def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = Fal
     if use_cache and key in cache:
         t = cache[key]
         try:
-            solver.set_tuning(t["col_tile"], t["row_rows"])
+            solver.set_tuning(t["col_tile"], t["row_rows"], t.get("col_pipe", [0, 0]))
+            if report is not None:
+                report["cached"] = True
             return solver.get_tuning()
         except Exception:
             pass
     prec = "fp64" if solver.precision.startswith("fp64") else "fp32_refined"
     best = solver.get_tuning()
-    report = {}
+    measured = {}
     for (knob, idx), kernels in _FAMILIES[prec].items():
         times = {}
         for v in _candidates(solver, knob):
-            trial = {"col_tile": list(best["col_tile"]), "row_rows": list(best["row_rows"])}
-            trial[knob][idx] = v
-            try:
-                solver.set_tuning(trial["col_tile"], trial["row_rows"])
-            except Exception:
-                continue
-            times[v] = sum(solver.time_kernel(k, reps) for k in kernels)
+            for pipe in ((0, 1) if knob == "col_tile" else (None,)):
+                trial = {k: list(best[k]) for k in ("col_tile", "row_rows", "col_pipe")}
+                trial[knob][idx] = v
+                if pipe is not None:
+                    trial["col_pipe"][idx] = pipe
+                try:
+                    solver.set_tuning(trial["col_tile"], trial["row_rows"], trial["col_pipe"])
+                except Exception:
+                    continue
+                label = f"{v}" if pipe is None else f"{v}{'p' if pipe else ''}"
+                times[label] = (sum(solver.time_kernel(k, reps) for k in kernels), v, pipe)
         if times:
-            v = min(times, key=times.get)
+            lab = min(times, key=lambda k: times[k][0])
+            _, v, pipe = times[lab]
             best[knob][idx] = v
-            report[f"{knob}[{idx}]"] = {str(k): round(t * 1e3, 2) for k, t in times.items()}
-    solver.set_tuning(best["col_tile"], best["row_rows"])
+            if pipe is not None:
+                best["col_pipe"][idx] = pipe
+            measured[f"{knob}[{idx}]"] = {k: round(t[0] * 1e3, 2) for k, t in times.items()}
+    solver.set_tuning(best["col_tile"], best["row_rows"], best["col_pipe"])
+    if report is not None:
+        report["us"] = measured
     if verbose:
-        print(json.dumps({"autotune": key, "us": report, "best": best}))
+        print(json.dumps({"autotune": key, "us": measured, "best": best}))
     if use_cache:
         cache[key] = best
         try:

@@ -16,7 +16,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libhc_gb300.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["hc_kernels_f32.cu", "hc_kernels_f64.cu", "hc_api.cu", "hc_noalloc.cu"]
+SOURCES = ["hc_kernels_f32.cu", "hc_kernels_f64.cu", "hc_kernels_df.cu", "hc_api.cu",
+           "hc_noalloc.cu"]
 HEADERS = ["hc_internal.cuh", "hc_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE] + ARCH

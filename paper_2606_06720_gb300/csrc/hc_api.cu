@@ -15,12 +15,14 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "hc.h"
 #include "hc_internal.cuh"
 
 using hc::cx;
+using hc::df64;
 
 namespace {
 
@@ -54,6 +56,7 @@ struct hc_ctx {
   int nx, ny, H;
   size_t n;  // points
   int refined;
+  int df;    // refined with double-float state and residual
   cudaStream_t stream;
   bool owns_ws;
   void* ws;
@@ -82,10 +85,13 @@ struct hc_ctx {
   // tables
   cx<float>*twx_f, *twy_f;
   cx<double>*twx_d, *twy_d;
+  cx<df64>*twx_q, *twy_q;
   float *kxd_f, *kyd_f, *hx_f, *hy_f;
   double *kxd_d, *kyd_d, *hx_d, *hy_d;
+  df64 *kxd_q, *kyd_q;
   hc::Geo<float> gf;
   hc::Geo<double> gd;
+  hc::Geo<df64> gq;  // double-float kernels (HC_FP32_REFINED_DF)
 
   hc::SolveState* st_host;  // pinned mirror for readback
   // graph mode: captured on a private stream (capture is illegal on the
@@ -178,6 +184,10 @@ void layout(hc_ctx* c, Layout& L) {
   c->hy_f = L.take<float>(sizeof(float) * c->ny);
   c->kxd_d = L.take<double>(sizeof(double) * c->H);
   c->kyd_d = L.take<double>(sizeof(double) * c->ny);
+  c->twx_q = L.take<cx<df64>>(sizeof(cx<df64>) * c->nx);
+  c->twy_q = L.take<cx<df64>>(sizeof(cx<df64>) * c->ny);
+  c->kxd_q = L.take<df64>(sizeof(df64) * c->H);
+  c->kyd_q = L.take<df64>(sizeof(df64) * c->ny);
   c->hx_d = L.take<double>(sizeof(double) * (c->H + 1));
   c->hy_d = L.take<double>(sizeof(double) * c->ny);
 }
@@ -193,7 +203,9 @@ int check_grid(const hc_grid* g) {
 
 int check_params(const hc_params* p) {
   if (!p) return HC_EINVAL;
-  if (p->precision != HC_FP64_PLAIN && p->precision != HC_FP32_REFINED) return HC_EINVAL;
+  if (p->precision != HC_FP64_PLAIN && p->precision != HC_FP32_REFINED &&
+      p->precision != HC_FP32_REFINED_DF)
+    return HC_EINVAL;
   if (!std::isfinite(p->c) || !std::isfinite(p->D) || !std::isfinite(p->gamma) ||
       !std::isfinite(p->dt) || p->dt < 0)
     return HC_EINVAL;
@@ -249,23 +261,27 @@ int cuda_fail(cudaError_t e, const char* call, int line) {
 
 int upload_tables(hc_ctx* c) {
   std::vector<double> re, im;
-  auto put_tw = [&](int N, cx<float>* df, cx<double>* dd) -> int {
+  auto put_tw = [&](int N, cx<float>* df, cx<double>* dd, cx<df64>* dq) -> int {
     twiddles(N, re, im);
     std::vector<cx<float>> hf(N);
     std::vector<cx<double>> hd(N);
+    std::vector<cx<df64>> hq(N);
     for (int m = 0; m < N; ++m) {
       hf[m].x = (float)re[m];
       hf[m].y = (float)im[m];
       hd[m].x = re[m];
       hd[m].y = im[m];
+      hq[m].x = df64(re[m]);
+      hq[m].y = df64(im[m]);
     }
     CU(cudaMemcpy(df, hf.data(), sizeof(cx<float>) * N, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(dd, hd.data(), sizeof(cx<double>) * N, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dq, hq.data(), sizeof(cx<df64>) * N, cudaMemcpyHostToDevice));
     return HC_OK;
   };
-  int rc = put_tw(c->nx, c->twx_f, c->twx_d);
+  int rc = put_tw(c->nx, c->twx_f, c->twx_d, c->twx_q);
   if (rc) return rc;
-  rc = put_tw(c->ny, c->twy_f, c->twy_d);
+  rc = put_tw(c->ny, c->twy_f, c->twy_d, c->twy_q);
   if (rc) return rc;
   std::vector<double> kx(c->H), ky(c->ny);
   for (int k = 0; k < c->H; ++k) kx[k] = (k == 0) ? 0.0 : xid(k, c->nx, c->grid.L[0]);
@@ -275,6 +291,9 @@ int upload_tables(hc_ctx* c) {
   CU(cudaMemcpy(c->kyd_d, ky.data(), sizeof(double) * c->ny, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c->kxd_f, kxf.data(), sizeof(float) * c->H, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c->kyd_f, kyf.data(), sizeof(float) * c->ny, cudaMemcpyHostToDevice));
+  std::vector<df64> kxq(kx.begin(), kx.end()), kyq(ky.begin(), ky.end());
+  CU(cudaMemcpy(c->kxd_q, kxq.data(), sizeof(df64) * c->H, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->kyd_q, kyq.data(), sizeof(df64) * c->ny, cudaMemcpyHostToDevice));
   return HC_OK;
 }
 
@@ -369,6 +388,20 @@ void plain_iter(hc_ctx* c) {
 
 // FP64 residual S - A p64 (after p64 += delta) and inner-CG initialisation.
 void refined_resid(hc_ctx* c) {
+  if (c->df) {
+    auto& q = c->gq;
+    cx<df64>* Gx = reinterpret_cast<cx<df64>*>(c->G64);
+    cx<df64>* Gy = Gx + (size_t)c->ny * c->H;
+    hc::col_grad<df64, df64>(q, hc::CG_ADDDELTA, reinterpret_cast<cx<df64>*>(c->p64), nullptr,
+                             nullptr, c->x32, Gx, Gy, c->st, 0, c->stream);
+    hc::row_apply<df64, float>(q, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1],
+                               (const float*)c->rf, Gx, Gy, nullptr, c->stream);
+    hc::col_div<df64>(q, hc::CD_RESID_REFINE, Gx, Gy, nullptr,
+                      reinterpret_cast<const cx<df64>*>(c->b64),
+                      reinterpret_cast<cx<df64>*>(c->r64), c->r32, c->x32, c->st, c->stream);
+    c->launches += 3;
+    return;
+  }
   auto& g = c->gd;
   cx<double>* Gx = c->G64;
   cx<double>* Gy = c->G64 + (size_t)c->ny * c->H;
@@ -401,8 +434,17 @@ template <typename T>
 void split_step_t(hc_ctx* c, hc::Geo<T>& g, cx<T>* G) {
   cx<T>* Gx = G;
   cx<T>* Gy = G + (size_t)c->ny * c->H;
-  hc::col_grad<T, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy, c->st, 0,
-                          c->stream);
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->df)
+      hc::col_grad<float, df64>(g, hc::CG_PLAIN, reinterpret_cast<cx<df64>*>(c->p64), nullptr,
+                                nullptr, nullptr, Gx, Gy, c->st, 0, c->stream);
+    else
+      hc::col_grad<float, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy,
+                                  c->st, 0, c->stream);
+  } else {
+    hc::col_grad<T, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy, c->st, 0,
+                            c->stream);
+  }
   hc::row_split<T>(g, Gx, Gy, (const T*)c->m[0], (const T*)c->m[1], Gx, Gy, split_coef(c->prm),
                    c->st, c->stream);
   hc::col_heat<T>(g, Gx, Gy, c->stream);
@@ -639,7 +681,7 @@ int hc_workspace_size(const hc_grid* grid, const hc_params* params, size_t* byte
   tmp.ny = grid->n[1];
   tmp.H = tmp.nx / 2;
   tmp.n = (size_t)tmp.nx * tmp.ny;
-  tmp.refined = params->precision == HC_FP32_REFINED;
+  tmp.refined = params->precision != HC_FP64_PLAIN;
   Layout L;
   layout(&tmp, L);
   *bytes = (L.off + kAlign - 1) / kAlign * kAlign;
@@ -665,7 +707,8 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   c->ny = grid->n[1];
   c->H = c->nx / 2;
   c->n = (size_t)c->nx * c->ny;
-  c->refined = params->precision == HC_FP32_REFINED;
+  c->refined = params->precision != HC_FP64_PLAIN;
+  c->df = params->precision == HC_FP32_REFINED_DF;
   c->stream = (cudaStream_t)params->stream;
   c->mean_r = 1.0;
   if (workspace) {
@@ -690,8 +733,12 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   layout(c, L);
   fill_geo<float>(c, c->gf, c->twx_f, c->twy_f, c->kxd_f, c->kyd_f, c->hx_f, c->hy_f);
   fill_geo<double>(c, c->gd, c->twx_d, c->twy_d, c->kxd_d, c->kyd_d, c->hx_d, c->hy_d);
+  fill_geo<df64>(c, c->gq, c->twx_q, c->twy_q, c->kxd_q, c->kyd_q, nullptr, nullptr);
+  c->gq.tc = c->gd.tc;
+  c->gq.ltc = c->gd.ltc;
   hc::set_smem_limits_f32();
   hc::set_smem_limits_f64();
+  hc::set_smem_limits_df();
   int rc = HC_OK;
   if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess) rc = HC_ECUDA;
   if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HC_ECUDA;
@@ -761,6 +808,17 @@ int hc_set_r(hc_ctx* c, const double* r, size_t count) {
 
 // Forward 2D transform of the FP64 field in stage -> projected FP64 spectrum.
 static int forward64(hc_ctx* c, cx<double>* out, hc::SolveState* norm_into) {
+  if (c->df) {
+    df64* phys = reinterpret_cast<df64*>(c->stage + c->n);
+    cx<df64>* rows = reinterpret_cast<cx<df64>*>(c->G64);
+    hc::convert<df64, double>(c->stage, phys, c->n, c->stream);
+    hc::row_r2c<df64>(c->gq, phys, nullptr, rows, nullptr, c->stream);
+    hc::col_fwd<df64>(c->gq, rows, nullptr, reinterpret_cast<cx<df64>*>(out), nullptr, 1, 1,
+                      norm_into, c->stream);
+    c->launches += 3;
+    CU(cudaGetLastError());
+    return HC_OK;
+  }
   cx<double>* rows = c->G64;
   hc::row_r2c<double>(c->gd, c->stage, nullptr, rows, nullptr, c->stream);
   hc::col_fwd<double>(c->gd, rows, nullptr, out, nullptr, 1, 1, norm_into, c->stream);
@@ -824,10 +882,20 @@ int hc_get_m(hc_ctx* c, double* out, size_t count) {
 
 int hc_get_p(hc_ctx* c, double* out, size_t count) {
   if (!c || !out || count != c->n) return HC_EINVAL;
-  cx<double>* rows = c->G64;
-  hc::col_inv<double>(c->gd, c->p64, rows, 1.0 / (double)c->n, c->stream);
-  hc::row_c2r<double>(c->gd, rows, nullptr, c->stage, nullptr, nullptr, 0, c->stream);
-  c->launches += 2;
+  if (c->df) {
+    cx<df64>* rows = reinterpret_cast<cx<df64>*>(c->G64);
+    df64* phys = reinterpret_cast<df64*>(c->stage + c->n);
+    hc::col_inv<df64>(c->gq, reinterpret_cast<const cx<df64>*>(c->p64), rows,
+                      df64(1.0 / (double)c->n), c->stream);
+    hc::row_c2r<df64>(c->gq, rows, nullptr, phys, nullptr, nullptr, 0, c->stream);
+    hc::convert<double, df64>(phys, c->stage, c->n, c->stream);
+    c->launches += 3;
+  } else {
+    cx<double>* rows = c->G64;
+    hc::col_inv<double>(c->gd, c->p64, rows, 1.0 / (double)c->n, c->stream);
+    hc::row_c2r<double>(c->gd, rows, nullptr, c->stage, nullptr, nullptr, 0, c->stream);
+    c->launches += 2;
+  }
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(out, c->stage, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -875,8 +943,12 @@ int hc_gradient(hc_ctx* c, double* out, size_t count) {
   if (c->refined) {
     cx<float>* Gx = c->G32;
     cx<float>* Gy = c->G32 + (size_t)c->ny * c->H;
-    hc::col_grad<float, double>(c->gf, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy,
-                                c->st, 0, c->stream);
+    if (c->df)
+      hc::col_grad<float, df64>(c->gf, hc::CG_PLAIN, reinterpret_cast<cx<df64>*>(c->p64), nullptr,
+                                nullptr, nullptr, Gx, Gy, c->st, 0, c->stream);
+    else
+      hc::col_grad<float, double>(c->gf, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy,
+                                  c->st, 0, c->stream);
     hc::row_c2r<float>(c->gf, Gx, Gy, (float*)Gx, (float*)Gy, nullptr, 0, c->stream);
     hc::convert<double, float>((const float*)Gx, c->stage, c->n, c->stream);
     hc::convert<double, float>((const float*)Gy, c->stage + c->n, c->n, c->stream);
@@ -979,6 +1051,8 @@ int hc_get_tuning(const hc_ctx* c, hc_tuning* t) {
   t->col_tile[1] = c->gd.tc;
   t->row_rows[0] = c->gf.rpc;
   t->row_rows[1] = c->gd.rpc;
+  t->col_pipe[0] = c->gf.pipe;
+  t->col_pipe[1] = c->gd.pipe;
   return HC_OK;
 }
 
@@ -996,7 +1070,14 @@ int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
     const size_t col_sm = 2 * (size_t)(c->ny + (c->ny >> 3)) * tc * esz + 1024;
     const size_t row_sm = (size_t)rpc * c->nx * esz + 1024;
     if (col_sm > (size_t)optin || row_sm > (size_t)optin) return HC_EINVAL;
+    if (t->col_pipe[p] != 0 && t->col_pipe[p] != 1) return HC_EINVAL;
+    if (t->col_pipe[p]) {
+      if ((tc * esz) % 16) return HC_EINVAL;
+      if (2 * col_sm > (size_t)optin) return HC_EINVAL;
+    }
   }
+  int nsm = 0;
+  CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   c->gf.tc = t->col_tile[0];
   c->gf.ltc = ilog2(t->col_tile[0]);
   c->gd.tc = t->col_tile[1];
@@ -1005,6 +1086,16 @@ int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
   c->gf.lrpc = ilog2(t->row_rows[0]);
   c->gd.rpc = t->row_rows[1];
   c->gd.lrpc = ilog2(t->row_rows[1]);
+  c->gf.pipe = t->col_pipe[0];
+  c->gd.pipe = t->col_pipe[1];
+  c->gf.pgrid = std::min(nsm, c->H / c->gf.tc);
+  c->gd.pgrid = std::min(nsm, c->H / c->gd.tc);
+  c->gq.tc = c->gd.tc;
+  c->gq.ltc = c->gd.ltc;
+  c->gq.rpc = c->gd.rpc;
+  c->gq.lrpc = c->gd.lrpc;
+  c->gq.pipe = c->gd.pipe;
+  c->gq.pgrid = c->gd.pgrid;
   if (c->graph_ready) {  // launch shapes are baked into the graph
     cudaGraphExecDestroy(c->gexec);
     c->graph_ready = false;
@@ -1055,21 +1146,41 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
           hc::cg_update<float>(g, c->x32, c->r32, c->d32, c->q32, ts, c->stream);
           break;
         case HC_K_RES_GRAD:
-          hc::col_grad<double, double>(gd, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx64,
-                                       Gy64, ts, 0, c->stream);
+          if (c->df)
+            hc::col_grad<df64, df64>(c->gq, hc::CG_PLAIN, reinterpret_cast<cx<df64>*>(c->p64),
+                                     nullptr, nullptr, nullptr, (cx<df64>*)Gx64, (cx<df64>*)Gy64, ts,
+                                     0, c->stream);
+          else
+            hc::col_grad<double, double>(gd, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx64,
+                                         Gy64, ts, 0, c->stream);
           break;
         case HC_K_RES_APPLY:
-          hc::row_apply<double, float>(gd, Gx64, Gy64, (const float*)c->m[0], (const float*)c->m[1],
-                                       (const float*)c->rf, c->r64, (cx<double>*)c->stage,
-                                       nullptr, c->stream);
+          if (c->df)
+            hc::row_apply<df64, float>(c->gq, (cx<df64>*)Gx64, (cx<df64>*)Gy64,
+                                       (const float*)c->m[0], (const float*)c->m[1],
+                                       (const float*)c->rf, (cx<df64>*)c->r64,
+                                       (cx<df64>*)c->stage, nullptr, c->stream);
+          else
+            hc::row_apply<double, float>(gd, Gx64, Gy64, (const float*)c->m[0],
+                                         (const float*)c->m[1], (const float*)c->rf, c->r64,
+                                         (cx<double>*)c->stage, nullptr, c->stream);
           break;
         case HC_K_RES_DIV:
-          hc::col_div<double>(gd, hc::CD_RESID_REFINE, Gx64, Gy64, nullptr, c->b64, c->r64, c->d32,
-                              c->q32, ts, c->stream);
+          if (c->df)
+            hc::col_div<df64>(c->gq, hc::CD_RESID_REFINE, (cx<df64>*)Gx64, (cx<df64>*)Gy64,
+                              nullptr, (const cx<df64>*)c->b64, (cx<df64>*)c->r64, c->d32, c->q32,
+                              ts, c->stream);
+          else
+            hc::col_div<double>(gd, hc::CD_RESID_REFINE, Gx64, Gy64, nullptr, c->b64, c->r64,
+                                c->d32, c->q32, ts, c->stream);
           break;
         case HC_K_SPLIT_GRAD:
-          hc::col_grad<float, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy, ts,
-                                      0, c->stream);
+          if (c->df)
+            hc::col_grad<float, df64>(g, hc::CG_PLAIN, reinterpret_cast<cx<df64>*>(c->p64), nullptr,
+                                      nullptr, nullptr, Gx, Gy, ts, 0, c->stream);
+          else
+            hc::col_grad<float, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy,
+                                        ts, 0, c->stream);
           break;
         case HC_K_SPLIT_ROW:
           hc::row_split<float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1], c->q32, c->x32,

@@ -22,6 +22,58 @@ struct alignas(2 * sizeof(T)) cx {
   T x, y;
 };
 
+// Double-float: the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
+// a 48-bit significand computed on the FP32 pipes (error-free transformations:
+// Knuth's TwoSum, Dekker's Fast2Sum, and the FMA-based exact product).  On
+// GB300 the FP64 pipe issues at 1/58 of the FP32 rate, so FP64-class residuals
+// run faster this way.  Additions use the normwise-accurate form: the absolute
+// error of a + b is below 2^-47 (|a| + |b|), the bound the FFT error analysis
+// needs.
+struct df64 {
+  float hi, lo;
+  df64() = default;
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ df64(float f) : hi(f), lo(0.0f) {}
+  __host__ __device__ df64(int i) : hi((float)i), lo(0.0f) {}
+  __host__ __device__ df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+
+__host__ __device__ inline df64 df_fast2sum(float a, float b) {  // needs |a| >= |b| or a == 0
+  const float s = a + b;
+  return df64(s, b - (s - a));
+}
+__host__ __device__ inline df64 df_2sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return df64(s, (a - (s - bb)) + (b - bb));
+}
+__host__ __device__ inline df64 operator+(df64 a, df64 b) {
+  df64 s = df_2sum(a.hi, b.hi);
+  s.lo += a.lo + b.lo;
+  return df_fast2sum(s.hi, s.lo);
+}
+__host__ __device__ inline df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__host__ __device__ inline df64 operator-(df64 a, df64 b) { return a + (-b); }
+__host__ __device__ inline df64 operator*(df64 a, df64 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast2sum(p, e);
+}
+__host__ __device__ inline df64 operator/(df64 a, df64 b) {
+  const float q1 = a.hi / b.hi;
+  const df64 r = a - b * df64(q1);
+  return df_fast2sum(q1, r.hi / b.hi);
+}
+__host__ __device__ inline bool operator>(df64 a, df64 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__host__ __device__ inline bool operator<(df64 a, df64 b) { return b > a; }
+__host__ __device__ inline bool operator>=(df64 a, df64 b) { return !(b > a); }
+__host__ __device__ inline bool operator==(df64 a, df64 b) { return a.hi == b.hi && a.lo == b.lo; }
+__host__ __device__ inline bool operator!=(df64 a, df64 b) { return !(a == b); }
+
 // Device-resident scalar state of one pressure solve (CG and refinement).
 // All reductions that feed it are computed in FP64 by the last CTA of the
 // producing kernel, summing the per-CTA partials in a fixed order.
@@ -92,6 +144,8 @@ struct Geo {
   const T* hy;               // heat factor exp(-D^2 xi_y^2 dt), ky < ny
   double* partials;          // per-CTA FP64 partial sums, 4 per CTA
   int npartials;             // capacity in CTAs
+  int pipe;                  // 1: column passes run persistent with cp.async double buffering
+  int pgrid;                 // CTAs of a persistent column pass (<= SMs, <= tiles)
 };
 
 // Split-step coefficients (Section 2.3), precomputed on the host in FP64.
@@ -168,6 +222,7 @@ void msum(const Geo<T>& g, const T* mx, const T* my, SolveState* st, cudaStream_
 // Opt every kernel of one precision in to the full shared memory per block.
 void set_smem_limits_f32();
 void set_smem_limits_f64();
+void set_smem_limits_df();
 // Solve bookkeeping (one thread): configuration, step start (counters, kappa,
 // thresholds), step end (stats and status accumulation), accumulator reset.
 void set_config(SolveState* st, SolveConfig cfg, cudaStream_t s);

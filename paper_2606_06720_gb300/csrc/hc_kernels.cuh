@@ -21,6 +21,8 @@
 // one pad element per 8 to break the stride-8 bank conflicts.
 #pragma once
 
+#include <type_traits>
+
 #include "hc_internal.cuh"
 #include "hc.h"
 
@@ -64,6 +66,11 @@ __device__ __forceinline__ cx<double> ldg(const cx<double>* p) {
   const double2 v = __ldg(reinterpret_cast<const double2*>(p));
   return cmk<double>(v.x, v.y);
 }
+__device__ __forceinline__ cx<df64> ldg(const cx<df64>* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return cmk<df64>(df64(v.x, v.y), df64(v.z, v.w));
+}
+__device__ __forceinline__ bool hc_finite(df64 x) { return isfinite(x.hi); }
 
 __device__ __forceinline__ float hc_expm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double hc_expm1(double x) { return expm1(x); }
@@ -101,9 +108,14 @@ __device__ __forceinline__ void dft8(cx<T>* v) {
   dft4<S>(o0, o1, o2, o3);
   const T h = (T)0.70710678118654752440;  // cos(pi/4)
   // W8 = (1 + S i)/sqrt(2); W8^2 = S i; W8^3 = (-1 + S i)/sqrt(2)
-  o1 = cmk<T>((o1.x - (T)S * o1.y) * h, (o1.y + (T)S * o1.x) * h);
+  if constexpr (S < 0) {
+    o1 = cmk<T>((o1.x + o1.y) * h, (o1.y - o1.x) * h);
+    o3 = cmk<T>((o3.y - o3.x) * h, -((o3.x + o3.y) * h));
+  } else {
+    o1 = cmk<T>((o1.x - o1.y) * h, (o1.y + o1.x) * h);
+    o3 = cmk<T>(-((o3.x + o3.y) * h), (o3.x - o3.y) * h);
+  }
   o2 = cmul_si<S>(o2);
-  o3 = cmk<T>((-o3.x - (T)S * o3.y) * h, (-o3.y + (T)S * o3.x) * h);
   v[0] = cadd(e0, o0);
   v[4] = csub(e0, o0);
   v[1] = cadd(e1, o1);
@@ -131,6 +143,10 @@ __device__ __forceinline__ int rswz<float>(int e) {
 }
 template <>
 __device__ __forceinline__ int rswz<double>(int e) {
+  return e ^ ((e >> 3) & 7);
+}
+template <>
+__device__ __forceinline__ int rswz<df64>(int e) {
   return e ^ ((e >> 3) & 7);
 }
 // Slot of element e: swizzled row slab (SWZ) or padded column slab with stride ks.
@@ -313,6 +329,13 @@ struct DotAcc<float> {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+template <>
+struct DotAcc<df64> {
+  df64 s = df64(0.0f, 0.0f);
+  __device__ __forceinline__ void add_prod(df64 x, df64 y) { s = s + x * y; }
+  __device__ __forceinline__ double value() const { return (double)s.hi + (double)s.lo; }
+};
+
 // Preconditioner symbol 1 / (kappa |xi~|^2) of the constant-coefficient
 // operator (0 on the null modes).
 template <typename T>
@@ -320,6 +343,14 @@ __device__ __forceinline__ T pinv_sym(const Geo<T>& g, int kx, int ky, T kappa) 
   const T a = g.kxd[kx], b = g.kyd[ky];
   const T s2 = a * a + b * b;
   return s2 > (T)0 ? (T)1 / (kappa * s2) : (T)0;
+}
+
+// The same symbol evaluated in FP32, as the inner FP32 CG evaluates it.
+template <typename T>
+__device__ __forceinline__ float pinv_f32(const Geo<T>& g, int kx, int ky, float kappa) {
+  const float a = (float)g.kxd[kx], b = (float)g.kyd[ky];
+  const float s2 = a * a + b * b;
+  return s2 > 0.0f ? 1.0f / (kappa * s2) : 0.0f;
 }
 
 // ------------------------------------------------------------------ row helpers
@@ -527,6 +558,47 @@ __global__ void __launch_bounds__(512) k_row_split(Geo<T> g, const cx<T>* Gx, co
   store_pair_r2c(v, slab, j, N, H, Mx + (size_t)y * H, My + (size_t)y * H);
 }
 
+// ------------------------------------------------------------------ solve-state finalizers
+// Plain CG start (one thread): r2 = ||b - A x0||^2, rz = <r, M^-1 r>.
+__device__ __forceinline__ void resid_init(SolveState* st, double r2, double rz) {
+  st->rnorm2 = r2;
+  st->rho = rz;
+  st->it = 0;
+  st->first = 1;
+  st->status = 0;
+  st->done = (r2 <= st->thresh2 || st->maxit <= 0) ? 1 : 0;
+  if (!isfinite(r2)) {
+    st->status = HC_ENONFINITE;
+    st->done = 1;
+  }
+  if (st->graph_mode) cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
+}
+
+// Refinement sweep start (one thread): r64 = ||S - A p64||^2 decides the outer
+// loop; r32, rz start the inner FP32 CG on A delta = r32 from delta = 0.
+__device__ __forceinline__ void resid_refine_init(SolveState* st, double r64, double r32,
+                                                  double rz) {
+  st->outer_r2 = r64;
+  const bool finite = isfinite(r64);
+  const bool conv = r64 <= st->outer_thresh2;
+  st->outer_done = (conv || !finite || st->sweeps >= st->max_sweeps) ? 1 : 0;
+  if (!finite) st->status = HC_ENONFINITE;
+  else if (!conv && st->outer_done) st->status = HC_ENOCONV;
+  else st->status = 0;
+  st->bnorm2 = r32;
+  st->thresh2 = st->inner_rtol2 * r32;
+  st->rnorm2 = r32;
+  st->rho = rz;
+  st->it = 0;
+  st->first = 1;
+  st->done = (st->outer_done || r32 == 0.0) ? 1 : 0;
+  if (!st->outer_done) st->sweeps += 1;
+  if (st->graph_mode) {
+    cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
+    cudaGraphSetConditional(st->h_outer, st->outer_done ? 0u : 1u);
+  }
+}
+
 // ------------------------------------------------------------------ column kernels
 // Thread layout of a column CTA: b = packed column within the tile (fastest),
 // j = FFT thread index; slab q at sm + q * slab_elems + b with stride tc.
@@ -628,9 +700,12 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
   const T ax = g.kxd[c.kx];
   const double w = c.kx == 0 ? 1.0 : 2.0;  // Parseval weight of a packed column
   double acc[3] = {0.0, 0.0, 0.0};
-  DotAcc<T> dq;
+  DotAcc<T> dq, r64acc;
+  DotAcc<float> r32acc, rzacc;
   T kappa = 0;
-  if (MODE == CD_RESID || MODE == CD_RESID_REFINE) kappa = (T)st->kappa;
+  float kappa_f = 0.0f;
+  if (MODE == CD_RESID) kappa = (T)st->kappa;
+  if (MODE == CD_RESID_REFINE) kappa_f = (float)st->kappa;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int ky = c.j + s * c.NY8;
@@ -655,13 +730,17 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
     } else {
       const cx<T> rv = csub(bvec[idx], q);
       out[idx] = rv;
-      acc[0] += w * ((double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y);
+      const T wt = (T)(float)w;
+      r64acc.add_prod(wt * rv.x, rv.x);
+      r64acc.add_prod(wt * rv.y, rv.y);
       const cx<float> rf = ccast<float>(rv);
       r32[idx] = rf;
       delta32[idx] = czero<float>();
-      const double r2f = (double)rf.x * (double)rf.x + (double)rf.y * (double)rf.y;
-      acc[1] += w * r2f;
-      acc[2] += w * r2f * (double)pinv_sym(g, c.kx, ky, kappa);
+      const float wf = (float)w, wpf = wf * pinv_f32(g, c.kx, ky, kappa_f);
+      r32acc.add_prod(wf * rf.x, rf.x);
+      r32acc.add_prod(wf * rf.y, rf.y);
+      rzacc.add_prod(wpf * rf.x, rf.x);
+      rzacc.add_prod(wpf * rf.y, rf.y);
     }
   }
   if constexpr (MODE == CD_PLAIN) return;
@@ -681,42 +760,14 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
     }
   } else if constexpr (MODE == CD_RESID) {
     double a2[2] = {acc[0], acc[1]}, t2[2];
-    if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0) {
-      st->rnorm2 = t2[0];
-      st->rho = t2[1];
-      st->it = 0;
-      st->first = 1;
-      st->status = 0;
-      st->done = (t2[0] <= st->thresh2 || st->maxit <= 0) ? 1 : 0;
-      if (!isfinite(t2[0])) {
-        st->status = HC_ENONFINITE;
-        st->done = 1;
-      }
-      if (st->graph_mode) cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
-    }
+    if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
+      resid_init(st, t2[0], t2[1]);
   } else {
-    if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot) && threadIdx.x == 0) {
-      st->outer_r2 = tot[0];
-      const bool finite = isfinite(tot[0]);
-      const bool conv = tot[0] <= st->outer_thresh2;
-      st->outer_done = (conv || !finite || st->sweeps >= st->max_sweeps) ? 1 : 0;
-      if (!finite) st->status = HC_ENONFINITE;
-      else if (!conv && st->outer_done) st->status = HC_ENOCONV;
-      else st->status = 0;
-      // inner FP32 CG on A delta = r32 from delta = 0
-      st->bnorm2 = tot[1];
-      st->thresh2 = st->inner_rtol2 * tot[1];
-      st->rnorm2 = tot[1];
-      st->rho = tot[2];
-      st->it = 0;
-      st->first = 1;
-      st->done = (st->outer_done || tot[1] == 0.0) ? 1 : 0;
-      if (!st->outer_done) st->sweeps += 1;
-      if (st->graph_mode) {
-        cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
-        cudaGraphSetConditional(st->h_outer, st->outer_done ? 0u : 1u);
-      }
-    }
+    acc[0] = r64acc.value();
+    acc[1] = r32acc.value();
+    acc[2] = rzacc.value();
+    if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot) && threadIdx.x == 0)
+      resid_refine_init(st, tot[0], tot[1], tot[2]);
   }
 }
 
@@ -831,6 +882,308 @@ __global__ void __launch_bounds__(512) k_col_inv(Geo<T> g, const cx<T>* __restri
   fft_canon<+1, 1>(v, sl, g.tc, c.j, g.lny, g.twy);
 #pragma unroll
   for (int s = 0; s < 8; ++s) out[(size_t)(c.j + s * c.NY8) * H + c.kx] = cscale(v[0][s], scale);
+}
+
+// ------------------------------------------------------------------ pipelined column passes
+// Persistent variants of the column passes: each CTA walks tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... and, while it transforms one tile, cp.async
+// copies the next tile's inputs into the other half of a double buffer.  A
+// buffer half holds two padded slabs (element (row, b) of slab q at
+// q*se + padk(row)*tc + b), so once a tile's values are in registers its
+// buffer half serves as the FFT exchange slabs.  Needs tc*sizeof(cx<T>) to be
+// a multiple of 16 bytes (the cp.async size).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_prev() {  // all groups but the newest complete
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <typename T, int NS>
+__device__ __forceinline__ void stage_cols(const Geo<T>& g, const cx<T>* a0, const cx<T>* a1,
+                                           cx<T>* buf, int se, int kx0) {
+  constexpr int lce = sizeof(cx<T>) == 8 ? 1 : 0;  // log2 complex elements per 16-byte copy
+  const int lcpr = g.ltc - lce;                     // log2 copies per row
+  const int per = g.ny << lcpr;
+  for (int c = threadIdx.x; c < NS * per; c += blockDim.x) {
+    const int q = (NS > 1 && c >= per) ? 1 : 0;
+    const int rem = c - q * per;
+    const int row = rem >> lcpr, ch = rem & ((1 << lcpr) - 1);
+    const cx<T>* src = (q ? a1 : a0) + (size_t)row * g.H + kx0 + (ch << lce);
+    cp_async16(buf + q * se + padk(row) * g.tc + (ch << lce), src);
+  }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(512) kp_col_grad(Geo<T> g, cx<T>* in, const cx<T>* __restrict__ rvec,
+                                                   cx<T>* dio, const cx<float>* __restrict__ delta,
+                                                   cx<T>* __restrict__ Gx, cx<T>* __restrict__ Gy,
+                                                   SolveState* st, int check_done) {
+  if (check_done && st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  constexpr int NS = MODE == CG_DUPDATE ? 2 : 1;
+  const int H = g.H, se = slab_elems(g), ntiles = g.H >> g.ltc;
+  const int b = threadIdx.x & (g.tc - 1), j = threadIdx.x >> g.ltc, NY8 = 1 << (g.lny - 3);
+  const T invn = (T)(1.0 / ((double)g.nx * (double)g.ny));
+  bool first = false, add_delta = false;
+  T beta = 0, kappa = 0;
+  if (MODE == CG_DUPDATE) {
+    first = st->first != 0;
+    beta = (T)st->beta;
+    kappa = (T)st->kappa;
+  }
+  if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
+  const cx<T>* s0 = MODE == CG_DUPDATE ? rvec : in;
+  const cx<T>* s1 = MODE == CG_DUPDATE ? dio : nullptr;
+  int half = 0;
+  int tile = blockIdx.x;
+  if (tile < ntiles) stage_cols<T, NS>(g, s0, s1, sm, se, tile << g.ltc);
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    if (nxt < ntiles) stage_cols<T, NS>(g, s0, s1, sm + (half ^ 1) * 2 * se, se, nxt << g.ltc);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+    cx<T>* cur = sm + half * 2 * se;
+    const int kx = (tile << g.ltc) + b;
+    const T ax = g.kxd[kx] * invn;
+    cx<float> dl[8];
+    if (MODE == CG_ADDDELTA && add_delta) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) dl[s] = delta[(size_t)(j + s * NY8) * H + kx];
+    }
+    cx<T> v[2][8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int ky = j + s * NY8;
+      const size_t idx = (size_t)ky * H + kx;
+      const int e = padk(ky) * g.tc + b;
+      cx<T> P;
+      if constexpr (MODE == CG_PLAIN) {
+        P = cur[e];
+      } else if constexpr (MODE == CG_DUPDATE) {
+        const T pv = pinv_sym(g, kx, ky, kappa);
+        const cx<T> z = cscale(cur[e], pv);
+        P = first ? z : cadd(z, cscale(cur[se + e], beta));
+        dio[idx] = P;
+      } else {
+        P = cur[e];
+        if (add_delta) {
+          P = cadd(P, ccast<T>(dl[s]));
+          in[idx] = P;
+        }
+      }
+      const T ay = g.kyd[ky] * invn;
+      v[0][s] = cmk<T>(-ax * P.y, ax * P.x);
+      v[1][s] = cmk<T>(-ay * P.y, ay * P.x);
+    }
+    cx<T>* const sl[2] = {cur + b, cur + se + b};
+    fft_canon<+1, 2>(v, sl, g.tc, j, g.lny, g.twy);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const size_t idx = (size_t)(j + s * NY8) * H + kx;
+      Gx[idx] = v[0][s];
+      Gy[idx] = v[1][s];
+    }
+    __syncthreads();
+    half ^= 1;
+  }
+  cp_async_wait_all();
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restrict__ Qx,
+                                                  const cx<T>* __restrict__ Qy,
+                                                  const cx<T>* __restrict__ d,
+                                                  const cx<T>* __restrict__ bvec,
+                                                  cx<T>* __restrict__ out, cx<float>* __restrict__ r32,
+                                                  cx<float>* __restrict__ delta32, SolveState* st) {
+  if (MODE == CD_CG && st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const int H = g.H, se = slab_elems(g), ntiles = g.H >> g.ltc;
+  const int b = threadIdx.x & (g.tc - 1), j = threadIdx.x >> g.ltc, NY8 = 1 << (g.lny - 3);
+  DotAcc<T> dq, r64acc;
+  DotAcc<float> r32acc, rzacc;
+  T kappa = 0;
+  float kappa_f = 0.0f;
+  if (MODE == CD_RESID) kappa = (T)st->kappa;
+  if (MODE == CD_RESID_REFINE) kappa_f = (float)st->kappa;
+  double accr[2] = {0.0, 0.0};
+  int half = 0;
+  int tile = blockIdx.x;
+  if (tile < ntiles) stage_cols<T, 2>(g, Qx, Qy, sm, se, tile << g.ltc);
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    if (nxt < ntiles) stage_cols<T, 2>(g, Qx, Qy, sm + (half ^ 1) * 2 * se, se, nxt << g.ltc);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+    cx<T>* cur = sm + half * 2 * se;
+    const int kx = (tile << g.ltc) + b;
+    cx<T> aux[8];  // d (CG) or b (residual), fetched early to overlap the FFT
+    if (MODE == CD_CG || MODE == CD_RESID || MODE == CD_RESID_REFINE) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) aux[s] = (MODE == CD_CG ? d : bvec)[(size_t)(j + s * NY8) * H + kx];
+    }
+    cx<T> v[2][8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int e = padk(j + s * NY8) * g.tc + b;
+      v[0][s] = cur[e];
+      v[1][s] = cur[se + e];
+    }
+    cx<T>* const sl[2] = {cur + b, cur + se + b};
+    fft_canon<-1, 2>(v, sl, g.tc, j, g.lny, g.twy);
+    const T ax = g.kxd[kx];
+    const double w = kx == 0 ? 1.0 : 2.0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int ky = j + s * NY8;
+      const size_t idx = (size_t)ky * H + kx;
+      const T ay = g.kyd[ky];
+      const cx<T> t = cmk<T>(ax * v[0][s].x + ay * v[1][s].x, ax * v[0][s].y + ay * v[1][s].y);
+      const cx<T> q = cmk<T>(t.y, -t.x);
+      if constexpr (MODE == CD_PLAIN) {
+        out[idx] = q;
+      } else if constexpr (MODE == CD_CG) {
+        out[idx] = q;
+        const T wt = (T)w;
+        dq.add_prod(wt * aux[s].x, q.x);
+        dq.add_prod(wt * aux[s].y, q.y);
+      } else if constexpr (MODE == CD_RESID) {
+        const cx<T> rv = csub(aux[s], q);
+        out[idx] = rv;
+        const double r2 = (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
+        accr[0] += w * r2;
+        accr[1] += w * r2 * (double)pinv_sym(g, kx, ky, kappa);
+      } else {
+        const cx<T> rv = csub(aux[s], q);
+        out[idx] = rv;
+        const T wt = (T)(float)w;
+        r64acc.add_prod(wt * rv.x, rv.x);
+        r64acc.add_prod(wt * rv.y, rv.y);
+        const cx<float> rf = ccast<float>(rv);
+        r32[idx] = rf;
+        delta32[idx] = czero<float>();
+        const float wf = (float)w, wpf = wf * pinv_f32(g, kx, ky, kappa_f);
+        r32acc.add_prod(wf * rf.x, rf.x);
+        r32acc.add_prod(wf * rf.y, rf.y);
+        rzacc.add_prod(wpf * rf.x, rf.x);
+        rzacc.add_prod(wpf * rf.y, rf.y);
+      }
+    }
+    __syncthreads();
+    half ^= 1;
+  }
+  cp_async_wait_all();
+  if constexpr (MODE == CD_PLAIN) return;
+  if constexpr (MODE == CD_CG) {
+    double a1[1] = {dq.value()}, t1[1];
+    if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0) {
+      const double dqv = t1[0];
+      if (dqv > 0 && isfinite(dqv)) {
+        st->alpha = st->rho / dqv;
+      } else {
+        st->alpha = 0;
+        st->done = 1;
+        if (!isfinite(dqv)) st->status = HC_ENONFINITE;
+      }
+      st->first = 0;
+    }
+  } else if constexpr (MODE == CD_RESID) {
+    double t2[2];
+    if (last_cta_sum<2>(accr, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
+      resid_init(st, t2[0], t2[1]);
+  } else {
+    double acc[3] = {r64acc.value(), r32acc.value(), rzacc.value()}, tot[3];
+    if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot) && threadIdx.x == 0)
+      resid_refine_init(st, tot[0], tot[1], tot[2]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) kp_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const int H = g.H, ny = g.ny, se = slab_elems(g), ntiles = g.H >> g.ltc;
+  const int b = threadIdx.x & (g.tc - 1), j = threadIdx.x >> g.ltc, NY8 = 1 << (g.lny - 3);
+  const T invn = (T)(1.0 / ((double)g.nx * (double)ny));
+  int half = 0;
+  int tile = blockIdx.x;
+  if (tile < ntiles) stage_cols<T, 2>(g, Mx, My, sm, se, tile << g.ltc);
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    if (nxt < ntiles) stage_cols<T, 2>(g, Mx, My, sm + (half ^ 1) * 2 * se, se, nxt << g.ltc);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+    cx<T>* cur = sm + half * 2 * se;
+    const int kx = (tile << g.ltc) + b;
+    cx<T> v[2][8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int e = padk(j + s * NY8) * g.tc + b;
+      v[0][s] = cur[e];
+      v[1][s] = cur[se + e];
+    }
+    cx<T>* const sl[2] = {cur + b, cur + se + b};
+    fft_canon<-1, 2>(v, sl, g.tc, j, g.lny, g.twy);
+    if (tile == 0) {
+      // packed kx = 0 / nx/2 column: separate with the ky <-> -ky symmetry
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int e = padk(j + s * NY8) * g.tc;
+        sl[0][e] = v[0][s];
+        sl[1][e] = v[1][s];
+      }
+      __syncthreads();
+      if (b == 0) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int ky = j + s * NY8;
+          const int kn = (ny - ky) & (ny - 1);
+          const T h0 = g.hx[0] * g.hy[ky] * invn, hN = g.hx[H] * g.hy[ky] * invn;
+          const T hp = (T)0.5 * (h0 + hN), hm = (T)0.5 * (h0 - hN);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const cx<T> pn = sl[q][padk(kn) * g.tc];
+            v[q][s] = cmk<T>(hp * v[q][s].x + hm * pn.x, hp * v[q][s].y - hm * pn.y);
+          }
+        }
+      }
+    }
+    if (kx != 0) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const T h = g.hx[kx] * g.hy[j + s * NY8] * invn;
+        v[0][s] = cscale(v[0][s], h);
+        v[1][s] = cscale(v[1][s], h);
+      }
+    }
+    fft_canon<+1, 2>(v, sl, g.tc, j, g.lny, g.twy);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const size_t idx = (size_t)(j + s * NY8) * H + kx;
+      Mx[idx] = v[0][s];
+      My[idx] = v[1][s];
+    }
+    __syncthreads();
+    half ^= 1;
+  }
+  cp_async_wait_all();
 }
 
 // ------------------------------------------------------------------ CG update
@@ -965,12 +1318,30 @@ template <typename T>
 void col_inv(const Geo<T>& g, const cx<T>* in, cx<T>* out, T scale, cudaStream_t s) {
   k_col_inv<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 1), s>>>(g, in, out, scale);
 }
+template <typename T>
+static inline size_t pipe_smem(const Geo<T>& g) {
+  return (size_t)4 * (g.ny + (g.ny >> 3)) * g.tc * sizeof(cx<T>);
+}
 template <typename T, typename Tin>
 void col_grad(const Geo<T>& g, int mode, cx<Tin>* in, const cx<T>* rvec, cx<T>* dio,
               const cx<float>* delta, cx<T>* Gx, cx<T>* Gy, SolveState* st, int check_done,
               cudaStream_t s) {
   const int nb = g.H >> g.ltc, nt = col_threads(g);
   const size_t sm = col_smem(g, 2);
+  if constexpr (std::is_same<T, Tin>::value) {
+    if (g.pipe) {
+      const size_t ps = pipe_smem(g);
+      if (mode == CG_PLAIN)
+        kp_col_grad<T, CG_PLAIN><<<g.pgrid, nt, ps, s>>>(g, in, rvec, dio, delta, Gx, Gy, st, check_done);
+      else if (mode == CG_DUPDATE)
+        kp_col_grad<T, CG_DUPDATE><<<g.pgrid, nt, ps, s>>>(g, in, rvec, dio, delta, Gx, Gy, st,
+                                                          check_done);
+      else
+        kp_col_grad<T, CG_ADDDELTA><<<g.pgrid, nt, ps, s>>>(g, in, rvec, dio, delta, Gx, Gy, st,
+                                                           check_done);
+      return;
+    }
+  }
   if (mode == CG_PLAIN)
     k_col_grad<T, Tin, CG_PLAIN><<<nb, nt, sm, s>>>(g, in, rvec, dio, delta, Gx, Gy, st, check_done);
   else if (mode == CG_DUPDATE)
@@ -986,6 +1357,24 @@ void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const 
              cudaStream_t s) {
   const int nb = g.H >> g.ltc, nt = col_threads(g);
   const size_t sm = col_smem(g, 2);
+  if (g.pipe) {
+    const size_t ps = pipe_smem(g);
+    switch (mode) {
+      case CD_PLAIN:
+        kp_col_div<T, CD_PLAIN><<<g.pgrid, nt, ps, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
+        break;
+      case CD_CG:
+        kp_col_div<T, CD_CG><<<g.pgrid, nt, ps, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
+        break;
+      case CD_RESID:
+        kp_col_div<T, CD_RESID><<<g.pgrid, nt, ps, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
+        break;
+      default:
+        kp_col_div<T, CD_RESID_REFINE><<<g.pgrid, nt, ps, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
+        break;
+    }
+    return;
+  }
   switch (mode) {
     case CD_PLAIN:
       k_col_div<T, CD_PLAIN><<<nb, nt, sm, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
@@ -1003,6 +1392,10 @@ void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const 
 }
 template <typename T>
 void col_heat(const Geo<T>& g, cx<T>* Mx, cx<T>* My, cudaStream_t s) {
+  if (g.pipe) {
+    kp_col_heat<T><<<g.pgrid, col_threads(g), pipe_smem(g), s>>>(g, Mx, My);
+    return;
+  }
   k_col_heat<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 2), s>>>(g, Mx, My);
 }
 template <typename T>
@@ -1046,6 +1439,14 @@ void set_smem_limits_t() {
   allow_smem(k_col_div<T, CD_CG>);
   allow_smem(k_col_div<T, CD_RESID>);
   allow_smem(k_col_div<T, CD_RESID_REFINE>);
+  allow_smem(kp_col_div<T, CD_PLAIN>);
+  allow_smem(kp_col_div<T, CD_CG>);
+  allow_smem(kp_col_div<T, CD_RESID>);
+  allow_smem(kp_col_div<T, CD_RESID_REFINE>);
+  allow_smem(kp_col_heat<T>);
+  allow_smem(kp_col_grad<T, CG_PLAIN>);
+  allow_smem(kp_col_grad<T, CG_DUPDATE>);
+  allow_smem(kp_col_grad<T, CG_ADDDELTA>);
 }
 template <typename T, typename Tin>
 void set_smem_limits_grad() {

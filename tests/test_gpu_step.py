@@ -67,11 +67,12 @@ def test_fp64_plain_100_steps_64(hc):
         assert rel_l2(s.get_p(), p) <= 1e-9
 
 
-def test_graph_and_host_loop_agree_bitwise(hc):
+@pytest.mark.parametrize("precision", ["fp32_refined", "fp32_refined_df"])
+def test_graph_and_host_loop_agree_bitwise(hc, precision):
     w = W.source_sink_2d(128, steps=3)
     outs = []
     for use_graph in (True, False):
-        with make_solver(hc, w, "fp32_refined", use_graph=use_graph) as s:
+        with make_solver(hc, w, precision, use_graph=use_graph) as s:
             st = s.step(3)
             outs.append((s.get_m(), s.get_p(), st.cg_iters, st.refine_sweeps))
     assert np.array_equal(outs[0][0], outs[1][0])
@@ -79,15 +80,16 @@ def test_graph_and_host_loop_agree_bitwise(hc):
     assert outs[0][2:] == outs[1][2:]
 
 
-def test_refined_512_hundred_steps(hc):
-    """512^2 source/sink workload, FP32 + FP64 refinement vs the FP64 oracle:
-    pressure relative residual <= 1e-8 at every step, m relative L2 <= 1e-5
-    after 100 steps."""
+@pytest.mark.parametrize("precision", ["fp32_refined", "fp32_refined_df"])
+def test_refined_512_hundred_steps(hc, precision):
+    """512^2 source/sink workload, FP32 + FP64(-class) refinement vs the FP64
+    oracle: pressure relative residual <= 1e-8 at every step, m relative L2
+    <= 1e-5 after 100 steps."""
     w = W.source_sink_2d(512, steps=100)
     g = O.Grid(w.n, w.L)
     prm = oprm(w, rtol=1e-10)
     m, p = w.m0.copy(), np.zeros(g.shape)
-    with make_solver(hc, w, "fp32_refined", rtol=1e-8) as s:
+    with make_solver(hc, w, precision, rtol=1e-8) as s:
         for k in range(w.steps):
             st = s.step(1)
             assert st.status == 0 and st.rel_residual <= 1e-8, (k, st)
@@ -102,13 +104,14 @@ def test_refined_512_hundred_steps(hc):
     assert ep <= 1e-5, ep
 
 
-def test_refined_residual_recomputed_by_oracle(hc):
-    """The FP64 residual the refined path certifies is the true one: recompute
-    ||S - A p|| / ||S|| with the oracle's operator for the GPU's p and the
+@pytest.mark.parametrize("precision", ["fp32_refined", "fp32_refined_df"])
+def test_refined_residual_recomputed_by_oracle(hc, precision):
+    """The residual the refined path certifies is the true one: recompute
+    ||S - A p|| / ||S|| with the oracle's FP64 operator for the GPU's p and the
     FP32-rounded m/r it solved with."""
     w = W.source_sink_2d(256, steps=1)
     g = O.Grid(w.n, w.L)
-    with make_solver(hc, w, "fp32_refined", rtol=1e-9) as s:
+    with make_solver(hc, w, precision, rtol=1e-9) as s:
         st = s.step(1)
         p = s.get_p()
     m32 = w.m0.astype(np.float32).astype(np.float64)
@@ -120,7 +123,8 @@ def test_refined_residual_recomputed_by_oracle(hc):
     assert abs(res - st.rel_residual) <= 1e-10 + 0.2 * res
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32_refined", 1e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32_refined", 1e-5),
+                                           ("fp32_refined_df", 1e-5)])
 def test_headline_2048_one_step(hc, precision, tol):
     """2048^2 source/sink workload in the launch configuration the benchmark
     times (graph mode): one step against the oracle at full size."""
@@ -198,15 +202,19 @@ def test_tuning_changes_only_summation_order(hc):
     outs = []
     with make_solver(hc, w, "fp64") as s:
         base = s.get_tuning()
-        for col, row in [((1, 1), (1, 1)), ((4, 2), (2, 1)), ((8, 4), (1, 2))]:
-            s.set_tuning(list(col), list(row))
+        for col, row, pipe in [((1, 1), (1, 1), (0, 0)), ((4, 2), (2, 1), (0, 0)),
+                               ((8, 4), (1, 2), (0, 0)), ((2, 1), (1, 1), (1, 1)),
+                               ((8, 4), (1, 1), (1, 1))]:
+            s.set_tuning(list(col), list(row), list(pipe))
             s.set_m(w.m0)
             s.set_p(np.zeros(w.shape))
             st = s.step(2)
             outs.append((s.get_m(), s.get_p()))
         for bad in [((3, 1), (1, 1)), ((64, 1), (1, 1)), ((1, 1), (1, 1024)), ((1, 0), (1, 1))]:
             with pytest.raises(hc.HuCaiError):
-                s.set_tuning(list(bad[0]), list(bad[1]))
+                s.set_tuning(list(bad[0]), list(bad[1]), [0, 0])
+        with pytest.raises(hc.HuCaiError):  # FP32 tile of 8 bytes: no 16-byte cp.async
+            s.set_tuning([1, 1], [1, 1], [1, 0])
         assert s.get_tuning()["col_tile"] == [8, 4]
     for m, p in outs[1:]:
         assert rel_l2(m, outs[0][0]) < 1e-12 and rel_l2(p, outs[0][1]) < 1e-11
@@ -225,3 +233,20 @@ def test_autotuner_picks_admissible_shapes(hc, tmp_path, monkeypatch):
         assert t2 == t
         st = s.step(1)
         assert st.status == 0 and st.rel_residual <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp32_refined", "fp32_refined_df"])
+def test_pipelined_column_passes_match_plain_ones(hc, precision):
+    """The persistent cp.async column passes compute the same step as the
+    one-tile-per-CTA passes (to the rounding of regrouped reductions)."""
+    w = W.source_sink_2d(512, steps=3)
+    outs = []
+    for pipe in ((0, 0), (1, 1)):
+        with make_solver(hc, w, precision) as s:
+            t = s.get_tuning()
+            s.set_tuning([2, 1], t["row_rows"], list(pipe))
+            st = s.step(3)
+            assert st.status == 0 and st.rel_residual <= w.cg_rtol
+            outs.append((s.get_m(), s.get_p()))
+    assert rel_l2(outs[1][0], outs[0][0]) < 1e-6
+    assert rel_l2(outs[1][1], outs[0][1]) < 1e-6
