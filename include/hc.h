@@ -196,6 +196,26 @@ int hc_time_kernel(hc_ctx* ctx, int kernel, int reps, double* ms_per_launch);
  * (graph launches count every kernel node). */
 int hc_launch_count(const hc_ctx* ctx, long long* count);
 
+/* --- Batched parameter sweeps --- */
+
+typedef struct hc_batch hc_batch; /* opaque; refers to (does not own) its contexts */
+
+/* Group `count` existing contexts (any mix of grids, parameters and precisions)
+ * so that one CUDA graph launch on `stream` advances every one of them by a
+ * step: the graph holds each context's step as an independent chain with its
+ * own device-side CG/refinement loops, so small grids run side by side.  The
+ * contexts must stay alive and keep their grids until hc_batch_destroy;
+ * changing a context's parameters or tuning afterwards requires rebuilding the
+ * batch.  Errors: HC_EINVAL (null/duplicate contexts, count < 1), HC_ECUDA. */
+int hc_batch_create(hc_batch** out, hc_ctx* const* ctxs, int count, void* stream);
+
+/* nsteps batched steps.  stats (may be NULL) receives count entries, the last
+ * step of each context.  Returns HC_OK or the first non-OK step status of any
+ * context (as hc_step does). */
+int hc_batch_step(hc_batch* batch, int nsteps, hc_step_stats* stats);
+
+void hc_batch_destroy(hc_batch* batch);
+
 /* --- Transform without device allocation (the paper has no counterpart) --- */
 
 #define HC_NOALLOC_MAX_POINTS 65536 /* nx*ny limit of hc_spectrum_noalloc */

@@ -87,6 +87,9 @@ def _load() -> C.CDLL:
         "hc_get_tuning": ([P, C.POINTER(hc_tuning)], C.c_int),
         "hc_set_tuning": ([P, C.POINTER(hc_tuning)], C.c_int),
         "hc_spectrum_noalloc": ([P, P, C.c_int, C.c_int, P], C.c_int),
+        "hc_batch_create": ([C.POINTER(P), C.POINTER(P), C.c_int, P], C.c_int),
+        "hc_batch_step": ([P, C.c_int, C.POINTER(hc_step_stats)], C.c_int),
+        "hc_batch_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -118,6 +121,9 @@ hc_time_kernel = lib.hc_time_kernel
 hc_get_tuning = lib.hc_get_tuning
 hc_set_tuning = lib.hc_set_tuning
 hc_spectrum_noalloc = lib.hc_spectrum_noalloc
+hc_batch_create = lib.hc_batch_create
+hc_batch_step = lib.hc_batch_step
+hc_batch_destroy = lib.hc_batch_destroy
 
 # kernel ids of hc_time_kernel (include/hc.h)
 KERNELS = ["cg_grad", "cg_apply", "cg_div", "cg_update", "res_grad", "res_apply", "res_div",
@@ -319,3 +325,41 @@ class Solver:
         v = C.c_longlong()
         _check(hc_launch_count(self.ctx, C.byref(v)), "hc_launch_count")
         return v.value
+
+
+class Batch:
+    """Several Solvers advanced together: one CUDA graph launch per step runs
+    every solver's step as an independent chain (hc_batch_*)."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.solvers = list(solvers)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.solvers[0].device)
+        arr = (C.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
+        self.b = C.c_void_p()
+        _check(hc_batch_create(C.byref(self.b), arr, len(self.solvers),
+                               C.c_void_p(self.stream.cuda_stream)), "hc_batch_create")
+
+    def step(self, nsteps: int = 1, allow=(HC_OK, HC_ENOCONV)):
+        st = (hc_step_stats * len(self.solvers))()
+        rc = hc_batch_step(self.b, int(nsteps), st)
+        _check(rc, "hc_batch_step", ok=allow)
+        return [StepStats(x.cg_iters, x.refine_sweeps, x.rel_residual, x.kappa, x.status, rc,
+                          x.total_cg_iters, x.total_sweeps) for x in st]
+
+    def close(self):
+        if getattr(self, "b", None) and self.b.value:
+            hc_batch_destroy(self.b)
+            self.b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -98,6 +98,8 @@ struct hc_ctx {
   // legacy default stream), launched on `stream`
   cudaStream_t cap_stream;
   cudaGraphExec_t gexec;
+  cudaGraphConditionalHandle h_own[2];  // handles of the context's own graph
+  int batch_handles;                    // 1 while st holds a batch graph's handles
   bool graph_ready;
   int graph_nodes_fixed, graph_nodes_body, graph_nodes_outer;
 };
@@ -515,76 +517,43 @@ int step_host(hc_ctx* c) {
 // run is skipped rather than repeated: step_begin opens the refinement loop,
 // the residual kernels open the CG loop, cg_update keeps it open while the
 // iteration cap and tolerance allow.
-int build_graph_on(hc_ctx* c);
-
-int build_graph(hc_ctx* c) {
-  if (!c->cap_stream) CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-  // everything issued before the capture must be complete: the private stream
-  // does not order against the context's stream
-  CU(cudaStreamSynchronize(c->stream));
-  cudaStream_t keep = c->stream;
-  c->stream = c->cap_stream;
-  long long before = c->launches;
-  int rc = build_graph_on(c);
-  c->stream = keep;
-  c->launches = before;  // capture launched nothing
-  if (rc) {
-    cudaStreamCaptureStatus cs;
-    if (cudaStreamIsCapturing(c->cap_stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
-      cudaGraph_t junk = nullptr;
-      cudaStreamEndCapture(c->cap_stream, &junk);
-      if (junk) cudaGraphDestroy(junk);
-    }
-    cudaGetLastError();
-  }
-  return rc;
-}
-
-int build_graph_on(hc_ctx* c) {
-  cudaGraph_t graph;
-  CU(cudaGraphCreate(&graph, 0));
-  cudaGraphConditionalHandle h_inner = 0, h_outer = 0;
-  // capture the straight-line prefix
+// Capture the step of context c into `target` as a chain with no dependencies
+// on what `target` already holds: the prefix kernels, the loop node(s), the
+// suffix kernels.  Returns the chain's conditional handles.  c->stream must be
+// a non-default stream that is not capturing.
+int build_chain(hc_ctx* c, cudaGraph_t target, cudaGraphConditionalHandle* hin,
+                cudaGraphConditionalHandle* hout) {
   cudaStream_t s = c->stream;
-  CU(cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaGraphConditionalHandle h_inner = 0, h_outer = 0;
+  CU(cudaStreamBeginCaptureToGraph(s, target, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   hc::step_begin(c->st, (int)c->n, s);
-  c->launches += 1;
   if (!c->refined) plain_init(c);
-  CU(cudaStreamEndCapture(s, &graph));
-  // the loop node(s), appended after the current sink of the graph
-  auto sink_of = [&](cudaGraph_t gr, cudaGraphNode_t& out) -> int {
-    size_t nn = 0;
-    CU(cudaGraphGetNodes(gr, nullptr, &nn));
-    std::vector<cudaGraphNode_t> nodes(nn);
-    CU(cudaGraphGetNodes(gr, nodes.data(), &nn));
-    out = nullptr;
-    for (auto nd : nodes) {
-      size_t nout = 0;
-      CU(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nout));
-      if (nout == 0) out = nd;
-    }
-    return HC_OK;
-  };
-  cudaGraphNode_t tail;
-  if (sink_of(graph, tail)) return HC_ECUDA;
-  cudaGraph_t loop_owner = graph;
+  // the chain's current tail, before leaving capture
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CU(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+  std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
+  cudaGraph_t same = target;
+  CU(cudaStreamEndCapture(s, &same));
   cudaGraphNode_t loop_node;
   cudaGraph_t body;
   if (c->refined) {
-    CU(cudaGraphConditionalHandleCreate(&h_outer, graph, 0, cudaGraphCondAssignDefault));
+    CU(cudaGraphConditionalHandleCreate(&h_outer, target, 0, cudaGraphCondAssignDefault));
     cudaGraphNodeParams op = {};
     op.type = cudaGraphNodeTypeConditional;
     op.conditional.handle = h_outer;
     op.conditional.type = cudaGraphCondTypeWhile;
     op.conditional.size = 1;
-    CU(cudaGraphAddNode(&loop_node, graph, &tail, nullptr, 1, &op));
+    CU(cudaGraphAddNode(&loop_node, target, tail.data(), nullptr, tail.size(), &op));
     cudaGraph_t obody = op.conditional.phGraph_out[0];
     CU(cudaStreamBeginCaptureToGraph(s, obody, nullptr, nullptr, 0,
                                      cudaStreamCaptureModeThreadLocal));
     refined_resid(c);
-    CU(cudaStreamEndCapture(s, &obody));
-    cudaGraphNode_t otail;
-    if (sink_of(obody, otail)) return HC_ECUDA;
+    CU(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+    std::vector<cudaGraphNode_t> otail(deps, deps + ndeps);
+    cudaGraph_t same_o = obody;
+    CU(cudaStreamEndCapture(s, &same_o));
     CU(cudaGraphConditionalHandleCreate(&h_inner, obody, 0, cudaGraphCondAssignDefault));
     cudaGraphNodeParams ip = {};
     ip.type = cudaGraphNodeTypeConditional;
@@ -592,17 +561,16 @@ int build_graph_on(hc_ctx* c) {
     ip.conditional.type = cudaGraphCondTypeWhile;
     ip.conditional.size = 1;
     cudaGraphNode_t inode;
-    CU(cudaGraphAddNode(&inode, obody, &otail, nullptr, 1, &ip));
+    CU(cudaGraphAddNode(&inode, obody, otail.data(), nullptr, otail.size(), &ip));
     body = ip.conditional.phGraph_out[0];
-    loop_owner = graph;
   } else {
-    CU(cudaGraphConditionalHandleCreate(&h_inner, graph, 0, cudaGraphCondAssignDefault));
+    CU(cudaGraphConditionalHandleCreate(&h_inner, target, 0, cudaGraphCondAssignDefault));
     cudaGraphNodeParams ip = {};
     ip.type = cudaGraphNodeTypeConditional;
     ip.conditional.handle = h_inner;
     ip.conditional.type = cudaGraphCondTypeWhile;
     ip.conditional.size = 1;
-    CU(cudaGraphAddNode(&loop_node, graph, &tail, nullptr, 1, &ip));
+    CU(cudaGraphAddNode(&loop_node, target, tail.data(), nullptr, tail.size(), &ip));
     body = ip.conditional.phGraph_out[0];
   }
   CU(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -610,22 +578,68 @@ int build_graph_on(hc_ctx* c) {
     refined_iter(c);
   else
     plain_iter(c);
-  CU(cudaStreamEndCapture(s, &body));
-  // suffix: split step and step end, after the loop node
-  CU(cudaStreamBeginCaptureToGraph(s, loop_owner, &loop_node, nullptr, 1,
+  cudaGraph_t same_b = body;
+  CU(cudaStreamEndCapture(s, &same_b));
+  CU(cudaStreamBeginCaptureToGraph(s, target, &loop_node, nullptr, 1,
                                    cudaStreamCaptureModeThreadLocal));
   split_step(c);
   hc::step_end(c->st, c->refined, s);
-  c->launches += 1;
-  CU(cudaStreamEndCapture(s, &graph));
-  CU(cudaGraphInstantiate(&c->gexec, graph, 0));
-  CU(cudaGraphDestroy(graph));
+  CU(cudaStreamEndCapture(s, &same));
+  *hin = h_inner;
+  *hout = h_outer;
+  return HC_OK;
+}
+
+void abort_capture(cudaStream_t s) {
+  cudaStreamCaptureStatus cs;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(s, &junk);
+  }
+  cudaGetLastError();
+}
+
+// Device handles the kernels drive: the context's own graph or a batch graph.
+int use_handles(hc_ctx* c, cudaGraphConditionalHandle hin, cudaGraphConditionalHandle hout) {
+  unsigned long long v[2] = {hin, hout};
+  CU(cudaMemcpy(&c->st->h_inner, v, sizeof(v), cudaMemcpyHostToDevice));
+  return HC_OK;
+}
+
+// One graph per context: step_begin, [plain: init residual, WHILE(cg) body]
+// or [refined: WHILE(outer){ residual, WHILE(inner) body }], split step,
+// step_end.  Loop conditions are set by the kernels (cudaGraphSetConditional)
+// and default to 0 at every launch, so a loop whose controlling kernel did not
+// run is skipped rather than repeated: step_begin opens the refinement loop,
+// the residual kernels open the CG loop, cg_update keeps it open while the
+// iteration cap and tolerance allow.
+int build_graph(hc_ctx* c) {
+  if (!c->cap_stream) CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  // everything issued before the capture must be complete: the private stream
+  // does not order against the context's stream
+  CU(cudaStreamSynchronize(c->stream));
+  cudaGraph_t graph;
+  CU(cudaGraphCreate(&graph, 0));
+  cudaStream_t keep = c->stream;
+  long long before = c->launches;
+  c->stream = c->cap_stream;
+  cudaGraphConditionalHandle hin = 0, hout = 0;
+  int rc = build_chain(c, graph, &hin, &hout);
+  c->stream = keep;
+  c->launches = before;  // capture launched nothing
+  if (rc) {
+    abort_capture(c->cap_stream);
+    cudaGraphDestroy(graph);
+    return rc;
+  }
+  cudaError_t e = cudaGraphInstantiate(&c->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __LINE__);
   c->graph_nodes_fixed = c->refined ? 1 + 4 + 1 : 1 + 3 + 4 + 1;
   c->graph_nodes_body = 4;
   c->graph_nodes_outer = 3;
-  // hand the handles to the kernels
-  CU(cudaMemcpy(&c->st->h_inner, &h_inner, sizeof(h_inner), cudaMemcpyHostToDevice));
-  CU(cudaMemcpy(&c->st->h_outer, &h_outer, sizeof(h_outer), cudaMemcpyHostToDevice));
+  c->h_own[0] = hin;
+  c->h_own[1] = hout;
   c->graph_ready = true;
   return HC_OK;
 }
@@ -709,6 +723,9 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   c->n = (size_t)c->nx * c->ny;
   c->refined = params->precision != HC_FP64_PLAIN;
   c->df = params->precision == HC_FP32_REFINED_DF;
+  c->graph_nodes_fixed = c->refined ? 1 + 4 + 1 : 1 + 3 + 4 + 1;
+  c->graph_nodes_body = 4;
+  c->graph_nodes_outer = 3;
   c->stream = (cudaStream_t)params->stream;
   c->mean_r = 1.0;
   if (workspace) {
@@ -912,7 +929,10 @@ int hc_step(hc_ctx* c, int nsteps, hc_step_stats* last) {
       int rc = build_graph(c);
       if (rc) return rc;
     }
-    int rc = set_graph_mode(c, 1);
+    int rc = use_handles(c, c->h_own[0], c->h_own[1]);
+    if (rc) return rc;
+    c->batch_handles = 0;
+    rc = set_graph_mode(c, 1);
     if (rc) return rc;
     for (int k = 0; k < nsteps; ++k) CU(cudaGraphLaunch(c->gexec, c->stream));
     rc = read_state(c);
@@ -1044,6 +1064,117 @@ int hc_spectrum(hc_ctx* c, const double* f, double* out, size_t count) {
 }
 
 const char* hc_last_cuda_error(void) { return g_last_error; }
+
+}  // extern "C"
+
+struct hc_batch {
+  std::vector<hc_ctx*> ctx;
+  std::vector<cudaGraphConditionalHandle> hin, hout;
+  cudaStream_t stream;
+  cudaStream_t cap;
+  cudaGraphExec_t exec;
+  bool ready;
+};
+
+extern "C" {
+
+int hc_batch_create(hc_batch** out, hc_ctx* const* ctxs, int count, void* stream) {
+  if (!out || !ctxs || count < 1) return HC_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) return HC_EINVAL;
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return HC_EINVAL;
+  }
+  hc_batch* b = new (std::nothrow) hc_batch;
+  if (!b) return HC_ENOMEM;
+  b->ctx.assign(ctxs, ctxs + count);
+  b->hin.assign(count, 0);
+  b->hout.assign(count, 0);
+  b->stream = (cudaStream_t)stream;
+  b->cap = nullptr;
+  b->ready = false;
+  auto fail = [&](int rc) {
+    if (b->cap) {
+      abort_capture(b->cap);
+      cudaStreamDestroy(b->cap);
+    }
+    delete b;
+    return rc;
+  };
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(HC_ECUDA);
+  cudaGraph_t graph;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return fail(HC_ECUDA);
+  for (int i = 0; i < count; ++i) {
+    hc_ctx* c = b->ctx[i];
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return fail(HC_ECUDA);
+    }
+    cudaStream_t keep = c->stream;
+    long long before = c->launches;
+    c->stream = b->cap;
+    int rc = build_chain(c, graph, &b->hin[i], &b->hout[i]);
+    c->stream = keep;
+    c->launches = before;
+    if (rc) {
+      cudaGraphDestroy(graph);
+      return fail(rc);
+    }
+  }
+  cudaError_t e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "cudaGraphInstantiate", __LINE__);
+    return fail(HC_ECUDA);
+  }
+  b->ready = true;
+  *out = b;
+  return HC_OK;
+}
+
+int hc_batch_step(hc_batch* b, int nsteps, hc_step_stats* stats) {
+  if (!b || nsteps < 0) return HC_EINVAL;
+  if (nsteps == 0) return HC_OK;
+  const int n = (int)b->ctx.size();
+  for (int i = 0; i < n; ++i) {
+    hc_ctx* c = b->ctx[i];
+    CU(cudaStreamSynchronize(c->stream));
+    int rc = use_handles(c, b->hin[i], b->hout[i]);
+    if (rc) return rc;
+    c->batch_handles = 1;
+    rc = set_graph_mode(c, 1);
+    if (rc) return rc;
+    hc::reset_accum(c->st, b->stream);
+    c->launches += 1;
+  }
+  for (int k = 0; k < nsteps; ++k) CU(cudaGraphLaunch(b->exec, b->stream));
+  for (int i = 0; i < n; ++i)
+    CU(cudaMemcpyAsync(b->ctx[i]->st_host, b->ctx[i]->st, sizeof(hc::SolveState),
+                       cudaMemcpyDeviceToHost, b->stream));
+  CU(cudaStreamSynchronize(b->stream));
+  int first_bad = HC_OK;
+  for (int i = 0; i < n; ++i) {
+    hc_ctx* c = b->ctx[i];
+    const hc::SolveState& h = *c->st_host;
+    c->launches += (long long)c->graph_nodes_fixed * nsteps + (long long)c->graph_nodes_body * h.acc_iters;
+    if (c->refined) c->launches += (long long)c->graph_nodes_outer * (h.acc_sweeps + nsteps);
+    if (stats) fill_stats(c, &stats[i]);
+    if (!first_bad && h.first_bad) first_bad = h.first_bad;
+    int rc = set_graph_mode(c, 0);
+    if (rc) return rc;
+  }
+  return first_bad;
+}
+
+void hc_batch_destroy(hc_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  if (b->ready) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
 
 int hc_get_tuning(const hc_ctx* c, hc_tuning* t) {
   if (!c || !t) return HC_EINVAL;

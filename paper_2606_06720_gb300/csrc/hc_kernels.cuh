@@ -576,6 +576,7 @@ __device__ __forceinline__ void resid_init(SolveState* st, double r2, double rz)
 
 // Refinement sweep start (one thread): r64 = ||S - A p64||^2 decides the outer
 // loop; r32, rz start the inner FP32 CG on A delta = r32 from delta = 0.
+// (r32 is r64 rounded to FP32, so both norms are on the same scale.)
 __device__ __forceinline__ void resid_refine_init(SolveState* st, double r64, double r32,
                                                   double rz) {
   st->outer_r2 = r64;
@@ -586,7 +587,9 @@ __device__ __forceinline__ void resid_refine_init(SolveState* st, double r64, do
   else if (!conv && st->outer_done) st->status = HC_ENOCONV;
   else st->status = 0;
   st->bnorm2 = r32;
-  st->thresh2 = st->inner_rtol2 * r32;
+  // the inner solve only has to bring this sweep below the outer target: stop
+  // at the larger of its own relative reduction and a tenth of the target
+  st->thresh2 = fmax(st->inner_rtol2 * r32, 0.01 * st->outer_thresh2);
   st->rnorm2 = r32;
   st->rho = rz;
   st->it = 0;
