@@ -94,6 +94,8 @@ def _load():
             lib.or_step.argtypes = [gp, C.POINTER(_Params), dp, dp, dp, dp, C.POINTER(_Stats)]
             lib.or_energy.argtypes = [gp, C.POINTER(_Params), dp, dp, dp]
             lib.or_energy.restype = C.c_double
+            lib.or_adjoint.argtypes = [gp, C.POINTER(_Params), dp, dp, dp, dp, C.c_int, dp, dp, dp,
+                                       dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -314,3 +316,21 @@ def energy(grid: Grid, prm: Params, r, m, p) -> float:
     g = grid.c()
     cp = prm.c_struct()
     return _load().or_energy(C.byref(g), C.byref(cp), _dp(r), _dp(m), _dp(p))
+
+
+def adjoint(grid: Grid, prm: Params, r, S, m0, p0, nsteps: int, lamT):
+    """Discrete adjoint of `nsteps` steps: returns dict with dc2, dD2 (floats)
+    and dr, dS (fields), dm0 (vector field), for dL/dm(T) = lamT."""
+    r, S = _f64(r), _f64(S)
+    m0 = _f64(m0).reshape((grid.dim,) + grid.shape)
+    p0 = _f64(p0).reshape(grid.shape)
+    lamT = _f64(lamT).reshape((grid.dim,) + grid.shape)
+    dc2, dD2 = C.c_double(), C.c_double()
+    dr, dS = np.empty(grid.shape), np.empty(grid.shape)
+    dm0 = np.empty((grid.dim,) + grid.shape)
+    g = grid.c()
+    cp = prm.c_struct()
+    _check(_load().or_adjoint(C.byref(g), C.byref(cp), _dp(r), _dp(S), _dp(m0), _dp(p0),
+                              int(nsteps), _dp(lamT), C.byref(dc2), C.byref(dD2), _dp(dr),
+                              _dp(dS), _dp(dm0)), "adjoint")
+    return {"dc2": dc2.value, "dD2": dD2.value, "dr": dr, "dS": dS, "dm0": dm0}

@@ -552,3 +552,192 @@ double or_energy(const or_grid* g, const or_params* prm, const double* r, const 
   return h * (0.5 * prm->D * prm->D * e_diff + 0.5 * c2 * e_r + 0.5 * c2 * e_act +
               e_rel / (2.0 * prm->gamma));
 }
+
+/* ------------------------------------------------------------------ */
+/* Discrete adjoint of the step (gradient of a loss on m(T))           */
+/* ------------------------------------------------------------------ */
+/* Forward map of one step, written as the composition the adjoint reverses:
+ *   p' = A(m)^+ P S                  (pressure, exact solve; P = null-space projection)
+ *   g  = G p'                         (spectral gradient)
+ *   a  = m + c^2 dt phi1(z) (m.g) g,  z = c^2 dt |g|^2   (activation, eq. m_activation_discrete)
+ *   b  = a s(|a|)                     (relaxation, eq. m_relaxation_discrete)
+ *   m' = H b,  H = F^-1 diag(exp(-D^2 |xi|^2 dt)) F       (diffusion)
+ * phi1(z) = (e^z - 1)/z is the form in which eq. (m_activation_discrete)
+ * depends on c^2 and g; the oracle's forward substep uses the paper's g-perp
+ * form, which equals it. */
+
+static double phi1(double z) { return z == 0 ? 1.0 : expm1(z) / z; }
+
+/* d phi1 / dz: series for small z (the closed form cancels), else closed form */
+static double dphi1(double z) {
+  if (fabs(z) < 0.5) {
+    /* sum_k z^k / ((k+2) k!) */
+    double term = 1.0, s = 0;
+    for (int k = 0; k < 18; ++k) {
+      if (k > 0) term *= z / k;
+      s += term / (k + 2);
+    }
+    return s;
+  }
+  return ((z - 1.0) * expm1(z) + z) / (z * z);
+}
+
+/* Relaxation b = a s(|a|) and its Jacobian J = s I + (f' - s) a a^T / |a|^2,
+ * f(rho) = rho s(rho) (the new modulus), for one point; returns s and writes
+ * the coefficient c1 = s, c2 = (f' - s)/|a|^2 so that J v = c1 v + c2 (a.v) a. */
+static void relax_jac(int dim, const double* a, double gamma, double dt, double* c1, double* c2) {
+  double n2 = 0;
+  for (int k = 0; k < dim; ++k) n2 += a[k] * a[k];
+  if (gamma == 1.0) { *c1 = exp(-dt); *c2 = 0; return; }
+  if (n2 == 0) { *c1 = gamma > 1.0 ? 1.0 : 0.0; *c2 = 0; return; }
+  double rho = sqrt(n2);
+  double e = 2.0 * (1.0 - gamma); /* b = rho^e - e dt */
+  double beta = pow(rho, e) - e * dt;
+  if (beta <= 0) { *c1 = 0; *c2 = 0; return; }
+  double f = pow(beta, 1.0 / e);
+  double fp = pow(beta, 1.0 / e - 1.0) * pow(rho, e - 1.0); /* df/drho */
+  double sv = f / rho;
+  *c1 = sv;
+  *c2 = (fp - sv) / n2;
+}
+
+int or_adjoint(const or_grid* g, const or_params* prm, const double* r, const double* S,
+               const double* m0, const double* p0, int nsteps, const double* lamT, double* dc2,
+               double* dD2, double* dr, double* dS, double* dm0) {
+  if (!valid_grid(g) || nsteps < 0) return OR_EINVAL;
+  size_t n = or_npts(g);
+  int dim = g->dim;
+  size_t vn = (size_t)dim * n;
+  double c2 = prm->c * prm->c, dtt = prm->dt, D2 = prm->D * prm->D;
+  /* forward, keeping m^k and p^{k+1} */
+  double* ms = (double*)malloc(sizeof(double) * vn * (nsteps + 1));
+  double* ps = (double*)malloc(sizeof(double) * n * (nsteps + 1));
+  double* lam = (double*)malloc(sizeof(double) * vn);
+  double* grad = (double*)malloc(sizeof(double) * vn);
+  double* gmu = (double*)malloc(sizeof(double) * vn);
+  double* a = (double*)malloc(sizeof(double) * vn);
+  double* b = (double*)malloc(sizeof(double) * vn);
+  double* lb = (double*)malloc(sizeof(double) * vn);
+  double* lg = (double*)malloc(sizeof(double) * vn);
+  double* lp = (double*)malloc(sizeof(double) * n);
+  double* mu = (double*)malloc(sizeof(double) * n);
+  double* t = (double*)malloc(sizeof(double) * n);
+  double complex* ct = (double complex*)malloc(sizeof(double complex) * n);
+  int rc = (!ms || !ps || !lam || !grad || !gmu || !a || !b || !lb || !lg || !lp || !mu || !t || !ct)
+               ? OR_ENOMEM : OR_OK;
+  if (!rc) {
+    memcpy(ms, m0, sizeof(double) * vn);
+    memcpy(ps, p0, sizeof(double) * n);
+    for (int k = 0; k < nsteps && !rc; ++k) {
+      memcpy(ms + vn * (k + 1), ms + vn * k, sizeof(double) * vn);
+      memcpy(ps + n * (k + 1), ps + n * k, sizeof(double) * n);
+      or_stats st;
+      int s_rc = or_step(g, prm, r, S, ms + vn * (k + 1), ps + n * (k + 1), &st);
+      if (s_rc && s_rc != OR_ENOCONV) rc = s_rc;
+    }
+  }
+  if (!rc) {
+    *dc2 = 0;
+    *dD2 = 0;
+    memset(dr, 0, sizeof(double) * n);
+    memset(dS, 0, sizeof(double) * n);
+    memcpy(lam, lamT, sizeof(double) * vn);
+  }
+  for (int k = nsteps - 1; k >= 0 && !rc; --k) {
+    const double* m = ms + vn * k;
+    const double* p = ps + n * (k + 1); /* solved with m^k */
+    double kappa = prm->kappa > 0 ? prm->kappa : or_kappa_default(g, m, r);
+    rc = or_gradient(g, p, grad);
+    if (rc) break;
+    /* recompute a and b */
+    memcpy(a, m, sizeof(double) * vn);
+    or_activation(dim, n, a, grad, prm->c, dtt);
+    memcpy(b, a, sizeof(double) * vn);
+    or_relaxation(dim, n, b, prm->gamma, dtt);
+    /* diffusion: lambda_b = H lambda (H symmetric); dL/dD^2 = <lambda, dH/dD^2 b> */
+    memcpy(lb, lam, sizeof(double) * vn);
+    rc = or_diffusion(g, lb, prm->D, dtt);
+    for (int c = 0; c < dim && !rc; ++c) {
+      for (size_t q = 0; q < n; ++q) ct[q] = b[(size_t)c * n + q];
+      rc = or_fftn(g, ct, -1);
+      for (size_t q = 0; q < n && !rc; ++q) {
+        double s2 = 0;
+        for (int ax = 0; ax < dim; ++ax) {
+          double x = or_xi(coord(g, q, ax), g->n[ax], g->L[ax]);
+          s2 += x * x;
+        }
+        ct[q] *= -s2 * dtt * exp(-D2 * s2 * dtt);
+      }
+      if (!rc) rc = or_fftn(g, ct, +1);
+      for (size_t q = 0; q < n && !rc; ++q) *dD2 += lam[(size_t)c * n + q] * creal(ct[q]);
+    }
+    if (rc) break;
+    /* pointwise: relaxation and activation Jacobians (both symmetric in m) */
+    for (size_t q = 0; q < n; ++q) {
+      double av[3] = {0, 0, 0}, gv[3] = {0, 0, 0}, mv[3] = {0, 0, 0}, l[3] = {0, 0, 0};
+      for (int c = 0; c < dim; ++c) {
+        av[c] = a[(size_t)c * n + q];
+        gv[c] = grad[(size_t)c * n + q];
+        mv[c] = m[(size_t)c * n + q];
+        l[c] = lb[(size_t)c * n + q];
+      }
+      double c1, c2r;
+      relax_jac(dim, av, prm->gamma, dtt, &c1, &c2r);
+      double al = av[0] * l[0] + av[1] * l[1] + av[2] * l[2];
+      double la[3];
+      for (int c = 0; c < 3; ++c) la[c] = c1 * l[c] + c2r * al * av[c]; /* lambda_a */
+      double g2 = gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2];
+      double z = c2 * dtt * g2;
+      double ph = phi1(z), dph = dphi1(z);
+      double mg = mv[0] * gv[0] + mv[1] * gv[1] + mv[2] * gv[2];
+      double gl = gv[0] * la[0] + gv[1] * la[1] + gv[2] * la[2];
+      *dc2 += gl * mg * dtt * (ph + z * dph);
+      for (int c = 0; c < dim; ++c) {
+        lam[(size_t)c * n + q] = la[c] + c2 * dtt * ph * gl * gv[c];
+        lg[(size_t)c * n + q] = c2 * dtt * (ph * (mg * la[c] + mv[c] * gl) + 2.0 * c2 * dtt * dph * mg * gl * gv[c]);
+      }
+    }
+    /* lambda_p = G^T lambda_g = -div lambda_g */
+    memset(lp, 0, sizeof(double) * n);
+    for (int c = 0; c < dim && !rc; ++c) {
+      for (size_t q = 0; q < n; ++q) ct[q] = lg[(size_t)c * n + q];
+      rc = or_fftn(g, ct, -1);
+      for (size_t q = 0; q < n && !rc; ++q)
+        ct[q] *= I * or_xi_deriv(coord(g, q, c), g->n[c], g->L[c]);
+      if (!rc) rc = or_fftn(g, ct, +1);
+      for (size_t q = 0; q < n && !rc; ++q) lp[q] -= creal(ct[q]);
+    }
+    if (rc) break;
+    or_project(g, lp);
+    /* adjoint pressure solve A mu = lambda_p (A symmetric) */
+    memset(mu, 0, sizeof(double) * n);
+    or_stats st;
+    int s_rc = or_pcg(g, m, r, lp, mu, kappa, prm->cg_rtol, prm->cg_maxit, &st);
+    if (s_rc && s_rc != OR_ENOCONV) { rc = s_rc; break; }
+    for (size_t q = 0; q < n; ++q) dS[q] += mu[q];
+    rc = or_gradient(g, mu, gmu);
+    if (rc) break;
+    /* d<mu, A(m, r) p>: -(grad mu . K grad p) */
+    for (size_t q = 0; q < n; ++q) {
+      double gm[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
+      for (int c = 0; c < dim; ++c) {
+        gm[c] = gmu[(size_t)c * n + q];
+        gp[c] = grad[(size_t)c * n + q];
+        mv[c] = m[(size_t)c * n + q];
+      }
+      double mgp = mv[0] * gp[0] + mv[1] * gp[1] + mv[2] * gp[2];
+      double mgm = mv[0] * gm[0] + mv[1] * gm[1] + mv[2] * gm[2];
+      dr[q] -= gm[0] * gp[0] + gm[1] * gp[1] + gm[2] * gp[2];
+      for (int c = 0; c < dim; ++c) lam[(size_t)c * n + q] -= gm[c] * mgp + gp[c] * mgm;
+    }
+    (void)t;
+  }
+  if (!rc) {
+    /* S enters through its projection: dL/dS = P dL/d(PS) */
+    or_project(g, dS);
+    memcpy(dm0, lam, sizeof(double) * vn);
+  }
+  free(ms); free(ps); free(lam); free(grad); free(gmu); free(a); free(b); free(lb); free(lg);
+  free(lp); free(mu); free(t); free(ct);
+  return rc;
+}

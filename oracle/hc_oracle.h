@@ -110,6 +110,16 @@ int or_diffusion(const or_grid* g, double* m, double D, double dt);
 int or_step(const or_grid* g, const or_params* prm, const double* r, const double* S,
             double* m, double* p, or_stats* st);
 
+/* Discrete adjoint of `nsteps` loop bodies of Algorithm 1 started from
+ * (m0, p0), treating every pressure solve as exact (run it with a tight
+ * cg_rtol).  lamT = dL/dm(T) for a loss L of the final conductivity.  Outputs
+ * dL/d(c^2), dL/d(D^2), dL/dr (field), dL/dS (field), dL/dm0 (vector field);
+ * gradients are with respect to the grid values (plain sums, no quadrature
+ * weights).  The forward states are kept in memory: small grids only. */
+int or_adjoint(const or_grid* g, const or_params* prm, const double* r, const double* S,
+               const double* m0, const double* p0, int nsteps, const double* lamT, double* dc2,
+               double* dD2, double* dr, double* dS, double* dm0);
+
 /* Discrete energy of Section 2.5 (quadrature weight h_x h_y [h_z], R10), with
  * p the pressure that belongs to m. */
 double or_energy(const or_grid* g, const or_params* prm, const double* r,
