@@ -469,6 +469,46 @@ def run_gb300(args) -> None:
                  "max_rel_residual": max(x.rel_residual for x in sts),
                  "one_graph_launch_per_step": True}
 
+    # ---- adjoint: loss ||m(T) - m_target||^2 on the 1024^2 problem, checkpointed
+    adjv = None
+    if not args.no_adjoint:
+        wa = W.source_sink_2d(1024, gamma=0.75)
+        wt = W.source_sink_2d(1024, gamma=0.75, seed=1)
+        Ka, every = args.adj_steps, max(1, args.adj_steps // 3)
+        sa = P.Solver(wa.n, wa.L, c=wa.c, D=wa.D, gamma=wa.gamma, dt=wa.dt,
+                      precision="fp32_refined", cg_rtol=CG_RTOL_REFINED, cg_maxit=2000,
+                      device=str(dev))
+        sa.set_r(wa.r)
+        sa.set_source(wa.S)
+        if not args.no_tune:
+            sa.set_m(wa.m0)
+            sa.step(1)
+            autotune(sa, reps=5)
+        sa.set_m(wt.m0)
+        sa.set_p(np.zeros(wa.shape))
+        sa.step(Ka)
+        m_target = sa.get_m()
+        sa.set_m(wa.m0)
+        sa.set_p(np.zeros(wa.shape))
+        sa.step(Ka)
+        lamT = 2.0 * (sa.get_m() - m_target)
+        sa.set_m(wa.m0)
+        sa.set_p(np.zeros(wa.shape))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        grads = sa.adjoint(Ka, lamT, every=every)
+        torch.cuda.synchronize()
+        secs = max_over_ranks(time.perf_counter() - t0)
+        sa.close()
+        adjv = {"value": world * wa.npts * Ka / secs / 1e6, "unit": UNIT,
+                "ms_per_step": secs / Ka * 1e3, "steps": Ka, "checkpoint_every": every,
+                "workload": "1024x1024 source/sink, gamma=0.75, FP32 + FP64 refinement; loss "
+                            "||m(T) - m_target||^2, m_target from the seed-1 m0; the time covers "
+                            "the checkpointed forward, the segment recomputation and the reverse "
+                            "sweep (gradients for c^2, D^2, r, S, m0)",
+                "dL_dc2": grads["dc2"], "dL_dD2": grads["dD2"]}
+
     # ---- plain FP64 path at equal accuracy
     fp64 = None
     if not args.no_fp64:
@@ -526,7 +566,8 @@ def run_gb300(args) -> None:
             "cg_iters_per_step": iters_per_step, "refine_sweeps_per_step": sweeps_per_step,
             "cg_iterations_per_s": world * iters_per_step * K / (ms_max / 1e3),
             "rel_residual_last_step": st.rel_residual,
-            "fp64_plain": fp64, "refined_df": dfv, "sweep": sweep, "kernels": kernels,
+            "fp64_plain": fp64, "refined_df": dfv, "sweep": sweep, "adjoint": adjv,
+            "kernels": kernels,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -546,6 +587,8 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-df", action="store_true", help="skip the double-float refinement leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched 48-instance sweep leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--adj-steps", type=int, default=60, help="adjoint leg: steps (C4 uses 500)")
     ap.add_argument("--inner-rtol", type=float, default=0.0,
                     help="inner FP32 CG reduction factor (0: library default)")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")

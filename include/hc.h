@@ -196,6 +196,34 @@ int hc_time_kernel(hc_ctx* ctx, int kernel, int reps, double* ms_per_launch);
  * (graph launches count every kernel node). */
 int hc_launch_count(const hc_ctx* ctx, long long* count);
 
+/* --- Adjoint (gradients of a loss on m(T)) --- */
+
+/* Bytes of device memory hc_adjoint needs for nsteps steps with a checkpoint
+ * every `every` steps: ceil(nsteps/every) checkpoints of (m, p), one segment
+ * of `every` states, and the reverse sweep's buffers.  HC_ENOTSUP in the
+ * double-float precision mode. */
+int hc_adjoint_workspace_size(const hc_ctx* ctx, int nsteps, int every, size_t* bytes);
+
+/* Discrete adjoint of nsteps loop bodies of Algorithm 1 started from the
+ * context's current (m, p): runs the forward steps (storing a checkpoint every
+ * `every` steps), then reverses them segment by segment, recomputing each
+ * segment's states from its checkpoint.  The pressure solves are differentiated
+ * as exact solves (the adjoint solve uses the same operator, which is
+ * symmetric, and the context's tolerance).
+ *   lamT: dL/dm(T), host, 2*nx*ny FP64 (component-major), for any loss L of
+ *         the final conductivity.
+ *   outputs (host FP64, each may be NULL): dL/d(c^2), dL/d(D^2) (scalars),
+ *         dL/dr (nx*ny), dL/dS (nx*ny, orthogonal to the null space), dL/dm0
+ *         (2*nx*ny); derivatives with respect to the grid values.
+ *   workspace: device memory of hc_adjoint_workspace_size bytes (256-byte
+ *         aligned) or NULL (the call allocates and frees its own).
+ * On return the context holds the forward state at step nsteps, as after
+ * hc_step(nsteps).  Returns HC_OK, HC_ENOCONV (some solve hit its cap; the
+ * gradients are still computed), or an error. */
+int hc_adjoint(hc_ctx* ctx, int nsteps, int every, const double* lamT, double* dL_dc2,
+               double* dL_dD2, double* dL_dr, double* dL_dS, double* dL_dm0, void* workspace,
+               size_t workspace_bytes);
+
 /* --- Batched parameter sweeps --- */
 
 typedef struct hc_batch hc_batch; /* opaque; refers to (does not own) its contexts */

@@ -87,6 +87,8 @@ def _load() -> C.CDLL:
         "hc_get_tuning": ([P, C.POINTER(hc_tuning)], C.c_int),
         "hc_set_tuning": ([P, C.POINTER(hc_tuning)], C.c_int),
         "hc_spectrum_noalloc": ([P, P, C.c_int, C.c_int, P], C.c_int),
+        "hc_adjoint_workspace_size": ([P, C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+        "hc_adjoint": ([P, C.c_int, C.c_int, dp, dp, dp, dp, dp, dp, P, C.c_size_t], C.c_int),
         "hc_batch_create": ([C.POINTER(P), C.POINTER(P), C.c_int, P], C.c_int),
         "hc_batch_step": ([P, C.c_int, C.POINTER(hc_step_stats)], C.c_int),
         "hc_batch_destroy": ([P], None),
@@ -121,6 +123,8 @@ hc_time_kernel = lib.hc_time_kernel
 hc_get_tuning = lib.hc_get_tuning
 hc_set_tuning = lib.hc_set_tuning
 hc_spectrum_noalloc = lib.hc_spectrum_noalloc
+hc_adjoint_workspace_size = lib.hc_adjoint_workspace_size
+hc_adjoint = lib.hc_adjoint
 hc_batch_create = lib.hc_batch_create
 hc_batch_step = lib.hc_batch_step
 hc_batch_destroy = lib.hc_batch_destroy
@@ -321,6 +325,28 @@ class Solver:
                       (C.c_int * 2)(*col_pipe))
         _check(hc_set_tuning(self.ctx, C.byref(t)), "hc_set_tuning")
 
+    def adjoint(self, nsteps: int, lamT, every: int = 50, allow=(HC_OK, HC_ENOCONV)) -> dict:
+        """Gradients of a loss on m(T) after `nsteps` steps from the current
+        state, given lamT = dL/dm(T) (see hc_adjoint).  Leaves the solver at
+        the forward state of step `nsteps`."""
+        import torch
+        nbytes = C.c_size_t()
+        _check(hc_adjoint_workspace_size(self.ctx, int(nsteps), int(every), C.byref(nbytes)),
+               "hc_adjoint_workspace_size")
+        ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+        base = (ws.data_ptr() + 255) // 256 * 256
+        lp, keep = _host_f64(lamT, 2 * self.npts)
+        dc2, dD2 = C.c_double(), C.c_double()
+        dr, dS = np.empty(self.shape), np.empty(self.shape)
+        dm0 = np.empty((2,) + self.shape)
+        dp_ = C.POINTER(C.c_double)
+        rc = hc_adjoint(self.ctx, int(nsteps), int(every), lp, C.byref(dc2), C.byref(dD2),
+                        dr.ctypes.data_as(dp_), dS.ctypes.data_as(dp_), dm0.ctypes.data_as(dp_),
+                        C.c_void_p(base), nbytes.value)
+        _check(rc, "hc_adjoint", ok=allow)
+        del ws
+        return {"dc2": dc2.value, "dD2": dD2.value, "dr": dr, "dS": dS, "dm0": dm0, "rc": rc}
+
     def launch_count(self) -> int:
         v = C.c_longlong()
         _check(hc_launch_count(self.ctx, C.byref(v)), "hc_launch_count")
@@ -363,3 +389,46 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _autograd_function():
+    import torch
+
+    class HuCaiSteps(torch.autograd.Function):
+        """m(T) = nsteps loop bodies of Algorithm 1 from (m0, p = 0) with
+        parameters c^2, D^2 and fields r, S, on a Solver; backward calls the
+        hand-written adjoint (hc_adjoint).  Inputs and output are CPU float64
+        tensors; c2 and D2 are 0-dim tensors."""
+
+        @staticmethod
+        def forward(ctx, solver, nsteps, every, c2, D2, r, S, m0):
+            ctx.solver, ctx.nsteps, ctx.every = solver, int(nsteps), int(every)
+            ctx.inputs = (float(c2), float(D2), r.detach().clone(), S.detach().clone(),
+                          m0.detach().clone())
+            HuCaiSteps._load(solver, *ctx.inputs)
+            solver.step(nsteps)
+            return torch.from_numpy(solver.get_m())
+
+        @staticmethod
+        def _load(solver, c2, D2, r, S, m0):
+            solver.set_params(c=float(np.sqrt(c2)), D=float(np.sqrt(D2)))
+            solver.set_r(r.contiguous())
+            solver.set_source(S.contiguous())
+            solver.set_m(m0.contiguous())
+            solver.set_p(np.zeros(solver.shape))
+
+        @staticmethod
+        def backward(ctx, grad_m):
+            solver = ctx.solver
+            HuCaiSteps._load(solver, *ctx.inputs)
+            g = solver.adjoint(ctx.nsteps, grad_m.detach().double().contiguous(), ctx.every)
+            t = lambda a: torch.as_tensor(a, dtype=torch.float64)
+            return (None, None, None, t(g["dc2"]), t(g["dD2"]), t(g["dr"]), t(g["dS"]),
+                    t(g["dm0"]))
+
+    return HuCaiSteps
+
+
+def hucai_steps(solver, nsteps, every, c2, D2, r, S, m0):
+    """Differentiable m(T) (torch.autograd); see HuCaiSteps."""
+    return _autograd_function().apply(solver, nsteps, every, c2, D2, r, S, m0)

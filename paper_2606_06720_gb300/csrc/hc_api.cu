@@ -89,6 +89,8 @@ struct hc_ctx {
   float *kxd_f, *kyd_f, *hx_f, *hy_f;
   double *kxd_d, *kyd_d, *hx_d, *hy_d;
   df64 *kxd_q, *kyd_q;
+  float *x2x_f, *x2y_f;
+  double *x2x_d, *x2y_d;
   hc::Geo<float> gf;
   hc::Geo<double> gd;
   hc::Geo<df64> gq;  // double-float kernels (HC_FP32_REFINED_DF)
@@ -190,6 +192,10 @@ void layout(hc_ctx* c, Layout& L) {
   c->twy_q = L.take<cx<df64>>(sizeof(cx<df64>) * c->ny);
   c->kxd_q = L.take<df64>(sizeof(df64) * c->H);
   c->kyd_q = L.take<df64>(sizeof(df64) * c->ny);
+  c->x2x_f = L.take<float>(sizeof(float) * (c->H + 1));
+  c->x2y_f = L.take<float>(sizeof(float) * c->ny);
+  c->x2x_d = L.take<double>(sizeof(double) * (c->H + 1));
+  c->x2y_d = L.take<double>(sizeof(double) * c->ny);
   c->hx_d = L.take<double>(sizeof(double) * (c->H + 1));
   c->hy_d = L.take<double>(sizeof(double) * c->ny);
 }
@@ -293,6 +299,14 @@ int upload_tables(hc_ctx* c) {
   CU(cudaMemcpy(c->kyd_d, ky.data(), sizeof(double) * c->ny, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c->kxd_f, kxf.data(), sizeof(float) * c->H, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c->kyd_f, kyf.data(), sizeof(float) * c->ny, cudaMemcpyHostToDevice));
+  std::vector<double> x2x(c->H + 1), x2y(c->ny);
+  for (int k = 0; k <= c->H; ++k) x2x[k] = xi(k, c->nx, c->grid.L[0]) * xi(k, c->nx, c->grid.L[0]);
+  for (int k = 0; k < c->ny; ++k) x2y[k] = xi(k, c->ny, c->grid.L[1]) * xi(k, c->ny, c->grid.L[1]);
+  std::vector<float> x2xf(x2x.begin(), x2x.end()), x2yf(x2y.begin(), x2y.end());
+  CU(cudaMemcpy(c->x2x_d, x2x.data(), sizeof(double) * (c->H + 1), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->x2y_d, x2y.data(), sizeof(double) * c->ny, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->x2x_f, x2xf.data(), sizeof(float) * (c->H + 1), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->x2y_f, x2yf.data(), sizeof(float) * c->ny, cudaMemcpyHostToDevice));
   std::vector<df64> kxq(kx.begin(), kx.end()), kyq(ky.begin(), ky.end());
   CU(cudaMemcpy(c->kxd_q, kxq.data(), sizeof(df64) * c->H, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c->kyd_q, kyq.data(), sizeof(df64) * c->ny, cudaMemcpyHostToDevice));
@@ -651,6 +665,12 @@ int set_graph_mode(hc_ctx* c, int on) {
   return HC_OK;
 }
 
+int restore_b2(hc_ctx* c, double b2) {
+  CU(cudaMemcpyAsync(&c->st->outer_b2, &b2, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
 int fill_stats(hc_ctx* c, hc_step_stats* out) {
   const hc::SolveState& h = *c->st_host;
   if (out) {
@@ -750,6 +770,10 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   layout(c, L);
   fill_geo<float>(c, c->gf, c->twx_f, c->twy_f, c->kxd_f, c->kyd_f, c->hx_f, c->hy_f);
   fill_geo<double>(c, c->gd, c->twx_d, c->twy_d, c->kxd_d, c->kyd_d, c->hx_d, c->hy_d);
+  c->gf.x2x = c->x2x_f;
+  c->gf.x2y = c->x2y_f;
+  c->gd.x2x = c->x2x_d;
+  c->gd.x2y = c->x2y_d;
   fill_geo<df64>(c, c->gq, c->twx_q, c->twy_q, c->kxd_q, c->kyd_q, nullptr, nullptr);
   c->gq.tc = c->gd.tc;
   c->gq.ltc = c->gd.ltc;
@@ -1064,6 +1088,287 @@ int hc_spectrum(hc_ctx* c, const double* f, double* out, size_t count) {
 }
 
 const char* hc_last_cuda_error(void) { return g_last_error; }
+
+}  // extern "C"
+
+namespace {
+
+// Layout of the adjoint's own memory (checkpoints, one segment of states, the
+// reverse sweep's buffers) for precision T.
+template <typename T>
+struct AdjLayout {
+  hc::AdjState* as;
+  cx<double>* b_save;   // S spectrum (the solve's right-hand side is borrowed)
+  T* mT;                // final m
+  cx<double>* pT;       // final p spectrum
+  T* cpm;               // checkpoints of m, ncp x 2n
+  cx<double>* cpp;      // checkpoints of p, ncp x n/2
+  T* segm;              // m^k of one segment, every x 2n
+  cx<double>* segp;     // p^{k+1} of one segment, every x n/2
+  cx<T>*A, *B, *C, *D;  // spectra: A, B, C two each, D one
+  T *lam, *lm;          // lambda and lambda_m (2n each)
+  double* dr;           // dL/dr accumulator (n)
+  cx<double>* dS;       // dL/dS accumulator, packed spectrum
+  double* cpk;          // sum |m|^2 (the kappa input) of each checkpoint
+  double* segk;         // ... of each state of the segment
+  double* kT;           // ... of the final state
+  size_t bytes;
+};
+
+template <typename T>
+void adj_layout(const hc_ctx* c, int nsteps, int every, char* base, AdjLayout<T>& a) {
+  Layout L;
+  L.base = base;
+  const size_t n = c->n, ns = (size_t)c->ny * c->H;
+  const size_t ncp = nsteps > 0 ? (size_t)((nsteps + every - 1) / every) : 1;
+  const size_t seg = (size_t)std::min(every, std::max(nsteps, 1));
+  a.as = L.take<hc::AdjState>(sizeof(hc::AdjState));
+  a.b_save = L.take<cx<double>>(sizeof(cx<double>) * ns);
+  a.mT = L.take<T>(sizeof(T) * 2 * n);
+  a.pT = L.take<cx<double>>(sizeof(cx<double>) * ns);
+  a.cpm = L.take<T>(sizeof(T) * 2 * n * ncp);
+  a.cpp = L.take<cx<double>>(sizeof(cx<double>) * ns * ncp);
+  a.segm = L.take<T>(sizeof(T) * 2 * n * seg);
+  a.segp = L.take<cx<double>>(sizeof(cx<double>) * ns * seg);
+  a.A = L.take<cx<T>>(sizeof(cx<T>) * 2 * ns);
+  a.B = L.take<cx<T>>(sizeof(cx<T>) * 2 * ns);
+  a.C = L.take<cx<T>>(sizeof(cx<T>) * 2 * ns);
+  a.D = L.take<cx<T>>(sizeof(cx<T>) * ns);
+  a.lam = L.take<T>(sizeof(T) * 2 * n);
+  a.lm = L.take<T>(sizeof(T) * 2 * n);
+  a.dr = L.take<double>(sizeof(double) * n);
+  a.dS = L.take<cx<double>>(sizeof(cx<double>) * ns);
+  a.cpk = L.take<double>(sizeof(double) * ncp);
+  a.segk = L.take<double>(sizeof(double) * seg);
+  a.kT = L.take<double>(sizeof(double));
+  a.bytes = (L.off + kAlign - 1) / kAlign * kAlign;
+}
+
+// The pressure solve of one step without the split step (host-driven loops).
+int solve_only(hc_ctx* c) {
+  hc::step_begin(c->st, (int)c->n, c->stream);
+  c->launches += 1;
+  if (!c->refined) {
+    plain_init(c);
+    return run_cg_host(c, false);
+  }
+  for (int sweep = 0;; ++sweep) {
+    refined_resid(c);
+    int rc = read_state(c);
+    if (rc) return rc;
+    if (c->st_host->outer_done) break;
+    rc = run_cg_host(c, true);
+    if (rc) return rc;
+    if (sweep > 1000) return HC_ETIMEOUT;
+  }
+  return HC_OK;
+}
+
+template <typename T>
+int copy_m(hc_ctx* c, T* dst, const T* src) {
+  CU(cudaMemcpyAsync(dst, src, sizeof(T) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  return HC_OK;
+}
+
+// A state is (m, p, sum |m|^2): restoring the exact sum keeps kappa, hence
+// every CG iterate of a recomputed step, identical to the original forward.
+template <typename T>
+int save_state(hc_ctx* c, T* m, cx<double>* p, double* msum) {
+  const size_t ns = (size_t)c->ny * c->H;
+  CU(cudaMemcpyAsync(msum, &c->st->msum, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(m, c->m[0], sizeof(T) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(m + c->n, c->m[1], sizeof(T) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  if (p) CU(cudaMemcpyAsync(p, c->p64, sizeof(cx<double>) * ns, cudaMemcpyDeviceToDevice, c->stream));
+  return HC_OK;
+}
+
+template <typename T>
+int load_state(hc_ctx* c, const T* m, const cx<double>* p, const double* msum) {
+  const size_t ns = (size_t)c->ny * c->H;
+  CU(cudaMemcpyAsync(c->m[0], m, sizeof(T) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->m[1], m + c->n, sizeof(T) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  if (p) CU(cudaMemcpyAsync(c->p64, p, sizeof(cx<double>) * ns, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(&c->st->msum, msum, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return HC_OK;
+}
+
+// Reverse of step k: lambda (a.lam) <- lambda^k from lambda^{k+1}; c holds m^k
+// and p64 holds p^{k+1}.
+template <typename T>
+int adj_reverse_step(hc_ctx* c, hc::Geo<T>& g, AdjLayout<T>& a, const cx<double>* pk1) {
+  const size_t ns = (size_t)c->ny * c->H;
+  cudaStream_t s = c->stream;
+  const T* mx = (const T*)c->m[0];
+  const T* my = (const T*)c->m[1];
+  cx<T>*A0 = a.A, *A1 = a.A + ns, *B0 = a.B, *B1 = a.B + ns, *C0 = a.C, *C1 = a.C + ns;
+  const hc::SplitCoef cf = split_coef(c->prm);
+  // grad p^{k+1} (rows) and b = R(A(m^k, g)) (rows)
+  hc::col_grad<T, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, A0, A1, c->st, 0, s);
+  hc::row_split<T>(g, A0, A1, mx, my, B0, B1, cf, c->st, s);
+  // lambda_b = H lambda (H is symmetric), as row spectra
+  hc::row_r2c<T>(g, a.lam, a.lam + c->n, C0, C1, s);
+  hc::col_heat<T>(g, C0, C1, s);
+  // dL/dD^2 = <lambda_b, (-|xi|^2 dt) b>
+  hc::col_lap_dot<T>(g, C0, B0, c->prm.dt, a.as, s);
+  hc::col_lap_dot<T>(g, C1, B1, c->prm.dt, a.as, s);
+  // pointwise Jacobians: lambda_m, lambda_g (rows over A), dL/dc^2
+  hc::row_adj_point<T>(g, A0, A1, C0, C1, mx, my, a.lm, a.lm + c->n, cf, a.as, s);
+  // lambda_p = -div lambda_g, the adjoint solve A mu = lambda_p
+  hc::col_div<T>(g, hc::CD_PLAIN, A0, A1, nullptr, nullptr, a.D, nullptr, nullptr, nullptr, s);
+  hc::spec_norm2<T>(g, a.D, c->st, s);
+  if constexpr (std::is_same<T, double>::value)
+    CU(cudaMemcpyAsync(c->b64, a.D, sizeof(cx<double>) * ns, cudaMemcpyDeviceToDevice, s));
+  else
+    hc::convert<double, float>(reinterpret_cast<const float*>(a.D), reinterpret_cast<double*>(c->b64),
+                               2 * ns, s);
+  CU(cudaMemsetAsync(c->p64, 0, sizeof(cx<double>) * ns, s));
+  c->launches += 12;
+  CU(cudaGetLastError());
+  int rc = solve_only(c);
+  if (rc) return rc;
+  hc::spec_accum<double>(c->gd, reinterpret_cast<double*>(a.dS), c->p64, s);
+  // grad mu, grad p^{k+1}, and the r, m terms of the solve
+  hc::col_grad<T, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, A0, A1, c->st, 0, s);
+  CU(cudaMemcpyAsync(c->p64, pk1, sizeof(cx<double>) * ns, cudaMemcpyDeviceToDevice, s));
+  hc::col_grad<T, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, B0, B1, c->st, 0, s);
+  hc::row_adj_press<T>(g, A0, A1, B0, B1, mx, my, a.lm, a.lm + c->n, a.lam, a.lam + c->n, a.dr, s);
+  c->launches += 4;
+  CU(cudaGetLastError());
+  return HC_OK;
+}
+
+template <typename T>
+int adjoint_t(hc_ctx* c, hc::Geo<T>& g, int nsteps, int every, const double* lamT, double* dc2,
+              double* dD2, double* dr, double* dS, double* dm0, char* ws) {
+  AdjLayout<T> a;
+  adj_layout<T>(c, nsteps, every, ws, a);
+  const size_t n = c->n, ns = (size_t)c->ny * c->H;
+  cudaStream_t s = c->stream;
+  CU(cudaMemsetAsync(a.as, 0, sizeof(hc::AdjState), s));
+  CU(cudaMemsetAsync(a.dr, 0, sizeof(double) * n, s));
+  CU(cudaMemsetAsync(a.dS, 0, sizeof(cx<double>) * ns, s));
+  CU(cudaMemcpyAsync(a.b_save, c->b64, sizeof(cx<double>) * ns, cudaMemcpyDeviceToDevice, s));
+  int rc = read_state(c);
+  if (rc) return rc;
+  const double b2_save = c->st_host->outer_b2;
+  int status = HC_OK;
+  // forward with checkpoints
+  for (int k = 0; k < nsteps; ++k) {
+    if (k % every == 0) {
+      rc = save_state<T>(c, a.cpm + 2 * n * (k / every), a.cpp + ns * (k / every),
+                         a.cpk + k / every);
+      if (rc) return rc;
+    }
+    rc = hc_step(c, 1, nullptr);
+    if (rc == HC_ENOCONV) status = status ? status : rc;
+    else if (rc) return rc;
+  }
+  rc = save_state<T>(c, a.mT, a.pT, a.kT);
+  if (rc) return rc;
+  // lambda(T)
+  CU(cudaMemcpyAsync(c->stage, lamT, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, s));
+  if constexpr (std::is_same<T, double>::value)
+    CU(cudaMemcpyAsync(a.lam, c->stage, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
+  else
+    hc::convert<float, double>(c->stage, a.lam, 2 * n, s);
+  // reverse, one segment at a time
+  const int nseg = nsteps > 0 ? (nsteps + every - 1) / every : 0;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int k0 = sg * every, k1 = std::min(k0 + every, nsteps);
+    rc = load_state<T>(c, a.cpm + 2 * n * sg, a.cpp + ns * sg, a.cpk + sg);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(c->b64, a.b_save, sizeof(cx<double>) * ns, cudaMemcpyDeviceToDevice, s));
+    rc = restore_b2(c, b2_save);
+    if (rc) return rc;
+    for (int k = k0; k < k1; ++k) {
+      rc = save_state<T>(c, a.segm + 2 * n * (k - k0), nullptr, a.segk + (k - k0));
+      if (rc) return rc;
+      rc = hc_step(c, 1, nullptr);
+      if (rc && rc != HC_ENOCONV) return rc;
+      CU(cudaMemcpyAsync(a.segp + ns * (k - k0), c->p64, sizeof(cx<double>) * ns,
+                         cudaMemcpyDeviceToDevice, s));
+    }
+    for (int k = k1 - 1; k >= k0; --k) {
+      rc = load_state<T>(c, a.segm + 2 * n * (k - k0), a.segp + ns * (k - k0), a.segk + (k - k0));
+      if (rc) return rc;
+      rc = adj_reverse_step<T>(c, g, a, a.segp + ns * (k - k0));
+      if (rc) return rc;
+    }
+  }
+  // restore the final forward state and the source
+  CU(cudaMemcpyAsync(c->b64, a.b_save, sizeof(cx<double>) * ns, cudaMemcpyDeviceToDevice, s));
+  rc = restore_b2(c, b2_save);
+  if (rc) return rc;
+  rc = load_state<T>(c, a.mT, a.pT, a.kT);
+  if (rc) return rc;
+  // outputs
+  hc::AdjState hs;
+  CU(cudaMemcpyAsync(&hs, a.as, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  if (dm0) {
+    if constexpr (std::is_same<T, double>::value)
+      CU(cudaMemcpyAsync(c->stage, a.lam, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
+    else
+      hc::convert<double, float>(a.lam, c->stage, 2 * n, s);
+    CU(cudaMemcpyAsync(dm0, c->stage, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, s));
+  }
+  if (dr) CU(cudaMemcpyAsync(dr, a.dr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  if (dS) {
+    cx<double>* rows = c->G64;
+    hc::col_inv<double>(c->gd, a.dS, rows, 1.0 / (double)n, s);
+    hc::row_c2r<double>(c->gd, rows, nullptr, c->stage, nullptr, nullptr, 0, s);
+    c->launches += 2;
+    CU(cudaMemcpyAsync(dS, c->stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  }
+  CU(cudaStreamSynchronize(s));
+  if (dc2) *dc2 = hs.dc2;
+  if (dD2) *dD2 = hs.dD2;
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hc_adjoint_workspace_size(const hc_ctx* c, int nsteps, int every, size_t* bytes) {
+  if (!c || !bytes || nsteps < 0 || every < 1) return HC_EINVAL;
+  if (c->df) return HC_ENOTSUP;
+  if (c->refined) {
+    AdjLayout<float> a;
+    adj_layout<float>(c, nsteps, every, nullptr, a);
+    *bytes = a.bytes;
+  } else {
+    AdjLayout<double> a;
+    adj_layout<double>(c, nsteps, every, nullptr, a);
+    *bytes = a.bytes;
+  }
+  return HC_OK;
+}
+
+int hc_adjoint(hc_ctx* c, int nsteps, int every, const double* lamT, double* dc2, double* dD2,
+               double* dr, double* dS, double* dm0, void* workspace, size_t workspace_bytes) {
+  if (!c || !lamT || nsteps < 0 || every < 1) return HC_EINVAL;
+  if (c->df) return HC_ENOTSUP;
+  if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return HC_EINVAL;
+  size_t need = 0;
+  int rc = hc_adjoint_workspace_size(c, nsteps, every, &need);
+  if (rc) return rc;
+  if (workspace && workspace_bytes < need) return HC_ENOMEM;
+  void* ws = workspace;
+  bool own = false;
+  if (!ws) {
+    if (cudaMalloc(&ws, need) != cudaSuccess) return HC_ENOMEM;
+    own = true;
+  }
+  if (c->refined)
+    rc = adjoint_t<float>(c, c->gf, nsteps, every, lamT, dc2, dD2, dr, dS, dm0, (char*)ws);
+  else
+    rc = adjoint_t<double>(c, c->gd, nsteps, every, lamT, dc2, dD2, dr, dS, dm0, (char*)ws);
+  if (own) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(ws);
+  }
+  return rc;
+}
 
 }  // extern "C"
 

@@ -146,7 +146,16 @@ struct Geo {
   int npartials;             // capacity in CTAs
   int pipe;                  // 1: column passes run persistent with cp.async double buffering
   int pgrid;                 // CTAs of a persistent column pass (<= SMs, <= tiles)
+  const T* x2x;              // xi_x^2 (positive Nyquist), kx = 0..H (H + 1 entries)
+  const T* x2y;              // xi_y^2, ky < ny
 };
+
+// Scalar results of the adjoint sweep (device).
+struct AdjState {
+  double dc2, dD2;           // dL/d(c^2), dL/d(D^2) accumulated over steps
+  unsigned int ticket[4];
+};
+enum { TA_POINT = 0, TA_LAP = 1 };
 
 // Split-step coefficients (Section 2.3), precomputed on the host in FP64.
 struct SplitCoef {
@@ -218,6 +227,30 @@ template <typename To, typename Ti>
 void convert(const Ti* in, To* out, size_t n, cudaStream_t s);
 template <typename T>
 void msum(const Geo<T>& g, const T* mx, const T* my, SolveState* st, cudaStream_t s);
+
+// ---- adjoint (discrete reverse of one step; see the kernels for the formulas)
+// Row pass: C2R(grad p), C2R(lambda_b) -> relaxation/activation Jacobians ->
+// lambda_m (physical) and lambda_g (row spectra, over G), dL/dc^2.
+template <typename T>
+void row_adj_point(const Geo<T>& g, cx<T>* G0, cx<T>* G1, const cx<T>* L0, const cx<T>* L1,
+                   const T* mx, const T* my, T* lmx, T* lmy, SplitCoef cf, AdjState* as,
+                   cudaStream_t s);
+// Row pass: C2R(grad mu), C2R(grad p) -> lambda = lambda_m - ((m.gp) gmu + (m.gmu) gp),
+// dr -= gmu . gp.
+template <typename T>
+void row_adj_press(const Geo<T>& g, const cx<T>* GM0, const cx<T>* GM1, const cx<T>* GP0,
+                   const cx<T>* GP1, const T* mx, const T* my, const T* lmx, const T* lmy, T* lx,
+                   T* ly, double* dr, cudaStream_t s);
+// Column pass, one component: dD2 += <lambda_b, (-|xi|^2 dt) b> from A = rows of
+// lambda_b (scaled for an unnormalised C2R) and B = rows of b.
+template <typename T>
+void col_lap_dot(const Geo<T>& g, const cx<T>* A, const cx<T>* B, double dt, AdjState* as,
+                 cudaStream_t s);
+// Spectral helpers: acc += v (FP64 accumulator); st->outer_b2 = ||v||^2 (Parseval weights).
+template <typename T>
+void spec_accum(const Geo<T>& g, double* acc, const cx<T>* v, cudaStream_t s);
+template <typename T>
+void spec_norm2(const Geo<T>& g, const cx<T>* v, SolveState* st, cudaStream_t s);
 
 // Opt every kernel of one precision in to the full shared memory per block.
 void set_smem_limits_f32();

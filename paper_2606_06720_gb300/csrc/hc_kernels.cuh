@@ -1268,6 +1268,241 @@ __global__ void __launch_bounds__(256) k_msum(Geo<T> g, const T* __restrict__ mx
   }
 }
 
+// ------------------------------------------------------------------ adjoint
+// Reverse of one step (m^k, p^{k+1}) -> lambda^k given lambda^{k+1}.  With
+// g = grad p^{k+1}, z = c^2 dt |g|^2, phi1(z) = expm1(z)/z:
+//   a = m + c^2 dt phi1 (m.g) g,   b = a s(|a|)   (activation, relaxation)
+//   lambda_a = J_rel(a) lambda_b,  J_rel = s I + (f' - s) a a^T / |a|^2 (symmetric)
+//   lambda_m = lambda_a + c^2 dt phi1 (g.lambda_a) g
+//   lambda_g = c^2 dt [phi1 ((m.g) lambda_a + m (g.lambda_a)) + 2 c^2 dt phi1'(z) (m.g)(g.lambda_a) g]
+//   dL/dc^2 += (g.lambda_a)(m.g) dt (phi1 + z phi1')
+// and, after the adjoint pressure solve A mu = -div lambda_g:
+//   lambda^k = lambda_m - ((m.grad p) grad mu + (m.grad mu) grad p),  dL/dr -= grad mu . grad p.
+
+template <typename T>
+__device__ __forceinline__ T dphi1(T z) {  // d/dz (expm1(z)/z), z >= 0
+  if (z < (T)0.5) {  // sum_k z^k / ((k+2) k!): the closed form cancels here
+    T term = (T)1, s = (T)0.5;
+#pragma unroll
+    for (int k = 1; k < 14; ++k) {
+      term = term * z / (T)k;
+      s = s + term / (T)(k + 2);
+    }
+    return s;
+  }
+  return ((z - (T)1) * hc_expm1(z) + z) / (z * z);
+}
+
+template <typename T>
+__device__ __forceinline__ void relax_jac(T ax, T ay, const SplitCoef& cf, T& c1, T& c2) {
+  c2 = (T)0;
+  if (cf.gamma_is_one) {
+    c1 = (T)cf.exp_mdt;
+    return;
+  }
+  const T n2 = ax * ax + ay * ay;
+  if (n2 == (T)0) {
+    c1 = cf.gamma > 1.0 ? (T)1 : (T)0;
+    return;
+  }
+  const T rho = hc_sqrt(n2);
+  const T e = (T)cf.pow_a;  // 2 (1 - gamma)
+  const T beta = hc_pow(rho, e) - (T)cf.two1mg_dt;
+  if (!(beta > (T)0)) {
+    c1 = (T)0;
+    return;
+  }
+  const T f = hc_pow(beta, (T)cf.pow_b);                         // new modulus
+  const T fp = hc_pow(beta, (T)cf.pow_b - (T)1) * hc_pow(rho, e - (T)1);  // d f / d rho
+  const T sv = f / rho;
+  c1 = sv;
+  c2 = (fp - sv) / n2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_row_adj_point(Geo<T> g, cx<T>* G0, cx<T>* G1,
+                                                       const cx<T>* L0, const cx<T>* L1,
+                                                       const T* __restrict__ mx,
+                                                       const T* __restrict__ my,
+                                                       T* __restrict__ lmx, T* __restrict__ lmy,
+                                                       SplitCoef cf, AdjState* as) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
+  const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
+  const int y = (blockIdx.x << g.lrpc) + rb;
+  cx<T>* slab = sm + rb * 2 * N;
+  cx<T>* const sl[2] = {slab, slab + N};
+  cx<T> v[2][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    v[0][s] = load_pair_c2r(G0 + (size_t)y * H, G1 + (size_t)y * H, j + s * N8, H);
+    v[1][s] = load_pair_c2r(L0 + (size_t)y * H, L1 + (size_t)y * H, j + s * N8, H);
+  }
+  fft_canon<+1, 2, true>(v, sl, 1, j, g.lnx, g.twx);
+  const size_t ro = (size_t)y * N;
+  const T c2dt = (T)cf.c2dt, dt = (T)cf.dt;
+  DotAcc<T> dc;
+  cx<T> w[1][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = j + s * N8;
+    const T gx = v[0][s].x, gy = v[0][s].y, lbx = v[1][s].x, lby = v[1][s].y;
+    const T mxv = mx[ro + x], myv = my[ro + x];
+    const T z = c2dt * (gx * gx + gy * gy);
+    const T ph = z > (T)0 ? hc_expm1(z) / z : (T)1;
+    const T dph = dphi1(z);
+    const T mg = mxv * gx + myv * gy;
+    const T ax = mxv + c2dt * ph * mg * gx, ay = myv + c2dt * ph * mg * gy;
+    T c1, c2r;
+    relax_jac(ax, ay, cf, c1, c2r);
+    const T al = ax * lbx + ay * lby;
+    const T lax = c1 * lbx + c2r * al * ax, lay = c1 * lby + c2r * al * ay;
+    const T gl = gx * lax + gy * lay;
+    lmx[ro + x] = lax + c2dt * ph * gl * gx;
+    lmy[ro + x] = lay + c2dt * ph * gl * gy;
+    const T t2 = (T)2 * c2dt * dph * mg * gl;
+    w[0][s] = cmk<T>(c2dt * (ph * (mg * lax + mxv * gl) + t2 * gx),
+                     c2dt * (ph * (mg * lay + myv * gl) + t2 * gy));
+    dc.add_prod(gl * mg, dt * (ph + z * dph));
+  }
+  cx<T>* const sl1[1] = {slab};
+  fft_canon<-1, 1, true>(w, sl1, 1, j, g.lnx, g.twx);
+  store_pair_r2c(w, slab, j, N, H, G0 + (size_t)y * H, G1 + (size_t)y * H);
+  double a1[1] = {dc.value()}, t1[1];
+  if (last_cta_sum<1>(a1, g.partials, &as->ticket[TA_POINT], t1) && threadIdx.x == 0)
+    as->dc2 += t1[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_row_adj_press(Geo<T> g, const cx<T>* __restrict__ GM0,
+                                                       const cx<T>* __restrict__ GM1,
+                                                       const cx<T>* __restrict__ GP0,
+                                                       const cx<T>* __restrict__ GP1,
+                                                       const T* __restrict__ mx,
+                                                       const T* __restrict__ my, const T* lmx,
+                                                       const T* lmy, T* lx, T* ly, double* dr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
+  const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
+  const int y = (blockIdx.x << g.lrpc) + rb;
+  cx<T>* slab = sm + rb * 2 * N;
+  cx<T>* const sl[2] = {slab, slab + N};
+  cx<T> v[2][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    v[0][s] = load_pair_c2r(GM0 + (size_t)y * H, GM1 + (size_t)y * H, j + s * N8, H);
+    v[1][s] = load_pair_c2r(GP0 + (size_t)y * H, GP1 + (size_t)y * H, j + s * N8, H);
+  }
+  fft_canon<+1, 2, true>(v, sl, 1, j, g.lnx, g.twx);
+  const size_t ro = (size_t)y * N;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const size_t i = ro + j + s * N8;
+    const T gmx = v[0][s].x, gmy = v[0][s].y, gpx = v[1][s].x, gpy = v[1][s].y;
+    const T mxv = mx[i], myv = my[i];
+    const T mgp = mxv * gpx + myv * gpy, mgm = mxv * gmx + myv * gmy;
+    const T nx_ = lmx[i] - (gmx * mgp + gpx * mgm);
+    const T ny_ = lmy[i] - (gmy * mgp + gpy * mgm);
+    lx[i] = nx_;
+    ly[i] = ny_;
+    dr[i] -= (double)(gmx * gpx + gmy * gpy);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_col_lap_dot(Geo<T> g, const cx<T>* __restrict__ A,
+                                                     const cx<T>* __restrict__ B, double dt,
+                                                     AdjState* as) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const ColIdx c = col_idx(g);
+  const int H = g.H, ny = g.ny;
+  const int se = slab_elems(g);
+  cx<T>* const sl[2] = {sm + c.b, sm + se + c.b};
+  cx<T> v[2][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const size_t idx = (size_t)(c.j + s * c.NY8) * H + c.kx;
+    v[0][s] = A[idx];
+    v[1][s] = B[idx];
+  }
+  fft_canon<-1, 2>(v, sl, g.tc, c.j, g.lny, g.twy);
+  const T tdt = (T)dt;
+  DotAcc<T> acc;
+  if (blockIdx.x == 0) {
+    // packed column: separate the kx = 0 (A) and kx = nx/2 (B) parts of both
+    // vectors with the ky <-> -ky symmetry before weighting them
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int e = padk(c.j + s * c.NY8) * g.tc;
+      sl[0][e] = v[0][s];
+      sl[1][e] = v[1][s];
+    }
+    __syncthreads();
+    if (c.b == 0) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int ky = c.j + s * c.NY8;
+        const int kn = (ny - ky) & (ny - 1);
+        const cx<T> pa = v[0][s], pb = v[1][s];
+        const cx<T> na = sl[0][padk(kn) * g.tc], nb = sl[1][padk(kn) * g.tc];
+        // A-part = (P + conj(P-))/2, B-part = (P - conj(P-))/(2i)
+        const cx<T> a0 = cmk<T>((T)0.5 * (pa.x + na.x), (T)0.5 * (pa.y - na.y));
+        const cx<T> a1 = cmk<T>((T)0.5 * (pa.y + na.y), (T)-0.5 * (pa.x - na.x));
+        const cx<T> b0 = cmk<T>((T)0.5 * (pb.x + nb.x), (T)0.5 * (pb.y - nb.y));
+        const cx<T> b1 = cmk<T>((T)0.5 * (pb.y + nb.y), (T)-0.5 * (pb.x - nb.x));
+        const T f0 = -(g.x2x[0] + g.x2y[ky]) * tdt, fN = -(g.x2x[H] + g.x2y[ky]) * tdt;
+        acc.add_prod(f0 * a0.x, b0.x);
+        acc.add_prod(f0 * a0.y, b0.y);
+        acc.add_prod(fN * a1.x, b1.x);
+        acc.add_prod(fN * a1.y, b1.y);
+      }
+    }
+  }
+  if (c.kx != 0) {
+    const T xx = g.x2x[c.kx];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const T f = (T)-2 * (xx + g.x2y[c.j + s * c.NY8]) * tdt;  // weight 2 for kx > 0
+      acc.add_prod(f * v[0][s].x, v[1][s].x);
+      acc.add_prod(f * v[0][s].y, v[1][s].y);
+    }
+  }
+  // A carries the row pass's inverse scaling (A = F_x(lambda_b) / nx, ready for
+  // an unnormalised C2R) while B = F_x(b); Parseval's 1/(nx ny) then leaves 1/ny
+  double a1[1] = {acc.value()}, t1[1];
+  if (last_cta_sum<1>(a1, g.partials, &as->ticket[TA_LAP], t1) && threadIdx.x == 0)
+    as->dD2 += t1[0] / (double)g.ny;
+}
+
+template <typename T>
+__global__ void k_spec_accum(double* __restrict__ acc, const cx<T>* __restrict__ v, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    acc[2 * i] += (double)v[i].x;
+    acc[2 * i + 1] += (double)v[i].y;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_spec_norm2(Geo<T> g, const cx<T>* __restrict__ v,
+                                                    SolveState* st) {
+  const size_t total = (size_t)g.ny * g.H;
+  DotAcc<T> a;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const T w = (i & (size_t)(g.H - 1)) == 0 ? (T)1 : (T)2;
+    a.add_prod(w * v[i].x, v[i].x);
+    a.add_prod(w * v[i].y, v[i].y);
+  }
+  double a1[1] = {a.value()}, t1[1];
+  if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_PROJ], t1) && threadIdx.x == 0)
+    st->outer_b2 = t1[0];
+}
+
 // ------------------------------------------------------------------ launchers
 template <typename T>
 static inline int row_threads(const Geo<T>& g) { return g.rpc << (g.lnx - 3); }
@@ -1414,6 +1649,34 @@ template <typename T>
 void msum(const Geo<T>& g, const T* mx, const T* my, SolveState* st, cudaStream_t s) {
   k_msum<T><<<upd_blocks((size_t)g.nx * g.ny), 256, 0, s>>>(g, mx, my, st);
 }
+template <typename T>
+void row_adj_point(const Geo<T>& g, cx<T>* G0, cx<T>* G1, const cx<T>* L0, const cx<T>* L1,
+                   const T* mx, const T* my, T* lmx, T* lmy, SplitCoef cf, AdjState* as,
+                   cudaStream_t s) {
+  k_row_adj_point<T><<<g.ny >> g.lrpc, row_threads(g), 2 * row_smem(g), s>>>(g, G0, G1, L0, L1, mx,
+                                                                             my, lmx, lmy, cf, as);
+}
+template <typename T>
+void row_adj_press(const Geo<T>& g, const cx<T>* GM0, const cx<T>* GM1, const cx<T>* GP0,
+                   const cx<T>* GP1, const T* mx, const T* my, const T* lmx, const T* lmy, T* lx,
+                   T* ly, double* dr, cudaStream_t s) {
+  k_row_adj_press<T><<<g.ny >> g.lrpc, row_threads(g), 2 * row_smem(g), s>>>(
+      g, GM0, GM1, GP0, GP1, mx, my, lmx, lmy, lx, ly, dr);
+}
+template <typename T>
+void col_lap_dot(const Geo<T>& g, const cx<T>* A, const cx<T>* B, double dt, AdjState* as,
+                 cudaStream_t s) {
+  k_col_lap_dot<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 2), s>>>(g, A, B, dt, as);
+}
+template <typename T>
+void spec_accum(const Geo<T>& g, double* acc, const cx<T>* v, cudaStream_t s) {
+  const size_t n = (size_t)g.ny * g.H;
+  k_spec_accum<T><<<upd_blocks(n), 256, 0, s>>>(acc, v, n);
+}
+template <typename T>
+void spec_norm2(const Geo<T>& g, const cx<T>* v, SolveState* st, cudaStream_t s) {
+  k_spec_norm2<T><<<upd_blocks((size_t)g.ny * g.H), 256, 0, s>>>(g, v, st);
+}
 
 // Allow a kernel the full opt-in shared memory of the device, less its own
 // static shared memory (the two together may not exceed the opt-in limit).
@@ -1450,6 +1713,9 @@ void set_smem_limits_t() {
   allow_smem(kp_col_grad<T, CG_PLAIN>);
   allow_smem(kp_col_grad<T, CG_DUPDATE>);
   allow_smem(kp_col_grad<T, CG_ADDDELTA>);
+  allow_smem(k_row_adj_point<T>);
+  allow_smem(k_row_adj_press<T>);
+  allow_smem(k_col_lap_dot<T>);
 }
 template <typename T, typename Tin>
 void set_smem_limits_grad() {

@@ -30,6 +30,16 @@ template void cg_update<float>(const Geo<float>&, cx<float>*, cx<float>*, const 
                                const cx<float>*, SolveState*, cudaStream_t);
 template void msum<float>(const Geo<float>&, const float*, const float*, SolveState*, cudaStream_t);
 
+template void row_adj_point<float>(const Geo<float>&, cx<float>*, cx<float>*, const cx<float>*, const cx<float>*,
+                                const float*, const float*, float*, float*, SplitCoef, AdjState*, cudaStream_t);
+template void row_adj_press<float>(const Geo<float>&, const cx<float>*, const cx<float>*, const cx<float>*,
+                                const cx<float>*, const float*, const float*, const float*, const float*, float*,
+                                float*, double*, cudaStream_t);
+template void col_lap_dot<float>(const Geo<float>&, const cx<float>*, const cx<float>*, double, AdjState*,
+                              cudaStream_t);
+template void spec_accum<float>(const Geo<float>&, double*, const cx<float>*, cudaStream_t);
+template void spec_norm2<float>(const Geo<float>&, const cx<float>*, SolveState*, cudaStream_t);
+
 void set_smem_limits_f32() {
   set_smem_limits_t<float>();
   set_smem_limits_grad<float, float>();

@@ -35,6 +35,16 @@ template void convert<double, double>(const double*, double*, size_t, cudaStream
 template void msum<double>(const Geo<double>&, const double*, const double*, SolveState*,
                            cudaStream_t);
 
+template void row_adj_point<double>(const Geo<double>&, cx<double>*, cx<double>*, const cx<double>*, const cx<double>*,
+                                const double*, const double*, double*, double*, SplitCoef, AdjState*, cudaStream_t);
+template void row_adj_press<double>(const Geo<double>&, const cx<double>*, const cx<double>*, const cx<double>*,
+                                const cx<double>*, const double*, const double*, const double*, const double*, double*,
+                                double*, double*, cudaStream_t);
+template void col_lap_dot<double>(const Geo<double>&, const cx<double>*, const cx<double>*, double, AdjState*,
+                              cudaStream_t);
+template void spec_accum<double>(const Geo<double>&, double*, const cx<double>*, cudaStream_t);
+template void spec_norm2<double>(const Geo<double>&, const cx<double>*, SolveState*, cudaStream_t);
+
 void set_smem_limits_f64() {
   set_smem_limits_t<double>();
   set_smem_limits_grad<double, double>();

@@ -1,0 +1,147 @@
+"""GPU adjoint (hc_adjoint) against the oracle's discrete adjoint, against
+central finite differences of the GPU's own forward map (64^2, the size the
+gradients are checked at), checkpoint invariance, and the torch.autograd
+wrapper."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_common import hc, rel_l2  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def problem(n=64):
+    w = W.source_sink_2d(n, steps=4, gamma=0.75)
+    # a gentler step so a few steps keep |grad p| moderate and gradients smooth
+    w.c, w.dt = 10.0, 1e-3
+    return w
+
+
+def make(hc, w, precision="fp64", rtol=1e-13):
+    s = hc.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision=precision,
+                  cg_rtol=rtol, cg_maxit=5000)
+    s.set_r(w.r)
+    s.set_source(w.S)
+    s.set_m(w.m0)
+    return s
+
+
+def test_adjoint_matches_oracle_adjoint_fp64(hc):
+    w = problem(64)
+    g = O.Grid(w.n, w.L)
+    rng = np.random.default_rng(4)
+    lam = rng.standard_normal((2,) + w.shape)
+    prm = O.Params(c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, cg_rtol=1e-13, cg_maxit=5000)
+    ref = O.adjoint(g, prm, w.r, w.S, w.m0, np.zeros(w.shape), 4, lam)
+    with make(hc, w) as s:
+        got = s.adjoint(4, lam, every=2)
+    assert np.isclose(got["dc2"], ref["dc2"], rtol=1e-8)
+    assert np.isclose(got["dD2"], ref["dD2"], rtol=1e-8)
+    for k in ("dr", "dS", "dm0"):
+        assert rel_l2(got[k], ref[k]) < 1e-8, k
+
+
+def test_adjoint_matches_central_differences_on_gpu(hc):
+    """Finite differences of the GPU forward itself at 64^2: relative error
+    <= 1e-4 for dL/dc^2, dL/dD^2 and sampled entries of dL/dr, dL/dS, dL/dm0."""
+    w = problem(64)
+    rng = np.random.default_rng(5)
+    lam = rng.standard_normal((2,) + w.shape)
+    nsteps = 3
+
+    def L_of(c=None, D=None, r=None, S=None, m0=None):
+        c = w.c if c is None else c
+        D = w.D if D is None else D
+        with hc.Solver(w.n, w.L, c=c, D=D, gamma=w.gamma, dt=w.dt, precision="fp64",
+                       cg_rtol=1e-14, cg_maxit=5000) as s:
+            s.set_r(w.r if r is None else r)
+            s.set_source(w.S if S is None else S)
+            s.set_m(w.m0 if m0 is None else m0)
+            s.step(nsteps)
+            return float((lam * s.get_m()).sum())
+
+    with make(hc, w, rtol=1e-14) as s:
+        adj = s.adjoint(nsteps, lam, every=2)
+    c2, D2 = w.c ** 2, w.D ** 2
+    h = 1e-4 * c2
+    fd = (L_of(c=np.sqrt(c2 + h)) - L_of(c=np.sqrt(c2 - h))) / (2 * h)
+    assert abs(adj["dc2"] - fd) <= 1e-4 * abs(fd)
+    h = 1e-3 * D2
+    fd = (L_of(D=np.sqrt(D2 + h)) - L_of(D=np.sqrt(D2 - h))) / (2 * h)
+    assert abs(adj["dD2"] - fd) <= 1e-4 * abs(fd)
+    for (j, i) in [(10, 20), (33, 47)]:
+        for key, field in (("dr", w.r), ("dS", w.S)):
+            hp, hm = field.copy(), field.copy()
+            hp[j, i] += 1e-5
+            hm[j, i] -= 1e-5
+            fd = (L_of(**{key[1:]: hp}) - L_of(**{key[1:]: hm})) / 2e-5
+            assert abs(adj[key][j, i] - fd) <= 1e-4 * np.abs(adj[key]).max(), key
+        mp, mm = w.m0.copy(), w.m0.copy()
+        mp[1, j, i] += 1e-6
+        mm[1, j, i] -= 1e-6
+        fd = (L_of(m0=mp) - L_of(m0=mm)) / 2e-6
+        assert abs(adj["dm0"][1, j, i] - fd) <= 1e-4 * np.abs(adj["dm0"]).max()
+
+
+def test_checkpoint_spacing_does_not_change_the_gradient(hc):
+    w = problem(64)
+    lam = np.random.default_rng(6).standard_normal((2,) + w.shape)
+    outs = []
+    for every in (1, 2, 5):
+        with make(hc, w) as s:
+            outs.append(s.adjoint(5, lam, every=every))
+    for o in outs[1:]:
+        assert o["dc2"] == outs[0]["dc2"] and o["dD2"] == outs[0]["dD2"]
+        for k in ("dr", "dS", "dm0"):
+            assert np.array_equal(o[k], outs[0][k])
+
+
+def test_adjoint_leaves_the_forward_state(hc):
+    w = problem(64)
+    lam = np.random.default_rng(7).standard_normal((2,) + w.shape)
+    with make(hc, w) as s:
+        s.step(3)
+        m_ref, p_ref = s.get_m(), s.get_p()
+    with make(hc, w) as s:
+        s.adjoint(3, lam, every=2)
+        assert np.array_equal(s.get_m(), m_ref)
+        assert np.array_equal(s.get_p(), p_ref)
+
+
+def test_refined_adjoint_close_to_oracle(hc):
+    """FP32 forward with FP64 refinement: gradients to FP32 accuracy."""
+    w = problem(128)
+    g = O.Grid(w.n, w.L)
+    lam = np.random.default_rng(8).standard_normal((2,) + w.shape)
+    prm = O.Params(c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, cg_rtol=1e-12, cg_maxit=5000)
+    ref = O.adjoint(g, prm, w.r, w.S, w.m0, np.zeros(w.shape), 3, lam)
+    with make(hc, w, "fp32_refined", rtol=1e-9) as s:
+        got = s.adjoint(3, lam, every=2)
+    assert np.isclose(got["dc2"], ref["dc2"], rtol=1e-3)
+    assert np.isclose(got["dD2"], ref["dD2"], rtol=1e-3)
+    for k in ("dr", "dS", "dm0"):
+        assert rel_l2(got[k], ref[k]) < 1e-3, k
+
+
+def test_autograd_function(hc):
+    import torch
+    w = problem(64)
+    with make(hc, w) as s:
+        c2 = torch.tensor(w.c ** 2, dtype=torch.float64, requires_grad=True)
+        D2 = torch.tensor(w.D ** 2, dtype=torch.float64, requires_grad=True)
+        r = torch.from_numpy(w.r.copy()).requires_grad_()
+        S = torch.from_numpy(w.S.copy()).requires_grad_()
+        m0 = torch.from_numpy(w.m0.copy()).requires_grad_()
+        target = torch.from_numpy(np.full((2,) + w.shape, 0.2))
+        mT = hc.hucai_steps(s, 2, 1, c2, D2, r, S, m0)
+        loss = ((mT - target) ** 2).sum()
+        loss.backward()
+        lam = 2 * (mT.detach().numpy() - 0.2)
+        s.set_params(c=w.c, D=w.D)
+        s.set_r(w.r); s.set_source(w.S); s.set_m(w.m0); s.set_p(np.zeros(w.shape))
+        ref = s.adjoint(2, lam, every=1)
+    assert np.isclose(c2.grad.item(), ref["dc2"], rtol=1e-12)
+    assert np.allclose(m0.grad.numpy(), ref["dm0"], rtol=1e-12, atol=0)
+    assert np.allclose(r.grad.numpy(), ref["dr"], rtol=1e-12, atol=0)
