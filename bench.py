@@ -62,6 +62,26 @@ BYTES_PER_POINT = {
 FP64_KERNELS = {"fp32_refined": {"res_grad", "res_apply", "res_div"},
                 "fp64": set(BYTES_PER_POINT["fp64"])}
 
+# DRAM bytes (read + write) per launch measured by ncu for the 2048^2 refined
+# workload with the current kernels (profiles/residual_and_cg_kernels_2048.md).
+# Set an entry to None when its kernel changes.
+NCU_TRAFFIC_2048 = {"res_grad": 54.9e6, "res_apply": 136.8e6, "res_div": 132.9e6,
+                    "cg_grad": 35.6e6, "cg_apply": 86.1e6, "cg_div": 50.6e6, "cg_update": 67.7e6}
+
+
+def shard(items: int, rank: int, world: int) -> list:
+    """Indices of the independent problems rank `rank` runs (round robin)."""
+    return [i for i in range(items) if i % world == rank]
+
+
+def aggregate(local_ms: float, local_units: float, world: int, reduce_max, reduce_sum):
+    """Whole-job throughput from per-rank timings: the slowest rank's time and
+    the units all ranks processed.  Returns (max_ms, units_total, units per
+    second)."""
+    ms = reduce_max(local_ms) if world > 1 else local_ms
+    units = reduce_sum(local_units) if world > 1 else local_units
+    return ms, units, units / (ms / 1e3)
+
 
 def fft_flops_per_point(kernel: str, nx: int, ny: int) -> float:
     """Algorithmic FLOPs per point and launch: 5 N log2 N per complex FFT of
@@ -342,14 +362,17 @@ def run_gb300(args) -> None:
         bytes_step += bpp * npts * cnt
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     dk = kernels[dom]
+    traffic = NCU_TRAFFIC_2048.get(dom) if w.n == (2048, 2048) else None
     if dk["bound"] == "alu":
         roofline = {"bound": "alu", "kernel": dom, "achieved": dk["alg_TFLOPs"],
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": dk["frac"],
-                    "traffic": None, "peak_source": "nominal FP64 (recipe table)"}
+                    "traffic": traffic, "peak_source": "nominal FP64 (recipe table)",
+                    "alg_bytes": BYTES_PER_POINT["fp32_refined"][dom] * npts}
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["alg_GBs"], "peak": hbm_peak,
-                    "unit": "GB/s", "frac": dk["frac"], "traffic": None,
-                    "peak_source": hbm_src}
+                    "unit": "GB/s", "frac": dk["frac"], "traffic": traffic,
+                    "peak_source": hbm_src,
+                    "alg_bytes": BYTES_PER_POINT["fp32_refined"][dom] * npts}
     share = dk["ms_per_step"] / (ms / K)
     roofline["share_of_step"] = share
 
@@ -421,7 +444,7 @@ def run_gb300(args) -> None:
     # ---- batched parameter sweep: 48 instances of mixed grids in one graph launch
     sweep = None
     if not args.no_sweep:
-        mine = [i for i in range(48) if i % world == rank]
+        mine = shard(48, rank, world)
         sws = [W.sweep_instance(i) for i in mine]
         solvers = []
         for wi in sws:
