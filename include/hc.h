@@ -15,11 +15,13 @@
  *
  * Conventions shared by every entry point
  *   - Grid (Section 2.2): n[a] nodes per axis, periodic end point excluded,
- *     x_i = i L[a] / n[a].  2D only: dim = 2, n[0] = nx, n[1] = ny, both powers
- *     of two in [8, 4096]; n[2] must be 1.
- *   - Field layout: row-major, x fastest.  A scalar field has nx*ny doubles at
- *     index j*nx + i.  A vector field (m) is component-major: component c of
- *     point (i, j) at c*nx*ny + j*nx + i, so count = 2*nx*ny.
+ *     x_i = i L[a] / n[a].  dim = 2: n[0] = nx, n[1] = ny, powers of two in
+ *     [8, 4096], n[2] = 1.  dim = 3 (the method's 3D case, Section 2.3):
+ *     nx, ny, nz powers of two in [8, 1024], nx*ny*nz <= 2^28.
+ *   - Field layout: row-major, x fastest.  A scalar field has npts = nx*ny*nz
+ *     doubles (nz = 1 in 2D) at index (k*ny + j)*nx + i.  A vector field (m,
+ *     the gradient) is component-major: component c of point q at c*npts + q,
+ *     so count = dim*npts.
  *   - Every host pointer is FP64 whatever the internal precision; it is read
  *     or written completely before the call returns (the call waits for its
  *     own copies), so the caller may reuse the buffer right away.
@@ -60,7 +62,7 @@ extern "C" {
 typedef struct hc_ctx hc_ctx; /* opaque; owns (or borrows) all device memory of one problem */
 
 typedef struct {
-  int dim;      /* 2 */
+  int dim;      /* 2 or 3 */
   int n[3];     /* nodes per axis (x, y, z) */
   double L[3];  /* domain lengths, > 0 */
 } hc_grid;
@@ -70,7 +72,7 @@ typedef struct {
   double cg_rtol;         /* stop when ||S - A p||_2 <= cg_rtol ||S||_2, S projected (Section 2.4; default 1e-7 if <= 0) */
   int cg_maxit;           /* CG iteration cap per solve; in refined mode per inner FP32 solve (default 1000 if <= 0) */
   int precision;          /* HC_FP64_PLAIN or HC_FP32_REFINED */
-  double kappa;           /* preconditioner constant; <= 0: mean(r) + mean(|m|^2)/2, recomputed every step */
+  double kappa;           /* preconditioner constant; <= 0: mean(r) + mean(|m|^2)/dim, recomputed every step */
   double inner_rtol;      /* refined mode: inner FP32 CG stops at this reduction of its own residual (default 1e-4 if <= 0) */
   int max_sweeps;         /* refined mode: cap on FP64 refinement sweeps per solve (default 10 if <= 0) */
   int use_graph;          /* 1: each step runs as one CUDA graph with device-side loop control; 0: host loop */
@@ -102,16 +104,16 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
  * the grid, precision and stream must match the ones given at creation. */
 int hc_set_params(hc_ctx* ctx, const hc_params* params);
 
-/* Background permeability r(x) (eq. 1.1a); count = nx*ny; requires r > 0
+/* Background permeability r(x) (eq. 1.1a); count = npts; requires r > 0
  * everywhere (the paper assumes r >= r0 > 0) and finite, else HC_EINVAL. */
 int hc_set_r(hc_ctx* ctx, const double* r, size_t count);
 
-/* Source/sink field S (eq. 1.1a); count = nx*ny.  Stored after projection onto
+/* Source/sink field S (eq. 1.1a); count = npts.  Stored after projection onto
  * the complement of the operator's null space (zero mean and no corner modes:
  * the solvability condition that the paper states as int S = 0). */
 int hc_set_source(hc_ctx* ctx, const double* S, size_t count);
 
-/* Conductivity m (count = 2*nx*ny, component-major). */
+/* Conductivity m (count = dim*npts, component-major). */
 int hc_set_m(hc_ctx* ctx, const double* m, size_t count);
 
 /* Pressure p used as the CG initial guess of the next step (Section 2.4 uses
@@ -123,28 +125,28 @@ int hc_set_p(hc_ctx* ctx, const double* p, size_t count);
  * step status (HC_ENOCONV: the steps still ran; HC_ENONFINITE: stopped). */
 int hc_step(hc_ctx* ctx, int nsteps, hc_step_stats* last);
 
-/* Copy the current p (count = nx*ny) or m (count = 2*nx*ny) to host memory. */
+/* Copy the current p (count = npts) or m (count = dim*npts) to host memory. */
 int hc_get_p(hc_ctx* ctx, double* out, size_t count);
 int hc_get_m(hc_ctx* ctx, double* out, size_t count);
 
 /* --- Component entry points (each runs one part of the step on the GPU) --- */
 
 /* Spectral gradient of the current p (Section 2.4 and Algorithm 1 "compute
- * gradient of p via FFT"): out = (d_x p, d_y p), count = 2*nx*ny. */
+ * gradient of p via FFT"): out = (d_x p, d_y p[, d_z p]), count = dim*npts. */
 int hc_gradient(hc_ctx* ctx, double* out, size_t count);
 
 /* Apply the discrete pressure operator of eq. (p_discrete) with the current m
- * and r: out = A f for the field f (count = nx*ny; f is projected first). */
+ * and r: out = A f for the field f (count = npts; f is projected first). */
 int hc_apply_operator(hc_ctx* ctx, const double* f, double* out, size_t count);
 
 /* Only Step 2 of Algorithm 1 (activation, relaxation, diffusion) with the
  * current p and m; m is updated in place on the device. */
 int hc_split_step(hc_ctx* ctx);
 
-/* Forward 2D DFT of a real field (count = nx*ny) in the packed half-spectrum
- * layout: out has ny*(nx/2) complex values (2*ny*(nx/2) doubles, re/im
- * interleaved); entry (ky, kx) for 1 <= kx < nx/2 is F[ky][kx] and entry
- * (ky, 0) is F[ky][0] + i F[ky][nx/2]. */
+/* Forward DFT of a real field (count = npts) in the packed half-spectrum
+ * layout: out has nz*ny*(nx/2) complex values (npts doubles, re/im
+ * interleaved); entry (kz, ky, kx) for 1 <= kx < nx/2 is F[kz][ky][kx] and
+ * entry (kz, ky, 0) is F[kz][ky][0] + i F[kz][ky][nx/2] (kz = 0 in 2D). */
 int hc_spectrum(hc_ctx* ctx, const double* f, double* out, size_t count);
 
 /* Launch shapes of the FFT passes, per arithmetic precision ([0] FP32
@@ -163,13 +165,19 @@ typedef struct {
 
 int hc_get_tuning(const hc_ctx* ctx, hc_tuning* out);
 /* HC_EINVAL if a value breaks the limits above or needs more shared memory
- * than a CTA may have. */
+ * than a CTA may have; HC_ENOTSUP on 3D grids (their launch shapes are fixed
+ * when the context is created). */
 int hc_set_tuning(hc_ctx* ctx, const hc_tuning* in);
 
 /* Kernels of one step, as timed by hc_time_kernel.  The CG_* kernels are the
  * CG iteration (FP32 inner CG in refined mode, FP64 CG in plain mode); RES_*
  * the FP64 residual evaluation (refined: p64 += delta then S - A p64; plain:
- * the initial residual); SPLIT_* Step 2 of Algorithm 1. */
+ * the initial residual); SPLIT_* Step 2 of Algorithm 1.  On a 3D grid the
+ * same ids time the 3D kernels: *_GRAD the z pass with the gradient
+ * multipliers, *_APPLY the row-pair pass, *_DIV the z pass with the
+ * divergence, *_YPASS the y pass between them, SPLIT_ROW the row pass with
+ * activation, relaxation and diffusion along x, SPLIT_HEAT / SPLIT_C2R the
+ * diffusion along y / along z. */
 enum {
   HC_K_CG_GRAD = 0,    /* column pass: d-update, i xi d / n, inverse FFT_y */
   HC_K_CG_APPLY = 1,   /* row pass: C2R, (m m^T + r I) g, R2C */
@@ -182,7 +190,9 @@ enum {
   HC_K_SPLIT_ROW = 8,  /* row pass: C2R, activation, relaxation, R2C */
   HC_K_SPLIT_HEAT = 9, /* column pass: FFT_y, heat factor, IFFT_y */
   HC_K_SPLIT_C2R = 10, /* row pass: C2R to physical m, sum |m|^2 */
-  HC_K_COUNT = 11
+  HC_K_CG_YPASS = 11,  /* 3D only: y pass (FFT of 3 fields) of the inner CG */
+  HC_K_RES_YPASS = 12, /* 3D only: y pass of the refinement residual */
+  HC_K_COUNT = 13
 };
 
 /* Launch one step kernel `reps` times back to back on the context's current
@@ -201,7 +211,7 @@ int hc_launch_count(const hc_ctx* ctx, long long* count);
 /* Bytes of device memory hc_adjoint needs for nsteps steps with a checkpoint
  * every `every` steps: ceil(nsteps/every) checkpoints of (m, p), one segment
  * of `every` states, and the reverse sweep's buffers.  HC_ENOTSUP in the
- * double-float precision mode. */
+ * double-float precision mode and on 3D grids. */
 int hc_adjoint_workspace_size(const hc_ctx* ctx, int nsteps, int every, size_t* bytes);
 
 /* Discrete adjoint of nsteps loop bodies of Algorithm 1 started from the

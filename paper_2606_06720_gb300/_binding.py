@@ -131,7 +131,7 @@ hc_batch_destroy = lib.hc_batch_destroy
 
 # kernel ids of hc_time_kernel (include/hc.h)
 KERNELS = ["cg_grad", "cg_apply", "cg_div", "cg_update", "res_grad", "res_apply", "res_div",
-           "split_grad", "split_row", "split_heat", "split_c2r"]
+           "split_grad", "split_row", "split_heat", "split_c2r", "cg_ypass", "res_ypass"]
 
 
 def strerror(code: int) -> str:
@@ -180,27 +180,34 @@ def _host_f64(a, count: int, writable: bool = False):
 class Solver:
     """One Hu-Cai problem on one GPU.
 
-    ``n = (nx, ny)`` nodes, ``L = (Lx, Ly)``; ``precision`` is ``"fp64"`` (plain),
-    ``"fp32_refined"`` (FP64 refinement) or ``"fp32_refined_df"`` (refinement in
-    double-float on the FP32 pipes).  Arrays use numpy shapes ``(ny, nx)`` for scalar
-    fields and ``(2, ny, nx)`` for m.
+    ``n = (nx, ny)`` or ``(nx, ny, nz)`` nodes, ``L`` the domain lengths (same
+    length); ``precision`` is ``"fp64"`` (plain), ``"fp32_refined"`` (FP64
+    refinement) or ``"fp32_refined_df"`` (refinement in double-float on the FP32
+    pipes).  Arrays use numpy shapes ``(ny, nx)`` / ``(nz, ny, nx)`` for scalar
+    fields and ``(dim, ...)`` for m and the gradient.
     """
 
-    def __init__(self, n, L=(1.0, 1.0), *, c: float, D: float, gamma: float, dt: float,
+    def __init__(self, n, L=None, *, c: float, D: float, gamma: float, dt: float,
                  precision: str = "fp32_refined", cg_rtol: float = 1e-8, cg_maxit: int = 1000,
                  kappa: float = 0.0, inner_rtol: float = 1e-4, max_sweeps: int = 10,
                  use_graph: bool = True, device: str = "cuda:0", stream=None):
         import torch
         self.torch = torch
         self.device = torch.device(device)
-        self.n = (int(n[0]), int(n[1]))
-        self.L = (float(L[0]), float(L[1]))
-        self.npts = self.n[0] * self.n[1]
-        self.shape = (self.n[1], self.n[0])
+        self.dim = len(n)
+        if self.dim not in (2, 3):
+            raise ValueError("n must have 2 or 3 entries")
+        self.n = tuple(int(v) for v in n)
+        self.L = tuple(float(v) for v in (L if L is not None else (1.0,) * self.dim))
+        if len(self.L) != self.dim:
+            raise ValueError("L must have as many entries as n")
+        self.npts = int(np.prod(self.n))
+        self.shape = tuple(reversed(self.n))
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.grid = hc_grid(2, (C.c_int * 3)(self.n[0], self.n[1], 1),
-                            (C.c_double * 3)(self.L[0], self.L[1], 1.0))
+        n3 = self.n + (1,) * (3 - self.dim)
+        L3 = self.L + (1.0,) * (3 - self.dim)
+        self.grid = hc_grid(self.dim, (C.c_int * 3)(*n3), (C.c_double * 3)(*L3))
         prec = {"fp64": HC_FP64_PLAIN, "fp64_plain": HC_FP64_PLAIN,
                 "fp32_refined": HC_FP32_REFINED, "fp32_refined_df": HC_FP32_REFINED_DF}[precision]
         self.precision = precision
@@ -253,8 +260,8 @@ class Solver:
         _check(hc_set_source(self.ctx, p, self.npts), "hc_set_source")
 
     def set_m(self, m):
-        p, keep = _host_f64(m, 2 * self.npts)
-        _check(hc_set_m(self.ctx, p, 2 * self.npts), "hc_set_m")
+        p, keep = _host_f64(m, self.dim * self.npts)
+        _check(hc_set_m(self.ctx, p, self.dim * self.npts), "hc_set_m")
 
     def set_p(self, p_):
         p, keep = _host_f64(p_, self.npts)
@@ -267,9 +274,9 @@ class Solver:
         return out
 
     def get_m(self, out=None):
-        out = np.empty((2,) + self.shape) if out is None else out
-        p, keep = _host_f64(out, 2 * self.npts, writable=True)
-        _check(hc_get_m(self.ctx, p, 2 * self.npts), "hc_get_m")
+        out = np.empty((self.dim,) + self.shape) if out is None else out
+        p, keep = _host_f64(out, self.dim * self.npts, writable=True)
+        _check(hc_get_m(self.ctx, p, self.dim * self.npts), "hc_get_m")
         return out
 
     # the step -------------------------------------------------------------
@@ -282,9 +289,9 @@ class Solver:
 
     # components ----------------------------------------------------------
     def gradient(self):
-        out = np.empty((2,) + self.shape)
-        p, keep = _host_f64(out, 2 * self.npts, writable=True)
-        _check(hc_gradient(self.ctx, p, 2 * self.npts), "hc_gradient")
+        out = np.empty((self.dim,) + self.shape)
+        p, keep = _host_f64(out, self.dim * self.npts, writable=True)
+        _check(hc_gradient(self.ctx, p, self.dim * self.npts), "hc_gradient")
         return out
 
     def apply_operator(self, f):
@@ -298,9 +305,9 @@ class Solver:
         _check(hc_split_step(self.ctx), "hc_split_step")
 
     def spectrum(self, f):
-        """Packed half spectrum, complex array of shape (ny, nx/2)."""
+        """Packed half spectrum, complex array of shape (ny, nx/2) or (nz, ny, nx/2)."""
         fp, keep = _host_f64(f, self.npts)
-        out = np.empty((self.n[1], self.n[0] // 2), dtype=np.complex128)
+        out = np.empty(self.shape[:-1] + (self.n[0] // 2,), dtype=np.complex128)
         op = out.view(np.float64).ctypes.data_as(C.POINTER(C.c_double))
         _check(hc_spectrum(self.ctx, fp, op, self.npts), "hc_spectrum")
         return out

@@ -1,7 +1,8 @@
 """Build the sm_103a shared library libhc_gb300.so in-tree with nvcc.
 
-The three translation units (FP32 kernels, FP64 kernels, host orchestration +
-C ABI) compile in parallel, then link into one shared object next to this file.
+The translation units (2D and 3D kernels per precision, host orchestration +
+C ABI, the allocation-free transform) compile in parallel, then link into one
+shared object next to this file.
 """
 from __future__ import annotations
 
@@ -16,9 +17,9 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libhc_gb300.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["hc_kernels_f32.cu", "hc_kernels_f64.cu", "hc_kernels_df.cu", "hc_api.cu",
-           "hc_noalloc.cu"]
-HEADERS = ["hc_internal.cuh", "hc_kernels.cuh"]
+SOURCES = ["hc_kernels_f32.cu", "hc_kernels_f64.cu", "hc_kernels_df.cu", "hc_kernels3d_f32.cu",
+           "hc_kernels3d_f64.cu", "hc_kernels3d_df.cu", "hc_api.cu", "hc_noalloc.cu"]
+HEADERS = ["hc_internal.cuh", "hc_kernels.cuh", "hc_kernels3d.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE] + ARCH
 

@@ -53,8 +53,10 @@ int ilog2(int v) {
 struct hc_ctx {
   hc_grid grid;
   hc_params prm;
-  int nx, ny, H;
+  int dim;   // 2 or 3
+  int nx, ny, nz, H;  // nz = 1 in 2D
   size_t n;  // points
+  size_t ns; // packed spectral values: nz * ny * H
   int refined;
   int df;    // refined with double-float state and residual
   cudaStream_t stream;
@@ -74,13 +76,13 @@ struct hc_ctx {
   cx<double>* r64;          // residual (FP64)
   cx<double>* d64;          // CG direction (plain mode)
   cx<double>* q64;          // A d (plain mode)
-  cx<double>* G64;          // 2 spectra: gradient / flux / m scratch (FP64)
+  cx<double>* G64;          // dim spectra: gradient / flux / m scratch (FP64)
   cx<float>* r32;           // refined: inner residual
   cx<float>* d32;           // refined: inner direction
   cx<float>* q32;           // refined: A d
   cx<float>* x32;           // refined: inner solution (correction delta)
-  cx<float>* G32;           // refined: 2 spectra scratch (FP32)
-  void* m[2];               // conductivity components (double or float)
+  cx<float>* G32;           // refined: dim spectra scratch (FP32)
+  void* m[3];               // conductivity components (double or float); m[2] in 3D only
   void* rf;                 // permeability r (double or float)
   // tables
   cx<float>*twx_f, *twy_f;
@@ -91,9 +93,20 @@ struct hc_ctx {
   df64 *kxd_q, *kyd_q;
   float *x2x_f, *x2y_f;
   double *x2x_d, *x2y_d;
+  cx<float>* twz_f;         // 3D only
+  cx<double>* twz_d;
+  cx<df64>* twz_q;
+  float *kzd_f, *hz_f;
+  double *kzd_d, *hz_d;
+  df64* kzd_q;
   hc::Geo<float> gf;
   hc::Geo<double> gd;
   hc::Geo<df64> gq;  // double-float kernels (HC_FP32_REFINED_DF)
+  // The same geometry seen as ny*nz rows of length nx: the 2D row kernels
+  // (R2C/C2R of single fields) run the x pass of a 3D grid through these.
+  hc::Geo<float> rowf;
+  hc::Geo<double> rowd;
+  hc::Geo<df64> rowq;
 
   hc::SolveState* st_host;  // pinned mirror for readback
   // graph mode: captured on a private stream (capture is illegal on the
@@ -147,25 +160,31 @@ double xi(int l, int N, double L) {
 // First-derivative multiplier, Nyquist entry zero.
 double xid(int l, int N, double L) { return (2 * l == N) ? 0.0 : xi(l, N, L); }
 
+// Most CTAs of any kernel that reduces through the per-CTA partials.
+size_t max_reducing_ctas(const hc_ctx* c) {
+  size_t m = std::max<size_t>({(size_t)c->H, (size_t)c->ny, (size_t)1216});
+  if (c->dim == 3) m = std::max(m, (size_t)c->ny * c->H);  // z pass with one column per CTA
+  return m;
+}
+
 void layout(hc_ctx* c, Layout& L) {
   const size_t n = c->n;
-  const size_t S64 = (size_t)c->ny * c->H * sizeof(cx<double>);
-  const size_t S32 = (size_t)c->ny * c->H * sizeof(cx<float>);
-  const int max_ctas = (int)std::max<size_t>({(size_t)c->H, (size_t)c->ny, (size_t)1216});
+  const int d = c->dim;
+  const size_t S64 = c->ns * sizeof(cx<double>);
+  const size_t S32 = c->ns * sizeof(cx<float>);
   c->st = L.take<hc::SolveState>(sizeof(hc::SolveState));
   c->st_time = L.take<hc::SolveState>(sizeof(hc::SolveState));
-  c->partials = L.take<double>(sizeof(double) * 4 * max_ctas);
-  c->stage = L.take<double>(sizeof(double) * 2 * n);
+  c->partials = L.take<double>(sizeof(double) * 4 * max_reducing_ctas(c));
+  c->stage = L.take<double>(sizeof(double) * d * n);
   c->p64 = L.take<cx<double>>(S64);
   c->b64 = L.take<cx<double>>(S64);
   c->r64 = L.take<cx<double>>(S64);
-  c->G64 = L.take<cx<double>>(2 * S64);
+  c->G64 = L.take<cx<double>>(d * S64);
   if (!c->refined) {
     c->d64 = L.take<cx<double>>(S64);
     c->q64 = L.take<cx<double>>(S64);
     c->r32 = c->d32 = c->q32 = c->x32 = c->G32 = nullptr;
-    c->m[0] = L.take<double>(sizeof(double) * n);
-    c->m[1] = L.take<double>(sizeof(double) * n);
+    for (int k = 0; k < d; ++k) c->m[k] = L.take<double>(sizeof(double) * n);
     c->rf = L.take<double>(sizeof(double) * n);
   } else {
     c->d64 = c->q64 = nullptr;
@@ -173,9 +192,8 @@ void layout(hc_ctx* c, Layout& L) {
     c->d32 = L.take<cx<float>>(S32);
     c->q32 = L.take<cx<float>>(S32);
     c->x32 = L.take<cx<float>>(S32);
-    c->G32 = L.take<cx<float>>(2 * S32);
-    c->m[0] = L.take<float>(sizeof(float) * n);
-    c->m[1] = L.take<float>(sizeof(float) * n);
+    c->G32 = L.take<cx<float>>(d * S32);
+    for (int k = 0; k < d; ++k) c->m[k] = L.take<float>(sizeof(float) * n);
     c->rf = L.take<float>(sizeof(float) * n);
   }
   c->twx_f = L.take<cx<float>>(sizeof(cx<float>) * c->nx);
@@ -198,12 +216,30 @@ void layout(hc_ctx* c, Layout& L) {
   c->x2y_d = L.take<double>(sizeof(double) * c->ny);
   c->hx_d = L.take<double>(sizeof(double) * (c->H + 1));
   c->hy_d = L.take<double>(sizeof(double) * c->ny);
+  if (d == 3) {
+    c->twz_f = L.take<cx<float>>(sizeof(cx<float>) * c->nz);
+    c->twz_d = L.take<cx<double>>(sizeof(cx<double>) * c->nz);
+    c->twz_q = L.take<cx<df64>>(sizeof(cx<df64>) * c->nz);
+    c->kzd_f = L.take<float>(sizeof(float) * c->nz);
+    c->kzd_d = L.take<double>(sizeof(double) * c->nz);
+    c->kzd_q = L.take<df64>(sizeof(df64) * c->nz);
+    c->hz_f = L.take<float>(sizeof(float) * c->nz);
+    c->hz_d = L.take<double>(sizeof(double) * c->nz);
+  }
 }
 
 int check_grid(const hc_grid* g) {
-  if (!g || g->dim != 2) return HC_EINVAL;
-  if (!is_pow2_in(g->n[0], 8, 4096) || !is_pow2_in(g->n[1], 8, 4096) || g->n[2] != 1)
-    return HC_EINVAL;
+  if (!g || (g->dim != 2 && g->dim != 3)) return HC_EINVAL;
+  if (g->dim == 2) {
+    if (!is_pow2_in(g->n[0], 8, 4096) || !is_pow2_in(g->n[1], 8, 4096) || g->n[2] != 1)
+      return HC_EINVAL;
+  } else {
+    if (!is_pow2_in(g->n[0], 8, 1024) || !is_pow2_in(g->n[1], 8, 1024) ||
+        !is_pow2_in(g->n[2], 8, 1024))
+      return HC_EINVAL;
+    if ((size_t)g->n[0] * g->n[1] * g->n[2] > ((size_t)1 << 28)) return HC_EINVAL;
+    if (!(g->L[2] > 0) || !std::isfinite(g->L[2])) return HC_EINVAL;
+  }
   if (!(g->L[0] > 0) || !(g->L[1] > 0) || !std::isfinite(g->L[0]) || !std::isfinite(g->L[1]))
     return HC_EINVAL;
   return HC_OK;
@@ -249,7 +285,56 @@ void fill_geo(hc_ctx* c, hc::Geo<T>& g, const cx<T>* twx, const cx<T>* twy, cons
   g.hx = hx;
   g.hy = hy;
   g.partials = c->partials;
-  g.npartials = (int)std::max<size_t>({(size_t)c->H, (size_t)c->ny, (size_t)1216});
+  g.npartials = (int)max_reducing_ctas(c);
+  g.nz = c->nz;
+  g.lnz = ilog2(c->nz);
+  g.twz = nullptr;
+  g.kzd = nullptr;
+  g.hz = nullptr;
+  g.upc = g.lupc = 0;
+  g.py = g.pz = hc::ColPass{};
+}
+
+// Tile of a 3D column pass of three fields: at most 256 threads (tc * L/8)
+// and, where possible, at most ~113 KB of shared memory so two CTAs fit an SM.
+hc::ColPass make_pass(int lL, long long cols, int nplanes, long long stride, long long pstride,
+                      size_t elem) {
+  const int L8 = 1 << (lL - 3);
+  long long tc = std::max(1, 256 / L8);
+  tc = std::min<long long>({tc, 32, cols});
+  while (tc > 1 && 3 * 9 * (size_t)L8 * tc * elem > 113 * 1024) tc >>= 1;
+  hc::ColPass p;
+  p.lL = lL;
+  p.ltc = ilog2((int)tc);
+  p.lt = ilog2((int)(cols / tc));
+  p.nplanes = nplanes;
+  p.stride = stride;
+  p.pstride = pstride;
+  return p;
+}
+
+template <typename T>
+void fill_geo3(hc_ctx* c, hc::Geo<T>& g, hc::Geo<T>& rows, const cx<T>* twz, const T* kzd,
+               const T* hz) {
+  const long long H = c->H, ny = c->ny;
+  g.twz = twz;
+  g.kzd = kzd;
+  g.hz = hz;
+  g.py = make_pass(g.lny, H, c->nz, H, ny * H, sizeof(cx<T>));
+  g.pz = make_pass(g.lnz, ny * H, 1, ny * H, 0, sizeof(cx<T>));
+  // row pairs: N/8 threads per pair, 256 threads per CTA
+  int upc = std::max(1, 256 >> (g.lnx - 3));
+  upc = std::min(upc, (int)((size_t)c->ny * c->nz / 2));
+  g.upc = upc;
+  g.lupc = ilog2(upc);
+  rows = g;
+  rows.ny = c->ny * c->nz;
+  rows.lny = g.lny + g.lnz;
+  int rpc = 256 >> (g.lnx - 3);
+  if (rpc < 1) rpc = 1;
+  if (rpc > rows.ny) rpc = rows.ny;
+  rows.rpc = rpc;
+  rows.lrpc = ilog2(rpc);
 }
 
 // Most recent CUDA failure seen by this library on the calling thread.
@@ -310,6 +395,17 @@ int upload_tables(hc_ctx* c) {
   std::vector<df64> kxq(kx.begin(), kx.end()), kyq(ky.begin(), ky.end());
   CU(cudaMemcpy(c->kxd_q, kxq.data(), sizeof(df64) * c->H, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c->kyd_q, kyq.data(), sizeof(df64) * c->ny, cudaMemcpyHostToDevice));
+  if (c->dim == 3) {
+    rc = put_tw(c->nz, c->twz_f, c->twz_d, c->twz_q);
+    if (rc) return rc;
+    std::vector<double> kz(c->nz);
+    for (int k = 0; k < c->nz; ++k) kz[k] = xid(k, c->nz, c->grid.L[2]);
+    std::vector<float> kzf(kz.begin(), kz.end());
+    std::vector<df64> kzq(kz.begin(), kz.end());
+    CU(cudaMemcpy(c->kzd_d, kz.data(), sizeof(double) * c->nz, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->kzd_f, kzf.data(), sizeof(float) * c->nz, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->kzd_q, kzq.data(), sizeof(df64) * c->nz, cudaMemcpyHostToDevice));
+  }
   return HC_OK;
 }
 
@@ -333,6 +429,20 @@ int upload_heat(hc_ctx* c) {
   CU(cudaMemcpyAsync(c->hx_f, hxf.data(), sizeof(float) * (c->H + 1), cudaMemcpyHostToDevice,
                      c->stream));
   CU(cudaMemcpyAsync(c->hy_f, hyf.data(), sizeof(float) * c->ny, cudaMemcpyHostToDevice, c->stream));
+  std::vector<double> hz;
+  std::vector<float> hzf;
+  if (c->dim == 3) {
+    hz.resize(c->nz);
+    for (int k = 0; k < c->nz; ++k) {
+      const double z = xi(k, c->nz, c->grid.L[2]);
+      hz[k] = std::exp(-D2dt * z * z);
+    }
+    hzf.assign(hz.begin(), hz.end());
+    CU(cudaMemcpyAsync(c->hz_d, hz.data(), sizeof(double) * c->nz, cudaMemcpyHostToDevice,
+                       c->stream));
+    CU(cudaMemcpyAsync(c->hz_f, hzf.data(), sizeof(float) * c->nz, cudaMemcpyHostToDevice,
+                       c->stream));
+  }
   CU(cudaStreamSynchronize(c->stream));  // host vectors die here
   return HC_OK;
 }
@@ -374,8 +484,42 @@ int push_config(hc_ctx* c) {
 }
 
 // ---------------------------------------------------------------- step pieces
+template <typename T>
+hc::Tri<cx<T>*> tri(cx<T>* G, size_t ns) {
+  return hc::Tri<cx<T>*>{{G, G + ns, G + 2 * ns}};
+}
+template <typename T>
+hc::Tri<const T*> mtri(hc_ctx* c) {
+  return hc::Tri<const T*>{{(const T*)c->m[0], (const T*)c->m[1], (const T*)c->m[2]}};
+}
+template <typename T>
+hc::Tri<T*> mtri_w(hc_ctx* c) {
+  return hc::Tri<T*>{{(T*)c->m[0], (T*)c->m[1], (T*)c->m[2]}};
+}
+
+// 3D operator apply on the spectral direction/iterate: z gradient pass (mode),
+// inverse y, row apply, forward y; the caller's z_div closes it.
+template <typename T, typename Tin, typename Tm>
+void apply3_open(hc_ctx* c, hc::Geo<T>& g, int mode, cx<Tin>* in, const cx<T>* rvec, cx<T>* dio,
+                 cx<T>* G, int check_done) {
+  auto Gt = tri(G, c->ns);
+  hc::z_grad<T, Tin>(g, mode, in, rvec, dio, c->x32, Gt, c->st, check_done, c->stream);
+  hc::axis_fft<T>(g, 1, +1, 3, Gt, Gt, (T)1, c->stream);
+  hc::row_apply3<T, Tm>(g, Gt, mtri<Tm>(c), (const Tm*)c->rf, Gt, check_done ? c->st : nullptr,
+                        c->stream);
+  hc::axis_fft<T>(g, 1, -1, 3, Gt, Gt, (T)1, c->stream);
+  c->launches += 4;
+}
+
 // r = b - A x0 in FP64 plain mode; initialises the CG state.
 void plain_init(hc_ctx* c) {
+  if (c->dim == 3) {
+    apply3_open<double, double, double>(c, c->gd, hc::CG_PLAIN, c->p64, nullptr, nullptr, c->G64, 0);
+    hc::z_div<double>(c->gd, hc::CD_RESID, tri(c->G64, c->ns), nullptr, c->b64, c->r64, nullptr,
+                      nullptr, c->st, c->stream);
+    c->launches += 1;
+    return;
+  }
   auto& g = c->gd;
   cx<double>* Gx = c->G64;
   cx<double>* Gy = c->G64 + (size_t)c->ny * c->H;
@@ -389,6 +533,15 @@ void plain_init(hc_ctx* c) {
 }
 
 void plain_iter(hc_ctx* c) {
+  if (c->dim == 3) {
+    apply3_open<double, double, double>(c, c->gd, hc::CG_DUPDATE, (cx<double>*)nullptr, c->r64,
+                                        c->d64, c->G64, 1);
+    hc::z_div<double>(c->gd, hc::CD_CG, tri(c->G64, c->ns), c->d64, nullptr, c->q64, nullptr,
+                      nullptr, c->st, c->stream);
+    hc::cg_update3<double>(c->gd, c->p64, c->r64, c->d64, c->q64, c->st, c->stream);
+    c->launches += 2;
+    return;
+  }
   auto& g = c->gd;
   cx<double>* Gx = c->G64;
   cx<double>* Gy = c->G64 + (size_t)c->ny * c->H;
@@ -404,6 +557,23 @@ void plain_iter(hc_ctx* c) {
 
 // FP64 residual S - A p64 (after p64 += delta) and inner-CG initialisation.
 void refined_resid(hc_ctx* c) {
+  if (c->dim == 3) {
+    if (c->df) {
+      auto* G = reinterpret_cast<cx<df64>*>(c->G64);
+      apply3_open<df64, df64, float>(c, c->gq, hc::CG_ADDDELTA, reinterpret_cast<cx<df64>*>(c->p64),
+                                     nullptr, nullptr, G, 0);
+      hc::z_div<df64>(c->gq, hc::CD_RESID_REFINE, tri(G, c->ns), nullptr,
+                      reinterpret_cast<const cx<df64>*>(c->b64), reinterpret_cast<cx<df64>*>(c->r64),
+                      c->r32, c->x32, c->st, c->stream);
+    } else {
+      apply3_open<double, double, float>(c, c->gd, hc::CG_ADDDELTA, c->p64, nullptr, nullptr,
+                                         c->G64, 0);
+      hc::z_div<double>(c->gd, hc::CD_RESID_REFINE, tri(c->G64, c->ns), nullptr, c->b64, c->r64,
+                        c->r32, c->x32, c->st, c->stream);
+    }
+    c->launches += 1;
+    return;
+  }
   if (c->df) {
     auto& q = c->gq;
     cx<df64>* Gx = reinterpret_cast<cx<df64>*>(c->G64);
@@ -431,6 +601,15 @@ void refined_resid(hc_ctx* c) {
 }
 
 void refined_iter(hc_ctx* c) {
+  if (c->dim == 3) {
+    apply3_open<float, float, float>(c, c->gf, hc::CG_DUPDATE, (cx<float>*)nullptr, c->r32, c->d32,
+                                     c->G32, 1);
+    hc::z_div<float>(c->gf, hc::CD_CG, tri(c->G32, c->ns), c->d32, nullptr, c->q32, nullptr,
+                     nullptr, c->st, c->stream);
+    hc::cg_update3<float>(c->gf, c->x32, c->r32, c->d32, c->q32, c->st, c->stream);
+    c->launches += 2;
+    return;
+  }
   auto& g = c->gf;
   cx<float>* Gx = c->G32;
   cx<float>* Gy = c->G32 + (size_t)c->ny * c->H;
@@ -468,7 +647,54 @@ void split_step_t(hc_ctx* c, hc::Geo<T>& g, cx<T>* G) {
   c->launches += 4;
 }
 
+// A f in 3D (forward transform with projection, apply, inverse transform).
+template <typename T, typename Tm>
+void apply_operator3(hc_ctx* c, hc::Geo<T>& g, hc::Geo<T>& rows, T* phys, cx<T>* G, cx<T>* dvec,
+                     cx<T>* qvec) {
+  auto Gt = tri(G, c->ns);
+  hc::row_r2c<T>(rows, phys, nullptr, G, nullptr, c->stream);
+  hc::axis_fft<T>(g, 1, -1, 1, Gt, Gt, (T)1, c->stream);
+  hc::z_fwd_project<T>(g, G, dvec, nullptr, c->stream);
+  apply3_open<T, T, Tm>(c, g, hc::CG_PLAIN, dvec, nullptr, nullptr, G, 0);
+  hc::z_div<T>(g, hc::CD_PLAIN, Gt, nullptr, nullptr, qvec, nullptr, nullptr, nullptr, c->stream);
+  hc::axis_fft<T>(g, 2, +1, 1, tri(qvec, c->ns), Gt, (T)(1.0 / (double)c->n), c->stream);
+  hc::axis_fft<T>(g, 1, +1, 1, Gt, Gt, (T)1, c->stream);
+  hc::row_c2r<T>(rows, G, nullptr, phys, nullptr, nullptr, 0, c->stream);
+  c->launches += 7;
+}
+
+// 3D: gradient of the new p (z pass from the FP64 spectrum, inverse y), the
+// row pass (C2R, activation, relaxation, diffusion along x, back to physical
+// m), diffusion along y, diffusion along z with sum |m|^2.
+template <typename T>
+void split_step3(hc_ctx* c, hc::Geo<T>& g, cx<T>* G) {
+  auto Gt = tri(G, c->ns);
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->df)
+      hc::z_grad<float, df64>(g, hc::CG_PLAIN, reinterpret_cast<cx<df64>*>(c->p64), nullptr,
+                              nullptr, nullptr, Gt, c->st, 0, c->stream);
+    else
+      hc::z_grad<float, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gt, c->st, 0,
+                                c->stream);
+  } else {
+    hc::z_grad<T, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gt, c->st, 0,
+                          c->stream);
+  }
+  hc::axis_fft<T>(g, 1, +1, 3, Gt, Gt, (T)1, c->stream);
+  hc::row_split3<T>(g, Gt, mtri_w<T>(c), split_coef(c->prm), c->st, c->stream);
+  hc::heat_axis<T>(g, 1, mtri_w<T>(c), c->st, c->stream);
+  hc::heat_axis<T>(g, 2, mtri_w<T>(c), c->st, c->stream);
+  c->launches += 5;
+}
+
 void split_step(hc_ctx* c) {
+  if (c->dim == 3) {
+    if (c->refined)
+      split_step3<float>(c, c->gf, c->G32);
+    else
+      split_step3<double>(c, c->gd, c->G64);
+    return;
+  }
   if (c->refined)
     split_step_t<float>(c, c->gf, c->G32);
   else
@@ -613,6 +839,15 @@ void abort_capture(cudaStream_t s) {
   cudaGetLastError();
 }
 
+// Kernels of one step's graph: fixed nodes (step_begin, [plain: initial
+// residual], split step, step_end), one CG iteration, one refinement residual.
+void set_node_counts(hc_ctx* c) {
+  const int split = c->dim == 3 ? 5 : 4, resid = c->dim == 3 ? 5 : 3;
+  c->graph_nodes_fixed = 1 + (c->refined ? 0 : resid) + split + 1;
+  c->graph_nodes_body = c->dim == 3 ? 6 : 4;
+  c->graph_nodes_outer = resid;
+}
+
 // Device handles the kernels drive: the context's own graph or a batch graph.
 int use_handles(hc_ctx* c, cudaGraphConditionalHandle hin, cudaGraphConditionalHandle hout) {
   unsigned long long v[2] = {hin, hout};
@@ -649,9 +884,7 @@ int build_graph(hc_ctx* c) {
   cudaError_t e = cudaGraphInstantiate(&c->gexec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __LINE__);
-  c->graph_nodes_fixed = c->refined ? 1 + 4 + 1 : 1 + 3 + 4 + 1;
-  c->graph_nodes_body = 4;
-  c->graph_nodes_outer = 3;
+  set_node_counts(c);
   c->h_own[0] = hin;
   c->h_own[1] = hout;
   c->graph_ready = true;
@@ -711,10 +944,13 @@ int hc_workspace_size(const hc_grid* grid, const hc_params* params, size_t* byte
   hc_ctx tmp;
   std::memset(&tmp, 0, sizeof(tmp));
   tmp.grid = *grid;
+  tmp.dim = grid->dim;
   tmp.nx = grid->n[0];
   tmp.ny = grid->n[1];
+  tmp.nz = grid->dim == 3 ? grid->n[2] : 1;
   tmp.H = tmp.nx / 2;
-  tmp.n = (size_t)tmp.nx * tmp.ny;
+  tmp.n = (size_t)tmp.nx * tmp.ny * tmp.nz;
+  tmp.ns = (size_t)tmp.nz * tmp.ny * tmp.H;
   tmp.refined = params->precision != HC_FP64_PLAIN;
   Layout L;
   layout(&tmp, L);
@@ -737,15 +973,16 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   c->grid = *grid;
   c->prm = *params;
   apply_defaults(c->prm);
+  c->dim = grid->dim;
   c->nx = grid->n[0];
   c->ny = grid->n[1];
+  c->nz = grid->dim == 3 ? grid->n[2] : 1;
   c->H = c->nx / 2;
-  c->n = (size_t)c->nx * c->ny;
+  c->n = (size_t)c->nx * c->ny * c->nz;
+  c->ns = (size_t)c->nz * c->ny * c->H;
   c->refined = params->precision != HC_FP64_PLAIN;
   c->df = params->precision == HC_FP32_REFINED_DF;
-  c->graph_nodes_fixed = c->refined ? 1 + 4 + 1 : 1 + 3 + 4 + 1;
-  c->graph_nodes_body = 4;
-  c->graph_nodes_outer = 3;
+  set_node_counts(c);
   c->stream = (cudaStream_t)params->stream;
   c->mean_r = 1.0;
   if (workspace) {
@@ -777,9 +1014,19 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   fill_geo<df64>(c, c->gq, c->twx_q, c->twy_q, c->kxd_q, c->kyd_q, nullptr, nullptr);
   c->gq.tc = c->gd.tc;
   c->gq.ltc = c->gd.ltc;
+  if (c->dim == 3) {
+    fill_geo3<float>(c, c->gf, c->rowf, c->twz_f, c->kzd_f, c->hz_f);
+    fill_geo3<double>(c, c->gd, c->rowd, c->twz_d, c->kzd_d, c->hz_d);
+    fill_geo3<df64>(c, c->gq, c->rowq, c->twz_q, c->kzd_q, nullptr);
+  }
   hc::set_smem_limits_f32();
   hc::set_smem_limits_f64();
   hc::set_smem_limits_df();
+  if (c->dim == 3) {
+    hc::set_smem_limits_3d_f32();
+    hc::set_smem_limits_3d_f64();
+    hc::set_smem_limits_3d_df();
+  }
   int rc = HC_OK;
   if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess) rc = HC_ECUDA;
   if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HC_ECUDA;
@@ -847,8 +1094,30 @@ int hc_set_r(hc_ctx* c, const double* r, size_t count) {
   return HC_OK;
 }
 
+// Forward 3D transform of the FP64 field in stage -> projected FP64 spectrum.
+static int forward64_3d(hc_ctx* c, cx<double>* out, hc::SolveState* norm_into) {
+  if (c->df) {
+    df64* phys = reinterpret_cast<df64*>(c->stage + c->n);
+    cx<df64>* rows = reinterpret_cast<cx<df64>*>(c->G64);
+    hc::convert<df64, double>(c->stage, phys, c->n, c->stream);
+    hc::row_r2c<df64>(c->rowq, phys, nullptr, rows, nullptr, c->stream);
+    hc::axis_fft<df64>(c->gq, 1, -1, 1, tri(rows, c->ns), tri(rows, c->ns), df64(1.0), c->stream);
+    hc::z_fwd_project<df64>(c->gq, rows, reinterpret_cast<cx<df64>*>(out), norm_into, c->stream);
+    c->launches += 4;
+  } else {
+    cx<double>* rows = c->G64;
+    hc::row_r2c<double>(c->rowd, c->stage, nullptr, rows, nullptr, c->stream);
+    hc::axis_fft<double>(c->gd, 1, -1, 1, tri(rows, c->ns), tri(rows, c->ns), 1.0, c->stream);
+    hc::z_fwd_project<double>(c->gd, rows, out, norm_into, c->stream);
+    c->launches += 3;
+  }
+  CU(cudaGetLastError());
+  return HC_OK;
+}
+
 // Forward 2D transform of the FP64 field in stage -> projected FP64 spectrum.
 static int forward64(hc_ctx* c, cx<double>* out, hc::SolveState* norm_into) {
+  if (c->dim == 3) return forward64_3d(c, out, norm_into);
   if (c->df) {
     df64* phys = reinterpret_cast<df64*>(c->stage + c->n);
     cx<df64>* rows = reinterpret_cast<cx<df64>*>(c->G64);
@@ -889,8 +1158,24 @@ int hc_set_p(hc_ctx* c, const double* p, size_t count) {
 }
 
 int hc_set_m(hc_ctx* c, const double* m, size_t count) {
-  if (!c || !m || count != 2 * c->n) return HC_EINVAL;
+  if (!c || !m || count != (size_t)c->dim * c->n) return HC_EINVAL;
   CU(cudaMemcpyAsync(c->stage, m, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+  if (c->dim == 3) {
+    for (int k = 0; k < 3; ++k) {
+      if (c->refined)
+        hc::convert<float, double>(c->stage + k * c->n, (float*)c->m[k], c->n, c->stream);
+      else
+        hc::convert<double, double>(c->stage + k * c->n, (double*)c->m[k], c->n, c->stream);
+    }
+    if (c->refined)
+      hc::msum3<float>(c->gf, mtri<float>(c), c->st, c->stream);
+    else
+      hc::msum3<double>(c->gd, mtri<double>(c), c->st, c->stream);
+    c->launches += 4;
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->stream));
+    return HC_OK;
+  }
   if (c->refined) {
     hc::convert<float, double>(c->stage, (float*)c->m[0], c->n, c->stream);
     hc::convert<float, double>(c->stage + c->n, (float*)c->m[1], c->n, c->stream);
@@ -907,15 +1192,14 @@ int hc_set_m(hc_ctx* c, const double* m, size_t count) {
 }
 
 int hc_get_m(hc_ctx* c, double* out, size_t count) {
-  if (!c || !out || count != 2 * c->n) return HC_EINVAL;
-  if (c->refined) {
-    hc::convert<double, float>((const float*)c->m[0], c->stage, c->n, c->stream);
-    hc::convert<double, float>((const float*)c->m[1], c->stage + c->n, c->n, c->stream);
-  } else {
-    hc::convert<double, double>((const double*)c->m[0], c->stage, c->n, c->stream);
-    hc::convert<double, double>((const double*)c->m[1], c->stage + c->n, c->n, c->stream);
+  if (!c || !out || count != (size_t)c->dim * c->n) return HC_EINVAL;
+  for (int k = 0; k < c->dim; ++k) {
+    if (c->refined)
+      hc::convert<double, float>((const float*)c->m[k], c->stage + k * c->n, c->n, c->stream);
+    else
+      hc::convert<double, double>((const double*)c->m[k], c->stage + k * c->n, c->n, c->stream);
   }
-  c->launches += 2;
+  c->launches += c->dim;
   CU(cudaMemcpyAsync(out, c->stage, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   return HC_OK;
@@ -923,6 +1207,30 @@ int hc_get_m(hc_ctx* c, double* out, size_t count) {
 
 int hc_get_p(hc_ctx* c, double* out, size_t count) {
   if (!c || !out || count != c->n) return HC_EINVAL;
+  if (c->dim == 3) {
+    if (c->df) {
+      auto* p = reinterpret_cast<cx<df64>*>(c->p64);
+      auto* rows = reinterpret_cast<cx<df64>*>(c->G64);
+      df64* phys = reinterpret_cast<df64*>(c->stage + c->n);
+      hc::axis_fft<df64>(c->gq, 2, +1, 1, tri(p, c->ns), tri(rows, c->ns), df64(1.0 / (double)c->n),
+                         c->stream);
+      hc::axis_fft<df64>(c->gq, 1, +1, 1, tri(rows, c->ns), tri(rows, c->ns), df64(1.0), c->stream);
+      hc::row_c2r<df64>(c->rowq, rows, nullptr, phys, nullptr, nullptr, 0, c->stream);
+      hc::convert<double, df64>(phys, c->stage, c->n, c->stream);
+      c->launches += 4;
+    } else {
+      cx<double>* rows = c->G64;
+      hc::axis_fft<double>(c->gd, 2, +1, 1, tri(c->p64, c->ns), tri(rows, c->ns),
+                           1.0 / (double)c->n, c->stream);
+      hc::axis_fft<double>(c->gd, 1, +1, 1, tri(rows, c->ns), tri(rows, c->ns), 1.0, c->stream);
+      hc::row_c2r<double>(c->rowd, rows, nullptr, c->stage, nullptr, nullptr, 0, c->stream);
+      c->launches += 3;
+    }
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(out, c->stage, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return HC_OK;
+  }
   if (c->df) {
     cx<df64>* rows = reinterpret_cast<cx<df64>*>(c->G64);
     df64* phys = reinterpret_cast<df64*>(c->stage + c->n);
@@ -982,9 +1290,39 @@ int hc_step(hc_ctx* c, int nsteps, hc_step_stats* last) {
   return c->st_host->first_bad;
 }
 
-int hc_gradient(hc_ctx* c, double* out, size_t count) {
-  if (!c || !out || count != 2 * c->n) return HC_EINVAL;
+static void gradient3(hc_ctx* c) {
+  const size_t n = c->n;
   if (c->refined) {
+    auto Gt = tri(c->G32, c->ns);
+    if (c->df)
+      hc::z_grad<float, df64>(c->gf, hc::CG_PLAIN, reinterpret_cast<cx<df64>*>(c->p64), nullptr,
+                              nullptr, nullptr, Gt, c->st, 0, c->stream);
+    else
+      hc::z_grad<float, double>(c->gf, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gt, c->st,
+                                0, c->stream);
+    hc::axis_fft<float>(c->gf, 1, +1, 3, Gt, Gt, 1.0f, c->stream);
+    float* f[3] = {(float*)Gt.v[0], (float*)Gt.v[1], (float*)Gt.v[2]};
+    hc::row_c2r<float>(c->rowf, Gt.v[0], Gt.v[1], f[0], f[1], nullptr, 0, c->stream);
+    hc::row_c2r<float>(c->rowf, Gt.v[2], nullptr, f[2], nullptr, nullptr, 0, c->stream);
+    for (int k = 0; k < 3; ++k) hc::convert<double, float>(f[k], c->stage + k * n, n, c->stream);
+    c->launches += 7;
+  } else {
+    auto Gt = tri(c->G64, c->ns);
+    hc::z_grad<double, double>(c->gd, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gt, c->st,
+                               0, c->stream);
+    hc::axis_fft<double>(c->gd, 1, +1, 3, Gt, Gt, 1.0, c->stream);
+    hc::row_c2r<double>(c->rowd, Gt.v[0], Gt.v[1], c->stage, c->stage + n, nullptr, 0, c->stream);
+    hc::row_c2r<double>(c->rowd, Gt.v[2], nullptr, c->stage + 2 * n, nullptr, nullptr, 0,
+                        c->stream);
+    c->launches += 4;
+  }
+}
+
+int hc_gradient(hc_ctx* c, double* out, size_t count) {
+  if (!c || !out || count != (size_t)c->dim * c->n) return HC_EINVAL;
+  if (c->dim == 3) {
+    gradient3(c);
+  } else if (c->refined) {
     cx<float>* Gx = c->G32;
     cx<float>* Gy = c->G32 + (size_t)c->ny * c->H;
     if (c->df)
@@ -1014,7 +1352,17 @@ int hc_gradient(hc_ctx* c, double* out, size_t count) {
 int hc_apply_operator(hc_ctx* c, const double* f, double* out, size_t count) {
   if (!c || !f || !out || count != c->n) return HC_EINVAL;
   CU(cudaMemcpyAsync(c->stage, f, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
-  if (c->refined) {
+  if (c->dim == 3) {
+    if (c->refined) {
+      float* fp = reinterpret_cast<float*>(c->q32);
+      hc::convert<float, double>(c->stage, fp, c->n, c->stream);
+      apply_operator3<float, float>(c, c->gf, c->rowf, fp, c->G32, c->d32, c->r32);
+      hc::convert<double, float>(fp, c->stage, c->n, c->stream);
+      c->launches += 2;
+    } else {
+      apply_operator3<double, double>(c, c->gd, c->rowd, c->stage, c->G64, c->d64, c->q64);
+    }
+  } else if (c->refined) {
     auto& g = c->gf;
     cx<float>* Gx = c->G32;
     cx<float>* Gy = c->G32 + (size_t)c->ny * c->H;
@@ -1065,8 +1413,27 @@ int hc_split_step(hc_ctx* c) {
 int hc_spectrum(hc_ctx* c, const double* f, double* out, size_t count) {
   if (!c || !f || !out || count != c->n) return HC_EINVAL;
   CU(cudaMemcpyAsync(c->stage, f, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
-  const size_t ns = (size_t)c->ny * c->H;
-  if (c->refined) {
+  const size_t ns = c->ns;
+  if (c->dim == 3) {
+    if (c->refined) {
+      float* fp = reinterpret_cast<float*>(c->q32);
+      auto Gt = tri(c->G32, ns);
+      hc::convert<float, double>(c->stage, fp, c->n, c->stream);
+      hc::row_r2c<float>(c->rowf, fp, nullptr, c->G32, nullptr, c->stream);
+      hc::axis_fft<float>(c->gf, 1, -1, 1, Gt, Gt, 1.0f, c->stream);
+      hc::axis_fft<float>(c->gf, 2, -1, 1, Gt, tri(c->d32, ns), 1.0f, c->stream);
+      hc::convert<double, float>(reinterpret_cast<const float*>(c->d32), c->stage, 2 * ns,
+                                 c->stream);
+      c->launches += 5;
+    } else {
+      auto Gt = tri(c->G64, ns);
+      hc::row_r2c<double>(c->rowd, c->stage, nullptr, c->G64, nullptr, c->stream);
+      hc::axis_fft<double>(c->gd, 1, -1, 1, Gt, Gt, 1.0, c->stream);
+      hc::axis_fft<double>(c->gd, 2, -1, 1, Gt, tri(reinterpret_cast<cx<double>*>(c->stage), ns),
+                           1.0, c->stream);
+      c->launches += 3;
+    }
+  } else if (c->refined) {
     auto& g = c->gf;
     float* fp = reinterpret_cast<float*>(c->q32);
     hc::convert<float, double>(c->stage, fp, c->n, c->stream);
@@ -1331,7 +1698,7 @@ extern "C" {
 
 int hc_adjoint_workspace_size(const hc_ctx* c, int nsteps, int every, size_t* bytes) {
   if (!c || !bytes || nsteps < 0 || every < 1) return HC_EINVAL;
-  if (c->df) return HC_ENOTSUP;
+  if (c->df || c->dim != 2) return HC_ENOTSUP;
   if (c->refined) {
     AdjLayout<float> a;
     adj_layout<float>(c, nsteps, every, nullptr, a);
@@ -1347,7 +1714,7 @@ int hc_adjoint_workspace_size(const hc_ctx* c, int nsteps, int every, size_t* by
 int hc_adjoint(hc_ctx* c, int nsteps, int every, const double* lamT, double* dc2, double* dD2,
                double* dr, double* dS, double* dm0, void* workspace, size_t workspace_bytes) {
   if (!c || !lamT || nsteps < 0 || every < 1) return HC_EINVAL;
-  if (c->df) return HC_ENOTSUP;
+  if (c->df || c->dim != 2) return HC_ENOTSUP;
   if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return HC_EINVAL;
   size_t need = 0;
   int rc = hc_adjoint_workspace_size(c, nsteps, every, &need);
@@ -1494,6 +1861,7 @@ int hc_get_tuning(const hc_ctx* c, hc_tuning* t) {
 
 int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
   if (!c || !t) return HC_EINVAL;
+  if (c->dim != 2) return HC_ENOTSUP;  // 3D launch shapes are fixed at creation
   int dev = 0, optin = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -1558,8 +1926,139 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
   for (int k = 0; k < 8; ++k) init.ticket[k] = 0;
   CU(cudaMemcpyAsync(c->st_time, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
   hc::SolveState* ts = c->st_time;
-  const size_t ns = (size_t)c->ny * c->H;
+  const size_t ns = c->ns;
+  if (c->dim == 2 && kernel >= HC_K_CG_YPASS) return HC_EINVAL;
+  // 3D: the same roles with the 3D kernels; the SPLIT_HEAT / SPLIT_C2R slots
+  // time the y and z diffusion passes.  Scratch outputs never alias inputs
+  // that a later repetition reads.
+  auto launch3 = [&]() {
+    const hc::SplitCoef cf = split_coef(c->prm);
+    if (c->refined) {
+      auto& g = c->gf;
+      auto G = tri(c->G32, ns);
+      auto* G64 = c->G64;
+      auto mw = hc::Tri<float*>{{(float*)c->q32, (float*)c->x32, (float*)c->d32}};
+      switch (kernel) {
+        case HC_K_CG_GRAD:
+          hc::z_grad<float, float>(g, hc::CG_DUPDATE, (cx<float>*)nullptr, c->r32, c->d32, nullptr,
+                                   G, ts, 1, c->stream);
+          break;
+        case HC_K_CG_YPASS:
+          hc::axis_fft<float>(g, 1, +1, 3, G, G, 1.0f, c->stream);
+          break;
+        case HC_K_CG_APPLY:
+          hc::row_apply3<float, float>(g, G, mtri<float>(c), (const float*)c->rf, G, ts, c->stream);
+          break;
+        case HC_K_CG_DIV:
+          hc::z_div<float>(g, hc::CD_CG, G, c->d32, nullptr, c->q32, nullptr, nullptr, ts, c->stream);
+          break;
+        case HC_K_CG_UPDATE:
+          hc::cg_update3<float>(g, c->x32, c->r32, c->d32, c->q32, ts, c->stream);
+          break;
+        case HC_K_RES_GRAD:
+          if (c->df)
+            hc::z_grad<df64, df64>(c->gq, hc::CG_PLAIN, reinterpret_cast<cx<df64>*>(c->p64),
+                                   nullptr, nullptr, nullptr, tri((cx<df64>*)G64, ns), ts, 0,
+                                   c->stream);
+          else
+            hc::z_grad<double, double>(c->gd, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr,
+                                       tri(G64, ns), ts, 0, c->stream);
+          break;
+        case HC_K_RES_YPASS:
+          if (c->df)
+            hc::axis_fft<df64>(c->gq, 1, +1, 3, tri((cx<df64>*)G64, ns), tri((cx<df64>*)G64, ns),
+                               df64(1.0), c->stream);
+          else
+            hc::axis_fft<double>(c->gd, 1, +1, 3, tri(G64, ns), tri(G64, ns), 1.0, c->stream);
+          break;
+        case HC_K_RES_APPLY:
+          if (c->df)
+            hc::row_apply3<df64, float>(c->gq, tri((cx<df64>*)G64, ns), mtri<float>(c),
+                                        (const float*)c->rf, tri((cx<df64>*)G64, ns), nullptr,
+                                        c->stream);
+          else
+            hc::row_apply3<double, float>(c->gd, tri(G64, ns), mtri<float>(c), (const float*)c->rf,
+                                          tri(G64, ns), nullptr, c->stream);
+          break;
+        case HC_K_RES_DIV:
+          if (c->df)
+            hc::z_div<df64>(c->gq, hc::CD_RESID_REFINE, tri((cx<df64>*)G64, ns), nullptr,
+                            (const cx<df64>*)c->b64, (cx<df64>*)c->r64, c->d32, c->q32, ts,
+                            c->stream);
+          else
+            hc::z_div<double>(c->gd, hc::CD_RESID_REFINE, tri(G64, ns), nullptr, c->b64, c->r64,
+                              c->d32, c->q32, ts, c->stream);
+          break;
+        case HC_K_SPLIT_GRAD:
+          hc::z_grad<float, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, G, ts, 0,
+                                    c->stream);
+          break;
+        case HC_K_SPLIT_ROW:
+          hc::row_split3<float>(g, G, mw, cf, ts, c->stream);
+          break;
+        case HC_K_SPLIT_HEAT:
+          hc::heat_axis<float>(g, 1, mw, ts, c->stream);
+          break;
+        default:
+          hc::heat_axis<float>(g, 2, mw, ts, c->stream);
+          break;
+      }
+    } else {
+      auto& g = c->gd;
+      auto G = tri(c->G64, ns);
+      // scratch m: the direction/product vectors (3 * ns complex doubles >= 3n doubles? no: use
+      // stage, which holds 3n doubles)
+      auto mw = hc::Tri<double*>{{c->stage, c->stage + c->n, c->stage + 2 * c->n}};
+      switch (kernel) {
+        case HC_K_CG_GRAD:
+          hc::z_grad<double, double>(g, hc::CG_DUPDATE, (cx<double>*)nullptr, c->r64, c->d64,
+                                     nullptr, G, ts, 1, c->stream);
+          break;
+        case HC_K_CG_YPASS:
+        case HC_K_RES_YPASS:
+          hc::axis_fft<double>(g, 1, +1, 3, G, G, 1.0, c->stream);
+          break;
+        case HC_K_CG_APPLY:
+          hc::row_apply3<double, double>(g, G, mtri<double>(c), (const double*)c->rf, G, ts,
+                                         c->stream);
+          break;
+        case HC_K_CG_DIV:
+          hc::z_div<double>(g, hc::CD_CG, G, c->d64, nullptr, c->q64, nullptr, nullptr, ts,
+                            c->stream);
+          break;
+        case HC_K_CG_UPDATE:
+          hc::cg_update3<double>(g, c->b64, c->r64, c->d64, c->q64, ts, c->stream);
+          break;
+        case HC_K_RES_GRAD:
+        case HC_K_SPLIT_GRAD:
+          hc::z_grad<double, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, G, ts, 0,
+                                     c->stream);
+          break;
+        case HC_K_RES_APPLY:
+          hc::row_apply3<double, double>(g, G, mtri<double>(c), (const double*)c->rf, G, nullptr,
+                                         c->stream);
+          break;
+        case HC_K_RES_DIV:
+          hc::z_div<double>(g, hc::CD_RESID, G, nullptr, c->b64, c->q64, nullptr, nullptr, ts,
+                            c->stream);
+          break;
+        case HC_K_SPLIT_ROW:
+          hc::row_split3<double>(g, G, mw, cf, ts, c->stream);
+          break;
+        case HC_K_SPLIT_HEAT:
+          hc::heat_axis<double>(g, 1, mw, ts, c->stream);
+          break;
+        default:
+          hc::heat_axis<double>(g, 2, mw, ts, c->stream);
+          break;
+      }
+    }
+  };
   auto launch = [&]() {
+    if (c->dim == 3) {
+      launch3();
+      return;
+    }
     if (c->refined) {
       auto& g = c->gf;
       auto& gd = c->gd;

@@ -129,6 +129,20 @@ struct SolveConfig {
 // Reduction sites (ticket indices).
 enum { TK_DIV = 0, TK_UPDATE = 1, TK_RESID = 2, TK_MSUM = 3, TK_PROJ = 4 };
 
+// One batched column pass of a 3D grid: transforms of length 2^lL whose
+// consecutive elements are `stride` apart, over tiles of 2^ltc adjacent
+// columns; 2^lt tiles per plane, `nplanes` planes `pstride` apart.
+struct ColPass {
+  int lL, ltc, lt, nplanes;
+  long long stride, pstride;
+};
+
+// Three pointers passed by value (the components of a 3D vector field).
+template <typename P>
+struct Tri {
+  P v[3];
+};
+
 // Geometry and tables for one precision.
 template <typename T>
 struct Geo {
@@ -148,6 +162,14 @@ struct Geo {
   int pgrid;                 // CTAs of a persistent column pass (<= SMs, <= tiles)
   const T* x2x;              // xi_x^2 (positive Nyquist), kx = 0..H (H + 1 entries)
   const T* x2y;              // xi_y^2, ky < ny
+  // 3D grids (nz = 1 in 2D).  Spectra are [nz][ny][H] packed as in 2D; the x
+  // pass runs over the ny*nz rows, the y and z passes are the ColPasses below.
+  int nz, lnz;
+  const cx<T>* twz;          // exp(-2 pi i m / nz), m < nz
+  const T* kzd;              // first-derivative wavenumbers along z, 0 at kz = nz/2
+  const T* hz;               // heat factor exp(-D^2 xi_z^2 dt), kz < nz
+  int upc, lupc;             // row pairs per CTA of the 3D row kernels
+  ColPass py, pz;            // y pass (per z plane) and z pass (over all ny*H columns)
 };
 
 // Scalar results of the adjoint sweep (device).
@@ -251,6 +273,47 @@ template <typename T>
 void spec_accum(const Geo<T>& g, double* acc, const cx<T>* v, cudaStream_t s);
 template <typename T>
 void spec_norm2(const Geo<T>& g, const cx<T>* v, SolveState* st, cudaStream_t s);
+
+// ---- 3D (dim = 3).  Spectral vectors are [nz][ny][H]; a physical real field
+// is also handled as [nz][ny][H] complex values (pairs of adjacent x values)
+// by the y and z heat passes.  Row kernels work on pairs of rows.
+// z pass of the gradient: 3 outputs i xi_a P / n, inverse FFT along z (modes as col_grad).
+template <typename T, typename Tin>
+void z_grad(const Geo<T>& g, int mode, cx<Tin>* in, const cx<T>* rvec, cx<T>* dio,
+            const cx<float>* delta, Tri<cx<T>*> G, SolveState* st, int check_done,
+            cudaStream_t s);
+// FFT along y (axis 1) or z (axis 2) of nv fields, times `scale`; in place allowed.
+template <typename T>
+void axis_fft(const Geo<T>& g, int axis, int sign, int nv, Tri<cx<T>*> in, Tri<cx<T>*> out,
+              T scale, cudaStream_t s);
+// Forward FFT along z of one field, corner-mode projection, ||.||^2 into st->outer_b2.
+template <typename T>
+void z_fwd_project(const Geo<T>& g, const cx<T>* in, cx<T>* out, SolveState* st, cudaStream_t s);
+// z pass of the divergence: q = -i xi . FFT_z(Q) (modes as col_div).
+template <typename T>
+void z_div(const Geo<T>& g, int mode, Tri<cx<T>*> Q, const cx<T>* d, const cx<T>* b, cx<T>* out,
+           cx<float>* r32, cx<float>* delta32, SolveState* st, cudaStream_t s);
+// Row pass of the 3D apply: C2R(grad p) -> q = (m.g) m + r g -> R2C(q).
+template <typename T, typename Tm>
+void row_apply3(const Geo<T>& g, Tri<cx<T>*> G, Tri<const Tm*> m, const Tm* r, Tri<cx<T>*> Q,
+                const SolveState* st, cudaStream_t s);
+// Row pass of the 3D split step: C2R(grad p) -> activation -> relaxation ->
+// diffusion along x; m updated in place (physical).
+template <typename T>
+void row_split3(const Geo<T>& g, Tri<cx<T>*> G, Tri<T*> m, SplitCoef cf, SolveState* st,
+                cudaStream_t s);
+// Diffusion along y (axis 1) or z (axis 2) of physical m, in place; axis 2
+// also sums |m|^2 into st->msum and flags non-finite values.
+template <typename T>
+void heat_axis(const Geo<T>& g, int axis, Tri<T*> m, SolveState* st, cudaStream_t s);
+template <typename T>
+void cg_update3(const Geo<T>& g, cx<T>* x, cx<T>* r, const cx<T>* d, const cx<T>* q,
+                SolveState* st, cudaStream_t s);
+template <typename T>
+void msum3(const Geo<T>& g, Tri<const T*> m, SolveState* st, cudaStream_t s);
+void set_smem_limits_3d_f32();
+void set_smem_limits_3d_f64();
+void set_smem_limits_3d_df();
 
 // Opt every kernel of one precision in to the full shared memory per block.
 void set_smem_limits_f32();

@@ -207,3 +207,69 @@ def test_preconditioner_inverts_constant_coefficient_operator():
     C = corner_modes(g)
     for c in C:
         assert np.abs(O.precond(g, kappa, c.reshape(g.shape))).max() < 1e-14
+
+
+def manufactured_3d(n, L):
+    """3D analogue of `manufactured`: band-limited p, m (3 components), r and
+    S = -div((m m^T + r I) grad p) from eq. (1.1a), symbolically."""
+    x, y, z = sp.symbols("x y z", real=True)
+    Lx, Ly, Lz = [sp.nsimplify(v) for v in L]
+    tx, ty, tz = 2 * sp.pi * x / Lx, 2 * sp.pi * y / Ly, 2 * sp.pi * z / Lz
+    p = sp.sin(tx) * sp.cos(ty + tz) + sp.Rational(1, 3) * sp.cos(2 * tz - tx)
+    m = [sp.Rational(3, 10) + sp.Rational(1, 5) * sp.cos(tz),
+         sp.Rational(2, 5) * sp.sin(tx),
+         sp.Rational(1, 4) * sp.cos(ty)]
+    r = sp.Rational(1, 10) + sp.Rational(1, 20) * sp.sin(ty)
+    grad = [sp.diff(p, v) for v in (x, y, z)]
+    mg = sum(mi * gi for mi, gi in zip(m, grad))
+    q = [mi * mg + r * gi for mi, gi in zip(m, grad)]
+    S = -(sp.diff(q[0], x) + sp.diff(q[1], y) + sp.diff(q[2], z))
+    f = sp.lambdify((x, y, z), (p, *m, r, S), "numpy")
+    Z, Y, X = np.meshgrid(np.arange(n[2]) * L[2] / n[2], np.arange(n[1]) * L[1] / n[1],
+                          np.arange(n[0]) * L[0] / n[0], indexing="ij")
+    vals = [np.broadcast_to(np.asarray(v, dtype=float), X.shape).copy() for v in f(X, Y, Z)]
+    P, M1, M2, M3, R, S = vals
+    return P, np.stack([M1, M2, M3]), R, S
+
+
+@pytest.mark.parametrize("n,L", [((16, 16, 16), (1.0, 1.0, 1.0)), ((16, 8, 32), (1.0, 0.5, 2.0))])
+def test_operator_manufactured_solution_3d(n, L):
+    g = O.Grid(n, L)
+    P, M, R, S = manufactured_3d(n, L)
+    assert np.abs(O.apply_A(g, M, R, P) - S).max() < 1e-11 * np.abs(S).max()
+    x, st = O.pcg(g, M, R, O.project(g, S), rtol=1e-13, maxit=500)
+    assert st.rc == O.OK
+    assert np.abs(x - P).max() < 1e-10 * np.abs(P).max()
+
+
+def test_dense_3d_symmetric_psd_with_eight_null_modes():
+    """Reading R2 in 3D: with the Nyquist first-derivative multiplier zeroed,
+    N(A) is spanned by the 8 modes whose wavenumbers are all 0 or N/2."""
+    g = O.Grid((4, 4, 4), (1.0, 0.5, 2.0))
+    m = RNG.uniform(-1, 1, (3,) + g.shape)
+    r = RNG.uniform(0.1, 0.3, g.shape)
+    A = assemble(g, m, r)
+    assert np.allclose(A, A.T, atol=1e-12 * np.abs(A).max())
+    w = np.linalg.eigvalsh(0.5 * (A + A.T))
+    assert w.min() > -1e-12 * w.max()
+    assert int((w > 1e-10 * w.max()).sum()) == 64 - 8
+    k = np.arange(4)
+    for ex in (0, 1):
+        for ey in (0, 1):
+            for ez in (0, 1):
+                v = (((-1.0) ** (ex * k))[None, None, :] * ((-1.0) ** (ey * k))[None, :, None]
+                     * ((-1.0) ** (ez * k))[:, None, None]).ravel()
+                assert np.abs(A @ v).max() < 1e-12 * np.abs(A).max()
+                assert np.abs(O.project(g, v.reshape(g.shape))).max() < 1e-14
+
+
+def test_constant_coefficient_operator_closed_form_3d():
+    g = O.Grid((8, 16, 8), (1.0, 2.0, 0.5))
+    r0 = 0.2
+    Z, Y, X = np.meshgrid(np.arange(8) * 0.5 / 8, np.arange(16) * 2.0 / 16, np.arange(8) / 8,
+                          indexing="ij")
+    p = np.cos(2 * np.pi * (1 * X + 3 * Y / 2.0 + 2 * Z / 0.5))
+    lam = r0 * (2 * np.pi) ** 2 * (1 + (3 / 2.0) ** 2 + (2 / 0.5) ** 2)
+    m = np.zeros((3,) + g.shape)
+    Ap = O.apply_A(g, m, np.full(g.shape, r0), p)
+    assert np.allclose(Ap, lam * p, atol=1e-11 * lam)
