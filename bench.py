@@ -59,8 +59,27 @@ BYTES_PER_POINT = {
         "split_c2r": 32,
     },
 }
-FP64_KERNELS = {"fp32_refined": {"res_grad", "res_apply", "res_div"},
+FP64_KERNELS = {"fp32_refined": {"res_grad", "res_apply", "res_div", "res_ypass"},
                 "fp64": set(BYTES_PER_POINT["fp64"])}
+
+# The 3D kernels (d = 3, n = nx*ny*nz points), refined path, same convention.
+# The y pass runs twice per operator apply (inverse before the row pass,
+# forward after it); split_heat / split_c2r are the y / z diffusion passes.
+BYTES_PER_POINT_3D = {
+    "cg_grad": 24,     # read r, d; write d, G0, G1, G2        6 F4
+    "cg_ypass": 24,    # read G0..G2; write G0..G2             6 F4
+    "cg_apply": 40,    # read G0..G2, m0..m2, r; write Q0..Q2 10 F4
+    "cg_div": 20,      # read Q0..Q2, d; write q               5 F4
+    "cg_update": 24,   # read x, r, d, q; write x, r           6 F4
+    "res_grad": 44,    # read p64, delta; write p64, 3 grads (F8)
+    "res_ypass": 48,   # 3 F8 in, 3 F8 out
+    "res_apply": 64,   # read 3 F8 + 4 F4; write 3 F8
+    "res_div": 48,     # read 3 F8 + b64; write r64 (F8), r32, delta (F4)
+    "split_grad": 20,  # read p64 (F8); write 3 F4
+    "split_row": 36,   # read 3 grads, 3 m; write 3 m          9 F4
+    "split_heat": 24,  # y diffusion of m in place             6 F4
+    "split_c2r": 24,   # z diffusion of m in place + sum |m|^2 6 F4
+}
 
 # DRAM bytes (read + write) per launch measured by ncu for the 2048^2 refined
 # workload with the current kernels (profiles/residual_and_cg_kernels_2048.md).
@@ -96,6 +115,38 @@ def fft_flops_per_point(kernel: str, nx: int, ny: int) -> float:
         "cg_update": 10, "split_row": 2 * row1 + 30, "split_heat": 2 * col2 + 3,
         "split_c2r": row1 + 2,
     }[kernel]
+
+
+def fft_flops_per_point_3d(kernel: str, nx: int, ny: int, nz: int) -> float:
+    """As fft_flops_per_point for the 3D kernels: column passes do three
+    complex FFTs per packed column (n/2 columns of length L: 7.5 log2 L per
+    point), the row-pair passes three complex row FFTs per pair of rows in
+    each direction (15 log2 nx per point)."""
+    lx, ly, lz = math.log2(nx), math.log2(ny), math.log2(nz)
+    return {
+        "cg_grad": 7.5 * lz + 6, "res_grad": 7.5 * lz + 4, "split_grad": 7.5 * lz + 3,
+        "cg_ypass": 7.5 * ly, "res_ypass": 7.5 * ly,
+        "cg_apply": 15 * lx + 11, "res_apply": 15 * lx + 11,
+        "cg_div": 7.5 * lz + 8, "res_div": 7.5 * lz + 12, "cg_update": 10,
+        "split_row": 30 * lx + 45, "split_heat": 15 * ly + 3, "split_c2r": 15 * lz + 5,
+    }[kernel]
+
+
+def kernel_table(s, counts: dict, bytes_pp: dict, flops_pp, fp64_names: set, npts: int,
+                 reps: int, hbm_peak: float) -> dict:
+    """Per-kernel CUDA-event durations (hc_time_kernel: back-to-back launches
+    on the same data) with algorithmic GB/s and TFLOP/s and the fraction of
+    the kernel's roof: HBM for the FP32 kernels, nominal FP64 for the FP64 ones."""
+    kernels = {}
+    for name, cnt in counts.items():
+        kms = s.time_kernel(name, reps=reps)
+        gbs = bytes_pp[name] * npts / (kms / 1e3) / 1e9
+        tfl = flops_pp(name) * npts / (kms / 1e3) / 1e12
+        is64 = name in fp64_names
+        kernels[name] = {"ms": kms, "launches_per_step": cnt, "ms_per_step": kms * cnt,
+                         "alg_GBs": gbs, "alg_TFLOPs": tfl, "bound": "alu" if is64 else "hbm",
+                         "frac": (tfl / FP64_PEAK_TFLOPS) if is64 else (gbs / hbm_peak)}
+    return kernels
 
 
 def measured_peaks() -> dict:
@@ -264,6 +315,63 @@ def run_accuracy(args) -> None:
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------- 3D leg
+def run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src) -> dict:
+    """The 256^3 source/sink workload (r = 0.1, sigma 0.05 pair at
+    (0.3,0.5,0.5)/(0.7,0.5,0.5), m0 ~ U[0,0.5], c = 25, D = 0.03,
+    gamma = 0.75, dt = 5e-4), FP32 + FP64 refinement to 1e-8, graph mode."""
+    import numpy as np
+    import torch
+    w = W.source_sink_3d(args.n3d)
+    s = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp32_refined",
+                 cg_rtol=CG_RTOL_REFINED, cg_maxit=2000, use_graph=not args.host_loop,
+                 device=str(dev))
+    s.set_r(w.r)
+    s.set_source(w.S)
+    s.set_m(w.m0)
+    s.step(max(args.warmup, 3) if args.only_3d else 3)
+    K3 = args.steps if args.only_3d else max(5, args.steps // 30)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed3d")
+    e0.record(s.stream)
+    st = s.step(K3)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    npts = w.npts
+    it = st.total_cg_iters / K3
+    sw = st.total_sweeps / K3
+    counts = {"cg_grad": it, "cg_ypass": 2 * it, "cg_apply": it, "cg_div": it, "cg_update": it,
+              "res_grad": sw + 1, "res_ypass": 2 * (sw + 1), "res_apply": sw + 1,
+              "res_div": sw + 1, "split_grad": 1, "split_row": 1, "split_heat": 1,
+              "split_c2r": 1}
+    kernels = kernel_table(s, counts, BYTES_PER_POINT_3D,
+                           lambda k: fft_flops_per_point_3d(k, *w.n),
+                           FP64_KERNELS["fp32_refined"], npts, max(3, args.kernel_reps // 3),
+                           hbm_peak)
+    s.close()
+    # dominant FP32 kernel of the CG iteration against HBM
+    fp32 = [k for k in kernels if kernels[k]["bound"] == "hbm"]
+    dom = max(fp32, key=lambda k: kernels[k]["ms_per_step"])
+    dk = kernels[dom]
+    return {"value": world * npts * K3 / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms / K3,
+            "steps": K3, "grid": list(w.n),
+            "workload": "source_sink_3d_%d: r=0.1, S=+G(0.3,0.5,0.5)-G(0.7,0.5,0.5) sigma 0.05 "
+                        "minus mean, m0~U[0,0.5] seed 0, c=25 D=0.03 gamma=0.75 dt=5e-4; "
+                        "FP32 + FP64 refinement, cg_rtol 1e-8" % args.n3d,
+            "cg_iters_per_step": it, "refine_sweeps_per_step": sw,
+            "rel_residual_last_step": st.rel_residual,
+            "roofline_fp32": {"bound": "hbm", "kernel": dom, "achieved": dk["alg_GBs"],
+                              "peak": hbm_peak, "unit": "GB/s", "frac": dk["frac"],
+                              "peak_source": hbm_src,
+                              "alg_bytes": BYTES_PER_POINT_3D[dom] * npts},
+            "kernels": kernels}
+
+
 # ----------------------------------------------------------------- GB300 arm
 def run_gb300(args) -> None:
     import numpy as np
@@ -346,20 +454,10 @@ def run_gb300(args) -> None:
               "cg_update": iters_per_step, "res_grad": sweeps_per_step + 1,
               "res_apply": sweeps_per_step + 1, "res_div": sweeps_per_step + 1, "split_grad": 1,
               "split_row": 1, "split_heat": 1, "split_c2r": 1}
-    kernels = {}
-    bytes_step = 0.0
-    for name, cnt in counts.items():
-        kms = s.time_kernel(name, reps=args.kernel_reps)
-        bpp = BYTES_PER_POINT["fp32_refined"][name]
-        fpp = fft_flops_per_point(name, *w.n)
-        is64 = name in FP64_KERNELS["fp32_refined"]
-        gbs = bpp * npts / (kms / 1e3) / 1e9
-        tfl = fpp * npts / (kms / 1e3) / 1e12
-        kernels[name] = {"ms": kms, "launches_per_step": cnt, "ms_per_step": kms * cnt,
-                         "alg_GBs": gbs, "alg_TFLOPs": tfl,
-                         "bound": "alu" if is64 else "hbm",
-                         "frac": (tfl / FP64_PEAK_TFLOPS) if is64 else (gbs / hbm_peak)}
-        bytes_step += bpp * npts * cnt
+    kernels = kernel_table(s, counts, BYTES_PER_POINT["fp32_refined"],
+                           lambda k: fft_flops_per_point(k, *w.n), FP64_KERNELS["fp32_refined"],
+                           npts, args.kernel_reps, hbm_peak)
+    bytes_step = sum(BYTES_PER_POINT["fp32_refined"][k] * npts * c for k, c in counts.items())
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     dk = kernels[dom]
     traffic = NCU_TRAFFIC_2048.get(dom) if w.n == (2048, 2048) else None
@@ -532,6 +630,11 @@ def run_gb300(args) -> None:
                             "sweep (gradients for c^2, D^2, r, S, m0)",
                 "dL_dc2": grads["dc2"], "dL_dD2": grads["dD2"]}
 
+    # ---- 3D: the 256^3 source/sink problem (d = 3), FP32 + FP64 refinement
+    three_d = None
+    if not args.no_3d:
+        three_d = run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src)
+
     # ---- plain FP64 path at equal accuracy
     fp64 = None
     if not args.no_fp64:
@@ -590,11 +693,24 @@ def run_gb300(args) -> None:
             "cg_iterations_per_s": world * iters_per_step * K / (ms_max / 1e3),
             "rel_residual_last_step": st.rel_residual,
             "fp64_plain": fp64, "refined_df": dfv, "sweep": sweep, "adjoint": adjv,
-            "kernels": kernels,
+            "three_d": three_d, "kernels": kernels,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_only_3d(args) -> None:
+    import torch
+    import workloads as W
+    import __graft_entry__
+    __graft_entry__._builder().build()
+    import paper_2606_06720_gb300 as P
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)
+    out = run_3d(P, W, args, torch.device("cuda", 0), lambda: None, lambda x: x, 1, hbm_peak,
+                 "measured" if "hbm_gbs" in peaks else "fallback")
+    print(json.dumps(out), flush=True)
 
 
 def main() -> None:
@@ -612,6 +728,10 @@ def main() -> None:
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched 48-instance sweep leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--adj-steps", type=int, default=60, help="adjoint leg: steps (C4 uses 500)")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D (256^3) leg")
+    ap.add_argument("--n3d", type=int, default=256, help="3D leg: grid points per axis")
+    ap.add_argument("--only-3d", action="store_true",
+                    help="run only the 3D leg, --steps/--warmup steps (for profiling)")
     ap.add_argument("--inner-rtol", type=float, default=0.0,
                     help="inner FP32 CG reduction factor (0: library default)")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
@@ -625,6 +745,8 @@ def main() -> None:
         ap.error("need --steps >= 1 and --warmup >= 0")
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_3d:
+        run_only_3d(args)
     elif args.accuracy:
         run_accuracy(args)
     else:
