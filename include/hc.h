@@ -49,6 +49,12 @@ extern "C" {
 #define HC_ETIMEOUT (-6)   /* a bounded device-side wait gave up */
 #define HC_ENOTSUP (-7)    /* valid request that this build does not implement */
 
+/* Why hc_run stopped (Algorithm 1's loop, Section 2.5). */
+#define HC_STOP_NONE 0      /* max_steps reached */
+#define HC_STOP_DELTA_M 1   /* Delta m <= eps */
+#define HC_STOP_ENERGY 2    /* the discrete energy did not decrease */
+#define HC_STOP_STATUS 3    /* a step failed (HC_ENONFINITE) */
+
 /* Arithmetic of the path. */
 #define HC_FP64_PLAIN 0   /* every kernel in IEEE FP64 */
 #define HC_FP32_REFINED 1 /* FFTs, operator applies and split step in FP32; pressure solve wrapped in
@@ -77,6 +83,7 @@ typedef struct {
   int max_sweeps;         /* refined mode: cap on FP64 refinement sweeps per solve (default 10 if <= 0) */
   int use_graph;          /* 1: each step runs as one CUDA graph with device-side loop control; 0: host loop */
   void* stream;           /* cudaStream_t the context launches on */
+  int diagnostics;        /* 1: every step also computes the energy and Delta m of Section 2.5 (see hc_step_stats) */
 } hc_params;
 
 typedef struct {
@@ -87,6 +94,17 @@ typedef struct {
   int status;          /* HC_OK, HC_ENOCONV or HC_ENONFINITE for that step */
   long long total_cg_iters; /* CG iterations summed over all steps of the hc_step call */
   long long total_sweeps;   /* refinement sweeps summed likewise */
+  /* With params.diagnostics (Section 2.5; discrete L2 norms with the cell volume as weight):
+   *   energy  = E_h(m) for the m the step started from, with that m's own pressure (the p the
+   *             step solved): D^2/2 ||grad m||^2 + c^2/2 ||r^(1/2) grad p||^2
+   *             + c^2/2 ||m . grad p||^2 + 1/(2 gamma) || |m|^gamma ||^2, gradients by the
+   *             spectral derivative of the scheme;
+   *   delta_m = ||m_new - m_old||_2 / (dt ||m_old||_2) of the step. */
+  double energy;
+  double delta_m;
+  int energy_valid;    /* 0 when the energy of the starting m is not known (diagnostics were off when it was made) */
+  int stop_reason;     /* hc_run: HC_STOP_*; hc_step: HC_STOP_NONE */
+  long long energy_step; /* hc_run with HC_STOP_ENERGY: 0-based index, within the call, of the step whose result did not lower the energy; else -1 */
 } hc_step_stats;
 
 /* Bytes of device workspace hc_create needs for this grid and precision. */
@@ -124,6 +142,20 @@ int hc_set_p(hc_ctx* ctx, const double* p, size_t count);
  * receives the stats of the final step.  Returns HC_OK, or the first non-OK
  * step status (HC_ENOCONV: the steps still ran; HC_ENONFINITE: stopped). */
 int hc_step(hc_ctx* ctx, int nsteps, hc_step_stats* last);
+
+/* Algorithm 1 with its stopping rules (Section 2.5): run loop bodies until
+ * Delta m <= eps (eps <= 0: never), or, when stop_on_energy is set, until the
+ * discrete energy does not decrease, or until max_steps.  Diagnostics are on
+ * for the call whatever params.diagnostics says.  The energy of a state is
+ * known once its pressure has been solved, i.e. during the next step, so an
+ * energy stop comes one step after the step that raised the energy
+ * (reported in last->energy_step).  In graph mode the loop runs as repeated
+ * launches of a step graph gated on the device (steps after a stop are
+ * skipped on the GPU); the host checks every few launches.
+ * *steps_done (may be NULL) gets the number of steps run; `last` the stats of
+ * the final step, with stop_reason.  Returns as hc_step. */
+int hc_run(hc_ctx* ctx, int max_steps, double eps, int stop_on_energy, int* steps_done,
+           hc_step_stats* last);
 
 /* Copy the current p (count = npts) or m (count = dim*npts) to host memory. */
 int hc_get_p(hc_ctx* ctx, double* out, size_t count);

@@ -334,3 +334,56 @@ def adjoint(grid: Grid, prm: Params, r, S, m0, p0, nsteps: int, lamT):
                               int(nsteps), _dp(lamT), C.byref(dc2), C.byref(dD2), _dp(dr),
                               _dp(dS), _dp(dm0)), "adjoint")
     return {"dc2": dc2.value, "dD2": dD2.value, "dr": dr, "dS": dS, "dm0": dm0}
+
+
+def delta_m(m_new, m_old, dt: float) -> float:
+    """Relative change of the conductivity per unit time (Section 2.5):
+    ||m^k - m^{k-1}||_2 / (dt ||m^{k-1}||_2), discrete L2 norms (the cell
+    volume cancels in the ratio)."""
+    m_new, m_old = _f64(m_new), _f64(m_old)
+    return float(np.sqrt(((m_new - m_old) ** 2).sum() / (m_old ** 2).sum()) / dt)
+
+
+@dataclass
+class RunResult:
+    m: np.ndarray
+    p: np.ndarray
+    steps: int
+    reason: int             # 0 max steps, 1 delta m <= eps, 2 energy not decreasing, 3 failed step
+    energies: list          # energies[k] = E_h(m^k) with its own pressure p[m^k]
+    delta_ms: list          # delta_ms[k] = Delta m of the step m^k -> m^{k+1}
+    energy_step: int = -1   # reason 2: the step whose result did not lower the energy
+
+
+def run(grid: Grid, prm: Params, r, S, m0, p0=None, max_steps: int = 1000, eps: float = 1e-4,
+        stop_on_energy: bool = True) -> RunResult:
+    """Algorithm 1's while loop with the two stopping rules of Section 2.5:
+    loop bodies continue while Delta m > eps (eps <= 0: never stop on it) and
+    the discrete energy decreases, at most max_steps of them.
+
+    The energy is read as a function of m alone, E_h(m) with the pressure
+    that solves eq. (1.1a) for that m.  The loop body from m^k solves exactly
+    that pressure, so E_h(m^k) becomes known in step k (0-based), and the
+    energy rule E_h(m^k) >= E_h(m^{k-1}) is applied after step k; it then
+    names step k-1 (the one that produced m^k) in energy_step.  The Delta m
+    rule is applied first.  Returns the state after the last step run."""
+    m = _f64(m0).reshape((grid.dim,) + grid.shape).copy()
+    p = np.zeros(grid.shape) if p0 is None else _f64(p0).reshape(grid.shape).copy()
+    energies, dms = [], []
+    reason, energy_step, steps = 0, -1, 0
+    for k in range(max_steps):
+        m_new, p, st = step(grid, prm, r, S, m, p)  # p = p[m^k]
+        steps = k + 1
+        if st.rc not in (OK, ENOCONV) or not np.isfinite(m_new).all():
+            m, reason = m_new, 3
+            break
+        energies.append(energy(grid, prm, r, m, p))
+        dms.append(delta_m(m_new, m, prm.dt))
+        m = m_new
+        if eps > 0 and dms[-1] <= eps:
+            reason = 1
+            break
+        if stop_on_energy and len(energies) >= 2 and not energies[-1] < energies[-2]:
+            reason, energy_step = 2, k - 1
+            break
+    return RunResult(m, p, steps, reason, energies, dms, energy_step)

@@ -20,6 +20,7 @@ _LIBNAME = os.path.join(HERE, "libhc_gb300.so")
 HC_OK, HC_EINVAL, HC_ENOMEM, HC_ECUDA = 0, -1, -2, -3
 HC_ENOCONV, HC_ENONFINITE, HC_ETIMEOUT, HC_ENOTSUP = -4, -5, -6, -7
 HC_FP64_PLAIN, HC_FP32_REFINED, HC_FP32_REFINED_DF = 0, 1, 2
+HC_STOP_NONE, HC_STOP_DELTA_M, HC_STOP_ENERGY, HC_STOP_STATUS = 0, 1, 2, 3
 
 
 class HuCaiError(RuntimeError):
@@ -39,7 +40,7 @@ class hc_params(C.Structure):
     _fields_ = [("c", C.c_double), ("D", C.c_double), ("gamma", C.c_double), ("dt", C.c_double),
                 ("cg_rtol", C.c_double), ("cg_maxit", C.c_int), ("precision", C.c_int),
                 ("kappa", C.c_double), ("inner_rtol", C.c_double), ("max_sweeps", C.c_int),
-                ("use_graph", C.c_int), ("stream", C.c_void_p)]
+                ("use_graph", C.c_int), ("stream", C.c_void_p), ("diagnostics", C.c_int)]
 
 
 class hc_tuning(C.Structure):
@@ -49,7 +50,8 @@ class hc_tuning(C.Structure):
 class hc_step_stats(C.Structure):
     _fields_ = [("cg_iters", C.c_int), ("refine_sweeps", C.c_int), ("rel_residual", C.c_double),
                 ("kappa", C.c_double), ("status", C.c_int), ("total_cg_iters", C.c_longlong),
-                ("total_sweeps", C.c_longlong)]
+                ("total_sweeps", C.c_longlong), ("energy", C.c_double), ("delta_m", C.c_double),
+                ("energy_valid", C.c_int), ("stop_reason", C.c_int), ("energy_step", C.c_longlong)]
 
 
 def library_path() -> str:
@@ -73,6 +75,8 @@ def _load() -> C.CDLL:
         "hc_set_m": ([P, dp, C.c_size_t], C.c_int),
         "hc_set_p": ([P, dp, C.c_size_t], C.c_int),
         "hc_step": ([P, C.c_int, C.POINTER(hc_step_stats)], C.c_int),
+        "hc_run": ([P, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(hc_step_stats)],
+                   C.c_int),
         "hc_get_p": ([P, dp, C.c_size_t], C.c_int),
         "hc_get_m": ([P, dp, C.c_size_t], C.c_int),
         "hc_gradient": ([P, dp, C.c_size_t], C.c_int),
@@ -111,6 +115,7 @@ hc_set_source = lib.hc_set_source
 hc_set_m = lib.hc_set_m
 hc_set_p = lib.hc_set_p
 hc_step = lib.hc_step
+hc_run = lib.hc_run
 hc_get_p = lib.hc_get_p
 hc_get_m = lib.hc_get_m
 hc_gradient = lib.hc_gradient
@@ -154,6 +159,18 @@ class StepStats:
     rc: int
     total_cg_iters: int = 0
     total_sweeps: int = 0
+    energy: float = 0.0          # E_h of the step's starting m (diagnostics on, energy_valid)
+    delta_m: float = 0.0         # Delta m of the step (diagnostics on)
+    energy_valid: int = 0
+    stop_reason: int = HC_STOP_NONE
+    energy_step: int = -1
+    steps: int = 0               # Solver.run: steps executed
+
+
+def _stats(st, rc: int, steps: int = 0) -> StepStats:
+    return StepStats(st.cg_iters, st.refine_sweeps, st.rel_residual, st.kappa, st.status, rc,
+                     st.total_cg_iters, st.total_sweeps, st.energy, st.delta_m, st.energy_valid,
+                     st.stop_reason, st.energy_step, steps)
 
 
 def _host_f64(a, count: int, writable: bool = False):
@@ -190,7 +207,8 @@ class Solver:
     def __init__(self, n, L=None, *, c: float, D: float, gamma: float, dt: float,
                  precision: str = "fp32_refined", cg_rtol: float = 1e-8, cg_maxit: int = 1000,
                  kappa: float = 0.0, inner_rtol: float = 1e-4, max_sweeps: int = 10,
-                 use_graph: bool = True, device: str = "cuda:0", stream=None):
+                 use_graph: bool = True, device: str = "cuda:0", stream=None,
+                 diagnostics: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -212,7 +230,8 @@ class Solver:
                 "fp32_refined": HC_FP32_REFINED, "fp32_refined_df": HC_FP32_REFINED_DF}[precision]
         self.precision = precision
         self.params = hc_params(c, D, gamma, dt, cg_rtol, int(cg_maxit), prec, kappa, inner_rtol,
-                                int(max_sweeps), int(bool(use_graph)), self.stream.cuda_stream)
+                                int(max_sweeps), int(bool(use_graph)), self.stream.cuda_stream,
+                                int(bool(diagnostics)))
         nbytes = C.c_size_t()
         _check(hc_workspace_size(C.byref(self.grid), C.byref(self.params), C.byref(nbytes)),
                "hc_workspace_size")
@@ -246,7 +265,7 @@ class Solver:
     # parameters and fields ----------------------------------------------
     def set_params(self, **kw):
         for k, v in kw.items():
-            if k == "use_graph":
+            if k in ("use_graph", "diagnostics"):
                 v = int(bool(v))
             setattr(self.params, k, v)
         _check(hc_set_params(self.ctx, C.byref(self.params)), "hc_set_params")
@@ -284,8 +303,18 @@ class Solver:
         st = hc_step_stats()
         rc = hc_step(self.ctx, int(nsteps), C.byref(st))
         _check(rc, "hc_step", ok=allow)
-        return StepStats(st.cg_iters, st.refine_sweeps, st.rel_residual, st.kappa, st.status, rc,
-                         st.total_cg_iters, st.total_sweeps)
+        return _stats(st, rc)
+
+    def run(self, max_steps: int, eps: float = 1e-4, stop_on_energy: bool = True,
+            allow=(HC_OK, HC_ENOCONV)) -> StepStats:
+        """Algorithm 1's loop with its stopping rules (hc_run): until
+        Delta m <= eps, the energy stops decreasing, or max_steps."""
+        st = hc_step_stats()
+        done = C.c_int()
+        rc = hc_run(self.ctx, int(max_steps), float(eps), int(bool(stop_on_energy)),
+                    C.byref(done), C.byref(st))
+        _check(rc, "hc_run", ok=allow)
+        return _stats(st, rc, done.value)
 
     # components ----------------------------------------------------------
     def gradient(self):
@@ -377,8 +406,7 @@ class Batch:
         st = (hc_step_stats * len(self.solvers))()
         rc = hc_batch_step(self.b, int(nsteps), st)
         _check(rc, "hc_batch_step", ok=allow)
-        return [StepStats(x.cg_iters, x.refine_sweeps, x.rel_residual, x.kappa, x.status, rc,
-                          x.total_cg_iters, x.total_sweeps) for x in st]
+        return [_stats(x, rc) for x in st]
 
     def close(self):
         if getattr(self, "b", None) and self.b.value:

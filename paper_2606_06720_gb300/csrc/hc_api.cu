@@ -28,6 +28,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kChunk = 4;  // CG iterations launched between host polls (host-loop mode)
+constexpr int kRunChunk = 16;  // gated step launches between host polls (hc_run, graph mode)
 
 struct Layout {
   size_t off = 0;
@@ -116,6 +117,11 @@ struct hc_ctx {
   cudaGraphConditionalHandle h_own[2];  // handles of the context's own graph
   int batch_handles;                    // 1 while st holds a batch graph's handles
   bool graph_ready;
+  // hc_run: the step wrapped in a device-gated IF node, diagnostics on
+  cudaGraphExec_t gexec_run;
+  cudaGraphConditionalHandle h_run[3];  // inner, outer, gate
+  bool run_graph_ready;
+  int force_diag;                       // 1 while hc_run runs (diagnostics forced on)
   int graph_nodes_fixed, graph_nodes_body, graph_nodes_outer;
 };
 
@@ -467,8 +473,18 @@ void apply_defaults(hc_params& p) {
   if (p.max_sweeps <= 0) p.max_sweeps = 10;
 }
 
+bool diag_on(const hc_ctx* c) { return c->prm.diagnostics != 0 || c->force_diag != 0; }
+
 int push_config(hc_ctx* c) {
   hc::SolveConfig cfg;
+  double h = 1.0;
+  for (int a = 0; a < c->dim; ++a) h *= c->grid.L[a] / (double)c->grid.n[a];
+  cfg.e_coef[0] = h * c->prm.D * c->prm.D / 2.0;
+  cfg.e_coef[1] = h * c->prm.c * c->prm.c / 2.0;
+  cfg.e_coef[2] = c->prm.gamma != 0.0 ? h / (2.0 * c->prm.gamma) : 0.0;
+  cfg.dt = c->prm.dt;
+  cfg.dim = c->dim;
+  cfg.diag = diag_on(c) ? 1 : 0;
   cfg.outer_thresh2_rel = c->prm.cg_rtol * c->prm.cg_rtol;
   cfg.inner_rtol2 = c->prm.inner_rtol * c->prm.inner_rtol;
   cfg.user_kappa = c->prm.kappa > 0 ? c->prm.kappa : 0.0;
@@ -640,9 +656,9 @@ void split_step_t(hc_ctx* c, hc::Geo<T>& g, cx<T>* G) {
     hc::col_grad<T, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy, c->st, 0,
                             c->stream);
   }
-  hc::row_split<T>(g, Gx, Gy, (const T*)c->m[0], (const T*)c->m[1], Gx, Gy, split_coef(c->prm),
-                   c->st, c->stream);
-  hc::col_heat<T>(g, Gx, Gy, c->stream);
+  hc::row_split<T>(g, Gx, Gy, (const T*)c->m[0], (const T*)c->m[1], (const T*)c->rf, Gx, Gy,
+                   split_coef(c->prm), c->st, c->stream);
+  hc::col_heat<T>(g, Gx, Gy, c->st, c->stream);
   hc::row_c2r<T>(g, Gx, Gy, (T*)c->m[0], (T*)c->m[1], c->st, 1, c->stream);
   c->launches += 4;
 }
@@ -663,6 +679,49 @@ void apply_operator3(hc_ctx* c, hc::Geo<T>& g, hc::Geo<T>& rows, T* phys, cx<T>*
   c->launches += 7;
 }
 
+// The row view (ny*nz rows of length nx) of a 3D grid, per precision.
+template <typename T>
+hc::Geo<T>& rows_of(hc_ctx* c);
+template <>
+hc::Geo<float>& rows_of<float>(hc_ctx* c) { return c->rowf; }
+template <>
+hc::Geo<double>& rows_of<double>(hc_ctx* c) { return c->rowd; }
+
+// sum |grad m|^2 of the current m (3D): x rows, y pass, z pass with the sum.
+template <typename T>
+void gradnorm3(hc_ctx* c, hc::Geo<T>& g, cx<T>* G, int into_next) {
+  hc::Geo<T>& rows = rows_of<T>(c);
+  auto Gt = tri(G, c->ns);
+  hc::row_r2c<T>(rows, (const T*)c->m[0], (const T*)c->m[1], Gt.v[0], Gt.v[1], c->stream);
+  hc::row_r2c<T>(rows, (const T*)c->m[2], nullptr, Gt.v[2], nullptr, c->stream);
+  hc::axis_fft<T>(g, 1, -1, 3, Gt, Gt, (T)1, c->stream);
+  hc::z_gradnorm<T>(g, Gt, c->st, into_next, c->stream);
+  c->launches += 4;
+}
+
+// sum |grad m|^2 of the current m into st->gm2 (after hc_set_m).
+void gradnorm_current(hc_ctx* c) {
+  if (c->dim == 3) {
+    if (c->refined)
+      gradnorm3<float>(c, c->gf, c->G32, 0);
+    else
+      gradnorm3<double>(c, c->gd, c->G64, 0);
+    return;
+  }
+  if (c->refined) {
+    cx<float>* Gx = c->G32;
+    cx<float>* Gy = c->G32 + c->ns;
+    hc::row_r2c<float>(c->gf, (const float*)c->m[0], (const float*)c->m[1], Gx, Gy, c->stream);
+    hc::col_gradnorm<float>(c->gf, Gx, Gy, c->st, 0, c->stream);
+  } else {
+    cx<double>* Gx = c->G64;
+    cx<double>* Gy = c->G64 + c->ns;
+    hc::row_r2c<double>(c->gd, (const double*)c->m[0], (const double*)c->m[1], Gx, Gy, c->stream);
+    hc::col_gradnorm<double>(c->gd, Gx, Gy, c->st, 0, c->stream);
+  }
+  c->launches += 2;
+}
+
 // 3D: gradient of the new p (z pass from the FP64 spectrum, inverse y), the
 // row pass (C2R, activation, relaxation, diffusion along x, back to physical
 // m), diffusion along y, diffusion along z with sum |m|^2.
@@ -681,10 +740,14 @@ void split_step3(hc_ctx* c, hc::Geo<T>& g, cx<T>* G) {
                           c->stream);
   }
   hc::axis_fft<T>(g, 1, +1, 3, Gt, Gt, (T)1, c->stream);
-  hc::row_split3<T>(g, Gt, mtri_w<T>(c), split_coef(c->prm), c->st, c->stream);
-  hc::heat_axis<T>(g, 1, mtri_w<T>(c), c->st, c->stream);
-  hc::heat_axis<T>(g, 2, mtri_w<T>(c), c->st, c->stream);
+  // the new m goes to the rows of G first, so the z pass still sees m^k (Delta m)
+  hc::Tri<T*> tmp = {{reinterpret_cast<T*>(Gt.v[0]), reinterpret_cast<T*>(Gt.v[1]),
+                      reinterpret_cast<T*>(Gt.v[2])}};
+  hc::row_split3<T>(g, Gt, mtri<T>(c), (const T*)c->rf, tmp, split_coef(c->prm), c->st, c->stream);
+  hc::heat_axis<T>(g, 1, tmp, tmp, c->st, c->stream);
+  hc::heat_axis<T>(g, 2, tmp, mtri_w<T>(c), c->st, c->stream);
   c->launches += 5;
+  if (diag_on(c)) gradnorm3<T>(c, g, G, 1);
 }
 
 void split_step(hc_ctx* c) {
@@ -849,8 +912,9 @@ void set_node_counts(hc_ctx* c) {
 }
 
 // Device handles the kernels drive: the context's own graph or a batch graph.
-int use_handles(hc_ctx* c, cudaGraphConditionalHandle hin, cudaGraphConditionalHandle hout) {
-  unsigned long long v[2] = {hin, hout};
+int use_handles(hc_ctx* c, cudaGraphConditionalHandle hin, cudaGraphConditionalHandle hout,
+                cudaGraphConditionalHandle hgate = 0) {
+  unsigned long long v[3] = {hin, hout, hgate};
   CU(cudaMemcpy(&c->st->h_inner, v, sizeof(v), cudaMemcpyHostToDevice));
   return HC_OK;
 }
@@ -891,6 +955,65 @@ int build_graph(hc_ctx* c) {
   return HC_OK;
 }
 
+// hc_run's graph: a gate kernel, then IF(not halted) { the step chain }.  A
+// stopping rule sets st->halt in step_end; later launches then skip the whole
+// step on the device.
+int build_run_graph(hc_ctx* c) {
+  if (!c->cap_stream) CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  CU(cudaStreamSynchronize(c->stream));
+  cudaGraph_t graph;
+  CU(cudaGraphCreate(&graph, 0));
+  cudaStream_t keep = c->stream;
+  const long long before = c->launches;
+  c->stream = c->cap_stream;
+  cudaGraphConditionalHandle hin = 0, hout = 0, hgate = 0;
+  auto capture = [&]() -> int {
+    cudaStream_t s = c->stream;
+    CU(cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    hc::run_gate(c->st, s);
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CU(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+    std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
+    cudaGraph_t same = graph;
+    CU(cudaStreamEndCapture(s, &same));
+    CU(cudaGraphConditionalHandleCreate(&hgate, graph, 0, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hgate;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t node;
+    CU(cudaGraphAddNode(&node, graph, tail.data(), nullptr, tail.size(), &ip));
+    return build_chain(c, ip.conditional.phGraph_out[0], &hin, &hout);
+  };
+  int rc = capture();
+  c->stream = keep;
+  c->launches = before;
+  if (rc) {
+    abort_capture(c->cap_stream);
+    cudaGraphDestroy(graph);
+    return rc;
+  }
+  cudaError_t e = cudaGraphInstantiate(&c->gexec_run, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __LINE__);
+  c->h_run[0] = hin;
+  c->h_run[1] = hout;
+  c->h_run[2] = hgate;
+  c->run_graph_ready = true;
+  return HC_OK;
+}
+
+void drop_graphs(hc_ctx* c) {
+  if (c->graph_ready) cudaGraphExecDestroy(c->gexec);
+  if (c->run_graph_ready) cudaGraphExecDestroy(c->gexec_run);
+  c->graph_ready = false;
+  c->run_graph_ready = false;
+}
+
 int set_graph_mode(hc_ctx* c, int on) {
   int v = on ? 1 : 0;
   CU(cudaMemcpyAsync(&c->st->graph_mode, &v, sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -915,6 +1038,11 @@ int fill_stats(hc_ctx* c, hc_step_stats* out) {
     out->status = h.step_status;
     out->total_cg_iters = h.acc_iters;
     out->total_sweeps = h.acc_sweeps;
+    out->energy = h.energy_valid ? h.energy : 0.0;
+    out->delta_m = h.diag ? h.delta_m : 0.0;
+    out->energy_valid = h.diag ? h.energy_valid : 0;
+    out->stop_reason = h.run_mode ? h.stop_reason : HC_STOP_NONE;
+    out->energy_step = (h.run_mode && h.stop_reason == HC_STOP_ENERGY) ? h.energy_step : -1;
   }
   return HC_OK;
 }
@@ -1051,7 +1179,7 @@ void hc_destroy(hc_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  if (c->graph_ready) cudaGraphExecDestroy(c->gexec);
+  drop_graphs(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->owns_ws && c->ws) cudaFree(c->ws);
   if (c->st_host) cudaFreeHost(c->st_host);
@@ -1066,11 +1194,9 @@ int hc_set_params(hc_ctx* c, const hc_params* p) {
   c->prm = np;
   int rc = upload_heat(c);
   if (!rc) rc = push_config(c);
-  if (!rc && c->graph_ready) {
-    // split coefficients are baked into the graph's kernel parameters
-    cudaGraphExecDestroy(c->gexec);
-    c->graph_ready = false;
-  }
+  // split coefficients (and, in 3D, whether the diagnostics passes run) are
+  // baked into the graphs
+  if (!rc) drop_graphs(c);
   return rc;
 }
 
@@ -1172,6 +1298,7 @@ int hc_set_m(hc_ctx* c, const double* m, size_t count) {
     else
       hc::msum3<double>(c->gd, mtri<double>(c), c->st, c->stream);
     c->launches += 4;
+    gradnorm_current(c);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(c->stream));
     return HC_OK;
@@ -1186,6 +1313,7 @@ int hc_set_m(hc_ctx* c, const double* m, size_t count) {
     hc::msum<double>(c->gd, (const double*)c->m[0], (const double*)c->m[1], c->st, c->stream);
   }
   c->launches += 3;
+  gradnorm_current(c);
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(c->stream));
   return HC_OK;
@@ -1316,6 +1444,80 @@ static void gradient3(hc_ctx* c) {
                         c->stream);
     c->launches += 4;
   }
+}
+
+int hc_run(hc_ctx* c, int max_steps, double eps, int stop_on_energy, int* steps_done,
+           hc_step_stats* last) {
+  if (!c || max_steps < 0) return HC_EINVAL;
+  if (steps_done) *steps_done = 0;
+  const int forced = c->prm.diagnostics ? 0 : 1;
+  if (forced) {
+    // the 3D diagnostics passes are captured only when diagnostics are on
+    c->force_diag = 1;
+    if (c->run_graph_ready) {
+      cudaGraphExecDestroy(c->gexec_run);
+      c->run_graph_ready = false;
+    }
+  }
+  int rc = push_config(c);
+  if (!rc) {
+    hc::set_run(c->st, 1, eps, stop_on_energy ? 1 : 0, c->stream);
+    hc::reset_accum(c->st, c->stream);
+    c->launches += 2;
+  }
+  if (!rc && max_steps > 0) {
+    if (c->prm.use_graph) {
+      if (!c->run_graph_ready) rc = build_run_graph(c);
+      if (!rc) rc = use_handles(c, c->h_run[0], c->h_run[1], c->h_run[2]);
+      c->batch_handles = 0;
+      if (!rc) rc = set_graph_mode(c, 1);
+      int launched = 0;
+      while (!rc && launched < max_steps) {
+        const int chunk = std::min(kRunChunk, max_steps - launched);
+        for (int k = 0; k < chunk && !rc; ++k) {
+          cudaError_t e = cudaGraphLaunch(c->gexec_run, c->stream);
+          if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphLaunch", __LINE__);
+        }
+        launched += chunk;
+        if (!rc) rc = read_state(c);
+        if (!rc && c->st_host->halt) break;
+      }
+      const int rc2 = set_graph_mode(c, 0);
+      if (!rc) rc = rc2;
+      if (!rc) {
+        const hc::SolveState& h = *c->st_host;
+        c->launches += launched;  // gate kernels
+        c->launches += (long long)c->graph_nodes_fixed * h.acc_steps +
+                       (long long)c->graph_nodes_body * h.acc_iters;
+        if (c->refined) c->launches += (long long)c->graph_nodes_outer * (h.acc_sweeps + h.acc_steps);
+      }
+    } else {
+      for (int k = 0; k < max_steps && !rc; ++k) {
+        rc = step_host(c);
+        if (!rc) rc = read_state(c);
+        if (!rc && c->st_host->halt) break;
+      }
+    }
+  }
+  if (!rc) rc = read_state(c);
+  if (!rc) fill_stats(c, last);
+  if (!rc && steps_done) *steps_done = c->st_host->acc_steps;
+  const int first_bad = rc ? rc : c->st_host->first_bad;
+  // leave run mode (the stats above were taken first) and the forced diagnostics
+  hc::set_run(c->st, 0, 0.0, 0, c->stream);
+  c->launches += 1;
+  if (forced) {
+    c->force_diag = 0;
+    const int rc3 = push_config(c);
+    if (!rc) rc = rc3;
+    if (c->run_graph_ready) {
+      cudaGraphExecDestroy(c->gexec_run);
+      c->run_graph_ready = false;
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize", __LINE__);
+  return rc ? rc : first_bad;
 }
 
 int hc_gradient(hc_ctx* c, double* out, size_t count) {
@@ -1571,10 +1773,10 @@ int adj_reverse_step(hc_ctx* c, hc::Geo<T>& g, AdjLayout<T>& a, const cx<double>
   const hc::SplitCoef cf = split_coef(c->prm);
   // grad p^{k+1} (rows) and b = R(A(m^k, g)) (rows)
   hc::col_grad<T, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, A0, A1, c->st, 0, s);
-  hc::row_split<T>(g, A0, A1, mx, my, B0, B1, cf, c->st, s);
+  hc::row_split<T>(g, A0, A1, mx, my, (const T*)c->rf, B0, B1, cf, c->st, s);
   // lambda_b = H lambda (H is symmetric), as row spectra
   hc::row_r2c<T>(g, a.lam, a.lam + c->n, C0, C1, s);
-  hc::col_heat<T>(g, C0, C1, s);
+  hc::col_heat<T>(g, C0, C1, nullptr, s);
   // dL/dD^2 = <lambda_b, (-|xi|^2 dt) b>
   hc::col_lap_dot<T>(g, C0, B0, c->prm.dt, a.as, s);
   hc::col_lap_dot<T>(g, C1, B1, c->prm.dt, a.as, s);
@@ -1900,10 +2102,7 @@ int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
   c->gq.lrpc = c->gd.lrpc;
   c->gq.pipe = c->gd.pipe;
   c->gq.pgrid = c->gd.pgrid;
-  if (c->graph_ready) {  // launch shapes are baked into the graph
-    cudaGraphExecDestroy(c->gexec);
-    c->graph_ready = false;
-  }
+  drop_graphs(c);  // launch shapes are baked into the graphs
   return HC_OK;
 }
 
@@ -1994,13 +2193,13 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
                                     c->stream);
           break;
         case HC_K_SPLIT_ROW:
-          hc::row_split3<float>(g, G, mw, cf, ts, c->stream);
+          hc::row_split3<float>(g, G, mtri<float>(c), (const float*)c->rf, mw, cf, ts, c->stream);
           break;
         case HC_K_SPLIT_HEAT:
-          hc::heat_axis<float>(g, 1, mw, ts, c->stream);
+          hc::heat_axis<float>(g, 1, mw, mw, ts, c->stream);
           break;
         default:
-          hc::heat_axis<float>(g, 2, mw, ts, c->stream);
+          hc::heat_axis<float>(g, 2, mw, mw, ts, c->stream);
           break;
       }
     } else {
@@ -2043,13 +2242,14 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
                             c->stream);
           break;
         case HC_K_SPLIT_ROW:
-          hc::row_split3<double>(g, G, mw, cf, ts, c->stream);
+          hc::row_split3<double>(g, G, mtri<double>(c), (const double*)c->rf, mw, cf, ts,
+                                 c->stream);
           break;
         case HC_K_SPLIT_HEAT:
-          hc::heat_axis<double>(g, 1, mw, ts, c->stream);
+          hc::heat_axis<double>(g, 1, mw, mw, ts, c->stream);
           break;
         default:
-          hc::heat_axis<double>(g, 2, mw, ts, c->stream);
+          hc::heat_axis<double>(g, 2, mw, mw, ts, c->stream);
           break;
       }
     }
@@ -2118,11 +2318,12 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
                                         ts, 0, c->stream);
           break;
         case HC_K_SPLIT_ROW:
-          hc::row_split<float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1], c->q32, c->x32,
+          hc::row_split<float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1],
+                               (const float*)c->rf, c->q32, c->x32,
                                split_coef(c->prm), ts, c->stream);
           break;
         case HC_K_SPLIT_HEAT:
-          hc::col_heat<float>(g, Gx, Gy, c->stream);
+          hc::col_heat<float>(g, Gx, Gy, ts, c->stream);
           break;
         default:
           hc::row_c2r<float>(g, Gx, Gy, (float*)c->q32, (float*)c->x32, ts, 1, c->stream);
@@ -2166,11 +2367,12 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
                               c->stream);
           break;
         case HC_K_SPLIT_ROW:
-          hc::row_split<double>(g, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1], c->q64,
+          hc::row_split<double>(g, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1],
+                                (const double*)c->rf, c->q64,
                                 (cx<double>*)c->stage, split_coef(c->prm), ts, c->stream);
           break;
         case HC_K_SPLIT_HEAT:
-          hc::col_heat<double>(g, Gx, Gy, c->stream);
+          hc::col_heat<double>(g, Gx, Gy, ts, c->stream);
           break;
         default:
           hc::row_c2r<double>(g, Gx, Gy, sx, sy, ts, 1, c->stream);

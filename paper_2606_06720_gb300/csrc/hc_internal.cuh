@@ -111,7 +111,33 @@ struct SolveState {
   int acc_steps;             // steps completed since the last reset
   unsigned long long h_inner;  // cudaGraphConditionalHandle of the CG loop
   unsigned long long h_outer;  // cudaGraphConditionalHandle of the refinement loop
+  unsigned long long h_gate;   // cudaGraphConditionalHandle of a gated step (hc_run)
   unsigned int ticket[8];    // last-CTA tickets, one per reduction site
+  // Diagnostics of Section 2.5, accumulated by the split step when diag != 0.
+  // A step solves p[m^k] and so evaluates E_h(m^k) with its own pressure.
+  double dsum[3];            // running step: sum r|g|^2, sum (m.g)^2, sum |m|^(2 gamma); m = m^k, g = grad p[m^k]
+  double gm2;                // sum |grad m|^2 of the current m (derivative multipliers of reading R1)
+  double gm2_next;           // the same for the m the running step produces
+  double dm2;                // running step: sum |m^{k+1} - m^k|^2
+  double msum_old;           // sum |m^k|^2 at the start of the running step
+  double energy;             // E_h(m^k) of the last completed step
+  double energy_prev;        // the value before it
+  double delta_m;            // Delta m of the last completed step
+  double e_coef[3];          // h D^2 / 2, h c^2 / 2, h / (2 gamma)  (h: cell volume)
+  double dt;
+  double eps_dm;             // run mode: stop once delta_m <= eps_dm
+  int dim;
+  int diag;                  // 1: the split step accumulates the diagnostics
+  int gm2_valid;             // gm2 belongs to the current m
+  int gm2_next_valid;        // the running step computed gm2_next
+  int energy_valid;          // energy holds E_h of the last step's starting m
+  int n_energy;              // energies computed since the last run reset
+  int run_mode;              // 1: step_end applies the stopping rules of Algorithm 1
+  int stop_energy;           // run mode: also stop when the energy does not decrease
+  int halt;                  // run mode: a stopping rule fired
+  int stop_reason;           // HC_STOP_* of the rule that fired
+  int energy_step;           // run mode: steps completed when the energy increase was seen
+  int pad1_;
 };
 
 // Values the host changes between steps (tolerances, caps, r statistics).
@@ -120,14 +146,18 @@ struct SolveConfig {
   double inner_rtol2;
   double user_kappa;
   double mean_r;
+  double e_coef[3];          // energy coefficients (see SolveState)
+  double dt;
   int maxit;
   int max_sweeps;
   int graph_mode;
   int refined;
+  int dim;
+  int diag;
 };
 
 // Reduction sites (ticket indices).
-enum { TK_DIV = 0, TK_UPDATE = 1, TK_RESID = 2, TK_MSUM = 3, TK_PROJ = 4 };
+enum { TK_DIV = 0, TK_UPDATE = 1, TK_RESID = 2, TK_MSUM = 3, TK_PROJ = 4, TK_DIAG = 5, TK_GRADM = 6 };
 
 // One batched column pass of a 3D grid: transforms of length 2^lL whose
 // consecutive elements are `stride` apart, over tiles of 2^ltc adjacent
@@ -199,7 +229,8 @@ enum ColDivMode { CD_PLAIN = 0, CD_CG = 1, CD_RESID = 2, CD_RESID_REFINE = 3 };
 // Row pass, forward: physical pair (a, b) -> packed row spectra (A, B). b/B may be null.
 template <typename T>
 void row_r2c(const Geo<T>& g, const T* a, const T* b, cx<T>* A, cx<T>* B, cudaStream_t s);
-// Row pass, inverse: packed row spectra -> physical pair; optional sum(a^2+b^2) into st->msum.
+// Row pass, inverse: packed row spectra -> physical pair; optional sum(a^2+b^2) into st->msum
+// (kappa_update = 1; with st->diag also sum |new - old|^2 of a, b into st->dm2).
 template <typename T>
 void row_c2r(const Geo<T>& g, const cx<T>* A, const cx<T>* B, T* a, T* b, SolveState* st,
              int kappa_update, cudaStream_t s);
@@ -207,10 +238,11 @@ void row_c2r(const Geo<T>& g, const cx<T>* A, const cx<T>* B, T* a, T* b, SolveS
 template <typename T, typename Tm>
 void row_apply(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const Tm* mx, const Tm* my,
                const Tm* r, cx<T>* Qx, cx<T>* Qy, const SolveState* st, cudaStream_t s);
-// Row pass of the split step: C2R(grad p) -> activation -> relaxation -> R2C(m).
+// Row pass of the split step: C2R(grad p) -> activation -> relaxation -> R2C(m);
+// with st->diag the energy's pointwise sums of (m^k, grad p) into st->dsum (r read then).
 template <typename T>
 void row_split(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const T* mx, const T* my,
-               cx<T>* Mx, cx<T>* My, SplitCoef cf, SolveState* st, cudaStream_t s);
+               const T* r, cx<T>* Mx, cx<T>* My, SplitCoef cf, SolveState* st, cudaStream_t s);
 // Column pass, forward FFT along y of nv (1|2) row-transformed fields; optional
 // projection + ||.||^2 of field 0 into st->outer_b2 (project=1).
 template <typename T>
@@ -237,9 +269,15 @@ template <typename T>
 void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const cx<T>* d,
              const cx<T>* b, cx<T>* out, cx<float>* r32, cx<float>* delta32, SolveState* st,
              cudaStream_t s);
-// Column pass of the diffusion: FFT_y, times exp(-D^2 |xi|^2 dt) / n, IFFT_y, in place.
+// Column pass of the diffusion: FFT_y, times exp(-D^2 |xi|^2 dt) / n, IFFT_y, in place;
+// with st && st->diag also sum |grad m_new|^2 into st->gm2_next.
 template <typename T>
-void col_heat(const Geo<T>& g, cx<T>* Mx, cx<T>* My, cudaStream_t s);
+void col_heat(const Geo<T>& g, cx<T>* Mx, cx<T>* My, SolveState* st, cudaStream_t s);
+// sum |grad m|^2 of m given as row spectra (Mx, My), into st->gm2 (into_next = 0) or
+// st->gm2_next (1).
+template <typename T>
+void col_gradnorm(const Geo<T>& g, const cx<T>* Mx, const cx<T>* My, SolveState* st, int into_next,
+                  cudaStream_t s);
 // CG update: x += alpha d, r -= alpha q, then ||r||^2 and <r, M^-1 r> -> beta, stop test.
 template <typename T>
 void cg_update(const Geo<T>& g, cx<T>* x, cx<T>* r, const cx<T>* d, const cx<T>* q, SolveState* st,
@@ -298,14 +336,20 @@ template <typename T, typename Tm>
 void row_apply3(const Geo<T>& g, Tri<cx<T>*> G, Tri<const Tm*> m, const Tm* r, Tri<cx<T>*> Q,
                 const SolveState* st, cudaStream_t s);
 // Row pass of the 3D split step: C2R(grad p) -> activation -> relaxation ->
-// diffusion along x; m updated in place (physical).
+// diffusion along x; reads m, writes mo (physical; mo may be the rows of G).
+// With st->diag also the energy's pointwise sums (r read then).
 template <typename T>
-void row_split3(const Geo<T>& g, Tri<cx<T>*> G, Tri<T*> m, SplitCoef cf, SolveState* st,
-                cudaStream_t s);
-// Diffusion along y (axis 1) or z (axis 2) of physical m, in place; axis 2
-// also sums |m|^2 into st->msum and flags non-finite values.
+void row_split3(const Geo<T>& g, Tri<cx<T>*> G, Tri<const T*> m, const T* r, Tri<T*> mo,
+                SplitCoef cf, SolveState* st, cudaStream_t s);
+// Diffusion along y (axis 1) or z (axis 2) of physical m, from mi to mo (may
+// alias); axis 2 also sums |mo|^2 into st->msum, flags non-finite values, and
+// with st->diag sums |mo - mo_old|^2 into st->dm2 (mo holds m^k on entry).
 template <typename T>
-void heat_axis(const Geo<T>& g, int axis, Tri<T*> m, SolveState* st, cudaStream_t s);
+void heat_axis(const Geo<T>& g, int axis, Tri<T*> mi, Tri<T*> mo, SolveState* st, cudaStream_t s);
+// sum |grad m|^2 of m given as its spectrum after the x and y passes (G), via
+// the z pass; into st->gm2 or st->gm2_next.
+template <typename T>
+void z_gradnorm(const Geo<T>& g, Tri<cx<T>*> G, SolveState* st, int into_next, cudaStream_t s);
 template <typename T>
 void cg_update3(const Geo<T>& g, cx<T>* x, cx<T>* r, const cx<T>* d, const cx<T>* q,
                 SolveState* st, cudaStream_t s);
@@ -325,5 +369,9 @@ void set_config(SolveState* st, SolveConfig cfg, cudaStream_t s);
 void step_begin(SolveState* st, int npts, cudaStream_t s);
 void step_end(SolveState* st, int refined, cudaStream_t s);
 void reset_accum(SolveState* st, cudaStream_t s);
+// Run mode of Algorithm 1's loop: stopping rules on/off, thresholds; clears halt.
+void set_run(SolveState* st, int run_mode, double eps_dm, int stop_energy, cudaStream_t s);
+// Sets st->h_gate to 1 unless a stopping rule fired (the gated step of hc_run).
+void run_gate(SolveState* st, cudaStream_t s);
 
 }  // namespace hc

@@ -441,11 +441,17 @@ __global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const
   for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
   fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   const size_t ro = (size_t)y * N;
-  DotAcc<T> m2;
+  DotAcc<T> m2, d2;
   bool finite = true;
+  const bool diag = kappa_update && st->diag;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = j + s * N8;
+    if (diag) {  // Delta m: this thread reads the old values it overwrites
+      const T da = v[0][s].x - a[ro + x], db = v[0][s].y - b[ro + x];
+      d2.add_prod(da, da);
+      d2.add_prod(db, db);
+    }
     a[ro + x] = v[0][s].x;
     if (b) b[ro + x] = v[0][s].y;
     if (kappa_update) {
@@ -455,11 +461,12 @@ __global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const
     }
   }
   if (kappa_update) {
-    double acc[1] = {m2.value()};
+    double acc[2] = {m2.value(), d2.value()};
     if (!finite) st->nonfinite = 1;
-    double tot[1];
-    if (last_cta_sum<1>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
+    double tot[2];
+    if (last_cta_sum<2>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
       st->msum = tot[0];
+      if (diag) st->dm2 = tot[1];
     }
   }
 }
@@ -498,10 +505,32 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
   store_pair_r2c(v, slab, j, N, H, Qx + (size_t)y * H, Qy + (size_t)y * H);
 }
 
+// Pointwise sums of the discrete energy (Section 2.5) at one point, from m^k
+// and g = grad p[m^k]: r |g|^2, (m.g)^2, |m|^(2 gamma).
+template <typename T>
+struct EnergyAcc {
+  DotAcc<T> er, ea, em;
+  __device__ __forceinline__ void add(T r, T g2, T mg, T n2, T gamma) {
+    er.add_prod(r, g2);
+    ea.add_prod(mg, mg);
+    em.add_prod(n2 > (T)0 ? hc_pow(n2, gamma) : (T)0, (T)1);
+  }
+  // every CTA calls this (the flag is grid-uniform); totals into st->dsum
+  __device__ __forceinline__ void finish(double* partials, SolveState* st) {
+    double a[3] = {er.value(), ea.value(), em.value()}, t[3];
+    if (last_cta_sum<3>(a, partials, &st->ticket[TK_DIAG], t) && threadIdx.x == 0) {
+      st->dsum[0] = t[0];
+      st->dsum[1] = t[1];
+      st->dsum[2] = t[2];
+    }
+  }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(512) k_row_split(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
                                                    const T* __restrict__ mx,
-                                                   const T* __restrict__ my, cx<T>* Mx, cx<T>* My,
+                                                   const T* __restrict__ my,
+                                                   const T* __restrict__ rr, cx<T>* Mx, cx<T>* My,
                                                    SplitCoef cf,
                                                    SolveState* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -520,11 +549,15 @@ __global__ void __launch_bounds__(512) k_row_split(Geo<T> g, const cx<T>* Gx, co
   const size_t ro = (size_t)y * N;
   const T c2dt = (T)cf.c2dt;
   bool finite = true;
+  const bool diag = st->diag != 0;
+  EnergyAcc<T> en;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = j + s * N8;
     const T gx = v[0][s].x, gy = v[0][s].y;
     T ax = mx[ro + x], ay = my[ro + x];
+    if (diag)
+      en.add(rr[ro + x], gx * gx + gy * gy, ax * gx + ay * gy, ax * ax + ay * ay, (T)cf.gamma);
     // Activation, exact solution of dm/dt = c^2 (g g^T) m over dt written as
     // m + c^2 dt phi1(c^2 |g|^2 dt) (m.g) g with phi1(z) = expm1(z)/z: the
     // same value as eq. (m_activation_discrete) without forming exp(z) - 1.
@@ -554,6 +587,7 @@ __global__ void __launch_bounds__(512) k_row_split(Geo<T> g, const cx<T>* Gx, co
     v[0][s] = cmk<T>(ax, ay);
   }
   if (!finite) st->nonfinite = 1;
+  if (diag) en.finish(g.partials, st);
   fft_canon<-1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   store_pair_r2c(v, slab, j, N, H, Mx + (size_t)y * H, My + (size_t)y * H);
 }
@@ -774,8 +808,37 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
   }
 }
 
+// sum over one thread's spectral values of w |xi~|^2 (|v0|^2 + |v1|^2) (w the
+// Parseval weight of the packed column kx, xi~ the R1 derivative multipliers;
+// the packed column's cross terms cancel over ky).
 template <typename T>
-__global__ void __launch_bounds__(512) k_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My) {  // in place
+__device__ __forceinline__ void gradnorm_acc(const Geo<T>& g, DotAcc<T>& acc, int kx, int ky,
+                                             const cx<T>& v0, const cx<T>& v1) {
+  const T a = g.kxd[kx], b = g.kyd[ky];
+  const T wk = (kx == 0 ? (T)1 : (T)2) * (a * a + b * b);
+  acc.add_prod(wk * v0.x, v0.x);
+  acc.add_prod(wk * v0.y, v0.y);
+  acc.add_prod(wk * v1.x, v1.x);
+  acc.add_prod(wk * v1.y, v1.y);
+}
+// Grid total of a per-CTA gradient-norm sum (every CTA calls it) times scale,
+// into st->gm2 or st->gm2_next.
+__device__ __forceinline__ void gradnorm_finish(double part, double scale, double* partials,
+                                                SolveState* st, int into_next) {
+  double a[1] = {part}, t[1];
+  if (last_cta_sum<1>(a, partials, &st->ticket[TK_GRADM], t) && threadIdx.x == 0) {
+    if (into_next) {
+      st->gm2_next = t[0] * scale;
+      st->gm2_next_valid = 1;
+    } else {
+      st->gm2 = t[0] * scale;
+      st->gm2_valid = 1;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My, SolveState* st) {  // in place
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const ColIdx c = col_idx(g);
@@ -825,6 +888,12 @@ __global__ void __launch_bounds__(512) k_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My
       v[0][s] = cscale(v[0][s], h);
       v[1][s] = cscale(v[1][s], h);
     }
+  }
+  if (st && st->diag) {  // v = F(m_new) / n: sum |grad m_new|^2 = n sum w |xi~|^2 |v|^2
+    DotAcc<T> ga;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) gradnorm_acc(g, ga, c.kx, c.j + s * c.NY8, v[0][s], v[1][s]);
+    gradnorm_finish(ga.value(), (double)g.nx * (double)ny, g.partials, st, 1);
   }
   fft_canon<+1, 2>(v, sl, g.tc, c.j, g.lny, g.twy);
 #pragma unroll
@@ -1116,12 +1185,14 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) kp_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My) {
+__global__ void __launch_bounds__(512) kp_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My, SolveState* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const int H = g.H, ny = g.ny, se = slab_elems(g), ntiles = g.H >> g.ltc;
   const int b = threadIdx.x & (g.tc - 1), j = threadIdx.x >> g.ltc, NY8 = 1 << (g.lny - 3);
   const T invn = (T)(1.0 / ((double)g.nx * (double)ny));
+  const bool diag = st && st->diag;
+  DotAcc<T> ga;
   int half = 0;
   int tile = blockIdx.x;
   if (tile < ntiles) stage_cols<T, 2>(g, Mx, My, sm, se, tile << g.ltc);
@@ -1176,6 +1247,10 @@ __global__ void __launch_bounds__(512) kp_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* M
         v[1][s] = cscale(v[1][s], h);
       }
     }
+    if (diag) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) gradnorm_acc(g, ga, kx, j + s * NY8, v[0][s], v[1][s]);
+    }
     fft_canon<+1, 2>(v, sl, g.tc, j, g.lny, g.twy);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
@@ -1187,6 +1262,31 @@ __global__ void __launch_bounds__(512) kp_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* M
     half ^= 1;
   }
   cp_async_wait_all();
+  if (diag) gradnorm_finish(ga.value(), (double)g.nx * (double)ny, g.partials, st, 1);
+}
+
+// sum |grad m|^2 from the row spectra of m (forward FFT_y of two fields, no store).
+template <typename T>
+__global__ void __launch_bounds__(512) k_col_gradnorm(Geo<T> g, const cx<T>* __restrict__ Mx,
+                                                      const cx<T>* __restrict__ My, SolveState* st,
+                                                      int into_next) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const ColIdx c = col_idx(g);
+  const int se = slab_elems(g);
+  cx<T>* const sl[2] = {sm + c.b, sm + se + c.b};
+  cx<T> v[2][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const size_t idx = (size_t)(c.j + s * c.NY8) * g.H + c.kx;
+    v[0][s] = Mx[idx];
+    v[1][s] = My[idx];
+  }
+  fft_canon<-1, 2>(v, sl, g.tc, c.j, g.lny, g.twy);
+  DotAcc<T> ga;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) gradnorm_acc(g, ga, c.kx, c.j + s * c.NY8, v[0][s], v[1][s]);
+  gradnorm_finish(ga.value(), 1.0 / ((double)g.nx * (double)g.ny), g.partials, st, into_next);
 }
 
 // ------------------------------------------------------------------ CG update
@@ -1538,9 +1638,9 @@ void row_apply(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const Tm* mx, 
 }
 template <typename T>
 void row_split(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const T* mx, const T* my,
-               cx<T>* Mx, cx<T>* My, SplitCoef cf, SolveState* st, cudaStream_t s) {
-  k_row_split<T><<<g.ny >> g.lrpc, row_threads(g), row_smem(g), s>>>(g, Gx, Gy, mx, my, Mx, My, cf,
-                                                                     st);
+               const T* r, cx<T>* Mx, cx<T>* My, SplitCoef cf, SolveState* st, cudaStream_t s) {
+  k_row_split<T><<<g.ny >> g.lrpc, row_threads(g), row_smem(g), s>>>(g, Gx, Gy, mx, my, r, Mx, My,
+                                                                     cf, st);
 }
 template <typename T>
 void col_fwd(const Geo<T>& g, const cx<T>* in0, const cx<T>* in1, cx<T>* out0, cx<T>* out1, int nv,
@@ -1629,12 +1729,17 @@ void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const 
   }
 }
 template <typename T>
-void col_heat(const Geo<T>& g, cx<T>* Mx, cx<T>* My, cudaStream_t s) {
+void col_heat(const Geo<T>& g, cx<T>* Mx, cx<T>* My, SolveState* st, cudaStream_t s) {
   if (g.pipe) {
-    kp_col_heat<T><<<g.pgrid, col_threads(g), pipe_smem(g), s>>>(g, Mx, My);
+    kp_col_heat<T><<<g.pgrid, col_threads(g), pipe_smem(g), s>>>(g, Mx, My, st);
     return;
   }
-  k_col_heat<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 2), s>>>(g, Mx, My);
+  k_col_heat<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 2), s>>>(g, Mx, My, st);
+}
+template <typename T>
+void col_gradnorm(const Geo<T>& g, const cx<T>* Mx, const cx<T>* My, SolveState* st, int into_next,
+                  cudaStream_t s) {
+  k_col_gradnorm<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 2), s>>>(g, Mx, My, st, into_next);
 }
 template <typename T>
 void cg_update(const Geo<T>& g, cx<T>* x, cx<T>* r, const cx<T>* d, const cx<T>* q, SolveState* st,
@@ -1701,6 +1806,7 @@ void set_smem_limits_t() {
   allow_smem(k_col_fwd<T, 2>);
   allow_smem(k_col_inv<T>);
   allow_smem(k_col_heat<T>);
+  allow_smem(k_col_gradnorm<T>);
   allow_smem(k_col_div<T, CD_PLAIN>);
   allow_smem(k_col_div<T, CD_CG>);
   allow_smem(k_col_div<T, CD_RESID>);

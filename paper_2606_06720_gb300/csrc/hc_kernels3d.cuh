@@ -422,9 +422,12 @@ __device__ __forceinline__ void act_relax3(T& ax, T& ay, T& az, T gx, T gy, T gz
   }
 }
 
+// mo may alias the rows of G: every unit reads its two rows of G into
+// registers before it writes the same rows of mo.
 template <typename T>
-__global__ void __launch_bounds__(256) k3_row_split(Geo<T> g, Tri<cx<T>*> G, Tri<T*> m, SplitCoef cf,
-                                                    SolveState* st) {
+__global__ void __launch_bounds__(256) k3_row_split(Geo<T> g, Tri<cx<T>*> G, Tri<const T*> m,
+                                                    const T* __restrict__ rr, Tri<T*> mo,
+                                                    SplitCoef cf, SolveState* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const RIdx3 r = ridx3(g);
@@ -435,12 +438,22 @@ __global__ void __launch_bounds__(256) k3_row_split(Geo<T> g, Tri<cx<T>*> G, Tri
   fft_canon<+1, 3, true>(v, sl, 1, r.j, g.lnx, g.twx);
   const size_t o0 = r.y0 * N, o1 = r.y1 * N;
   bool finite = true;
+  const bool diag = st->diag != 0;
+  EnergyAcc<T> en;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = r.j + s * r.N8;
     T ax = m.v[0][o0 + x], ay = m.v[1][o0 + x], az = m.v[2][o0 + x];
-    act_relax3(ax, ay, az, v[0][s].x, v[0][s].y, v[2][s].x, cf);
     T bx = m.v[0][o1 + x], by = m.v[1][o1 + x], bz = m.v[2][o1 + x];
+    if (diag) {
+      const T g0x = v[0][s].x, g0y = v[0][s].y, g0z = v[2][s].x;
+      const T g1x = v[1][s].x, g1y = v[1][s].y, g1z = v[2][s].y;
+      en.add(rr[o0 + x], g0x * g0x + g0y * g0y + g0z * g0z, ax * g0x + ay * g0y + az * g0z,
+             ax * ax + ay * ay + az * az, (T)cf.gamma);
+      en.add(rr[o1 + x], g1x * g1x + g1y * g1y + g1z * g1z, bx * g1x + by * g1y + bz * g1z,
+             bx * bx + by * by + bz * bz, (T)cf.gamma);
+    }
+    act_relax3(ax, ay, az, v[0][s].x, v[0][s].y, v[2][s].x, cf);
     act_relax3(bx, by, bz, v[1][s].x, v[1][s].y, v[2][s].y, cf);
     finite = finite && hc_finite(ax) && hc_finite(ay) && hc_finite(az) && hc_finite(bx) &&
              hc_finite(by) && hc_finite(bz);
@@ -449,6 +462,7 @@ __global__ void __launch_bounds__(256) k3_row_split(Geo<T> g, Tri<cx<T>*> G, Tri
     v[2][s] = cmk<T>(az, bz);
   }
   if (!finite) st->nonfinite = 1;
+  if (diag) en.finish(g.partials, st);
   // diffusion along x: a real, even multiplier on complex rows
   fft_canon<-1, 3, true>(v, sl, 1, r.j, g.lnx, g.twx);
   const T invN = (T)(1.0 / (double)N);
@@ -463,18 +477,19 @@ __global__ void __launch_bounds__(256) k3_row_split(Geo<T> g, Tri<cx<T>*> G, Tri
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = r.j + s * r.N8;
-    m.v[0][o0 + x] = v[0][s].x;
-    m.v[1][o0 + x] = v[0][s].y;
-    m.v[2][o0 + x] = v[2][s].x;
-    m.v[0][o1 + x] = v[1][s].x;
-    m.v[1][o1 + x] = v[1][s].y;
-    m.v[2][o1 + x] = v[2][s].y;
+    mo.v[0][o0 + x] = v[0][s].x;
+    mo.v[1][o0 + x] = v[0][s].y;
+    mo.v[2][o0 + x] = v[2][s].x;
+    mo.v[0][o1 + x] = v[1][s].x;
+    mo.v[1][o1 + x] = v[1][s].y;
+    mo.v[2][o1 + x] = v[2][s].y;
   }
 }
 
 // ------------------------------------------------------------------ heat along y or z
 template <typename T>
-__global__ void __launch_bounds__(256) k3_heat(Geo<T> g, int axis, Tri<cx<T>*> M, SolveState* st) {
+__global__ void __launch_bounds__(256) k3_heat(Geo<T> g, int axis, Tri<cx<T>*> M, Tri<cx<T>*> Mo,
+                                               SolveState* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const ColPass& p = axis == 1 ? g.py : g.pz;
@@ -499,14 +514,21 @@ __global__ void __launch_bounds__(256) k3_heat(Geo<T> g, int axis, Tri<cx<T>*> M
     for (int q = 0; q < 3; ++q) v[q][s] = cscale(v[q][s], f);
   }
   fft_canon<+1, 3>(v, sl, 1 << p.ltc, c.j, p.lL, tw);
-  DotAcc<T> m2;
+  DotAcc<T> m2, d2;
   bool finite = true;
+  const bool dm = axis == 2 && st->diag;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const size_t idx = c.base + (size_t)(c.j + s * c.L8) * (size_t)p.stride;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      M.v[q][idx] = v[q][s];
+      if (dm) {  // Mo still holds m^k here: this thread overwrites exactly what it reads
+        const cx<T> o = Mo.v[q][idx];
+        const T dx = v[q][s].x - o.x, dy = v[q][s].y - o.y;
+        d2.add_prod(dx, dx);
+        d2.add_prod(dy, dy);
+      }
+      Mo.v[q][idx] = v[q][s];
       if (axis == 2) {
         m2.add_prod(v[q][s].x, v[q][s].x);
         m2.add_prod(v[q][s].y, v[q][s].y);
@@ -516,10 +538,49 @@ __global__ void __launch_bounds__(256) k3_heat(Geo<T> g, int axis, Tri<cx<T>*> M
   }
   if (axis == 2) {
     if (!finite) st->nonfinite = 1;
-    double acc[1] = {m2.value()}, tot[1];
-    if (last_cta_sum<1>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0)
+    double acc[2] = {m2.value(), d2.value()}, tot[2];
+    if (last_cta_sum<2>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
       st->msum = tot[0];
+      if (dm) st->dm2 = tot[1];
+    }
   }
+}
+
+// sum |grad m|^2 from the spectrum of m after the x and y passes: forward FFT
+// along z of three fields, sum w |xi~|^2 |F|^2 / n (no store).
+template <typename T>
+__global__ void __launch_bounds__(256) k3_zgradnorm(Geo<T> g, Tri<cx<T>*> Q, SolveState* st,
+                                                    int into_next) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const ColPass& p = g.pz;
+  const CIdx3 c = cidx3(p);
+  const int se = slab3(p);
+  cx<T>* const sl[3] = {sm + c.b, sm + se + c.b, sm + 2 * se + c.b};
+  cx<T> v[3][8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const size_t idx = c.base + (size_t)(c.j + s * c.L8) * (size_t)p.stride;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[q][s] = Q.v[q][idx];
+  }
+  fft_canon<-1, 3>(v, sl, 1 << p.ltc, c.j, p.lL, g.twz);
+  const int kx = c.col & (g.H - 1), ky = c.col >> g.lH;
+  const T a = g.kxd[kx], b = g.kyd[ky];
+  const T wxy = a * a + b * b, w = kx == 0 ? (T)1 : (T)2;
+  DotAcc<T> ga;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const T cz = g.kzd[c.j + s * c.L8];
+    const T wk = w * (wxy + cz * cz);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      ga.add_prod(wk * v[q][s].x, v[q][s].x);
+      ga.add_prod(wk * v[q][s].y, v[q][s].y);
+    }
+  }
+  gradnorm_finish(ga.value(), 1.0 / ((double)g.nx * (double)g.ny * (double)g.nz), g.partials, st,
+                  into_next);
 }
 
 // ------------------------------------------------------------------ CG update, |m|^2
@@ -668,16 +729,23 @@ void row_apply3(const Geo<T>& g, Tri<cx<T>*> G, Tri<const Tm*> m, const Tm* r, T
   k3_row_apply<T, Tm><<<row3_ctas(g), row3_threads(g), row3_smem(g), s>>>(g, G, m, r, Q, st);
 }
 template <typename T>
-void row_split3(const Geo<T>& g, Tri<cx<T>*> G, Tri<T*> m, SplitCoef cf, SolveState* st,
-                cudaStream_t s) {
-  k3_row_split<T><<<row3_ctas(g), row3_threads(g), row3_smem(g), s>>>(g, G, m, cf, st);
+void row_split3(const Geo<T>& g, Tri<cx<T>*> G, Tri<const T*> m, const T* r, Tri<T*> mo,
+                SplitCoef cf, SolveState* st, cudaStream_t s) {
+  k3_row_split<T><<<row3_ctas(g), row3_threads(g), row3_smem(g), s>>>(g, G, m, r, mo, cf, st);
 }
 template <typename T>
-void heat_axis(const Geo<T>& g, int axis, Tri<T*> m, SolveState* st, cudaStream_t s) {
+void heat_axis(const Geo<T>& g, int axis, Tri<T*> mi, Tri<T*> mo, SolveState* st, cudaStream_t s) {
   const ColPass& p = axis == 1 ? g.py : g.pz;
-  Tri<cx<T>*> M = {{reinterpret_cast<cx<T>*>(m.v[0]), reinterpret_cast<cx<T>*>(m.v[1]),
-                    reinterpret_cast<cx<T>*>(m.v[2])}};
-  k3_heat<T><<<pass_ctas(p), pass_threads(p), pass_smem<T>(p, 3), s>>>(g, axis, M, st);
+  Tri<cx<T>*> Mi = {{reinterpret_cast<cx<T>*>(mi.v[0]), reinterpret_cast<cx<T>*>(mi.v[1]),
+                     reinterpret_cast<cx<T>*>(mi.v[2])}};
+  Tri<cx<T>*> Mo = {{reinterpret_cast<cx<T>*>(mo.v[0]), reinterpret_cast<cx<T>*>(mo.v[1]),
+                     reinterpret_cast<cx<T>*>(mo.v[2])}};
+  k3_heat<T><<<pass_ctas(p), pass_threads(p), pass_smem<T>(p, 3), s>>>(g, axis, Mi, Mo, st);
+}
+template <typename T>
+void z_gradnorm(const Geo<T>& g, Tri<cx<T>*> G, SolveState* st, int into_next, cudaStream_t s) {
+  k3_zgradnorm<T><<<pass_ctas(g.pz), pass_threads(g.pz), pass_smem<T>(g.pz, 3), s>>>(g, G, st,
+                                                                                     into_next);
 }
 template <typename T>
 void cg_update3(const Geo<T>& g, cx<T>* x, cx<T>* r, const cx<T>* d, const cx<T>* q,
@@ -693,6 +761,7 @@ template <typename T>
 void set_smem_limits_3d_t() {
   allow_smem(k3_row_split<T>);
   allow_smem(k3_heat<T>);
+  allow_smem(k3_zgradnorm<T>);
   allow_smem(k3_axis_fft<T, -1, 1>);
   allow_smem(k3_axis_fft<T, -1, 3>);
   allow_smem(k3_axis_fft<T, +1, 1>);

@@ -20,9 +20,11 @@ template void z_div<float>(const Geo<float>&, int, Tri<cx<float>*>, const cx<flo
 template void row_apply3<float, float>(const Geo<float>&, Tri<cx<float>*>, Tri<const float*>,
                                        const float*, Tri<cx<float>*>, const SolveState*,
                                        cudaStream_t);
-template void row_split3<float>(const Geo<float>&, Tri<cx<float>*>, Tri<float*>, SplitCoef,
-                                SolveState*, cudaStream_t);
-template void heat_axis<float>(const Geo<float>&, int, Tri<float*>, SolveState*, cudaStream_t);
+template void row_split3<float>(const Geo<float>&, Tri<cx<float>*>, Tri<const float*>, const float*,
+                                Tri<float*>, SplitCoef, SolveState*, cudaStream_t);
+template void heat_axis<float>(const Geo<float>&, int, Tri<float*>, Tri<float*>, SolveState*,
+                               cudaStream_t);
+template void z_gradnorm<float>(const Geo<float>&, Tri<cx<float>*>, SolveState*, int, cudaStream_t);
 template void cg_update3<float>(const Geo<float>&, cx<float>*, cx<float>*, const cx<float>*,
                                 const cx<float>*, SolveState*, cudaStream_t);
 template void msum3<float>(const Geo<float>&, Tri<const float*>, SolveState*, cudaStream_t);

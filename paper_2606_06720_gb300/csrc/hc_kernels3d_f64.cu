@@ -19,9 +19,11 @@ template void row_apply3<double, double>(const Geo<double>&, Tri<cx<double>*>, T
 template void row_apply3<double, float>(const Geo<double>&, Tri<cx<double>*>, Tri<const float*>,
                                         const float*, Tri<cx<double>*>, const SolveState*,
                                         cudaStream_t);
-template void row_split3<double>(const Geo<double>&, Tri<cx<double>*>, Tri<double*>, SplitCoef,
-                                 SolveState*, cudaStream_t);
-template void heat_axis<double>(const Geo<double>&, int, Tri<double*>, SolveState*, cudaStream_t);
+template void row_split3<double>(const Geo<double>&, Tri<cx<double>*>, Tri<const double*>, const double*,
+                                Tri<double*>, SplitCoef, SolveState*, cudaStream_t);
+template void heat_axis<double>(const Geo<double>&, int, Tri<double*>, Tri<double*>, SolveState*,
+                               cudaStream_t);
+template void z_gradnorm<double>(const Geo<double>&, Tri<cx<double>*>, SolveState*, int, cudaStream_t);
 template void cg_update3<double>(const Geo<double>&, cx<double>*, cx<double>*, const cx<double>*,
                                  const cx<double>*, SolveState*, cudaStream_t);
 template void msum3<double>(const Geo<double>&, Tri<const double*>, SolveState*, cudaStream_t);

@@ -11,7 +11,7 @@ template void row_apply<float, float>(const Geo<float>&, const cx<float>*, const
                                       const float*, const float*, const float*, cx<float>*,
                                       cx<float>*, const SolveState*, cudaStream_t);
 template void row_split<float>(const Geo<float>&, const cx<float>*, const cx<float>*, const float*,
-                               const float*, cx<float>*, cx<float>*, SplitCoef, SolveState*,
+                               const float*, const float*, cx<float>*, cx<float>*, SplitCoef, SolveState*,
                                cudaStream_t);
 template void col_fwd<float>(const Geo<float>&, const cx<float>*, const cx<float>*, cx<float>*,
                              cx<float>*, int, int, SolveState*, cudaStream_t);
@@ -25,7 +25,9 @@ template void col_grad<float, float>(const Geo<float>&, int, cx<float>*, const c
 template void col_div<float>(const Geo<float>&, int, const cx<float>*, const cx<float>*,
                              const cx<float>*, const cx<float>*, cx<float>*, cx<float>*, cx<float>*,
                              SolveState*, cudaStream_t);
-template void col_heat<float>(const Geo<float>&, cx<float>*, cx<float>*, cudaStream_t);
+template void col_heat<float>(const Geo<float>&, cx<float>*, cx<float>*, SolveState*, cudaStream_t);
+template void col_gradnorm<float>(const Geo<float>&, const cx<float>*, const cx<float>*, SolveState*, int,
+                                 cudaStream_t);
 template void cg_update<float>(const Geo<float>&, cx<float>*, cx<float>*, const cx<float>*,
                                const cx<float>*, SolveState*, cudaStream_t);
 template void msum<float>(const Geo<float>&, const float*, const float*, SolveState*, cudaStream_t);

@@ -13,9 +13,9 @@ template void row_apply<double, double>(const Geo<double>&, const cx<double>*, c
 template void row_apply<double, float>(const Geo<double>&, const cx<double>*, const cx<double>*,
                                        const float*, const float*, const float*, cx<double>*,
                                        cx<double>*, const SolveState*, cudaStream_t);
-template void row_split<double>(const Geo<double>&, const cx<double>*, const cx<double>*,
-                                const double*, const double*, cx<double>*, cx<double>*, SplitCoef,
-                                SolveState*, cudaStream_t);
+template void row_split<double>(const Geo<double>&, const cx<double>*, const cx<double>*, const double*,
+                               const double*, const double*, cx<double>*, cx<double>*, SplitCoef, SolveState*,
+                               cudaStream_t);
 template void col_fwd<double>(const Geo<double>&, const cx<double>*, const cx<double>*, cx<double>*,
                               cx<double>*, int, int, SolveState*, cudaStream_t);
 template void col_inv<double>(const Geo<double>&, const cx<double>*, cx<double>*, double,
@@ -26,7 +26,9 @@ template void col_grad<double, double>(const Geo<double>&, int, cx<double>*, con
 template void col_div<double>(const Geo<double>&, int, const cx<double>*, const cx<double>*,
                               const cx<double>*, const cx<double>*, cx<double>*, cx<float>*,
                               cx<float>*, SolveState*, cudaStream_t);
-template void col_heat<double>(const Geo<double>&, cx<double>*, cx<double>*, cudaStream_t);
+template void col_heat<double>(const Geo<double>&, cx<double>*, cx<double>*, SolveState*, cudaStream_t);
+template void col_gradnorm<double>(const Geo<double>&, const cx<double>*, const cx<double>*, SolveState*, int,
+                                 cudaStream_t);
 template void cg_update<double>(const Geo<double>&, cx<double>*, cx<double>*, const cx<double>*,
                                 const cx<double>*, SolveState*, cudaStream_t);
 template void convert<double, float>(const float*, double*, size_t, cudaStream_t);
@@ -52,6 +54,12 @@ void set_smem_limits_f64() {
 }
 
 __global__ void k_set_config(SolveState* st, SolveConfig c) {
+  st->e_coef[0] = c.e_coef[0];
+  st->e_coef[1] = c.e_coef[1];
+  st->e_coef[2] = c.e_coef[2];
+  st->dt = c.dt;
+  st->dim = c.dim;
+  st->diag = c.diag;
   st->outer_rtol2 = c.outer_thresh2_rel;
   st->inner_rtol2 = c.inner_rtol2;
   st->user_kappa = c.user_kappa;
@@ -63,7 +71,11 @@ __global__ void k_set_config(SolveState* st, SolveConfig c) {
 }
 
 __global__ void k_step_begin(SolveState* st, int npts) {
-  st->kappa = st->user_kappa > 0 ? st->user_kappa : st->mean_r + st->msum / (double)npts / 2.0;
+  // reading R3: kappa = mean(r) + mean(|m|^2) / d
+  st->kappa = st->user_kappa > 0 ? st->user_kappa
+                                 : st->mean_r + st->msum / (double)npts / (double)st->dim;
+  st->msum_old = st->msum;
+  st->gm2_next_valid = 0;
   st->outer_thresh2 = st->outer_rtol2 * st->outer_b2;
   st->it = 0;
   st->total_it = 0;
@@ -77,6 +89,9 @@ __global__ void k_step_begin(SolveState* st, int npts) {
   if (st->graph_mode && st->refined) cudaGraphSetConditional(st->h_outer, 1u);
 }
 
+// Diagnostics of Section 2.5 for the step that just ran from m^k: the energy
+// E_h(m^k) (with p[m^k], the pressure this step solved) and Delta m^{k+1}.
+// In run mode, the stopping rules of Algorithm 1's loop.
 __global__ void k_step_end(SolveState* st, int refined) {
   const int status = st->nonfinite ? HC_ENONFINITE : st->status;
   st->step_status = status;
@@ -84,6 +99,54 @@ __global__ void k_step_end(SolveState* st, int refined) {
   st->acc_iters += st->total_it;
   st->acc_sweeps += st->sweeps;
   st->acc_steps += 1;
+  if (st->diag) {
+    if (st->gm2_valid) {
+      st->energy_prev = st->energy;
+      st->energy = st->e_coef[0] * st->gm2 + st->e_coef[1] * (st->dsum[0] + st->dsum[1]) +
+                   st->e_coef[2] * st->dsum[2];
+      st->energy_valid = 1;
+      st->n_energy += 1;
+    } else {
+      st->energy_valid = 0;
+    }
+    st->delta_m = st->msum_old > 0 ? sqrt(st->dm2 / st->msum_old) / st->dt : 0.0;
+    st->gm2 = st->gm2_next;
+    st->gm2_valid = st->gm2_next_valid;
+  } else {
+    st->energy_valid = 0;
+    st->gm2_valid = 0;
+  }
+  if (st->run_mode && !st->halt) {
+    int reason = HC_STOP_NONE;
+    if (status == HC_ENONFINITE) {
+      reason = HC_STOP_STATUS;
+    } else if (st->diag && st->eps_dm > 0 && st->delta_m <= st->eps_dm) {
+      reason = HC_STOP_DELTA_M;
+    } else if (st->stop_energy && st->energy_valid && st->n_energy >= 2 &&
+               !(st->energy < st->energy_prev)) {
+      // this step evaluated E(m^k) >= E(m^{k-1}); the previous step made m^k
+      reason = HC_STOP_ENERGY;
+      st->energy_step = st->acc_steps - 2;
+    }
+    if (reason != HC_STOP_NONE) {
+      st->halt = 1;
+      st->stop_reason = reason;
+    }
+  }
+}
+
+__global__ void k_set_run(SolveState* st, int run_mode, double eps_dm, int stop_energy) {
+  st->run_mode = run_mode;
+  st->eps_dm = eps_dm;
+  st->stop_energy = stop_energy;
+  st->halt = 0;
+  st->stop_reason = HC_STOP_NONE;
+  st->energy_step = -1;
+  st->n_energy = 0;
+}
+
+__global__ void k_run_gate(SolveState* st) {
+  cudaGraphSetConditional(st->h_gate, st->halt ? 0u : 1u);
 }
 
 __global__ void k_reset_accum(SolveState* st) {
@@ -97,5 +160,9 @@ void set_config(SolveState* st, SolveConfig cfg, cudaStream_t s) { k_set_config<
 void step_begin(SolveState* st, int npts, cudaStream_t s) { k_step_begin<<<1, 1, 0, s>>>(st, npts); }
 void step_end(SolveState* st, int refined, cudaStream_t s) { k_step_end<<<1, 1, 0, s>>>(st, refined); }
 void reset_accum(SolveState* st, cudaStream_t s) { k_reset_accum<<<1, 1, 0, s>>>(st); }
+void set_run(SolveState* st, int run_mode, double eps_dm, int stop_energy, cudaStream_t s) {
+  k_set_run<<<1, 1, 0, s>>>(st, run_mode, eps_dm, stop_energy);
+}
+void run_gate(SolveState* st, cudaStream_t s) { k_run_gate<<<1, 1, 0, s>>>(st); }
 
 }  // namespace hc

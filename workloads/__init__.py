@@ -184,3 +184,63 @@ def source_sink_3d(n: int, steps: int = 500) -> Workload:
     S = minus_mean(gaussian(nn, (0.3, 0.5, 0.5), 0.05) - gaussian(nn, (0.7, 0.5, 0.5), 0.05))
     return Workload("source_sink_3d_%d" % n, nn, (1.0, 1.0, 1.0), 25.0, 0.03, 0.75, 5e-4, steps,
                     1e-8, np.full((n, n, n), 0.1), S, uniform_m((n, n, n), 3, 0.0, 0.5, 0))
+
+
+# ---------------------------------------------------------------- the paper's analytic inputs
+# Section 3.1 (initial conductivities m^A, m^B, m^const), Section 3.2 (one
+# source and four sinks, S_4) and Section 3.3 (internal sink, S_int), on the
+# unit square, evaluated as printed at the nodes x_i = i / N (no periodic
+# image: the Gaussians of S are below 1e-100 at the boundary; m^A is 3.7e-6
+# there, which the paper treats as periodic).
+
+def _xy(n: int):
+    x = node_coords(n)
+    return np.meshgrid(x, x)  # X[j, i] = x_i, Y[j, i] = y_j
+
+
+def paper_m_ini(n: int, kind: str) -> np.ndarray:
+    """m^A = (exp(-1e4 (y-0.5)^2 - 50 (x-0.5)^2), 0), m^B = (exp(-50 (y-0.5)^2
+    - 50 (x-0.5)^2), 0), m^const = (1, 1); shape (2, n, n)."""
+    X, Y = _xy(n)
+    if kind == "A":
+        m1 = np.exp(-1e4 * (Y - 0.5) ** 2 - 50.0 * (X - 0.5) ** 2)
+    elif kind == "B":
+        m1 = np.exp(-50.0 * (Y - 0.5) ** 2 - 50.0 * (X - 0.5) ** 2)
+    elif kind == "const":
+        return np.ones((2, n, n))
+    else:
+        raise ValueError(kind)
+    return np.stack([m1, np.zeros_like(m1)])
+
+
+def paper_S4(n: int) -> np.ndarray:
+    """S_4 = exp(-1000 |x - (0.5,0.5)|^2) - sum_i exp(-1000 |x - x_i|^2) / 4,
+    sinks at (0.2,0.2), (0.2,0.8), (0.8,0.2), (0.8,0.8)."""
+    X, Y = _xy(n)
+    S = np.exp(-1000.0 * ((Y - 0.5) ** 2 + (X - 0.5) ** 2))
+    for xi, yi in ((0.2, 0.2), (0.2, 0.8), (0.8, 0.2), (0.8, 0.8)):
+        S = S - 0.25 * np.exp(-1000.0 * ((Y - yi) ** 2 + (X - xi) ** 2))
+    return S
+
+
+def paper_Sint(n: int) -> np.ndarray:
+    """S_int = exp(-1000 |x - (0.5,0.5)|^2) - pi / 1000."""
+    X, Y = _xy(n)
+    return np.exp(-1000.0 * ((Y - 0.5) ** 2 + (X - 0.5) ** 2)) - math.pi / 1000.0
+
+
+def paper_four_sinks(n: int, gamma: float = 1.0, steps: int = 30000) -> Workload:
+    """Section 3.2: r = 0.1, c = 200, D = 0.0025, dt = 0.005, S_4, m^A
+    (t_end = 150); CG threshold 1e-7 and Delta m <= 1e-4 (Section 3.1)."""
+    return Workload("paper_four_sinks_%d_g%g" % (n, gamma), (n, n), (1.0, 1.0), 200.0, 0.0025,
+                    gamma, 0.005, steps, 1e-7, np.full((n, n), 0.1), paper_S4(n),
+                    paper_m_ini(n, "A"))
+
+
+def paper_internal_sink(n: int, gamma: float = 0.75, kind: str = "const",
+                        steps: int = 40000) -> Workload:
+    """Section 3.3: r = 0.1, c = 200, D = 0.0025, dt = 0.005, S_int, m^const
+    (or m^A / m^B, Section 3.3's comparison at t = 200)."""
+    return Workload("paper_internal_sink_%d_%s" % (n, kind), (n, n), (1.0, 1.0), 200.0, 0.0025,
+                    gamma, 0.005, steps, 1e-7, np.full((n, n), 0.1), paper_Sint(n),
+                    paper_m_ini(n, kind))
