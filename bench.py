@@ -315,6 +315,59 @@ def run_accuracy(args) -> None:
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------- diagnostics leg
+def run_diagnostics(P, W, args, dev, barrier, max_over_ranks, world, headline) -> dict:
+    """(a) The headline 2048^2 workload with the energy and Delta m computed
+    every step, run as Algorithm 1's loop (hc_run: eps 1e-4, energy rule on;
+    neither fires within the steps timed): its throughput against the
+    headline's.  (b) The paper's own setups of Sections 3.2-3.3 at 512^2
+    (c = 200, D = 0.0025, dt = 0.005, CG threshold 1e-7 relative): one source
+    and four sinks from m^A (gamma = 1), and the internal sink from m^const
+    (gamma = 0.75), each run through hc_run."""
+    import numpy as np
+    import torch
+    out = {}
+    w = W.source_sink_2d(N_GRID)
+    K = max(10, args.steps // 10)
+    s = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp32_refined",
+                 cg_rtol=CG_RTOL_REFINED, cg_maxit=2000, device=str(dev), diagnostics=True)
+    s.set_r(w.r)
+    s.set_source(w.S)
+    s.set_m(w.m0)
+    s.run(3, eps=1e-4)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = s.run(K, eps=1e-4, stop_on_energy=True)
+    secs = max_over_ranks(time.perf_counter() - t0)
+    s.close()
+    v = world * w.npts * st.steps / secs / 1e6
+    out["headline_with_diagnostics"] = {
+        "value": v, "unit": UNIT, "steps": st.steps, "stop_reason": st.stop_reason,
+        "cost_vs_headline": headline / v - 1.0, "energy": st.energy, "delta_m": st.delta_m,
+        "path": "hc_run (gated step graph, host checks every 16 launches)"}
+    for name, wp in (("paper_four_sinks_512_gamma1", W.paper_four_sinks(512, 1.0)),
+                     ("paper_internal_sink_512_mconst", W.paper_internal_sink(512, 0.75))):
+        sp = P.Solver(wp.n, wp.L, c=wp.c, D=wp.D, gamma=wp.gamma, dt=wp.dt,
+                      precision="fp32_refined", cg_rtol=wp.cg_rtol, cg_maxit=2000,
+                      device=str(dev))
+        sp.set_r(wp.r)
+        sp.set_source(wp.S)
+        sp.set_m(wp.m0)
+        Kp = max(20, args.steps // 5)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stp = sp.run(Kp, eps=1e-4, stop_on_energy=True)
+        secs = max_over_ranks(time.perf_counter() - t0)
+        sp.close()
+        out[name] = {"value": world * wp.npts * stp.steps / secs / 1e6, "unit": UNIT,
+                     "steps": stp.steps, "t_end": stp.steps * wp.dt,
+                     "stop_reason": stp.stop_reason, "energy": stp.energy,
+                     "delta_m": stp.delta_m, "cg_iters_last_step": stp.cg_iters}
+    return out
+
+
 # ----------------------------------------------------------------- 3D leg
 def run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src) -> dict:
     """The 256^3 source/sink workload (r = 0.1, sigma 0.05 pair at
@@ -630,6 +683,11 @@ def run_gb300(args) -> None:
                             "sweep (gradients for c^2, D^2, r, S, m0)",
                 "dL_dc2": grads["dc2"], "dL_dD2": grads["dD2"]}
 
+    # ---- diagnostics (Section 2.5) and Algorithm 1's loop with its stopping rules
+    diag = None
+    if not args.no_diag:
+        diag = run_diagnostics(P, W, args, dev, barrier, max_over_ranks, world, value)
+
     # ---- 3D: the 256^3 source/sink problem (d = 3), FP32 + FP64 refinement
     three_d = None
     if not args.no_3d:
@@ -693,7 +751,7 @@ def run_gb300(args) -> None:
             "cg_iterations_per_s": world * iters_per_step * K / (ms_max / 1e3),
             "rel_residual_last_step": st.rel_residual,
             "fp64_plain": fp64, "refined_df": dfv, "sweep": sweep, "adjoint": adjv,
-            "three_d": three_d, "kernels": kernels,
+            "three_d": three_d, "diagnostics": diag, "kernels": kernels,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -729,6 +787,8 @@ def main() -> None:
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--adj-steps", type=int, default=60, help="adjoint leg: steps (C4 uses 500)")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D (256^3) leg")
+    ap.add_argument("--no-diag", action="store_true",
+                    help="skip the diagnostics / stopping-rule leg")
     ap.add_argument("--n3d", type=int, default=256, help="3D leg: grid points per axis")
     ap.add_argument("--only-3d", action="store_true",
                     help="run only the 3D leg, --steps/--warmup steps (for profiling)")
