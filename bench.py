@@ -43,7 +43,7 @@ BYTES_PER_POINT = {
     "fp32_refined": {
         "cg_grad": 20,     # read r, d; write d, Gx, Gy          5 F4
         "cg_apply": 28,    # read Gx, Gy, mx, my, r; write Qx, Qy 7 F4
-        "cg_div": 16,      # read Qx, Qy, d; write q              4 F4
+        "cg_div": 12,      # read Qx, Qy; write q                 3 F4 (alpha comes from cg_apply)
         "cg_update": 24,   # read x, r, d, q; write x, r          6 F4
         "res_grad": 24,    # read p64; write Gx64, Gy64           3 F8
         "res_apply": 44,   # read Gx64, Gy64 (2 F8), m, r (3 F4); write 2 F8
@@ -54,7 +54,7 @@ BYTES_PER_POINT = {
         "split_c2r": 16,   # read Mx, My; write mx, my            4 F4
     },
     "fp64": {
-        "cg_grad": 40, "cg_apply": 56, "cg_div": 32, "cg_update": 48, "res_grad": 24,
+        "cg_grad": 40, "cg_apply": 56, "cg_div": 24, "cg_update": 48, "res_grad": 24,
         "res_apply": 56, "res_div": 32, "split_grad": 24, "split_row": 48, "split_heat": 32,
         "split_c2r": 32,
     },
@@ -69,7 +69,7 @@ BYTES_PER_POINT_3D = {
     "cg_grad": 24,     # read r, d; write d, G0, G1, G2        6 F4
     "cg_ypass": 24,    # read G0..G2; write G0..G2             6 F4
     "cg_apply": 40,    # read G0..G2, m0..m2, r; write Q0..Q2 10 F4
-    "cg_div": 20,      # read Q0..Q2, d; write q               5 F4
+    "cg_div": 16,      # read Q0..Q2; write q                  4 F4
     "cg_update": 24,   # read x, r, d, q; write x, r           6 F4
     "res_grad": 44,    # read p64, delta; write p64, 3 grads (F8)
     "res_ypass": 48,   # 3 F8 in, 3 F8 out
@@ -85,7 +85,7 @@ BYTES_PER_POINT_3D = {
 # workload with the current kernels (profiles/residual_and_cg_kernels_2048.md).
 # Set an entry to None when its kernel changes.
 NCU_TRAFFIC_2048 = {"res_grad": 54.9e6, "res_apply": 136.8e6, "res_div": 132.9e6,
-                    "cg_grad": 35.6e6, "cg_apply": 86.1e6, "cg_div": 50.6e6, "cg_update": 67.7e6}
+                    "cg_grad": 35.6e6, "cg_apply": None, "cg_div": None, "cg_update": 67.7e6}
 
 
 def shard(items: int, rank: int, world: int) -> list:

@@ -192,7 +192,8 @@ typedef struct {
   int row_rows[2];
   int col_pipe[2]; /* 1: the CG/residual/heat column passes run persistent, prefetching the next
                       tile with cp.async while transforming the current one; needs
-                      col_tile * (8 bytes FP32 | 16 bytes FP64) to be a multiple of 16 */
+                      col_tile * (8 bytes FP32 | 16 bytes FP64) to be a multiple of 16, or
+                      one FP32 column (8-byte copies) */
 } hc_tuning;
 
 int hc_get_tuning(const hc_ctx* ctx, hc_tuning* out);

@@ -31,10 +31,15 @@ def _cache_path() -> str:
                           os.path.join(os.path.expanduser("~"), ".cache", "hucai_gb300", "tuning.json"))
 
 
+# Bumped whenever the kernels' launch-shape trade-offs change, so cached
+# choices made for older kernels are not reused.
+_KERNELS_VERSION = 2
+
+
 def _key(solver) -> str:
     import torch
     name = torch.cuda.get_device_name(solver.device)
-    return f"{name}|{solver.n[0]}x{solver.n[1]}|{solver.precision}"
+    return f"{name}|{solver.n[0]}x{solver.n[1]}|{solver.precision}|k{_KERNELS_VERSION}"
 
 
 def _candidates(solver, knob: str):
@@ -56,7 +61,10 @@ def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = Fal
              report: dict | None = None) -> dict:
     """Pick the fastest launch shapes for this solver and apply them; returns
     the tuning.  If `report` is a dict it receives the cache key and the
-    measured microseconds per candidate (empty when the cache answered)."""
+    measured microseconds per candidate (empty when the cache answered).
+    3D grids have fixed launch shapes: their tuning is returned unchanged."""
+    if getattr(solver, "dim", 2) != 2:
+        return solver.get_tuning()
     path = _cache_path()
     key = _key(solver)
     if report is not None:

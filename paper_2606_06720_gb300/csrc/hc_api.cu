@@ -2074,11 +2074,13 @@ int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
     if (tc < 1 || (tc & (tc - 1)) || tc > 32 || tc > c->H || (tc << (lny - 3)) > 512) return HC_EINVAL;
     if (rpc < 1 || (rpc & (rpc - 1)) || rpc > c->ny || (rpc << (lnx - 3)) > 512) return HC_EINVAL;
     const size_t col_sm = 2 * (size_t)(c->ny + (c->ny >> 3)) * tc * esz + 1024;
-    const size_t row_sm = (size_t)rpc * c->nx * esz + 1024;
+    // the apply row pass also stages m and r (FP32 unless plain FP64)
+    const size_t msz = (p == 1 && !c->refined) ? sizeof(double) : sizeof(float);
+    const size_t row_sm = (size_t)rpc * c->nx * (esz + 3 * msz) + 1024;
     if (col_sm > (size_t)optin || row_sm > (size_t)optin) return HC_EINVAL;
     if (t->col_pipe[p] != 0 && t->col_pipe[p] != 1) return HC_EINVAL;
     if (t->col_pipe[p]) {
-      if ((tc * esz) % 16) return HC_EINVAL;
+      if ((tc * esz) % 16 && tc * esz != 8) return HC_EINVAL;  // 16-byte copies, or one FP32 column
       if (2 * col_sm > (size_t)optin) return HC_EINVAL;
     }
   }
@@ -2117,6 +2119,7 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
   init.first = 1;
   init.alpha = 0;
   init.beta = 0;
+  init.rho = 0;  // alpha = rho / <d, A d> stays 0 whichever kernel computes it
   init.maxit = 0x7fffffff;
   init.thresh2 = -1.0;
   init.outer_thresh2 = -1.0;
@@ -2322,8 +2325,8 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
                                (const float*)c->rf, c->q32, c->x32,
                                split_coef(c->prm), ts, c->stream);
           break;
-        case HC_K_SPLIT_HEAT:
-          hc::col_heat<float>(g, Gx, Gy, ts, c->stream);
+        case HC_K_SPLIT_HEAT:  // on scratch: each launch rescales its data
+          hc::col_heat<float>(g, c->q32, c->x32, ts, c->stream);
           break;
         default:
           hc::row_c2r<float>(g, Gx, Gy, (float*)c->q32, (float*)c->x32, ts, 1, c->stream);
@@ -2371,8 +2374,8 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
                                 (const double*)c->rf, c->q64,
                                 (cx<double>*)c->stage, split_coef(c->prm), ts, c->stream);
           break;
-        case HC_K_SPLIT_HEAT:
-          hc::col_heat<double>(g, Gx, Gy, ts, c->stream);
+        case HC_K_SPLIT_HEAT:  // on scratch: each launch rescales its data
+          hc::col_heat<double>(g, c->q64, (cx<double>*)c->stage, ts, c->stream);
           break;
         default:
           hc::row_c2r<double>(g, Gx, Gy, sx, sy, ts, 1, c->stream);

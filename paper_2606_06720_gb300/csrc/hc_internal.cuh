@@ -235,9 +235,11 @@ template <typename T>
 void row_c2r(const Geo<T>& g, const cx<T>* A, const cx<T>* B, T* a, T* b, SolveState* st,
              int kappa_update, cudaStream_t s);
 // Row pass of the operator apply: C2R(gx, gy) -> q = (m.g) m + r g -> R2C(q).
+// With st (a CG iteration) also alpha = rho / <d, A d> from this pass, and the
+// pass is skipped when st->done.
 template <typename T, typename Tm>
 void row_apply(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const Tm* mx, const Tm* my,
-               const Tm* r, cx<T>* Qx, cx<T>* Qy, const SolveState* st, cudaStream_t s);
+               const Tm* r, cx<T>* Qx, cx<T>* Qy, SolveState* st, cudaStream_t s);
 // Row pass of the split step: C2R(grad p) -> activation -> relaxation -> R2C(m);
 // with st->diag the energy's pointwise sums of (m^k, grad p) into st->dsum (r read then).
 template <typename T>
@@ -334,7 +336,7 @@ void z_div(const Geo<T>& g, int mode, Tri<cx<T>*> Q, const cx<T>* d, const cx<T>
 // Row pass of the 3D apply: C2R(grad p) -> q = (m.g) m + r g -> R2C(q).
 template <typename T, typename Tm>
 void row_apply3(const Geo<T>& g, Tri<cx<T>*> G, Tri<const Tm*> m, const Tm* r, Tri<cx<T>*> Q,
-                const SolveState* st, cudaStream_t s);
+                SolveState* st, cudaStream_t s);
 // Row pass of the 3D split step: C2R(grad p) -> activation -> relaxation ->
 // diffusion along x; reads m, writes mo (physical; mo may be the rows of G).
 // With st->diag also the energy's pointwise sums (r read then).

@@ -156,6 +156,28 @@ __device__ __forceinline__ int slot(int e, int ks) {
 }
 
 // ------------------------------------------------------------------ FFT core
+// Twiddles w^r = exp(S 2 pi i r k / (R Ns)), r = 1..R-1, of one butterfly.  FP32:
+// one table load and the powers by complex products (w^2 = w w, w^3 = w^2 w,
+// w^4 = w^2 w^2, ...; a few ulp, far below the FP32 transform's own error),
+// which replaces R-2 dependent L1 round trips per pass with FMAs.  FP64 and
+// double-float kernels are bound by their arithmetic and load every power.
+template <int S, int R, typename T>
+__device__ __forceinline__ void twiddle_powers(cx<T> (&w)[R], const cx<T>* __restrict__ tw,
+                                               int step) {
+  if constexpr (std::is_same<T, float>::value) {
+    w[1] = ldg(&tw[step]);
+    if (S > 0) w[1].y = -w[1].y;
+#pragma unroll
+    for (int r = 2; r < R; ++r) w[r] = (r & 1) ? cmul(w[r - 1], w[1]) : cmul(w[r >> 1], w[r >> 1]);
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      w[r] = ldg(&tw[r * step]);
+      if (S > 0) w[r].y = -w[r].y;
+    }
+  }
+}
+
 // NV transforms of length N = 2^lN (lN >= 3), one per slab, computed by the
 // N/8 threads j = 0..N/8-1 of each transform.  v[q][s] holds element
 // j + s N/8 on entry (input) and on exit (output).  Element e of slab q lives
@@ -172,14 +194,12 @@ __device__ __forceinline__ void fft_canon(cx<T> (&v)[NV][8], cx<T>* const* sl, i
     if (rem >= 3) {
       const int k = j & ((1 << lNs) - 1);
       if (lNs > 0) {
-        const int step = k << (lN - 3 - lNs);  // k * N / (8 Ns)
+        cx<T> w[8];
+        twiddle_powers<S, 8>(w, tw, k << (lN - 3 - lNs));  // step k * N / (8 Ns)
 #pragma unroll
-        for (int r = 1; r < 8; ++r) {
-          cx<T> w = ldg(&tw[r * step]);
-          if (S > 0) w.y = -w.y;
+        for (int r = 1; r < 8; ++r)
 #pragma unroll
-          for (int q = 0; q < NV; ++q) v[q][r] = cmul(v[q][r], w);
-        }
+          for (int q = 0; q < NV; ++q) v[q][r] = cmul(v[q][r], w[r]);
       }
 #pragma unroll
       for (int q = 0; q < NV; ++q) dft8<S>(v[q]);
@@ -208,14 +228,12 @@ __device__ __forceinline__ void fft_canon(cx<T> (&v)[NV][8], cx<T>* const* sl, i
       for (int u = 0; u < 2; ++u) {
         const int jj = j + u * N8;
         const int k = jj & ((1 << lNs) - 1);
-        const int step = k << (lN - 2 - lNs);
+        cx<T> w[4];
+        twiddle_powers<S, 4>(w, tw, k << (lN - 2 - lNs));
 #pragma unroll
-        for (int r = 1; r < 4; ++r) {
-          cx<T> w = ldg(&tw[r * step]);
-          if (S > 0) w.y = -w.y;
+        for (int r = 1; r < 4; ++r)
 #pragma unroll
-          for (int q = 0; q < NV; ++q) v[q][u + 2 * r] = cmul(v[q][u + 2 * r], w);
-        }
+          for (int q = 0; q < NV; ++q) v[q][u + 2 * r] = cmul(v[q][u + 2 * r], w[r]);
 #pragma unroll
         for (int q = 0; q < NV; ++q) dft4<S>(v[q][u], v[q][u + 2], v[q][u + 4], v[q][u + 6]);
       }
@@ -353,6 +371,27 @@ __device__ __forceinline__ float pinv_f32(const Geo<T>& g, int kx, int ky, float
   return s2 > 0.0f ? 1.0f / (kappa * s2) : 0.0f;
 }
 
+// ------------------------------------------------------------------ cp.async
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+// 8-byte variant (cp.async.ca: the .cg form takes 16 bytes only), for tiles
+// whose rows are one FP32 complex value wide.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_prev() {  // all groups but the newest complete
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // ------------------------------------------------------------------ row helpers
 // Element k of Z = A_full + i B_full, the spectrum of the complex row a + i b,
 // from the packed Hermitian half spectra A, B (B may be null: b = 0).
@@ -471,12 +510,33 @@ __global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const
   }
 }
 
-template <typename T, typename Tm>
+// CG step length from the row pass.  With g = grad d (the physical gradient
+// this pass receives) and K = m m^T + r I, the spectral <d, A d> equals
+// n sum_x g . K g = n sum_x (m.g)^2 + r |g|^2 (summation by parts: the
+// spectral derivative with the R1 multipliers is skew-adjoint), so alpha =
+// rho / <d, A d> is known here and the divergence pass needs neither d nor a
+// reduction.
+__device__ __forceinline__ void cg_alpha_from(SolveState* st, double gkg, double n) {
+  const double dq = gkg * n;
+  if (dq > 0 && isfinite(dq)) {
+    st->alpha = st->rho / dq;
+  } else {
+    st->alpha = 0;
+    st->done = 1;
+    if (!isfinite(dq)) st->status = HC_ENONFINITE;
+  }
+  st->first = 0;
+}
+
+// Row pass of the operator apply.  The CTA's rows of m and r are staged into
+// shared memory with cp.async at the start, so their latency overlaps the
+// inverse transform.  DOT: the CG variant (alpha, see cg_alpha_from).
+template <typename T, typename Tm, bool DOT>
 __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
                                                    const Tm* __restrict__ mx,
                                                    const Tm* __restrict__ my,
                                                    const Tm* __restrict__ rr, cx<T>* Qx, cx<T>* Qy,
-                                                   const SolveState* __restrict__ st) {
+                                                   SolveState* st) {
   if (st && st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
@@ -485,24 +545,48 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
   const int y = (blockIdx.x << g.lrpc) + rb;
   cx<T>* slab = sm + rb * N;
   cx<T>* const sl[1] = {slab};
+  // stage rows [y0, y0 + rpc) of mx, my, r (contiguous) behind the slabs
+  Tm* sf = reinterpret_cast<Tm*>(sm + ((size_t)g.rpc << g.lnx));
+  {
+    const size_t row0 = ((size_t)blockIdx.x << g.lrpc) * N;
+    const int per = (int)(((size_t)g.rpc * N * sizeof(Tm)) >> 4);  // 16-byte chunks per field
+    for (int c = threadIdx.x; c < 3 * per; c += blockDim.x) {
+      const int q = c >= 2 * per ? 2 : (c >= per ? 1 : 0), ch = c - q * per;
+      const Tm* src = (q == 0 ? mx : (q == 1 ? my : rr)) + row0;
+      cp_async16(reinterpret_cast<char*>(sf + (size_t)q * g.rpc * N) + 16 * (size_t)ch,
+                 reinterpret_cast<const char*>(src) + 16 * (size_t)ch);
+    }
+    cp_async_commit();
+  }
   const cx<T>* Ar = Gx + (size_t)y * H;
   const cx<T>* Br = Gy + (size_t)y * H;
   cx<T> v[1][8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
   fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
+  cp_async_wait_all();
+  __syncthreads();
   // v = grad p (gx + i gy) at x = j + s N/8: apply (m (x) m + r I)
-  const size_t ro = (size_t)y * N;
+  const Tm* smx = sf + (size_t)rb * N;
+  const Tm* smy = smx + (size_t)g.rpc * N;
+  const Tm* srr = smy + (size_t)g.rpc * N;
+  DotAcc<T> gkg;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = j + s * N8;
     const T gx = v[0][s].x, gy = v[0][s].y;
-    const T ax = (T)mx[ro + x], ay = (T)my[ro + x], r = (T)rr[ro + x];
+    const T ax = (T)smx[x], ay = (T)smy[x], r = (T)srr[x];
     const T mg = ax * gx + ay * gy;
+    if (DOT) gkg.add_prod(mg * mg + r * (gx * gx + gy * gy), (T)1);  // one compensated add per point
     v[0][s] = cmk<T>(ax * mg + r * gx, ay * mg + r * gy);
   }
   fft_canon<-1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   store_pair_r2c(v, slab, j, N, H, Qx + (size_t)y * H, Qy + (size_t)y * H);
+  if (DOT) {
+    double a1[1] = {gkg.value()}, t1[1];
+    if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0)
+      cg_alpha_from(st, t1[0], (double)g.nx * (double)g.ny);
+  }
 }
 
 // Pointwise sums of the discrete energy (Section 2.5) at one point, from m^k
@@ -753,11 +837,7 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
     if constexpr (MODE == CD_PLAIN) {
       out[idx] = q;
     } else if constexpr (MODE == CD_CG) {
-      out[idx] = q;
-      const cx<T> dv = d[idx];
-      const T wt = (T)w;  // 1 or 2: exact
-      dq.add_prod(wt * dv.x, q.x);
-      dq.add_prod(wt * dv.y, q.y);
+      out[idx] = q;  // alpha came from the row pass (cg_alpha_from)
     } else if constexpr (MODE == CD_RESID) {
       const cx<T> rv = csub(bvec[idx], q);
       out[idx] = rv;
@@ -780,22 +860,9 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
       rzacc.add_prod(wpf * rf.y, rf.y);
     }
   }
-  if constexpr (MODE == CD_PLAIN) return;
+  if constexpr (MODE == CD_PLAIN || MODE == CD_CG) return;
   double tot[3];
-  if constexpr (MODE == CD_CG) {
-    double a1[1] = {dq.value()}, t1[1];
-    if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0) {
-      const double dq = t1[0];
-      if (dq > 0 && isfinite(dq)) {
-        st->alpha = st->rho / dq;
-      } else {
-        st->alpha = 0;
-        st->done = 1;
-        if (!isfinite(dq)) st->status = HC_ENONFINITE;
-      }
-      st->first = 0;
-    }
-  } else if constexpr (MODE == CD_RESID) {
+  if constexpr (MODE == CD_RESID) {
     double a2[2] = {acc[0], acc[1]}, t2[2];
     if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
       resid_init(st, t2[0], t2[1]);
@@ -964,24 +1031,19 @@ __global__ void __launch_bounds__(512) k_col_inv(Geo<T> g, const cx<T>* __restri
 // q*se + padk(row)*tc + b), so once a tile's values are in registers its
 // buffer half serves as the FFT exchange slabs.  Needs tc*sizeof(cx<T>) to be
 // a multiple of 16 bytes (the cp.async size).
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_prev() {  // all groups but the newest complete
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
-
 template <typename T, int NS>
 __device__ __forceinline__ void stage_cols(const Geo<T>& g, const cx<T>* a0, const cx<T>* a1,
                                            cx<T>* buf, int se, int kx0) {
   constexpr int lce = sizeof(cx<T>) == 8 ? 1 : 0;  // log2 complex elements per 16-byte copy
+  if (sizeof(cx<T>) == 8 && g.ltc == 0) {  // one FP32 column: 8-byte copies
+    const int per = g.ny;
+    for (int c = threadIdx.x; c < NS * per; c += blockDim.x) {
+      const int q = (NS > 1 && c >= per) ? 1 : 0;
+      const int row = c - q * per;
+      cp_async8(buf + q * se + padk(row), (q ? a1 : a0) + (size_t)row * g.H + kx0);
+    }
+    return;
+  }
   const int lcpr = g.ltc - lce;                     // log2 copies per row
   const int per = g.ny << lcpr;
   for (int c = threadIdx.x; c < NS * per; c += blockDim.x) {
@@ -1103,10 +1165,10 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
     __syncthreads();
     cx<T>* cur = sm + half * 2 * se;
     const int kx = (tile << g.ltc) + b;
-    cx<T> aux[8];  // d (CG) or b (residual), fetched early to overlap the FFT
-    if (MODE == CD_CG || MODE == CD_RESID || MODE == CD_RESID_REFINE) {
+    cx<T> aux[8];  // b (residual), fetched early to overlap the FFT
+    if (MODE == CD_RESID || MODE == CD_RESID_REFINE) {
 #pragma unroll
-      for (int s = 0; s < 8; ++s) aux[s] = (MODE == CD_CG ? d : bvec)[(size_t)(j + s * NY8) * H + kx];
+      for (int s = 0; s < 8; ++s) aux[s] = bvec[(size_t)(j + s * NY8) * H + kx];
     }
     cx<T> v[2][8];
 #pragma unroll
@@ -1129,10 +1191,7 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
       if constexpr (MODE == CD_PLAIN) {
         out[idx] = q;
       } else if constexpr (MODE == CD_CG) {
-        out[idx] = q;
-        const T wt = (T)w;
-        dq.add_prod(wt * aux[s].x, q.x);
-        dq.add_prod(wt * aux[s].y, q.y);
+        out[idx] = q;  // alpha came from the row pass (cg_alpha_from)
       } else if constexpr (MODE == CD_RESID) {
         const cx<T> rv = csub(aux[s], q);
         out[idx] = rv;
@@ -1159,21 +1218,8 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
     half ^= 1;
   }
   cp_async_wait_all();
-  if constexpr (MODE == CD_PLAIN) return;
-  if constexpr (MODE == CD_CG) {
-    double a1[1] = {dq.value()}, t1[1];
-    if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0) {
-      const double dqv = t1[0];
-      if (dqv > 0 && isfinite(dqv)) {
-        st->alpha = st->rho / dqv;
-      } else {
-        st->alpha = 0;
-        st->done = 1;
-        if (!isfinite(dqv)) st->status = HC_ENONFINITE;
-      }
-      st->first = 0;
-    }
-  } else if constexpr (MODE == CD_RESID) {
+  if constexpr (MODE == CD_PLAIN || MODE == CD_CG) return;
+  if constexpr (MODE == CD_RESID) {
     double t2[2];
     if (last_cta_sum<2>(accr, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
       resid_init(st, t2[0], t2[1]);
@@ -1632,9 +1678,14 @@ void row_c2r(const Geo<T>& g, const cx<T>* A, const cx<T>* B, T* a, T* b, SolveS
 }
 template <typename T, typename Tm>
 void row_apply(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const Tm* mx, const Tm* my,
-               const Tm* r, cx<T>* Qx, cx<T>* Qy, const SolveState* st, cudaStream_t s) {
-  k_row_apply<T, Tm><<<g.ny >> g.lrpc, row_threads(g), row_smem(g), s>>>(g, Gx, Gy, mx, my, r, Qx,
-                                                                         Qy, st);
+               const Tm* r, cx<T>* Qx, cx<T>* Qy, SolveState* st, cudaStream_t s) {
+  const size_t sm = row_smem(g) + (size_t)3 * g.rpc * g.nx * sizeof(Tm);
+  if (st)
+    k_row_apply<T, Tm, true><<<g.ny >> g.lrpc, row_threads(g), sm, s>>>(g, Gx, Gy, mx, my, r, Qx,
+                                                                       Qy, st);
+  else
+    k_row_apply<T, Tm, false><<<g.ny >> g.lrpc, row_threads(g), sm, s>>>(g, Gx, Gy, mx, my, r, Qx,
+                                                                        Qy, st);
 }
 template <typename T>
 void row_split(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const T* mx, const T* my,
@@ -1800,7 +1851,8 @@ template <typename T>
 void set_smem_limits_t() {
   allow_smem(k_row_r2c<T>);
   allow_smem(k_row_c2r<T>);
-  allow_smem(k_row_apply<T, T>);
+  allow_smem(k_row_apply<T, T, false>);
+  allow_smem(k_row_apply<T, T, true>);
   allow_smem(k_row_split<T>);
   allow_smem(k_col_fwd<T, 1>);
   allow_smem(k_col_fwd<T, 2>);

@@ -293,11 +293,7 @@ __global__ void __launch_bounds__(256) k3_zdiv(Geo<T> g, Tri<cx<T>*> Q, const cx
     if constexpr (MODE == CD_PLAIN) {
       out[idx] = q;
     } else if constexpr (MODE == CD_CG) {
-      out[idx] = q;
-      const cx<T> dv = d[idx];
-      const T wt = (T)w;
-      dq.add_prod(wt * dv.x, q.x);
-      dq.add_prod(wt * dv.y, q.y);
+      out[idx] = q;  // alpha came from the row pass (cg_alpha_from)
     } else if constexpr (MODE == CD_RESID) {
       const cx<T> rv = csub(bvec[idx], q);
       out[idx] = rv;
@@ -320,22 +316,9 @@ __global__ void __launch_bounds__(256) k3_zdiv(Geo<T> g, Tri<cx<T>*> Q, const cx
       rzacc.add_prod(wpf * rf.y, rf.y);
     }
   }
-  if constexpr (MODE == CD_PLAIN) return;
+  if constexpr (MODE == CD_PLAIN || MODE == CD_CG) return;
   double tot[3];
-  if constexpr (MODE == CD_CG) {
-    double a1[1] = {dq.value()}, t1[1];
-    if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0) {
-      const double dqs = t1[0];
-      if (dqs > 0 && isfinite(dqs)) {
-        st->alpha = st->rho / dqs;
-      } else {
-        st->alpha = 0;
-        st->done = 1;
-        if (!isfinite(dqs)) st->status = HC_ENONFINITE;
-      }
-      st->first = 0;
-    }
-  } else if constexpr (MODE == CD_RESID) {
+  if constexpr (MODE == CD_RESID) {
     double a2[2] = {acc[0], acc[1]}, t2[2];
     if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
       resid_init(st, t2[0], t2[1]);
@@ -349,10 +332,11 @@ __global__ void __launch_bounds__(256) k3_zdiv(Geo<T> g, Tri<cx<T>*> Q, const cx
 }
 
 // ------------------------------------------------------------------ row pairs
-template <typename T, typename Tm>
+// DOT: the CG variant, alpha = rho / (n sum g . K g) as in the 2D row pass.
+template <typename T, typename Tm, bool DOT>
 __global__ void __launch_bounds__(256) k3_row_apply(Geo<T> g, Tri<cx<T>*> G, Tri<const Tm*> m,
                                                     const Tm* __restrict__ rr, Tri<cx<T>*> Q,
-                                                    const SolveState* __restrict__ st) {
+                                                    SolveState* st) {
   if (st && st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
@@ -363,6 +347,7 @@ __global__ void __launch_bounds__(256) k3_row_apply(Geo<T> g, Tri<cx<T>*> G, Tri
   load_rows3(v, G, r, H);
   fft_canon<+1, 3, true>(v, sl, 1, r.j, g.lnx, g.twx);
   const size_t o0 = r.y0 * N, o1 = r.y1 * N;
+  DotAcc<T> gkg;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = r.j + s * r.N8;
@@ -371,6 +356,7 @@ __global__ void __launch_bounds__(256) k3_row_apply(Geo<T> g, Tri<cx<T>*> G, Tri
       const T ax = (T)m.v[0][o0 + x], ay = (T)m.v[1][o0 + x], az = (T)m.v[2][o0 + x];
       const T rv = (T)rr[o0 + x];
       const T mg = ax * gx + ay * gy + az * gz;
+      if (DOT) gkg.add_prod(mg * mg + rv * (gx * gx + gy * gy + gz * gz), (T)1);
       v[0][s] = cmk<T>(ax * mg + rv * gx, ay * mg + rv * gy);
       v[2][s].x = az * mg + rv * gz;
     }
@@ -379,6 +365,7 @@ __global__ void __launch_bounds__(256) k3_row_apply(Geo<T> g, Tri<cx<T>*> G, Tri
       const T ax = (T)m.v[0][o1 + x], ay = (T)m.v[1][o1 + x], az = (T)m.v[2][o1 + x];
       const T rv = (T)rr[o1 + x];
       const T mg = ax * gx + ay * gy + az * gz;
+      if (DOT) gkg.add_prod(mg * mg + rv * (gx * gx + gy * gy + gz * gz), (T)1);
       v[1][s] = cmk<T>(ax * mg + rv * gx, ay * mg + rv * gy);
       v[2][s].y = az * mg + rv * gz;
     }
@@ -388,6 +375,11 @@ __global__ void __launch_bounds__(256) k3_row_apply(Geo<T> g, Tri<cx<T>*> G, Tri
   const Tri<cx<T>*> A = {{Q.v[0] + s0, Q.v[0] + s1, Q.v[2] + s0}};
   const Tri<cx<T>*> B = {{Q.v[1] + s0, Q.v[1] + s1, Q.v[2] + s1}};
   store_pairs_r2c<3>(v, sl, r.j, N, H, A, B);
+  if (DOT) {
+    double a1[1] = {gkg.value()}, t1[1];
+    if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0)
+      cg_alpha_from(st, t1[0], (double)g.nx * (double)g.ny * (double)g.nz);
+  }
 }
 
 // Activation (rank-one phi1 form of eq. m_activation_discrete) and relaxation
@@ -725,8 +717,11 @@ void z_div(const Geo<T>& g, int mode, Tri<cx<T>*> Q, const cx<T>* d, const cx<T>
 }
 template <typename T, typename Tm>
 void row_apply3(const Geo<T>& g, Tri<cx<T>*> G, Tri<const Tm*> m, const Tm* r, Tri<cx<T>*> Q,
-                const SolveState* st, cudaStream_t s) {
-  k3_row_apply<T, Tm><<<row3_ctas(g), row3_threads(g), row3_smem(g), s>>>(g, G, m, r, Q, st);
+                SolveState* st, cudaStream_t s) {
+  if (st)
+    k3_row_apply<T, Tm, true><<<row3_ctas(g), row3_threads(g), row3_smem(g), s>>>(g, G, m, r, Q, st);
+  else
+    k3_row_apply<T, Tm, false><<<row3_ctas(g), row3_threads(g), row3_smem(g), s>>>(g, G, m, r, Q, st);
 }
 template <typename T>
 void row_split3(const Geo<T>& g, Tri<cx<T>*> G, Tri<const T*> m, const T* r, Tri<T*> mo,
@@ -774,7 +769,8 @@ void set_smem_limits_3d_t() {
 }
 template <typename T, typename Tm>
 void set_smem_limits_row3() {
-  allow_smem(k3_row_apply<T, Tm>);
+  allow_smem(k3_row_apply<T, Tm, false>);
+  allow_smem(k3_row_apply<T, Tm, true>);
 }
 template <typename T, typename Tin>
 void set_smem_limits_zgrad() {

@@ -12,7 +12,7 @@ template void z_fwd_project<df64>(const Geo<df64>&, const cx<df64>*, cx<df64>*, 
 template void z_div<df64>(const Geo<df64>&, int, Tri<cx<df64>*>, const cx<df64>*, const cx<df64>*,
                           cx<df64>*, cx<float>*, cx<float>*, SolveState*, cudaStream_t);
 template void row_apply3<df64, float>(const Geo<df64>&, Tri<cx<df64>*>, Tri<const float*>,
-                                      const float*, Tri<cx<df64>*>, const SolveState*,
+                                      const float*, Tri<cx<df64>*>, SolveState*,
                                       cudaStream_t);
 
 void set_smem_limits_3d_df() {

@@ -18,7 +18,7 @@ template void z_div<float>(const Geo<float>&, int, Tri<cx<float>*>, const cx<flo
                            const cx<float>*, cx<float>*, cx<float>*, cx<float>*, SolveState*,
                            cudaStream_t);
 template void row_apply3<float, float>(const Geo<float>&, Tri<cx<float>*>, Tri<const float*>,
-                                       const float*, Tri<cx<float>*>, const SolveState*,
+                                       const float*, Tri<cx<float>*>, SolveState*,
                                        cudaStream_t);
 template void row_split3<float>(const Geo<float>&, Tri<cx<float>*>, Tri<const float*>, const float*,
                                 Tri<float*>, SplitCoef, SolveState*, cudaStream_t);

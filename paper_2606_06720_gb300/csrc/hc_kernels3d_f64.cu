@@ -14,10 +14,10 @@ template void z_div<double>(const Geo<double>&, int, Tri<cx<double>*>, const cx<
                             const cx<double>*, cx<double>*, cx<float>*, cx<float>*, SolveState*,
                             cudaStream_t);
 template void row_apply3<double, double>(const Geo<double>&, Tri<cx<double>*>, Tri<const double*>,
-                                         const double*, Tri<cx<double>*>, const SolveState*,
+                                         const double*, Tri<cx<double>*>, SolveState*,
                                          cudaStream_t);
 template void row_apply3<double, float>(const Geo<double>&, Tri<cx<double>*>, Tri<const float*>,
-                                        const float*, Tri<cx<double>*>, const SolveState*,
+                                        const float*, Tri<cx<double>*>, SolveState*,
                                         cudaStream_t);
 template void row_split3<double>(const Geo<double>&, Tri<cx<double>*>, Tri<const double*>, const double*,
                                 Tri<double*>, SplitCoef, SolveState*, cudaStream_t);

@@ -11,7 +11,7 @@ template void row_c2r<df64>(const Geo<df64>&, const cx<df64>*, const cx<df64>*, 
                             SolveState*, int, cudaStream_t);
 template void row_apply<df64, float>(const Geo<df64>&, const cx<df64>*, const cx<df64>*,
                                      const float*, const float*, const float*, cx<df64>*,
-                                     cx<df64>*, const SolveState*, cudaStream_t);
+                                     cx<df64>*, SolveState*, cudaStream_t);
 template void col_fwd<df64>(const Geo<df64>&, const cx<df64>*, const cx<df64>*, cx<df64>*,
                             cx<df64>*, int, int, SolveState*, cudaStream_t);
 template void col_inv<df64>(const Geo<df64>&, const cx<df64>*, cx<df64>*, df64, cudaStream_t);
@@ -30,7 +30,8 @@ template void convert<double, df64>(const df64*, double*, size_t, cudaStream_t);
 void set_smem_limits_df() {
   allow_smem(k_row_r2c<df64>);
   allow_smem(k_row_c2r<df64>);
-  allow_smem(k_row_apply<df64, float>);
+  allow_smem(k_row_apply<df64, float, false>);
+  allow_smem(k_row_apply<df64, float, true>);
   allow_smem(k_col_fwd<df64, 1>);
   allow_smem(k_col_fwd<df64, 2>);
   allow_smem(k_col_inv<df64>);

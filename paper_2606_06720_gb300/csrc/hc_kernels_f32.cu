@@ -9,7 +9,7 @@ template void row_c2r<float>(const Geo<float>&, const cx<float>*, const cx<float
                              SolveState*, int, cudaStream_t);
 template void row_apply<float, float>(const Geo<float>&, const cx<float>*, const cx<float>*,
                                       const float*, const float*, const float*, cx<float>*,
-                                      cx<float>*, const SolveState*, cudaStream_t);
+                                      cx<float>*, SolveState*, cudaStream_t);
 template void row_split<float>(const Geo<float>&, const cx<float>*, const cx<float>*, const float*,
                                const float*, const float*, cx<float>*, cx<float>*, SplitCoef, SolveState*,
                                cudaStream_t);

@@ -9,10 +9,10 @@ template void row_c2r<double>(const Geo<double>&, const cx<double>*, const cx<do
                               double*, SolveState*, int, cudaStream_t);
 template void row_apply<double, double>(const Geo<double>&, const cx<double>*, const cx<double>*,
                                         const double*, const double*, const double*, cx<double>*,
-                                        cx<double>*, const SolveState*, cudaStream_t);
+                                        cx<double>*, SolveState*, cudaStream_t);
 template void row_apply<double, float>(const Geo<double>&, const cx<double>*, const cx<double>*,
                                        const float*, const float*, const float*, cx<double>*,
-                                       cx<double>*, const SolveState*, cudaStream_t);
+                                       cx<double>*, SolveState*, cudaStream_t);
 template void row_split<double>(const Geo<double>&, const cx<double>*, const cx<double>*, const double*,
                                const double*, const double*, cx<double>*, cx<double>*, SplitCoef, SolveState*,
                                cudaStream_t);
@@ -50,7 +50,8 @@ template void spec_norm2<double>(const Geo<double>&, const cx<double>*, SolveSta
 void set_smem_limits_f64() {
   set_smem_limits_t<double>();
   set_smem_limits_grad<double, double>();
-  allow_smem(k_row_apply<double, float>);
+  allow_smem(k_row_apply<double, float, false>);
+  allow_smem(k_row_apply<double, float, true>);
 }
 
 __global__ void k_set_config(SolveState* st, SolveConfig c) {

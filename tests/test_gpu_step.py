@@ -213,8 +213,8 @@ def test_tuning_changes_only_summation_order(hc):
         for bad in [((3, 1), (1, 1)), ((64, 1), (1, 1)), ((1, 1), (1, 1024)), ((1, 0), (1, 1))]:
             with pytest.raises(hc.HuCaiError):
                 s.set_tuning(list(bad[0]), list(bad[1]), [0, 0])
-        with pytest.raises(hc.HuCaiError):  # FP32 tile of 8 bytes: no 16-byte cp.async
-            s.set_tuning([1, 1], [1, 1], [1, 0])
+        with pytest.raises(hc.HuCaiError):  # col_pipe is 0 or 1
+            s.set_tuning([2, 1], [1, 1], [2, 0])
         assert s.get_tuning()["col_tile"] == [8, 4]
     for m, p in outs[1:]:
         assert rel_l2(m, outs[0][0]) < 1e-12 and rel_l2(p, outs[0][1]) < 1e-11
@@ -241,12 +241,14 @@ def test_pipelined_column_passes_match_plain_ones(hc, precision):
     one-tile-per-CTA passes (to the rounding of regrouped reductions)."""
     w = W.source_sink_2d(512, steps=3)
     outs = []
-    for pipe in ((0, 0), (1, 1)):
+    # (FP32 tile, pipe): 16-byte copies, and one FP32 column with 8-byte copies
+    for col, pipe in (((2, 1), (0, 0)), ((2, 1), (1, 1)), ((1, 1), (1, 0))):
         with make_solver(hc, w, precision) as s:
             t = s.get_tuning()
-            s.set_tuning([2, 1], t["row_rows"], list(pipe))
+            s.set_tuning(list(col), t["row_rows"], list(pipe))
             st = s.step(3)
             assert st.status == 0 and st.rel_residual <= w.cg_rtol
             outs.append((s.get_m(), s.get_p()))
-    assert rel_l2(outs[1][0], outs[0][0]) < 1e-6
-    assert rel_l2(outs[1][1], outs[0][1]) < 1e-6
+    for m, p in outs[1:]:
+        assert rel_l2(m, outs[0][0]) < 1e-6
+        assert rel_l2(p, outs[0][1]) < 1e-6
