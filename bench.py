@@ -52,6 +52,9 @@ BYTES_PER_POINT = {
         "split_row": 24,   # read Gx, Gy, mx, my; write Mx, My    6 F4
         "split_heat": 16,  # read Mx, My; write Mx, My            4 F4
         "split_c2r": 16,   # read Mx, My; write mx, my            4 F4
+        "first_grad": 16,  # read p64 (F8); write Gx, Gy (2 F4)
+        "first_apply": 28, # read Gx, Gy, mx, my, r; write Qx, Qy  7 F4
+        "first_div": 20,   # read Qx, Qy, b32; write r32, delta   5 F4
     },
     "fp64": {
         "cg_grad": 40, "cg_apply": 56, "cg_div": 24, "cg_update": 48, "res_grad": 24,
@@ -79,6 +82,9 @@ BYTES_PER_POINT_3D = {
     "split_row": 36,   # read 3 grads, 3 m; write 3 m          9 F4
     "split_heat": 24,  # y diffusion of m in place             6 F4
     "split_c2r": 24,   # z diffusion of m in place + sum |m|^2 6 F4
+    "first_grad": 20,  # read p64 (F8); write 3 F4
+    "first_apply": 40, # as cg_apply
+    "first_div": 24,   # read Q0..Q2, b32; write r32, delta  6 F4
 }
 
 # DRAM bytes (read + write) per launch measured by ncu for the 2048^2 refined
@@ -113,7 +119,8 @@ def fft_flops_per_point(kernel: str, nx: int, ny: int) -> float:
         "cg_apply": 2 * row1 + 9, "res_apply": 2 * row1 + 9,
         "cg_div": col2 + 6, "res_div": col2 + 10,
         "cg_update": 10, "split_row": 2 * row1 + 30, "split_heat": 2 * col2 + 3,
-        "split_c2r": row1 + 2,
+        "split_c2r": row1 + 2, "first_grad": col2 + 2, "first_apply": 2 * row1 + 9,
+        "first_div": col2 + 10,
     }[kernel]
 
 
@@ -129,6 +136,7 @@ def fft_flops_per_point_3d(kernel: str, nx: int, ny: int, nz: int) -> float:
         "cg_apply": 15 * lx + 11, "res_apply": 15 * lx + 11,
         "cg_div": 7.5 * lz + 8, "res_div": 7.5 * lz + 12, "cg_update": 10,
         "split_row": 30 * lx + 45, "split_heat": 15 * ly + 3, "split_c2r": 15 * lz + 5,
+        "first_grad": 7.5 * lz + 3, "first_apply": 15 * lx + 11, "first_div": 7.5 * lz + 12,
     }[kernel]
 
 
@@ -398,10 +406,11 @@ def run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src) -
     npts = w.npts
     it = st.total_cg_iters / K3
     sw = st.total_sweeps / K3
+    r64 = sw + 1 - st.total_first_fp32 / K3  # FP64 residuals per step
     counts = {"cg_grad": it, "cg_ypass": 2 * it, "cg_apply": it, "cg_div": it, "cg_update": it,
-              "res_grad": sw + 1, "res_ypass": 2 * (sw + 1), "res_apply": sw + 1,
-              "res_div": sw + 1, "split_grad": 1, "split_row": 1, "split_heat": 1,
-              "split_c2r": 1}
+              "res_grad": r64, "res_ypass": 2 * r64, "res_apply": r64, "res_div": r64,
+              "split_grad": 1, "split_row": 1, "split_heat": 1, "split_c2r": 1,
+              "first_grad": 1, "first_apply": 1, "first_div": 1}
     kernels = kernel_table(s, counts, BYTES_PER_POINT_3D,
                            lambda k: fft_flops_per_point_3d(k, *w.n),
                            FP64_KERNELS["fp32_refined"], npts, max(3, args.kernel_reps // 3),
@@ -417,6 +426,7 @@ def run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src) -
                         "minus mean, m0~U[0,0.5] seed 0, c=25 D=0.03 gamma=0.75 dt=5e-4; "
                         "FP32 + FP64 refinement, cg_rtol 1e-8" % args.n3d,
             "cg_iters_per_step": it, "refine_sweeps_per_step": sw,
+            "fp64_residuals_per_step": r64,
             "rel_residual_last_step": st.rel_residual,
             "roofline_fp32": {"bound": "hbm", "kernel": dom, "achieved": dk["alg_GBs"],
                               "peak": hbm_peak, "unit": "GB/s", "frac": dk["frac"],
@@ -503,10 +513,12 @@ def run_gb300(args) -> None:
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    first_per_step = st.total_first_fp32 / K
+    res64 = sweeps_per_step + 1 - first_per_step  # FP64 residuals per step
     counts = {"cg_grad": iters_per_step, "cg_apply": iters_per_step, "cg_div": iters_per_step,
-              "cg_update": iters_per_step, "res_grad": sweeps_per_step + 1,
-              "res_apply": sweeps_per_step + 1, "res_div": sweeps_per_step + 1, "split_grad": 1,
-              "split_row": 1, "split_heat": 1, "split_c2r": 1}
+              "cg_update": iters_per_step, "res_grad": res64, "res_apply": res64, "res_div": res64,
+              "split_grad": 1, "split_row": 1, "split_heat": 1, "split_c2r": 1,
+              "first_grad": 1, "first_apply": 1, "first_div": 1}
     kernels = kernel_table(s, counts, BYTES_PER_POINT["fp32_refined"],
                            lambda k: fft_flops_per_point(k, *w.n), FP64_KERNELS["fp32_refined"],
                            npts, args.kernel_reps, hbm_peak)
@@ -748,6 +760,7 @@ def run_gb300(args) -> None:
             "clocks": clk.summary(),
             "hbm_gbs": bytes_step * K / (ms / 1e3) / 1e9,
             "cg_iters_per_step": iters_per_step, "refine_sweeps_per_step": sweeps_per_step,
+            "fp64_residuals_per_step": res64,
             "cg_iterations_per_s": world * iters_per_step * K / (ms_max / 1e3),
             "rel_residual_last_step": st.rel_residual,
             "fp64_plain": fp64, "refined_df": dfv, "sweep": sweep, "adjoint": adjv,

@@ -84,11 +84,17 @@ typedef struct {
   int use_graph;          /* 1: each step runs as one CUDA graph with device-side loop control; 0: host loop */
   void* stream;           /* cudaStream_t the context launches on */
   int diagnostics;        /* 1: every step also computes the energy and Delta m of Section 2.5 (see hc_step_stats) */
+  int fp64_first_residual; /* refined modes.  0 (default): when the warm start is off by more than
+                              1e-5 ||S||, the first refinement sweep solves for S - A p^k evaluated
+                              in FP32 (a low-precision first solve, as mixed-precision iterative
+                              refinement starts); the FP64 residual after it removes that
+                              evaluation's error.  1: every sweep starts from an FP64 residual.
+                              Either way every convergence test uses an FP64 residual. */
 } hc_params;
 
 typedef struct {
   int cg_iters;        /* CG iterations of the last step's pressure solve (summed over sweeps) */
-  int refine_sweeps;   /* refined mode: inner solves run; plain mode: 0 */
+  int refine_sweeps;   /* refined mode: inner solves run (FP64 residuals: refine_sweeps + 1 - first_sweep_fp32); plain mode: 0 */
   double rel_residual; /* ||S - A p||_2 / ||S||_2 at exit: FP64-evaluated in refined mode, recursive in plain mode */
   double kappa;        /* preconditioner constant used */
   int status;          /* HC_OK, HC_ENOCONV or HC_ENONFINITE for that step */
@@ -105,6 +111,8 @@ typedef struct {
   int energy_valid;    /* 0 when the energy of the starting m is not known (diagnostics were off when it was made) */
   int stop_reason;     /* hc_run: HC_STOP_*; hc_step: HC_STOP_NONE */
   long long energy_step; /* hc_run with HC_STOP_ENERGY: 0-based index, within the call, of the step whose result did not lower the energy; else -1 */
+  int first_sweep_fp32;  /* refined modes: the step's first sweep started from the FP32 residual */
+  long long total_first_fp32; /* such steps summed over the call */
 } hc_step_stats;
 
 /* Bytes of device workspace hc_create needs for this grid and precision. */
@@ -225,7 +233,10 @@ enum {
   HC_K_SPLIT_C2R = 10, /* row pass: C2R to physical m, sum |m|^2 */
   HC_K_CG_YPASS = 11,  /* 3D only: y pass (FFT of 3 fields) of the inner CG */
   HC_K_RES_YPASS = 12, /* 3D only: y pass of the refinement residual */
-  HC_K_COUNT = 13
+  HC_K_FIRST_GRAD = 13,  /* refined: the FP32 first residual's gradient pass (from p64) */
+  HC_K_FIRST_APPLY = 14, /* refined: its row pass (2D) / row-pair pass (3D) */
+  HC_K_FIRST_DIV = 15,   /* refined: its divergence pass, r32 = b32 - q and the inner-CG start */
+  HC_K_COUNT = 16
 };
 
 /* Launch one step kernel `reps` times back to back on the context's current

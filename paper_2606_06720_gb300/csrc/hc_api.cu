@@ -51,6 +51,12 @@ int ilog2(int v) {
 
 }  // namespace
 
+// Conditional handles of one step chain: the CG loop of the refinement sweeps
+// (or of plain PCG), the refinement loop, and the first (FP32-started) inner loop.
+struct Handles {
+  cudaGraphConditionalHandle inner = 0, outer = 0, first = 0;
+};
+
 struct hc_ctx {
   hc_grid grid;
   hc_params prm;
@@ -78,6 +84,7 @@ struct hc_ctx {
   cx<double>* d64;          // CG direction (plain mode)
   cx<double>* q64;          // A d (plain mode)
   cx<double>* G64;          // dim spectra: gradient / flux / m scratch (FP64)
+  cx<float>* b32;           // refined: FP32 copy of the projected source spectrum
   cx<float>* r32;           // refined: inner residual
   cx<float>* d32;           // refined: inner direction
   cx<float>* q32;           // refined: A d
@@ -114,12 +121,13 @@ struct hc_ctx {
   // legacy default stream), launched on `stream`
   cudaStream_t cap_stream;
   cudaGraphExec_t gexec;
-  cudaGraphConditionalHandle h_own[2];  // handles of the context's own graph
+  Handles h_own;                        // handles of the context's own graph
   int batch_handles;                    // 1 while st holds a batch graph's handles
   bool graph_ready;
   // hc_run: the step wrapped in a device-gated IF node, diagnostics on
   cudaGraphExec_t gexec_run;
-  cudaGraphConditionalHandle h_run[3];  // inner, outer, gate
+  Handles h_run;                        // handles of the run graph's step chain
+  cudaGraphConditionalHandle h_gate;
   bool run_graph_ready;
   int force_diag;                       // 1 while hc_run runs (diagnostics forced on)
   int graph_nodes_fixed, graph_nodes_body, graph_nodes_outer;
@@ -189,11 +197,12 @@ void layout(hc_ctx* c, Layout& L) {
   if (!c->refined) {
     c->d64 = L.take<cx<double>>(S64);
     c->q64 = L.take<cx<double>>(S64);
-    c->r32 = c->d32 = c->q32 = c->x32 = c->G32 = nullptr;
+    c->b32 = c->r32 = c->d32 = c->q32 = c->x32 = c->G32 = nullptr;
     for (int k = 0; k < d; ++k) c->m[k] = L.take<double>(sizeof(double) * n);
     c->rf = L.take<double>(sizeof(double) * n);
   } else {
     c->d64 = c->q64 = nullptr;
+    c->b32 = L.take<cx<float>>(S32);
     c->r32 = L.take<cx<float>>(S32);
     c->d32 = L.take<cx<float>>(S32);
     c->q32 = L.take<cx<float>>(S32);
@@ -483,6 +492,8 @@ int push_config(hc_ctx* c) {
   cfg.e_coef[1] = h * c->prm.c * c->prm.c / 2.0;
   cfg.e_coef[2] = c->prm.gamma != 0.0 ? h / (2.0 * c->prm.gamma) : 0.0;
   cfg.dt = c->prm.dt;
+  // refined: FP32 first sweep when the warm start is off by more than 1e-5 ||S||
+  cfg.first32_min2 = (c->refined && !c->prm.fp64_first_residual) ? 1e-10 : 0.0;
   cfg.dim = c->dim;
   cfg.diag = diag_on(c) ? 1 : 0;
   cfg.outer_thresh2_rel = c->prm.cg_rtol * c->prm.cg_rtol;
@@ -569,6 +580,41 @@ void plain_iter(hc_ctx* c) {
                       c->stream);
   hc::cg_update<double>(g, c->p64, c->r64, c->d64, c->q64, c->st, c->stream);
   c->launches += 4;
+}
+
+// Refined modes: S - A p^k in FP32 from the warm start, the first inner
+// solve's right-hand side (resid_first_init decides whether it is used).
+void first_resid32(hc_ctx* c) {
+  auto& g = c->gf;
+  if (c->dim == 3) {
+    auto Gt = tri(c->G32, c->ns);
+    if (c->df)
+      hc::z_grad<float, df64>(g, hc::CG_PLAIN, reinterpret_cast<cx<df64>*>(c->p64), nullptr, nullptr,
+                              nullptr, Gt, c->st, 0, c->stream);
+    else
+      hc::z_grad<float, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gt, c->st, 0,
+                                c->stream);
+    hc::axis_fft<float>(g, 1, +1, 3, Gt, Gt, 1.0f, c->stream);
+    hc::row_apply3<float, float>(g, Gt, mtri<float>(c), (const float*)c->rf, Gt, nullptr, c->stream);
+    hc::axis_fft<float>(g, 1, -1, 3, Gt, Gt, 1.0f, c->stream);
+    hc::z_div<float>(g, hc::CD_RESID_FIRST, Gt, nullptr, c->b32, nullptr, c->r32, c->x32, c->st,
+                     c->stream);
+    c->launches += 5;
+    return;
+  }
+  cx<float>* Gx = c->G32;
+  cx<float>* Gy = c->G32 + c->ns;
+  if (c->df)
+    hc::col_grad<float, df64>(g, hc::CG_PLAIN, reinterpret_cast<cx<df64>*>(c->p64), nullptr, nullptr,
+                              nullptr, Gx, Gy, c->st, 0, c->stream);
+  else
+    hc::col_grad<float, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy, c->st, 0,
+                                c->stream);
+  hc::row_apply<float, float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1],
+                              (const float*)c->rf, Gx, Gy, nullptr, c->stream);
+  hc::col_div<float>(g, hc::CD_RESID_FIRST, Gx, Gy, nullptr, c->b32, nullptr, c->r32, c->x32, c->st,
+                     c->stream);
+  c->launches += 3;
 }
 
 // FP64 residual S - A p64 (after p64 += delta) and inner-CG initialisation.
@@ -795,9 +841,16 @@ int step_host(hc_ctx* c) {
     int rc = run_cg_host(c, false);
     if (rc) return rc;
   } else {
+    first_resid32(c);
+    int rc = read_state(c);
+    if (rc) return rc;
+    if (!c->st_host->done) {
+      rc = run_cg_host(c, true);
+      if (rc) return rc;
+    }
     for (int sweep = 0;; ++sweep) {
       refined_resid(c);
-      int rc = read_state(c);
+      rc = read_state(c);
       if (rc) return rc;
       if (c->st_host->outer_done) break;
       rc = run_cg_host(c, true);
@@ -824,72 +877,88 @@ int step_host(hc_ctx* c) {
 // on what `target` already holds: the prefix kernels, the loop node(s), the
 // suffix kernels.  Returns the chain's conditional handles.  c->stream must be
 // a non-default stream that is not capturing.
-int build_chain(hc_ctx* c, cudaGraph_t target, cudaGraphConditionalHandle* hin,
-                cudaGraphConditionalHandle* hout) {
+//   plain:   step_begin, initial residual, WHILE(inner){CG}, split, step_end
+//   refined: step_begin, FP32 residual, WHILE(first){CG},
+//            WHILE(outer){FP64 residual, WHILE(inner){CG}}, split, step_end
+int build_chain(hc_ctx* c, cudaGraph_t target, Handles* h) {
   cudaStream_t s = c->stream;
-  cudaGraphConditionalHandle h_inner = 0, h_outer = 0;
-  CU(cudaStreamBeginCaptureToGraph(s, target, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  hc::step_begin(c->st, (int)c->n, s);
-  if (!c->refined) plain_init(c);
-  // the chain's current tail, before leaving capture
+  Handles hh;
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  CU(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
-  std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
-  cudaGraph_t same = target;
-  CU(cudaStreamEndCapture(s, &same));
+  // the tail of the capture running on s, which then ends
+  auto end_capture = [&](cudaGraph_t g, std::vector<cudaGraphNode_t>& tail) -> int {
+    CU(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+    tail.assign(deps, deps + ndeps);
+    cudaGraph_t same = g;
+    CU(cudaStreamEndCapture(s, &same));
+    return HC_OK;
+  };
+  // a WHILE node after `after` in graph g; returns its body
+  auto add_while = [&](cudaGraph_t g, const std::vector<cudaGraphNode_t>& after,
+                       cudaGraphConditionalHandle* hd, cudaGraphNode_t* node,
+                       cudaGraph_t* body) -> int {
+    CU(cudaGraphConditionalHandleCreate(hd, g, 0, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = *hd;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    CU(cudaGraphAddNode(node, g, after.data(), nullptr, after.size(), &p));
+    *body = p.conditional.phGraph_out[0];
+    return HC_OK;
+  };
+  auto capture_iter = [&](cudaGraph_t body) -> int {
+    CU(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    if (c->refined)
+      refined_iter(c);
+    else
+      plain_iter(c);
+    cudaGraph_t same = body;
+    CU(cudaStreamEndCapture(s, &same));
+    return HC_OK;
+  };
+  std::vector<cudaGraphNode_t> tail;
+  CU(cudaStreamBeginCaptureToGraph(s, target, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  hc::step_begin(c->st, (int)c->n, s);
+  if (c->refined)
+    first_resid32(c);
+  else
+    plain_init(c);
+  int rc = end_capture(target, tail);
+  if (rc) return rc;
   cudaGraphNode_t loop_node;
   cudaGraph_t body;
   if (c->refined) {
-    CU(cudaGraphConditionalHandleCreate(&h_outer, target, 0, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams op = {};
-    op.type = cudaGraphNodeTypeConditional;
-    op.conditional.handle = h_outer;
-    op.conditional.type = cudaGraphCondTypeWhile;
-    op.conditional.size = 1;
-    CU(cudaGraphAddNode(&loop_node, target, tail.data(), nullptr, tail.size(), &op));
-    cudaGraph_t obody = op.conditional.phGraph_out[0];
+    // the first inner loop, then the refinement loop with its own inner loop
+    cudaGraphNode_t first_node;
+    rc = add_while(target, tail, &hh.first, &first_node, &body);
+    if (!rc) rc = capture_iter(body);
+    if (rc) return rc;
+    cudaGraph_t obody;
+    rc = add_while(target, std::vector<cudaGraphNode_t>{first_node}, &hh.outer, &loop_node, &obody);
+    if (rc) return rc;
     CU(cudaStreamBeginCaptureToGraph(s, obody, nullptr, nullptr, 0,
                                      cudaStreamCaptureModeThreadLocal));
     refined_resid(c);
-    CU(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
-    std::vector<cudaGraphNode_t> otail(deps, deps + ndeps);
-    cudaGraph_t same_o = obody;
-    CU(cudaStreamEndCapture(s, &same_o));
-    CU(cudaGraphConditionalHandleCreate(&h_inner, obody, 0, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams ip = {};
-    ip.type = cudaGraphNodeTypeConditional;
-    ip.conditional.handle = h_inner;
-    ip.conditional.type = cudaGraphCondTypeWhile;
-    ip.conditional.size = 1;
+    std::vector<cudaGraphNode_t> otail;
+    rc = end_capture(obody, otail);
+    if (rc) return rc;
     cudaGraphNode_t inode;
-    CU(cudaGraphAddNode(&inode, obody, otail.data(), nullptr, otail.size(), &ip));
-    body = ip.conditional.phGraph_out[0];
+    rc = add_while(obody, otail, &hh.inner, &inode, &body);
   } else {
-    CU(cudaGraphConditionalHandleCreate(&h_inner, target, 0, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams ip = {};
-    ip.type = cudaGraphNodeTypeConditional;
-    ip.conditional.handle = h_inner;
-    ip.conditional.type = cudaGraphCondTypeWhile;
-    ip.conditional.size = 1;
-    CU(cudaGraphAddNode(&loop_node, target, tail.data(), nullptr, tail.size(), &ip));
-    body = ip.conditional.phGraph_out[0];
+    rc = add_while(target, tail, &hh.inner, &loop_node, &body);
   }
-  CU(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  if (c->refined)
-    refined_iter(c);
-  else
-    plain_iter(c);
-  cudaGraph_t same_b = body;
-  CU(cudaStreamEndCapture(s, &same_b));
+  if (!rc) rc = capture_iter(body);
+  if (rc) return rc;
   CU(cudaStreamBeginCaptureToGraph(s, target, &loop_node, nullptr, 1,
                                    cudaStreamCaptureModeThreadLocal));
   split_step(c);
   hc::step_end(c->st, c->refined, s);
+  cudaGraph_t same = target;
   CU(cudaStreamEndCapture(s, &same));
-  *hin = h_inner;
-  *hout = h_outer;
+  *h = hh;
   return HC_OK;
 }
 
@@ -902,19 +971,29 @@ void abort_capture(cudaStream_t s) {
   cudaGetLastError();
 }
 
-// Kernels of one step's graph: fixed nodes (step_begin, [plain: initial
-// residual], split step, step_end), one CG iteration, one refinement residual.
+// Kernels of one step's graph: fixed nodes (step_begin, the initial residual
+// (plain FP64, or the refined modes' FP32 one), split step, step_end), one CG
+// iteration, one FP64 refinement residual.
 void set_node_counts(hc_ctx* c) {
   const int split = c->dim == 3 ? 5 : 4, resid = c->dim == 3 ? 5 : 3;
-  c->graph_nodes_fixed = 1 + (c->refined ? 0 : resid) + split + 1;
+  c->graph_nodes_fixed = 1 + resid + split + 1;
   c->graph_nodes_body = c->dim == 3 ? 6 : 4;
   c->graph_nodes_outer = resid;
 }
 
+// Kernels that ran in graph launches, from the accumulated step statistics.
+long long graph_kernel_count(const hc_ctx* c, const hc::SolveState& h) {
+  long long n = (long long)c->graph_nodes_fixed * h.acc_steps +
+                (long long)c->graph_nodes_body * h.acc_iters;
+  // FP64 residuals: one per inner solve not started in FP32, plus the final check
+  if (c->refined)
+    n += (long long)c->graph_nodes_outer * (h.acc_sweeps - h.acc_first + h.acc_steps);
+  return n;
+}
+
 // Device handles the kernels drive: the context's own graph or a batch graph.
-int use_handles(hc_ctx* c, cudaGraphConditionalHandle hin, cudaGraphConditionalHandle hout,
-                cudaGraphConditionalHandle hgate = 0) {
-  unsigned long long v[3] = {hin, hout, hgate};
+int use_handles(hc_ctx* c, const Handles& h, cudaGraphConditionalHandle hgate = 0) {
+  unsigned long long v[4] = {h.inner, h.outer, hgate, h.first};
   CU(cudaMemcpy(&c->st->h_inner, v, sizeof(v), cudaMemcpyHostToDevice));
   return HC_OK;
 }
@@ -936,8 +1015,8 @@ int build_graph(hc_ctx* c) {
   cudaStream_t keep = c->stream;
   long long before = c->launches;
   c->stream = c->cap_stream;
-  cudaGraphConditionalHandle hin = 0, hout = 0;
-  int rc = build_chain(c, graph, &hin, &hout);
+  Handles hh;
+  int rc = build_chain(c, graph, &hh);
   c->stream = keep;
   c->launches = before;  // capture launched nothing
   if (rc) {
@@ -949,8 +1028,7 @@ int build_graph(hc_ctx* c) {
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __LINE__);
   set_node_counts(c);
-  c->h_own[0] = hin;
-  c->h_own[1] = hout;
+  c->h_own = hh;
   c->graph_ready = true;
   return HC_OK;
 }
@@ -966,7 +1044,8 @@ int build_run_graph(hc_ctx* c) {
   cudaStream_t keep = c->stream;
   const long long before = c->launches;
   c->stream = c->cap_stream;
-  cudaGraphConditionalHandle hin = 0, hout = 0, hgate = 0;
+  Handles hh;
+  cudaGraphConditionalHandle hgate = 0;
   auto capture = [&]() -> int {
     cudaStream_t s = c->stream;
     CU(cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
@@ -987,7 +1066,7 @@ int build_run_graph(hc_ctx* c) {
     ip.conditional.size = 1;
     cudaGraphNode_t node;
     CU(cudaGraphAddNode(&node, graph, tail.data(), nullptr, tail.size(), &ip));
-    return build_chain(c, ip.conditional.phGraph_out[0], &hin, &hout);
+    return build_chain(c, ip.conditional.phGraph_out[0], &hh);
   };
   int rc = capture();
   c->stream = keep;
@@ -1000,9 +1079,8 @@ int build_run_graph(hc_ctx* c) {
   cudaError_t e = cudaGraphInstantiate(&c->gexec_run, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __LINE__);
-  c->h_run[0] = hin;
-  c->h_run[1] = hout;
-  c->h_run[2] = hgate;
+  c->h_run = hh;
+  c->h_gate = hgate;
   c->run_graph_ready = true;
   return HC_OK;
 }
@@ -1043,6 +1121,8 @@ int fill_stats(hc_ctx* c, hc_step_stats* out) {
     out->energy_valid = h.diag ? h.energy_valid : 0;
     out->stop_reason = h.run_mode ? h.stop_reason : HC_STOP_NONE;
     out->energy_step = (h.run_mode && h.stop_reason == HC_STOP_ENERGY) ? h.energy_step : -1;
+    out->first_sweep_fp32 = h.first_used;
+    out->total_first_fp32 = h.acc_first;
   }
   return HC_OK;
 }
@@ -1270,6 +1350,16 @@ int hc_set_source(hc_ctx* c, const double* S, size_t count) {
   CU(cudaMemcpyAsync(c->stage, S, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
   int rc = forward64(c, c->b64, c->st);
   if (rc) return rc;
+  if (c->refined) {  // FP32 copy for the first sweep's residual
+    if (c->df)
+      hc::convert<float, df64>(reinterpret_cast<const df64*>(c->b64), reinterpret_cast<float*>(c->b32),
+                               2 * c->ns, c->stream);
+    else
+      hc::convert<float, double>(reinterpret_cast<const double*>(c->b64),
+                                 reinterpret_cast<float*>(c->b32), 2 * c->ns, c->stream);
+    c->launches += 1;
+    CU(cudaGetLastError());
+  }
   CU(cudaStreamSynchronize(c->stream));
   return HC_OK;
 }
@@ -1389,7 +1479,7 @@ int hc_step(hc_ctx* c, int nsteps, hc_step_stats* last) {
       int rc = build_graph(c);
       if (rc) return rc;
     }
-    int rc = use_handles(c, c->h_own[0], c->h_own[1]);
+    int rc = use_handles(c, c->h_own);
     if (rc) return rc;
     c->batch_handles = 0;
     rc = set_graph_mode(c, 1);
@@ -1399,10 +1489,7 @@ int hc_step(hc_ctx* c, int nsteps, hc_step_stats* last) {
     int rc2 = set_graph_mode(c, 0);
     if (rc) return rc;
     if (rc2) return rc2;
-    const hc::SolveState& h = *c->st_host;
-    // kernels that ran: fixed nodes per step, body per CG iteration, outer body per sweep + 1
-    c->launches += (long long)c->graph_nodes_fixed * nsteps + (long long)c->graph_nodes_body * h.acc_iters;
-    if (c->refined) c->launches += (long long)c->graph_nodes_outer * (h.acc_sweeps + nsteps);
+    c->launches += graph_kernel_count(c, *c->st_host);
   } else {
     for (int k = 0; k < nsteps; ++k) {
       int rc = step_host(c);
@@ -1468,7 +1555,7 @@ int hc_run(hc_ctx* c, int max_steps, double eps, int stop_on_energy, int* steps_
   if (!rc && max_steps > 0) {
     if (c->prm.use_graph) {
       if (!c->run_graph_ready) rc = build_run_graph(c);
-      if (!rc) rc = use_handles(c, c->h_run[0], c->h_run[1], c->h_run[2]);
+      if (!rc) rc = use_handles(c, c->h_run, c->h_gate);
       c->batch_handles = 0;
       if (!rc) rc = set_graph_mode(c, 1);
       int launched = 0;
@@ -1485,11 +1572,8 @@ int hc_run(hc_ctx* c, int max_steps, double eps, int stop_on_energy, int* steps_
       const int rc2 = set_graph_mode(c, 0);
       if (!rc) rc = rc2;
       if (!rc) {
-        const hc::SolveState& h = *c->st_host;
         c->launches += launched;  // gate kernels
-        c->launches += (long long)c->graph_nodes_fixed * h.acc_steps +
-                       (long long)c->graph_nodes_body * h.acc_iters;
-        if (c->refined) c->launches += (long long)c->graph_nodes_outer * (h.acc_sweeps + h.acc_steps);
+        c->launches += graph_kernel_count(c, *c->st_host);
       }
     } else {
       for (int k = 0; k < max_steps && !rc; ++k) {
@@ -1943,7 +2027,7 @@ int hc_adjoint(hc_ctx* c, int nsteps, int every, const double* lamT, double* dc2
 
 struct hc_batch {
   std::vector<hc_ctx*> ctx;
-  std::vector<cudaGraphConditionalHandle> hin, hout;
+  std::vector<Handles> h;
   cudaStream_t stream;
   cudaStream_t cap;
   cudaGraphExec_t exec;
@@ -1963,8 +2047,7 @@ int hc_batch_create(hc_batch** out, hc_ctx* const* ctxs, int count, void* stream
   hc_batch* b = new (std::nothrow) hc_batch;
   if (!b) return HC_ENOMEM;
   b->ctx.assign(ctxs, ctxs + count);
-  b->hin.assign(count, 0);
-  b->hout.assign(count, 0);
+  b->h.assign(count, Handles{});
   b->stream = (cudaStream_t)stream;
   b->cap = nullptr;
   b->ready = false;
@@ -1988,7 +2071,7 @@ int hc_batch_create(hc_batch** out, hc_ctx* const* ctxs, int count, void* stream
     cudaStream_t keep = c->stream;
     long long before = c->launches;
     c->stream = b->cap;
-    int rc = build_chain(c, graph, &b->hin[i], &b->hout[i]);
+    int rc = build_chain(c, graph, &b->h[i]);
     c->stream = keep;
     c->launches = before;
     if (rc) {
@@ -2014,7 +2097,7 @@ int hc_batch_step(hc_batch* b, int nsteps, hc_step_stats* stats) {
   for (int i = 0; i < n; ++i) {
     hc_ctx* c = b->ctx[i];
     CU(cudaStreamSynchronize(c->stream));
-    int rc = use_handles(c, b->hin[i], b->hout[i]);
+    int rc = use_handles(c, b->h[i]);
     if (rc) return rc;
     c->batch_handles = 1;
     rc = set_graph_mode(c, 1);
@@ -2031,8 +2114,7 @@ int hc_batch_step(hc_batch* b, int nsteps, hc_step_stats* stats) {
   for (int i = 0; i < n; ++i) {
     hc_ctx* c = b->ctx[i];
     const hc::SolveState& h = *c->st_host;
-    c->launches += (long long)c->graph_nodes_fixed * nsteps + (long long)c->graph_nodes_body * h.acc_iters;
-    if (c->refined) c->launches += (long long)c->graph_nodes_outer * (h.acc_sweeps + nsteps);
+    c->launches += graph_kernel_count(c, h);
     if (stats) fill_stats(c, &stats[i]);
     if (!first_bad && h.first_bad) first_bad = h.first_bad;
     int rc = set_graph_mode(c, 0);
@@ -2129,7 +2211,8 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
   CU(cudaMemcpyAsync(c->st_time, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
   hc::SolveState* ts = c->st_time;
   const size_t ns = c->ns;
-  if (c->dim == 2 && kernel >= HC_K_CG_YPASS) return HC_EINVAL;
+  if (c->dim == 2 && (kernel == HC_K_CG_YPASS || kernel == HC_K_RES_YPASS)) return HC_EINVAL;
+  if (!c->refined && kernel >= HC_K_FIRST_GRAD) return HC_EINVAL;
   // 3D: the same roles with the 3D kernels; the SPLIT_HEAT / SPLIT_C2R slots
   // time the y and z diffusion passes.  Scratch outputs never alias inputs
   // that a later repetition reads.
@@ -2200,6 +2283,22 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
           break;
         case HC_K_SPLIT_HEAT:
           hc::heat_axis<float>(g, 1, mw, mw, ts, c->stream);
+          break;
+        case HC_K_FIRST_GRAD:
+          if (c->df)
+            hc::z_grad<float, df64>(g, hc::CG_PLAIN, reinterpret_cast<cx<df64>*>(c->p64), nullptr,
+                                    nullptr, nullptr, G, ts, 0, c->stream);
+          else
+            hc::z_grad<float, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, G, ts, 0,
+                                      c->stream);
+          break;
+        case HC_K_FIRST_APPLY:
+          hc::row_apply3<float, float>(g, G, mtri<float>(c), (const float*)c->rf, G, nullptr,
+                                       c->stream);
+          break;
+        case HC_K_FIRST_DIV:
+          hc::z_div<float>(g, hc::CD_RESID_FIRST, G, nullptr, c->b32, nullptr, c->d32, c->q32, ts,
+                           c->stream);
           break;
         default:
           hc::heat_axis<float>(g, 2, mw, mw, ts, c->stream);
@@ -2327,6 +2426,22 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
           break;
         case HC_K_SPLIT_HEAT:  // on scratch: each launch rescales its data
           hc::col_heat<float>(g, c->q32, c->x32, ts, c->stream);
+          break;
+        case HC_K_FIRST_GRAD:
+          if (c->df)
+            hc::col_grad<float, df64>(g, hc::CG_PLAIN, reinterpret_cast<cx<df64>*>(c->p64), nullptr,
+                                      nullptr, nullptr, Gx, Gy, ts, 0, c->stream);
+          else
+            hc::col_grad<float, double>(g, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr, Gx, Gy,
+                                        ts, 0, c->stream);
+          break;
+        case HC_K_FIRST_APPLY:
+          hc::row_apply<float, float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1],
+                                      (const float*)c->rf, c->q32, c->x32, nullptr, c->stream);
+          break;
+        case HC_K_FIRST_DIV:
+          hc::col_div<float>(g, hc::CD_RESID_FIRST, Gx, Gy, nullptr, c->b32, nullptr, c->d32, c->q32,
+                             ts, c->stream);
           break;
         default:
           hc::row_c2r<float>(g, Gx, Gy, (float*)c->q32, (float*)c->x32, ts, 1, c->stream);

@@ -112,6 +112,11 @@ struct SolveState {
   unsigned long long h_inner;  // cudaGraphConditionalHandle of the CG loop
   unsigned long long h_outer;  // cudaGraphConditionalHandle of the refinement loop
   unsigned long long h_gate;   // cudaGraphConditionalHandle of a gated step (hc_run)
+  unsigned long long h_first;  // cudaGraphConditionalHandle of the first (FP32-started) inner loop
+  unsigned long long h_cur;    // the inner-loop handle the CG kernels drive (set by whoever opens it)
+  double first32_min2;       // refined: FP32 first sweep only if ||S - A p||^2 > this * ||S||^2 (0: off)
+  int acc_first;             // FP32 first sweeps summed over the steps since the last reset
+  int first_used;            // the running / last step ran an FP32 first sweep
   unsigned int ticket[8];    // last-CTA tickets, one per reduction site
   // Diagnostics of Section 2.5, accumulated by the split step when diag != 0.
   // A step solves p[m^k] and so evaluates E_h(m^k) with its own pressure.
@@ -148,6 +153,7 @@ struct SolveConfig {
   double mean_r;
   double e_coef[3];          // energy coefficients (see SolveState)
   double dt;
+  double first32_min2;       // see SolveState
   int maxit;
   int max_sweeps;
   int graph_mode;
@@ -223,7 +229,7 @@ struct SplitCoef {
 
 // Column-kernel modes.
 enum ColGradMode { CG_PLAIN = 0, CG_DUPDATE = 1, CG_ADDDELTA = 2 };
-enum ColDivMode { CD_PLAIN = 0, CD_CG = 1, CD_RESID = 2, CD_RESID_REFINE = 3 };
+enum ColDivMode { CD_PLAIN = 0, CD_CG = 1, CD_RESID = 2, CD_RESID_REFINE = 3, CD_RESID_FIRST = 4 };
 
 // ---------------- launchers (defined per precision) ----------------
 // Row pass, forward: physical pair (a, b) -> packed row spectra (A, B). b/B may be null.
@@ -267,6 +273,8 @@ void col_grad(const Geo<T>& g, int mode, cx<Tin>* in, const cx<T>* rvec, cx<T>* 
 //   CD_RESID:        out (r) = b - q; ||r||^2, <r, M^-1 r> -> CG initialisation
 //   CD_RESID_REFINE: as CD_RESID in FP64 plus r32 = float(r), delta = 0, and the
 //                    outer convergence test
+//   CD_RESID_FIRST:  (FP32) r32 = b32 - q, delta = 0, and the start of the first
+//                    inner solve (b = the FP32 copy of S; out unused)
 template <typename T>
 void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const cx<T>* d,
              const cx<T>* b, cx<T>* out, cx<float>* r32, cx<float>* delta32, SolveState* st,

@@ -689,7 +689,33 @@ __device__ __forceinline__ void resid_init(SolveState* st, double r2, double rz)
     st->status = HC_ENONFINITE;
     st->done = 1;
   }
+  st->h_cur = st->h_inner;
   if (st->graph_mode) cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
+}
+
+// Refined modes, first sweep (one thread).  r32 = S - A p^k evaluated in FP32
+// from the warm start: the right-hand side of the first inner solve, as in
+// mixed-precision iterative refinement, whose first solve is a low-precision
+// solve of the original system.  Its error, ~1e-7 ||S||, is removed by the
+// FP64 residual that follows the solve; every convergence decision uses an
+// FP64 residual.  Used only when the warm start is far from the solution
+// (||r32||^2 > first32_min2 ||S||^2), else the step goes straight to FP64.
+__device__ __forceinline__ void resid_first_init(SolveState* st, double r32, double rz) {
+  const bool use = st->first32_min2 > 0 && isfinite(r32) && r32 > st->first32_min2 * st->outer_b2;
+  st->bnorm2 = r32;
+  st->thresh2 = fmax(st->inner_rtol2 * r32, 0.01 * st->outer_thresh2);
+  st->rnorm2 = r32;
+  st->rho = rz;
+  st->it = 0;
+  st->first = 1;
+  st->done = use ? 0 : 1;
+  st->first_used = use ? 1 : 0;
+  if (use) {
+    st->sweeps = 1;  // the next FP64 residual adds this sweep's correction
+    st->acc_first += 1;
+  }
+  st->h_cur = st->h_first;
+  if (st->graph_mode) cudaGraphSetConditional(st->h_first, use ? 1u : 0u);
 }
 
 // Refinement sweep start (one thread): r64 = ||S - A p64||^2 decides the outer
@@ -714,6 +740,7 @@ __device__ __forceinline__ void resid_refine_init(SolveState* st, double r64, do
   st->first = 1;
   st->done = (st->outer_done || r32 == 0.0) ? 1 : 0;
   if (!st->outer_done) st->sweeps += 1;
+  st->h_cur = st->h_inner;
   if (st->graph_mode) {
     cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
     cudaGraphSetConditional(st->h_outer, st->outer_done ? 0u : 1u);
@@ -826,7 +853,7 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
   T kappa = 0;
   float kappa_f = 0.0f;
   if (MODE == CD_RESID) kappa = (T)st->kappa;
-  if (MODE == CD_RESID_REFINE) kappa_f = (float)st->kappa;
+  if (MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) kappa_f = (float)st->kappa;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int ky = c.j + s * c.NY8;
@@ -844,6 +871,15 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
       const double r2 = (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
       acc[0] += w * r2;
       acc[1] += w * r2 * (double)pinv_sym(g, c.kx, ky, kappa);
+    } else if constexpr (MODE == CD_RESID_FIRST) {
+      const cx<float> rf = ccast<float>(csub(bvec[idx], q));
+      r32[idx] = rf;
+      delta32[idx] = czero<float>();
+      const float wf = (float)w, wpf = wf * pinv_f32(g, c.kx, ky, kappa_f);
+      r32acc.add_prod(wf * rf.x, rf.x);
+      r32acc.add_prod(wf * rf.y, rf.y);
+      rzacc.add_prod(wpf * rf.x, rf.x);
+      rzacc.add_prod(wpf * rf.y, rf.y);
     } else {
       const cx<T> rv = csub(bvec[idx], q);
       out[idx] = rv;
@@ -866,6 +902,10 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
     double a2[2] = {acc[0], acc[1]}, t2[2];
     if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
       resid_init(st, t2[0], t2[1]);
+  } else if constexpr (MODE == CD_RESID_FIRST) {
+    double a2[2] = {r32acc.value(), rzacc.value()}, t2[2];
+    if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
+      resid_first_init(st, t2[0], t2[1]);
   } else {
     acc[0] = r64acc.value();
     acc[1] = r32acc.value();
@@ -1151,7 +1191,7 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
   T kappa = 0;
   float kappa_f = 0.0f;
   if (MODE == CD_RESID) kappa = (T)st->kappa;
-  if (MODE == CD_RESID_REFINE) kappa_f = (float)st->kappa;
+  if (MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) kappa_f = (float)st->kappa;
   double accr[2] = {0.0, 0.0};
   int half = 0;
   int tile = blockIdx.x;
@@ -1166,7 +1206,7 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
     cx<T>* cur = sm + half * 2 * se;
     const int kx = (tile << g.ltc) + b;
     cx<T> aux[8];  // b (residual), fetched early to overlap the FFT
-    if (MODE == CD_RESID || MODE == CD_RESID_REFINE) {
+    if (MODE == CD_RESID || MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) {
 #pragma unroll
       for (int s = 0; s < 8; ++s) aux[s] = bvec[(size_t)(j + s * NY8) * H + kx];
     }
@@ -1198,6 +1238,15 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
         const double r2 = (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
         accr[0] += w * r2;
         accr[1] += w * r2 * (double)pinv_sym(g, kx, ky, kappa);
+      } else if constexpr (MODE == CD_RESID_FIRST) {
+        const cx<float> rf = ccast<float>(csub(aux[s], q));
+        r32[idx] = rf;
+        delta32[idx] = czero<float>();
+        const float wf = (float)w, wpf = wf * pinv_f32(g, kx, ky, kappa_f);
+        r32acc.add_prod(wf * rf.x, rf.x);
+        r32acc.add_prod(wf * rf.y, rf.y);
+        rzacc.add_prod(wpf * rf.x, rf.x);
+        rzacc.add_prod(wpf * rf.y, rf.y);
       } else {
         const cx<T> rv = csub(aux[s], q);
         out[idx] = rv;
@@ -1223,6 +1272,10 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
     double t2[2];
     if (last_cta_sum<2>(accr, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
       resid_init(st, t2[0], t2[1]);
+  } else if constexpr (MODE == CD_RESID_FIRST) {
+    double a2[2] = {r32acc.value(), rzacc.value()}, t2[2];
+    if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
+      resid_first_init(st, t2[0], t2[1]);
   } else {
     double acc[3] = {r64acc.value(), r32acc.value(), rzacc.value()}, tot[3];
     if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot) && threadIdx.x == 0)
@@ -1343,7 +1396,7 @@ __global__ void __launch_bounds__(256) k_cg_update(Geo<T> g, cx<T>* __restrict__
                                                    const cx<T>* __restrict__ q, SolveState* st) {
   if (st->done) {
     if (st->graph_mode && blockIdx.x == 0 && threadIdx.x == 0)
-      cudaGraphSetConditional(st->h_inner, 0u);
+      cudaGraphSetConditional(st->h_cur, 0u);
     return;
   }
   const T alpha = (T)st->alpha;
@@ -1385,7 +1438,7 @@ __global__ void __launch_bounds__(256) k_cg_update(Geo<T> g, cx<T>* __restrict__
       st->done = 1;
       st->status = HC_ENOCONV;
     }
-    if (st->graph_mode) cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
+    if (st->graph_mode) cudaGraphSetConditional(st->h_cur, st->done ? 0u : 1u);
   }
 }
 
@@ -1758,6 +1811,10 @@ void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const 
       case CD_RESID:
         kp_col_div<T, CD_RESID><<<g.pgrid, nt, ps, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
         break;
+      case CD_RESID_FIRST:
+        if constexpr (std::is_same<T, float>::value)
+          kp_col_div<T, CD_RESID_FIRST><<<g.pgrid, nt, ps, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
+        break;
       default:
         kp_col_div<T, CD_RESID_REFINE><<<g.pgrid, nt, ps, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
         break;
@@ -1773,6 +1830,10 @@ void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const 
       break;
     case CD_RESID:
       k_col_div<T, CD_RESID><<<nb, nt, sm, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
+      break;
+    case CD_RESID_FIRST:
+      if constexpr (std::is_same<T, float>::value)
+        k_col_div<T, CD_RESID_FIRST><<<nb, nt, sm, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
       break;
     default:
       k_col_div<T, CD_RESID_REFINE><<<nb, nt, sm, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
@@ -1863,6 +1924,10 @@ void set_smem_limits_t() {
   allow_smem(k_col_div<T, CD_CG>);
   allow_smem(k_col_div<T, CD_RESID>);
   allow_smem(k_col_div<T, CD_RESID_REFINE>);
+  if constexpr (std::is_same<T, float>::value) {
+    allow_smem(k_col_div<T, CD_RESID_FIRST>);
+    allow_smem(kp_col_div<T, CD_RESID_FIRST>);
+  }
   allow_smem(kp_col_div<T, CD_PLAIN>);
   allow_smem(kp_col_div<T, CD_CG>);
   allow_smem(kp_col_div<T, CD_RESID>);

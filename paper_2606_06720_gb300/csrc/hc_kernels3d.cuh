@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256) k3_zdiv(Geo<T> g, Tri<cx<T>*> Q, const cx
   T kappa = 0;
   float kappa_f = 0.0f;
   if (MODE == CD_RESID) kappa = (T)st->kappa;
-  if (MODE == CD_RESID_REFINE) kappa_f = (float)st->kappa;
+  if (MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) kappa_f = (float)st->kappa;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int kz = c.j + s * c.L8;
@@ -300,6 +300,15 @@ __global__ void __launch_bounds__(256) k3_zdiv(Geo<T> g, Tri<cx<T>*> Q, const cx
       const double r2 = (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
       acc[0] += w * r2;
       acc[1] += w * r2 * (double)pinv3(g, kx, ky, kz, kappa);
+    } else if constexpr (MODE == CD_RESID_FIRST) {
+      const cx<float> rf = ccast<float>(csub(bvec[idx], q));
+      r32[idx] = rf;
+      delta32[idx] = czero<float>();
+      const float wf = (float)w, wpf = wf * pinv3_f32(g, kx, ky, kz, kappa_f);
+      r32acc.add_prod(wf * rf.x, rf.x);
+      r32acc.add_prod(wf * rf.y, rf.y);
+      rzacc.add_prod(wpf * rf.x, rf.x);
+      rzacc.add_prod(wpf * rf.y, rf.y);
     } else {
       const cx<T> rv = csub(bvec[idx], q);
       out[idx] = rv;
@@ -322,6 +331,10 @@ __global__ void __launch_bounds__(256) k3_zdiv(Geo<T> g, Tri<cx<T>*> Q, const cx
     double a2[2] = {acc[0], acc[1]}, t2[2];
     if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
       resid_init(st, t2[0], t2[1]);
+  } else if constexpr (MODE == CD_RESID_FIRST) {
+    double a2[2] = {r32acc.value(), rzacc.value()}, t2[2];
+    if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
+      resid_first_init(st, t2[0], t2[1]);
   } else {
     acc[0] = r64acc.value();
     acc[1] = r32acc.value();
@@ -583,7 +596,7 @@ __global__ void __launch_bounds__(256) k3_cg_update(Geo<T> g, cx<T>* __restrict_
                                                     const cx<T>* __restrict__ q, SolveState* st) {
   if (st->done) {
     if (st->graph_mode && blockIdx.x == 0 && threadIdx.x == 0)
-      cudaGraphSetConditional(st->h_inner, 0u);
+      cudaGraphSetConditional(st->h_cur, 0u);
     return;
   }
   const T alpha = (T)st->alpha;
@@ -626,7 +639,7 @@ __global__ void __launch_bounds__(256) k3_cg_update(Geo<T> g, cx<T>* __restrict_
       st->done = 1;
       st->status = HC_ENOCONV;
     }
-    if (st->graph_mode) cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
+    if (st->graph_mode) cudaGraphSetConditional(st->h_cur, st->done ? 0u : 1u);
   }
 }
 
@@ -710,6 +723,10 @@ void z_div(const Geo<T>& g, int mode, Tri<cx<T>*> Q, const cx<T>* d, const cx<T>
     case CD_RESID:
       k3_zdiv<T, CD_RESID><<<nb, nt, sm, s>>>(g, Q, d, b, out, r32, delta32, st);
       break;
+    case CD_RESID_FIRST:
+      if constexpr (std::is_same<T, float>::value)
+        k3_zdiv<T, CD_RESID_FIRST><<<nb, nt, sm, s>>>(g, Q, d, b, out, r32, delta32, st);
+      break;
     default:
       k3_zdiv<T, CD_RESID_REFINE><<<nb, nt, sm, s>>>(g, Q, d, b, out, r32, delta32, st);
       break;
@@ -766,6 +783,7 @@ void set_smem_limits_3d_t() {
   allow_smem(k3_zdiv<T, CD_CG>);
   allow_smem(k3_zdiv<T, CD_RESID>);
   allow_smem(k3_zdiv<T, CD_RESID_REFINE>);
+  if constexpr (std::is_same<T, float>::value) allow_smem(k3_zdiv<T, CD_RESID_FIRST>);
 }
 template <typename T, typename Tm>
 void set_smem_limits_row3() {

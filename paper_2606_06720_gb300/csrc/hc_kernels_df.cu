@@ -26,6 +26,7 @@ template void col_div<df64>(const Geo<df64>&, int, const cx<df64>*, const cx<df6
                             SolveState*, cudaStream_t);
 template void convert<df64, double>(const double*, df64*, size_t, cudaStream_t);
 template void convert<double, df64>(const df64*, double*, size_t, cudaStream_t);
+template void convert<float, df64>(const df64*, float*, size_t, cudaStream_t);
 
 void set_smem_limits_df() {
   allow_smem(k_row_r2c<df64>);

@@ -59,6 +59,7 @@ __global__ void k_set_config(SolveState* st, SolveConfig c) {
   st->e_coef[1] = c.e_coef[1];
   st->e_coef[2] = c.e_coef[2];
   st->dt = c.dt;
+  st->first32_min2 = c.first32_min2;
   st->dim = c.dim;
   st->diag = c.diag;
   st->outer_rtol2 = c.outer_thresh2_rel;
@@ -77,6 +78,7 @@ __global__ void k_step_begin(SolveState* st, int npts) {
                                  : st->mean_r + st->msum / (double)npts / (double)st->dim;
   st->msum_old = st->msum;
   st->gm2_next_valid = 0;
+  st->first_used = 0;
   st->outer_thresh2 = st->outer_rtol2 * st->outer_b2;
   st->it = 0;
   st->total_it = 0;
@@ -151,6 +153,7 @@ __global__ void k_run_gate(SolveState* st) {
 }
 
 __global__ void k_reset_accum(SolveState* st) {
+  st->acc_first = 0;
   st->first_bad = 0;
   st->acc_iters = 0;
   st->acc_sweeps = 0;

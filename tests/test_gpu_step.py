@@ -252,3 +252,33 @@ def test_pipelined_column_passes_match_plain_ones(hc, precision):
     for m, p in outs[1:]:
         assert rel_l2(m, outs[0][0]) < 1e-6
         assert rel_l2(p, outs[0][1]) < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp32_refined", "fp32_refined_df"])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_fp32_first_sweep_keeps_the_fp64_certificate(hc, precision, use_graph):
+    """The refined modes start the first sweep from S - A p^k evaluated in
+    FP32 when the warm start is far off (here: every step of the 256^2
+    source/sink run).  Each step still ends on an FP64-certified residual,
+    checked again with the oracle's operator, and the trajectory agrees with
+    the all-FP64-residual variant to the solver tolerance."""
+    w = W.source_sink_2d(256, steps=5)
+    g = O.Grid(w.n, w.L)
+    m32 = lambda m: m.astype(np.float32).astype(np.float64)  # noqa: E731
+    r32 = m32(w.r)
+    b = O.project(g, w.S)
+    outs = []
+    for fp64_first in (False, True):
+        with make_solver(hc, w, precision, rtol=1e-8, use_graph=use_graph,
+                         fp64_first_residual=fp64_first) as s:
+            for k in range(5):
+                m_prev = s.get_m()
+                st = s.step(1)
+                assert st.status == 0
+                assert st.first_sweep_fp32 == (0 if fp64_first else 1)
+                p = s.get_p()
+                res = np.linalg.norm(b - O.apply_A(g, m_prev, r32, p)) / np.linalg.norm(b)
+                assert st.rel_residual <= 1e-8 and res <= 1.2e-8, (k, res)
+            outs.append((s.get_m(), s.get_p()))
+    assert rel_l2(outs[0][0], outs[1][0]) < 1e-6
+    assert rel_l2(outs[0][1], outs[1][1]) < 1e-6
