@@ -184,8 +184,8 @@ __device__ __forceinline__ void twiddle_powers(cx<T> (&w)[R], const cx<T>* __res
 // at sl[q][padk(e) * ks].  Every thread of the CTA must call this together.
 // tw[m] = exp(-2 pi i m / N); the inverse uses the conjugates.
 template <int S, int NV, bool SWZ = false, typename T>
-__device__ __forceinline__ void fft_canon(cx<T> (&v)[NV][8], cx<T>* const* sl, int ks, int j,
-                                          int lN, const cx<T>* __restrict__ tw) {
+__device__ __forceinline__ void fft_rt(cx<T> (&v)[NV][8], cx<T>* const* sl, int ks, int j, int lN,
+                                       const cx<T>* __restrict__ tw) {
   const int N8 = 1 << (lN - 3);
   int lNs = 0;
   int rem = lN;
@@ -255,6 +255,110 @@ __device__ __forceinline__ void fft_canon(cx<T> (&v)[NV][8], cx<T>* const* sl, i
       return;
     }
   }
+}
+
+// Compile-time-length variant of fft_rt, same contract.  With the pass
+// stride a constant, every slot address is one per-thread base plus a
+// constant: a pass writes elements base + (r << LNS) and reads j + s N/8,
+// whose two parts occupy disjoint bits, and both the swizzle (bitwise linear:
+// rswz(a ^ b) = rswz(a) ^ rswz(b)) and the padding (padk(a + b) = padk(a) +
+// padk(b) when b is a multiple of 8 or a < 8 with a's base a multiple of 8)
+// split over them.  That removes the per-access index arithmetic.
+template <typename T>
+__host__ __device__ constexpr int rswz_c(int e) {
+  return std::is_same<T, float>::value ? (e ^ (((e >> 4) & 7) | (((e >> 4) & 4) << 1)))
+                                       : (e ^ ((e >> 3) & 7));
+}
+template <typename T, bool SWZ>
+__device__ __forceinline__ int slot_base(int e, int ks) {
+  return SWZ ? rswz<T>(e) : padk(e) * ks;
+}
+template <typename T, bool SWZ>
+__device__ __forceinline__ int slot_plus(int b, int c, int ks) {  // slot of (base of b) + c
+  return SWZ ? (b ^ rswz_c<T>(c)) : b + (c + (c >> 3)) * ks;
+}
+
+template <int S, int NV, bool SWZ, int LN, int LNS, typename T>
+__device__ __forceinline__ void fft_static_pass(cx<T> (&v)[NV][8], cx<T>* const* sl, int ks, int j,
+                                                int jslot, const cx<T>* __restrict__ tw) {
+  constexpr int REM = LN - LNS;
+  constexpr int N8 = 1 << (LN - 3);
+  if constexpr (REM >= 3) {
+    const int k = j & ((1 << LNS) - 1);
+    if constexpr (LNS > 0) {
+      cx<T> w[8];
+      twiddle_powers<S, 8>(w, tw, k << (LN - 3 - LNS));
+#pragma unroll
+      for (int r = 1; r < 8; ++r)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q][r] = cmul(v[q][r], w[r]);
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) dft8<S>(v[q]);
+    if constexpr (REM > 3) {
+      const int bslot = slot_base<T, SWZ>(((j >> LNS) << (LNS + 3)) + k, ks);
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int e = slot_plus<T, SWZ>(bslot, r << LNS, ks);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sl[q][e] = v[q][r];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int e = slot_plus<T, SWZ>(jslot, s * N8, ks);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q][s] = sl[q][e];
+      }
+      fft_static_pass<S, NV, SWZ, LN, LNS + 3>(v, sl, ks, j, jslot, tw);
+    }
+  } else if constexpr (REM == 2) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int k = (j + u * N8) & ((1 << LNS) - 1);
+      cx<T> w[4];
+      twiddle_powers<S, 4>(w, tw, k << (LN - 2 - LNS));
+#pragma unroll
+      for (int r = 1; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q][u + 2 * r] = cmul(v[q][u + 2 * r], w[r]);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) dft4<S>(v[q][u], v[q][u + 2], v[q][u + 4], v[q][u + 6]);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = (j + u * N8) & ((1 << LNS) - 1);
+      cx<T> w = ldg(&tw[k << (LN - 1 - LNS)]);
+      if (S > 0) w.y = -w.y;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        v[q][u + 4] = cmul(v[q][u + 4], w);
+        dft2<S>(v[q][u], v[q][u + 4]);
+      }
+    }
+  }
+}
+
+// The transform every kernel calls: FP32 transforms of length 2^8 .. 2^12 (the
+// grids whose speed matters) use the compile-time-length code, all others the
+// runtime-length loop.  lN is uniform across the CTA.
+template <int S, int NV, bool SWZ = false, typename T>
+__device__ __forceinline__ void fft_canon(cx<T> (&v)[NV][8], cx<T>* const* sl, int ks, int j,
+                                          int lN, const cx<T>* __restrict__ tw) {
+  if constexpr (std::is_same<T, float>::value) {
+    const int js = slot_base<T, SWZ>(j, ks);
+    switch (lN) {
+      case 8: fft_static_pass<S, NV, SWZ, 8, 0>(v, sl, ks, j, js, tw); return;
+      case 9: fft_static_pass<S, NV, SWZ, 9, 0>(v, sl, ks, j, js, tw); return;
+      case 10: fft_static_pass<S, NV, SWZ, 10, 0>(v, sl, ks, j, js, tw); return;
+      case 11: fft_static_pass<S, NV, SWZ, 11, 0>(v, sl, ks, j, js, tw); return;
+      case 12: fft_static_pass<S, NV, SWZ, 12, 0>(v, sl, ks, j, js, tw); return;
+      default: break;
+    }
+  }
+  fft_rt<S, NV, SWZ>(v, sl, ks, j, lN, tw);
 }
 
 // ------------------------------------------------------------------ reductions
