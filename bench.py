@@ -88,10 +88,10 @@ BYTES_PER_POINT_3D = {
 }
 
 # DRAM bytes (read + write) per launch measured by ncu for the 2048^2 refined
-# workload with the current kernels (profiles/residual_and_cg_kernels_2048.md).
+# workload with the current kernels (profiles/launches_refined_2048.md).
 # Set an entry to None when its kernel changes.
-NCU_TRAFFIC_2048 = {"res_grad": 54.9e6, "res_apply": 136.8e6, "res_div": 132.9e6,
-                    "cg_grad": 35.6e6, "cg_apply": None, "cg_div": None, "cg_update": 67.7e6}
+NCU_TRAFFIC_2048 = {"res_grad": 54.9e6, "res_apply": None, "res_div": 132.9e6,
+                    "cg_grad": 35.6e6, "cg_apply": 84.8e6, "cg_div": 33.6e6, "cg_update": 67.2e6}
 
 
 def shard(items: int, rank: int, world: int) -> list:

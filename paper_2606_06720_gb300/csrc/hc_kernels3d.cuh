@@ -603,14 +603,10 @@ __global__ void __launch_bounds__(256) k3_cg_update(Geo<T> g, cx<T>* __restrict_
   const T kappa = (T)st->kappa;
   const size_t total = (size_t)g.nz * g.ny * g.H;
   DotAcc<T> rr, rz;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
+  auto upd = [&](size_t i, cx<T> dv, cx<T> xv, cx<T> qv, cx<T> rv) {
     const int kx = (int)(i & (size_t)(g.H - 1));
     const int ky = (int)((i >> g.lH) & (size_t)(g.ny - 1));
     const int kz = (int)(i >> (g.lH + g.lny));
-    const cx<T> dv = d[i];
-    const cx<T> xv = x[i], qv = q[i];
-    cx<T> rv = r[i];
     x[i] = cmk<T>(xv.x + alpha * dv.x, xv.y + alpha * dv.y);
     rv = cmk<T>(rv.x - alpha * qv.x, rv.y - alpha * qv.y);
     r[i] = rv;
@@ -620,7 +616,23 @@ __global__ void __launch_bounds__(256) k3_cg_update(Geo<T> g, cx<T>* __restrict_
     rr.add_prod(wt * rv.y, rv.y);
     rz.add_prod(wp * rv.x, rv.x);
     rz.add_prod(wp * rv.y, rv.y);
+  };
+  constexpr int U = 4;  // four elements per trip, all loads issued first
+  const size_t S = (size_t)gridDim.x * blockDim.x;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (U - 1) * S < total; i += U * S) {
+    cx<T> dv[U], xv[U], qv[U], rv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      dv[u] = d[i + u * S];
+      xv[u] = x[i + u * S];
+      qv[u] = q[i + u * S];
+      rv[u] = r[i + u * S];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) upd(i + u * S, dv[u], xv[u], qv[u], rv[u]);
   }
+  for (; i < total; i += S) upd(i, d[i], x[i], q[i], r[i]);
   double acc[2] = {rr.value(), rz.value()};
   double tot[2];
   if (last_cta_sum<2>(acc, g.partials, &st->ticket[TK_UPDATE], tot) && threadIdx.x == 0) {
