@@ -201,7 +201,8 @@ typedef struct {
   int col_pipe[2]; /* 1: the CG/residual/heat column passes run persistent, prefetching the next
                       tile with cp.async while transforming the current one; needs
                       col_tile * (8 bytes FP32 | 16 bytes FP64) to be a multiple of 16, or
-                      one FP32 column (8-byte copies) */
+                      one FP32 column (8-byte copies); 2 (FP32 only): as 1 with the two
+                      transforms of a column on two halves of a 2x larger CTA */
 } hc_tuning;
 
 int hc_get_tuning(const hc_ctx* ctx, hc_tuning* out);

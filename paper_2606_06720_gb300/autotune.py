@@ -33,7 +33,7 @@ def _cache_path() -> str:
 
 # Bumped whenever the kernels' launch-shape trade-offs change, so cached
 # choices made for older kernels are not reused.
-_KERNELS_VERSION = 2
+_KERNELS_VERSION = 3
 
 
 def _key(solver) -> str:
@@ -92,7 +92,8 @@ def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = Fal
     for (knob, idx), kernels in _FAMILIES[prec].items():
         times = {}
         for v in _candidates(solver, knob):
-            for pipe in ((0, 1) if knob == "col_tile" else (None,)):
+            pipes = ((0, 1, 2) if idx == 0 else (0, 1)) if knob == "col_tile" else (None,)
+            for pipe in pipes:
                 trial = {k: list(best[k]) for k in ("col_tile", "row_rows", "col_pipe")}
                 trial[knob][idx] = v
                 if pipe is not None:
@@ -101,7 +102,7 @@ def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = Fal
                     solver.set_tuning(trial["col_tile"], trial["row_rows"], trial["col_pipe"])
                 except Exception:
                     continue
-                label = f"{v}" if pipe is None else f"{v}{'p' if pipe else ''}"
+                label = f"{v}" if pipe is None else f"{v}{['', 'p', 'q'][pipe]}"
                 times[label] = (sum(solver.time_kernel(k, reps) for k in kernels), v, pipe)
         if times:
             lab = min(times, key=lambda k: times[k][0])

@@ -2160,7 +2160,9 @@ int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
     const size_t msz = (p == 1 && !c->refined) ? sizeof(double) : sizeof(float);
     const size_t row_sm = (size_t)rpc * c->nx * (esz + 3 * msz) + 1024;
     if (col_sm > (size_t)optin || row_sm > (size_t)optin) return HC_EINVAL;
-    if (t->col_pipe[p] != 0 && t->col_pipe[p] != 1) return HC_EINVAL;
+    // col_pipe 2 (field-split pipelined passes, 2x the threads) exists for FP32 only
+    if (t->col_pipe[p] < 0 || t->col_pipe[p] > (p == 0 ? 2 : 1)) return HC_EINVAL;
+    if (t->col_pipe[p] == 2 && (tc << (lny - 3)) > 512) return HC_EINVAL;
     if (t->col_pipe[p]) {
       if ((tc * esz) % 16 && tc * esz != 8) return HC_EINVAL;  // 16-byte copies, or one FP32 column
       if (2 * col_sm > (size_t)optin) return HC_EINVAL;

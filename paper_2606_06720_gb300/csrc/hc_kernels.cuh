@@ -1221,6 +1221,10 @@ __global__ void __launch_bounds__(512) kp_col_grad(Geo<T> g, cx<T>* in, const cx
   if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
   const cx<T>* s0 = MODE == CG_DUPDATE ? rvec : in;
   const cx<T>* s1 = MODE == CG_DUPDATE ? dio : nullptr;
+  // this thread's rows are the same in every tile: load their wavenumbers once
+  T kyv[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) kyv[s] = g.kyd[j + s * NY8];
   int half = 0;
   int tile = blockIdx.x;
   if (tile < ntiles) stage_cols<T, NS>(g, s0, s1, sm, se, tile << g.ltc);
@@ -1233,7 +1237,8 @@ __global__ void __launch_bounds__(512) kp_col_grad(Geo<T> g, cx<T>* in, const cx
     __syncthreads();
     cx<T>* cur = sm + half * 2 * se;
     const int kx = (tile << g.ltc) + b;
-    const T ax = g.kxd[kx] * invn;
+    const T kxv = g.kxd[kx];
+    const T ax = kxv * invn;
     cx<float> dl[8];
     if (MODE == CG_ADDDELTA && add_delta) {
 #pragma unroll
@@ -1249,7 +1254,8 @@ __global__ void __launch_bounds__(512) kp_col_grad(Geo<T> g, cx<T>* in, const cx
       if constexpr (MODE == CG_PLAIN) {
         P = cur[e];
       } else if constexpr (MODE == CG_DUPDATE) {
-        const T pv = pinv_sym(g, kx, ky, kappa);
+        const T s2 = kxv * kxv + kyv[s] * kyv[s];
+        const T pv = s2 > (T)0 ? (T)1 / (kappa * s2) : (T)0;  // pinv_sym
         const cx<T> z = cscale(cur[e], pv);
         P = first ? z : cadd(z, cscale(cur[se + e], beta));
         dio[idx] = P;
@@ -1260,7 +1266,7 @@ __global__ void __launch_bounds__(512) kp_col_grad(Geo<T> g, cx<T>* in, const cx
           in[idx] = P;
         }
       }
-      const T ay = g.kyd[ky] * invn;
+      const T ay = kyv[s] * invn;
       v[0][s] = cmk<T>(-ax * P.y, ax * P.x);
       v[1][s] = cmk<T>(-ay * P.y, ay * P.x);
     }
@@ -1297,6 +1303,9 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
   if (MODE == CD_RESID) kappa = (T)st->kappa;
   if (MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) kappa_f = (float)st->kappa;
   double accr[2] = {0.0, 0.0};
+  T kyv[8];  // this thread's rows are the same in every tile
+#pragma unroll
+  for (int s = 0; s < 8; ++s) kyv[s] = g.kyd[j + s * NY8];
   int half = 0;
   int tile = blockIdx.x;
   if (tile < ntiles) stage_cols<T, 2>(g, Qx, Qy, sm, se, tile << g.ltc);
@@ -1329,7 +1338,7 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
     for (int s = 0; s < 8; ++s) {
       const int ky = j + s * NY8;
       const size_t idx = (size_t)ky * H + kx;
-      const T ay = g.kyd[ky];
+      const T ay = kyv[s];
       const cx<T> t = cmk<T>(ax * v[0][s].x + ay * v[1][s].x, ax * v[0][s].y + ay * v[1][s].y);
       const cx<T> q = cmk<T>(t.y, -t.x);
       if constexpr (MODE == CD_PLAIN) {
@@ -1384,6 +1393,172 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
     double acc[3] = {r64acc.value(), r32acc.value(), rzacc.value()}, tot[3];
     if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot) && threadIdx.x == 0)
       resid_refine_init(st, tot[0], tot[1], tot[2]);
+  }
+}
+
+// Field-split variants of the pipelined FP32 column passes (col_pipe = 2).
+// The two transforms of a tile column go to two halves of the CTA, one
+// transform per thread: threads [0, P) work on field 0, [P, 2P) on field 1,
+// P = tc * ny/8.  Half the data registers per thread and twice the resident
+// warps of the NV = 2 kernels, for the same staging and shared memory; both
+// halves read the same staged inputs.
+template <int MODE>
+__global__ void __launch_bounds__(1024) kq_col_grad(Geo<float> g, cx<float>* in,
+                                                    const cx<float>* __restrict__ rvec,
+                                                    cx<float>* dio, const cx<float>* __restrict__ delta,
+                                                    cx<float>* __restrict__ Gx,
+                                                    cx<float>* __restrict__ Gy, SolveState* st,
+                                                    int check_done) {
+  using T = float;
+  if (check_done && st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  constexpr int NS = MODE == CG_DUPDATE ? 2 : 1;
+  const int H = g.H, se = slab_elems(g), ntiles = g.H >> g.ltc;
+  const int P = g.tc << (g.lny - 3);
+  const int f = threadIdx.x >= P ? 1 : 0;
+  const int t = threadIdx.x - f * P;
+  const int b = t & (g.tc - 1), j = t >> g.ltc, NY8 = 1 << (g.lny - 3);
+  const T invn = (T)(1.0 / ((double)g.nx * (double)g.ny));
+  bool first = false, add_delta = false;
+  T beta = 0, kappa = 0;
+  if (MODE == CG_DUPDATE) {
+    first = st->first != 0;
+    beta = (T)st->beta;
+    kappa = (T)st->kappa;
+  }
+  if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
+  const cx<T>* s0 = MODE == CG_DUPDATE ? rvec : in;
+  const cx<T>* s1 = MODE == CG_DUPDATE ? dio : nullptr;
+  cx<T>* out = f ? Gy : Gx;
+  int half = 0;
+  int tile = blockIdx.x;
+  if (tile < ntiles) stage_cols<T, NS>(g, s0, s1, sm, se, tile << g.ltc);
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    if (nxt < ntiles) stage_cols<T, NS>(g, s0, s1, sm + (half ^ 1) * 2 * se, se, nxt << g.ltc);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+    cx<T>* cur = sm + half * 2 * se;
+    const int kx = (tile << g.ltc) + b;
+    const T ax = g.kxd[kx] * invn;
+    cx<T> v[1][8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int ky = j + s * NY8;
+      const size_t idx = (size_t)ky * H + kx;
+      const int e = padk(ky) * g.tc + b;
+      cx<T> Pv;
+      if constexpr (MODE == CG_PLAIN) {
+        Pv = cur[e];
+      } else if constexpr (MODE == CG_DUPDATE) {
+        const cx<T> z = cscale(cur[e], pinv_sym(g, kx, ky, kappa));
+        Pv = first ? z : cadd(z, cscale(cur[se + e], beta));
+        if (!f) dio[idx] = Pv;
+      } else {
+        Pv = cur[e];
+        if (add_delta) {
+          Pv = cadd(Pv, delta[idx]);
+          if (!f) in[idx] = Pv;
+        }
+      }
+      const T a = f ? g.kyd[ky] * invn : ax;
+      v[0][s] = cmk<T>(-a * Pv.y, a * Pv.x);  // i (k/n) P
+    }
+    cx<T>* const sl[1] = {cur + f * se + b};
+    fft_canon<+1, 1>(v, sl, g.tc, j, g.lny, g.twy);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) out[(size_t)(j + s * NY8) * H + kx] = v[0][s];
+    __syncthreads();
+    half ^= 1;
+  }
+  cp_async_wait_all();
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(1024) kq_col_div(Geo<float> g, const cx<float>* __restrict__ Qx,
+                                                   const cx<float>* __restrict__ Qy,
+                                                   const cx<float>* __restrict__ bvec,
+                                                   cx<float>* __restrict__ out,
+                                                   cx<float>* __restrict__ r32,
+                                                   cx<float>* __restrict__ delta32, SolveState* st) {
+  using T = float;
+  if (MODE == CD_CG && st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  const int H = g.H, se = slab_elems(g), ntiles = g.H >> g.ltc;
+  const int P = g.tc << (g.lny - 3);
+  const int f = threadIdx.x >= P ? 1 : 0;
+  const int t = threadIdx.x - f * P;
+  const int b = t & (g.tc - 1), j = t >> g.ltc, NY8 = 1 << (g.lny - 3);
+  DotAcc<float> r32acc, rzacc;
+  const float kappa_f = MODE == CD_RESID_FIRST ? (float)st->kappa : 0.0f;
+  int half = 0;
+  int tile = blockIdx.x;
+  if (tile < ntiles) stage_cols<T, 2>(g, Qx, Qy, sm, se, tile << g.ltc);
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    if (nxt < ntiles) stage_cols<T, 2>(g, Qx, Qy, sm + (half ^ 1) * 2 * se, se, nxt << g.ltc);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+    cx<T>* cur = sm + half * 2 * se;
+    const int kx = (tile << g.ltc) + b;
+    cx<T> aux[8];  // b (first residual), fetched early to overlap the FFT
+    if (MODE == CD_RESID_FIRST && !f) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) aux[s] = bvec[(size_t)(j + s * NY8) * H + kx];
+    }
+    cx<T> v[1][8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) v[0][s] = cur[f * se + padk(j + s * NY8) * g.tc + b];
+    cx<T>* const sl[1] = {cur + f * se + b};
+    fft_canon<-1, 1>(v, sl, g.tc, j, g.lny, g.twy);
+    // field 1 hands ky * FFT(Qy) to field 0 through its slab
+    __syncthreads();
+    if (f) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int ky = j + s * NY8;
+        cur[se + padk(ky) * g.tc + b] = cscale(v[0][s], g.kyd[ky]);
+      }
+    }
+    __syncthreads();
+    if (!f) {
+      const T ax = g.kxd[kx];
+      const float w = kx == 0 ? 1.0f : 2.0f;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int ky = j + s * NY8;
+        const size_t idx = (size_t)ky * H + kx;
+        const cx<T> yv = cur[se + padk(ky) * g.tc + b];
+        const cx<T> tq = cmk<T>(ax * v[0][s].x + yv.x, ax * v[0][s].y + yv.y);
+        const cx<T> q = cmk<T>(tq.y, -tq.x);  // -i (kx Qx + ky Qy)
+        if constexpr (MODE == CD_RESID_FIRST) {
+          const cx<float> rf = csub(aux[s], q);
+          r32[idx] = rf;
+          delta32[idx] = czero<float>();
+          const float wpf = w * pinv_f32(g, kx, ky, kappa_f);
+          r32acc.add_prod(w * rf.x, rf.x);
+          r32acc.add_prod(w * rf.y, rf.y);
+          rzacc.add_prod(wpf * rf.x, rf.x);
+          rzacc.add_prod(wpf * rf.y, rf.y);
+        } else {
+          out[idx] = q;  // CD_PLAIN; CD_CG (alpha came from the row pass)
+        }
+      }
+    }
+    __syncthreads();
+    half ^= 1;
+  }
+  cp_async_wait_all();
+  if constexpr (MODE == CD_RESID_FIRST) {
+    double a2[2] = {r32acc.value(), rzacc.value()}, t2[2];
+    if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
+      resid_first_init(st, t2[0], t2[1]);
   }
 }
 
@@ -1887,6 +2062,20 @@ void col_grad(const Geo<T>& g, int mode, cx<Tin>* in, const cx<T>* rvec, cx<T>* 
               cudaStream_t s) {
   const int nb = g.H >> g.ltc, nt = col_threads(g);
   const size_t sm = col_smem(g, 2);
+  if constexpr (std::is_same<T, Tin>::value && std::is_same<T, float>::value) {
+    if (g.pipe == 2) {
+      const size_t ps = pipe_smem(g);
+      if (mode == CG_PLAIN)
+        kq_col_grad<CG_PLAIN><<<g.pgrid, 2 * nt, ps, s>>>(g, in, rvec, dio, delta, Gx, Gy, st, check_done);
+      else if (mode == CG_DUPDATE)
+        kq_col_grad<CG_DUPDATE><<<g.pgrid, 2 * nt, ps, s>>>(g, in, rvec, dio, delta, Gx, Gy, st,
+                                                           check_done);
+      else
+        kq_col_grad<CG_ADDDELTA><<<g.pgrid, 2 * nt, ps, s>>>(g, in, rvec, dio, delta, Gx, Gy, st,
+                                                            check_done);
+      return;
+    }
+  }
   if constexpr (std::is_same<T, Tin>::value) {
     if (g.pipe) {
       const size_t ps = pipe_smem(g);
@@ -1916,6 +2105,18 @@ void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const 
              cudaStream_t s) {
   const int nb = g.H >> g.ltc, nt = col_threads(g);
   const size_t sm = col_smem(g, 2);
+  if constexpr (std::is_same<T, float>::value) {
+    if (g.pipe == 2 && mode != CD_RESID && mode != CD_RESID_REFINE) {
+      const size_t ps = pipe_smem(g);
+      if (mode == CD_PLAIN)
+        kq_col_div<CD_PLAIN><<<g.pgrid, 2 * nt, ps, s>>>(g, Qx, Qy, b, out, r32, delta32, st);
+      else if (mode == CD_CG)
+        kq_col_div<CD_CG><<<g.pgrid, 2 * nt, ps, s>>>(g, Qx, Qy, b, out, r32, delta32, st);
+      else
+        kq_col_div<CD_RESID_FIRST><<<g.pgrid, 2 * nt, ps, s>>>(g, Qx, Qy, b, out, r32, delta32, st);
+      return;
+    }
+  }
   if (g.pipe) {
     const size_t ps = pipe_smem(g);
     switch (mode) {
@@ -2044,6 +2245,12 @@ void set_smem_limits_t() {
   if constexpr (std::is_same<T, float>::value) {
     allow_smem(k_col_div<T, CD_RESID_FIRST>);
     allow_smem(kp_col_div<T, CD_RESID_FIRST>);
+    allow_smem(kq_col_grad<CG_PLAIN>);
+    allow_smem(kq_col_grad<CG_DUPDATE>);
+    allow_smem(kq_col_grad<CG_ADDDELTA>);
+    allow_smem(kq_col_div<CD_PLAIN>);
+    allow_smem(kq_col_div<CD_CG>);
+    allow_smem(kq_col_div<CD_RESID_FIRST>);
   }
   allow_smem(kp_col_div<T, CD_PLAIN>);
   allow_smem(kp_col_div<T, CD_CG>);
