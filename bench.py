@@ -32,7 +32,7 @@ UNIT = "Mpoint-steps/s"
 N_GRID = 2048
 CG_RTOL_REFINED = 1e-8      # the refined path's pressure tolerance
 FP64_EQUAL_RTOL = 1e-4      # loosest plain-FP64 tolerance reaching m rel. L2 <= 1e-5 at 100 steps
-                            # (calibrated with --accuracy)
+                            # (calibrated with --accuracy: rtol 1e-4 gives 1.06e-6, 1e-3 gives 1.75e-5)
 HBM_PEAK_FALLBACK = 6800.0  # GB/s, recipe fallback when MEASURED_PEAKS.json is absent
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 of GB300 (recipe table); a plain-ALU bound
 
