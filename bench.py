@@ -88,8 +88,7 @@ BYTES_PER_POINT_3D = {
 }
 
 # DRAM bytes (read + write) per launch measured by ncu for the 2048^2 refined
-# workload with the current kernels (profiles/launches_refined_2048.md and
-# profiles/residual_and_cg_kernels_2048.md).
+# workload with the current kernels (from the committed ncu summaries).
 # Set an entry to None when its kernel changes.
 NCU_TRAFFIC_2048 = {"res_grad": 104.5e6, "res_apply": 134.4e6, "res_div": 133.2e6,
                     "cg_grad": 35.6e6, "cg_apply": 84.8e6, "cg_div": 33.6e6, "cg_update": 67.2e6}
