@@ -18,7 +18,8 @@ pytestmark = pytest.mark.gpu
 
 RNG = np.random.default_rng(33)
 TOL = {"fp64": 1e-12, "fp32_refined": 2e-6, "fp32_refined_df": 2e-6}
-SHAPES3 = [(8, 8, 8), (16, 8, 32), (32, 64, 16), (8, 128, 8), (128, 8, 16), (64, 64, 64)]
+SHAPES3 = [(8, 8, 8), (16, 8, 32), (32, 64, 16), (8, 128, 8), (128, 8, 16), (64, 64, 64),
+           (1024, 8, 16), (8, 1024, 8), (16, 8, 1024)]   # the last three: the longest axes
 
 
 def packed3(F: np.ndarray) -> np.ndarray:
@@ -64,7 +65,8 @@ def test_gradient_3d_matches_oracle(hc, precision, n, L):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
 @pytest.mark.parametrize("n,L", [((16, 8, 32), (1.0, 0.5, 2.0)), ((32, 32, 32), (1.0, 1.0, 1.0)),
-                                 ((8, 64, 16), (1.0, 1.0, 0.5))])
+                                 ((8, 64, 16), (1.0, 1.0, 0.5)), ((1024, 8, 8), (2.0, 1.0, 1.0)),
+                                 ((8, 8, 1024), (1.0, 1.0, 1.0))])
 def test_operator_3d_matches_oracle(hc, precision, n, L):
     g = O.Grid(n, L)
     m = RNG.uniform(-0.5, 0.5, (3,) + g.shape)

@@ -285,3 +285,61 @@ def test_fp32_first_sweep_keeps_the_fp64_certificate(hc, precision, use_graph):
             outs.append((s.get_m(), s.get_p()))
     assert rel_l2(outs[0][0], outs[1][0]) < 1e-6
     assert rel_l2(outs[0][1], outs[1][1]) < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp32_refined", "fp32_refined_df"])
+@pytest.mark.parametrize("case", ["zero_source", "zero_m", "min_grid", "long_x", "long_y"])
+def test_edge_cases_refined(hc, precision, case):
+    """Degenerate inputs and extreme shapes on the refined paths: S = 0 gives
+    p = 0 with no sweep; m = 0 is the constant-coefficient Laplacian; the 8x8
+    grid (one radix-8 pass per axis) and the 4096-long axes.  Every step ends
+    on a residual certified with the oracle's operator."""
+    n, L = {"min_grid": (8, 8), "long_x": (4096, 8), "long_y": (8, 4096)}.get(case, (64, 32)), None
+    g = O.Grid(n)
+    rng = np.random.default_rng(12)
+    r = W.smooth_r(n, 3)
+    S = W.minus_mean(rng.standard_normal(g.shape))
+    m = rng.uniform(0, 0.8, (2,) + g.shape)
+    if case == "zero_source":
+        S = np.zeros(g.shape)
+    if case == "zero_m":
+        m = np.zeros((2,) + g.shape)
+    r32 = r.astype(np.float32).astype(np.float64)
+    b = O.project(g, S)
+    with hc.Solver(n, L, c=3.0, D=0.05, gamma=0.75, dt=1e-3, precision=precision, cg_rtol=1e-8,
+                   cg_maxit=3000) as s:
+        s.set_r(r)
+        s.set_source(S)
+        s.set_m(m)
+        for _ in range(3):
+            m_prev = s.get_m()
+            st = s.step(1)
+            assert st.status == 0
+            p = s.get_p()
+            if case == "zero_source":
+                assert not p.any() and st.refine_sweeps == 0 and st.first_sweep_fp32 == 0
+                continue
+            res = np.linalg.norm(b - O.apply_A(g, m_prev, r32, p)) / np.linalg.norm(b)
+            assert res <= 1.2e-8, res
+
+
+@pytest.mark.parametrize("precision", ["fp32_refined"])
+def test_largest_2d_grid_one_step(hc, precision):
+    """4096^2 (the largest 2D grid) source/sink step in graph mode: FP64
+    residual certified with the oracle's operator at full size, and the new m
+    equal to the oracle's split step applied with the GPU's p."""
+    w = W.source_sink_2d(4096, steps=1)
+    g = O.Grid(w.n, w.L)
+    with make_solver(hc, w, precision, rtol=1e-8) as s:
+        st = s.step(1)
+        assert st.status == 0
+        p = s.get_p()
+        m1 = s.get_m()
+    m0 = w.m0.astype(np.float32).astype(np.float64)
+    r32 = w.r.astype(np.float32).astype(np.float64)
+    b = O.project(g, w.S)
+    res = np.linalg.norm(b - O.apply_A(g, m0, r32, p)) / np.linalg.norm(b)
+    assert res <= 1.2e-8, res
+    gp = O.gradient(g, p)
+    ref = O.diffusion(g, O.relaxation(O.activation(m0, gp, w.c, w.dt), w.gamma, w.dt), w.D, w.dt)
+    assert rel_l2(m1, ref) < 2e-6
