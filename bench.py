@@ -55,6 +55,9 @@ BYTES_PER_POINT = {
         "first_grad": 16,  # read p64 (F8); write Gx, Gy (2 F4)
         "first_apply": 28, # read Gx, Gy, mx, my, r; write Qx, Qy  7 F4
         "first_div": 20,   # read Qx, Qy, b32; write r32, delta   5 F4
+        "mid_grad": 24,    # as res_grad (double-float grads are F8 too)
+        "mid_apply": 44,   # as res_apply
+        "mid_div": 32,     # read Qx, Qy, b (3 F8); write r32, delta (2 F4)
     },
     "fp64": {
         "cg_grad": 40, "cg_apply": 56, "cg_div": 24, "cg_update": 48, "res_grad": 24,
@@ -64,6 +67,9 @@ BYTES_PER_POINT = {
 }
 FP64_KERNELS = {"fp32_refined": {"res_grad", "res_apply", "res_div", "res_ypass"},
                 "fp64": set(BYTES_PER_POINT["fp64"])}
+# Double-float kernels (the mid-step residual of the FP64-refined path): bound
+# by the FP32 pipes running the emulated arithmetic; no roofline fraction.
+DF_KERNELS = {"mid_grad", "mid_apply", "mid_div", "mid_ypass"}
 
 # The 3D kernels (d = 3, n = nx*ny*nz points), refined path, same convention.
 # The y pass runs twice per operator apply (inverse before the row pass,
@@ -85,6 +91,10 @@ BYTES_PER_POINT_3D = {
     "first_grad": 20,  # read p64 (F8); write 3 F4
     "first_apply": 40, # as cg_apply
     "first_div": 24,   # read Q0..Q2, b32; write r32, delta  6 F4
+    "mid_grad": 44,    # as res_grad
+    "mid_ypass": 48,   # as res_ypass
+    "mid_apply": 64,   # as res_apply
+    "mid_div": 40,     # read 3 F8 + b (F8); write r32, delta (F4)
 }
 
 # DRAM bytes (read + write) per launch measured by ncu for the 2048^2 refined
@@ -120,7 +130,8 @@ def fft_flops_per_point(kernel: str, nx: int, ny: int) -> float:
         "cg_div": col2 + 6, "res_div": col2 + 10,
         "cg_update": 10, "split_row": 2 * row1 + 30, "split_heat": 2 * col2 + 3,
         "split_c2r": row1 + 2, "first_grad": col2 + 2, "first_apply": 2 * row1 + 9,
-        "first_div": col2 + 10,
+        "first_div": col2 + 10, "mid_grad": col2 + 2, "mid_apply": 2 * row1 + 9,
+        "mid_div": col2 + 10,
     }[kernel]
 
 
@@ -137,6 +148,8 @@ def fft_flops_per_point_3d(kernel: str, nx: int, ny: int, nz: int) -> float:
         "cg_div": 7.5 * lz + 8, "res_div": 7.5 * lz + 12, "cg_update": 10,
         "split_row": 30 * lx + 45, "split_heat": 15 * ly + 3, "split_c2r": 15 * lz + 5,
         "first_grad": 7.5 * lz + 3, "first_apply": 15 * lx + 11, "first_div": 7.5 * lz + 12,
+        "mid_grad": 7.5 * lz + 4, "mid_ypass": 7.5 * ly, "mid_apply": 15 * lx + 11,
+        "mid_div": 7.5 * lz + 12,
     }[kernel]
 
 
@@ -151,9 +164,12 @@ def kernel_table(s, counts: dict, bytes_pp: dict, flops_pp, fp64_names: set, npt
         gbs = bytes_pp[name] * npts / (kms / 1e3) / 1e9
         tfl = flops_pp(name) * npts / (kms / 1e3) / 1e12
         is64 = name in fp64_names
+        isdf = name in DF_KERNELS
         kernels[name] = {"ms": kms, "launches_per_step": cnt, "ms_per_step": kms * cnt,
-                         "alg_GBs": gbs, "alg_TFLOPs": tfl, "bound": "alu" if is64 else "hbm",
-                         "frac": (tfl / FP64_PEAK_TFLOPS) if is64 else (gbs / hbm_peak)}
+                         "alg_GBs": gbs, "alg_TFLOPs": tfl,
+                         "bound": "alu-df" if isdf else ("alu" if is64 else "hbm"),
+                         "frac": None if isdf else ((tfl / FP64_PEAK_TFLOPS) if is64
+                                                    else (gbs / hbm_peak))}
     return kernels
 
 
@@ -406,11 +422,14 @@ def run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src) -
     npts = w.npts
     it = st.total_cg_iters / K3
     sw = st.total_sweeps / K3
-    r64 = sw + 1 - st.total_first_fp32 / K3  # FP64 residuals per step
+    r64 = st.total_refine_residuals / K3  # FP64 residuals per step
+    mid = st.total_mid_df / K3           # double-float mid-step residuals per step
     counts = {"cg_grad": it, "cg_ypass": 2 * it, "cg_apply": it, "cg_div": it, "cg_update": it,
               "res_grad": r64, "res_ypass": 2 * r64, "res_apply": r64, "res_div": r64,
               "split_grad": 1, "split_row": 1, "split_heat": 1, "split_c2r": 1,
               "first_grad": 1, "first_apply": 1, "first_div": 1}
+    if mid > 0:
+        counts.update({"mid_grad": mid, "mid_ypass": 2 * mid, "mid_apply": mid, "mid_div": mid})
     kernels = kernel_table(s, counts, BYTES_PER_POINT_3D,
                            lambda k: fft_flops_per_point_3d(k, *w.n),
                            FP64_KERNELS["fp32_refined"], npts, max(3, args.kernel_reps // 3),
@@ -426,7 +445,7 @@ def run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src) -
                         "minus mean, m0~U[0,0.5] seed 0, c=25 D=0.03 gamma=0.75 dt=5e-4; "
                         "FP32 + FP64 refinement, cg_rtol 1e-8" % args.n3d,
             "cg_iters_per_step": it, "refine_sweeps_per_step": sw,
-            "fp64_residuals_per_step": r64,
+            "fp64_residuals_per_step": r64, "df_mid_residuals_per_step": mid,
             "rel_residual_last_step": st.rel_residual,
             "roofline_fp32": {"bound": "hbm", "kernel": dom, "achieved": dk["alg_GBs"],
                               "peak": hbm_peak, "unit": "GB/s", "frac": dk["frac"],
@@ -513,12 +532,14 @@ def run_gb300(args) -> None:
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    first_per_step = st.total_first_fp32 / K
-    res64 = sweeps_per_step + 1 - first_per_step  # FP64 residuals per step
+    res64 = st.total_refine_residuals / K  # FP64 residuals per step
+    mid_per_step = st.total_mid_df / K     # double-float mid-step residuals per step
     counts = {"cg_grad": iters_per_step, "cg_apply": iters_per_step, "cg_div": iters_per_step,
               "cg_update": iters_per_step, "res_grad": res64, "res_apply": res64, "res_div": res64,
               "split_grad": 1, "split_row": 1, "split_heat": 1, "split_c2r": 1,
               "first_grad": 1, "first_apply": 1, "first_div": 1}
+    if mid_per_step > 0:
+        counts.update({"mid_grad": mid_per_step, "mid_apply": mid_per_step, "mid_div": mid_per_step})
     kernels = kernel_table(s, counts, BYTES_PER_POINT["fp32_refined"],
                            lambda k: fft_flops_per_point(k, *w.n), FP64_KERNELS["fp32_refined"],
                            npts, args.kernel_reps, hbm_peak)
@@ -760,7 +781,7 @@ def run_gb300(args) -> None:
             "clocks": clk.summary(),
             "hbm_gbs": bytes_step * K / (ms / 1e3) / 1e9,
             "cg_iters_per_step": iters_per_step, "refine_sweeps_per_step": sweeps_per_step,
-            "fp64_residuals_per_step": res64,
+            "fp64_residuals_per_step": res64, "df_mid_residuals_per_step": mid_per_step,
             "cg_iterations_per_s": world * iters_per_step * K / (ms_max / 1e3),
             "rel_residual_last_step": st.rel_residual,
             "fp64_plain": fp64, "refined_df": dfv, "sweep": sweep, "adjoint": adjv,

@@ -90,11 +90,16 @@ typedef struct {
                               refinement starts); the FP64 residual after it removes that
                               evaluation's error.  1: every sweep starts from an FP64 residual.
                               Either way every convergence test uses an FP64 residual. */
+  int fp64_mid_residual;   /* HC_FP32_REFINED.  0 (default): the residual that follows an FP32 first
+                              sweep (it only supplies the second inner solve's right-hand side) is
+                              evaluated in double-float on the FP32 pipes, with p += delta still
+                              accumulated in FP64; the refinement loop after it is decided by FP64
+                              residuals.  1: that residual is FP64 too. */
 } hc_params;
 
 typedef struct {
   int cg_iters;        /* CG iterations of the last step's pressure solve (summed over sweeps) */
-  int refine_sweeps;   /* refined mode: inner solves run (FP64 residuals: refine_sweeps + 1 - first_sweep_fp32); plain mode: 0 */
+  int refine_sweeps;   /* refined mode: inner solves run; plain mode: 0 */
   double rel_residual; /* ||S - A p||_2 / ||S||_2 at exit: FP64-evaluated in refined mode, recursive in plain mode */
   double kappa;        /* preconditioner constant used */
   int status;          /* HC_OK, HC_ENOCONV or HC_ENONFINITE for that step */
@@ -113,6 +118,11 @@ typedef struct {
   long long energy_step; /* hc_run with HC_STOP_ENERGY: 0-based index, within the call, of the step whose result did not lower the energy; else -1 */
   int first_sweep_fp32;  /* refined modes: the step's first sweep started from the FP32 residual */
   long long total_first_fp32; /* such steps summed over the call */
+  int mid_residual_df;   /* HC_FP32_REFINED: the step evaluated the double-float mid-step residual */
+  long long total_mid_df;     /* such steps summed over the call */
+  int refine_residuals;  /* refined modes: residuals evaluated in the mode's refinement arithmetic
+                            (FP64; double-float in HC_FP32_REFINED_DF), the final one included */
+  long long total_refine_residuals; /* summed over the call */
 } hc_step_stats;
 
 /* Bytes of device workspace hc_create needs for this grid and precision. */
@@ -237,7 +247,11 @@ enum {
   HC_K_FIRST_GRAD = 13,  /* refined: the FP32 first residual's gradient pass (from p64) */
   HC_K_FIRST_APPLY = 14, /* refined: its row pass (2D) / row-pair pass (3D) */
   HC_K_FIRST_DIV = 15,   /* refined: its divergence pass, r32 = b32 - q and the inner-CG start */
-  HC_K_COUNT = 16
+  HC_K_MID_GRAD = 16,    /* HC_FP32_REFINED: the double-float mid-step residual's gradient pass (from p64) */
+  HC_K_MID_APPLY = 17,   /* its row pass (2D) / row-pair pass (3D) */
+  HC_K_MID_DIV = 18,     /* its divergence pass */
+  HC_K_MID_YPASS = 19,   /* 3D only: its y pass */
+  HC_K_COUNT = 20
 };
 
 /* Launch one step kernel `reps` times back to back on the context's current

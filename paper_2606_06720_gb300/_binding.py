@@ -41,7 +41,7 @@ class hc_params(C.Structure):
                 ("cg_rtol", C.c_double), ("cg_maxit", C.c_int), ("precision", C.c_int),
                 ("kappa", C.c_double), ("inner_rtol", C.c_double), ("max_sweeps", C.c_int),
                 ("use_graph", C.c_int), ("stream", C.c_void_p), ("diagnostics", C.c_int),
-                ("fp64_first_residual", C.c_int)]
+                ("fp64_first_residual", C.c_int), ("fp64_mid_residual", C.c_int)]
 
 
 class hc_tuning(C.Structure):
@@ -53,7 +53,9 @@ class hc_step_stats(C.Structure):
                 ("kappa", C.c_double), ("status", C.c_int), ("total_cg_iters", C.c_longlong),
                 ("total_sweeps", C.c_longlong), ("energy", C.c_double), ("delta_m", C.c_double),
                 ("energy_valid", C.c_int), ("stop_reason", C.c_int), ("energy_step", C.c_longlong),
-                ("first_sweep_fp32", C.c_int), ("total_first_fp32", C.c_longlong)]
+                ("first_sweep_fp32", C.c_int), ("total_first_fp32", C.c_longlong),
+                ("mid_residual_df", C.c_int), ("total_mid_df", C.c_longlong),
+                ("refine_residuals", C.c_int), ("total_refine_residuals", C.c_longlong)]
 
 
 def library_path() -> str:
@@ -139,7 +141,7 @@ hc_batch_destroy = lib.hc_batch_destroy
 # kernel ids of hc_time_kernel (include/hc.h)
 KERNELS = ["cg_grad", "cg_apply", "cg_div", "cg_update", "res_grad", "res_apply", "res_div",
            "split_grad", "split_row", "split_heat", "split_c2r", "cg_ypass", "res_ypass",
-           "first_grad", "first_apply", "first_div"]
+           "first_grad", "first_apply", "first_div", "mid_grad", "mid_apply", "mid_div", "mid_ypass"]
 
 
 def strerror(code: int) -> str:
@@ -170,13 +172,18 @@ class StepStats:
     steps: int = 0               # Solver.run: steps executed
     first_sweep_fp32: int = 0    # refined: the last step's first sweep started from an FP32 residual
     total_first_fp32: int = 0
+    mid_residual_df: int = 0     # fp32_refined: the last step evaluated the double-float mid-step residual
+    total_mid_df: int = 0
+    refine_residuals: int = 0    # refined: residuals in the mode's refinement arithmetic (last step)
+    total_refine_residuals: int = 0
 
 
 def _stats(st, rc: int, steps: int = 0) -> StepStats:
     return StepStats(st.cg_iters, st.refine_sweeps, st.rel_residual, st.kappa, st.status, rc,
                      st.total_cg_iters, st.total_sweeps, st.energy, st.delta_m, st.energy_valid,
                      st.stop_reason, st.energy_step, steps, st.first_sweep_fp32,
-                     st.total_first_fp32)
+                     st.total_first_fp32, st.mid_residual_df, st.total_mid_df,
+                     st.refine_residuals, st.total_refine_residuals)
 
 
 def _host_f64(a, count: int, writable: bool = False):
@@ -214,7 +221,8 @@ class Solver:
                  precision: str = "fp32_refined", cg_rtol: float = 1e-8, cg_maxit: int = 1000,
                  kappa: float = 0.0, inner_rtol: float = 1e-4, max_sweeps: int = 10,
                  use_graph: bool = True, device: str = "cuda:0", stream=None,
-                 diagnostics: bool = False, fp64_first_residual: bool = False):
+                 diagnostics: bool = False, fp64_first_residual: bool = False,
+                 fp64_mid_residual: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -237,7 +245,8 @@ class Solver:
         self.precision = precision
         self.params = hc_params(c, D, gamma, dt, cg_rtol, int(cg_maxit), prec, kappa, inner_rtol,
                                 int(max_sweeps), int(bool(use_graph)), self.stream.cuda_stream,
-                                int(bool(diagnostics)), int(bool(fp64_first_residual)))
+                                int(bool(diagnostics)), int(bool(fp64_first_residual)),
+                                int(bool(fp64_mid_residual)))
         nbytes = C.c_size_t()
         _check(hc_workspace_size(C.byref(self.grid), C.byref(self.params), C.byref(nbytes)),
                "hc_workspace_size")
@@ -271,7 +280,7 @@ class Solver:
     # parameters and fields ----------------------------------------------
     def set_params(self, **kw):
         for k, v in kw.items():
-            if k in ("use_graph", "diagnostics", "fp64_first_residual"):
+            if k in ("use_graph", "diagnostics", "fp64_first_residual", "fp64_mid_residual"):
                 v = int(bool(v))
             setattr(self.params, k, v)
         _check(hc_set_params(self.ctx, C.byref(self.params)), "hc_set_params")

@@ -52,9 +52,10 @@ int ilog2(int v) {
 }  // namespace
 
 // Conditional handles of one step chain: the CG loop of the refinement sweeps
-// (or of plain PCG), the refinement loop, and the first (FP32-started) inner loop.
+// (or of plain PCG), the refinement loop, the first (FP32-started) inner loop,
+// and the mid-step residual block (IF) with its inner loop.
 struct Handles {
-  cudaGraphConditionalHandle inner = 0, outer = 0, first = 0;
+  cudaGraphConditionalHandle inner = 0, outer = 0, first = 0, mid = 0, mid_inner = 0;
 };
 
 struct hc_ctx {
@@ -66,6 +67,7 @@ struct hc_ctx {
   size_t ns; // packed spectral values: nz * ny * H
   int refined;
   int df;    // refined with double-float state and residual
+  int mid_df;  // HC_FP32_REFINED: the residual after an FP32 first sweep is double-float
   cudaStream_t stream;
   bool owns_ws;
   void* ws;
@@ -85,6 +87,7 @@ struct hc_ctx {
   cx<double>* q64;          // A d (plain mode)
   cx<double>* G64;          // dim spectra: gradient / flux / m scratch (FP64)
   cx<float>* b32;           // refined: FP32 copy of the projected source spectrum
+  cx<df64>* bq;             // HC_FP32_REFINED: double-float copy of it (mid-step residual)
   cx<float>* r32;           // refined: inner residual
   cx<float>* d32;           // refined: inner direction
   cx<float>* q32;           // refined: A d
@@ -198,10 +201,12 @@ void layout(hc_ctx* c, Layout& L) {
     c->d64 = L.take<cx<double>>(S64);
     c->q64 = L.take<cx<double>>(S64);
     c->b32 = c->r32 = c->d32 = c->q32 = c->x32 = c->G32 = nullptr;
+    c->bq = nullptr;
     for (int k = 0; k < d; ++k) c->m[k] = L.take<double>(sizeof(double) * n);
     c->rf = L.take<double>(sizeof(double) * n);
   } else {
     c->d64 = c->q64 = nullptr;
+    c->bq = c->df ? nullptr : L.take<cx<df64>>(S64);
     c->b32 = L.take<cx<float>>(S32);
     c->r32 = L.take<cx<float>>(S32);
     c->d32 = L.take<cx<float>>(S32);
@@ -482,6 +487,12 @@ void apply_defaults(hc_params& p) {
   if (p.max_sweeps <= 0) p.max_sweeps = 10;
 }
 
+// HC_FP32_REFINED evaluates the residual after an FP32 first sweep in
+// double-float unless either switch asks for FP64 there.
+int mid_df_on(const hc_ctx* c) {
+  return (c->refined && !c->df && !c->prm.fp64_first_residual && !c->prm.fp64_mid_residual) ? 1 : 0;
+}
+
 bool diag_on(const hc_ctx* c) { return c->prm.diagnostics != 0 || c->force_diag != 0; }
 
 int push_config(hc_ctx* c) {
@@ -494,6 +505,7 @@ int push_config(hc_ctx* c) {
   cfg.dt = c->prm.dt;
   // refined: FP32 first sweep when the warm start is off by more than 1e-5 ||S||
   cfg.first32_min2 = (c->refined && !c->prm.fp64_first_residual) ? 1e-10 : 0.0;
+  cfg.mid_df = c->mid_df;
   cfg.dim = c->dim;
   cfg.diag = diag_on(c) ? 1 : 0;
   cfg.outer_thresh2_rel = c->prm.cg_rtol * c->prm.cg_rtol;
@@ -659,6 +671,31 @@ void refined_resid(hc_ctx* c) {
                                (const float*)c->rf, Gx, Gy, nullptr, c->stream);
   hc::col_div<double>(g, hc::CD_RESID_REFINE, Gx, Gy, nullptr, c->b64, c->r64, c->r32, c->x32,
                       c->st, c->stream);
+  c->launches += 3;
+}
+
+// HC_FP32_REFINED, after an FP32 first sweep: p64 += delta (FP64), then
+// S - A p64 in double-float, the second inner solve's right-hand side
+// (resid_mid_init); the same kernels as the double-float mode's residual,
+// reading and updating the FP64 spectrum.  r64 is not written.
+void mid_resid(hc_ctx* c) {
+  auto& q = c->gq;
+  if (c->dim == 3) {
+    auto* G = reinterpret_cast<cx<df64>*>(c->G64);
+    apply3_open<df64, double, float>(c, q, hc::CG_ADDDELTA, c->p64, nullptr, nullptr, G, 0);
+    hc::z_div<df64>(q, hc::CD_RESID_REFINE, tri(G, c->ns), nullptr, c->bq, nullptr, c->r32, c->x32,
+                    c->st, c->stream);
+    c->launches += 1;
+    return;
+  }
+  cx<df64>* Gx = reinterpret_cast<cx<df64>*>(c->G64);
+  cx<df64>* Gy = Gx + (size_t)c->ny * c->H;
+  hc::col_grad<df64, double>(q, hc::CG_ADDDELTA, c->p64, nullptr, nullptr, c->x32, Gx, Gy, c->st, 0,
+                             c->stream);
+  hc::row_apply<df64, float>(q, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1],
+                             (const float*)c->rf, Gx, Gy, nullptr, c->stream);
+  hc::col_div<df64>(q, hc::CD_RESID_REFINE, Gx, Gy, nullptr, c->bq, nullptr, c->r32, c->x32, c->st,
+                    c->stream);
   c->launches += 3;
 }
 
@@ -848,6 +885,15 @@ int step_host(hc_ctx* c) {
       rc = run_cg_host(c, true);
       if (rc) return rc;
     }
+    if (c->st_host->mid_phase) {
+      mid_resid(c);
+      rc = read_state(c);
+      if (rc) return rc;
+      if (!c->st_host->done) {
+        rc = run_cg_host(c, true);
+        if (rc) return rc;
+      }
+    }
     for (int sweep = 0;; ++sweep) {
       refined_resid(c);
       rc = read_state(c);
@@ -879,6 +925,7 @@ int step_host(hc_ctx* c) {
 // a non-default stream that is not capturing.
 //   plain:   step_begin, initial residual, WHILE(inner){CG}, split, step_end
 //   refined: step_begin, FP32 residual, WHILE(first){CG},
+//            [HC_FP32_REFINED: IF(mid){double-float residual, WHILE(mid_inner){CG}}],
 //            WHILE(outer){FP64 residual, WHILE(inner){CG}}, split, step_end
 int build_chain(hc_ctx* c, cudaGraph_t target, Handles* h) {
   cudaStream_t s = c->stream;
@@ -894,15 +941,15 @@ int build_chain(hc_ctx* c, cudaGraph_t target, Handles* h) {
     CU(cudaStreamEndCapture(s, &same));
     return HC_OK;
   };
-  // a WHILE node after `after` in graph g; returns its body
+  // a WHILE (or IF) node after `after` in graph g; returns its body
   auto add_while = [&](cudaGraph_t g, const std::vector<cudaGraphNode_t>& after,
                        cudaGraphConditionalHandle* hd, cudaGraphNode_t* node,
-                       cudaGraph_t* body) -> int {
+                       cudaGraph_t* body, bool is_if = false) -> int {
     CU(cudaGraphConditionalHandleCreate(hd, g, 0, cudaGraphCondAssignDefault));
     cudaGraphNodeParams p = {};
     p.type = cudaGraphNodeTypeConditional;
     p.conditional.handle = *hd;
-    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.type = is_if ? cudaGraphCondTypeIf : cudaGraphCondTypeWhile;
     p.conditional.size = 1;
     CU(cudaGraphAddNode(node, g, after.data(), nullptr, after.size(), &p));
     *body = p.conditional.phGraph_out[0];
@@ -936,6 +983,23 @@ int build_chain(hc_ctx* c, cudaGraph_t target, Handles* h) {
     rc = add_while(target, tail, &hh.first, &first_node, &body);
     if (!rc) rc = capture_iter(body);
     if (rc) return rc;
+    if (c->mid_df) {
+      // IF(mid){double-float residual, WHILE(mid_inner){CG}}
+      cudaGraphNode_t mid_node, mi_node;
+      cudaGraph_t mbody;
+      rc = add_while(target, std::vector<cudaGraphNode_t>{first_node}, &hh.mid, &mid_node, &mbody,
+                     true);
+      if (rc) return rc;
+      CU(cudaStreamBeginCaptureToGraph(s, mbody, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal));
+      mid_resid(c);
+      std::vector<cudaGraphNode_t> mtail;
+      rc = end_capture(mbody, mtail);
+      if (!rc) rc = add_while(mbody, mtail, &hh.mid_inner, &mi_node, &body);
+      if (!rc) rc = capture_iter(body);
+      if (rc) return rc;
+      first_node = mid_node;
+    }
     cudaGraph_t obody;
     rc = add_while(target, std::vector<cudaGraphNode_t>{first_node}, &hh.outer, &loop_node, &obody);
     if (rc) return rc;
@@ -985,9 +1049,8 @@ void set_node_counts(hc_ctx* c) {
 long long graph_kernel_count(const hc_ctx* c, const hc::SolveState& h) {
   long long n = (long long)c->graph_nodes_fixed * h.acc_steps +
                 (long long)c->graph_nodes_body * h.acc_iters;
-  // FP64 residuals: one per inner solve not started in FP32, plus the final check
-  if (c->refined)
-    n += (long long)c->graph_nodes_outer * (h.acc_sweeps - h.acc_first + h.acc_steps);
+  // refinement residuals (FP64 or double-float), the mid-step one included
+  if (c->refined) n += (long long)c->graph_nodes_outer * (h.acc_res_full + h.acc_mid);
   return n;
 }
 
@@ -995,6 +1058,8 @@ long long graph_kernel_count(const hc_ctx* c, const hc::SolveState& h) {
 int use_handles(hc_ctx* c, const Handles& h, cudaGraphConditionalHandle hgate = 0) {
   unsigned long long v[4] = {h.inner, h.outer, hgate, h.first};
   CU(cudaMemcpy(&c->st->h_inner, v, sizeof(v), cudaMemcpyHostToDevice));
+  unsigned long long w[2] = {h.mid, h.mid_inner};
+  CU(cudaMemcpy(&c->st->h_mid, w, sizeof(w), cudaMemcpyHostToDevice));
   return HC_OK;
 }
 
@@ -1123,6 +1188,10 @@ int fill_stats(hc_ctx* c, hc_step_stats* out) {
     out->energy_step = (h.run_mode && h.stop_reason == HC_STOP_ENERGY) ? h.energy_step : -1;
     out->first_sweep_fp32 = h.first_used;
     out->total_first_fp32 = h.acc_first;
+    out->mid_residual_df = h.mid_used;
+    out->total_mid_df = h.acc_mid;
+    out->refine_residuals = c->refined ? h.res_full : 0;
+    out->total_refine_residuals = c->refined ? h.acc_res_full : 0;
   }
   return HC_OK;
 }
@@ -1160,6 +1229,7 @@ int hc_workspace_size(const hc_grid* grid, const hc_params* params, size_t* byte
   tmp.n = (size_t)tmp.nx * tmp.ny * tmp.nz;
   tmp.ns = (size_t)tmp.nz * tmp.ny * tmp.H;
   tmp.refined = params->precision != HC_FP64_PLAIN;
+  tmp.df = params->precision == HC_FP32_REFINED_DF;
   Layout L;
   layout(&tmp, L);
   *bytes = (L.off + kAlign - 1) / kAlign * kAlign;
@@ -1190,6 +1260,7 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   c->ns = (size_t)c->nz * c->ny * c->H;
   c->refined = params->precision != HC_FP64_PLAIN;
   c->df = params->precision == HC_FP32_REFINED_DF;
+  c->mid_df = mid_df_on(c);
   set_node_counts(c);
   c->stream = (cudaStream_t)params->stream;
   c->mean_r = 1.0;
@@ -1272,6 +1343,7 @@ int hc_set_params(hc_ctx* c, const hc_params* p) {
   hc_params np = *p;
   apply_defaults(np);
   c->prm = np;
+  c->mid_df = mid_df_on(c);
   int rc = upload_heat(c);
   if (!rc) rc = push_config(c);
   // split coefficients (and, in 3D, whether the diagnostics passes run) are
@@ -1351,6 +1423,11 @@ int hc_set_source(hc_ctx* c, const double* S, size_t count) {
   int rc = forward64(c, c->b64, c->st);
   if (rc) return rc;
   if (c->refined) {  // FP32 copy for the first sweep's residual
+    if (c->bq) {       // double-float copy for the mid-step residual
+      hc::convert<df64, double>(reinterpret_cast<const double*>(c->b64), reinterpret_cast<df64*>(c->bq),
+                                2 * c->ns, c->stream);
+      c->launches += 1;
+    }
     if (c->df)
       hc::convert<float, df64>(reinterpret_cast<const df64*>(c->b64), reinterpret_cast<float*>(c->b32),
                                2 * c->ns, c->stream);
@@ -2215,6 +2292,8 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
   const size_t ns = c->ns;
   if (c->dim == 2 && (kernel == HC_K_CG_YPASS || kernel == HC_K_RES_YPASS)) return HC_EINVAL;
   if (!c->refined && kernel >= HC_K_FIRST_GRAD) return HC_EINVAL;
+  if (kernel >= HC_K_MID_GRAD && (c->df || !c->refined)) return HC_EINVAL;  // HC_FP32_REFINED only
+  if (c->dim == 2 && kernel == HC_K_MID_YPASS) return HC_EINVAL;
   // 3D: the same roles with the 3D kernels; the SPLIT_HEAT / SPLIT_C2R slots
   // time the y and z diffusion passes.  Scratch outputs never alias inputs
   // that a later repetition reads.
@@ -2301,6 +2380,22 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
         case HC_K_FIRST_DIV:
           hc::z_div<float>(g, hc::CD_RESID_FIRST, G, nullptr, c->b32, nullptr, c->d32, c->q32, ts,
                            c->stream);
+          break;
+        case HC_K_MID_GRAD:
+          hc::z_grad<df64, double>(c->gq, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr,
+                                   tri((cx<df64>*)G64, ns), ts, 0, c->stream);
+          break;
+        case HC_K_MID_YPASS:
+          hc::axis_fft<df64>(c->gq, 1, +1, 3, tri((cx<df64>*)G64, ns), tri((cx<df64>*)G64, ns),
+                             df64(1.0), c->stream);
+          break;
+        case HC_K_MID_APPLY:
+          hc::row_apply3<df64, float>(c->gq, tri((cx<df64>*)G64, ns), mtri<float>(c),
+                                      (const float*)c->rf, tri((cx<df64>*)G64, ns), nullptr, c->stream);
+          break;
+        case HC_K_MID_DIV:
+          hc::z_div<df64>(c->gq, hc::CD_RESID_REFINE, tri((cx<df64>*)G64, ns), nullptr, c->bq, nullptr,
+                          c->d32, c->q32, ts, c->stream);
           break;
         default:
           hc::heat_axis<float>(g, 2, mw, mw, ts, c->stream);
@@ -2444,6 +2539,19 @@ int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
         case HC_K_FIRST_DIV:
           hc::col_div<float>(g, hc::CD_RESID_FIRST, Gx, Gy, nullptr, c->b32, nullptr, c->d32, c->q32,
                              ts, c->stream);
+          break;
+        case HC_K_MID_GRAD:
+          hc::col_grad<df64, double>(c->gq, hc::CG_PLAIN, c->p64, nullptr, nullptr, nullptr,
+                                     (cx<df64>*)Gx64, (cx<df64>*)Gy64, ts, 0, c->stream);
+          break;
+        case HC_K_MID_APPLY:
+          hc::row_apply<df64, float>(c->gq, (cx<df64>*)Gx64, (cx<df64>*)Gy64, (const float*)c->m[0],
+                                     (const float*)c->m[1], (const float*)c->rf, (cx<df64>*)c->r64,
+                                     (cx<df64>*)c->stage, nullptr, c->stream);
+          break;
+        case HC_K_MID_DIV:
+          hc::col_div<df64>(c->gq, hc::CD_RESID_REFINE, (cx<df64>*)Gx64, (cx<df64>*)Gy64, nullptr,
+                            c->bq, nullptr, c->d32, c->q32, ts, c->stream);
           break;
         default:
           hc::row_c2r<float>(g, Gx, Gy, (float*)c->q32, (float*)c->x32, ts, 1, c->stream);

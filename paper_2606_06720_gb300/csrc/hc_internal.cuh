@@ -114,9 +114,17 @@ struct SolveState {
   unsigned long long h_gate;   // cudaGraphConditionalHandle of a gated step (hc_run)
   unsigned long long h_first;  // cudaGraphConditionalHandle of the first (FP32-started) inner loop
   unsigned long long h_cur;    // the inner-loop handle the CG kernels drive (set by whoever opens it)
+  unsigned long long h_mid;        // cudaGraphConditionalHandle of the mid-step residual block (IF)
+  unsigned long long h_mid_inner;  // cudaGraphConditionalHandle of the inner loop after it
   double first32_min2;       // refined: FP32 first sweep only if ||S - A p||^2 > this * ||S||^2 (0: off)
   int acc_first;             // FP32 first sweeps summed over the steps since the last reset
   int first_used;            // the running / last step ran an FP32 first sweep
+  int mid_df;                // HC_FP32_REFINED: the residual after an FP32 first sweep is evaluated in double-float
+  int mid_phase;             // the next refinement residual is that double-float mid-step one
+  int mid_used;              // the running / last step evaluated it
+  int acc_mid;               // such residuals summed over the steps since the last reset
+  int res_full;              // running / last step: residuals in the mode's full refinement arithmetic
+  int acc_res_full;          // summed likewise
   unsigned int ticket[8];    // last-CTA tickets, one per reduction site
   // Diagnostics of Section 2.5, accumulated by the split step when diag != 0.
   // A step solves p[m^k] and so evaluates E_h(m^k) with its own pressure.
@@ -154,6 +162,7 @@ struct SolveConfig {
   double e_coef[3];          // energy coefficients (see SolveState)
   double dt;
   double first32_min2;       // see SolveState
+  int mid_df;                // see SolveState
   int maxit;
   int max_sweeps;
   int graph_mode;

@@ -818,8 +818,35 @@ __device__ __forceinline__ void resid_first_init(SolveState* st, double r32, dou
     st->sweeps = 1;  // the next FP64 residual adds this sweep's correction
     st->acc_first += 1;
   }
+  st->mid_phase = (use && st->mid_df) ? 1 : 0;
   st->h_cur = st->h_first;
-  if (st->graph_mode) cudaGraphSetConditional(st->h_first, use ? 1u : 0u);
+  if (st->graph_mode) {
+    cudaGraphSetConditional(st->h_first, use ? 1u : 0u);
+    if (st->mid_df) cudaGraphSetConditional(st->h_mid, st->mid_phase ? 1u : 0u);
+  }
+}
+
+// Mid-step residual (one thread), HC_FP32_REFINED after an FP32 first sweep:
+// S - A p64 evaluated in double-float (p64 += delta still in FP64).  It only
+// supplies the right-hand side of the second inner solve, whose error it
+// bounds at ~1e-14 ||S||; it never ends the refinement loop, which runs next
+// and is decided by an FP64 residual.  The second solve is skipped when this
+// residual is already below a tenth of the target.
+__device__ __forceinline__ void resid_mid_init(SolveState* st, double r2, double r32, double rz) {
+  st->mid_phase = 0;
+  st->mid_used = 1;
+  st->acc_mid += 1;
+  const bool finite = isfinite(r2);
+  st->bnorm2 = r32;
+  st->thresh2 = fmax(st->inner_rtol2 * r32, 0.01 * st->outer_thresh2);
+  st->rnorm2 = r32;
+  st->rho = rz;
+  st->it = 0;
+  st->first = 1;
+  st->done = (!finite || r32 == 0.0 || r2 <= 0.01 * st->outer_thresh2) ? 1 : 0;
+  if (!st->done) st->sweeps += 1;
+  st->h_cur = st->h_mid_inner;
+  if (st->graph_mode) cudaGraphSetConditional(st->h_mid_inner, st->done ? 0u : 1u);
 }
 
 // Refinement sweep start (one thread): r64 = ||S - A p64||^2 decides the outer
@@ -827,6 +854,8 @@ __device__ __forceinline__ void resid_first_init(SolveState* st, double r32, dou
 // (r32 is r64 rounded to FP32, so both norms are on the same scale.)
 __device__ __forceinline__ void resid_refine_init(SolveState* st, double r64, double r32,
                                                   double rz) {
+  st->res_full += 1;
+  st->acc_res_full += 1;
   st->outer_r2 = r64;
   const bool finite = isfinite(r64);
   const bool conv = r64 <= st->outer_thresh2;
@@ -848,6 +877,32 @@ __device__ __forceinline__ void resid_refine_init(SolveState* st, double r64, do
   if (st->graph_mode) {
     cudaGraphSetConditional(st->h_inner, st->done ? 0u : 1u);
     cudaGraphSetConditional(st->h_outer, st->outer_done ? 0u : 1u);
+  }
+}
+
+// The finalizer of a refinement-residual kernel: the mid-step one when it is
+// pending, else a sweep of the refinement loop.
+__device__ __forceinline__ void resid_sweep_init(SolveState* st, double r2, double r32, double rz) {
+  if (st->mid_phase)
+    resid_mid_init(st, r2, r32, rz);
+  else
+    resid_refine_init(st, r2, r32, rz);
+}
+
+// p64 += delta at one spectral value, then that value in the kernel's type.
+// A double spectrum takes the correction in FP64 whatever T is.
+template <typename T, typename Tin>
+__device__ __forceinline__ cx<T> add_delta_at(cx<Tin>* in, size_t idx, cx<float> dl) {
+  if constexpr (std::is_same<Tin, double>::value) {
+    cx<double> pd = in[idx];
+    pd.x += (double)dl.x;
+    pd.y += (double)dl.y;
+    in[idx] = pd;
+    return ccast<T>(pd);
+  } else {
+    const cx<T> P = cadd(ccast<T>(in[idx]), ccast<T>(dl));
+    in[idx] = ccast<Tin>(P);
+    return P;
   }
 }
 
@@ -908,11 +963,7 @@ __global__ void __launch_bounds__(512) k_col_grad(Geo<T> g, cx<Tin>* in, const c
       dio[idx] = P;
     } else {
       // FP64 correction accumulation p64 += delta (refinement)
-      P = ccast<T>(in[idx]);
-      if (add_delta) {
-        P = cadd(P, ccast<T>(delta[idx]));
-        in[idx] = ccast<Tin>(P);
-      }
+      P = add_delta ? add_delta_at<T>(in, idx, delta[idx]) : ccast<T>(in[idx]);
     }
     const T ay = g.kyd[ky] * invn;
     v[0][s] = cmk<T>(-ax * P.y, ax * P.x);  // i (kx/n) P
@@ -986,7 +1037,7 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
       rzacc.add_prod(wpf * rf.y, rf.y);
     } else {
       const cx<T> rv = csub(bvec[idx], q);
-      out[idx] = rv;
+      if (out) out[idx] = rv;
       const T wt = (T)(float)w;
       r64acc.add_prod(wt * rv.x, rv.x);
       r64acc.add_prod(wt * rv.y, rv.y);
@@ -1015,7 +1066,7 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
     acc[1] = r32acc.value();
     acc[2] = rzacc.value();
     if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot) && threadIdx.x == 0)
-      resid_refine_init(st, tot[0], tot[1], tot[2]);
+      resid_sweep_init(st, tot[0], tot[1], tot[2]);
   }
 }
 
@@ -1362,7 +1413,7 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
         rzacc.add_prod(wpf * rf.y, rf.y);
       } else {
         const cx<T> rv = csub(aux[s], q);
-        out[idx] = rv;
+        if (out) out[idx] = rv;
         const T wt = (T)(float)w;
         r64acc.add_prod(wt * rv.x, rv.x);
         r64acc.add_prod(wt * rv.y, rv.y);
@@ -1392,7 +1443,7 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
   } else {
     double acc[3] = {r64acc.value(), r32acc.value(), rzacc.value()}, tot[3];
     if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot) && threadIdx.x == 0)
-      resid_refine_init(st, tot[0], tot[1], tot[2]);
+      resid_sweep_init(st, tot[0], tot[1], tot[2]);
   }
 }
 

@@ -169,11 +169,7 @@ __global__ void __launch_bounds__(256) k3_zgrad(Geo<T> g, cx<Tin>* in, const cx<
       P = first ? z : cadd(z, cscale(dio[idx], beta));
       dio[idx] = P;
     } else {
-      P = ccast<T>(in[idx]);
-      if (add_delta) {
-        P = cadd(P, ccast<T>(delta[idx]));
-        in[idx] = ccast<Tin>(P);
-      }
+      P = add_delta ? add_delta_at<T>(in, idx, delta[idx]) : ccast<T>(in[idx]);
     }
     const T az = g.kzd[kz] * invn;
     v[0][s] = cmk<T>(-ax * P.y, ax * P.x);  // i (kx/n) P
@@ -311,7 +307,7 @@ __global__ void __launch_bounds__(256) k3_zdiv(Geo<T> g, Tri<cx<T>*> Q, const cx
       rzacc.add_prod(wpf * rf.y, rf.y);
     } else {
       const cx<T> rv = csub(bvec[idx], q);
-      out[idx] = rv;
+      if (out) out[idx] = rv;
       const T wt = (T)(float)w;
       r64acc.add_prod(wt * rv.x, rv.x);
       r64acc.add_prod(wt * rv.y, rv.y);
@@ -340,7 +336,7 @@ __global__ void __launch_bounds__(256) k3_zdiv(Geo<T> g, Tri<cx<T>*> Q, const cx
     acc[1] = r32acc.value();
     acc[2] = rzacc.value();
     if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot) && threadIdx.x == 0)
-      resid_refine_init(st, tot[0], tot[1], tot[2]);
+      resid_sweep_init(st, tot[0], tot[1], tot[2]);
   }
 }
 

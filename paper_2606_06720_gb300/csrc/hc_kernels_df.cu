@@ -18,6 +18,9 @@ template void col_inv<df64>(const Geo<df64>&, const cx<df64>*, cx<df64>*, df64, 
 template void col_grad<df64, df64>(const Geo<df64>&, int, cx<df64>*, const cx<df64>*, cx<df64>*,
                                    const cx<float>*, cx<df64>*, cx<df64>*, SolveState*, int,
                                    cudaStream_t);
+template void col_grad<df64, double>(const Geo<df64>&, int, cx<double>*, const cx<df64>*, cx<df64>*,
+                                     const cx<float>*, cx<df64>*, cx<df64>*, SolveState*, int,
+                                     cudaStream_t);
 template void col_grad<float, df64>(const Geo<float>&, int, cx<df64>*, const cx<float>*,
                                     cx<float>*, const cx<float>*, cx<float>*, cx<float>*,
                                     SolveState*, int, cudaStream_t);
@@ -48,6 +51,7 @@ void set_smem_limits_df() {
   allow_smem(kp_col_grad<df64, CG_DUPDATE>);
   allow_smem(kp_col_grad<df64, CG_ADDDELTA>);
   set_smem_limits_grad<df64, df64>();
+  set_smem_limits_grad<df64, double>();
   set_smem_limits_grad<float, df64>();
 }
 

@@ -60,6 +60,7 @@ __global__ void k_set_config(SolveState* st, SolveConfig c) {
   st->e_coef[2] = c.e_coef[2];
   st->dt = c.dt;
   st->first32_min2 = c.first32_min2;
+  st->mid_df = c.mid_df;
   st->dim = c.dim;
   st->diag = c.diag;
   st->outer_rtol2 = c.outer_thresh2_rel;
@@ -79,6 +80,9 @@ __global__ void k_step_begin(SolveState* st, int npts) {
   st->msum_old = st->msum;
   st->gm2_next_valid = 0;
   st->first_used = 0;
+  st->mid_phase = 0;
+  st->mid_used = 0;
+  st->res_full = 0;
   st->outer_thresh2 = st->outer_rtol2 * st->outer_b2;
   st->it = 0;
   st->total_it = 0;
@@ -154,6 +158,8 @@ __global__ void k_run_gate(SolveState* st) {
 
 __global__ void k_reset_accum(SolveState* st) {
   st->acc_first = 0;
+  st->acc_mid = 0;
+  st->acc_res_full = 0;
   st->first_bad = 0;
   st->acc_iters = 0;
   st->acc_sweeps = 0;

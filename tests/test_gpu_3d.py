@@ -167,6 +167,43 @@ def test_steps_3d_refined_match_oracle(hc, precision):
         assert rel_l2(p, p_ref) < 1e-6
 
 
+def test_double_float_mid_residual_3d(hc):
+    """3D fp32_refined: the residual after the FP32 first sweep is evaluated in
+    double-float; every step still ends on an FP64 residual (checked with the
+    oracle's operator), one fewer per step than with fp64_mid_residual, and
+    the graph counts the mid-step block's kernels."""
+    w = W.source_sink_3d(32)
+    g = O.Grid(w.n, w.L)
+    b = O.project(g, w.S)
+    r32 = w.r.astype(np.float32).astype(np.float64)
+    outs, extra = [], []
+    for fp64_mid in (False, True):
+        with solver(hc, w.n, w.L, "fp32_refined", c=w.c, D=w.D, gamma=w.gamma, dt=w.dt,
+                    cg_rtol=1e-8, fp64_mid_residual=fp64_mid) as s:
+            s.set_r(w.r)
+            s.set_source(w.S)
+            s.set_m(w.m0)
+            for k in range(5):
+                m_prev = s.get_m()
+                before = s.launch_count()
+                st = s.step(1)
+                launched = s.launch_count() - before
+                assert st.status == hc.HC_OK and st.first_sweep_fp32 == 1
+                assert st.mid_residual_df == (0 if fp64_mid else 1)
+                # each sweep after the FP32 one starts from an FP64 residual, and one
+                # more certifies; the double-float residual starts the second sweep
+                # (or, already below the target, replaces it)
+                want = st.refine_sweeps if fp64_mid else max(1, st.refine_sweeps - 1)
+                assert st.refine_residuals == want, (k, st)
+                res = b - O.apply_A(g, m_prev, r32, s.get_p())
+                assert np.linalg.norm(res) <= 1.2e-8 * np.linalg.norm(b), k
+                # fixed nodes, 6 per CG iteration, 5 per refinement residual
+                extra.append(launched - 6 * st.cg_iters - 5 * (st.refine_residuals + st.mid_residual_df))
+            outs.append((s.get_m(), s.get_p()))
+    assert rel_l2(outs[0][0], outs[1][0]) < 1e-6 and rel_l2(outs[0][1], outs[1][1]) < 1e-6
+    assert len(set(extra)) == 1, extra
+
+
 def test_graph_and_host_loop_agree_3d(hc):
     n, L = (32, 16, 16), (1.0, 0.5, 0.5)
     g, r, S, m0 = _problem(n, L)

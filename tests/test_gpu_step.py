@@ -287,6 +287,49 @@ def test_fp32_first_sweep_keeps_the_fp64_certificate(hc, precision, use_graph):
     assert rel_l2(outs[0][1], outs[1][1]) < 1e-6
 
 
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_double_float_mid_residual_keeps_the_fp64_certificate(hc, use_graph):
+    """fp32_refined evaluates the residual after the FP32 first sweep in
+    double-float (p += delta in FP64).  It only feeds the second inner solve:
+    every step still ends on an FP64 residual, checked again with the
+    oracle's operator, with one FP64 residual fewer per step than with
+    fp64_mid_residual.  Trajectories agree to the solver tolerance, and
+    the graph's kernel bookkeeping counts the mid-step block."""
+    w = W.source_sink_2d(256, steps=5)
+    g = O.Grid(w.n, w.L)
+    m32 = lambda m: m.astype(np.float32).astype(np.float64)  # noqa: E731
+    r32 = m32(w.r)
+    b = O.project(g, w.S)
+    outs, extra = [], []
+    for fp64_mid in (False, True):
+        with make_solver(hc, w, "fp32_refined", rtol=1e-8, use_graph=use_graph,
+                         fp64_mid_residual=fp64_mid) as s:
+            for k in range(5):
+                m_prev = s.get_m()
+                before = s.launch_count()
+                st = s.step(1)
+                launched = s.launch_count() - before
+                assert st.status == 0 and st.first_sweep_fp32 == 1
+                assert st.mid_residual_df == (0 if fp64_mid else 1)
+                # each sweep after the FP32 one starts from an FP64 residual, and one
+                # more certifies; the double-float residual starts the second sweep
+                # (or, already below the target, replaces it)
+                want = st.refine_sweeps if fp64_mid else max(1, st.refine_sweeps - 1)
+                assert st.refine_residuals == want, (k, st)
+                p = s.get_p()
+                res = np.linalg.norm(b - O.apply_A(g, m_prev, r32, p)) / np.linalg.norm(b)
+                assert st.rel_residual <= 1e-8 and res <= 1.2e-8, (k, res)
+                if use_graph:
+                    # fixed nodes, 4 per CG iteration, 3 per refinement residual
+                    extra.append(launched - 4 * st.cg_iters
+                                 - 3 * (st.refine_residuals + st.mid_residual_df))
+            outs.append((s.get_m(), s.get_p()))
+    assert rel_l2(outs[0][0], outs[1][0]) < 1e-6
+    assert rel_l2(outs[0][1], outs[1][1]) < 1e-6
+    if use_graph:
+        assert len(set(extra)) == 1, extra
+
+
 @pytest.mark.parametrize("precision", ["fp32_refined", "fp32_refined_df"])
 @pytest.mark.parametrize("case", ["zero_source", "zero_m", "min_grid", "long_x", "long_y"])
 def test_edge_cases_refined(hc, precision, case):
