@@ -31,9 +31,14 @@ def _cache_path() -> str:
                           os.path.join(os.path.expanduser("~"), ".cache", "hucai_gb300", "tuning.json"))
 
 
+# Launches per step of each kernel relative to the once-per-step ones: the CG
+# kernels run every iteration (about 20 per step on the large grids), so a
+# shared knob is chosen by the weighted sum of the kernels' times.
+_WEIGHT = {"cg_grad": 20, "cg_apply": 20, "cg_div": 20}
+
 # Bumped whenever the kernels' launch-shape trade-offs change, so cached
 # choices made for older kernels are not reused.
-_KERNELS_VERSION = 3
+_KERNELS_VERSION = 4
 
 
 def _key(solver) -> str:
@@ -61,7 +66,8 @@ def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = Fal
              report: dict | None = None) -> dict:
     """Pick the fastest launch shapes for this solver and apply them; returns
     the tuning.  If `report` is a dict it receives the cache key and the
-    measured microseconds per candidate (empty when the cache answered).
+    measured microseconds per candidate, weighted by launches per step
+    (empty when the cache answered).
     3D grids have fixed launch shapes: their tuning is returned unchanged."""
     if getattr(solver, "dim", 2) != 2:
         return solver.get_tuning()
@@ -103,7 +109,8 @@ def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = Fal
                 except Exception:
                     continue
                 label = f"{v}" if pipe is None else f"{v}{['', 'p', 'q'][pipe]}"
-                times[label] = (sum(solver.time_kernel(k, reps) for k in kernels), v, pipe)
+                times[label] = (sum(_WEIGHT.get(k, 1) * solver.time_kernel(k, reps)
+                                    for k in kernels), v, pipe)
         if times:
             lab = min(times, key=lambda k: times[k][0])
             _, v, pipe = times[lab]

@@ -514,33 +514,72 @@ __device__ __forceinline__ cx<T> load_pair_c2r(const cx<T>* __restrict__ A,
   return cmk<T>(a.x + b.y, b.x - a.y);  // conj(A) + i conj(B)
 }
 
-// From the canonical-order spectrum Z of the complex row a + i b, write the
-// packed half spectra of a and b (B may be null).
-template <typename T>
-__device__ __forceinline__ void store_pair_r2c(cx<T> (&v)[1][8], cx<T>* slab, int j, int N, int H,
-                                               cx<T>* __restrict__ A, cx<T>* __restrict__ B) {
+// The canonical-order input of the complex row a + i b of each of NV rows
+// (thread j, slot s: element j + s N/8) from their packed half spectra A, B
+// (both present).  With H = 4 N/8, slots 0..3 lie below the Nyquist index and
+// slots 4..7 above it (mirrored, conjugated); only thread 0 meets the two
+// special elements 0 and H, which share the packed slot 0.
+template <int NV, typename T>
+__device__ __forceinline__ void load_rows_c2r(cx<T> (&v)[NV][8], const cx<T>* const* A,
+                                              const cx<T>* const* B, int j, int N8) {
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int idx = s < 4 ? j + s * N8 : ((s == 4 && j == 0) ? 0 : (8 - s) * N8 - j);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const cx<T> a = A[q][idx], b = B[q][idx];
+      if (s == 0)
+        v[q][s] = j == 0 ? cmk<T>(a.x, b.x) : cmk<T>(a.x - b.y, a.y + b.x);
+      else if (s < 4)
+        v[q][s] = cmk<T>(a.x - b.y, a.y + b.x);  // A + i B
+      else if (s == 4)
+        v[q][s] = j == 0 ? cmk<T>(a.y, b.y) : cmk<T>(a.x + b.y, b.x - a.y);
+      else
+        v[q][s] = cmk<T>(a.x + b.y, b.x - a.y);  // conj(A) + i conj(B)
+    }
+  }
+}
+
+// From the canonical-order spectra Z of NV complex rows a + i b, write the
+// packed half spectra of a and b (B[q] may be null).
+template <int NV, typename T>
+__device__ __forceinline__ void store_rows_r2c(cx<T> (&v)[NV][8], cx<T>* const* slab, int j, int N,
+                                               int H, cx<T>* const* A, cx<T>* const* B) {
   const int N8 = N >> 3;
   __syncthreads();
 #pragma unroll
-  for (int s = 0; s < 8; ++s) slab[rswz<T>(j + s * N8)] = v[0][s];
+  for (int s = 0; s < 8; ++s)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) slab[q][rswz<T>(j + s * N8)] = v[q][s];
   __syncthreads();
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int k = j + s * N8;  // k < H
-    const cx<T> z = slab[rswz<T>(k)];
-    cx<T> a, b;
-    if (k == 0) {
-      const cx<T> zh = slab[rswz<T>(H)];
-      a = cmk<T>(z.x, zh.x);
-      b = cmk<T>(z.y, zh.y);
-    } else {
-      const cx<T> zc = slab[rswz<T>(N - k)];
-      a = cmk<T>((T)0.5 * (z.x + zc.x), (T)0.5 * (z.y - zc.y));
-      b = cmk<T>((T)0.5 * (z.y + zc.y), (T)-0.5 * (z.x - zc.x));
+    const int kc = k == 0 ? H : N - k;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const cx<T> z = slab[q][rswz<T>(k)];
+      const cx<T> zc = slab[q][rswz<T>(kc)];
+      cx<T> a, b;
+      if (k == 0) {
+        a = cmk<T>(z.x, zc.x);
+        b = cmk<T>(z.y, zc.y);
+      } else {
+        a = cmk<T>((T)0.5 * (z.x + zc.x), (T)0.5 * (z.y - zc.y));
+        b = cmk<T>((T)0.5 * (z.y + zc.y), (T)-0.5 * (z.x - zc.x));
+      }
+      A[q][k] = a;
+      if (B[q]) B[q][k] = b;
     }
-    A[k] = a;
-    if (B) B[k] = b;
   }
+}
+template <typename T>
+__device__ __forceinline__ void store_pair_r2c(cx<T> (&v)[1][8], cx<T>* slab, int j, int N, int H,
+                                               cx<T>* __restrict__ A, cx<T>* __restrict__ B) {
+  cx<T>* const sl[1] = {slab};
+  cx<T>* const a[1] = {A};
+  cx<T>* const b[1] = {B};
+  store_rows_r2c<1>(v, sl, j, N, H, a, b);
 }
 
 // ------------------------------------------------------------------ row kernels
@@ -634,8 +673,11 @@ __device__ __forceinline__ void cg_alpha_from(SolveState* st, double gkg, double
 
 // Row pass of the operator apply.  The CTA's rows of m and r are staged into
 // shared memory with cp.async at the start, so their latency overlaps the
-// inverse transform.  DOT: the CG variant (alpha, see cg_alpha_from).
-template <typename T, typename Tm, bool DOT>
+// inverse transform.  DOT: the CG variant (alpha, see cg_alpha_from).  NV
+// rows per thread: a group of N/8 threads transforms NV rows together,
+// sharing twiddles, slot addresses and barriers (the CTA's rpc rows form
+// rpc / NV groups).
+template <typename T, typename Tm, bool DOT, int NV>
 __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
                                                    const Tm* __restrict__ mx,
                                                    const Tm* __restrict__ my,
@@ -646,10 +688,22 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
   const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
-  const int y = (blockIdx.x << g.lrpc) + rb;
-  cx<T>* slab = sm + rb * N;
-  cx<T>* const sl[1] = {slab};
-  // stage rows [y0, y0 + rpc) of mx, my, r (contiguous) behind the slabs
+  const int r0 = rb * NV;                        // first of this group's rows within the CTA
+  const int y0 = (blockIdx.x << g.lrpc) + r0;
+  cx<T>* sl[NV];
+  const cx<T>* Ar[NV];
+  const cx<T>* Br[NV];
+  cx<T>* Qa[NV];
+  cx<T>* Qb[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    sl[q] = sm + (size_t)(r0 + q) * N;
+    Ar[q] = Gx + (size_t)(y0 + q) * H;
+    Br[q] = Gy + (size_t)(y0 + q) * H;
+    Qa[q] = Qx + (size_t)(y0 + q) * H;
+    Qb[q] = Qy + (size_t)(y0 + q) * H;
+  }
+  // stage the CTA's rows of mx, my, r (contiguous) behind the slabs
   Tm* sf = reinterpret_cast<Tm*>(sm + ((size_t)g.rpc << g.lnx));
   {
     const size_t row0 = ((size_t)blockIdx.x << g.lrpc) * N;
@@ -662,30 +716,30 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
     }
     cp_async_commit();
   }
-  const cx<T>* Ar = Gx + (size_t)y * H;
-  const cx<T>* Br = Gy + (size_t)y * H;
-  cx<T> v[1][8];
-#pragma unroll
-  for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
-  fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
+  cx<T> v[NV][8];
+  load_rows_c2r<NV>(v, Ar, Br, j, N8);
+  fft_canon<+1, NV, true>(v, sl, 1, j, g.lnx, g.twx);
   cp_async_wait_all();
   __syncthreads();
   // v = grad p (gx + i gy) at x = j + s N/8: apply (m (x) m + r I)
-  const Tm* smx = sf + (size_t)rb * N;
-  const Tm* smy = smx + (size_t)g.rpc * N;
-  const Tm* srr = smy + (size_t)g.rpc * N;
   DotAcc<T> gkg;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int x = j + s * N8;
-    const T gx = v[0][s].x, gy = v[0][s].y;
-    const T ax = (T)smx[x], ay = (T)smy[x], r = (T)srr[x];
-    const T mg = ax * gx + ay * gy;
-    if (DOT) gkg.add_prod(mg * mg + r * (gx * gx + gy * gy), (T)1);  // one compensated add per point
-    v[0][s] = cmk<T>(ax * mg + r * gx, ay * mg + r * gy);
+  for (int q = 0; q < NV; ++q) {
+    const Tm* smx = sf + (size_t)(r0 + q) * N;
+    const Tm* smy = smx + (size_t)g.rpc * N;
+    const Tm* srr = smy + (size_t)g.rpc * N;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int x = j + s * N8;
+      const T gx = v[q][s].x, gy = v[q][s].y;
+      const T ax = (T)smx[x], ay = (T)smy[x], r = (T)srr[x];
+      const T mg = ax * gx + ay * gy;
+      if (DOT) gkg.add_prod(mg * mg + r * (gx * gx + gy * gy), (T)1);  // one compensated add per point
+      v[q][s] = cmk<T>(ax * mg + r * gx, ay * mg + r * gy);
+    }
   }
-  fft_canon<-1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
-  store_pair_r2c(v, slab, j, N, H, Qx + (size_t)y * H, Qy + (size_t)y * H);
+  fft_canon<-1, NV, true>(v, sl, 1, j, g.lnx, g.twx);
+  store_rows_r2c<NV>(v, sl, j, N, H, Qa, Qb);
   if (DOT) {
     double a1[1] = {gkg.value()}, t1[1];
     if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0)
@@ -2076,12 +2130,22 @@ template <typename T, typename Tm>
 void row_apply(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const Tm* mx, const Tm* my,
                const Tm* r, cx<T>* Qx, cx<T>* Qy, SolveState* st, cudaStream_t s) {
   const size_t sm = row_smem(g) + (size_t)3 * g.rpc * g.nx * sizeof(Tm);
+  if constexpr (std::is_same<T, float>::value) {
+    if (g.rpc >= 2) {  // two rows per thread
+      const int nt = row_threads(g) >> 1;
+      if (st)
+        k_row_apply<T, Tm, true, 2><<<g.ny >> g.lrpc, nt, sm, s>>>(g, Gx, Gy, mx, my, r, Qx, Qy, st);
+      else
+        k_row_apply<T, Tm, false, 2><<<g.ny >> g.lrpc, nt, sm, s>>>(g, Gx, Gy, mx, my, r, Qx, Qy, st);
+      return;
+    }
+  }
   if (st)
-    k_row_apply<T, Tm, true><<<g.ny >> g.lrpc, row_threads(g), sm, s>>>(g, Gx, Gy, mx, my, r, Qx,
-                                                                       Qy, st);
+    k_row_apply<T, Tm, true, 1><<<g.ny >> g.lrpc, row_threads(g), sm, s>>>(g, Gx, Gy, mx, my, r, Qx,
+                                                                          Qy, st);
   else
-    k_row_apply<T, Tm, false><<<g.ny >> g.lrpc, row_threads(g), sm, s>>>(g, Gx, Gy, mx, my, r, Qx,
-                                                                        Qy, st);
+    k_row_apply<T, Tm, false, 1><<<g.ny >> g.lrpc, row_threads(g), sm, s>>>(g, Gx, Gy, mx, my, r, Qx,
+                                                                           Qy, st);
 }
 template <typename T>
 void row_split(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const T* mx, const T* my,
@@ -2281,8 +2345,12 @@ template <typename T>
 void set_smem_limits_t() {
   allow_smem(k_row_r2c<T>);
   allow_smem(k_row_c2r<T>);
-  allow_smem(k_row_apply<T, T, false>);
-  allow_smem(k_row_apply<T, T, true>);
+  allow_smem(k_row_apply<T, T, false, 1>);
+  allow_smem(k_row_apply<T, T, true, 1>);
+  if constexpr (std::is_same<T, float>::value) {
+    allow_smem(k_row_apply<T, T, false, 2>);
+    allow_smem(k_row_apply<T, T, true, 2>);
+  }
   allow_smem(k_row_split<T>);
   allow_smem(k_col_fwd<T, 1>);
   allow_smem(k_col_fwd<T, 2>);

@@ -34,8 +34,8 @@ template void convert<float, df64>(const df64*, float*, size_t, cudaStream_t);
 void set_smem_limits_df() {
   allow_smem(k_row_r2c<df64>);
   allow_smem(k_row_c2r<df64>);
-  allow_smem(k_row_apply<df64, float, false>);
-  allow_smem(k_row_apply<df64, float, true>);
+  allow_smem(k_row_apply<df64, float, false, 1>);
+  allow_smem(k_row_apply<df64, float, true, 1>);
   allow_smem(k_col_fwd<df64, 1>);
   allow_smem(k_col_fwd<df64, 2>);
   allow_smem(k_col_inv<df64>);

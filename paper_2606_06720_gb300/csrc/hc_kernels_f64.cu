@@ -50,8 +50,8 @@ template void spec_norm2<double>(const Geo<double>&, const cx<double>*, SolveSta
 void set_smem_limits_f64() {
   set_smem_limits_t<double>();
   set_smem_limits_grad<double, double>();
-  allow_smem(k_row_apply<double, float, false>);
-  allow_smem(k_row_apply<double, float, true>);
+  allow_smem(k_row_apply<double, float, false, 1>);
+  allow_smem(k_row_apply<double, float, true, 1>);
 }
 
 __global__ void k_set_config(SolveState* st, SolveConfig c) {

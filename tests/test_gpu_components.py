@@ -70,6 +70,28 @@ def test_operator_matches_oracle(hc, precision, n, L):
     assert rel_l2(Af, ref) < TOL[precision] * 5
 
 
+@pytest.mark.parametrize("n", [(2048, 64), (512, 256), (64, 32)])
+@pytest.mark.parametrize("rows", [1, 2, 4, 8])
+def test_operator_row_pairs_match_oracle(hc, n, rows):
+    """The FP32 row pass transforms two rows per thread when a CTA holds two or
+    more rows (row_rows >= 2), one otherwise; every admissible setting matches
+    the oracle's operator."""
+    if rows * n[0] // 8 > 512:
+        pytest.skip("more than 512 threads per CTA")
+    g = O.Grid(n)
+    m = RNG.uniform(0, 1, (2,) + g.shape)
+    r = W.smooth_r(n, 1)
+    f = RNG.standard_normal(g.shape)
+    with solver(hc, n, precision="fp32_refined") as s:
+        t = s.get_tuning()
+        s.set_tuning(t["col_tile"], [rows, t["row_rows"][1]], t["col_pipe"])
+        s.set_m(m)
+        s.set_r(r)
+        Af = s.apply_operator(f)
+    ref = O.apply_A(g, m, r, O.project(g, f))
+    assert rel_l2(Af, ref) < TOL["fp32_refined"] * 5
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
 @pytest.mark.parametrize("gamma", [0.5, 0.75, 1.0, 1.5])
 def test_split_step_matches_oracle(hc, precision, gamma):

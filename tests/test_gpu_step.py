@@ -257,6 +257,24 @@ def test_pipelined_column_passes_match_plain_ones(hc, precision):
         assert rel_l2(p, outs[0][1]) < 1e-6
 
 
+def test_row_pairs_match_single_rows(hc):
+    """The FP32 CG row pass with two rows per thread (row_rows 2 and 4) takes
+    the same steps as with one row per CTA, to the rounding of the regrouped
+    <d, A d> reduction; every step stays certified."""
+    w = W.source_sink_2d(512, steps=3)
+    outs = []
+    for rows in (1, 2, 4):
+        with make_solver(hc, w, "fp32_refined") as s:
+            t = s.get_tuning()
+            s.set_tuning(t["col_tile"], [rows, t["row_rows"][1]], t["col_pipe"])
+            st = s.step(3)
+            assert st.status == 0 and st.rel_residual <= w.cg_rtol
+            outs.append((s.get_m(), s.get_p()))
+    for m, p in outs[1:]:
+        assert rel_l2(m, outs[0][0]) < 1e-6
+        assert rel_l2(p, outs[0][1]) < 1e-6
+
+
 @pytest.mark.parametrize("precision", ["fp32_refined", "fp32_refined_df"])
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_fp32_first_sweep_keeps_the_fp64_certificate(hc, precision, use_graph):
