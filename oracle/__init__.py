@@ -79,12 +79,14 @@ def _load():
             lib.or_apply_K.argtypes = [C.c_int, C.c_size_t, dp, dp, dp, dp]
             lib.or_apply_K.restype = None
             lib.or_apply_A.argtypes = [gp, dp, dp, dp, dp]
-            lib.or_precond.argtypes = [gp, C.c_double, dp, dp]
+            lib.or_precond.argtypes = [gp, dp, dp, dp]
+            lib.or_kbar_default.argtypes = [gp, dp, dp, dp]
+            lib.or_kbar_default.restype = None
             lib.or_project.argtypes = [gp, dp]
             lib.or_project.restype = None
             lib.or_kappa_default.argtypes = [gp, dp, dp]
             lib.or_kappa_default.restype = C.c_double
-            lib.or_pcg.argtypes = [gp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_int,
+            lib.or_pcg.argtypes = [gp, dp, dp, dp, dp, dp, C.c_double, C.c_int,
                                    C.POINTER(_Stats)]
             lib.or_activation.argtypes = [C.c_int, C.c_size_t, dp, dp, C.c_double, C.c_double]
             lib.or_activation.restype = None
@@ -238,11 +240,37 @@ def apply_A(grid: Grid, m, r, p) -> np.ndarray:
     return out
 
 
-def precond(grid: Grid, kappa: float, res) -> np.ndarray:
+def kbar_array(dim: int, kbar) -> np.ndarray:
+    """The preconditioner matrix in the oracle's layout (xx, yy, zz, xy, xz, yz)
+    from a scalar kappa (kappa I), a dim x dim symmetric matrix, or the
+    6-vector itself."""
+    a = np.asarray(kbar, dtype=np.float64)
+    if a.ndim == 0:
+        return np.array([float(a) if e < dim else 0.0 for e in range(6)])
+    if a.shape == (6,):
+        return a.copy()
+    M = np.zeros((3, 3))
+    M[:dim, :dim] = a
+    return np.array([M[0, 0], M[1, 1], M[2, 2], M[0, 1], M[0, 2], M[1, 2]])
+
+
+def precond(grid: Grid, kbar, res) -> np.ndarray:
+    """z = F^-1[F(res) / (xi~^T Kbar xi~)] (reading R3); kbar as in kbar_array."""
     res = _f64(res)
     out = np.empty(grid.shape)
     g = grid.c()
-    _check(_load().or_precond(C.byref(g), kappa, _dp(res), _dp(out)), "precond")
+    kb = kbar_array(grid.dim, kbar)
+    _check(_load().or_precond(C.byref(g), _dp(kb), _dp(res), _dp(out)), "precond")
+    return out
+
+
+def kbar_default(grid: Grid, m, r) -> np.ndarray:
+    """The default preconditioner matrix mean(m m^T) + mean(r) I (reading R3),
+    as the 6-vector xx, yy, zz, xy, xz, yz."""
+    m, r = _f64(m), _f64(r)
+    out = np.zeros(6)
+    g = grid.c()
+    _load().or_kbar_default(C.byref(g), _dp(m), _dp(r), _dp(out))
     return out
 
 
@@ -259,16 +287,16 @@ def kappa_default(grid: Grid, m, r) -> float:
     return _load().or_kappa_default(C.byref(g), _dp(m), _dp(r))
 
 
-def pcg(grid: Grid, m, r, b, x0=None, kappa: float | None = None, rtol: float = 1e-10,
-        maxit: int = 1000):
-    """Returns (x, Stats); raises nothing on non-convergence (Stats.rc says)."""
+def pcg(grid: Grid, m, r, b, x0=None, kappa=None, rtol: float = 1e-10, maxit: int = 1000):
+    """Returns (x, Stats); raises nothing on non-convergence (Stats.rc says).
+    kappa: None for the default Kbar of R3, else a scalar kappa (kappa I), a
+    dim x dim matrix or the 6-vector of kbar_array."""
     m, r, b = _f64(m), _f64(r), _f64(b)
     x = np.zeros(grid.shape) if x0 is None else _f64(x0).reshape(grid.shape).copy()
-    if kappa is None:
-        kappa = kappa_default(grid, m, r)
+    kb = kbar_default(grid, m, r) if kappa is None else kbar_array(grid.dim, kappa)
     st = _Stats()
     g = grid.c()
-    rc = _load().or_pcg(C.byref(g), _dp(m), _dp(r), _dp(b), _dp(x), kappa, rtol, int(maxit),
+    rc = _load().or_pcg(C.byref(g), _dp(m), _dp(r), _dp(b), _dp(x), _dp(kb), rtol, int(maxit),
                         C.byref(st))
     if rc not in (OK, ENOCONV):
         _check(rc, "pcg")

@@ -15,8 +15,10 @@
  *   R2  the null space of the discrete operator is spanned by the 2^dim corner
  *       modes (every index 0 or N/2); S, p and the CG iterates are kept
  *       orthogonal to it;
- *   R3  preconditioner: constant-coefficient operator kappa * (-Laplacian) with
- *       kappa = mean(r) + mean(|m|^2)/dim, inverted on the non-null modes;
+ *   R3  preconditioner: the constant-coefficient operator -div(Kbar grad) with
+ *       Kbar = mean over the grid of K = m m^T + r I (a constant symmetric
+ *       matrix), built from the same derivative symbols and inverted on the
+ *       non-null modes; a user kappa > 0 gives Kbar = kappa I;
  *   R4  CG stops when ||res||_2 <= rtol ||S||_2 (plain Euclidean norms);
  *   R5  p^0 = 0 unless the caller supplies one;
  *   R6  the activation uses grad p^{k+1} (Algorithm 1 solves for p first);
@@ -274,20 +276,29 @@ int or_apply_A(const or_grid* g, const double* m, const double* r, const double*
   return rc;
 }
 
-int or_precond(const or_grid* g, double kappa, const double* res, double* z) {
-  if (!valid_grid(g) || !(kappa > 0)) return OR_EINVAL;
+/* Entry (a, b) of the symmetric matrix stored as xx, yy, zz, xy, xz, yz. */
+static double kbar_at(const double* kbar, int a, int b) {
+  static const int idx[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+  return kbar[idx[a][b]];
+}
+
+int or_precond(const or_grid* g, const double* kbar, const double* res, double* z) {
+  if (!valid_grid(g) || !kbar) return OR_EINVAL;
+  for (int a = 0; a < g->dim; ++a)
+    if (!(kbar_at(kbar, a, a) > 0)) return OR_EINVAL;
   size_t npts = or_npts(g);
   double complex* t = (double complex*)malloc(sizeof(double complex) * npts);
   if (!t) return OR_ENOMEM;
   for (size_t q = 0; q < npts; ++q) t[q] = res[q];
   int rc = or_fftn(g, t, -1);
   for (size_t q = 0; q < npts && !rc; ++q) {
-    double s = 0; /* |xi~|^2, the symbol of -Laplacian built from the same derivatives */
-    for (int c = 0; c < g->dim; ++c) {
-      double x = or_xi_deriv(coord(g, q, c), g->n[c], g->L[c]);
-      s += x * x;
-    }
-    t[q] = (s > 0) ? t[q] / (kappa * s) : 0;
+    /* xi~^T Kbar xi~, the symbol of -div(Kbar grad) built from the same derivatives */
+    double xi[3] = {0, 0, 0};
+    for (int c = 0; c < g->dim; ++c) xi[c] = or_xi_deriv(coord(g, q, c), g->n[c], g->L[c]);
+    double s = 0;
+    for (int a = 0; a < g->dim; ++a)
+      for (int b = 0; b < g->dim; ++b) s += xi[a] * kbar_at(kbar, a, b) * xi[b];
+    t[q] = (s > 0) ? t[q] / s : 0;
   }
   if (!rc) rc = or_fftn(g, t, +1);
   if (!rc)
@@ -322,6 +333,22 @@ void or_project(const or_grid* g, double* f) {
   }
 }
 
+void or_kbar_default(const or_grid* g, const double* m, const double* r, double* kbar) {
+  size_t npts = or_npts(g);
+  int dim = g->dim;
+  static const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+  double sr = 0;
+  for (size_t q = 0; q < npts; ++q) sr += r[q];
+  for (int e = 0; e < 6; ++e) {
+    kbar[e] = 0;
+    if (pa[e] >= dim || pb[e] >= dim) continue;
+    double s = 0;
+    for (size_t q = 0; q < npts; ++q) s += m[(size_t)pa[e] * npts + q] * m[(size_t)pb[e] * npts + q];
+    kbar[e] = s / (double)npts + (pa[e] == pb[e] ? sr / (double)npts : 0.0);
+  }
+}
+
+/* trace(Kbar) / dim of the default Kbar: the isotropic part, reported as kappa */
 double or_kappa_default(const or_grid* g, const double* m, const double* r) {
   size_t npts = or_npts(g);
   double sr = 0, sm = 0;
@@ -330,6 +357,16 @@ double or_kappa_default(const or_grid* g, const double* m, const double* r) {
     for (int c = 0; c < g->dim; ++c) sm += m[(size_t)c * npts + q] * m[(size_t)c * npts + q];
   }
   return sr / (double)npts + sm / (double)npts / (double)g->dim;
+}
+
+/* Kbar of a solve: the caller's kappa I when kappa > 0, else the default (R3). */
+static void or_kbar_for(const or_grid* g, const or_params* prm, const double* m, const double* r,
+                        double* kbar) {
+  if (prm->kappa > 0) {
+    for (int e = 0; e < 6; ++e) kbar[e] = (e < g->dim) ? prm->kappa : 0.0;
+  } else {
+    or_kbar_default(g, m, r, kbar);
+  }
 }
 
 static double dot(size_t n, const double* a, const double* b) {
@@ -343,8 +380,10 @@ static double dot(size_t n, const double* a, const double* b) {
 /* ------------------------------------------------------------------ */
 
 int or_pcg(const or_grid* g, const double* m, const double* r, const double* b, double* x,
-           double kappa, double rtol, int maxit, or_stats* st) {
-  if (!valid_grid(g) || !(kappa > 0) || maxit < 0) return OR_EINVAL;
+           const double* kbar, double rtol, int maxit, or_stats* st) {
+  if (!valid_grid(g) || !kbar || maxit < 0) return OR_EINVAL;
+  double kappa = 0; /* reported: trace(Kbar) / dim */
+  for (int a = 0; a < g->dim; ++a) kappa += kbar[a] / (double)g->dim;
   size_t n = or_npts(g);
   double* res = (double*)malloc(sizeof(double) * n);
   double* z = (double*)malloc(sizeof(double) * n);
@@ -369,7 +408,7 @@ int or_pcg(const or_grid* g, const double* m, const double* r, const double* b, 
   if (!rc) {
     for (size_t i = 0; i < n; ++i) res[i] = b[i] - q[i];
     rnorm = sqrt(dot(n, res, res));
-    rc = or_precond(g, kappa, res, z);
+    rc = or_precond(g, kbar, res, z);
   }
   if (!rc) {
     memcpy(d, z, sizeof(double) * n);
@@ -381,7 +420,7 @@ int or_pcg(const or_grid* g, const double* m, const double* r, const double* b, 
       for (size_t i = 0; i < n; ++i) x[i] += alpha * d[i];
       for (size_t i = 0; i < n; ++i) res[i] -= alpha * q[i];
       rnorm = sqrt(dot(n, res, res));
-      rc = or_precond(g, kappa, res, z);
+      rc = or_precond(g, kbar, res, z);
       if (rc) break;
       double rho_new = dot(n, res, z);
       double beta = rho_new / rho;
@@ -495,10 +534,11 @@ int or_step(const or_grid* g, const or_params* prm, const double* r, const doubl
   if (!b || !grad) { free(b); free(grad); return OR_ENOMEM; }
   memcpy(b, S, sizeof(double) * npts);
   or_project(g, b); /* solvability: S orthogonal to the null space (R2) */
-  double kappa = prm->kappa > 0 ? prm->kappa : or_kappa_default(g, m, r);
+  double kbar[6];
+  or_kbar_for(g, prm, m, r, kbar);
   or_stats local;
   /* Step 1: pressure from m^k, warm start p^k */
-  int rc = or_pcg(g, m, r, b, p, kappa, prm->cg_rtol, prm->cg_maxit, &local);
+  int rc = or_pcg(g, m, r, b, p, kbar, prm->cg_rtol, prm->cg_maxit, &local);
   int solve_rc = rc;
   if (rc == OR_ENOCONV) rc = OR_OK; /* state still advanced, flag returned below */
   /* Step 2: splitting with grad p^{k+1} (R6) */
@@ -646,7 +686,8 @@ int or_adjoint(const or_grid* g, const or_params* prm, const double* r, const do
   for (int k = nsteps - 1; k >= 0 && !rc; --k) {
     const double* m = ms + vn * k;
     const double* p = ps + n * (k + 1); /* solved with m^k */
-    double kappa = prm->kappa > 0 ? prm->kappa : or_kappa_default(g, m, r);
+    double kbar[6];
+    or_kbar_for(g, prm, m, r, kbar);
     rc = or_gradient(g, p, grad);
     if (rc) break;
     /* recompute a and b */
@@ -712,7 +753,7 @@ int or_adjoint(const or_grid* g, const or_params* prm, const double* r, const do
     /* adjoint pressure solve A mu = lambda_p (A symmetric) */
     memset(mu, 0, sizeof(double) * n);
     or_stats st;
-    int s_rc = or_pcg(g, m, r, lp, mu, kappa, prm->cg_rtol, prm->cg_maxit, &st);
+    int s_rc = or_pcg(g, m, r, lp, mu, kbar, prm->cg_rtol, prm->cg_maxit, &st);
     if (s_rc && s_rc != OR_ENOCONV) { rc = s_rc; break; }
     for (size_t q = 0; q < n; ++q) dS[q] += mu[q];
     rc = or_gradient(g, mu, gmu);

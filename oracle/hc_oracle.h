@@ -39,14 +39,14 @@ typedef struct {
   double c, D, gamma, dt;  /* model parameters of eqs (1.1a)-(1.1b) and the time step */
   double cg_rtol;          /* stop when ||S - A p||_2 <= cg_rtol ||S||_2 (reading R4) */
   int cg_maxit;            /* iteration cap */
-  double kappa;            /* preconditioner constant; <= 0 selects the default rule R3 */
+  double kappa;            /* > 0: preconditioner kappa (-Laplacian); <= 0: the default Kbar of R3 */
 } or_params;
 
 typedef struct {
   int cg_iters;             /* CG iterations of the pressure solve */
   double rel_residual;      /* recursively updated ||r|| / ||S|| at exit */
   double true_rel_residual; /* ||S - A p|| / ||S|| recomputed at exit */
-  double kappa;             /* preconditioner constant that was used */
+  double kappa;             /* trace(Kbar) / dim of the preconditioner that was used */
 } or_stats;
 
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_ENOCONV = -4, OR_ENONFINITE = -5 };
@@ -82,20 +82,25 @@ void or_apply_K(int dim, size_t npts, const double* m, const double* r,
 /* Discrete pressure operator of eq. (p_discrete): A p = -F^-1[i xi . F(K F^-1[i xi F p])]. */
 int or_apply_A(const or_grid* g, const double* m, const double* r, const double* p, double* Ap);
 
-/* Constant-coefficient preconditioner (R3): z = F^-1[ F(res) / (kappa |xi~|^2) ],
- * zero on the null modes. */
-int or_precond(const or_grid* g, double kappa, const double* res, double* z);
+/* Constant-coefficient preconditioner (R3): z = F^-1[ F(res) / (xi~^T Kbar xi~) ],
+ * zero on the null modes.  kbar: the symmetric matrix Kbar as 6 doubles
+ * xx, yy, zz, xy, xz, yz (2D reads xx, yy, xy); its diagonal must be > 0. */
+int or_precond(const or_grid* g, const double* kbar, const double* res, double* z);
 
 /* Remove the null-space components of A (the 2^dim corner modes, R2) in place. */
 void or_project(const or_grid* g, double* f);
 
-/* Default preconditioner constant (R3): mean(r) + mean(|m|^2) / dim. */
+/* Default Kbar (R3): mean(m m^T) + mean(r) I, in the layout of or_precond. */
+void or_kbar_default(const or_grid* g, const double* m, const double* r, double* kbar);
+
+/* Its isotropic part trace(Kbar) / dim = mean(r) + mean(|m|^2) / dim, the
+ * value reported as kappa. */
 double or_kappa_default(const or_grid* g, const double* m, const double* r);
 
 /* Preconditioned CG (Section 2.4) for A p = b, b projected; p in/out holds the
  * initial guess on entry.  Returns OR_OK or OR_ENOCONV. */
 int or_pcg(const or_grid* g, const double* m, const double* r, const double* b, double* p,
-           double kappa, double rtol, int maxit, or_stats* st);
+           const double* kbar, double rtol, int maxit, or_stats* st);
 
 /* Exact activation substep, eq. (m_activation_discrete), pointwise. */
 void or_activation(int dim, size_t npts, double* m, const double* grad_p, double c, double dt);

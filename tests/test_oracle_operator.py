@@ -158,17 +158,62 @@ def test_pcg_constant_coefficient_converges_in_one_iteration():
     assert np.allclose(x, np.fft.ifft2(ph).real, atol=1e-12)
 
 
+def test_pcg_constant_anisotropic_coefficient_converges_in_one_iteration():
+    """With constant m and r the default preconditioner -div(Kbar grad), Kbar =
+    mean(m m^T) + mean(r) I = K, is the operator itself: one iteration, and the
+    closed form p^ = S^ / (xi~^T K xi~) off the null modes (reading R3)."""
+    g = O.Grid((16, 32), (1.0, 2.0))
+    mc, r0 = np.array([0.6, -0.3]), 0.15
+    m = np.broadcast_to(mc[:, None, None], (2,) + g.shape).copy()
+    r = np.full(g.shape, r0)
+    S = O.project(g, RNG.standard_normal(g.shape))
+    x, st = O.pcg(g, m, r, S, rtol=1e-12, maxit=10)
+    assert st.rc == O.OK and st.cg_iters == 1
+    n = g.n
+    lx = np.arange(n[0]); ly = np.arange(n[1])
+    xix = np.where(lx < n[0] // 2, 2 * np.pi * lx / 1.0, np.where(lx == n[0] // 2, 0.0, 2 * np.pi * (lx - n[0]) / 1.0))
+    xiy = np.where(ly < n[1] // 2, 2 * np.pi * ly / 2.0, np.where(ly == n[1] // 2, 0.0, 2 * np.pi * (ly - n[1]) / 2.0))
+    X, Y = xix[None, :], xiy[:, None]
+    sym = (mc[0] * X + mc[1] * Y) ** 2 + r0 * (X ** 2 + Y ** 2)
+    Sh = np.fft.fft2(S)
+    ph = np.where(sym > 0, Sh / np.where(sym > 0, sym, 1), 0)
+    assert np.allclose(x, np.fft.ifft2(ph).real, atol=1e-12)
+    # kappa is reported as trace(Kbar) / dim
+    assert st.kappa == pytest.approx(r0 + (mc ** 2).sum() / 2, rel=1e-14)
+
+
+def test_preconditioner_on_single_mode_3d():
+    """One Fourier mode cos(xi . x) is an eigenfunction of -div(Kbar grad) with
+    eigenvalue xi^T Kbar xi (xi written out by hand, off the Nyquist indices)."""
+    g = O.Grid((8, 16, 8), (1.0, 2.0, 0.5))
+    K = np.array([[0.5, 0.1, -0.2], [0.1, 0.4, 0.05], [-0.2, 0.05, 0.3]])
+    kvec = np.array([1, 3, 2])  # mode indices along x, y, z
+    xi = 2 * np.pi * kvec / np.array(g.L)
+    xs = [np.arange(n) * (Lx / n) for n, Lx in zip(g.n, g.L)]
+    Z, Yg, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    f = np.cos(xi[0] * X + xi[1] * Yg + xi[2] * Z)
+    z = O.precond(g, K, f)
+    assert np.allclose(z, f / (xi @ K @ xi), atol=1e-12)
+
+
 def test_pcg_iterations_within_condition_bound():
-    """Generalised eigenvalues of (A, kappa L) lie in [min eig K, max eig K]/kappa,
-    so the CG error bound gives it <= ceil(sqrt(cond)/2 * ln(2/rtol))."""
+    """Generalised eigenvalues of (A, -div(Kbar grad)) lie between the extreme
+    pointwise eigenvalues of Kbar^-1/2 K(x) Kbar^-1/2, so the CG error bound
+    gives it <= ceil(sqrt(cond)/2 * ln(2/rtol))."""
     g = O.Grid((32, 32))
     m = RNG.uniform(0, 1, (2,) + g.shape)
     r = RNG.uniform(0.05, 0.15, g.shape)
     S = O.project(g, RNG.standard_normal(g.shape))
     rtol = 1e-10
-    cond = (r + (m ** 2).sum(0)).max() / r.min()
+    kb = O.kbar_default(g, m, r)
+    Kbar = np.array([[kb[0], kb[3]], [kb[3], kb[1]]])
+    w, V = np.linalg.eigh(Kbar)
+    Kih = V @ np.diag(w ** -0.5) @ V.T
+    K = np.einsum("a...,b...->...ab", m, m) + r[..., None, None] * np.eye(2)
+    lam = np.linalg.eigvalsh(Kih @ K @ Kih)
+    cond = lam.max() / lam.min()
     # bound on ||e||_A; relative residual picks up at most sqrt(cond(A)) more
-    condA = cond * (2 * np.pi * 16) ** 2 / (2 * np.pi) ** 2
+    condA = cond * (w.max() / w.min()) * (2 * np.pi * 16) ** 2 / (2 * np.pi) ** 2
     bound = int(np.ceil(0.5 * np.sqrt(cond) * np.log(2 * np.sqrt(condA) / rtol)))
     x, st = O.pcg(g, m, r, S, rtol=rtol, maxit=10000)
     assert st.rc == O.OK
