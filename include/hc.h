@@ -78,7 +78,9 @@ typedef struct {
   double cg_rtol;         /* stop when ||S - A p||_2 <= cg_rtol ||S||_2, S projected (Section 2.4; default 1e-7 if <= 0) */
   int cg_maxit;           /* CG iteration cap per solve; in refined mode per inner FP32 solve (default 1000 if <= 0) */
   int precision;          /* HC_FP64_PLAIN or HC_FP32_REFINED */
-  double kappa;           /* preconditioner constant; <= 0: mean(r) + mean(|m|^2)/dim, recomputed every step */
+  double kappa;           /* > 0: preconditioner kappa (-Laplacian); <= 0: -div(Kbar grad) with
+                             Kbar = mean(m m^T) + mean(r) I, recomputed every step (reading of the
+                             conclusion's constant-coefficient preconditioner) */
   double inner_rtol;      /* refined mode: inner FP32 CG stops at this reduction of its own residual (default 1e-4 if <= 0) */
   int max_sweeps;         /* refined mode: cap on FP64 refinement sweeps per solve (default 10 if <= 0) */
   int use_graph;          /* 1: each step runs as one CUDA graph with device-side loop control; 0: host loop */
@@ -101,7 +103,7 @@ typedef struct {
   int cg_iters;        /* CG iterations of the last step's pressure solve (summed over sweeps) */
   int refine_sweeps;   /* refined mode: inner solves run; plain mode: 0 */
   double rel_residual; /* ||S - A p||_2 / ||S||_2 at exit: FP64-evaluated in refined mode, recursive in plain mode */
-  double kappa;        /* preconditioner constant used */
+  double kappa;        /* trace(Kbar) / dim of the preconditioner used (the isotropic part) */
   int status;          /* HC_OK, HC_ENOCONV or HC_ENONFINITE for that step */
   long long total_cg_iters; /* CG iterations summed over all steps of the hc_step call */
   long long total_sweeps;   /* refinement sweeps summed likewise */

@@ -191,7 +191,7 @@ void layout(hc_ctx* c, Layout& L) {
   const size_t S32 = c->ns * sizeof(cx<float>);
   c->st = L.take<hc::SolveState>(sizeof(hc::SolveState));
   c->st_time = L.take<hc::SolveState>(sizeof(hc::SolveState));
-  c->partials = L.take<double>(sizeof(double) * 4 * max_reducing_ctas(c));
+  c->partials = L.take<double>(sizeof(double) * hc::kPartialStride * max_reducing_ctas(c));
   c->stage = L.take<double>(sizeof(double) * d * n);
   c->p64 = L.take<cx<double>>(S64);
   c->b64 = L.take<cx<double>>(S64);
@@ -1839,11 +1839,17 @@ struct AdjLayout {
   T *lam, *lm;          // lambda and lambda_m (2n each)
   double* dr;           // dL/dr accumulator (n)
   cx<double>* dS;       // dL/dS accumulator, packed spectrum
-  double* cpk;          // sum |m|^2 (the kappa input) of each checkpoint
+  double* cpk;          // sum |m|^2 and sum m_a m_b (the preconditioner's input) of each checkpoint
   double* segk;         // ... of each state of the segment
   double* kT;           // ... of the final state
   size_t bytes;
 };
+
+// Doubles of the sums of m kept with a state: sum |m|^2 and the six sums
+// m_a m_b (contiguous in SolveState).
+constexpr int kMsums = 7;
+static_assert(offsetof(hc::SolveState, mm) == offsetof(hc::SolveState, msum) + sizeof(double),
+              "the sums of m must be contiguous");
 
 template <typename T>
 void adj_layout(const hc_ctx* c, int nsteps, int every, char* base, AdjLayout<T>& a) {
@@ -1868,9 +1874,9 @@ void adj_layout(const hc_ctx* c, int nsteps, int every, char* base, AdjLayout<T>
   a.lm = L.take<T>(sizeof(T) * 2 * n);
   a.dr = L.take<double>(sizeof(double) * n);
   a.dS = L.take<cx<double>>(sizeof(cx<double>) * ns);
-  a.cpk = L.take<double>(sizeof(double) * ncp);
-  a.segk = L.take<double>(sizeof(double) * seg);
-  a.kT = L.take<double>(sizeof(double));
+  a.cpk = L.take<double>(sizeof(double) * kMsums * ncp);
+  a.segk = L.take<double>(sizeof(double) * kMsums * seg);
+  a.kT = L.take<double>(sizeof(double) * kMsums);
   a.bytes = (L.off + kAlign - 1) / kAlign * kAlign;
 }
 
@@ -1900,12 +1906,14 @@ int copy_m(hc_ctx* c, T* dst, const T* src) {
   return HC_OK;
 }
 
-// A state is (m, p, sum |m|^2): restoring the exact sum keeps kappa, hence
-// every CG iterate of a recomputed step, identical to the original forward.
+// A state is (m, p, the sums of m): restoring the exact sums keeps the
+// preconditioner, hence every CG iterate of a recomputed step, identical to
+// the original forward.
 template <typename T>
 int save_state(hc_ctx* c, T* m, cx<double>* p, double* msum) {
   const size_t ns = (size_t)c->ny * c->H;
-  CU(cudaMemcpyAsync(msum, &c->st->msum, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(msum, &c->st->msum, sizeof(double) * kMsums, cudaMemcpyDeviceToDevice,
+                     c->stream));
   CU(cudaMemcpyAsync(m, c->m[0], sizeof(T) * c->n, cudaMemcpyDeviceToDevice, c->stream));
   CU(cudaMemcpyAsync(m + c->n, c->m[1], sizeof(T) * c->n, cudaMemcpyDeviceToDevice, c->stream));
   if (p) CU(cudaMemcpyAsync(p, c->p64, sizeof(cx<double>) * ns, cudaMemcpyDeviceToDevice, c->stream));
@@ -1918,7 +1926,8 @@ int load_state(hc_ctx* c, const T* m, const cx<double>* p, const double* msum) {
   CU(cudaMemcpyAsync(c->m[0], m, sizeof(T) * c->n, cudaMemcpyDeviceToDevice, c->stream));
   CU(cudaMemcpyAsync(c->m[1], m + c->n, sizeof(T) * c->n, cudaMemcpyDeviceToDevice, c->stream));
   if (p) CU(cudaMemcpyAsync(c->p64, p, sizeof(cx<double>) * ns, cudaMemcpyDeviceToDevice, c->stream));
-  CU(cudaMemcpyAsync(&c->st->msum, msum, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(&c->st->msum, msum, sizeof(double) * kMsums, cudaMemcpyDeviceToDevice,
+                     c->stream));
   return HC_OK;
 }
 
@@ -1986,7 +1995,7 @@ int adjoint_t(hc_ctx* c, hc::Geo<T>& g, int nsteps, int every, const double* lam
   for (int k = 0; k < nsteps; ++k) {
     if (k % every == 0) {
       rc = save_state<T>(c, a.cpm + 2 * n * (k / every), a.cpp + ns * (k / every),
-                         a.cpk + k / every);
+                         a.cpk + kMsums * (k / every));
       if (rc) return rc;
     }
     rc = hc_step(c, 1, nullptr);
@@ -2005,13 +2014,13 @@ int adjoint_t(hc_ctx* c, hc::Geo<T>& g, int nsteps, int every, const double* lam
   const int nseg = nsteps > 0 ? (nsteps + every - 1) / every : 0;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int k0 = sg * every, k1 = std::min(k0 + every, nsteps);
-    rc = load_state<T>(c, a.cpm + 2 * n * sg, a.cpp + ns * sg, a.cpk + sg);
+    rc = load_state<T>(c, a.cpm + 2 * n * sg, a.cpp + ns * sg, a.cpk + kMsums * sg);
     if (rc) return rc;
     CU(cudaMemcpyAsync(c->b64, a.b_save, sizeof(cx<double>) * ns, cudaMemcpyDeviceToDevice, s));
     rc = restore_b2(c, b2_save);
     if (rc) return rc;
     for (int k = k0; k < k1; ++k) {
-      rc = save_state<T>(c, a.segm + 2 * n * (k - k0), nullptr, a.segk + (k - k0));
+      rc = save_state<T>(c, a.segm + 2 * n * (k - k0), nullptr, a.segk + kMsums * (k - k0));
       if (rc) return rc;
       rc = hc_step(c, 1, nullptr);
       if (rc && rc != HC_ENOCONV) return rc;
@@ -2019,7 +2028,8 @@ int adjoint_t(hc_ctx* c, hc::Geo<T>& g, int nsteps, int every, const double* lam
                          cudaMemcpyDeviceToDevice, s));
     }
     for (int k = k1 - 1; k >= k0; --k) {
-      rc = load_state<T>(c, a.segm + 2 * n * (k - k0), a.segp + ns * (k - k0), a.segk + (k - k0));
+      rc = load_state<T>(c, a.segm + 2 * n * (k - k0), a.segp + ns * (k - k0),
+                         a.segk + kMsums * (k - k0));
       if (rc) return rc;
       rc = adj_reverse_step<T>(c, g, a, a.segp + ns * (k - k0));
       if (rc) return rc;

@@ -82,9 +82,11 @@ struct SolveState {
   double rnorm2;             // ||r||^2 of the CG recursion (spectral weights)
   double bnorm2;             // ||b||^2 of the right-hand side of the running CG
   double thresh2;            // CG stops when rnorm2 <= thresh2
-  double kappa;              // preconditioner constant of this step
+  double kappa;              // trace(Kbar) / dim of this step's preconditioner (reported)
+  double kbar[6];            // preconditioner matrix Kbar (xx, yy, zz, xy, xz, yz), reading R3
   double mean_r;             // mean of r (set with r)
   double msum;               // sum |m|^2 of the current m
+  double mm[6];              // sum m_a m_b of the current m (xx, yy, zz, xy, xz, yz); follows msum
   double outer_r2;           // refined: ||S - A p64||^2 at the last FP64 evaluation
   double outer_b2;           // ||S||^2 (spectral weights)
   double outer_thresh2;      // refined: (cg_rtol ||S||)^2
@@ -171,6 +173,9 @@ struct SolveConfig {
   int diag;
 };
 
+// Doubles of per-CTA partial sums a reducing kernel may hand to its last CTA.
+constexpr int kPartialStride = 8;
+
 // Reduction sites (ticket indices).
 enum { TK_DIV = 0, TK_UPDATE = 1, TK_RESID = 2, TK_MSUM = 3, TK_PROJ = 4, TK_DIAG = 5, TK_GRADM = 6 };
 
@@ -201,7 +206,7 @@ struct Geo {
   const T* kyd;              // first-derivative wavenumbers along y, ky < ny, 0 at ky = ny/2
   const T* hx;               // heat factor exp(-D^2 xi_x^2 dt), kx = 0..H (H + 1 entries)
   const T* hy;               // heat factor exp(-D^2 xi_y^2 dt), ky < ny
-  double* partials;          // per-CTA FP64 partial sums, 4 per CTA
+  double* partials;          // per-CTA FP64 partial sums, kPartialStride per CTA
   int npartials;             // capacity in CTAs
   int pipe;                  // 1: column passes run persistent with cp.async double buffering
   int pgrid;                 // CTAs of a persistent column pass (<= SMs, <= tiles)

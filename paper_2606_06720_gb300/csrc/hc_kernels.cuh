@@ -397,7 +397,7 @@ __device__ __forceinline__ bool last_cta_sum(double (&v)[K], double* partials,
   block_sum<K>(v);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) partials[blockIdx.x * 4 + k] = v[k];
+    for (int k = 0; k < K; ++k) partials[blockIdx.x * kPartialStride + k] = v[k];
     __threadfence();
     unsigned int t = atomicAdd(ticket, 1u);
     s_last = (t == gridDim.x - 1) ? 1u : 0u;
@@ -412,7 +412,7 @@ __device__ __forceinline__ bool last_cta_sum(double (&v)[K], double* partials,
   for (int k = 0; k < K; ++k) w[k] = 0.0;
   for (unsigned int c = threadIdx.x; c < gridDim.x; c += blockDim.x)
 #pragma unroll
-    for (int k = 0; k < K; ++k) w[k] += __ldcg(&partials[c * 4 + k]);
+    for (int k = 0; k < K; ++k) w[k] += __ldcg(&partials[c * kPartialStride + k]);
   block_sum<K>(w);
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -458,21 +458,47 @@ struct DotAcc<df64> {
   __device__ __forceinline__ double value() const { return (double)s.hi + (double)s.lo; }
 };
 
-// Preconditioner symbol 1 / (kappa |xi~|^2) of the constant-coefficient
-// operator (0 on the null modes).
+// The sums sum m_a m_b of the current m (2D: xx, yy, xy) and sum |m|^2, the
+// inputs of the next step's preconditioner (reading R3).
+__device__ __forceinline__ void set_mm2(SolveState* st, double xx, double yy, double xy) {
+  st->mm[0] = xx;
+  st->mm[1] = yy;
+  st->mm[2] = 0.0;
+  st->mm[3] = xy;
+  st->mm[4] = 0.0;
+  st->mm[5] = 0.0;
+  st->msum = xx + yy;
+}
+
+// The preconditioner matrix Kbar of reading R3 (constant, symmetric positive
+// definite: the grid mean of m m^T + r I) in the kernel's type.
 template <typename T>
-__device__ __forceinline__ T pinv_sym(const Geo<T>& g, int kx, int ky, T kappa) {
-  const T a = g.kxd[kx], b = g.kyd[ky];
-  const T s2 = a * a + b * b;
-  return s2 > (T)0 ? (T)1 / (kappa * s2) : (T)0;
+struct Pc {
+  T xx, yy, zz, xy, xz, yz;
+};
+template <typename T>
+__device__ __forceinline__ Pc<T> pc_of(const SolveState* st) {
+  return Pc<T>{(T)st->kbar[0], (T)st->kbar[1], (T)st->kbar[2],
+               (T)st->kbar[3], (T)st->kbar[4], (T)st->kbar[5]};
+}
+
+// Preconditioner symbol 1 / (xi~^T Kbar xi~) of the constant-coefficient
+// operator -div(Kbar grad) at derivative multipliers (a, b) (0 on the null
+// modes, where a = b = 0).
+template <typename T>
+__device__ __forceinline__ T pinv_ab(T a, T b, const Pc<T>& k) {
+  const T s2 = k.xx * a * a + (T)2 * k.xy * a * b + k.yy * b * b;
+  return s2 > (T)0 ? (T)1 / s2 : (T)0;
+}
+template <typename T>
+__device__ __forceinline__ T pinv_sym(const Geo<T>& g, int kx, int ky, const Pc<T>& k) {
+  return pinv_ab(g.kxd[kx], g.kyd[ky], k);
 }
 
 // The same symbol evaluated in FP32, as the inner FP32 CG evaluates it.
 template <typename T>
-__device__ __forceinline__ float pinv_f32(const Geo<T>& g, int kx, int ky, float kappa) {
-  const float a = (float)g.kxd[kx], b = (float)g.kyd[ky];
-  const float s2 = a * a + b * b;
-  return s2 > 0.0f ? 1.0f / (kappa * s2) : 0.0f;
+__device__ __forceinline__ float pinv_f32(const Geo<T>& g, int kx, int ky, const Pc<float>& k) {
+  return pinv_ab((float)g.kxd[kx], (float)g.kyd[ky], k);
 }
 
 // ------------------------------------------------------------------ cp.async
@@ -623,7 +649,7 @@ __global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const
   for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
   fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   const size_t ro = (size_t)y * N;
-  DotAcc<T> m2, d2;
+  DotAcc<T> mxx, myy, mxy, d2;
   bool finite = true;
   const bool diag = kappa_update && st->diag;
 #pragma unroll
@@ -637,18 +663,19 @@ __global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const
     a[ro + x] = v[0][s].x;
     if (b) b[ro + x] = v[0][s].y;
     if (kappa_update) {
-      m2.add_prod(v[0][s].x, v[0][s].x);
-      m2.add_prod(v[0][s].y, v[0][s].y);
+      mxx.add_prod(v[0][s].x, v[0][s].x);
+      myy.add_prod(v[0][s].y, v[0][s].y);
+      mxy.add_prod(v[0][s].x, v[0][s].y);
       finite = finite && hc_finite(v[0][s].x) && hc_finite(v[0][s].y);
     }
   }
   if (kappa_update) {
-    double acc[2] = {m2.value(), d2.value()};
+    double acc[4] = {mxx.value(), myy.value(), mxy.value(), d2.value()};
     if (!finite) st->nonfinite = 1;
-    double tot[2];
-    if (last_cta_sum<2>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
-      st->msum = tot[0];
-      if (diag) st->dm2 = tot[1];
+    double tot[4];
+    if (last_cta_sum<4>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
+      set_mm2(st, tot[0], tot[1], tot[2]);
+      if (diag) st->dm2 = tot[3];
     }
   }
 }
@@ -995,11 +1022,12 @@ __global__ void __launch_bounds__(512) k_col_grad(Geo<T> g, cx<Tin>* in, const c
   const T invn = (T)(1.0 / ((double)g.nx * (double)g.ny));
   const T ax = g.kxd[c.kx] * invn;
   bool first = false, add_delta = false;
-  T beta = 0, kappa = 0;
+  T beta = 0;
+  Pc<T> pc{};
   if (MODE == CG_DUPDATE) {
     first = st->first != 0;
     beta = (T)st->beta;
-    kappa = (T)st->kappa;
+    pc = pc_of<T>(st);
   }
   if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
   cx<T> v[2][8];
@@ -1011,7 +1039,7 @@ __global__ void __launch_bounds__(512) k_col_grad(Geo<T> g, cx<Tin>* in, const c
     if constexpr (MODE == CG_PLAIN) {
       P = ccast<T>(in[idx]);
     } else if constexpr (MODE == CG_DUPDATE) {
-      const T pv = pinv_sym(g, c.kx, ky, kappa);
+      const T pv = pinv_sym(g, c.kx, ky, pc);
       const cx<T> z = cscale(rvec[idx], pv);
       P = first ? z : cadd(z, cscale(dio[idx], beta));
       dio[idx] = P;
@@ -1059,10 +1087,10 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
   double acc[3] = {0.0, 0.0, 0.0};
   DotAcc<T> dq, r64acc;
   DotAcc<float> r32acc, rzacc;
-  T kappa = 0;
-  float kappa_f = 0.0f;
-  if (MODE == CD_RESID) kappa = (T)st->kappa;
-  if (MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) kappa_f = (float)st->kappa;
+  Pc<T> pc{};
+  Pc<float> pcf{};
+  if (MODE == CD_RESID) pc = pc_of<T>(st);
+  if (MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) pcf = pc_of<float>(st);
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int ky = c.j + s * c.NY8;
@@ -1079,12 +1107,12 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
       out[idx] = rv;
       const double r2 = (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
       acc[0] += w * r2;
-      acc[1] += w * r2 * (double)pinv_sym(g, c.kx, ky, kappa);
+      acc[1] += w * r2 * (double)pinv_sym(g, c.kx, ky, pc);
     } else if constexpr (MODE == CD_RESID_FIRST) {
       const cx<float> rf = ccast<float>(csub(bvec[idx], q));
       r32[idx] = rf;
       delta32[idx] = czero<float>();
-      const float wf = (float)w, wpf = wf * pinv_f32(g, c.kx, ky, kappa_f);
+      const float wf = (float)w, wpf = wf * pinv_f32(g, c.kx, ky, pcf);
       r32acc.add_prod(wf * rf.x, rf.x);
       r32acc.add_prod(wf * rf.y, rf.y);
       rzacc.add_prod(wpf * rf.x, rf.x);
@@ -1098,7 +1126,7 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
       const cx<float> rf = ccast<float>(rv);
       r32[idx] = rf;
       delta32[idx] = czero<float>();
-      const float wf = (float)w, wpf = wf * pinv_f32(g, c.kx, ky, kappa_f);
+      const float wf = (float)w, wpf = wf * pinv_f32(g, c.kx, ky, pcf);
       r32acc.add_prod(wf * rf.x, rf.x);
       r32acc.add_prod(wf * rf.y, rf.y);
       rzacc.add_prod(wpf * rf.x, rf.x);
@@ -1317,11 +1345,12 @@ __global__ void __launch_bounds__(512) kp_col_grad(Geo<T> g, cx<T>* in, const cx
   const int b = threadIdx.x & (g.tc - 1), j = threadIdx.x >> g.ltc, NY8 = 1 << (g.lny - 3);
   const T invn = (T)(1.0 / ((double)g.nx * (double)g.ny));
   bool first = false, add_delta = false;
-  T beta = 0, kappa = 0;
+  T beta = 0;
+  Pc<T> pc{};
   if (MODE == CG_DUPDATE) {
     first = st->first != 0;
     beta = (T)st->beta;
-    kappa = (T)st->kappa;
+    pc = pc_of<T>(st);
   }
   if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
   const cx<T>* s0 = MODE == CG_DUPDATE ? rvec : in;
@@ -1359,8 +1388,7 @@ __global__ void __launch_bounds__(512) kp_col_grad(Geo<T> g, cx<T>* in, const cx
       if constexpr (MODE == CG_PLAIN) {
         P = cur[e];
       } else if constexpr (MODE == CG_DUPDATE) {
-        const T s2 = kxv * kxv + kyv[s] * kyv[s];
-        const T pv = s2 > (T)0 ? (T)1 / (kappa * s2) : (T)0;  // pinv_sym
+        const T pv = pinv_ab(kxv, kyv[s], pc);
         const cx<T> z = cscale(cur[e], pv);
         P = first ? z : cadd(z, cscale(cur[se + e], beta));
         dio[idx] = P;
@@ -1403,10 +1431,10 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
   const int b = threadIdx.x & (g.tc - 1), j = threadIdx.x >> g.ltc, NY8 = 1 << (g.lny - 3);
   DotAcc<T> dq, r64acc;
   DotAcc<float> r32acc, rzacc;
-  T kappa = 0;
-  float kappa_f = 0.0f;
-  if (MODE == CD_RESID) kappa = (T)st->kappa;
-  if (MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) kappa_f = (float)st->kappa;
+  Pc<T> pc{};
+  Pc<float> pcf{};
+  if (MODE == CD_RESID) pc = pc_of<T>(st);
+  if (MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) pcf = pc_of<float>(st);
   double accr[2] = {0.0, 0.0};
   T kyv[8];  // this thread's rows are the same in every tile
 #pragma unroll
@@ -1455,12 +1483,12 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
         out[idx] = rv;
         const double r2 = (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
         accr[0] += w * r2;
-        accr[1] += w * r2 * (double)pinv_sym(g, kx, ky, kappa);
+        accr[1] += w * r2 * (double)pinv_sym(g, kx, ky, pc);
       } else if constexpr (MODE == CD_RESID_FIRST) {
         const cx<float> rf = ccast<float>(csub(aux[s], q));
         r32[idx] = rf;
         delta32[idx] = czero<float>();
-        const float wf = (float)w, wpf = wf * pinv_f32(g, kx, ky, kappa_f);
+        const float wf = (float)w, wpf = wf * pinv_f32(g, kx, ky, pcf);
         r32acc.add_prod(wf * rf.x, rf.x);
         r32acc.add_prod(wf * rf.y, rf.y);
         rzacc.add_prod(wpf * rf.x, rf.x);
@@ -1474,7 +1502,7 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
         const cx<float> rf = ccast<float>(rv);
         r32[idx] = rf;
         delta32[idx] = czero<float>();
-        const float wf = (float)w, wpf = wf * pinv_f32(g, kx, ky, kappa_f);
+        const float wf = (float)w, wpf = wf * pinv_f32(g, kx, ky, pcf);
         r32acc.add_prod(wf * rf.x, rf.x);
         r32acc.add_prod(wf * rf.y, rf.y);
         rzacc.add_prod(wpf * rf.x, rf.x);
@@ -1526,11 +1554,12 @@ __global__ void __launch_bounds__(1024) kq_col_grad(Geo<float> g, cx<float>* in,
   const int b = t & (g.tc - 1), j = t >> g.ltc, NY8 = 1 << (g.lny - 3);
   const T invn = (T)(1.0 / ((double)g.nx * (double)g.ny));
   bool first = false, add_delta = false;
-  T beta = 0, kappa = 0;
+  T beta = 0;
+  Pc<T> pc{};
   if (MODE == CG_DUPDATE) {
     first = st->first != 0;
     beta = (T)st->beta;
-    kappa = (T)st->kappa;
+    pc = pc_of<T>(st);
   }
   if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
   const cx<T>* s0 = MODE == CG_DUPDATE ? rvec : in;
@@ -1559,7 +1588,7 @@ __global__ void __launch_bounds__(1024) kq_col_grad(Geo<float> g, cx<float>* in,
       if constexpr (MODE == CG_PLAIN) {
         Pv = cur[e];
       } else if constexpr (MODE == CG_DUPDATE) {
-        const cx<T> z = cscale(cur[e], pinv_sym(g, kx, ky, kappa));
+        const cx<T> z = cscale(cur[e], pinv_sym(g, kx, ky, pc));
         Pv = first ? z : cadd(z, cscale(cur[se + e], beta));
         if (!f) dio[idx] = Pv;
       } else {
@@ -1599,7 +1628,7 @@ __global__ void __launch_bounds__(1024) kq_col_div(Geo<float> g, const cx<float>
   const int t = threadIdx.x - f * P;
   const int b = t & (g.tc - 1), j = t >> g.ltc, NY8 = 1 << (g.lny - 3);
   DotAcc<float> r32acc, rzacc;
-  const float kappa_f = MODE == CD_RESID_FIRST ? (float)st->kappa : 0.0f;
+  const Pc<float> pcf = MODE == CD_RESID_FIRST ? pc_of<float>(st) : Pc<float>{};
   int half = 0;
   int tile = blockIdx.x;
   if (tile < ntiles) stage_cols<T, 2>(g, Qx, Qy, sm, se, tile << g.ltc);
@@ -1646,7 +1675,7 @@ __global__ void __launch_bounds__(1024) kq_col_div(Geo<float> g, const cx<float>
           const cx<float> rf = csub(aux[s], q);
           r32[idx] = rf;
           delta32[idx] = czero<float>();
-          const float wpf = w * pinv_f32(g, kx, ky, kappa_f);
+          const float wpf = w * pinv_f32(g, kx, ky, pcf);
           r32acc.add_prod(w * rf.x, rf.x);
           r32acc.add_prod(w * rf.y, rf.y);
           rzacc.add_prod(wpf * rf.x, rf.x);
@@ -1784,7 +1813,7 @@ __global__ void __launch_bounds__(256) k_cg_update(Geo<T> g, cx<T>* __restrict__
     return;
   }
   const T alpha = (T)st->alpha;
-  const T kappa = (T)st->kappa;
+  const Pc<T> pc = pc_of<T>(st);
   const size_t total = (size_t)g.ny * g.H;
   DotAcc<T> rr, rz;
   auto upd = [&](size_t i, cx<T> dv, cx<T> xv, cx<T> qv, cx<T> rv) {
@@ -1794,7 +1823,7 @@ __global__ void __launch_bounds__(256) k_cg_update(Geo<T> g, cx<T>* __restrict__
     rv = cmk<T>(rv.x - alpha * qv.x, rv.y - alpha * qv.y);
     r[i] = rv;
     const T wt = kx == 0 ? (T)1 : (T)2;
-    const T wp = wt * pinv_sym(g, kx, ky, kappa);  // weight times preconditioner symbol
+    const T wp = wt * pinv_sym(g, kx, ky, pc);  // weight times preconditioner symbol
     rr.add_prod(wt * rv.x, rv.x);
     rr.add_prod(wt * rv.y, rv.y);
     rz.add_prod(wp * rv.x, rv.x);
@@ -1851,17 +1880,17 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_msum(Geo<T> g, const T* __restrict__ mx,
                                               const T* __restrict__ my, SolveState* st) {
   const size_t n = (size_t)g.nx * g.ny;
-  DotAcc<T> m2;
+  DotAcc<T> mxx, myy, mxy;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
-    m2.add_prod(mx[i], mx[i]);
-    m2.add_prod(my[i], my[i]);
+    mxx.add_prod(mx[i], mx[i]);
+    myy.add_prod(my[i], my[i]);
+    mxy.add_prod(mx[i], my[i]);
   }
-  double acc[1] = {m2.value()};
-  double tot[1];
-  if (last_cta_sum<1>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
-    st->msum = tot[0];
-  }
+  double acc[3] = {mxx.value(), myy.value(), mxy.value()};
+  double tot[3];
+  if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0)
+    set_mm2(st, tot[0], tot[1], tot[2]);
 }
 
 // ------------------------------------------------------------------ adjoint

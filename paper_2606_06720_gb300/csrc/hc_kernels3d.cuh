@@ -49,18 +49,28 @@ __device__ __forceinline__ CIdx3 cidx3(const ColPass& p) {
 // Elements of one padded slab of a column pass: (L + L/8) * tc.
 __device__ __forceinline__ int slab3(const ColPass& p) { return (9 << (p.lL - 3)) << p.ltc; }
 
-// Preconditioner symbol 1 / (kappa |xi~|^2) in 3D (0 on the 8 null modes).
+// The sums sum m_a m_b of the current m (xx, yy, zz, xy, xz, yz) and sum |m|^2,
+// the inputs of the next step's preconditioner (reading R3).
+__device__ __forceinline__ void set_mm3(SolveState* st, const double* t) {
+#pragma unroll
+  for (int e = 0; e < 6; ++e) st->mm[e] = t[e];
+  st->msum = t[0] + t[1] + t[2];
+}
+
+// Preconditioner symbol 1 / (xi~^T Kbar xi~) in 3D (0 on the 8 null modes).
 template <typename T>
-__device__ __forceinline__ T pinv3(const Geo<T>& g, int kx, int ky, int kz, T kappa) {
-  const T a = g.kxd[kx], b = g.kyd[ky], c = g.kzd[kz];
-  const T s2 = a * a + b * b + c * c;
-  return s2 > (T)0 ? (T)1 / (kappa * s2) : (T)0;
+__device__ __forceinline__ T pinv3_abc(T a, T b, T c, const Pc<T>& k) {
+  const T s2 = k.xx * a * a + k.yy * b * b + k.zz * c * c +
+               (T)2 * (k.xy * a * b + k.xz * a * c + k.yz * b * c);
+  return s2 > (T)0 ? (T)1 / s2 : (T)0;
 }
 template <typename T>
-__device__ __forceinline__ float pinv3_f32(const Geo<T>& g, int kx, int ky, int kz, float kappa) {
-  const float a = (float)g.kxd[kx], b = (float)g.kyd[ky], c = (float)g.kzd[kz];
-  const float s2 = a * a + b * b + c * c;
-  return s2 > 0.0f ? 1.0f / (kappa * s2) : 0.0f;
+__device__ __forceinline__ T pinv3(const Geo<T>& g, int kx, int ky, int kz, const Pc<T>& k) {
+  return pinv3_abc(g.kxd[kx], g.kyd[ky], g.kzd[kz], k);
+}
+template <typename T>
+__device__ __forceinline__ float pinv3_f32(const Geo<T>& g, int kx, int ky, int kz, const Pc<float>& k) {
+  return pinv3_abc((float)g.kxd[kx], (float)g.kyd[ky], (float)g.kzd[kz], k);
 }
 
 // From NV canonical-order row spectra Z_q (of complex rows a_q + i b_q), write
@@ -148,11 +158,12 @@ __global__ void __launch_bounds__(256) k3_zgrad(Geo<T> g, cx<Tin>* in, const cx<
   const int kx = c.col & (g.H - 1), ky = c.col >> g.lH;
   const T ax = g.kxd[kx] * invn, ay = g.kyd[ky] * invn;
   bool first = false, add_delta = false;
-  T beta = 0, kappa = 0;
+  T beta = 0;
+  Pc<T> pc{};
   if (MODE == CG_DUPDATE) {
     first = st->first != 0;
     beta = (T)st->beta;
-    kappa = (T)st->kappa;
+    pc = pc_of<T>(st);
   }
   if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
   cx<T> v[3][8];
@@ -164,7 +175,7 @@ __global__ void __launch_bounds__(256) k3_zgrad(Geo<T> g, cx<Tin>* in, const cx<
     if constexpr (MODE == CG_PLAIN) {
       P = ccast<T>(in[idx]);
     } else if constexpr (MODE == CG_DUPDATE) {
-      const T pv = pinv3(g, kx, ky, kz, kappa);
+      const T pv = pinv3(g, kx, ky, kz, pc);
       const cx<T> z = cscale(rvec[idx], pv);
       P = first ? z : cadd(z, cscale(dio[idx], beta));
       dio[idx] = P;
@@ -274,10 +285,10 @@ __global__ void __launch_bounds__(256) k3_zdiv(Geo<T> g, Tri<cx<T>*> Q, const cx
   double acc[3] = {0.0, 0.0, 0.0};
   DotAcc<T> dq, r64acc;
   DotAcc<float> r32acc, rzacc;
-  T kappa = 0;
-  float kappa_f = 0.0f;
-  if (MODE == CD_RESID) kappa = (T)st->kappa;
-  if (MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) kappa_f = (float)st->kappa;
+  Pc<T> pc{};
+  Pc<float> pcf{};
+  if (MODE == CD_RESID) pc = pc_of<T>(st);
+  if (MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) pcf = pc_of<float>(st);
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int kz = c.j + s * c.L8;
@@ -295,12 +306,12 @@ __global__ void __launch_bounds__(256) k3_zdiv(Geo<T> g, Tri<cx<T>*> Q, const cx
       out[idx] = rv;
       const double r2 = (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
       acc[0] += w * r2;
-      acc[1] += w * r2 * (double)pinv3(g, kx, ky, kz, kappa);
+      acc[1] += w * r2 * (double)pinv3(g, kx, ky, kz, pc);
     } else if constexpr (MODE == CD_RESID_FIRST) {
       const cx<float> rf = ccast<float>(csub(bvec[idx], q));
       r32[idx] = rf;
       delta32[idx] = czero<float>();
-      const float wf = (float)w, wpf = wf * pinv3_f32(g, kx, ky, kz, kappa_f);
+      const float wf = (float)w, wpf = wf * pinv3_f32(g, kx, ky, kz, pcf);
       r32acc.add_prod(wf * rf.x, rf.x);
       r32acc.add_prod(wf * rf.y, rf.y);
       rzacc.add_prod(wpf * rf.x, rf.x);
@@ -314,7 +325,7 @@ __global__ void __launch_bounds__(256) k3_zdiv(Geo<T> g, Tri<cx<T>*> Q, const cx
       const cx<float> rf = ccast<float>(rv);
       r32[idx] = rf;
       delta32[idx] = czero<float>();
-      const float wf = (float)w, wpf = wf * pinv3_f32(g, kx, ky, kz, kappa_f);
+      const float wf = (float)w, wpf = wf * pinv3_f32(g, kx, ky, kz, pcf);
       r32acc.add_prod(wf * rf.x, rf.x);
       r32acc.add_prod(wf * rf.y, rf.y);
       rzacc.add_prod(wpf * rf.x, rf.x);
@@ -515,7 +526,7 @@ __global__ void __launch_bounds__(256) k3_heat(Geo<T> g, int axis, Tri<cx<T>*> M
     for (int q = 0; q < 3; ++q) v[q][s] = cscale(v[q][s], f);
   }
   fft_canon<+1, 3>(v, sl, 1 << p.ltc, c.j, p.lL, tw);
-  DotAcc<T> m2, d2;
+  DotAcc<T> mm[6], d2;  // sum m_a m_b: xx, yy, zz, xy, xz, yz
   bool finite = true;
   const bool dm = axis == 2 && st->diag;
 #pragma unroll
@@ -530,19 +541,26 @@ __global__ void __launch_bounds__(256) k3_heat(Geo<T> g, int axis, Tri<cx<T>*> M
         d2.add_prod(dy, dy);
       }
       Mo.v[q][idx] = v[q][s];
-      if (axis == 2) {
-        m2.add_prod(v[q][s].x, v[q][s].x);
-        m2.add_prod(v[q][s].y, v[q][s].y);
-        finite = finite && hc_finite(v[q][s].x) && hc_finite(v[q][s].y);
+      if (axis == 2) finite = finite && hc_finite(v[q][s].x) && hc_finite(v[q][s].y);
+    }
+    if (axis == 2) {  // the three components of the same two points
+      constexpr int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        mm[e].add_prod(v[pa[e]][s].x, v[pb[e]][s].x);
+        mm[e].add_prod(v[pa[e]][s].y, v[pb[e]][s].y);
       }
     }
   }
   if (axis == 2) {
     if (!finite) st->nonfinite = 1;
-    double acc[2] = {m2.value(), d2.value()}, tot[2];
-    if (last_cta_sum<2>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
-      st->msum = tot[0];
-      if (dm) st->dm2 = tot[1];
+    double acc[7], tot[7];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) acc[e] = mm[e].value();
+    acc[6] = d2.value();
+    if (last_cta_sum<7>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
+      set_mm3(st, tot);
+      if (dm) st->dm2 = tot[6];
     }
   }
 }
@@ -596,7 +614,7 @@ __global__ void __launch_bounds__(256) k3_cg_update(Geo<T> g, cx<T>* __restrict_
     return;
   }
   const T alpha = (T)st->alpha;
-  const T kappa = (T)st->kappa;
+  const Pc<T> pc = pc_of<T>(st);
   const size_t total = (size_t)g.nz * g.ny * g.H;
   DotAcc<T> rr, rz;
   auto upd = [&](size_t i, cx<T> dv, cx<T> xv, cx<T> qv, cx<T> rv) {
@@ -607,7 +625,7 @@ __global__ void __launch_bounds__(256) k3_cg_update(Geo<T> g, cx<T>* __restrict_
     rv = cmk<T>(rv.x - alpha * qv.x, rv.y - alpha * qv.y);
     r[i] = rv;
     const T wt = kx == 0 ? (T)1 : (T)2;
-    const T wp = wt * pinv3(g, kx, ky, kz, kappa);
+    const T wp = wt * pinv3(g, kx, ky, kz, pc);
     rr.add_prod(wt * rv.x, rv.x);
     rr.add_prod(wt * rv.y, rv.y);
     rz.add_prod(wp * rv.x, rv.x);
@@ -654,16 +672,19 @@ __global__ void __launch_bounds__(256) k3_cg_update(Geo<T> g, cx<T>* __restrict_
 template <typename T>
 __global__ void __launch_bounds__(256) k3_msum(Geo<T> g, Tri<const T*> m, SolveState* st) {
   const size_t n = (size_t)g.nx * g.ny * g.nz;
-  DotAcc<T> m2;
+  constexpr int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+  DotAcc<T> mm[6];
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
+    const T v[3] = {m.v[0][i], m.v[1][i], m.v[2][i]};
 #pragma unroll
-    for (int q = 0; q < 3; ++q) m2.add_prod(m.v[q][i], m.v[q][i]);
+    for (int e = 0; e < 6; ++e) mm[e].add_prod(v[pa[e]], v[pb[e]]);
   }
-  double acc[1] = {m2.value()};
-  double tot[1];
-  if (last_cta_sum<1>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0)
-    st->msum = tot[0];
+  double acc[6], tot[6];
+#pragma unroll
+  for (int e = 0; e < 6; ++e) acc[e] = mm[e].value();
+  if (last_cta_sum<6>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0)
+    set_mm3(st, tot);
 }
 
 // ------------------------------------------------------------------ launchers

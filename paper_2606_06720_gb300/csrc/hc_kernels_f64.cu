@@ -74,9 +74,21 @@ __global__ void k_set_config(SolveState* st, SolveConfig c) {
 }
 
 __global__ void k_step_begin(SolveState* st, int npts) {
-  // reading R3: kappa = mean(r) + mean(|m|^2) / d
-  st->kappa = st->user_kappa > 0 ? st->user_kappa
-                                 : st->mean_r + st->msum / (double)npts / (double)st->dim;
+  // reading R3: Kbar = mean(m m^T) + mean(r) I, or the caller's kappa I;
+  // kappa = trace(Kbar) / d is reported
+  for (int e = 0; e < 6; ++e) {
+    const bool diag = e < 3, used = st->dim == 3 || e == 0 || e == 1 || e == 3;
+    double v = 0.0;
+    if (used) {
+      if (st->user_kappa > 0)
+        v = diag ? st->user_kappa : 0.0;
+      else
+        v = st->mm[e] / (double)npts + (diag ? st->mean_r : 0.0);
+    }
+    st->kbar[e] = v;
+  }
+  st->kappa = 0.0;
+  for (int a = 0; a < st->dim; ++a) st->kappa += st->kbar[a] / (double)st->dim;
   st->msum_old = st->msum;
   st->gm2_next_valid = 0;
   st->first_used = 0;
