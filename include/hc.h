@@ -215,6 +215,10 @@ typedef struct {
                       col_tile * (8 bytes FP32 | 16 bytes FP64) to be a multiple of 16, or
                       one FP32 column (8-byte copies); 2 (FP32 only): as 1 with the two
                       transforms of a column on two halves of a 2x larger CTA */
+  int row_pipe[2]; /* [0] = 1: the FP32 operator-apply row pass runs persistent, one CTA per
+                      resident slot, prefetching the next row block with cp.async while
+                      transforming the current one (needs 48 row_rows nx bytes of shared
+                      memory); [1] must be 0 */
 } hc_tuning;
 
 int hc_get_tuning(const hc_ctx* ctx, hc_tuning* out);

@@ -45,7 +45,8 @@ class hc_params(C.Structure):
 
 
 class hc_tuning(C.Structure):
-    _fields_ = [("col_tile", C.c_int * 2), ("row_rows", C.c_int * 2), ("col_pipe", C.c_int * 2)]
+    _fields_ = [("col_tile", C.c_int * 2), ("row_rows", C.c_int * 2), ("col_pipe", C.c_int * 2),
+                ("row_pipe", C.c_int * 2)]
 
 
 class hc_step_stats(C.Structure):
@@ -367,13 +368,14 @@ class Solver:
         t = hc_tuning()
         _check(hc_get_tuning(self.ctx, C.byref(t)), "hc_get_tuning")
         return {"col_tile": list(t.col_tile), "row_rows": list(t.row_rows),
-                "col_pipe": list(t.col_pipe)}
+                "col_pipe": list(t.col_pipe), "row_pipe": list(t.row_pipe)}
 
-    def set_tuning(self, col_tile, row_rows, col_pipe=None):
-        if col_pipe is None:
-            col_pipe = self.get_tuning()["col_pipe"]
+    def set_tuning(self, col_tile, row_rows, col_pipe=None, row_pipe=None):
+        cur = self.get_tuning() if col_pipe is None or row_pipe is None else None
+        col_pipe = cur["col_pipe"] if col_pipe is None else col_pipe
+        row_pipe = cur["row_pipe"] if row_pipe is None else row_pipe
         t = hc_tuning((C.c_int * 2)(*col_tile), (C.c_int * 2)(*row_rows),
-                      (C.c_int * 2)(*col_pipe))
+                      (C.c_int * 2)(*col_pipe), (C.c_int * 2)(*row_pipe))
         _check(hc_set_tuning(self.ctx, C.byref(t)), "hc_set_tuning")
 
     def adjoint(self, nsteps: int, lamT, every: int = 50, allow=(HC_OK, HC_ENOCONV)) -> dict:

@@ -38,7 +38,7 @@ _WEIGHT = {"cg_grad": 20, "cg_apply": 20, "cg_div": 20}
 
 # Bumped whenever the kernels' launch-shape trade-offs change, so cached
 # choices made for older kernels are not reused.
-_KERNELS_VERSION = 4
+_KERNELS_VERSION = 5
 
 
 def _key(solver) -> str:
@@ -86,7 +86,8 @@ def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = Fal
     if use_cache and key in cache:
         t = cache[key]
         try:
-            solver.set_tuning(t["col_tile"], t["row_rows"], t.get("col_pipe", [0, 0]))
+            solver.set_tuning(t["col_tile"], t["row_rows"], t.get("col_pipe", [0, 0]),
+                              t.get("row_pipe", [0, 0]))
             if report is not None:
                 report["cached"] = True
             return solver.get_tuning()
@@ -98,27 +99,33 @@ def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = Fal
     for (knob, idx), kernels in _FAMILIES[prec].items():
         times = {}
         for v in _candidates(solver, knob):
-            pipes = ((0, 1, 2) if idx == 0 else (0, 1)) if knob == "col_tile" else (None,)
+            # the knob's pipelined variants: col_pipe 0/1/2 (2: FP32 only) for
+            # the column passes, row_pipe 0/1 for the FP32 apply row pass
+            if knob == "col_tile":
+                pipes, pkey = ((0, 1, 2) if idx == 0 else (0, 1)), "col_pipe"
+            else:
+                pipes, pkey = ((0, 1) if idx == 0 else (None,)), "row_pipe"
             for pipe in pipes:
-                trial = {k: list(best[k]) for k in ("col_tile", "row_rows", "col_pipe")}
+                trial = {k: list(best[k]) for k in ("col_tile", "row_rows", "col_pipe", "row_pipe")}
                 trial[knob][idx] = v
                 if pipe is not None:
-                    trial["col_pipe"][idx] = pipe
+                    trial[pkey][idx] = pipe
                 try:
-                    solver.set_tuning(trial["col_tile"], trial["row_rows"], trial["col_pipe"])
+                    solver.set_tuning(trial["col_tile"], trial["row_rows"], trial["col_pipe"],
+                                      trial["row_pipe"])
                 except Exception:
                     continue
                 label = f"{v}" if pipe is None else f"{v}{['', 'p', 'q'][pipe]}"
                 times[label] = (sum(_WEIGHT.get(k, 1) * solver.time_kernel(k, reps)
-                                    for k in kernels), v, pipe)
+                                    for k in kernels), v, pipe, pkey)
         if times:
             lab = min(times, key=lambda k: times[k][0])
-            _, v, pipe = times[lab]
+            _, v, pipe, pkey = times[lab]
             best[knob][idx] = v
             if pipe is not None:
-                best["col_pipe"][idx] = pipe
+                best[pkey][idx] = pipe
             measured[f"{knob}[{idx}]"] = {k: round(t[0] * 1e3, 2) for k, t in times.items()}
-    solver.set_tuning(best["col_tile"], best["row_rows"], best["col_pipe"])
+    solver.set_tuning(best["col_tile"], best["row_rows"], best["col_pipe"], best["row_pipe"])
     if report is not None:
         report["us"] = measured
     if verbose:

@@ -2227,6 +2227,8 @@ int hc_get_tuning(const hc_ctx* c, hc_tuning* t) {
   t->row_rows[1] = c->gd.rpc;
   t->col_pipe[0] = c->gf.pipe;
   t->col_pipe[1] = c->gd.pipe;
+  t->row_pipe[0] = c->gf.rpipe;
+  t->row_pipe[1] = 0;
   return HC_OK;
 }
 
@@ -2255,6 +2257,19 @@ int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
       if (2 * col_sm > (size_t)optin) return HC_EINVAL;
     }
   }
+  // persistent FP32 apply row pass: [0] only, and its two stage buffers must fit
+  if (t->row_pipe[1] != 0 || t->row_pipe[0] < 0 || t->row_pipe[0] > 1) return HC_EINVAL;
+  int rgrid = 0;
+  if (t->row_pipe[0]) {
+    const int rpc = t->row_rows[0];
+    const size_t ps = hc::row_pipe_smem(rpc, c->nx);
+    if (ps > (size_t)optin) return HC_EINVAL;
+    const int per_sm = hc::row_pipe_ctas_per_sm(rpc << (lnx - 3), ps);
+    if (per_sm < 1) return HC_EINVAL;
+    int nsm0 = 0;
+    CU(cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev));
+    rgrid = std::min(c->ny / rpc, nsm0 * per_sm);
+  }
   int nsm = 0;
   CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   c->gf.tc = t->col_tile[0];
@@ -2267,6 +2282,8 @@ int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
   c->gd.lrpc = ilog2(t->row_rows[1]);
   c->gf.pipe = t->col_pipe[0];
   c->gd.pipe = t->col_pipe[1];
+  c->gf.rpipe = t->row_pipe[0];
+  c->gf.rgrid = rgrid;
   c->gf.pgrid = std::min(nsm, c->H / c->gf.tc);
   c->gd.pgrid = std::min(nsm, c->H / c->gd.tc);
   c->gq.tc = c->gd.tc;

@@ -210,6 +210,8 @@ struct Geo {
   int npartials;             // capacity in CTAs
   int pipe;                  // 1: column passes run persistent with cp.async double buffering
   int pgrid;                 // CTAs of a persistent column pass (<= SMs, <= tiles)
+  int rpipe;                 // 1 (FP32): the apply row pass runs persistent with cp.async double buffering
+  int rgrid;                 // CTAs of that pass (resident CTAs, <= row blocks)
   const T* x2x;              // xi_x^2 (positive Nyquist), kx = 0..H (H + 1 entries)
   const T* x2y;              // xi_y^2, ky < ny
   // 3D grids (nz = 1 in 2D).  Spectra are [nz][ny][H] packed as in 2D; the x
@@ -254,9 +256,14 @@ void row_r2c(const Geo<T>& g, const T* a, const T* b, cx<T>* A, cx<T>* B, cudaSt
 template <typename T>
 void row_c2r(const Geo<T>& g, const cx<T>* A, const cx<T>* B, T* a, T* b, SolveState* st,
              int kappa_update, cudaStream_t s);
+// Shared memory of the persistent FP32 apply row pass: the transform slabs and
+// two stage buffers of the row block's Gx, Gy, mx, my, r (each rpc N 4 bytes).
+inline size_t row_pipe_smem(int rpc, int nx) { return (size_t)48 * rpc * nx; }
+// Resident CTAs per SM of that pass at this shape (0 if it cannot run).
+int row_pipe_ctas_per_sm(int threads, size_t smem);
 // Row pass of the operator apply: C2R(gx, gy) -> q = (m.g) m + r g -> R2C(q).
 // With st (a CG iteration) also alpha = rho / <d, A d> from this pass, and the
-// pass is skipped when st->done.
+// pass is skipped when st->done.  FP32 with g.rpipe: the persistent variant.
 template <typename T, typename Tm>
 void row_apply(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const Tm* mx, const Tm* my,
                const Tm* r, cx<T>* Qx, cx<T>* Qy, SolveState* st, cudaStream_t s);

@@ -649,7 +649,10 @@ __global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const
   for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
   fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   const size_t ro = (size_t)y * N;
-  DotAcc<T> mxx, myy, mxy, d2;
+  // this thread's 8 points: plain FMA sums of m_a m_b (the preconditioner's
+  // input), FP64 across threads
+  T mxx = (T)0, myy = (T)0, mxy = (T)0;
+  DotAcc<T> d2;
   bool finite = true;
   const bool diag = kappa_update && st->diag;
 #pragma unroll
@@ -663,14 +666,14 @@ __global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const
     a[ro + x] = v[0][s].x;
     if (b) b[ro + x] = v[0][s].y;
     if (kappa_update) {
-      mxx.add_prod(v[0][s].x, v[0][s].x);
-      myy.add_prod(v[0][s].y, v[0][s].y);
-      mxy.add_prod(v[0][s].x, v[0][s].y);
+      mxx = mxx + v[0][s].x * v[0][s].x;
+      myy = myy + v[0][s].y * v[0][s].y;
+      mxy = mxy + v[0][s].x * v[0][s].y;
       finite = finite && hc_finite(v[0][s].x) && hc_finite(v[0][s].y);
     }
   }
   if (kappa_update) {
-    double acc[4] = {mxx.value(), myy.value(), mxy.value(), d2.value()};
+    double acc[4] = {(double)mxx, (double)myy, (double)mxy, d2.value()};
     if (!finite) st->nonfinite = 1;
     double tot[4];
     if (last_cta_sum<4>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
@@ -767,6 +770,83 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
   }
   fft_canon<-1, NV, true>(v, sl, 1, j, g.lnx, g.twx);
   store_rows_r2c<NV>(v, sl, j, N, H, Qa, Qb);
+  if (DOT) {
+    double a1[1] = {gkg.value()}, t1[1];
+    if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0)
+      cg_alpha_from(st, t1[0], (double)g.nx * (double)g.ny);
+  }
+}
+
+// Persistent FP32 row pass of the operator apply (g.rpipe): CTA b walks the
+// row blocks b, b + grid, ... (rpc rows each, one row per N/8 threads).  Two
+// stage buffers hold a block's Gx, Gy, mx, my, r rows (five contiguous pieces
+// of rpc N 4 bytes); the next block's are copied with cp.async while the
+// current one is transformed, so the loads' latency overlaps the FFTs.  Same
+// arithmetic as k_row_apply<float, float, DOT, 1>.
+template <bool DOT>
+__global__ void __launch_bounds__(512) kp_row_apply(Geo<float> g, const cx<float>* Gx,
+                                                    const cx<float>* Gy, const float* mx,
+                                                    const float* my, const float* rr,
+                                                    cx<float>* Qx, cx<float>* Qy, SolveState* st) {
+  if (st && st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int l8 = g.lnx - 3, N = g.nx, H = g.H, N8 = 1 << l8;
+  const int rb = threadIdx.x >> l8, j = threadIdx.x & (N8 - 1);
+  const int rpc = g.rpc, nblk = g.ny >> g.lrpc;
+  const size_t piece = (size_t)rpc * N * 4;  // bytes of one field's rows in a block
+  cx<float>* sl[1] = {reinterpret_cast<cx<float>*>(smem_raw) + (size_t)rb * N};
+  unsigned char* bufs = smem_raw + 2 * piece;  // after the rpc slabs (rpc N complex)
+  auto stage = [&](int blk, int b) {
+    const int per = (int)(piece >> 4);  // 16-byte chunks per field
+    unsigned char* dst = bufs + (size_t)b * 5 * piece;
+    for (int c = threadIdx.x; c < 5 * per; c += blockDim.x) {
+      const int f = c / per, ch = c - f * per;
+      const unsigned char* src;
+      if (f < 2)
+        src = reinterpret_cast<const unsigned char*>((f == 0 ? Gx : Gy) + (size_t)blk * rpc * H);
+      else
+        src = reinterpret_cast<const unsigned char*>((f == 2 ? mx : (f == 3 ? my : rr)) +
+                                                     (size_t)blk * rpc * N);
+      cp_async16(dst + (size_t)f * piece + 16 * (size_t)ch, src + 16 * (size_t)ch);
+    }
+  };
+  int blk = blockIdx.x, buf = 0;
+  if (blk < nblk) stage(blk, 0);
+  cp_async_commit();
+  DotAcc<float> gkg;
+  for (; blk < nblk; blk += gridDim.x) {
+    const int nxt = blk + gridDim.x;
+    if (nxt < nblk) stage(nxt, buf ^ 1);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+    const unsigned char* B = bufs + (size_t)buf * 5 * piece;
+    const cx<float>* A1[1] = {reinterpret_cast<const cx<float>*>(B) + (size_t)rb * H};
+    const cx<float>* B1[1] = {reinterpret_cast<const cx<float>*>(B + piece) + (size_t)rb * H};
+    const float* smx = reinterpret_cast<const float*>(B + 2 * piece) + (size_t)rb * N;
+    const float* smy = reinterpret_cast<const float*>(B + 3 * piece) + (size_t)rb * N;
+    const float* srr = reinterpret_cast<const float*>(B + 4 * piece) + (size_t)rb * N;
+    cx<float> v[1][8];
+    load_rows_c2r<1>(v, A1, B1, j, N8);
+    fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int x = j + s * N8;
+      const float gx = v[0][s].x, gy = v[0][s].y;
+      const float ax = smx[x], ay = smy[x], r = srr[x];
+      const float mg = ax * gx + ay * gy;
+      if (DOT) gkg.add_prod(mg * mg + r * (gx * gx + gy * gy), 1.0f);
+      v[0][s] = cmk<float>(ax * mg + r * gx, ay * mg + r * gy);
+    }
+    fft_canon<-1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
+    const size_t y = (size_t)blk * rpc + rb;
+    cx<float>* Qa[1] = {Qx + y * H};
+    cx<float>* Qb[1] = {Qy + y * H};
+    store_rows_r2c<1>(v, sl, j, N, H, Qa, Qb);
+    __syncthreads();  // this buffer is refilled by the stage issued next iteration
+    buf ^= 1;
+  }
+  cp_async_wait_all();
   if (DOT) {
     double a1[1] = {gkg.value()}, t1[1];
     if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0)
@@ -1803,7 +1883,7 @@ __global__ void __launch_bounds__(512) k_col_gradnorm(Geo<T> g, const cx<T>* __r
 
 // ------------------------------------------------------------------ CG update
 template <typename T>
-__global__ void __launch_bounds__(256) k_cg_update(Geo<T> g, cx<T>* __restrict__ x,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_cg_update(Geo<T> g, cx<T>* __restrict__ x,
                                                    cx<T>* __restrict__ r,
                                                    const cx<T>* __restrict__ d,
                                                    const cx<T>* __restrict__ q, SolveState* st) {
@@ -2159,6 +2239,16 @@ template <typename T, typename Tm>
 void row_apply(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const Tm* mx, const Tm* my,
                const Tm* r, cx<T>* Qx, cx<T>* Qy, SolveState* st, cudaStream_t s) {
   const size_t sm = row_smem(g) + (size_t)3 * g.rpc * g.nx * sizeof(Tm);
+  if constexpr (std::is_same<T, float>::value && std::is_same<Tm, float>::value) {
+    if (g.rpipe) {
+      const size_t ps = row_pipe_smem(g.rpc, g.nx);
+      if (st)
+        kp_row_apply<true><<<g.rgrid, row_threads(g), ps, s>>>(g, Gx, Gy, mx, my, r, Qx, Qy, st);
+      else
+        kp_row_apply<false><<<g.rgrid, row_threads(g), ps, s>>>(g, Gx, Gy, mx, my, r, Qx, Qy, st);
+      return;
+    }
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (g.rpc >= 2) {  // two rows per thread
       const int nt = row_threads(g) >> 1;

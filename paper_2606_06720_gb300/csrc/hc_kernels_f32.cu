@@ -42,7 +42,19 @@ template void col_lap_dot<float>(const Geo<float>&, const cx<float>*, const cx<f
 template void spec_accum<float>(const Geo<float>&, double*, const cx<float>*, cudaStream_t);
 template void spec_norm2<float>(const Geo<float>&, const cx<float>*, SolveState*, cudaStream_t);
 
+int row_pipe_ctas_per_sm(int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kp_row_apply<true>, threads, smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 void set_smem_limits_f32() {
+  allow_smem(kp_row_apply<true>);
+  allow_smem(kp_row_apply<false>);
   set_smem_limits_t<float>();
   set_smem_limits_grad<float, float>();
   set_smem_limits_grad<float, double>();

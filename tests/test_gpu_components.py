@@ -72,19 +72,21 @@ def test_operator_matches_oracle(hc, precision, n, L):
 
 @pytest.mark.parametrize("n", [(2048, 64), (512, 256), (64, 32)])
 @pytest.mark.parametrize("rows", [1, 2, 4, 8])
-def test_operator_row_pairs_match_oracle(hc, n, rows):
+@pytest.mark.parametrize("pipe", [0, 1])
+def test_operator_row_pairs_match_oracle(hc, n, rows, pipe):
     """The FP32 row pass transforms two rows per thread when a CTA holds two or
-    more rows (row_rows >= 2), one otherwise; every admissible setting matches
-    the oracle's operator."""
-    if rows * n[0] // 8 > 512:
-        pytest.skip("more than 512 threads per CTA")
+    more rows (row_rows >= 2), one otherwise; with row_pipe it runs persistent,
+    prefetching the next row block.  Every admissible setting matches the
+    oracle's operator."""
+    if rows * n[0] // 8 > 512 or (pipe and 48 * rows * n[0] > 227 * 1024):
+        pytest.skip("more than 512 threads or too much shared memory per CTA")
     g = O.Grid(n)
     m = RNG.uniform(0, 1, (2,) + g.shape)
     r = W.smooth_r(n, 1)
     f = RNG.standard_normal(g.shape)
     with solver(hc, n, precision="fp32_refined") as s:
         t = s.get_tuning()
-        s.set_tuning(t["col_tile"], [rows, t["row_rows"][1]], t["col_pipe"])
+        s.set_tuning(t["col_tile"], [rows, t["row_rows"][1]], t["col_pipe"], [pipe, 0])
         s.set_m(m)
         s.set_r(r)
         Af = s.apply_operator(f)

@@ -246,6 +246,9 @@ def test_tuning_changes_only_summation_order(hc):
             s.set_tuning([2, 1], [1, 1], [3, 0])
         with pytest.raises(hc.HuCaiError):
             s.set_tuning([2, 1], [1, 1], [0, 2])
+        for bad_row_pipe in ([2, 0], [0, 1], [-1, 0]):  # 0/1, and only for the FP32 passes
+            with pytest.raises(hc.HuCaiError):
+                s.set_tuning([2, 1], [1, 1], [0, 0], bad_row_pipe)
         assert s.get_tuning()["col_tile"] == [8, 4]
     for m, p in outs[1:]:
         assert rel_l2(m, outs[0][0]) < 1e-12 and rel_l2(p, outs[0][1]) < 1e-11
@@ -287,15 +290,16 @@ def test_pipelined_column_passes_match_plain_ones(hc, precision):
 
 
 def test_row_pairs_match_single_rows(hc):
-    """The FP32 CG row pass with two rows per thread (row_rows 2 and 4) takes
-    the same steps as with one row per CTA, to the rounding of the regrouped
-    <d, A d> reduction; every step stays certified."""
+    """The FP32 CG row pass with two rows per thread (row_rows 2 and 4), and
+    the persistent prefetching one (row_pipe), take the same steps as one row
+    per CTA, to the rounding of the regrouped <d, A d> reduction; every step
+    stays certified."""
     w = W.source_sink_2d(512, steps=3)
     outs = []
-    for rows in (1, 2, 4):
+    for rows, pipe in ((1, 0), (2, 0), (4, 0), (1, 1), (4, 1)):
         with make_solver(hc, w, "fp32_refined") as s:
             t = s.get_tuning()
-            s.set_tuning(t["col_tile"], [rows, t["row_rows"][1]], t["col_pipe"])
+            s.set_tuning(t["col_tile"], [rows, t["row_rows"][1]], t["col_pipe"], [pipe, 0])
             st = s.step(3)
             assert st.status == 0 and st.rel_residual <= w.cg_rtol
             outs.append((s.get_m(), s.get_p()))
