@@ -213,8 +213,7 @@ typedef struct {
   int col_pipe[2]; /* 1: the CG/residual/heat column passes run persistent, prefetching the next
                       tile with cp.async while transforming the current one; needs
                       col_tile * (8 bytes FP32 | 16 bytes FP64) to be a multiple of 16, or
-                      one FP32 column (8-byte copies); 2 (FP32 only): as 1 with the two
-                      transforms of a column on two halves of a 2x larger CTA */
+                      one FP32 column (8-byte copies) */
   int row_pipe[2]; /* [0] = 1: the FP32 operator-apply row pass runs persistent, one CTA per
                       resident slot, prefetching the next row block with cp.async while
                       transforming the current one (needs 48 row_rows nx bytes of shared
@@ -239,7 +238,7 @@ int hc_set_tuning(hc_ctx* ctx, const hc_tuning* in);
 enum {
   HC_K_CG_GRAD = 0,    /* column pass: d-update, i xi d / n, inverse FFT_y */
   HC_K_CG_APPLY = 1,   /* row pass: C2R, (m m^T + r I) g, R2C */
-  HC_K_CG_DIV = 2,     /* column pass: FFT_y, -i xi . q, <d, A d> */
+  HC_K_CG_DIV = 2,     /* column pass: FFT_y, -i xi . q (alpha comes from the row pass) */
   HC_K_CG_UPDATE = 3,  /* x += alpha d, r -= alpha A d, <r, M^-1 r> */
   HC_K_RES_GRAD = 4,
   HC_K_RES_APPLY = 5,

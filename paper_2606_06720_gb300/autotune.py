@@ -38,7 +38,7 @@ _WEIGHT = {"cg_grad": 20, "cg_apply": 20, "cg_div": 20}
 
 # Bumped whenever the kernels' launch-shape trade-offs change, so cached
 # choices made for older kernels are not reused.
-_KERNELS_VERSION = 5
+_KERNELS_VERSION = 6
 
 
 def _key(solver) -> str:
@@ -99,10 +99,10 @@ def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = Fal
     for (knob, idx), kernels in _FAMILIES[prec].items():
         times = {}
         for v in _candidates(solver, knob):
-            # the knob's pipelined variants: col_pipe 0/1/2 (2: FP32 only) for
-            # the column passes, row_pipe 0/1 for the FP32 apply row pass
+            # the knob's pipelined variants: col_pipe 0/1 for the column
+            # passes, row_pipe 0/1 for the FP32 apply row pass
             if knob == "col_tile":
-                pipes, pkey = ((0, 1, 2) if idx == 0 else (0, 1)), "col_pipe"
+                pipes, pkey = (0, 1), "col_pipe"
             else:
                 pipes, pkey = ((0, 1) if idx == 0 else (None,)), "row_pipe"
             for pipe in pipes:

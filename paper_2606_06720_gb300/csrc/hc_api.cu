@@ -712,6 +712,7 @@ void refined_iter(hc_ctx* c) {
   auto& g = c->gf;
   cx<float>* Gx = c->G32;
   cx<float>* Gy = c->G32 + (size_t)c->ny * c->H;
+  // r32, d32, q32 and x32 are column-major
   hc::col_grad<float, float>(g, hc::CG_DUPDATE, (cx<float>*)nullptr, c->r32, c->d32, nullptr, Gx,
                              Gy, c->st, 1, c->stream);
   hc::row_apply<float, float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1],
@@ -1428,7 +1429,12 @@ int hc_set_source(hc_ctx* c, const double* S, size_t count) {
                                 2 * c->ns, c->stream);
       c->launches += 1;
     }
-    if (c->df)
+    if (c->dim == 2) {  // the 2D refinement keeps its FP32 vectors column-major
+      if (c->df)
+        hc::to_cm<df64>(c->gf, reinterpret_cast<const cx<df64>*>(c->b64), c->b32, c->stream);
+      else
+        hc::to_cm<double>(c->gf, c->b64, c->b32, c->stream);
+    } else if (c->df)
       hc::convert<float, df64>(reinterpret_cast<const df64*>(c->b64), reinterpret_cast<float*>(c->b32),
                                2 * c->ns, c->stream);
     else
@@ -2249,9 +2255,7 @@ int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
     const size_t msz = (p == 1 && !c->refined) ? sizeof(double) : sizeof(float);
     const size_t row_sm = (size_t)rpc * c->nx * (esz + 3 * msz) + 1024;
     if (col_sm > (size_t)optin || row_sm > (size_t)optin) return HC_EINVAL;
-    // col_pipe 2 (field-split pipelined passes, 2x the threads) exists for FP32 only
-    if (t->col_pipe[p] < 0 || t->col_pipe[p] > (p == 0 ? 2 : 1)) return HC_EINVAL;
-    if (t->col_pipe[p] == 2 && (tc << (lny - 3)) > 512) return HC_EINVAL;
+    if (t->col_pipe[p] < 0 || t->col_pipe[p] > 1) return HC_EINVAL;
     if (t->col_pipe[p]) {
       if ((tc * esz) % 16 && tc * esz != 8) return HC_EINVAL;  // 16-byte copies, or one FP32 column
       if (2 * col_sm > (size_t)optin) return HC_EINVAL;

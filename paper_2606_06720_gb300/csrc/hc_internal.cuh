@@ -316,6 +316,10 @@ void cg_update(const Geo<T>& g, cx<T>* x, cx<T>* r, const cx<T>* d, const cx<T>*
 // Elementwise conversions and helpers.
 template <typename To, typename Ti>
 void convert(const Ti* in, To* out, size_t n, cudaStream_t s);
+// Packed 2D spectrum (row-major) -> FP32 column-major copy, the layout of the
+// 2D refinement's FP32 vectors (r, delta, the CG direction, S).
+template <typename Ti>
+void to_cm(const Geo<float>& g, const cx<Ti>* in, cx<float>* out, cudaStream_t s);
 template <typename T>
 void msum(const Geo<T>& g, const T* mx, const T* my, SolveState* st, cudaStream_t s);
 

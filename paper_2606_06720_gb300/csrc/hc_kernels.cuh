@@ -1041,6 +1041,26 @@ __device__ __forceinline__ void resid_refine_init(SolveState* st, double r64, do
   }
 }
 
+// End of a CG iteration (one thread): ||r||^2 and rho = <r, M^-1 r> of the
+// updated residual give beta, and the stop test closes or keeps the loop.
+__device__ __forceinline__ void cg_step_finish(SolveState* st, double rr, double rz) {
+  st->rnorm2 = rr;
+  st->beta = st->rho > 0 ? rz / st->rho : 0.0;
+  st->rho = rz;
+  st->it += 1;
+  st->total_it += 1;
+  if (!isfinite(rr)) {
+    st->status = HC_ENONFINITE;
+    st->done = 1;
+  } else if (rr <= st->thresh2) {
+    st->done = 1;
+  } else if (st->it >= st->maxit) {
+    st->done = 1;
+    st->status = HC_ENOCONV;
+  }
+  if (st->graph_mode) cudaGraphSetConditional(st->h_cur, st->done ? 0u : 1u);
+}
+
 // The finalizer of a refinement-residual kernel: the mid-step one when it is
 // pending, else a sweep of the refinement loop.
 __device__ __forceinline__ void resid_sweep_init(SolveState* st, double r2, double r32, double rz) {
@@ -1082,6 +1102,13 @@ __device__ __forceinline__ ColIdx col_idx(const Geo<T>& g) {
   c.NY8 = 1 << (g.lny - 3);
   return c;
 }
+// Column-major index of (ky, kx) in a packed spectral vector of the 2D
+// refinement (r, delta, the CG direction, the FP32 copy of S): one column
+// tile of a column pass is contiguous there, so its loads and stores coalesce.
+template <typename T>
+__device__ __forceinline__ size_t cmi(const Geo<T>& g, int ky, int kx) {
+  return ((size_t)kx << g.lny) + (size_t)ky;
+}
 template <typename T>
 __device__ __forceinline__ int slab_elems(const Geo<T>& g) {
   return (g.ny + (g.ny >> 3)) * g.tc;
@@ -1119,13 +1146,15 @@ __global__ void __launch_bounds__(512) k_col_grad(Geo<T> g, cx<Tin>* in, const c
     if constexpr (MODE == CG_PLAIN) {
       P = ccast<T>(in[idx]);
     } else if constexpr (MODE == CG_DUPDATE) {
+      // the FP32 refinement's vectors are column-major; plain FP64 CG's row-major
+      const size_t vi = std::is_same<T, float>::value ? cmi(g, ky, c.kx) : idx;
       const T pv = pinv_sym(g, c.kx, ky, pc);
-      const cx<T> z = cscale(rvec[idx], pv);
-      P = first ? z : cadd(z, cscale(dio[idx], beta));
-      dio[idx] = P;
+      const cx<T> z = cscale(rvec[vi], pv);
+      P = first ? z : cadd(z, cscale(dio[vi], beta));
+      dio[vi] = P;
     } else {
-      // FP64 correction accumulation p64 += delta (refinement)
-      P = add_delta ? add_delta_at<T>(in, idx, delta[idx]) : ccast<T>(in[idx]);
+      // FP64 correction accumulation p64 += delta (refinement; delta column-major)
+      P = add_delta ? add_delta_at<T>(in, idx, delta[cmi(g, ky, c.kx)]) : ccast<T>(in[idx]);
     }
     const T ay = g.kyd[ky] * invn;
     v[0][s] = cmk<T>(-ax * P.y, ax * P.x);  // i (kx/n) P
@@ -1181,7 +1210,9 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
     if constexpr (MODE == CD_PLAIN) {
       out[idx] = q;
     } else if constexpr (MODE == CD_CG) {
-      out[idx] = q;  // alpha came from the row pass (cg_alpha_from)
+      // alpha came from the row pass (cg_alpha_from); the FP32 refinement's
+      // q is column-major, plain FP64 CG's row-major
+      out[std::is_same<T, float>::value ? cmi(g, ky, c.kx) : idx] = q;
     } else if constexpr (MODE == CD_RESID) {
       const cx<T> rv = csub(bvec[idx], q);
       out[idx] = rv;
@@ -1189,9 +1220,10 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
       acc[0] += w * r2;
       acc[1] += w * r2 * (double)pinv_sym(g, c.kx, ky, pc);
     } else if constexpr (MODE == CD_RESID_FIRST) {
-      const cx<float> rf = ccast<float>(csub(bvec[idx], q));
-      r32[idx] = rf;
-      delta32[idx] = czero<float>();
+      const size_t ci = cmi(g, ky, c.kx);  // b32, r32 and delta32 are column-major
+      const cx<float> rf = ccast<float>(csub(bvec[ci], q));
+      r32[ci] = rf;
+      delta32[ci] = czero<float>();
       const float wf = (float)w, wpf = wf * pinv_f32(g, c.kx, ky, pcf);
       r32acc.add_prod(wf * rf.x, rf.x);
       r32acc.add_prod(wf * rf.y, rf.y);
@@ -1204,8 +1236,9 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
       r64acc.add_prod(wt * rv.x, rv.x);
       r64acc.add_prod(wt * rv.y, rv.y);
       const cx<float> rf = ccast<float>(rv);
-      r32[idx] = rf;
-      delta32[idx] = czero<float>();
+      const size_t ci = cmi(g, ky, c.kx);  // r32 and delta32 are column-major
+      r32[ci] = rf;
+      delta32[ci] = czero<float>();
       const float wf = (float)w, wpf = wf * pinv_f32(g, c.kx, ky, pcf);
       r32acc.add_prod(wf * rf.x, rf.x);
       r32acc.add_prod(wf * rf.y, rf.y);
@@ -1388,9 +1421,21 @@ __global__ void __launch_bounds__(512) k_col_inv(Geo<T> g, const cx<T>* __restri
 // q*se + padk(row)*tc + b), so once a tile's values are in registers its
 // buffer half serves as the FFT exchange slabs.  Needs tc*sizeof(cx<T>) to be
 // a multiple of 16 bytes (the cp.async size).
-template <typename T, int NS>
+template <typename T, int NS, bool CM = false>
 __device__ __forceinline__ void stage_cols(const Geo<T>& g, const cx<T>* a0, const cx<T>* a1,
                                            cx<T>* buf, int se, int kx0) {
+  if constexpr (CM) {  // column-major FP32 vectors: 8-byte copies down each column
+    static_assert(sizeof(cx<T>) == 8, "column-major staging is for FP32 vectors");
+    const int per = g.ny << g.ltc;
+    for (int c = threadIdx.x; c < NS * per; c += blockDim.x) {
+      const int q = (NS > 1 && c >= per) ? 1 : 0;
+      const int rem = c - q * per;
+      const int bcol = rem >> g.lny, row = rem & (g.ny - 1);
+      cp_async8(buf + q * se + padk(row) * g.tc + bcol,
+                (q ? a1 : a0) + ((size_t)(kx0 + bcol) << g.lny) + row);
+    }
+    return;
+  }
   constexpr int lce = sizeof(cx<T>) == 8 ? 1 : 0;  // log2 complex elements per 16-byte copy
   if (sizeof(cx<T>) == 8 && g.ltc == 0) {  // one FP32 column: 8-byte copies
     const int per = g.ny;
@@ -1441,11 +1486,13 @@ __global__ void __launch_bounds__(512) kp_col_grad(Geo<T> g, cx<T>* in, const cx
   for (int s = 0; s < 8; ++s) kyv[s] = g.kyd[j + s * NY8];
   int half = 0;
   int tile = blockIdx.x;
-  if (tile < ntiles) stage_cols<T, NS>(g, s0, s1, sm, se, tile << g.ltc);
+  // the FP32 refinement's r and d are column-major
+  constexpr bool CMV = MODE == CG_DUPDATE && std::is_same<T, float>::value;
+  if (tile < ntiles) stage_cols<T, NS, CMV>(g, s0, s1, sm, se, tile << g.ltc);
   cp_async_commit();
   for (; tile < ntiles; tile += gridDim.x) {
     const int nxt = tile + gridDim.x;
-    if (nxt < ntiles) stage_cols<T, NS>(g, s0, s1, sm + (half ^ 1) * 2 * se, se, nxt << g.ltc);
+    if (nxt < ntiles) stage_cols<T, NS, CMV>(g, s0, s1, sm + (half ^ 1) * 2 * se, se, nxt << g.ltc);
     cp_async_commit();
     cp_async_wait_prev();
     __syncthreads();
@@ -1456,7 +1503,7 @@ __global__ void __launch_bounds__(512) kp_col_grad(Geo<T> g, cx<T>* in, const cx
     cx<float> dl[8];
     if (MODE == CG_ADDDELTA && add_delta) {
 #pragma unroll
-      for (int s = 0; s < 8; ++s) dl[s] = delta[(size_t)(j + s * NY8) * H + kx];
+      for (int s = 0; s < 8; ++s) dl[s] = delta[cmi(g, j + s * NY8, kx)];
     }
     cx<T> v[2][8];
 #pragma unroll
@@ -1471,7 +1518,7 @@ __global__ void __launch_bounds__(512) kp_col_grad(Geo<T> g, cx<T>* in, const cx
         const T pv = pinv_ab(kxv, kyv[s], pc);
         const cx<T> z = cscale(cur[e], pv);
         P = first ? z : cadd(z, cscale(cur[se + e], beta));
-        dio[idx] = P;
+        dio[CMV ? cmi(g, ky, kx) : idx] = P;
       } else {
         P = cur[e];
         if (add_delta) {
@@ -1532,9 +1579,12 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
     cx<T>* cur = sm + half * 2 * se;
     const int kx = (tile << g.ltc) + b;
     cx<T> aux[8];  // b (residual), fetched early to overlap the FFT
-    if (MODE == CD_RESID || MODE == CD_RESID_REFINE || MODE == CD_RESID_FIRST) {
+    if (MODE == CD_RESID || MODE == CD_RESID_REFINE) {
 #pragma unroll
       for (int s = 0; s < 8; ++s) aux[s] = bvec[(size_t)(j + s * NY8) * H + kx];
+    } else if (MODE == CD_RESID_FIRST) {  // b32 is column-major
+#pragma unroll
+      for (int s = 0; s < 8; ++s) aux[s] = bvec[cmi(g, j + s * NY8, kx)];
     }
     cx<T> v[2][8];
 #pragma unroll
@@ -1557,7 +1607,8 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
       if constexpr (MODE == CD_PLAIN) {
         out[idx] = q;
       } else if constexpr (MODE == CD_CG) {
-        out[idx] = q;  // alpha came from the row pass (cg_alpha_from)
+        // alpha came from the row pass (cg_alpha_from); FP32 q column-major
+        out[std::is_same<T, float>::value ? cmi(g, ky, kx) : idx] = q;
       } else if constexpr (MODE == CD_RESID) {
         const cx<T> rv = csub(aux[s], q);
         out[idx] = rv;
@@ -1566,8 +1617,9 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
         accr[1] += w * r2 * (double)pinv_sym(g, kx, ky, pc);
       } else if constexpr (MODE == CD_RESID_FIRST) {
         const cx<float> rf = ccast<float>(csub(aux[s], q));
-        r32[idx] = rf;
-        delta32[idx] = czero<float>();
+        const size_t ci = cmi(g, ky, kx);  // r32 and delta32 are column-major
+        r32[ci] = rf;
+        delta32[ci] = czero<float>();
         const float wf = (float)w, wpf = wf * pinv_f32(g, kx, ky, pcf);
         r32acc.add_prod(wf * rf.x, rf.x);
         r32acc.add_prod(wf * rf.y, rf.y);
@@ -1580,8 +1632,9 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
         r64acc.add_prod(wt * rv.x, rv.x);
         r64acc.add_prod(wt * rv.y, rv.y);
         const cx<float> rf = ccast<float>(rv);
-        r32[idx] = rf;
-        delta32[idx] = czero<float>();
+        const size_t ci = cmi(g, ky, kx);
+        r32[ci] = rf;
+        delta32[ci] = czero<float>();
         const float wf = (float)w, wpf = wf * pinv_f32(g, kx, ky, pcf);
         r32acc.add_prod(wf * rf.x, rf.x);
         r32acc.add_prod(wf * rf.y, rf.y);
@@ -1606,173 +1659,6 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
     double acc[3] = {r64acc.value(), r32acc.value(), rzacc.value()}, tot[3];
     if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot) && threadIdx.x == 0)
       resid_sweep_init(st, tot[0], tot[1], tot[2]);
-  }
-}
-
-// Field-split variants of the pipelined FP32 column passes (col_pipe = 2).
-// The two transforms of a tile column go to two halves of the CTA, one
-// transform per thread: threads [0, P) work on field 0, [P, 2P) on field 1,
-// P = tc * ny/8.  Half the data registers per thread and twice the resident
-// warps of the NV = 2 kernels, for the same staging and shared memory; both
-// halves read the same staged inputs.
-template <int MODE>
-__global__ void __launch_bounds__(1024) kq_col_grad(Geo<float> g, cx<float>* in,
-                                                    const cx<float>* __restrict__ rvec,
-                                                    cx<float>* dio, const cx<float>* __restrict__ delta,
-                                                    cx<float>* __restrict__ Gx,
-                                                    cx<float>* __restrict__ Gy, SolveState* st,
-                                                    int check_done) {
-  using T = float;
-  if (check_done && st->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
-  constexpr int NS = MODE == CG_DUPDATE ? 2 : 1;
-  const int H = g.H, se = slab_elems(g), ntiles = g.H >> g.ltc;
-  const int P = g.tc << (g.lny - 3);
-  const int f = threadIdx.x >= P ? 1 : 0;
-  const int t = threadIdx.x - f * P;
-  const int b = t & (g.tc - 1), j = t >> g.ltc, NY8 = 1 << (g.lny - 3);
-  const T invn = (T)(1.0 / ((double)g.nx * (double)g.ny));
-  bool first = false, add_delta = false;
-  T beta = 0;
-  Pc<T> pc{};
-  if (MODE == CG_DUPDATE) {
-    first = st->first != 0;
-    beta = (T)st->beta;
-    pc = pc_of<T>(st);
-  }
-  if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
-  const cx<T>* s0 = MODE == CG_DUPDATE ? rvec : in;
-  const cx<T>* s1 = MODE == CG_DUPDATE ? dio : nullptr;
-  cx<T>* out = f ? Gy : Gx;
-  int half = 0;
-  int tile = blockIdx.x;
-  if (tile < ntiles) stage_cols<T, NS>(g, s0, s1, sm, se, tile << g.ltc);
-  cp_async_commit();
-  for (; tile < ntiles; tile += gridDim.x) {
-    const int nxt = tile + gridDim.x;
-    if (nxt < ntiles) stage_cols<T, NS>(g, s0, s1, sm + (half ^ 1) * 2 * se, se, nxt << g.ltc);
-    cp_async_commit();
-    cp_async_wait_prev();
-    __syncthreads();
-    cx<T>* cur = sm + half * 2 * se;
-    const int kx = (tile << g.ltc) + b;
-    const T ax = g.kxd[kx] * invn;
-    cx<T> v[1][8];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const int ky = j + s * NY8;
-      const size_t idx = (size_t)ky * H + kx;
-      const int e = padk(ky) * g.tc + b;
-      cx<T> Pv;
-      if constexpr (MODE == CG_PLAIN) {
-        Pv = cur[e];
-      } else if constexpr (MODE == CG_DUPDATE) {
-        const cx<T> z = cscale(cur[e], pinv_sym(g, kx, ky, pc));
-        Pv = first ? z : cadd(z, cscale(cur[se + e], beta));
-        if (!f) dio[idx] = Pv;
-      } else {
-        Pv = cur[e];
-        if (add_delta) {
-          Pv = cadd(Pv, delta[idx]);
-          if (!f) in[idx] = Pv;
-        }
-      }
-      const T a = f ? g.kyd[ky] * invn : ax;
-      v[0][s] = cmk<T>(-a * Pv.y, a * Pv.x);  // i (k/n) P
-    }
-    cx<T>* const sl[1] = {cur + f * se + b};
-    fft_canon<+1, 1>(v, sl, g.tc, j, g.lny, g.twy);
-#pragma unroll
-    for (int s = 0; s < 8; ++s) out[(size_t)(j + s * NY8) * H + kx] = v[0][s];
-    __syncthreads();
-    half ^= 1;
-  }
-  cp_async_wait_all();
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(1024) kq_col_div(Geo<float> g, const cx<float>* __restrict__ Qx,
-                                                   const cx<float>* __restrict__ Qy,
-                                                   const cx<float>* __restrict__ bvec,
-                                                   cx<float>* __restrict__ out,
-                                                   cx<float>* __restrict__ r32,
-                                                   cx<float>* __restrict__ delta32, SolveState* st) {
-  using T = float;
-  if (MODE == CD_CG && st->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
-  const int H = g.H, se = slab_elems(g), ntiles = g.H >> g.ltc;
-  const int P = g.tc << (g.lny - 3);
-  const int f = threadIdx.x >= P ? 1 : 0;
-  const int t = threadIdx.x - f * P;
-  const int b = t & (g.tc - 1), j = t >> g.ltc, NY8 = 1 << (g.lny - 3);
-  DotAcc<float> r32acc, rzacc;
-  const Pc<float> pcf = MODE == CD_RESID_FIRST ? pc_of<float>(st) : Pc<float>{};
-  int half = 0;
-  int tile = blockIdx.x;
-  if (tile < ntiles) stage_cols<T, 2>(g, Qx, Qy, sm, se, tile << g.ltc);
-  cp_async_commit();
-  for (; tile < ntiles; tile += gridDim.x) {
-    const int nxt = tile + gridDim.x;
-    if (nxt < ntiles) stage_cols<T, 2>(g, Qx, Qy, sm + (half ^ 1) * 2 * se, se, nxt << g.ltc);
-    cp_async_commit();
-    cp_async_wait_prev();
-    __syncthreads();
-    cx<T>* cur = sm + half * 2 * se;
-    const int kx = (tile << g.ltc) + b;
-    cx<T> aux[8];  // b (first residual), fetched early to overlap the FFT
-    if (MODE == CD_RESID_FIRST && !f) {
-#pragma unroll
-      for (int s = 0; s < 8; ++s) aux[s] = bvec[(size_t)(j + s * NY8) * H + kx];
-    }
-    cx<T> v[1][8];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) v[0][s] = cur[f * se + padk(j + s * NY8) * g.tc + b];
-    cx<T>* const sl[1] = {cur + f * se + b};
-    fft_canon<-1, 1>(v, sl, g.tc, j, g.lny, g.twy);
-    // field 1 hands ky * FFT(Qy) to field 0 through its slab
-    __syncthreads();
-    if (f) {
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const int ky = j + s * NY8;
-        cur[se + padk(ky) * g.tc + b] = cscale(v[0][s], g.kyd[ky]);
-      }
-    }
-    __syncthreads();
-    if (!f) {
-      const T ax = g.kxd[kx];
-      const float w = kx == 0 ? 1.0f : 2.0f;
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const int ky = j + s * NY8;
-        const size_t idx = (size_t)ky * H + kx;
-        const cx<T> yv = cur[se + padk(ky) * g.tc + b];
-        const cx<T> tq = cmk<T>(ax * v[0][s].x + yv.x, ax * v[0][s].y + yv.y);
-        const cx<T> q = cmk<T>(tq.y, -tq.x);  // -i (kx Qx + ky Qy)
-        if constexpr (MODE == CD_RESID_FIRST) {
-          const cx<float> rf = csub(aux[s], q);
-          r32[idx] = rf;
-          delta32[idx] = czero<float>();
-          const float wpf = w * pinv_f32(g, kx, ky, pcf);
-          r32acc.add_prod(w * rf.x, rf.x);
-          r32acc.add_prod(w * rf.y, rf.y);
-          rzacc.add_prod(wpf * rf.x, rf.x);
-          rzacc.add_prod(wpf * rf.y, rf.y);
-        } else {
-          out[idx] = q;  // CD_PLAIN; CD_CG (alpha came from the row pass)
-        }
-      }
-    }
-    __syncthreads();
-    half ^= 1;
-  }
-  cp_async_wait_all();
-  if constexpr (MODE == CD_RESID_FIRST) {
-    double a2[2] = {r32acc.value(), rzacc.value()}, t2[2];
-    if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
-      resid_first_init(st, t2[0], t2[1]);
   }
 }
 
@@ -1896,9 +1782,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_cg_update(Geo<T
   const Pc<T> pc = pc_of<T>(st);
   const size_t total = (size_t)g.ny * g.H;
   DotAcc<T> rr, rz;
+  // the FP32 refinement's vectors are column-major, plain FP64 CG's row-major
+  constexpr bool CM = std::is_same<T, float>::value;
   auto upd = [&](size_t i, cx<T> dv, cx<T> xv, cx<T> qv, cx<T> rv) {
-    const int kx = (int)(i & (size_t)(g.H - 1));
-    const int ky = (int)(i >> g.lH);
+    const int kx = CM ? (int)(i >> g.lny) : (int)(i & (size_t)(g.H - 1));
+    const int ky = CM ? (int)(i & (size_t)(g.ny - 1)) : (int)(i >> g.lH);
     x[i] = cmk<T>(xv.x + alpha * dv.x, xv.y + alpha * dv.y);
     rv = cmk<T>(rv.x - alpha * qv.x, rv.y - alpha * qv.y);
     r[i] = rv;
@@ -1928,27 +1816,24 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_cg_update(Geo<T
   for (; i < total; i += S) upd(i, d[i], x[i], q[i], r[i]);
   double acc[2] = {rr.value(), rz.value()};
   double tot[2];
-  if (last_cta_sum<2>(acc, g.partials, &st->ticket[TK_UPDATE], tot) && threadIdx.x == 0) {
-    const double rho_new = tot[1];
-    st->rnorm2 = tot[0];
-    st->beta = st->rho > 0 ? rho_new / st->rho : 0.0;
-    st->rho = rho_new;
-    st->it += 1;
-    st->total_it += 1;
-    if (!isfinite(tot[0])) {
-      st->status = HC_ENONFINITE;
-      st->done = 1;
-    } else if (tot[0] <= st->thresh2) {
-      st->done = 1;
-    } else if (st->it >= st->maxit) {
-      st->done = 1;
-      st->status = HC_ENOCONV;
-    }
-    if (st->graph_mode) cudaGraphSetConditional(st->h_cur, st->done ? 0u : 1u);
-  }
+  if (last_cta_sum<2>(acc, g.partials, &st->ticket[TK_UPDATE], tot) && threadIdx.x == 0)
+    cg_step_finish(st, tot[0], tot[1]);
 }
 
 // ------------------------------------------------------------------ elementwise
+// Packed 2D spectrum (ny rows of H values, row-major) -> FP32 column-major
+// copy (cmi), for the 2D refinement's FP32 source spectrum.
+template <typename Ti>
+__global__ void k_to_cm(Geo<float> g, const cx<Ti>* __restrict__ in, cx<float>* __restrict__ out) {
+  const size_t n = (size_t)g.ny * g.H;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n;
+       o += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(o >> g.lny), ky = (int)(o & (size_t)(g.ny - 1));
+    const cx<Ti> v = in[(size_t)ky * g.H + kx];
+    out[o] = cmk<float>((float)v.x, (float)v.y);
+  }
+}
+
 template <typename To, typename Ti>
 __global__ void k_convert(const Ti* __restrict__ in, To* __restrict__ out, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -2290,26 +2175,13 @@ template <typename T>
 static inline size_t pipe_smem(const Geo<T>& g) {
   return (size_t)4 * (g.ny + (g.ny >> 3)) * g.tc * sizeof(cx<T>);
 }
+
 template <typename T, typename Tin>
 void col_grad(const Geo<T>& g, int mode, cx<Tin>* in, const cx<T>* rvec, cx<T>* dio,
               const cx<float>* delta, cx<T>* Gx, cx<T>* Gy, SolveState* st, int check_done,
               cudaStream_t s) {
   const int nb = g.H >> g.ltc, nt = col_threads(g);
   const size_t sm = col_smem(g, 2);
-  if constexpr (std::is_same<T, Tin>::value && std::is_same<T, float>::value) {
-    if (g.pipe == 2) {
-      const size_t ps = pipe_smem(g);
-      if (mode == CG_PLAIN)
-        kq_col_grad<CG_PLAIN><<<g.pgrid, 2 * nt, ps, s>>>(g, in, rvec, dio, delta, Gx, Gy, st, check_done);
-      else if (mode == CG_DUPDATE)
-        kq_col_grad<CG_DUPDATE><<<g.pgrid, 2 * nt, ps, s>>>(g, in, rvec, dio, delta, Gx, Gy, st,
-                                                           check_done);
-      else
-        kq_col_grad<CG_ADDDELTA><<<g.pgrid, 2 * nt, ps, s>>>(g, in, rvec, dio, delta, Gx, Gy, st,
-                                                            check_done);
-      return;
-    }
-  }
   if constexpr (std::is_same<T, Tin>::value) {
     if (g.pipe) {
       const size_t ps = pipe_smem(g);
@@ -2339,18 +2211,6 @@ void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const 
              cudaStream_t s) {
   const int nb = g.H >> g.ltc, nt = col_threads(g);
   const size_t sm = col_smem(g, 2);
-  if constexpr (std::is_same<T, float>::value) {
-    if (g.pipe == 2 && mode != CD_RESID && mode != CD_RESID_REFINE) {
-      const size_t ps = pipe_smem(g);
-      if (mode == CD_PLAIN)
-        kq_col_div<CD_PLAIN><<<g.pgrid, 2 * nt, ps, s>>>(g, Qx, Qy, b, out, r32, delta32, st);
-      else if (mode == CD_CG)
-        kq_col_div<CD_CG><<<g.pgrid, 2 * nt, ps, s>>>(g, Qx, Qy, b, out, r32, delta32, st);
-      else
-        kq_col_div<CD_RESID_FIRST><<<g.pgrid, 2 * nt, ps, s>>>(g, Qx, Qy, b, out, r32, delta32, st);
-      return;
-    }
-  }
   if (g.pipe) {
     const size_t ps = pipe_smem(g);
     switch (mode) {
@@ -2367,6 +2227,7 @@ void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const 
         if constexpr (std::is_same<T, float>::value)
           kp_col_div<T, CD_RESID_FIRST><<<g.pgrid, nt, ps, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
         break;
+
       default:
         kp_col_div<T, CD_RESID_REFINE><<<g.pgrid, nt, ps, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
         break;
@@ -2387,6 +2248,7 @@ void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const 
       if constexpr (std::is_same<T, float>::value)
         k_col_div<T, CD_RESID_FIRST><<<nb, nt, sm, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
       break;
+
     default:
       k_col_div<T, CD_RESID_REFINE><<<nb, nt, sm, s>>>(g, Qx, Qy, d, b, out, r32, delta32, st);
       break;
@@ -2409,6 +2271,10 @@ template <typename T>
 void cg_update(const Geo<T>& g, cx<T>* x, cx<T>* r, const cx<T>* d, const cx<T>* q, SolveState* st,
                cudaStream_t s) {
   k_cg_update<T><<<upd_blocks((size_t)g.ny * g.H), 256, 0, s>>>(g, x, r, d, q, st);
+}
+template <typename Ti>
+void to_cm(const Geo<float>& g, const cx<Ti>* in, cx<float>* out, cudaStream_t s) {
+  k_to_cm<Ti><<<upd_blocks((size_t)g.ny * g.H), 256, 0, s>>>(g, in, out);
 }
 template <typename To, typename Ti>
 void convert(const Ti* in, To* out, size_t n, cudaStream_t s) {
@@ -2483,12 +2349,6 @@ void set_smem_limits_t() {
   if constexpr (std::is_same<T, float>::value) {
     allow_smem(k_col_div<T, CD_RESID_FIRST>);
     allow_smem(kp_col_div<T, CD_RESID_FIRST>);
-    allow_smem(kq_col_grad<CG_PLAIN>);
-    allow_smem(kq_col_grad<CG_DUPDATE>);
-    allow_smem(kq_col_grad<CG_ADDDELTA>);
-    allow_smem(kq_col_div<CD_PLAIN>);
-    allow_smem(kq_col_div<CD_CG>);
-    allow_smem(kq_col_div<CD_RESID_FIRST>);
   }
   allow_smem(kp_col_div<T, CD_PLAIN>);
   allow_smem(kp_col_div<T, CD_CG>);

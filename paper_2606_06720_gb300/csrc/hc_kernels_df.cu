@@ -27,6 +27,7 @@ template void col_grad<float, df64>(const Geo<float>&, int, cx<df64>*, const cx<
 template void col_div<df64>(const Geo<df64>&, int, const cx<df64>*, const cx<df64>*,
                             const cx<df64>*, const cx<df64>*, cx<df64>*, cx<float>*, cx<float>*,
                             SolveState*, cudaStream_t);
+template void to_cm<df64>(const Geo<float>&, const cx<df64>*, cx<float>*, cudaStream_t);
 template void convert<df64, double>(const double*, df64*, size_t, cudaStream_t);
 template void convert<double, df64>(const df64*, double*, size_t, cudaStream_t);
 template void convert<float, df64>(const df64*, float*, size_t, cudaStream_t);

@@ -30,6 +30,7 @@ template void col_gradnorm<float>(const Geo<float>&, const cx<float>*, const cx<
                                  cudaStream_t);
 template void cg_update<float>(const Geo<float>&, cx<float>*, cx<float>*, const cx<float>*,
                                const cx<float>*, SolveState*, cudaStream_t);
+template void to_cm<double>(const Geo<float>&, const cx<double>*, cx<float>*, cudaStream_t);
 template void msum<float>(const Geo<float>&, const float*, const float*, SolveState*, cudaStream_t);
 
 template void row_adj_point<float>(const Geo<float>&, cx<float>*, cx<float>*, const cx<float>*, const cx<float>*,

@@ -242,10 +242,9 @@ def test_tuning_changes_only_summation_order(hc):
         for bad in [((3, 1), (1, 1)), ((64, 1), (1, 1)), ((1, 1), (1, 1024)), ((1, 0), (1, 1))]:
             with pytest.raises(hc.HuCaiError):
                 s.set_tuning(list(bad[0]), list(bad[1]), [0, 0])
-        with pytest.raises(hc.HuCaiError):  # col_pipe 0, 1 or (FP32 kernels only) 2
-            s.set_tuning([2, 1], [1, 1], [3, 0])
-        with pytest.raises(hc.HuCaiError):
-            s.set_tuning([2, 1], [1, 1], [0, 2])
+        for bad_pipe in ([2, 0], [0, 2], [-1, 0]):  # col_pipe 0 or 1
+            with pytest.raises(hc.HuCaiError):
+                s.set_tuning([2, 1], [1, 1], bad_pipe)
         for bad_row_pipe in ([2, 0], [0, 1], [-1, 0]):  # 0/1, and only for the FP32 passes
             with pytest.raises(hc.HuCaiError):
                 s.set_tuning([2, 1], [1, 1], [0, 0], bad_row_pipe)
@@ -276,8 +275,7 @@ def test_pipelined_column_passes_match_plain_ones(hc, precision):
     w = W.source_sink_2d(512, steps=3)
     outs = []
     # (FP32 tile, pipe): 16-byte copies, and one FP32 column with 8-byte copies
-    for col, pipe in (((2, 1), (0, 0)), ((2, 1), (1, 1)), ((1, 1), (1, 0)), ((2, 1), (2, 0)),
-                      ((4, 1), (2, 1))):
+    for col, pipe in (((2, 1), (0, 0)), ((2, 1), (1, 1)), ((1, 1), (1, 0)), ((4, 2), (0, 1))):
         with make_solver(hc, w, precision) as s:
             t = s.get_tuning()
             s.set_tuning(list(col), t["row_rows"], list(pipe))
