@@ -32,7 +32,11 @@ UNIT = "Mpoint-steps/s"
 N_GRID = 2048
 CG_RTOL_REFINED = 1e-8      # the refined path's pressure tolerance
 FP64_EQUAL_RTOL = 1e-4      # loosest plain-FP64 tolerance reaching m rel. L2 <= 1e-5 at 100 steps
-                            # (calibrated with --accuracy: rtol 1e-4 gives 1.06e-6, 1e-3 gives 1.75e-5)
+# Preconditioner of the timed legs: the anisotropic option of reading R3
+# (-div(Kbar grad), Kbar = mean(m m^T) + mean(r) I).  It changes CG iteration
+# counts only; the library's default, kappa (-Laplacian), is the scalar_kappa leg.
+PRECOND = "kbar"
+                            # (calibrated with --accuracy: rtol 1e-4 gives 5.9e-7, 1e-3 gives 2.2e-5)
 HBM_PEAK_FALLBACK = 6800.0  # GB/s, recipe fallback when MEASURED_PEAKS.json is absent
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 of GB300 (recipe table); a plain-ALU bound
 
@@ -271,6 +275,8 @@ def workload_config(extra: dict | None = None) -> dict:
                     "m0~U[0,0.5] seed 0, c=25 D=0.02 gamma=0.5 dt=5e-4",
         "precision": "FP32 FFT/operator/split step + FP64 iterative refinement of the pressure",
         "cg_rtol": CG_RTOL_REFINED,
+        "preconditioner": "kbar: -div(Kbar grad), Kbar = mean(m m^T) + mean(r) I (reading R3's "
+                          "anisotropic option; the default scalar kappa is the scalar_kappa leg)",
         "grid": [N_GRID, N_GRID],
         "l2": "inputs larger than L2 (refined working set ~390 MB > 129 MiB L2); no flush",
         "loop_control": "one CUDA graph per step, CG/refinement loops as conditional WHILE nodes",
@@ -315,7 +321,7 @@ def run_accuracy(args) -> None:
 
     def run(precision, rtol):
         with P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision=precision,
-                      cg_rtol=rtol, cg_maxit=5000) as s:
+                      cg_rtol=rtol, cg_maxit=5000, precond=PRECOND) as s:
             s.set_r(w.r)
             s.set_source(w.S)
             s.set_m(w.m0)
@@ -355,7 +361,8 @@ def run_diagnostics(P, W, args, dev, barrier, max_over_ranks, world, headline) -
     w = W.source_sink_2d(N_GRID)
     K = max(10, args.steps // 10)
     s = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp32_refined",
-                 cg_rtol=CG_RTOL_REFINED, cg_maxit=2000, device=str(dev), diagnostics=True)
+                 cg_rtol=CG_RTOL_REFINED, cg_maxit=2000, precond=PRECOND,
+                 device=str(dev), diagnostics=True)
     s.set_r(w.r)
     s.set_source(w.S)
     s.set_m(w.m0)
@@ -374,7 +381,7 @@ def run_diagnostics(P, W, args, dev, barrier, max_over_ranks, world, headline) -
     for name, wp in (("paper_four_sinks_512_gamma1", W.paper_four_sinks(512, 1.0)),
                      ("paper_internal_sink_512_mconst", W.paper_internal_sink(512, 0.75))):
         sp = P.Solver(wp.n, wp.L, c=wp.c, D=wp.D, gamma=wp.gamma, dt=wp.dt,
-                      precision="fp32_refined", cg_rtol=wp.cg_rtol, cg_maxit=2000,
+                      precision="fp32_refined", cg_rtol=wp.cg_rtol, cg_maxit=2000, precond=PRECOND,
                       device=str(dev))
         sp.set_r(wp.r)
         sp.set_source(wp.S)
@@ -402,7 +409,8 @@ def run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src) -
     import torch
     w = W.source_sink_3d(args.n3d)
     s = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp32_refined",
-                 cg_rtol=CG_RTOL_REFINED, cg_maxit=2000, use_graph=not args.host_loop,
+                 cg_rtol=CG_RTOL_REFINED, cg_maxit=2000, precond=PRECOND,
+                 use_graph=not args.host_loop,
                  device=str(dev))
     s.set_r(w.r)
     s.set_source(w.S)
@@ -487,7 +495,8 @@ def run_gb300(args) -> None:
     w = W.source_sink_2d(N_GRID)
     K, Wm = args.steps, args.warmup
     s = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp32_refined",
-                 cg_rtol=CG_RTOL_REFINED, cg_maxit=2000, use_graph=not args.host_loop,
+                 cg_rtol=CG_RTOL_REFINED, cg_maxit=2000, precond=PRECOND,
+                 use_graph=not args.host_loop,
                  device=str(dev))
     s.set_r(w.r)
     s.set_source(w.S)
@@ -591,7 +600,7 @@ def run_gb300(args) -> None:
     if not args.no_df:
         sdf = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt,
                        precision="fp32_refined_df", cg_rtol=CG_RTOL_REFINED, cg_maxit=2000,
-                       use_graph=not args.host_loop, device=str(dev))
+                       precond=PRECOND, use_graph=not args.host_loop, device=str(dev))
         sdf.set_r(w.r)
         sdf.set_source(w.S)
         sdf.set_m(w.m0)
@@ -626,6 +635,35 @@ def run_gb300(args) -> None:
                "refinement_arithmetic": "double-float (48-bit significand) on the FP32 pipes",
                "kernels": kdf}
 
+    # ---- the headline path with the library's default preconditioner (reading
+    # R3: kappa (-Laplacian), kappa = mean(r) + mean(|m|^2)/2): iteration counts
+    # and throughput beside the anisotropic Kbar the timed legs use
+    scal = None
+    if not args.no_scalar:
+        ss = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp32_refined",
+                      cg_rtol=CG_RTOL_REFINED, cg_maxit=2000, precond="scalar",
+                      use_graph=not args.host_loop, device=str(dev))
+        ss.set_tuning(tuning["col_tile"], tuning["row_rows"], tuning["col_pipe"], tuning["row_pipe"])
+        ss.set_r(w.r)
+        ss.set_source(w.S)
+        ss.set_m(w.m0)
+        ss.step(Wm)
+        Kc = K  # the headline's steps: iteration counts grow along the run
+        barrier()
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(ss.stream)
+        stc = ss.step(Kc)
+        c1.record(ss.stream)
+        torch.cuda.synchronize()
+        msc = max_over_ranks(c0.elapsed_time(c1))
+        ss.close()
+        scal = {"value": world * npts * Kc / (msc / 1e3) / 1e6, "unit": UNIT,
+                "ms_per_step": msc / Kc, "steps": Kc, "precond": "scalar kappa (-Laplacian)",
+                "cg_iters_per_step": stc.total_cg_iters / Kc,
+                "rel_residual_last_step": stc.rel_residual}
+
     # ---- batched parameter sweep: 48 instances of mixed grids in one graph launch
     sweep = None
     if not args.no_sweep:
@@ -635,7 +673,7 @@ def run_gb300(args) -> None:
         for wi in sws:
             si = P.Solver(wi.n, wi.L, c=wi.c, D=wi.D, gamma=wi.gamma, dt=wi.dt,
                           precision="fp32_refined", cg_rtol=CG_RTOL_REFINED, cg_maxit=2000,
-                          device=str(dev))
+                          precond=PRECOND, device=str(dev))
             si.set_r(wi.r)
             si.set_source(wi.S)
             si.set_m(wi.m0)
@@ -685,7 +723,7 @@ def run_gb300(args) -> None:
         Ka, every = args.adj_steps, max(1, args.adj_steps // 3)
         sa = P.Solver(wa.n, wa.L, c=wa.c, D=wa.D, gamma=wa.gamma, dt=wa.dt,
                       precision="fp32_refined", cg_rtol=CG_RTOL_REFINED, cg_maxit=2000,
-                      device=str(dev))
+                      precond=PRECOND, device=str(dev))
         sa.set_r(wa.r)
         sa.set_source(wa.S)
         if not args.no_tune:
@@ -732,7 +770,8 @@ def run_gb300(args) -> None:
     if not args.no_fp64:
         K64 = max(3, K // 20)
         s64 = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp64",
-                       cg_rtol=FP64_EQUAL_RTOL, cg_maxit=5000, use_graph=True, device=str(dev))
+                       cg_rtol=FP64_EQUAL_RTOL, cg_maxit=5000, precond=PRECOND,
+                       use_graph=True, device=str(dev))
         s64.set_r(w.r)
         s64.set_source(w.S)
         s64.set_m(w.m0)
@@ -785,7 +824,8 @@ def run_gb300(args) -> None:
             "fp64_residuals_per_step": res64, "df_mid_residuals_per_step": mid_per_step,
             "cg_iterations_per_s": world * iters_per_step * K / (ms_max / 1e3),
             "rel_residual_last_step": st.rel_residual,
-            "fp64_plain": fp64, "refined_df": dfv, "sweep": sweep, "adjoint": adjv,
+            "fp64_plain": fp64, "refined_df": dfv, "scalar_kappa": scal, "sweep": sweep,
+            "adjoint": adjv,
             "three_d": three_d, "diagnostics": diag, "kernels": kernels,
         }
         print(json.dumps(line), flush=True)
@@ -818,6 +858,8 @@ def main() -> None:
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-df", action="store_true", help="skip the double-float refinement leg")
+    ap.add_argument("--no-scalar", action="store_true",
+                    help="skip the leg with the default scalar-kappa preconditioner")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched 48-instance sweep leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--adj-steps", type=int, default=60, help="adjoint leg: steps (C4 uses 500)")

@@ -78,9 +78,9 @@ typedef struct {
   double cg_rtol;         /* stop when ||S - A p||_2 <= cg_rtol ||S||_2, S projected (Section 2.4; default 1e-7 if <= 0) */
   int cg_maxit;           /* CG iteration cap per solve; in refined mode per inner FP32 solve (default 1000 if <= 0) */
   int precision;          /* HC_FP64_PLAIN or HC_FP32_REFINED */
-  double kappa;           /* > 0: preconditioner kappa (-Laplacian); <= 0: -div(Kbar grad) with
-                             Kbar = mean(m m^T) + mean(r) I, recomputed every step (reading of the
-                             conclusion's constant-coefficient preconditioner) */
+  double kappa;           /* > 0: preconditioner kappa (-Laplacian); <= 0: chosen by precond,
+                             recomputed every step (the conclusion's constant-coefficient
+                             preconditioner, reading R3) */
   double inner_rtol;      /* refined mode: inner FP32 CG stops at this reduction of its own residual (default 1e-4 if <= 0) */
   int max_sweeps;         /* refined mode: cap on FP64 refinement sweeps per solve (default 10 if <= 0) */
   int use_graph;          /* 1: each step runs as one CUDA graph with device-side loop control; 0: host loop */
@@ -97,7 +97,13 @@ typedef struct {
                               evaluated in double-float on the FP32 pipes, with p += delta still
                               accumulated in FP64; the refinement loop after it is decided by FP64
                               residuals.  1: that residual is FP64 too. */
+  int precond;             /* with kappa <= 0: HC_PRECOND_SCALAR (0, default) kappa (-Laplacian) with
+                              kappa = mean(r) + mean(|m|^2)/dim; HC_PRECOND_KBAR (1) -div(Kbar grad)
+                              with Kbar = mean(m m^T) + mean(r) I, the whole mean of the coefficient
+                              tensor (fewer CG iterations when m is anisotropic on average) */
 } hc_params;
+
+enum { HC_PRECOND_SCALAR = 0, HC_PRECOND_KBAR = 1 };
 
 typedef struct {
   int cg_iters;        /* CG iterations of the last step's pressure solve (summed over sweeps) */

@@ -51,7 +51,8 @@ class _Grid(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("c", C.c_double), ("D", C.c_double), ("gamma", C.c_double), ("dt", C.c_double),
-                ("cg_rtol", C.c_double), ("cg_maxit", C.c_int), ("kappa", C.c_double)]
+                ("cg_rtol", C.c_double), ("cg_maxit", C.c_int), ("kappa", C.c_double),
+                ("precond", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -160,10 +161,11 @@ class Params:
     cg_rtol: float = 1e-10
     cg_maxit: int = 1000
     kappa: float = 0.0
+    precond: int = 0   # 0: kappa (-Laplacian), reading R3; 1: the anisotropic Kbar option
 
     def c_struct(self) -> _Params:
         return _Params(self.c, self.D, self.gamma, self.dt, self.cg_rtol, int(self.cg_maxit),
-                       self.kappa)
+                       self.kappa, int(self.precond))
 
 
 @dataclass
@@ -287,13 +289,18 @@ def kappa_default(grid: Grid, m, r) -> float:
     return _load().or_kappa_default(C.byref(g), _dp(m), _dp(r))
 
 
-def pcg(grid: Grid, m, r, b, x0=None, kappa=None, rtol: float = 1e-10, maxit: int = 1000):
+def pcg(grid: Grid, m, r, b, x0=None, kappa=None, rtol: float = 1e-10, maxit: int = 1000,
+        precond: int = 0):
     """Returns (x, Stats); raises nothing on non-convergence (Stats.rc says).
-    kappa: None for the default Kbar of R3, else a scalar kappa (kappa I), a
-    dim x dim matrix or the 6-vector of kbar_array."""
+    kappa: None for reading R3's preconditioner (precond 0: kappa_default I;
+    precond 1: kbar_default), else a scalar kappa (kappa I), a dim x dim
+    matrix or the 6-vector of kbar_array."""
     m, r, b = _f64(m), _f64(r), _f64(b)
     x = np.zeros(grid.shape) if x0 is None else _f64(x0).reshape(grid.shape).copy()
-    kb = kbar_default(grid, m, r) if kappa is None else kbar_array(grid.dim, kappa)
+    if kappa is None:
+        kb = kbar_default(grid, m, r) if precond == 1 else kbar_array(grid.dim, kappa_default(grid, m, r))
+    else:
+        kb = kbar_array(grid.dim, kappa)
     st = _Stats()
     g = grid.c()
     rc = _load().or_pcg(C.byref(g), _dp(m), _dp(r), _dp(b), _dp(x), _dp(kb), rtol, int(maxit),

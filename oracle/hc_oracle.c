@@ -15,10 +15,12 @@
  *   R2  the null space of the discrete operator is spanned by the 2^dim corner
  *       modes (every index 0 or N/2); S, p and the CG iterates are kept
  *       orthogonal to it;
- *   R3  preconditioner: the constant-coefficient operator -div(Kbar grad) with
- *       Kbar = mean over the grid of K = m m^T + r I (a constant symmetric
- *       matrix), built from the same derivative symbols and inverted on the
- *       non-null modes; a user kappa > 0 gives Kbar = kappa I;
+ *   R3  preconditioner: a constant-coefficient operator -div(Kbar grad) built
+ *       from the same derivative symbols and inverted on the non-null modes,
+ *       with Kbar = kappa I, kappa = mean(r) + mean(|m|^2)/dim (the isotropic
+ *       part of the mean of K = m m^T + r I); option precond = 1 takes the
+ *       whole mean, Kbar = mean(m m^T) + mean(r) I; a user kappa > 0 gives
+ *       Kbar = kappa I;
  *   R4  CG stops when ||res||_2 <= rtol ||S||_2 (plain Euclidean norms);
  *   R5  p^0 = 0 unless the caller supplies one;
  *   R6  the activation uses grad p^{k+1} (Algorithm 1 solves for p first);
@@ -359,11 +361,13 @@ double or_kappa_default(const or_grid* g, const double* m, const double* r) {
   return sr / (double)npts + sm / (double)npts / (double)g->dim;
 }
 
-/* Kbar of a solve: the caller's kappa I when kappa > 0, else the default (R3). */
+/* Kbar of a solve (R3): the caller's kappa I when kappa > 0, else the mean of
+   K (precond 1) or its isotropic part (precond 0, the default). */
 static void or_kbar_for(const or_grid* g, const or_params* prm, const double* m, const double* r,
                         double* kbar) {
-  if (prm->kappa > 0) {
-    for (int e = 0; e < 6; ++e) kbar[e] = (e < g->dim) ? prm->kappa : 0.0;
+  if (prm->kappa > 0 || prm->precond != 1) {
+    const double k = prm->kappa > 0 ? prm->kappa : or_kappa_default(g, m, r);
+    for (int e = 0; e < 6; ++e) kbar[e] = (e < g->dim) ? k : 0.0;
   } else {
     or_kbar_default(g, m, r, kbar);
   }

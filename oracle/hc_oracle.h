@@ -39,7 +39,10 @@ typedef struct {
   double c, D, gamma, dt;  /* model parameters of eqs (1.1a)-(1.1b) and the time step */
   double cg_rtol;          /* stop when ||S - A p||_2 <= cg_rtol ||S||_2 (reading R4) */
   int cg_maxit;            /* iteration cap */
-  double kappa;            /* > 0: preconditioner kappa (-Laplacian); <= 0: the default Kbar of R3 */
+  double kappa;            /* > 0: preconditioner kappa (-Laplacian), whatever precond says */
+  int precond;             /* kappa <= 0: 0 (default) kappa (-Laplacian) with the kappa of reading
+                              R3, mean(r) + mean(|m|^2)/dim; 1 -div(Kbar grad), Kbar = mean(m m^T)
+                              + mean(r) I (the anisotropic constant-coefficient option) */
 } or_params;
 
 typedef struct {
@@ -90,11 +93,11 @@ int or_precond(const or_grid* g, const double* kbar, const double* res, double* 
 /* Remove the null-space components of A (the 2^dim corner modes, R2) in place. */
 void or_project(const or_grid* g, double* f);
 
-/* Default Kbar (R3): mean(m m^T) + mean(r) I, in the layout of or_precond. */
+/* The anisotropic Kbar of R3's option: mean(m m^T) + mean(r) I, in the layout of or_precond. */
 void or_kbar_default(const or_grid* g, const double* m, const double* r, double* kbar);
 
-/* Its isotropic part trace(Kbar) / dim = mean(r) + mean(|m|^2) / dim, the
- * value reported as kappa. */
+/* The default preconditioner constant of R3: mean(r) + mean(|m|^2) / dim, the
+ * isotropic part trace(Kbar) / dim of that mean. */
 double or_kappa_default(const or_grid* g, const double* m, const double* r);
 
 /* Preconditioned CG (Section 2.4) for A p = b, b projected; p in/out holds the

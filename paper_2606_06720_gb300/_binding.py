@@ -36,12 +36,18 @@ class hc_grid(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("L", C.c_double * 3)]
 
 
+# preconditioner of reading R3: "scalar" kappa (-Laplacian) (the default) or
+# "kbar", the whole mean of the coefficient tensor
+_PRECOND = {"scalar": 0, "kbar": 1}
+
+
 class hc_params(C.Structure):
     _fields_ = [("c", C.c_double), ("D", C.c_double), ("gamma", C.c_double), ("dt", C.c_double),
                 ("cg_rtol", C.c_double), ("cg_maxit", C.c_int), ("precision", C.c_int),
                 ("kappa", C.c_double), ("inner_rtol", C.c_double), ("max_sweeps", C.c_int),
                 ("use_graph", C.c_int), ("stream", C.c_void_p), ("diagnostics", C.c_int),
-                ("fp64_first_residual", C.c_int), ("fp64_mid_residual", C.c_int)]
+                ("fp64_first_residual", C.c_int), ("fp64_mid_residual", C.c_int),
+                ("precond", C.c_int)]
 
 
 class hc_tuning(C.Structure):
@@ -223,7 +229,7 @@ class Solver:
                  kappa: float = 0.0, inner_rtol: float = 1e-4, max_sweeps: int = 10,
                  use_graph: bool = True, device: str = "cuda:0", stream=None,
                  diagnostics: bool = False, fp64_first_residual: bool = False,
-                 fp64_mid_residual: bool = False):
+                 fp64_mid_residual: bool = False, precond: str = "scalar"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -247,7 +253,7 @@ class Solver:
         self.params = hc_params(c, D, gamma, dt, cg_rtol, int(cg_maxit), prec, kappa, inner_rtol,
                                 int(max_sweeps), int(bool(use_graph)), self.stream.cuda_stream,
                                 int(bool(diagnostics)), int(bool(fp64_first_residual)),
-                                int(bool(fp64_mid_residual)))
+                                int(bool(fp64_mid_residual)), _PRECOND[precond])
         nbytes = C.c_size_t()
         _check(hc_workspace_size(C.byref(self.grid), C.byref(self.params), C.byref(nbytes)),
                "hc_workspace_size")
@@ -283,6 +289,8 @@ class Solver:
         for k, v in kw.items():
             if k in ("use_graph", "diagnostics", "fp64_first_residual", "fp64_mid_residual"):
                 v = int(bool(v))
+            if k == "precond":
+                v = _PRECOND[v] if isinstance(v, str) else int(v)
             setattr(self.params, k, v)
         _check(hc_set_params(self.ctx, C.byref(self.params)), "hc_set_params")
 

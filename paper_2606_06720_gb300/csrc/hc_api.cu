@@ -270,6 +270,7 @@ int check_params(const hc_params* p) {
   if (p->precision != HC_FP64_PLAIN && p->precision != HC_FP32_REFINED &&
       p->precision != HC_FP32_REFINED_DF)
     return HC_EINVAL;
+  if (p->precond != HC_PRECOND_SCALAR && p->precond != HC_PRECOND_KBAR) return HC_EINVAL;
   if (!std::isfinite(p->c) || !std::isfinite(p->D) || !std::isfinite(p->gamma) ||
       !std::isfinite(p->dt) || p->dt < 0)
     return HC_EINVAL;
@@ -506,6 +507,7 @@ int push_config(hc_ctx* c) {
   // refined: FP32 first sweep when the warm start is off by more than 1e-5 ||S||
   cfg.first32_min2 = (c->refined && !c->prm.fp64_first_residual) ? 1e-10 : 0.0;
   cfg.mid_df = c->mid_df;
+  cfg.precond = c->prm.precond == HC_PRECOND_KBAR ? HC_PRECOND_KBAR : HC_PRECOND_SCALAR;
   cfg.dim = c->dim;
   cfg.diag = diag_on(c) ? 1 : 0;
   cfg.outer_thresh2_rel = c->prm.cg_rtol * c->prm.cg_rtol;

@@ -122,6 +122,7 @@ struct SolveState {
   int acc_first;             // FP32 first sweeps summed over the steps since the last reset
   int first_used;            // the running / last step ran an FP32 first sweep
   int mid_df;                // HC_FP32_REFINED: the residual after an FP32 first sweep is evaluated in double-float
+  int precond;               // HC_PRECOND_SCALAR | HC_PRECOND_KBAR (with no user kappa)
   int mid_phase;             // the next refinement residual is that double-float mid-step one
   int mid_used;              // the running / last step evaluated it
   int acc_mid;               // such residuals summed over the steps since the last reset
@@ -165,6 +166,7 @@ struct SolveConfig {
   double dt;
   double first32_min2;       // see SolveState
   int mid_df;                // see SolveState
+  int precond;               // see SolveState
   int maxit;
   int max_sweeps;
   int graph_mode;

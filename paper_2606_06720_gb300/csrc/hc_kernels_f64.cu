@@ -61,6 +61,7 @@ __global__ void k_set_config(SolveState* st, SolveConfig c) {
   st->dt = c.dt;
   st->first32_min2 = c.first32_min2;
   st->mid_df = c.mid_df;
+  st->precond = c.precond;
   st->dim = c.dim;
   st->diag = c.diag;
   st->outer_rtol2 = c.outer_thresh2_rel;
@@ -74,17 +75,16 @@ __global__ void k_set_config(SolveState* st, SolveConfig c) {
 }
 
 __global__ void k_step_begin(SolveState* st, int npts) {
-  // reading R3: Kbar = mean(m m^T) + mean(r) I, or the caller's kappa I;
-  // kappa = trace(Kbar) / d is reported
+  // reading R3: Kbar = kappa I with kappa = mean(r) + mean(|m|^2) / d, or
+  // the caller's kappa; option HC_PRECOND_KBAR: Kbar = mean(m m^T) + mean(r) I.
+  // kappa = trace(Kbar) / d is reported.
+  const double kiso = st->user_kappa > 0 ? st->user_kappa
+                                         : st->mean_r + st->msum / (double)npts / (double)st->dim;
+  const bool aniso = st->user_kappa <= 0 && st->precond == HC_PRECOND_KBAR;
   for (int e = 0; e < 6; ++e) {
     const bool diag = e < 3, used = st->dim == 3 || e == 0 || e == 1 || e == 3;
     double v = 0.0;
-    if (used) {
-      if (st->user_kappa > 0)
-        v = diag ? st->user_kappa : 0.0;
-      else
-        v = st->mm[e] / (double)npts + (diag ? st->mean_r : 0.0);
-    }
+    if (used) v = aniso ? st->mm[e] / (double)npts + (diag ? st->mean_r : 0.0) : (diag ? kiso : 0.0);
     st->kbar[e] = v;
   }
   st->kappa = 0.0;

@@ -187,25 +187,32 @@ def test_edge_cases_fp64(hc, case):
 @pytest.mark.parametrize("n", [(64, 32), (16, 16, 32)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
 def test_preconditioner_is_exact_for_constant_coefficients(hc, n, precision):
-    """With constant m and r the preconditioner -div(Kbar grad), Kbar =
-    mean(m m^T) + mean(r) I, is the operator itself (reading R3): the solve
-    from p = 0 takes one CG iteration (per sweep), the reported kappa is
-    trace(Kbar) / dim, and p is the oracle's solution."""
+    """With constant m and r the anisotropic option of reading R3,
+    -div(Kbar grad) with Kbar = mean(m m^T) + mean(r) I, is the operator
+    itself: the solve from p = 0 takes one CG iteration (per sweep), the
+    reported kappa is trace(Kbar) / dim, and p is the oracle's solution.  The
+    default isotropic kappa (-Laplacian) needs more iterations there."""
     dim = len(n)
     g = O.Grid(n)
     mc, r0 = np.array([0.6, -0.3, 0.2][:dim]), 0.15
     m = np.broadcast_to(mc.reshape((dim,) + (1,) * dim), (dim,) + g.shape).copy()
     r = np.full(g.shape, r0)
     S = O.project(g, np.random.default_rng(5).standard_normal(g.shape))
-    with hc.Solver(n, precision=precision, c=1.0, D=0.01, gamma=0.75, dt=1e-4,
-                   cg_rtol=1e-10, cg_maxit=50) as s:
-        s.set_r(r)
-        s.set_source(S)
-        s.set_m(m)
-        st = s.step(1)
-        p = s.get_p()
-    assert st.status == 0
+    iters = {}
+    for pc in ("scalar", "kbar"):
+        with hc.Solver(n, precision=precision, c=1.0, D=0.01, gamma=0.75, dt=1e-4,
+                       cg_rtol=1e-10, cg_maxit=50, precond=pc) as s:
+            s.set_r(r)
+            s.set_source(S)
+            s.set_m(m)
+            st = s.step(1)
+            p = s.get_p()
+        assert st.status == 0
+        iters[pc] = st
+    st = iters["kbar"]
     assert st.cg_iters <= max(1, st.refine_sweeps), st
+    assert iters["scalar"].cg_iters > st.cg_iters
+    assert iters["scalar"].kappa == pytest.approx(st.kappa, rel=1e-6)
     assert st.kappa == pytest.approx(r0 + (mc ** 2).sum() / dim, rel=1e-6)
     if precision != "fp64":  # the refined modes hold m and r in FP32 (reading R16)
         m, r = (a.astype(np.float32).astype(np.float64) for a in (m, r))

@@ -159,16 +159,19 @@ def test_pcg_constant_coefficient_converges_in_one_iteration():
 
 
 def test_pcg_constant_anisotropic_coefficient_converges_in_one_iteration():
-    """With constant m and r the default preconditioner -div(Kbar grad), Kbar =
-    mean(m m^T) + mean(r) I = K, is the operator itself: one iteration, and the
-    closed form p^ = S^ / (xi~^T K xi~) off the null modes (reading R3)."""
+    """With constant m and r the anisotropic option of reading R3,
+    -div(Kbar grad) with Kbar = mean(m m^T) + mean(r) I = K, is the operator
+    itself: one iteration, and the closed form p^ = S^ / (xi~^T K xi~) off the
+    null modes."""
     g = O.Grid((16, 32), (1.0, 2.0))
     mc, r0 = np.array([0.6, -0.3]), 0.15
     m = np.broadcast_to(mc[:, None, None], (2,) + g.shape).copy()
     r = np.full(g.shape, r0)
     S = O.project(g, RNG.standard_normal(g.shape))
-    x, st = O.pcg(g, m, r, S, rtol=1e-12, maxit=10)
+    x, st = O.pcg(g, m, r, S, rtol=1e-12, maxit=10, precond=1)
     assert st.rc == O.OK and st.cg_iters == 1
+    # the default (isotropic kappa) preconditioner is not exact here
+    assert O.pcg(g, m, r, S, rtol=1e-12, maxit=10)[1].cg_iters > 1
     n = g.n
     lx = np.arange(n[0]); ly = np.arange(n[1])
     xix = np.where(lx < n[0] // 2, 2 * np.pi * lx / 1.0, np.where(lx == n[0] // 2, 0.0, 2 * np.pi * (lx - n[0]) / 1.0))
@@ -196,16 +199,18 @@ def test_preconditioner_on_single_mode_3d():
     assert np.allclose(z, f / (xi @ K @ xi), atol=1e-12)
 
 
-def test_pcg_iterations_within_condition_bound():
+@pytest.mark.parametrize("precond", [0, 1])
+def test_pcg_iterations_within_condition_bound(precond):
     """Generalised eigenvalues of (A, -div(Kbar grad)) lie between the extreme
     pointwise eigenvalues of Kbar^-1/2 K(x) Kbar^-1/2, so the CG error bound
-    gives it <= ceil(sqrt(cond)/2 * ln(2/rtol))."""
+    gives it <= ceil(sqrt(cond)/2 * ln(2/rtol)); both preconditioners of
+    reading R3."""
     g = O.Grid((32, 32))
     m = RNG.uniform(0, 1, (2,) + g.shape)
     r = RNG.uniform(0.05, 0.15, g.shape)
     S = O.project(g, RNG.standard_normal(g.shape))
     rtol = 1e-10
-    kb = O.kbar_default(g, m, r)
+    kb = O.kbar_default(g, m, r) if precond else O.kbar_array(2, O.kappa_default(g, m, r))
     Kbar = np.array([[kb[0], kb[3]], [kb[3], kb[1]]])
     w, V = np.linalg.eigh(Kbar)
     Kih = V @ np.diag(w ** -0.5) @ V.T
@@ -215,7 +220,7 @@ def test_pcg_iterations_within_condition_bound():
     # bound on ||e||_A; relative residual picks up at most sqrt(cond(A)) more
     condA = cond * (w.max() / w.min()) * (2 * np.pi * 16) ** 2 / (2 * np.pi) ** 2
     bound = int(np.ceil(0.5 * np.sqrt(cond) * np.log(2 * np.sqrt(condA) / rtol)))
-    x, st = O.pcg(g, m, r, S, rtol=rtol, maxit=10000)
+    x, st = O.pcg(g, m, r, S, rtol=rtol, maxit=10000, precond=precond)
     assert st.rc == O.OK
     assert st.cg_iters <= bound
     assert st.true_rel_residual < 10 * rtol
