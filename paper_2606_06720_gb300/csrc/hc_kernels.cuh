@@ -523,26 +523,9 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // ------------------------------------------------------------------ row helpers
-// Element k of Z = A_full + i B_full, the spectrum of the complex row a + i b,
-// from the packed Hermitian half spectra A, B (B may be null: b = 0).
-template <typename T>
-__device__ __forceinline__ cx<T> load_pair_c2r(const cx<T>* __restrict__ A,
-                                               const cx<T>* __restrict__ B, int k, int H) {
-  if (k == 0 || k == H) {
-    cx<T> a = A[0], b = B ? B[0] : czero<T>();
-    return k == 0 ? cmk<T>(a.x, b.x) : cmk<T>(a.y, b.y);
-  }
-  if (k < H) {
-    cx<T> a = A[k], b = B ? B[k] : czero<T>();
-    return cmk<T>(a.x - b.y, a.y + b.x);  // A + i B
-  }
-  cx<T> a = A[2 * H - k], b = B ? B[2 * H - k] : czero<T>();
-  return cmk<T>(a.x + b.y, b.x - a.y);  // conj(A) + i conj(B)
-}
-
 // The canonical-order input of the complex row a + i b of each of NV rows
 // (thread j, slot s: element j + s N/8) from their packed half spectra A, B
-// (both present).  With H = 4 N/8, slots 0..3 lie below the Nyquist index and
+// (B[q] null: b = 0).  With H = 4 N/8, slots 0..3 lie below the Nyquist index and
 // slots 4..7 above it (mirrored, conjugated); only thread 0 meets the two
 // special elements 0 and H, which share the packed slot 0.
 template <int NV, typename T>
@@ -553,7 +536,7 @@ __device__ __forceinline__ void load_rows_c2r(cx<T> (&v)[NV][8], const cx<T>* co
     const int idx = s < 4 ? j + s * N8 : ((s == 4 && j == 0) ? 0 : (8 - s) * N8 - j);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      const cx<T> a = A[q][idx], b = B[q][idx];
+      const cx<T> a = A[q][idx], b = B[q] ? B[q][idx] : czero<T>();
       if (s == 0)
         v[q][s] = j == 0 ? cmk<T>(a.x, b.x) : cmk<T>(a.x - b.y, a.y + b.x);
       else if (s < 4)
@@ -642,11 +625,10 @@ __global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const
   const int y = (blockIdx.x << g.lrpc) + rb;
   cx<T>* slab = sm + rb * N;
   cx<T>* const sl[1] = {slab};
-  const cx<T>* Ar = A + (size_t)y * H;
-  const cx<T>* Br = B ? B + (size_t)y * H : nullptr;
+  const cx<T>* Ar[1] = {A + (size_t)y * H};
+  const cx<T>* Br[1] = {B ? B + (size_t)y * H : nullptr};
   cx<T> v[1][8];
-#pragma unroll
-  for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
+  load_rows_c2r<1>(v, Ar, Br, j, N8);
   fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   const size_t ro = (size_t)y * N;
   // this thread's 8 points: plain FMA sums of m_a m_b (the preconditioner's
@@ -751,8 +733,10 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
   fft_canon<+1, NV, true>(v, sl, 1, j, g.lnx, g.twx);
   cp_async_wait_all();
   __syncthreads();
-  // v = grad p (gx + i gy) at x = j + s N/8: apply (m (x) m + r I)
-  DotAcc<T> gkg;
+  // v = grad p (gx + i gy) at x = j + s N/8: apply (m (x) m + r I).  The
+  // <d, A d> partial of a thread sums nv * 8 non-negative terms: plain
+  // accumulation, FP64 across threads.
+  T gkg = (T)0;
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     const Tm* smx = sf + (size_t)(r0 + q) * N;
@@ -764,14 +748,14 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
       const T gx = v[q][s].x, gy = v[q][s].y;
       const T ax = (T)smx[x], ay = (T)smy[x], r = (T)srr[x];
       const T mg = ax * gx + ay * gy;
-      if (DOT) gkg.add_prod(mg * mg + r * (gx * gx + gy * gy), (T)1);  // one compensated add per point
+      if (DOT) gkg = gkg + (mg * mg + r * (gx * gx + gy * gy));
       v[q][s] = cmk<T>(ax * mg + r * gx, ay * mg + r * gy);
     }
   }
   fft_canon<-1, NV, true>(v, sl, 1, j, g.lnx, g.twx);
   store_rows_r2c<NV>(v, sl, j, N, H, Qa, Qb);
   if (DOT) {
-    double a1[1] = {gkg.value()}, t1[1];
+    double a1[1] = {(double)gkg}, t1[1];
     if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0)
       cg_alpha_from(st, t1[0], (double)g.nx * (double)g.ny);
   }
@@ -889,11 +873,10 @@ __global__ void __launch_bounds__(512) k_row_split(Geo<T> g, const cx<T>* Gx, co
   const int y = (blockIdx.x << g.lrpc) + rb;
   cx<T>* slab = sm + rb * N;
   cx<T>* const sl[1] = {slab};
-  const cx<T>* Ar = Gx + (size_t)y * H;
-  const cx<T>* Br = Gy + (size_t)y * H;
+  const cx<T>* Ar[1] = {Gx + (size_t)y * H};
+  const cx<T>* Br[1] = {Gy + (size_t)y * H};
   cx<T> v[1][8];
-#pragma unroll
-  for (int s = 0; s < 8; ++s) v[0][s] = load_pair_c2r(Ar, Br, j + s * N8, H);
+  load_rows_c2r<1>(v, Ar, Br, j, N8);
   fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   const size_t ro = (size_t)y * N;
   const T c2dt = (T)cf.c2dt;
@@ -1924,10 +1907,10 @@ __global__ void __launch_bounds__(512) k_row_adj_point(Geo<T> g, cx<T>* G0, cx<T
   cx<T>* slab = sm + rb * 2 * N;
   cx<T>* const sl[2] = {slab, slab + N};
   cx<T> v[2][8];
-#pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    v[0][s] = load_pair_c2r(G0 + (size_t)y * H, G1 + (size_t)y * H, j + s * N8, H);
-    v[1][s] = load_pair_c2r(L0 + (size_t)y * H, L1 + (size_t)y * H, j + s * N8, H);
+  {
+    const cx<T>* A2[2] = {G0 + (size_t)y * H, L0 + (size_t)y * H};
+    const cx<T>* B2[2] = {G1 + (size_t)y * H, L1 + (size_t)y * H};
+    load_rows_c2r<2>(v, A2, B2, j, N8);
   }
   fft_canon<+1, 2, true>(v, sl, 1, j, g.lnx, g.twx);
   const size_t ro = (size_t)y * N;
@@ -1980,10 +1963,10 @@ __global__ void __launch_bounds__(512) k_row_adj_press(Geo<T> g, const cx<T>* __
   cx<T>* slab = sm + rb * 2 * N;
   cx<T>* const sl[2] = {slab, slab + N};
   cx<T> v[2][8];
-#pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    v[0][s] = load_pair_c2r(GM0 + (size_t)y * H, GM1 + (size_t)y * H, j + s * N8, H);
-    v[1][s] = load_pair_c2r(GP0 + (size_t)y * H, GP1 + (size_t)y * H, j + s * N8, H);
+  {
+    const cx<T>* A2[2] = {GM0 + (size_t)y * H, GP0 + (size_t)y * H};
+    const cx<T>* B2[2] = {GM1 + (size_t)y * H, GP1 + (size_t)y * H};
+    load_rows_c2r<2>(v, A2, B2, j, N8);
   }
   fft_canon<+1, 2, true>(v, sl, 1, j, g.lnx, g.twx);
   const size_t ro = (size_t)y * N;

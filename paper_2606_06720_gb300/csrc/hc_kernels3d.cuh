@@ -133,13 +133,9 @@ template <typename T>
 __device__ __forceinline__ void load_rows3(cx<T> (&v)[3][8], const Tri<cx<T>*>& G,
                                            const RIdx3& r, int H) {
   const size_t o0 = r.y0 * H, o1 = r.y1 * H;
-#pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int k = r.j + s * r.N8;
-    v[0][s] = load_pair_c2r<T>(G.v[0] + o0, G.v[1] + o0, k, H);
-    v[1][s] = load_pair_c2r<T>(G.v[0] + o1, G.v[1] + o1, k, H);
-    v[2][s] = load_pair_c2r<T>(G.v[2] + o0, G.v[2] + o1, k, H);
-  }
+  const cx<T>* A3[3] = {G.v[0] + o0, G.v[0] + o1, G.v[2] + o0};
+  const cx<T>* B3[3] = {G.v[1] + o0, G.v[1] + o1, G.v[2] + o1};
+  load_rows_c2r<3>(v, A3, B3, r.j, r.N8);
 }
 
 // ------------------------------------------------------------------ z pass: gradient
