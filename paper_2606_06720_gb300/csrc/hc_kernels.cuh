@@ -720,11 +720,12 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
   {
     const size_t row0 = ((size_t)blockIdx.x << g.lrpc) * N;
     const int per = (int)(((size_t)g.rpc * N * sizeof(Tm)) >> 4);  // 16-byte chunks per field
-    for (int c = threadIdx.x; c < 3 * per; c += blockDim.x) {
-      const int q = c >= 2 * per ? 2 : (c >= per ? 1 : 0), ch = c - q * per;
-      const Tm* src = (q == 0 ? mx : (q == 1 ? my : rr)) + row0;
-      cp_async16(reinterpret_cast<char*>(sf + (size_t)q * g.rpc * N) + 16 * (size_t)ch,
-                 reinterpret_cast<const char*>(src) + 16 * (size_t)ch);
+    const Tm* const src[3] = {mx + row0, my + row0, rr + row0};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      char* dst = reinterpret_cast<char*>(sf + (size_t)q * g.rpc * N);
+      const char* from = reinterpret_cast<const char*>(src[q]);
+      for (int c = threadIdx.x; c < per; c += blockDim.x) cp_async16(dst + 16 * c, from + 16 * c);
     }
     cp_async_commit();
   }
