@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(256) k3_zgradnorm(Geo<T> g, Tri<cx<T>*> Q, Sol
 
 // ------------------------------------------------------------------ CG update, |m|^2
 template <typename T>
-__global__ void __launch_bounds__(256) k3_cg_update(Geo<T> g, cx<T>* __restrict__ x,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k3_cg_update(Geo<T> g, cx<T>* __restrict__ x,
                                                     cx<T>* __restrict__ r,
                                                     const cx<T>* __restrict__ d,
                                                     const cx<T>* __restrict__ q, SolveState* st) {
