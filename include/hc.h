@@ -121,7 +121,7 @@ typedef struct {
    *   delta_m = ||m_new - m_old||_2 / (dt ||m_old||_2) of the step. */
   double energy;
   double delta_m;
-  int energy_valid;    /* 0 when the energy of the starting m is not known (diagnostics were off when it was made) */
+  int energy_valid;    /* 0 when the energy of the starting m is not known (diagnostics were off when it was made or set) */
   int stop_reason;     /* hc_run: HC_STOP_*; hc_step: HC_STOP_NONE */
   long long energy_step; /* hc_run with HC_STOP_ENERGY: 0-based index, within the call, of the step whose result did not lower the energy; else -1 */
   int first_sweep_fp32;  /* refined modes: the step's first sweep started from the FP32 residual */
@@ -157,7 +157,9 @@ int hc_set_r(hc_ctx* ctx, const double* r, size_t count);
  * the solvability condition that the paper states as int S = 0). */
 int hc_set_source(hc_ctx* ctx, const double* S, size_t count);
 
-/* Conductivity m (count = dim*npts, component-major). */
+/* Conductivity m (count = dim*npts, component-major).  With params.diagnostics it also
+ * computes the gradient norm that the energy of this m needs; without, the first step's energy
+ * is unknown (energy_valid = 0) unless hc_run, which computes it, takes the step. */
 int hc_set_m(hc_ctx* ctx, const double* m, size_t count);
 
 /* Pressure p used as the CG initial guess of the next step (Section 2.4 uses

@@ -1458,6 +1458,18 @@ int hc_set_p(hc_ctx* c, const double* p, size_t count) {
   return HC_OK;
 }
 
+// After hc_set_m: sum |grad m|^2 of the new m, which only the energy of
+// Section 2.5 uses; without diagnostics it is marked unknown instead (hc_run
+// computes it when it turns the diagnostics on).
+static int gm2_for_new_m(hc_ctx* c) {
+  if (diag_on(c)) {
+    gradnorm_current(c);
+    return HC_OK;
+  }
+  CU(cudaMemsetAsync(&c->st->gm2_valid, 0, sizeof(int), c->stream));
+  return HC_OK;
+}
+
 int hc_set_m(hc_ctx* c, const double* m, size_t count) {
   if (!c || !m || count != (size_t)c->dim * c->n) return HC_EINVAL;
   CU(cudaMemcpyAsync(c->stage, m, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
@@ -1473,7 +1485,8 @@ int hc_set_m(hc_ctx* c, const double* m, size_t count) {
     else
       hc::msum3<double>(c->gd, mtri<double>(c), c->st, c->stream);
     c->launches += 4;
-    gradnorm_current(c);
+    int rc = gm2_for_new_m(c);
+    if (rc) return rc;
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(c->stream));
     return HC_OK;
@@ -1488,7 +1501,8 @@ int hc_set_m(hc_ctx* c, const double* m, size_t count) {
     hc::msum<double>(c->gd, (const double*)c->m[0], (const double*)c->m[1], c->st, c->stream);
   }
   c->launches += 3;
-  gradnorm_current(c);
+  int rc = gm2_for_new_m(c);
+  if (rc) return rc;
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(c->stream));
   return HC_OK;
@@ -1633,6 +1647,9 @@ int hc_run(hc_ctx* c, int max_steps, double eps, int stop_on_energy, int* steps_
   }
   int rc = push_config(c);
   if (!rc) {
+    // the energy of the current m needs its gradient norm, which nothing
+    // computed while the diagnostics were off
+    if (forced) gradnorm_current(c);
     hc::set_run(c->st, 1, eps, stop_on_energy ? 1 : 0, c->stream);
     hc::reset_accum(c->st, c->stream);
     c->launches += 2;
