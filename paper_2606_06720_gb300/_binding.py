@@ -21,6 +21,7 @@ HC_OK, HC_EINVAL, HC_ENOMEM, HC_ECUDA = 0, -1, -2, -3
 HC_ENOCONV, HC_ENONFINITE, HC_ETIMEOUT, HC_ENOTSUP = -4, -5, -6, -7
 HC_FP64_PLAIN, HC_FP32_REFINED, HC_FP32_REFINED_DF = 0, 1, 2
 HC_STOP_NONE, HC_STOP_DELTA_M, HC_STOP_ENERGY, HC_STOP_STATUS = 0, 1, 2, 3
+HC_PRECOND_SCALAR, HC_PRECOND_KBAR = 0, 1
 
 
 class HuCaiError(RuntimeError):
@@ -38,7 +39,7 @@ class hc_grid(C.Structure):
 
 # preconditioner of reading R3: "scalar" kappa (-Laplacian) (the default) or
 # "kbar", the whole mean of the coefficient tensor
-_PRECOND = {"scalar": 0, "kbar": 1}
+_PRECOND = {"scalar": HC_PRECOND_SCALAR, "kbar": HC_PRECOND_KBAR}
 
 
 class hc_params(C.Structure):

@@ -74,3 +74,33 @@ def test_invalid_params_are_rejected_on_the_host(lib):
     # null context pointers
     assert Bd.hc_step(None, 1, None) == Bd.HC_EINVAL
     assert Bd.hc_set_r(None, None, 0) == Bd.HC_EINVAL
+
+
+def test_precond_and_refinement_options_on_the_host(lib):
+    """The preconditioner option takes the two values of reading R3 only, and
+    the FP64-refined mode's workspace holds the double-float copy of S that
+    its mid-step residual reads (n/2 packed values of 16 bytes)."""
+    from paper_2606_06720_gb300 import _binding as Bd
+    n = (64, 32)
+    g = Bd.hc_grid(2, (C.c_int * 3)(n[0], n[1], 1), (C.c_double * 3)(1.0, 1.0, 1.0))
+
+    def params(**kw):
+        p = Bd.hc_params(10.0, 0.05, 0.75, 1e-3, 1e-10, 100, Bd.HC_FP32_REFINED, 0.0, 1e-4, 10, 0,
+                         None)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    nb = C.c_size_t()
+    for pc in (Bd.HC_PRECOND_SCALAR, Bd.HC_PRECOND_KBAR):
+        assert Bd.hc_workspace_size(C.byref(g), C.byref(params(precond=pc)), C.byref(nb)) == 0
+    ctx = C.c_void_p()
+    for pc in (2, -1):
+        assert Bd.hc_workspace_size(C.byref(g), C.byref(params(precond=pc)), C.byref(nb)) == Bd.HC_EINVAL
+        assert Bd.hc_create(C.byref(ctx), C.byref(g), C.byref(params(precond=pc)), None, 0) == Bd.HC_EINVAL
+    sizes = {}
+    for prec in (Bd.HC_FP32_REFINED, Bd.HC_FP32_REFINED_DF):
+        assert Bd.hc_workspace_size(C.byref(g), C.byref(params(precision=prec)), C.byref(nb)) == 0
+        sizes[prec] = nb.value
+    extra = sizes[Bd.HC_FP32_REFINED] - sizes[Bd.HC_FP32_REFINED_DF]
+    assert n[0] // 2 * n[1] * 16 <= extra <= n[0] // 2 * n[1] * 16 + 256
