@@ -363,15 +363,18 @@ __device__ __forceinline__ void fft_canon(cx<T> (&v)[NV][8], cx<T>* const* sl, i
 
 // ------------------------------------------------------------------ reductions
 // Block-reduce K doubles; thread 0 gets the block total.
-template <int K>
+// WARP_DONE: the values are already warp sums held by lane 0 (warp_sum_pair).
+template <int K, bool WARP_DONE = false>
 __device__ __forceinline__ void block_sum(double (&v)[K]) {
   __shared__ double red[32 * K];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
+  if (!WARP_DONE) {
 #pragma unroll
-  for (int k = 0; k < K; ++k)
+    for (int k = 0; k < K; ++k)
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+      for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+  }
   __syncthreads();
   if (lane == 0)
 #pragma unroll
@@ -390,11 +393,11 @@ __device__ __forceinline__ void block_sum(double (&v)[K]) {
 // Write this CTA's K partial sums; returns true (in every thread) in the CTA
 // that arrived last, which then holds the grand totals in tot (fixed order:
 // CTA 0, 1, 2, ...), and re-arms the ticket.
-template <int K>
+template <int K, bool WARP_DONE = false>
 __device__ __forceinline__ bool last_cta_sum(double (&v)[K], double* partials,
                                              unsigned int* ticket, double (&tot)[K]) {
   __shared__ unsigned int s_last;
-  block_sum<K>(v);
+  block_sum<K, WARP_DONE>(v);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) partials[blockIdx.x * kPartialStride + k] = v[k];
@@ -450,6 +453,23 @@ struct DotAcc<float> {
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
+
+// Warp sum of float pairs hi + lo into lane 0, in fixed order, each step an
+// exact TwoSum of the high parts (about 48 significant bits): on this part
+// the FP64 pipe is narrow, and this keeps the per-thread shuffle reduction of
+// FP32 kernels off it.
+__device__ __forceinline__ double warp_sum_pair(float hi, float lo) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float h2 = __shfl_down_sync(0xffffffffu, hi, off);
+    const float l2 = __shfl_down_sync(0xffffffffu, lo, off);
+    const float t = hi + h2;
+    const float bp = t - hi;
+    lo = lo + l2 + ((hi - (t - bp)) + (h2 - bp));
+    hi = t;
+  }
+  return (double)hi + (double)lo;
+}
 
 template <>
 struct DotAcc<df64> {
@@ -756,9 +776,16 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
   fft_canon<-1, NV, true>(v, sl, 1, j, g.lnx, g.twx);
   store_rows_r2c<NV>(v, sl, j, N, H, Qa, Qb);
   if (DOT) {
-    double a1[1] = {(double)gkg}, t1[1];
-    if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0)
-      cg_alpha_from(st, t1[0], (double)g.nx * (double)g.ny);
+    double t1[1];
+    bool last;
+    if constexpr (std::is_same<T, float>::value) {
+      double a1[1] = {warp_sum_pair(gkg, 0.0f)};
+      last = last_cta_sum<1, true>(a1, g.partials, &st->ticket[TK_DIV], t1);
+    } else {
+      double a1[1] = {(double)gkg};
+      last = last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1);
+    }
+    if (last && threadIdx.x == 0) cg_alpha_from(st, t1[0], (double)g.nx * (double)g.ny);
   }
 }
 
@@ -1798,10 +1825,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_cg_update(Geo<T
     for (int u = 0; u < U; ++u) upd(i + u * S, dv[u], xv[u], qv[u], rv[u]);
   }
   for (; i < total; i += S) upd(i, d[i], x[i], q[i], r[i]);
-  double acc[2] = {rr.value(), rz.value()};
   double tot[2];
-  if (last_cta_sum<2>(acc, g.partials, &st->ticket[TK_UPDATE], tot) && threadIdx.x == 0)
-    cg_step_finish(st, tot[0], tot[1]);
+  bool last;
+  if constexpr (std::is_same<T, float>::value) {
+    double acc[2] = {warp_sum_pair(rr.hi, rr.lo), warp_sum_pair(rz.hi, rz.lo)};
+    last = last_cta_sum<2, true>(acc, g.partials, &st->ticket[TK_UPDATE], tot);
+  } else {
+    double acc[2] = {rr.value(), rz.value()};
+    last = last_cta_sum<2>(acc, g.partials, &st->ticket[TK_UPDATE], tot);
+  }
+  if (last && threadIdx.x == 0) cg_step_finish(st, tot[0], tot[1]);
 }
 
 // ------------------------------------------------------------------ elementwise
