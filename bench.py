@@ -105,7 +105,7 @@ BYTES_PER_POINT_3D = {
 # workload with the current kernels (from the committed ncu summaries).
 # Set an entry to None when its kernel changes.
 NCU_TRAFFIC_2048 = {"res_grad": 104.5e6, "res_apply": 128.2e6, "res_div": 133.2e6,
-                    "cg_grad": 36.2e6, "cg_apply": 84.6e6, "cg_div": 33.6e6, "cg_update": 67.3e6,
+                    "cg_grad": 36.2e6, "cg_apply": 84.8e6, "cg_div": 33.6e6, "cg_update": 67.3e6,
                     "mid_grad": 100.9e6, "mid_apply": 130.8e6, "mid_div": 114.2e6,
                     "split_row": 67.2e6, "split_c2r": 33.7e6}
 
