@@ -253,8 +253,9 @@ enum ColDivMode { CD_PLAIN = 0, CD_CG = 1, CD_RESID = 2, CD_RESID_REFINE = 3, CD
 // Row pass, forward: physical pair (a, b) -> packed row spectra (A, B). b/B may be null.
 template <typename T>
 void row_r2c(const Geo<T>& g, const T* a, const T* b, cx<T>* A, cx<T>* B, cudaStream_t s);
-// Row pass, inverse: packed row spectra -> physical pair; optional sum(a^2+b^2) into st->msum
-// (kappa_update = 1; with st->diag also sum |new - old|^2 of a, b into st->dm2).
+// Row pass, inverse: packed row spectra -> physical pair; with kappa_update = 1 also the sums of
+// a^2, b^2, a b into st->mm and st->msum (the next preconditioner's input), and with st->diag
+// sum |new - old|^2 of a, b into st->dm2.
 template <typename T>
 void row_c2r(const Geo<T>& g, const cx<T>* A, const cx<T>* B, T* a, T* b, SolveState* st,
              int kappa_update, cudaStream_t s);
@@ -379,7 +380,7 @@ template <typename T>
 void row_split3(const Geo<T>& g, Tri<cx<T>*> G, Tri<const T*> m, const T* r, Tri<T*> mo,
                 SplitCoef cf, SolveState* st, cudaStream_t s);
 // Diffusion along y (axis 1) or z (axis 2) of physical m, from mi to mo (may
-// alias); axis 2 also sums |mo|^2 into st->msum, flags non-finite values, and
+// alias); axis 2 also sums mo_a mo_b into st->mm and st->msum, flags non-finite values, and
 // with st->diag sums |mo - mo_old|^2 into st->dm2 (mo holds m^k on entry).
 template <typename T>
 void heat_axis(const Geo<T>& g, int axis, Tri<T*> mi, Tri<T*> mo, SolveState* st, cudaStream_t s);
