@@ -301,7 +301,8 @@ def run_reference(args) -> None:
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": K, "warmup": Wm, "ms_per_step": secs / K * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(),
+        "config": workload_config({"preconditioner": "scalar kappa (-Laplacian), the oracle's "
+                                                        "default reading R3"}),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"the same workload resampled at {n}x{n}; each timed step is one "
                                    f"FP64 oracle step (warm-started, cg_rtol {CG_RTOL_REFINED})"},
