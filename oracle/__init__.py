@@ -64,7 +64,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = C.CDLL(build())
+            # HC_ORACLE_LIB names another build of hc_oracle.c: the test that
+            # plants mistakes in copies of the source loads those builds.
+            lib = C.CDLL(os.environ.get("HC_ORACLE_LIB") or build())
             dp = C.POINTER(C.c_double)
             gp = C.POINTER(_Grid)
             lib.or_set_threads.argtypes = [C.c_int]

@@ -237,6 +237,25 @@ def test_pcg_warm_start_at_solution_takes_no_iteration():
     assert np.array_equal(x2, O.project(g, x))
 
 
+def test_pcg_stopping_rule_is_relative_to_the_source():
+    """Reading R4: CG stops at ||S - A p||_2 <= rtol ||S||_2. The rule is relative, so
+    scaling S by a power of two scales every iterate exactly. The iteration count and the
+    result are then unchanged up to that factor. An absolute rule would stop the scaled
+    problems at other counts."""
+    g = O.Grid((16, 16))
+    m = RNG.uniform(0, 1, (2,) + g.shape)
+    r = np.full(g.shape, 0.1)
+    S = O.project(g, RNG.standard_normal(g.shape))
+    x, st = O.pcg(g, m, r, S, rtol=1e-10)
+    assert st.rc == 0
+    for k in (-30, 30):
+        s = 2.0 ** k
+        xs, sts = O.pcg(g, m, r, s * S, rtol=1e-10)
+        assert sts.rc == 0 and sts.cg_iters == st.cg_iters
+        assert np.array_equal(xs, s * x)
+        assert sts.rel_residual == st.rel_residual
+
+
 def test_pcg_zero_source_gives_zero_pressure():
     g = O.Grid((8, 8))
     m = RNG.uniform(0, 1, (2,) + g.shape)

@@ -1,0 +1,162 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case below plants one mistake in a copy of oracle/hc_oracle.c, the kind
+a reader might miss: a dropped term, a wrong sign, index, exponent or factor,
+a transposed operand, swapped substeps. The copy is built into its own
+library in a temporary folder, and the oracle's pin tests (tests/test_oracle_*.py)
+run against it in a subprocess through HC_ORACLE_LIB. A mistake counts as
+caught when some pin fails. The unchanged source, built the same way, must
+pass them all: that shows the harness itself is sound.
+
+Everything runs on the CPU. The mistakes live only in temporary copies."""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "hc_oracle.c")
+HDR = os.path.join(ROOT, "oracle", "hc_oracle.h")
+PIN_TESTS = sorted(
+    os.path.join("tests", f) for f in os.listdir(os.path.join(ROOT, "tests"))
+    if f.startswith("test_oracle_") and f.endswith(".py"))
+
+# (name, text in hc_oracle.c, replacement)
+MUTANTS = [
+    # transforms and Fourier variables
+    ("dft_sign", "double ang = sign * 2.0 * M_PI * (double)jk / n;",
+     "double ang = -sign * 2.0 * M_PI * (double)jk / n;"),
+    ("fft_twiddle_sign", "double ang = sign * 2.0 * M_PI * (double)k / n;",
+     "double ang = -sign * 2.0 * M_PI * (double)k / n;"),
+    ("fft_butterfly_order", "a[s + k + half] = u - v;", "a[s + k + half] = v - u;"),
+    ("xi_nyquist_negative", "return (l <= N / 2) ?", "return (l < N / 2) ?"),
+    ("xi_deriv_nyquist_kept", "if (2 * l == N) return 0.0; /* R1 */", "if (0) return 0.0;"),
+    ("gradient_sign",
+     "t[q] = I * or_xi_deriv(coord(g, q, c), g->n[c], g->L[c]) * fh[q];",
+     "t[q] = -I * or_xi_deriv(coord(g, q, c), g->n[c], g->L[c]) * fh[q];"),
+    ("gradient_wrong_length",
+     "t[q] = I * or_xi_deriv(coord(g, q, c), g->n[c], g->L[c]) * fh[q];",
+     "t[q] = I * or_xi_deriv(coord(g, q, c), g->n[c], g->L[0]) * fh[q];"),
+    # pressure operator
+    ("K_drops_r", "m[(size_t)c * npts + p] * mv + r[p] * v[(size_t)c * npts + p];",
+     "m[(size_t)c * npts + p] * mv;"),
+    ("K_transposed_rank_one", "m[(size_t)c * npts + p] * mv + r[p]",
+     "v[(size_t)c * npts + p] * mv + r[p]"),
+    ("A_divergence_sign", "Ap[q] = -creal(div[q]);", "Ap[q] = creal(div[q]);"),
+    # Not a mistake, so not listed: keeping +pi N / L at the Nyquist index of the
+    # divergence. There i xi multiplies a self-conjugate coefficient, and the real part
+    # of the inverse transform drops the result, as reading R1 states.
+    ("A_divergence_wrong_axis",
+     "div[q] += I * or_xi_deriv(coord(g, q, c), g->n[c], g->L[c]) * t[q];",
+     "div[q] += I * or_xi_deriv(coord(g, q, 0), g->n[0], g->L[0]) * t[q];"),
+    ("projection_wrong_mean", "s /= (double)npts;", "s /= (double)(npts - 1);"),
+    # preconditioner and CG
+    ("precond_symbol_index", "s += xi[a] * kbar_at(kbar, a, b) * xi[b];",
+     "s += xi[a] * kbar_at(kbar, a, a) * xi[b];"),
+    ("kbar_offdiag_square", "s += m[(size_t)pa[e] * npts + q] * m[(size_t)pb[e] * npts + q];",
+     "s += m[(size_t)pa[e] * npts + q] * m[(size_t)pa[e] * npts + q];"),
+    ("kappa_no_dim_division", "return sr / (double)npts + sm / (double)npts / (double)g->dim;",
+     "return sr / (double)npts + sm / (double)npts;"),
+    ("precond_option_swapped", "if (prm->kappa > 0 || prm->precond != 1) {",
+     "if (prm->kappa > 0 || prm->precond == 1) {"),
+    ("cg_no_initial_projection",
+     "or_project(g, x); /* initial guess into the complement of the null space (R2) */", ""),
+    ("cg_absolute_stop", "while (rnorm > rtol * bnorm && it < maxit) {",
+     "while (rnorm > rtol && it < maxit) {"),
+    ("cg_beta_inverted", "double beta = rho_new / rho;", "double beta = rho / rho_new;"),
+    ("cg_alpha_wrong_denominator", "double alpha = rho / dot(n, d, q);",
+     "double alpha = rho / dot(n, d, d);"),
+    # splitting substeps
+    ("activation_exponent_sign", "double e = exp(c * c * g2 * dt);", "double e = exp(-c * c * g2 * dt);"),
+    ("activation_gperp_sign", "double gperp[2] = {-g[1], g[0]};", "double gperp[2] = {g[1], g[0]};"),
+    ("activation_3d_drops_projection",
+     "out[a] = mm[a] - g[a] * gm / g2 + g[a] * gm * e / g2;",
+     "out[a] = mm[a] + g[a] * gm * e / g2;"),
+    ("relaxation_exponent", "pow(b, 1.0 / (2.0 * (1.0 - gamma)))", "pow(b, 1.0 / (1.0 - gamma))"),
+    ("relaxation_dt_factor", "- 2.0 * (1.0 - gamma) * dt;", "- (1.0 - gamma) * dt;"),
+    ("relaxation_no_indicator", "double scale = (b >= 0) ?", "double scale = (1) ?"),
+    ("relaxation_gamma_one_sign", "*= exp(-dt);\n      continue;", "*= exp(dt);\n      continue;"),
+    ("diffusion_D_not_squared", "t[q] *= exp(-D * D * s * dt);", "t[q] *= exp(-D * s * dt);"),
+    ("diffusion_drops_nyquist", "double x = or_xi(coord(g, q, a), g->n[a], g->L[a]);",
+     "double x = or_xi_deriv(coord(g, q, a), g->n[a], g->L[a]);"),
+    # Algorithm 1's order
+    ("step_relaxation_before_activation",
+     "or_activation(dim, npts, m, grad, prm->c, prm->dt);\n    or_relaxation(dim, npts, m, prm->gamma, prm->dt);",
+     "or_relaxation(dim, npts, m, prm->gamma, prm->dt);\n    or_activation(dim, npts, m, grad, prm->c, prm->dt);"),
+    ("step_gradient_of_source", "  if (!rc) rc = or_gradient(g, p, grad);\n  if (!rc) {",
+     "  if (!rc) rc = or_gradient(g, b, grad);\n  if (!rc) {"),
+    ("step_no_source_projection",
+     "or_project(g, b); /* solvability: S orthogonal to the null space (R2) */", ""),
+    # energy
+    ("energy_one_derivative_direction", "q < (size_t)dim * npts; ++q) e_diff", "q < npts; ++q) e_diff"),
+    ("energy_flow_term_factor", "0.5 * c2 * e_r +", "c2 * e_r +"),
+    ("energy_gamma_power", "e_rel += pow(m2, prm->gamma);", "e_rel += pow(m2, 2.0 * prm->gamma);"),
+    # adjoint. Not listed, because they change nothing: dropping the projection of
+    # lambda_p, a spectral divergence with no null-mode content; and dropping the final
+    # projection of dL/dS, a sum of adjoint pressures that CG keeps in the complement.
+    ("adjoint_relax_gamma_one", "if (gamma == 1.0) { *c1 = exp(-dt);", "if (gamma == 1.0) { *c1 = 1.0;"),
+    ("adjoint_pressure_of_wrong_step", "const double* p = ps + n * (k + 1); /* solved with m^k */",
+     "const double* p = ps + n * k;"),
+    ("adjoint_divergence_sign", "lp[q] -= creal(ct[q]);", "lp[q] += creal(ct[q]);"),
+    ("adjoint_dr_sign", "dr[q] -= gm[0] * gp[0]", "dr[q] += gm[0] * gp[0]"),
+    ("adjoint_drops_dphi_term", " + 2.0 * c2 * dtt * dph * mg * gl * gv[c]);", ");"),
+    ("adjoint_dphi1_series", "s += term / (k + 2);", "s += term / (k + 1);"),
+    ("adjoint_dD2_missing_dt", "ct[q] *= -s2 * dtt * exp(-D2 * s2 * dtt);",
+     "ct[q] *= -s2 * exp(-D2 * s2 * dtt);"),
+    ("adjoint_relax_jacobian", "* pow(rho, e - 1.0); /* df/drho */", "* pow(rho, e); /* df/drho */"),
+    ("adjoint_drops_symmetric_m_term", "-= gm[c] * mgp + gp[c] * mgm;", "-= gm[c] * mgp;"),
+]
+
+CONTROL = ("unchanged_source", None, None)
+
+
+def _build_and_run(base, source, case):
+    name, old, new = case
+    d = os.path.join(base, name)
+    os.makedirs(d)
+    shutil.copy(HDR, d)
+    text = source if old is None else source.replace(old, new)
+    with open(os.path.join(d, "hc_oracle.c"), "w") as f:
+        f.write(text)
+    lib = os.path.join(d, "libhc_oracle.so")
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                    "-fPIC", "-shared", "-o", lib, "hc_oracle.c", "-lm"], check=True, cwd=d)
+    env = dict(os.environ, HC_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu",
+                        "-p", "no:cacheprovider", *PIN_TESTS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return name, r.returncode, r.stdout[-3000:] + r.stderr[-1000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    base = str(tmp_path_factory.mktemp("oracle_mutants"))
+    with open(SRC) as f:
+        source = f.read()
+    for name, old, _ in MUTANTS:
+        assert source.count(old) == 1, f"{name}: the planted text must occur exactly once"
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        done = list(ex.map(lambda c: _build_and_run(base, source, c), [CONTROL] + MUTANTS))
+    return {name: (rc, out) for name, rc, out in done}
+
+
+def test_harness_control_passes(outcomes):
+    rc, out = outcomes[CONTROL[0]]
+    assert rc == 0, out
+
+
+def test_mutant_names_unique():
+    names = [m[0] for m in MUTANTS]
+    assert len(names) == len(set(names))
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_pins_catch_mutant(outcomes, name):
+    rc, out = outcomes[name]
+    # 1: some pin failed.  0 would mean the mistake went unnoticed; any other
+    # code means the copy crashed or pytest could not run, which proves nothing.
+    assert rc == 1, f"{name}: pins exit code {rc}\n{out}"
