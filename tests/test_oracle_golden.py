@@ -16,83 +16,12 @@ The expected numbers were computed by hand, not by a program, so they
 are independent of the oracle's code. Trigonometric fields are evaluated on
 the grid nodes x_i = i L / N."""
 import math
-import os
-import re
 
 import numpy as np
 import pytest
 
 import oracle as O
-
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.txt")
-
-
-def _factor(tok: str) -> float:
-    neg = tok.startswith("-")
-    t = tok[1:] if neg else tok
-    if t == "pi":
-        v = math.pi
-    elif (mt := re.fullmatch(r"ln\(([0-9.]+)\)", t)):
-        v = math.log(float(mt.group(1)))
-    elif (mt := re.fullmatch(r"sqrt\(([0-9.]+)\)", t)):
-        v = math.sqrt(float(mt.group(1)))
-    else:
-        v = float(t)
-    return -v if neg else v
-
-
-def num(tok: str) -> float:
-    parts = re.split(r"([*/])", tok.strip())
-    v = _factor(parts[0])
-    for op, f in zip(parts[1::2], parts[2::2]):
-        v = v * _factor(f) if op == "*" else v / _factor(f)
-    return v
-
-
-def vec(tok: str) -> np.ndarray:
-    return np.array([num(t) for t in tok.split(",")])
-
-
-def coords(n, L):
-    """Node coordinates, one array per axis, in the oracle's (.., y, x) layout."""
-    axes = [np.arange(N) * (Lx / N) for N, Lx in zip(n, L)]
-    grids = np.meshgrid(*axes[::-1], indexing="ij")
-    return grids[::-1]
-
-
-def field(spec: str, n, L) -> np.ndarray:
-    X = coords(n, L)
-    out = np.zeros(X[0].shape)
-    for term in spec.split(","):
-        if ":" not in term:
-            out += num(term)
-            continue
-        amp, trig, *k = term.split(":")
-        assert trig in ("cos", "sin") and len(k) == len(n)
-        arg = sum(2 * math.pi * int(ka) * Xa / La for ka, Xa, La in zip(k, X, L))
-        out += num(amp) * (np.cos(arg) if trig == "cos" else np.sin(arg))
-    return out
-
-
-def load_cases():
-    cases = []
-    with open(GOLDEN) as f:
-        for lineno, line in enumerate(f, 1):
-            line = line.strip()
-            if not line or line.startswith("#"):
-                continue
-            kind, *kv = [s.strip() for s in line.split(";")]
-            d = dict(s.split("=", 1) for s in kv)
-            assert "cite" in d, f"line {lineno} cites no passage"
-            cases.append(pytest.param(kind, d, id=f"{kind}-line{lineno}"))
-    return cases
-
-
-CASES = load_cases()
-
-
-def of_kind(kind):
-    return [c for c in CASES if c.values[0] == kind]
+from golden_cases import CASES, field, num, of_kind, vec
 
 
 def grid_of(d):
@@ -181,8 +110,11 @@ def test_energy(kind, d):
     g, n, L = grid_of(d)
     m = np.stack([field(d[f"m{a}"], n, L) for a in range(len(n))])
     prm = O.Params(c=num(d["c"]), D=num(d["D"]), gamma=num(d["gamma"]), dt=1e-3)
-    E = O.energy(g, prm, field(d["r"], n, L), m, field(d["p"], n, L))
+    r, p = field(d["r"], n, L), field(d["p"], n, L)
+    E = O.energy(g, prm, r, m, p)
     assert E == pytest.approx(num(d["E"]), rel=1e-12)
+    if "S" in d:  # the fixture's p is the pressure of its S
+        assert np.allclose(O.apply_A(g, m, r, p), field(d["S"], n, L), rtol=0, atol=1e-12)
 
 
 def test_number_and_field_grammar():
