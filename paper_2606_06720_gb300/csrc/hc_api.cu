@@ -1925,12 +1925,6 @@ int solve_only(hc_ctx* c) {
   return HC_OK;
 }
 
-template <typename T>
-int copy_m(hc_ctx* c, T* dst, const T* src) {
-  CU(cudaMemcpyAsync(dst, src, sizeof(T) * c->n, cudaMemcpyDeviceToDevice, c->stream));
-  return HC_OK;
-}
-
 // A state is (m, p, the sums of m): restoring the exact sums keeps the
 // preconditioner, hence every CG iterate of a recomputed step, identical to
 // the original forward.
