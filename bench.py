@@ -199,10 +199,14 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_id: str):
+    def __init__(self, gpu_id: str, path: str = None):
+        """path: where the raw samples go (kept); default a temporary file."""
         self.gpu_id = gpu_id
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        if path is None:
+            import tempfile
+            path = os.path.join(tempfile.gettempdir(), f"hc_bench_clocks_{os.getpid()}.csv")
+        self.path = path
 
     def __enter__(self):
         try:
@@ -522,7 +526,7 @@ def run_gb300(args) -> None:
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     launches0 = s.launch_count()
-    with ClockSampler(gpu_id) as clk:
+    with ClockSampler(gpu_id, args.clocks_csv) as clk:
         barrier()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed")
@@ -878,6 +882,8 @@ def main() -> None:
                     help="host-driven CG loop instead of graphs (ncu cannot profile kernel "
                          "nodes of graphs with conditional nodes)")
     ap.add_argument("--accuracy", action="store_true", help="equal-accuracy calibration")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="keep the raw nvidia-smi samples of the timed region in this file")
     ap.add_argument("--acc-steps", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
