@@ -48,6 +48,7 @@ extern "C" {
 #define HC_ENONFINITE (-5) /* NaN/Inf in p or m, e.g. the activation exponential overflowed (Remark 2.1) */
 #define HC_ETIMEOUT (-6)   /* a bounded device-side wait gave up */
 #define HC_ENOTSUP (-7)    /* valid request that this build does not implement */
+#define HC_EBOUNDS (-8)    /* bounds-checked build: a guard zone after a device buffer was written */
 
 /* Why hc_run stopped (Algorithm 1's loop, Section 2.5). */
 #define HC_STOP_NONE 0      /* max_steps reached */
@@ -351,6 +352,33 @@ void hc_batch_destroy(hc_batch* batch);
  * the array's device address and raises the kernels' shared-memory limit):
  * make that first call before any stream capture. */
 int hc_spectrum_noalloc(const double* f, double* out, int nx, int ny, void* stream);
+
+/* --- Bounds-checked build (no counterpart in the paper) ---
+ *
+ * The library also builds as libhc_gb300_check.so, compiled with HC_CHECK=1.
+ * Its kernels are the production kernels. Every device buffer carved from a
+ * workspace (the context's, and the adjoint's) is followed by a guard zone of
+ * HC_REDZONE_BYTES bytes plus the alignment gap before the next buffer, filled
+ * with the byte 0xA5 when the workspace is set up. A kernel or copy that writes
+ * past the end of a buffer by up to that much changes the zone. The checked
+ * build stands in for a memory checker on machines where none may run.
+ *
+ * hc_check_redzones scans every guard zone of ctx: one kernel on the context's
+ * stream, then a synchronisation. It returns HC_EBOUNDS if any byte changed,
+ * with *zone = the first damaged zone in carve order and *owner_bytes = the size
+ * of the buffer that zone follows; otherwise HC_OK with *zone = -1. *nzones gets
+ * the number of zones checked (0 in the production build, where the call does
+ * nothing and returns HC_OK). Any output pointer may be null. Scans from
+ * several threads are serialised inside the library. hc_adjoint scans its own
+ * workspace's zones before it returns, and reports damage as HC_EBOUNDS.
+ *
+ * hc_check_poke is a test hook of the checked build. It overwrites one byte of
+ * zone `zone` with a host-issued cudaMemsetAsync (no kernel, inside the
+ * workspace), so a test can see the scan report it. It returns HC_EINVAL for a
+ * zone out of range, and HC_ENOTSUP in the production build. */
+#define HC_REDZONE_BYTES 65536
+int hc_check_redzones(hc_ctx* ctx, int* nzones, int* zone, size_t* owner_bytes);
+int hc_check_poke(hc_ctx* ctx, int zone);
 
 void hc_destroy(hc_ctx* ctx);
 const char* hc_strerror(int code);

@@ -15,10 +15,13 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-_LIBNAME = os.path.join(HERE, "libhc_gb300.so")
+# HC_GB300_CHECK=1 in the environment loads the bounds-checked build instead
+# (same kernels; guard zones after every workspace buffer, see hc_check_redzones).
+CHECKED = os.environ.get("HC_GB300_CHECK", "0") == "1"
+_LIBNAME = os.path.join(HERE, "libhc_gb300_check.so" if CHECKED else "libhc_gb300.so")
 
 HC_OK, HC_EINVAL, HC_ENOMEM, HC_ECUDA = 0, -1, -2, -3
-HC_ENOCONV, HC_ENONFINITE, HC_ETIMEOUT, HC_ENOTSUP = -4, -5, -6, -7
+HC_ENOCONV, HC_ENONFINITE, HC_ETIMEOUT, HC_ENOTSUP, HC_EBOUNDS = -4, -5, -6, -7, -8
 HC_FP64_PLAIN, HC_FP32_REFINED, HC_FP32_REFINED_DF = 0, 1, 2
 HC_STOP_NONE, HC_STOP_DELTA_M, HC_STOP_ENERGY, HC_STOP_STATUS = 0, 1, 2, 3
 HC_PRECOND_SCALAR, HC_PRECOND_KBAR = 0, 1
@@ -108,6 +111,9 @@ def _load() -> C.CDLL:
         "hc_batch_create": ([C.POINTER(P), C.POINTER(P), C.c_int, P], C.c_int),
         "hc_batch_step": ([P, C.c_int, C.POINTER(hc_step_stats)], C.c_int),
         "hc_batch_destroy": ([P], None),
+        "hc_check_redzones": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)],
+                              C.c_int),
+        "hc_check_poke": ([P, C.c_int], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -145,6 +151,8 @@ hc_adjoint = lib.hc_adjoint
 hc_batch_create = lib.hc_batch_create
 hc_batch_step = lib.hc_batch_step
 hc_batch_destroy = lib.hc_batch_destroy
+hc_check_redzones = lib.hc_check_redzones
+hc_check_poke = lib.hc_check_poke
 
 # kernel ids of hc_time_kernel (include/hc.h)
 KERNELS = ["cg_grad", "cg_apply", "cg_div", "cg_update", "res_grad", "res_apply", "res_div",
@@ -408,6 +416,13 @@ class Solver:
         _check(rc, "hc_adjoint", ok=allow)
         del ws
         return {"dc2": dc2.value, "dD2": dD2.value, "dr": dr, "dS": dS, "dm0": dm0, "rc": rc}
+
+    def check_redzones(self) -> dict:
+        """Guard-zone scan of the bounds-checked build (hc_check_redzones):
+        {"rc", "zones", "zone", "owner_bytes"}; zones = 0 in the product build."""
+        nz, zone, owner = C.c_int(), C.c_int(), C.c_size_t()
+        rc = hc_check_redzones(self.ctx, C.byref(nz), C.byref(zone), C.byref(owner))
+        return {"rc": rc, "zones": nz.value, "zone": zone.value, "owner_bytes": owner.value}
 
     def launch_count(self) -> int:
         v = C.c_longlong()

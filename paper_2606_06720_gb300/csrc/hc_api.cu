@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -30,14 +31,48 @@ constexpr size_t kAlign = 256;
 constexpr int kChunk = 4;  // CG iterations launched between host polls (host-loop mode)
 constexpr int kRunChunk = 16;  // gated step launches between host polls (hc_run, graph mode)
 
+#ifndef HC_CHECK
+#define HC_CHECK 0
+#endif
+
+// Bounds-checked build (HC_CHECK=1): each buffer carved from a workspace is
+// followed by a guard zone (the alignment gap plus kRedzone bytes) holding
+// kPattern.  The production build carves no zones.
+constexpr size_t kRedzone = HC_CHECK ? (size_t)HC_REDZONE_BYTES : 0;
+constexpr int kMaxZones = 128;
+constexpr unsigned char kPattern = 0xA5;
+
+// Guard zones of one workspace, in carve order.
+struct Zones {
+  int n = 0;        // zones recorded (at most kMaxZones)
+  int carved = 0;   // zones carved; more than n means the table overflowed
+  size_t start[kMaxZones];  // byte offset from the workspace base
+  size_t len[kMaxZones];
+  size_t owner[kMaxZones];  // bytes of the buffer the zone follows
+};
+
 struct Layout {
   size_t off = 0;
   char* base = nullptr;
+  Zones* zones = nullptr;
   template <typename P>
   P* take(size_t bytes) {
     off = (off + kAlign - 1) / kAlign * kAlign;
     P* p = base ? reinterpret_cast<P*>(base + off) : nullptr;
     off += bytes;
+    if (kRedzone) {
+      const size_t end = (off + kAlign - 1) / kAlign * kAlign + kRedzone;
+      if (zones) {
+        if (zones->n < kMaxZones) {
+          zones->start[zones->n] = off;
+          zones->len[zones->n] = end - off;
+          zones->owner[zones->n] = bytes;
+          ++zones->n;
+        }
+        ++zones->carved;
+      }
+      off = end;
+    }
     return p;
   }
 };
@@ -61,6 +96,7 @@ struct Handles {
 struct hc_ctx {
   hc_grid grid;
   hc_params prm;
+  Zones zones;  // guard zones of the workspace (bounds-checked build only)
   int dim;   // 2 or 3
   int nx, ny, nz, H;  // nz = 1 in 2D
   size_t n;  // points
@@ -372,6 +408,71 @@ int cuda_fail(cudaError_t e, const char* call, int line) {
     cudaError_t e_ = (x);                                       \
     if (e_ != cudaSuccess) return cuda_fail(e_, #x, __LINE__);  \
   } while (0)
+
+// ------------------------------------------------------------------ guard zones
+#if HC_CHECK
+__device__ unsigned int g_zone_bad[kMaxZones];  // damaged bytes per zone of one scan
+
+struct ZoneScan {
+  const unsigned char* base;
+  int n;
+  unsigned long long start[kMaxZones];
+  unsigned int len[kMaxZones];
+};
+
+// One CTA per zone counts the bytes that no longer hold the pattern.
+__global__ void __launch_bounds__(256) k_redzone_scan(ZoneScan z) {
+  const int k = blockIdx.x;
+  if (k >= z.n) return;
+  const unsigned char* p = z.base + z.start[k];
+  unsigned int bad = 0;
+  for (unsigned int i = threadIdx.x; i < z.len[k]; i += blockDim.x) bad += p[i] != kPattern;
+  if (bad) atomicAdd(&g_zone_bad[k], bad);
+}
+
+std::mutex g_zone_mu;  // g_zone_bad serves one scan at a time
+#endif
+
+// Writes the pattern into every zone of a workspace (nothing without zones).
+int fill_zones(cudaStream_t s, char* base, const Zones& z) {
+  for (int k = 0; k < z.n; ++k) CU(cudaMemsetAsync(base + z.start[k], kPattern, z.len[k], s));
+  return HC_OK;
+}
+
+// Scans the zones of a workspace on stream s and waits for the result:
+// HC_EBOUNDS with *bad = the first damaged zone, else HC_OK with *bad = -1.
+int scan_zones(cudaStream_t s, const char* base, const Zones& z, int* bad) {
+  *bad = -1;
+#if HC_CHECK
+  if (z.n == 0) return HC_OK;
+  std::lock_guard<std::mutex> lock(g_zone_mu);
+  void* dbad = nullptr;
+  CU(cudaGetSymbolAddress(&dbad, g_zone_bad));
+  CU(cudaMemsetAsync(dbad, 0, sizeof(unsigned int) * z.n, s));
+  ZoneScan zs;
+  zs.base = reinterpret_cast<const unsigned char*>(base);
+  zs.n = z.n;
+  for (int k = 0; k < z.n; ++k) {
+    zs.start[k] = z.start[k];
+    zs.len[k] = (unsigned int)z.len[k];
+  }
+  k_redzone_scan<<<z.n, 256, 0, s>>>(zs);
+  CU(cudaGetLastError());
+  unsigned int hbad[kMaxZones];
+  CU(cudaMemcpyAsync(hbad, dbad, sizeof(unsigned int) * z.n, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  for (int k = 0; k < z.n; ++k)
+    if (hbad[k]) {
+      *bad = k;
+      return HC_EBOUNDS;
+    }
+#else
+  (void)s;
+  (void)base;
+  (void)z;
+#endif
+  return HC_OK;
+}
 
 int upload_tables(hc_ctx* c) {
   std::vector<double> re, im;
@@ -1215,6 +1316,7 @@ const char* hc_strerror(int code) {
     case HC_ENONFINITE: return "non-finite value in p or m";
     case HC_ETIMEOUT: return "bounded wait gave up";
     case HC_ENOTSUP: return "not supported by this build";
+    case HC_EBOUNDS: return "a guard zone after a device buffer was overwritten (bounds-checked build)";
     default: return "unknown error";
   }
 }
@@ -1286,6 +1388,7 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   }
   Layout L;
   L.base = static_cast<char*>(c->ws);
+  L.zones = &c->zones;
   layout(c, L);
   fill_geo<float>(c, c->gf, c->twx_f, c->twy_f, c->kxd_f, c->kyd_f, c->hx_f, c->hy_f);
   fill_geo<double>(c, c->gd, c->twx_d, c->twy_d, c->kxd_d, c->kyd_d, c->hx_d, c->hy_d);
@@ -1311,6 +1414,7 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   }
   int rc = HC_OK;
   if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess) rc = HC_ECUDA;
+  if (!rc) rc = fill_zones(c->stream, static_cast<char*>(c->ws), c->zones);
   if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HC_ECUDA;
   if (!rc) rc = upload_tables(c);
   if (!rc) rc = upload_heat(c);
@@ -1326,6 +1430,29 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
     return rc;
   }
   *out = c;
+  return HC_OK;
+}
+
+int hc_check_redzones(hc_ctx* c, int* nzones, int* zone, size_t* owner_bytes) {
+  if (nzones) *nzones = 0;
+  if (zone) *zone = -1;
+  if (owner_bytes) *owner_bytes = 0;
+  if (!c) return HC_EINVAL;
+  if (nzones) *nzones = c->zones.n;
+  if (c->zones.carved > c->zones.n) return HC_ENOTSUP;  // more buffers than the zone table holds
+  int bad = -1;
+  const int rc = scan_zones(c->stream, static_cast<const char*>(c->ws), c->zones, &bad);
+  if (zone) *zone = bad;
+  if (bad >= 0 && owner_bytes) *owner_bytes = c->zones.owner[bad];
+  return rc;
+}
+
+int hc_check_poke(hc_ctx* c, int zone) {
+  if (!kRedzone) return HC_ENOTSUP;
+  if (!c || zone < 0 || zone >= c->zones.n) return HC_EINVAL;
+  char* at = static_cast<char*>(c->ws) + c->zones.start[zone] + c->zones.len[zone] / 2;
+  CU(cudaMemsetAsync(at, 0, 1, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
   return HC_OK;
 }
 
@@ -1877,9 +2004,11 @@ static_assert(offsetof(hc::SolveState, mm) == offsetof(hc::SolveState, msum) + s
               "the sums of m must be contiguous");
 
 template <typename T>
-void adj_layout(const hc_ctx* c, int nsteps, int every, char* base, AdjLayout<T>& a) {
+void adj_layout(const hc_ctx* c, int nsteps, int every, char* base, AdjLayout<T>& a,
+                Zones* zones = nullptr) {
   Layout L;
   L.base = base;
+  L.zones = zones;
   const size_t n = c->n, ns = (size_t)c->ny * c->H;
   const size_t ncp = nsteps > 0 ? (size_t)((nsteps + every - 1) / every) : 1;
   const size_t seg = (size_t)std::min(every, std::max(nsteps, 1));
@@ -2118,10 +2247,28 @@ int hc_adjoint(hc_ctx* c, int nsteps, int every, const double* lamT, double* dc2
     if (cudaMalloc(&ws, need) != cudaSuccess) return HC_ENOMEM;
     own = true;
   }
-  if (c->refined)
-    rc = adjoint_t<float>(c, c->gf, nsteps, every, lamT, dc2, dD2, dr, dS, dm0, (char*)ws);
-  else
-    rc = adjoint_t<double>(c, c->gd, nsteps, every, lamT, dc2, dD2, dr, dS, dm0, (char*)ws);
+  Zones zones;  // the adjoint workspace's guard zones (bounds-checked build)
+  if (kRedzone) {
+    if (c->refined) {
+      AdjLayout<float> t;
+      adj_layout<float>(c, nsteps, every, (char*)ws, t, &zones);
+    } else {
+      AdjLayout<double> t;
+      adj_layout<double>(c, nsteps, every, (char*)ws, t, &zones);
+    }
+    rc = fill_zones(c->stream, (char*)ws, zones);
+  }
+  if (!rc) {
+    if (c->refined)
+      rc = adjoint_t<float>(c, c->gf, nsteps, every, lamT, dc2, dD2, dr, dS, dm0, (char*)ws);
+    else
+      rc = adjoint_t<double>(c, c->gd, nsteps, every, lamT, dc2, dD2, dr, dS, dm0, (char*)ws);
+  }
+  if (kRedzone && rc != HC_ECUDA) {
+    int bad = -1;
+    const int zrc = scan_zones(c->stream, (const char*)ws, zones, &bad);
+    if (zrc == HC_EBOUNDS || (zrc && !rc)) rc = zrc;
+  }
   if (own) {
     cudaStreamSynchronize(c->stream);
     cudaFree(ws);

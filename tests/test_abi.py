@@ -104,3 +104,63 @@ def test_precond_and_refinement_options_on_the_host(lib):
         sizes[prec] = nb.value
     extra = sizes[Bd.HC_FP32_REFINED] - sizes[Bd.HC_FP32_REFINED_DF]
     assert n[0] // 2 * n[1] * 16 <= extra <= n[0] // 2 * n[1] * 16 + 256
+
+
+# --- the bounds-checked build (libhc_gb300_check.so, HC_CHECK=1) -------------------------------
+
+@pytest.fixture(scope="module")
+def lib_check(lib):
+    import __graft_entry__
+    return C.CDLL(__graft_entry__._builder().LIB_CHECK)
+
+
+def test_checked_library_exports_every_declared_symbol(lib_check):
+    missing = [n for n in declared_functions() if not hasattr(lib_check, n)]
+    assert not missing, missing
+
+
+def _workspace_bytes(l, n, precision):
+    from paper_2606_06720_gb300 import _binding as Bd
+    l.hc_workspace_size.argtypes = [C.POINTER(Bd.hc_grid), C.POINTER(Bd.hc_params),
+                                    C.POINTER(C.c_size_t)]
+    g = Bd.hc_grid(len(n), (C.c_int * 3)(*(tuple(n) + (1,) * (3 - len(n)))),
+                   (C.c_double * 3)(1.0, 1.0, 1.0))
+    p = Bd.hc_params(10.0, 0.05, 0.75, 1e-3, 1e-10, 100, precision, 0.0, 1e-4, 10, 0, None)
+    nb = C.c_size_t()
+    assert l.hc_workspace_size(C.byref(g), C.byref(p), C.byref(nb)) == 0
+    return nb.value
+
+
+@pytest.mark.parametrize("n", [(64, 32), (16, 16, 16)])
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_checked_workspace_carries_a_guard_zone_per_buffer(lib, lib_check, n, precision):
+    """Every buffer of the checked build is followed by HC_REDZONE_BYTES of
+    guard zone: the workspace grows by at least that much per buffer (the
+    context carves more than 30 buffers)."""
+    extra = _workspace_bytes(lib_check, n, precision) - _workspace_bytes(lib, n, precision)
+    assert extra >= 30 * 65536
+    assert extra % 256 == 0
+
+
+def test_check_entry_points_without_a_context(lib, lib_check):
+    for l in (lib, lib_check):
+        l.hc_check_redzones.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_size_t)]
+        l.hc_check_poke.argtypes = [C.c_void_p, C.c_int]
+        nz, zone, owner = C.c_int(7), C.c_int(7), C.c_size_t(7)
+        assert l.hc_check_redzones(None, C.byref(nz), C.byref(zone), C.byref(owner)) == -1
+        assert (nz.value, zone.value, owner.value) == (0, -1, 0)
+        assert l.hc_check_redzones(None, None, None, None) == -1
+    assert lib.hc_check_poke(None, 0) == -7        # HC_ENOTSUP: the product build has no zones
+    assert lib_check.hc_check_poke(None, 0) == -1  # HC_EINVAL: no context
+
+
+def test_hc_check_changes_only_the_host_orchestration():
+    """The checked library links the product's kernel objects and recompiles
+    only hc_api.cu. That holds while no other translation unit, and no header
+    they include, tests HC_CHECK."""
+    csrc = os.path.join(ROOT, "paper_2606_06720_gb300", "csrc")
+    users = [f for f in sorted(os.listdir(csrc)) if "HC_CHECK" in open(os.path.join(csrc, f)).read()]
+    assert users == ["hc_api.cu"]
+    header = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "hc.h")).read(), flags=re.S)
+    assert "HC_CHECK" not in header
