@@ -139,6 +139,39 @@ def test_dense_8x8_symmetric_psd_nullspace_and_solve():
     assert np.abs(x_cg.ravel() - x_ls).max() < 1e-9 * np.abs(x_ls).max()
 
 
+@pytest.mark.parametrize("n", [(9, 4), (5, 7)])
+def test_projection_on_odd_grids_is_the_projector_onto_the_range(n):
+    """An odd axis has no Nyquist index, so its alternating mode is not a
+    null mode. The operator's null space, from the SVD of its dense
+    assembly, is then the constants plus the Nyquist modes of the even axes.
+    project() must be the orthogonal projector onto its complement."""
+    g = O.Grid(n, (1.0, 0.7))
+    m = RNG.uniform(0, 1, (2,) + g.shape)
+    r = RNG.uniform(0.05, 0.2, g.shape)
+    A = assemble(g, m, r)
+    U, sv, _ = np.linalg.svd(A)
+    null = U[:, sv < 1e-9 * sv.max()]
+    assert null.shape[1] == (2 if (n[0] % 2 == 0 or n[1] % 2 == 0) else 1)
+    f = RNG.standard_normal(g.shape).ravel()
+    want = f - null @ (null.T @ f)
+    assert np.allclose(O.project(g, f.reshape(g.shape)).ravel(), want, atol=1e-12)
+
+
+def test_pcg_reports_the_residual_it_reached():
+    """The reported relative residual is ||S - A x||_2 / ||S||_2 of the
+    returned x, recomputed here with numpy's norm (reading R4)."""
+    g = O.Grid((16, 8), (1.0, 0.5))
+    m = RNG.uniform(0, 1, (2,) + g.shape)
+    r = RNG.uniform(0.05, 0.2, g.shape)
+    S = O.project(g, RNG.standard_normal(g.shape))
+    for rtol in (1e-3, 1e-9):
+        x, st = O.pcg(g, m, r, S, rtol=rtol)
+        res = np.linalg.norm(S - O.apply_A(g, m, r, x)) / np.linalg.norm(S)
+        assert st.true_rel_residual == pytest.approx(res, rel=1e-6, abs=1e-15)
+        assert st.rel_residual == pytest.approx(res, rel=1e-3)   # recurrence vs recomputed
+        assert res <= rtol * 1.01
+
+
 def test_pcg_constant_coefficient_converges_in_one_iteration():
     g = O.Grid((16, 32), (1.0, 2.0))
     r0 = 0.2

@@ -53,9 +53,23 @@ MUTANTS = [
      "div[q] += I * or_xi_deriv(coord(g, q, c), g->n[c], g->L[c]) * t[q];",
      "div[q] += I * or_xi_deriv(coord(g, q, 0), g->n[0], g->L[0]) * t[q];"),
     ("projection_wrong_mean", "s /= (double)npts;", "s /= (double)(npts - 1);"),
+    ("projection_odd_axes_have_nyquist", "if (((e >> a) & 1) && (g->n[a] % 2)) ok = 0;",
+     "if (0) ok = 0;"),
+    ("projection_parity_of_one_axis",
+     "        if ((e >> a) & 1) par += coord(g, q, a);\n      s += ",
+     "        if ((e >> a) & 1) par += coord(g, q, 0);\n      s += "),
+    ("fft_axis_stride", "for (int b = 0; b < ax; ++b) stride *= (size_t)g->n[b];",
+     "for (int b = 0; b < ax && b < 1; ++b) stride *= (size_t)g->n[b];"),
     # preconditioner and CG
     ("precond_symbol_index", "s += xi[a] * kbar_at(kbar, a, b) * xi[b];",
      "s += xi[a] * kbar_at(kbar, a, a) * xi[b];"),
+    ("kbar_index_table_xz_yz", "static const int idx[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};",
+     "static const int idx[3][3] = {{0, 3, 5}, {3, 1, 4}, {5, 4, 2}};"),
+    ("kbar_pairs_swapped", "pb[6] = {0, 1, 2, 1, 2, 2};", "pb[6] = {0, 1, 2, 1, 1, 2};"),
+    ("kappa_fixed_dimension", "return sr / (double)npts + sm / (double)npts / (double)g->dim;",
+     "return sr / (double)npts + sm / (double)npts / 2.0;"),
+    ("dot_skips_last_entry", "for (size_t i = 0; i < n; ++i) s += a[i] * b[i];",
+     "for (size_t i = 0; i + 1 < n; ++i) s += a[i] * b[i];"),
     ("kbar_offdiag_square", "s += m[(size_t)pa[e] * npts + q] * m[(size_t)pb[e] * npts + q];",
      "s += m[(size_t)pa[e] * npts + q] * m[(size_t)pa[e] * npts + q];"),
     ("kappa_no_dim_division", "return sr / (double)npts + sm / (double)npts / (double)g->dim;",
@@ -72,12 +86,16 @@ MUTANTS = [
     # splitting substeps
     ("activation_exponent_sign", "double e = exp(c * c * g2 * dt);", "double e = exp(-c * c * g2 * dt);"),
     ("activation_gperp_sign", "double gperp[2] = {-g[1], g[0]};", "double gperp[2] = {g[1], g[0]};"),
+    ("activation_norm_drops_z", "double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];",
+     "double g2 = g[0] * g[0] + g[1] * g[1];"),
     ("activation_3d_drops_projection",
      "out[a] = mm[a] - g[a] * gm / g2 + g[a] * gm * e / g2;",
      "out[a] = mm[a] + g[a] * gm * e / g2;"),
     ("relaxation_exponent", "pow(b, 1.0 / (2.0 * (1.0 - gamma)))", "pow(b, 1.0 / (1.0 - gamma))"),
     ("relaxation_dt_factor", "- 2.0 * (1.0 - gamma) * dt;", "- (1.0 - gamma) * dt;"),
     ("relaxation_no_indicator", "double scale = (b >= 0) ?", "double scale = (1) ?"),
+    ("relaxation_gamma_one_loose_compare", "if (gamma == 1.0) { /* m exp(-dt) */",
+     "if (fabs(gamma - 1.0) < 0.3) { /* m exp(-dt) */"),
     ("relaxation_gamma_one_sign", "*= exp(-dt);\n      continue;", "*= exp(dt);\n      continue;"),
     ("diffusion_D_not_squared", "t[q] *= exp(-D * D * s * dt);", "t[q] *= exp(-D * s * dt);"),
     ("diffusion_drops_nyquist", "double x = or_xi(coord(g, q, a), g->n[a], g->L[a]);",
@@ -93,6 +111,7 @@ MUTANTS = [
     # energy
     ("energy_one_derivative_direction", "q < (size_t)dim * npts; ++q) e_diff", "q < npts; ++q) e_diff"),
     ("energy_flow_term_factor", "0.5 * c2 * e_r +", "c2 * e_r +"),
+    ("energy_flow_uses_m_squared", "mg += mc * gc;", "mg += mc * mc;"),
     ("energy_gamma_power", "e_rel += pow(m2, prm->gamma);", "e_rel += pow(m2, 2.0 * prm->gamma);"),
     # adjoint. Not listed, because they change nothing: dropping the projection of
     # lambda_p, a spectral divergence with no null-mode content; and dropping the final
