@@ -127,6 +127,28 @@ MUTANTS = [
      "ct[q] *= -s2 * exp(-D2 * s2 * dtt);"),
     ("adjoint_relax_jacobian", "* pow(rho, e - 1.0); /* df/drho */", "* pow(rho, e); /* df/drho */"),
     ("adjoint_drops_symmetric_m_term", "-= gm[c] * mgp + gp[c] * mgm;", "-= gm[c] * mgp;"),
+    ("adjoint_dc2_drops_dphi", "*dc2 += gl * mg * dtt * (ph + z * dph);", "*dc2 += gl * mg * dtt * ph;"),
+    ("adjoint_lambda_drops_activation",
+     "lam[(size_t)c * n + q] = la[c] + c2 * dtt * ph * gl * gv[c];", "lam[(size_t)c * n + q] = la[c];"),
+    ("adjoint_factor_two", "2.0 * c2 * dtt * dph * mg * gl * gv[c]", "1.0 * c2 * dtt * dph * mg * gl * gv[c]"),
+    ("adjoint_relax_unnormalised", "*c2 = (fp - sv) / n2;", "*c2 = (fp - sv);"),
+    ("adjoint_relax_zero_branch", "if (n2 == 0) { *c1 = gamma > 1.0 ? 1.0 : 0.0; *c2 = 0; return; }",
+     "if (n2 == 0) { *c1 = 1.0; *c2 = 0; return; }"),
+    ("adjoint_relax_extinct_branch", "if (beta <= 0) { *c1 = 0; *c2 = 0; return; }",
+     "if (beta <= 0) { *c1 = 1; *c2 = 0; return; }"),
+    ("adjoint_dD2_sign", "ct[q] *= -s2 * dtt * exp(-D2 * s2 * dtt);", "ct[q] *= s2 * dtt * exp(-D2 * s2 * dtt);"),
+    ("adjoint_skips_heat_transpose", "rc = or_diffusion(g, lb, prm->D, dtt);", "rc = 0;"),
+    ("adjoint_m_dot_g_drops_z", "double mg = mv[0] * gv[0] + mv[1] * gv[1] + mv[2] * gv[2];",
+     "double mg = mv[0] * gv[0] + mv[1] * gv[1];"),
+    ("adjoint_lambda_g_swapped", "ph * (mg * la[c] + mv[c] * gl)", "ph * (mg * la[c] + gv[c] * gl)"),
+    ("adjoint_dS_overwritten", "for (size_t q = 0; q < n; ++q) dS[q] += mu[q];",
+     "for (size_t q = 0; q < n; ++q) dS[q] = mu[q];"),
+    ("adjoint_dr_overwritten", "dr[q] -= gm[0] * gp[0] + gm[1] * gp[1] + gm[2] * gp[2];",
+     "dr[q] = -(gm[0] * gp[0] + gm[1] * gp[1] + gm[2] * gp[2]);"),
+    ("adjoint_dphi1_closed_form_sign", "return ((z - 1.0) * expm1(z) + z) / (z * z);",
+     "return ((z - 1.0) * expm1(z) - z) / (z * z);"),
+    ("adjoint_phi1_at_zero", "static double phi1(double z) { return z == 0 ? 1.0 : expm1(z) / z; }",
+     "static double phi1(double z) { return z == 0 ? 0.0 : expm1(z) / z; }"),
 ]
 
 CONTROL = ("unchanged_source", None, None)
