@@ -43,6 +43,46 @@ def test_adjoint_matches_oracle_adjoint_fp64(hc):
         assert rel_l2(got[k], ref[k]) < 1e-8, k
 
 
+def special_problem(case):
+    """The regimes where the adjoint's pointwise Jacobians switch branch:
+    conductivity exactly 0 and conductivity that dies out in one step (gamma
+    < 1), m = 0 with gamma > 1, activation exponents past the phi_1' series
+    range, and no activation at all (c = 0)."""
+    w = problem(64)
+    if case in ("zero_and_extinct", "zero_gamma_above_one"):
+        w.gamma = 0.5 if case == "zero_and_extinct" else 1.5
+        for j, i in [(5, 9), (40, 13), (63, 0)]:
+            w.m0[:, j, i] = 0.0
+        if case == "zero_and_extinct":
+            for j, i in [(20, 30), (0, 63)]:
+                w.m0[:, j, i] = (0.3 * w.dt, -0.2 * w.dt)
+    elif case == "large_exponent":
+        g = O.Grid(w.n, w.L)
+        prm = O.Params(c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, cg_rtol=1e-13, cg_maxit=5000)
+        _, p1, _ = O.step(g, prm, w.r, w.S, w.m0.copy(), np.zeros(w.shape))
+        g2 = (O.gradient(g, p1) ** 2).sum(0)
+        w.c = float(np.sqrt(2.0 / (w.dt * g2.max())))   # largest c^2 dt |grad p|^2 about 2
+    elif case == "no_activation":
+        w.c = 0.0
+    return w
+
+
+@pytest.mark.parametrize("case", ["zero_and_extinct", "zero_gamma_above_one", "large_exponent",
+                                  "no_activation"])
+def test_adjoint_special_regimes_match_oracle(hc, case):
+    w = special_problem(case)
+    g = O.Grid(w.n, w.L)
+    lam = np.random.default_rng(9).standard_normal((2,) + w.shape)
+    prm = O.Params(c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, cg_rtol=1e-13, cg_maxit=5000)
+    ref = O.adjoint(g, prm, w.r, w.S, w.m0, np.zeros(w.shape), 3, lam)
+    with make(hc, w) as s:
+        got = s.adjoint(3, lam, every=2)
+    assert np.isclose(got["dc2"], ref["dc2"], rtol=1e-8), (got["dc2"], ref["dc2"])
+    assert np.isclose(got["dD2"], ref["dD2"], rtol=1e-8)
+    for k in ("dr", "dS", "dm0"):
+        assert rel_l2(got[k], ref[k]) < 1e-8, k
+
+
 def test_adjoint_matches_central_differences_on_gpu(hc):
     """Finite differences of the GPU forward itself at 64^2: relative error
     <= 1e-4 for dL/dc^2, dL/dD^2 and sampled entries of dL/dr, dL/dS, dL/dm0."""
