@@ -1,0 +1,112 @@
+"""Properties that the mathematics fixes for any grid and any fields, checked
+on the oracle with randomly drawn sizes (odd and even, 2D and 3D) and values:
+
+- Transforms: the inverse transform undoes the forward one, and Parseval's
+  identity holds.
+- Operator of eq. (p_discrete): symmetric, positive semi-definite, and blind to
+  the null space (A P = A, with P the projection of reading R2).
+- Projection: idempotent, and orthogonal.
+- Relaxation, eq. (m_relaxation_discrete): keeps the direction of m and never
+  grows |m| (gamma > 0).
+- Activation, eq. (m_activation_discrete): leaves the part of m across grad p
+  unchanged and never shrinks the part along it.
+- Diffusion, eq. (diffusion_space_discrete): keeps the mean of each component
+  and never grows its L2 norm.
+"""
+import numpy as np
+import pytest
+
+hyp = pytest.importorskip("hypothesis")
+from hypothesis import given, settings, strategies as st  # noqa: E402
+
+import oracle as O  # noqa: E402
+
+SETTINGS = settings(max_examples=25, deadline=None, derandomize=True)
+axis = st.integers(min_value=2, max_value=12)
+seeds = st.integers(min_value=0, max_value=2**31 - 1)
+
+
+@st.composite
+def grids(draw, dims=(2, 3)):
+    dim = draw(st.sampled_from(dims))
+    n = tuple(draw(axis) if dim == 2 else draw(st.integers(2, 6)) for _ in range(dim))
+    L = tuple(draw(st.floats(0.3, 3.0)) for _ in range(dim))
+    return O.Grid(n, L)
+
+
+def fields(g, seed):
+    rng = np.random.default_rng(seed)
+    m = rng.uniform(-1, 1, (g.dim,) + g.shape)
+    r = rng.uniform(0.05, 0.5, g.shape)
+    return rng, m, r
+
+
+@SETTINGS
+@given(grids(), seeds)
+def test_transform_round_trip_and_parseval(g, seed):
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape)
+    F = O.fftn(g, f, -1)
+    back = O.fftn(g, F, +1)   # the inverse carries the 1/n
+    assert np.allclose(back, f, atol=1e-12)
+    assert np.isclose((abs(F) ** 2).sum(), g.npts * (abs(f) ** 2).sum(), rtol=1e-12)
+
+
+@SETTINGS
+@given(grids(), seeds)
+def test_operator_symmetric_psd_and_blind_to_the_null_space(g, seed):
+    rng, m, r = fields(g, seed)
+    u, v = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    Au, Av = O.apply_A(g, m, r, u), O.apply_A(g, m, r, v)
+    scale = np.abs(Au).max() * np.abs(v).max() * g.npts
+    assert abs((v * Au).sum() - (u * Av).sum()) <= 1e-12 * scale
+    assert (u * Au).sum() >= -1e-12 * scale
+    assert np.allclose(O.apply_A(g, m, r, O.project(g, u)), Au, atol=1e-11 * np.abs(Au).max())
+
+
+@SETTINGS
+@given(grids(), seeds)
+def test_projection_idempotent_and_orthogonal(g, seed):
+    f = np.random.default_rng(seed).standard_normal(g.shape)
+    P = O.project(g, f)
+    assert np.allclose(O.project(g, P), P, atol=1e-13)
+    assert abs((P * (f - P)).sum()) <= 1e-12 * (f * f).sum()
+    assert abs(P.sum()) <= 1e-11 * np.abs(f).sum()   # the constant mode is always removed
+
+
+@SETTINGS
+@given(st.integers(2, 3), seeds, st.floats(0.05, 3.0), st.floats(1e-4, 0.5))
+def test_relaxation_keeps_direction_and_never_grows(dim, seed, gamma, dt):
+    m = np.random.default_rng(seed).uniform(-1, 1, (dim, 64))
+    out = O.relaxation(m, gamma, dt)
+    nm, no = np.linalg.norm(m, axis=0), np.linalg.norm(out, axis=0)
+    assert np.all(no <= nm * (1 + 1e-14))
+    alive = no > 0
+    cosang = (m * out).sum(0)[alive] / (nm[alive] * no[alive])
+    assert np.allclose(cosang, 1.0, atol=1e-12)
+
+
+@SETTINGS
+@given(st.integers(2, 3), seeds, st.floats(0.0, 5.0), st.floats(1e-4, 0.2))
+def test_activation_changes_only_the_part_along_the_gradient(dim, seed, c, dt):
+    rng = np.random.default_rng(seed)
+    m = rng.uniform(-1, 1, (dim, 64))
+    gp = rng.uniform(-1, 1, (dim, 64))
+    out = O.activation(m, gp, c, dt)
+    g2 = (gp * gp).sum(0)
+    along_in, along_out = (m * gp).sum(0), (out * gp).sum(0)
+    perp_in = m - along_in / g2 * gp
+    perp_out = out - along_out / g2 * gp
+    assert np.allclose(perp_out, perp_in, atol=1e-12)
+    assert np.all(np.abs(along_out) >= np.abs(along_in) * (1 - 1e-14))
+    assert np.all(np.sign(along_out) == np.sign(along_in))
+
+
+@SETTINGS
+@given(grids(), seeds, st.floats(0.0, 0.3), st.floats(1e-4, 0.1))
+def test_diffusion_keeps_means_and_never_grows_the_norm(g, seed, D, dt):
+    _, m, _ = fields(g, seed)
+    out = O.diffusion(g, m, D, dt)
+    for c in range(g.dim):
+        assert np.isclose(out[c].mean(), m[c].mean(), atol=1e-13)
+        assert np.linalg.norm(out[c]) <= np.linalg.norm(m[c]) * (1 + 1e-13)
