@@ -8,9 +8,9 @@ a difference would point to a race. At full size the persistent column passes
 hold several tiles per CTA and double-buffer them with asynchronous copies,
 which is where a missing barrier would show.
 
-Cases: the 2048² source/sink steps in each precision, with the default launch
-shapes and with the prefetching column and row passes; and the 256³ refined
-steps."""
+Cases: the 2048² source/sink steps in each precision with the default launch
+shapes; the FP32 refinement with the persistent column passes, the persistent
+row pass, and both; and the 256³ refined steps."""
 import numpy as np
 import pytest
 
@@ -34,9 +34,12 @@ def run(hc, w, precision, nsteps, tuning=None):
         return s.get_m(), s.get_p(), (st.total_cg_iters, st.total_sweeps, st.rel_residual)
 
 
+# tuning = (col_pipe, row_pipe), [FP32 passes, FP64 passes]. At 2048² only the FP32 column
+# passes may run persistent: the FP64 double buffer would not fit in shared memory.
 @pytest.mark.parametrize("precision,tuning", [("fp32_refined", None), ("fp32_refined_df", None),
-                                              ("fp64", None), ("fp32_refined", ([1, 1], [0, 0])),
-                                              ("fp32_refined", ([0, 0], [1, 0]))])
+                                              ("fp64", None), ("fp32_refined", ([1, 0], [0, 0])),
+                                              ("fp32_refined", ([0, 0], [1, 0])),
+                                              ("fp32_refined", ([1, 0], [1, 0]))])
 def test_2048_steps_repeat_bitwise(hc, precision, tuning):
     w = W.source_sink_2d(2048, steps=3)
     a = run(hc, w, precision, 3 if precision != "fp64" else 1, tuning)
