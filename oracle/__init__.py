@@ -335,7 +335,10 @@ def diffusion(grid: Grid, m, D: float, dt: float) -> np.ndarray:
 
 
 def step(grid: Grid, prm: Params, r, S, m, p):
-    """One loop body of Algorithm 1.  Returns (m_new, p_new, Stats)."""
+    """One loop body of Algorithm 1.  Returns (m_new, p_new, Stats).  A step
+    that left NaN/Inf in m (the activation exponential overflowed, Remark 2.1)
+    returns that state with Stats.rc = ENONFINITE, as the library reports it;
+    invalid arguments raise."""
     r, S = _f64(r), _f64(S)
     m2 = _f64(m).reshape((grid.dim,) + grid.shape).copy()
     p2 = _f64(p).reshape(grid.shape).copy()
@@ -343,7 +346,7 @@ def step(grid: Grid, prm: Params, r, S, m, p):
     g = grid.c()
     cp = prm.c_struct()
     rc = _load().or_step(C.byref(g), C.byref(cp), _dp(r), _dp(S), _dp(m2), _dp(p2), C.byref(st))
-    if rc not in (OK, ENOCONV):
+    if rc not in (OK, ENOCONV, ENONFINITE):
         _check(rc, "step")
     return m2, p2, _stats(st, rc)
 

@@ -88,6 +88,36 @@ def test_energy_rule_stops_after_the_increase_is_seen():
     assert np.allclose(res2.energies[:len(e)], e, rtol=1e-12)
 
 
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")   # Delta m of m = 0 is 0/0
+def test_energy_rule_stops_on_equal_energies():
+    """Section 2.5 stops the loop when E_h^k >= E_h^(k-1), equality included.
+    With m0 = 0 the conductivity stays 0 (every substep maps 0 to 0) and the
+    warm-started pressure repeats exactly, so E_h(m^1) = E_h(m^0) and the loop
+    stops after its second body, naming the first."""
+    g = O.Grid((16, 16))
+    w = W.source_sink_2d(16, steps=1)
+    prm = O.Params(c=3.0, D=0.05, gamma=0.75, dt=1e-3, cg_rtol=1e-12)
+    res = O.run(g, prm, w.r, w.S, np.zeros((2,) + g.shape), max_steps=10, eps=0.0)
+    assert res.reason == 2 and res.steps == 2 and res.energy_step == 0
+    assert res.energies[1] == res.energies[0] > 0
+    assert not res.m.any()
+
+
+def test_run_stops_on_a_failed_step_and_returns_its_state():
+    """Remark 2.1: exp(c^2 |grad p|^2 dt) must stay bounded. When it overflows
+    the step reports ENONFINITE, and the loop stops there with reason 3 and
+    returns the state that step produced."""
+    n = 32
+    g = O.Grid((n, n))
+    w = W.source_sink_2d(n, steps=1)
+    prm = O.Params(c=1e4, D=0.02, gamma=0.5, dt=1e-3, cg_rtol=1e-10)
+    m_new, _, st = O.step(g, prm, w.r, w.S, w.m0, np.zeros(g.shape))
+    assert st.rc == O.ENONFINITE and not np.isfinite(m_new).all()
+    res = O.run(g, prm, w.r, w.S, w.m0, max_steps=5, eps=0.0)
+    assert res.reason == 3 and res.steps == 1 and res.energies == []
+    assert not np.isfinite(res.m).all()
+
+
 def test_paper_sources_satisfy_the_solvability_condition():
     """Section 3: int S_4 = 0 and int S_int = 0 (the Gaussians' integral over
     the plane is pi/1000); on a fine grid the node sums agree to quadrature

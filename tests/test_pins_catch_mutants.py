@@ -1,14 +1,19 @@
 """The oracle's pins catch plausible mistakes.
 
-Each case below plants one mistake in a copy of oracle/hc_oracle.c, the kind
-a reader might miss: a dropped term, a wrong sign, index, exponent or factor,
-a transposed operand, swapped substeps. The copy is built into its own
-library in a temporary folder, and the oracle's pin tests (tests/test_oracle_*.py)
-run against it in a subprocess through HC_ORACLE_LIB. A mistake counts as
-caught when some pin fails. The unchanged source, built the same way, must
-pass them all: that shows the harness itself is sound.
+Each case below plants one mistake, the kind a reader might miss: a dropped
+term, a wrong sign, index, exponent or factor, a transposed operand, swapped
+substeps. The oracle's pin tests (tests/test_oracle_*.py) then run against
+it in a subprocess. A mistake counts as caught when some pin fails.
 
-Everything runs on the CPU. The mistakes live only in temporary copies."""
+- A mistake in oracle/hc_oracle.c: the mutated copy is built into its own
+  library in a temporary folder, and the pins load it through HC_ORACLE_LIB.
+- A mistake in oracle/__init__.py, the host logic such as Algorithm 1's loop
+  and its stopping rules: the pins run in a temporary copy of the tests, the
+  oracle package and the input generators, with the mutated module.
+
+The unchanged sources, run the same two ways, must pass every pin: that shows
+the harness itself is sound. Everything runs on the CPU. The mistakes live
+only in temporary copies."""
 import os
 import shutil
 import subprocess
@@ -20,6 +25,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "hc_oracle.c")
 HDR = os.path.join(ROOT, "oracle", "hc_oracle.h")
+PY_SRC = os.path.join(ROOT, "oracle", "__init__.py")
 PIN_TESTS = sorted(
     os.path.join("tests", f) for f in os.listdir(os.path.join(ROOT, "tests"))
     if f.startswith("test_oracle_") and f.endswith(".py"))
@@ -151,7 +157,29 @@ MUTANTS = [
      "static double phi1(double z) { return z == 0 ? 0.0 : expm1(z) / z; }"),
 ]
 
+# (name, text in oracle/__init__.py, replacement). Not listed, for lack of a case
+# that tells them apart: "Delta m < eps" for "<= eps" (differs only at exact equality),
+# and applying the energy rule before the Delta m rule (differs only when both fire
+# in the same step).
+PY_MUTANTS = [
+    ("delta_m_relative_to_new_m", "/ (m_old ** 2).sum()) / dt)", "/ (m_new ** 2).sum()) / dt)"),
+    ("delta_m_not_per_unit_time", "/ (m_old ** 2).sum()) / dt)", "/ (m_old ** 2).sum()))"),
+    ("run_energy_of_the_new_m", "energies.append(energy(grid, prm, r, m, p))",
+     "energies.append(energy(grid, prm, r, m_new, p))"),
+    ("run_names_the_wrong_step", "reason, energy_step = 2, k - 1", "reason, energy_step = 2, k"),
+    ("run_energy_rule_needs_an_increase", "not energies[-1] < energies[-2]",
+     "energies[-1] > energies[-2]"),
+    ("run_returns_the_state_before_a_failure", "m, reason = m_new, 3", "reason = 3"),
+    ("kbar_array_offdiag_order",
+     "return np.array([M[0, 0], M[1, 1], M[2, 2], M[0, 1], M[0, 2], M[1, 2]])",
+     "return np.array([M[0, 0], M[1, 1], M[2, 2], M[0, 1], M[1, 2], M[0, 2]])"),
+    ("pcg_ignores_the_preconditioner_option",
+     "kb = kbar_default(grid, m, r) if precond == 1 else kbar_array(grid.dim, kappa_default(grid, m, r))",
+     "kb = kbar_array(grid.dim, kappa_default(grid, m, r))"),
+]
+
 CONTROL = ("unchanged_source", None, None)
+PY_CONTROL = ("unchanged_python", None, None)
 
 
 def _build_and_run(base, source, case):
@@ -172,30 +200,59 @@ def _build_and_run(base, source, case):
     return name, r.returncode, r.stdout[-3000:] + r.stderr[-1000:]
 
 
+def _run_python(base, lib, source, case):
+    """The pins in a sandbox holding a copy of the tests, the input generators
+    and the oracle package with the planted mistake (the C library unchanged)."""
+    name, old, new = case
+    d = os.path.join(base, name)
+    skip = shutil.ignore_patterns("__pycache__", "*.so", "*.tmp")
+    shutil.copytree(os.path.join(ROOT, "workloads"), os.path.join(d, "workloads"), ignore=skip)
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(d, "oracle"), ignore=skip)
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(d, "tests", "golden"))
+    for f in [os.path.basename(t) for t in PIN_TESTS] + ["conftest.py", "golden_cases.py"]:
+        shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(d, "tests", f))
+    with open(os.path.join(d, "oracle", "__init__.py"), "w") as f:
+        f.write(source if old is None else source.replace(old, new))
+    env = dict(os.environ, HC_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu",
+                        "-p", "no:cacheprovider", *PIN_TESTS],
+                       cwd=d, env=env, capture_output=True, text=True, timeout=600)
+    return name, r.returncode, r.stdout[-3000:] + r.stderr[-1000:]
+
+
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
+    import oracle
+    lib = oracle.build()   # the unchanged library, for the Python mutants
     base = str(tmp_path_factory.mktemp("oracle_mutants"))
     with open(SRC) as f:
         source = f.read()
+    with open(PY_SRC) as f:
+        py_source = f.read()
     for name, old, _ in MUTANTS:
         assert source.count(old) == 1, f"{name}: the planted text must occur exactly once"
+    for name, old, _ in PY_MUTANTS:
+        assert py_source.count(old) == 1, f"{name}: the planted text must occur exactly once"
+    jobs = [lambda c=c: _build_and_run(base, source, c) for c in [CONTROL] + MUTANTS]
+    jobs += [lambda c=c: _run_python(base, lib, py_source, c) for c in [PY_CONTROL] + PY_MUTANTS]
     workers = max(1, min(8, os.cpu_count() or 1))
     with ThreadPoolExecutor(max_workers=workers) as ex:
-        done = list(ex.map(lambda c: _build_and_run(base, source, c), [CONTROL] + MUTANTS))
+        done = list(ex.map(lambda job: job(), jobs))
     return {name: (rc, out) for name, rc, out in done}
 
 
-def test_harness_control_passes(outcomes):
-    rc, out = outcomes[CONTROL[0]]
+@pytest.mark.parametrize("name", [CONTROL[0], PY_CONTROL[0]])
+def test_harness_control_passes(outcomes, name):
+    rc, out = outcomes[name]
     assert rc == 0, out
 
 
 def test_mutant_names_unique():
-    names = [m[0] for m in MUTANTS]
+    names = [m[0] for m in MUTANTS + PY_MUTANTS] + [CONTROL[0], PY_CONTROL[0]]
     assert len(names) == len(set(names))
 
 
-@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS + PY_MUTANTS])
 def test_pins_catch_mutant(outcomes, name):
     rc, out = outcomes[name]
     # 1: some pin failed.  0 would mean the mistake went unnoticed; any other
