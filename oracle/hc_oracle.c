@@ -28,6 +28,37 @@
  *   R8  in 3D the perpendicular projector g_perp g_perp^T / |g|^2 is I - g g^T/|g|^2;
  *   R10 discrete L2 norms in the energy carry the quadrature weight h_x h_y [h_z];
  *   R11 Lie splitting, every substep with the full dt, order A -> R -> D.
+ *
+ * What pins each function (tests/test_oracle_*.py). Every value there comes
+ * from the mathematics or a library routine, not from this file. No function
+ * is parity unpinned.
+ *   or_dft1, or_fft1, or_fftn  the DFT's definition summed directly; numpy's FFT;
+ *                              Parseval and the round trip on random grids.
+ *   or_xi, or_xi_deriv         the wavenumber table of Section 2.3.3, worked by hand.
+ *   or_gradient                exact derivatives of trigonometric polynomials, 2D and 3D.
+ *   or_apply_K, or_apply_A     the tensor's eigenvectors; constant-coefficient closed forms;
+ *                              a sympy manufactured solution; dense assembly (symmetric,
+ *                              semi-definite, the 2^dim corner null modes); hand-worked
+ *                              variable-coefficient cases.
+ *   or_project                 the null space of the assembled operator (eigen- or singular
+ *                              vectors), odd grids included; idempotent and orthogonal.
+ *   or_precond, or_kbar_default, or_kappa_default
+ *                              one CG iteration when the coefficient is constant; a 3D
+ *                              eigenfunction; hand-worked kappa and Kbar.
+ *   or_pcg                     numpy's least-squares solution; condition-number iteration
+ *                              bounds; exact invariance under a power-of-two scaling of S;
+ *                              the reported residual recomputed.
+ *   or_activation              scipy's matrix exponential; RK4; hand-worked projector-form cases.
+ *   or_relaxation              closed forms (gamma = 1, 1/2); RK4 of the radial equation;
+ *                              hand-worked cases in every regime.
+ *   or_diffusion               single-mode decay, the Nyquist mode included, 2D and 3D.
+ *   or_step                    the energy identity; energy decrease for small dt; symmetries;
+ *                              special cases; the order of Algorithm 1.
+ *   or_energy                  hand-worked values of every term.
+ *   or_adjoint                 finite differences of the forward map: 2D and 3D, every
+ *                              relaxation branch, m = 0 and extinction, c = 0.
+ * tests/test_pins_catch_mutants.py plants mistakes in copies of this file and
+ * requires each to fail some pin.
  */
 #include "hc_oracle.h"
 
