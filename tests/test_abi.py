@@ -164,3 +164,45 @@ def test_hc_check_changes_only_the_host_orchestration():
     assert users == ["hc_api.cu"]
     header = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "hc.h")).read(), flags=re.S)
     assert "HC_CHECK" not in header
+
+
+def test_binding_marshals_host_buffers_without_a_gpu(lib):
+    """_host_f64: FP64 C-contiguous arrays pass through, others are copied for
+    inputs and refused for outputs; sizes are checked; torch CPU tensors must
+    be contiguous FP64."""
+    import numpy as np
+    import torch
+    from paper_2606_06720_gb300 import _binding as Bd
+    a = np.arange(12, dtype=np.float64).reshape(3, 4)
+    p, keep = Bd._host_f64(a, 12)
+    assert keep is a
+    p, keep = Bd._host_f64(a.T, 12)                     # non-contiguous input: copied
+    assert keep is not a and keep.flags["C_CONTIGUOUS"] and np.array_equal(keep, a.T)
+    p, keep = Bd._host_f64(a.astype(np.float32), 12)    # other dtype: converted
+    assert keep.dtype == np.float64
+    with pytest.raises(ValueError):
+        Bd._host_f64(a.T, 12, writable=True)            # an output must be written in place
+    with pytest.raises(ValueError):
+        Bd._host_f64(a, 13)
+    t = torch.zeros(12, dtype=torch.float64)
+    p, keep = Bd._host_f64(t, 12)
+    assert keep is t
+    for bad in (torch.zeros(12, dtype=torch.float32), torch.zeros(4, 6, dtype=torch.float64).t()):
+        with pytest.raises(ValueError):
+            Bd._host_f64(bad, 12)
+
+
+def test_error_codes_and_messages(lib):
+    from paper_2606_06720_gb300 import _binding as Bd
+    codes = [Bd.HC_OK, Bd.HC_EINVAL, Bd.HC_ENOMEM, Bd.HC_ECUDA, Bd.HC_ENOCONV, Bd.HC_ENONFINITE,
+             Bd.HC_ETIMEOUT, Bd.HC_ENOTSUP, Bd.HC_EBOUNDS]
+    assert codes == [0, -1, -2, -3, -4, -5, -6, -7, -8]
+    msgs = [Bd.strerror(c) for c in codes]
+    assert len(set(msgs)) == len(msgs) and "unknown" not in " ".join(msgs)
+    assert "guard zone" in Bd.strerror(Bd.HC_EBOUNDS)
+    assert Bd.strerror(-99) == "unknown error"
+    err = Bd.HuCaiError(Bd.HC_EBOUNDS, "hc_check_redzones")
+    assert "hc_check_redzones" in str(err) and err.code == -8
+    with pytest.raises(Bd.HuCaiError):
+        Bd._check(Bd.HC_EINVAL, "x")
+    Bd._check(Bd.HC_ENOCONV, "x", ok=(Bd.HC_OK, Bd.HC_ENOCONV))
