@@ -42,10 +42,11 @@ constexpr size_t kRedzone = HC_CHECK ? (size_t)HC_REDZONE_BYTES : 0;
 constexpr int kMaxZones = 128;
 constexpr unsigned char kPattern = 0xA5;
 
-// Guard zones of one workspace, in carve order.
+// Guard zones of one workspace, in carve order.  A plain aggregate: the
+// context holding one is cleared with memset, a local one is value-initialised.
 struct Zones {
-  int n = 0;        // zones recorded (at most kMaxZones)
-  int carved = 0;   // zones carved; more than n means the table overflowed
+  int n;       // zones recorded (at most kMaxZones)
+  int carved;  // zones carved; more than n means the table overflowed
   size_t start[kMaxZones];  // byte offset from the workspace base
   size_t len[kMaxZones];
   size_t owner[kMaxZones];  // bytes of the buffer the zone follows
@@ -1080,7 +1081,7 @@ int build_chain(hc_ctx* c, cudaGraph_t target, Handles* h) {
   int rc = end_capture(target, tail);
   if (rc) return rc;
   cudaGraphNode_t loop_node;
-  cudaGraph_t body;
+  cudaGraph_t body = nullptr;
   if (c->refined) {
     // the first inner loop, then the refinement loop with its own inner loop
     cudaGraphNode_t first_node;
@@ -1090,7 +1091,7 @@ int build_chain(hc_ctx* c, cudaGraph_t target, Handles* h) {
     if (c->mid_df) {
       // IF(mid){double-float residual, WHILE(mid_inner){CG}}
       cudaGraphNode_t mid_node, mi_node;
-      cudaGraph_t mbody;
+      cudaGraph_t mbody = nullptr;
       rc = add_while(target, std::vector<cudaGraphNode_t>{first_node}, &hh.mid, &mid_node, &mbody,
                      true);
       if (rc) return rc;
@@ -1104,7 +1105,7 @@ int build_chain(hc_ctx* c, cudaGraph_t target, Handles* h) {
       if (rc) return rc;
       first_node = mid_node;
     }
-    cudaGraph_t obody;
+    cudaGraph_t obody = nullptr;
     rc = add_while(target, std::vector<cudaGraphNode_t>{first_node}, &hh.outer, &loop_node, &obody);
     if (rc) return rc;
     CU(cudaStreamBeginCaptureToGraph(s, obody, nullptr, nullptr, 0,
@@ -1323,8 +1324,7 @@ const char* hc_strerror(int code) {
 
 int hc_workspace_size(const hc_grid* grid, const hc_params* params, size_t* bytes) {
   if (check_grid(grid) || check_params(params) || !bytes) return HC_EINVAL;
-  hc_ctx tmp;
-  std::memset(&tmp, 0, sizeof(tmp));
+  hc_ctx tmp{};  // every member zero (or its default)
   tmp.grid = *grid;
   tmp.dim = grid->dim;
   tmp.nx = grid->n[0];
@@ -1350,9 +1350,8 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   size_t need = 0;
   hc_workspace_size(grid, params, &need);
   if (workspace && workspace_bytes < need) return HC_ENOMEM;
-  hc_ctx* c = new (std::nothrow) hc_ctx;
+  hc_ctx* c = new (std::nothrow) hc_ctx();  // value-initialised: every member zero (or its default)
   if (!c) return HC_ENOMEM;
-  std::memset(c, 0, sizeof(*c));
   c->grid = *grid;
   c->prm = *params;
   apply_defaults(c->prm);
@@ -2247,7 +2246,7 @@ int hc_adjoint(hc_ctx* c, int nsteps, int every, const double* lamT, double* dc2
     if (cudaMalloc(&ws, need) != cudaSuccess) return HC_ENOMEM;
     own = true;
   }
-  Zones zones;  // the adjoint workspace's guard zones (bounds-checked build)
+  Zones zones{};  // the adjoint workspace's guard zones (bounds-checked build)
   if (kRedzone) {
     if (c->refined) {
       AdjLayout<float> t;
