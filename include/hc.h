@@ -134,7 +134,9 @@ typedef struct {
   long long total_refine_residuals; /* summed over the call */
 } hc_step_stats;
 
-/* Bytes of device workspace hc_create needs for this grid and precision. */
+/* Bytes of device workspace hc_create needs for this grid and precision
+ * (host arithmetic only, no GPU work).  Errors: HC_EINVAL for an unsupported
+ * grid, invalid params or a NULL bytes. */
 int hc_workspace_size(const hc_grid* grid, const hc_params* params, size_t* bytes);
 
 /* Create a context.  If workspace is non-NULL it must be a device pointer to at
@@ -145,8 +147,11 @@ int hc_workspace_size(const hc_grid* grid, const hc_params* params, size_t* byte
 int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* workspace,
               size_t workspace_bytes);
 
-/* Replace the scalar parameters (c, D, gamma, dt, tolerances, kappa, use_graph);
- * the grid, precision and stream must match the ones given at creation. */
+/* Replace the scalar parameters (c, D, gamma, dt, tolerances, kappa, use_graph,
+ * diagnostics, precond ...; Algorithm 1 inputs); the grid, precision and stream
+ * must match the ones given at creation.  The step graphs are rebuilt at the
+ * next step.  Errors: HC_EINVAL (invalid params, or another precision or
+ * stream), HC_ECUDA. */
 int hc_set_params(hc_ctx* ctx, const hc_params* params);
 
 /* Background permeability r(x) (eq. 1.1a); count = npts; requires r > 0
@@ -155,16 +160,22 @@ int hc_set_r(hc_ctx* ctx, const double* r, size_t count);
 
 /* Source/sink field S (eq. 1.1a); count = npts.  Stored after projection onto
  * the complement of the operator's null space (zero mean and no corner modes:
- * the solvability condition that the paper states as int S = 0). */
+ * the solvability condition that the paper states as int S = 0).
+ * Errors: HC_EINVAL (NULL, wrong count, a non-finite value), HC_ECUDA. */
 int hc_set_source(hc_ctx* ctx, const double* S, size_t count);
 
-/* Conductivity m (count = dim*npts, component-major).  With params.diagnostics it also
- * computes the gradient norm that the energy of this m needs; without, the first step's energy
- * is unknown (energy_valid = 0) unless hc_run, which computes it, takes the step. */
+/* Conductivity m (count = dim*npts, component-major; the initial m0 of
+ * Algorithm 1).  With params.diagnostics it also computes the gradient norm
+ * that the energy of this m needs; without, the first step's energy is
+ * unknown (energy_valid = 0) unless hc_run, which computes it, takes the step.
+ * The refined modes hold m in FP32.  Errors: HC_EINVAL (NULL, wrong count),
+ * HC_ECUDA; non-finite values are not checked here (the next step reports
+ * HC_ENONFINITE). */
 int hc_set_m(hc_ctx* ctx, const double* m, size_t count);
 
 /* Pressure p used as the CG initial guess of the next step (Section 2.4 uses
- * p^k; default 0).  Projected like S. */
+ * p^k; default 0).  Projected like S.  Errors: HC_EINVAL (NULL, wrong count),
+ * HC_ECUDA. */
 int hc_set_p(hc_ctx* ctx, const double* p, size_t count);
 
 /* Run nsteps passes of the loop body of Algorithm 1.  `last` (may be NULL)
@@ -186,14 +197,19 @@ int hc_step(hc_ctx* ctx, int nsteps, hc_step_stats* last);
 int hc_run(hc_ctx* ctx, int max_steps, double eps, int stop_on_energy, int* steps_done,
            hc_step_stats* last);
 
-/* Copy the current p (count = npts) or m (count = dim*npts) to host memory. */
+/* Copy the current p (count = npts) or m (count = dim*npts), the outputs of
+ * Algorithm 1, to host memory in the field layout above; the call waits for
+ * the copy.  Errors: HC_EINVAL (NULL, wrong count), HC_ECUDA. */
 int hc_get_p(hc_ctx* ctx, double* out, size_t count);
 int hc_get_m(hc_ctx* ctx, double* out, size_t count);
 
 /* --- Component entry points (each runs one part of the step on the GPU) --- */
 
 /* Spectral gradient of the current p (Section 2.4 and Algorithm 1 "compute
- * gradient of p via FFT"): out = (d_x p, d_y p[, d_z p]), count = dim*npts. */
+ * gradient of p via FFT"): out = (d_x p, d_y p[, d_z p]), count = dim*npts,
+ * component-major host memory.  Errors: HC_EINVAL (NULL, wrong count),
+ * HC_ECUDA.  The same holds for the component calls below: they run on the
+ * context's stream and wait for their own results. */
 int hc_gradient(hc_ctx* ctx, double* out, size_t count);
 
 /* Apply the discrete pressure operator of eq. (p_discrete) with the current m
