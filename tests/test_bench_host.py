@@ -37,3 +37,35 @@ def test_clock_samples_default_to_a_temporary_file():
     import bench
     clk = bench.ClockSampler("0")
     assert os.path.dirname(clk.path) == tempfile.gettempdir()
+
+
+def _reference_arm(env_extra):
+    import json
+    import subprocess
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "2", "--warmup", "1", "--ref-n", "32"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    return [json.loads(l) for l in lines]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference times the CPU oracle and prints one JSON line
+    with the keys of the bench contract, on the host (no GPU needed)."""
+    (line,) = _reference_arm({"RANK": "0", "WORLD_SIZE": "1"})
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["value"] > 0 and line["unit"] == "Mpoint-steps/s" and line["higher_is_better"]
+    assert line["dtype"] == "f64" and line["data"] == "synthetic" and line["vs_baseline"] is None
+    assert abs(line["ms_per_step"] * line["value"] - 32 * 32 * 1e-3) < 1e-6 * 32 * 32
+    cpu = line["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"]
+    assert "32x32" in cpu["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "workload" in line["config"]
+
+
+def test_reference_arm_is_silent_on_other_ranks():
+    assert _reference_arm({"RANK": "1", "WORLD_SIZE": "2"}) == []
