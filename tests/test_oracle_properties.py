@@ -110,3 +110,21 @@ def test_diffusion_keeps_means_and_never_grows_the_norm(g, seed, D, dt):
     for c in range(g.dim):
         assert np.isclose(out[c].mean(), m[c].mean(), atol=1e-13)
         assert np.linalg.norm(out[c]) <= np.linalg.norm(m[c]) * (1 + 1e-13)
+
+
+@SETTINGS
+@given(grids(dims=(2,)), seeds, st.floats(0.5, 2.0), st.floats(0.1, 1.0), st.floats(0.3, 3.0))
+def test_energy_scales_term_by_term(g, seed, gamma, D, lam):
+    """With c = 0 the energy of Section 2.5 has two terms of fixed degree:
+    E(lam m) = lam^2 E_diff(m) + lam^(2 gamma) E_relax(m). E_diff is the energy
+    with the relaxation term scaled out, E_relax the one with D = 0."""
+    _, m, r = fields(g, seed)
+    p = np.zeros(g.shape)
+    full = O.Params(c=0.0, D=D, gamma=gamma, dt=1e-3)
+    no_diff = O.Params(c=0.0, D=0.0, gamma=gamma, dt=1e-3)
+    E_relax = O.energy(g, no_diff, r, m, p)
+    E_diff = O.energy(g, full, r, m, p) - E_relax
+    got = O.energy(g, full, r, lam * m, p)
+    want = lam ** 2 * E_diff + lam ** (2 * gamma) * E_relax
+    assert np.isclose(got, want, rtol=1e-11)
+    assert E_diff >= 0 and E_relax > 0
