@@ -126,8 +126,9 @@ def test_refined_residual_recomputed_by_oracle(hc, precision):
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32_refined", 1e-5),
                                            ("fp32_refined_df", 1e-5)])
 def test_headline_2048_one_step(hc, precision, tol):
-    """2048^2 source/sink workload in the launch configuration the benchmark
-    times (graph mode): one step against the oracle at full size."""
+    """2048^2 source/sink workload in graph mode with the default launch
+    shapes: one step against the oracle at full size (the bench's own tuned
+    configuration is the next test)."""
     w = W.source_sink_2d(2048, steps=1)
     g = O.Grid(w.n, w.L)
     m_ref, p_ref, st_ref = O.step(g, oprm(w, rtol=1e-8), w.r, w.S, w.m0, np.zeros(g.shape))
@@ -138,6 +139,31 @@ def test_headline_2048_one_step(hc, precision, tol):
     # FP64: the same iteration as the oracle, so p agrees to rounding; refined:
     # p is determined to the CG tolerance only
     assert em <= tol and ep <= (tol if precision == "fp64" else 1e-6), (em, ep)
+
+
+@pytest.mark.parametrize("precision", ["fp32_refined", "fp32_refined_df"])
+def test_headline_2048_in_the_bench_configuration(hc, precision, tmp_path, monkeypatch):
+    """The 2048^2 step exactly as bench.py times it: the K-bar preconditioner
+    option and the launch shapes its autotuner picks after one step on the
+    workload's own data (a fresh tuning cache), then m and p reset. One step
+    against the oracle with the same preconditioner: certified residual, and
+    m within the 1e-5 bar."""
+    from paper_2606_06720_gb300.autotune import autotune
+    monkeypatch.setenv("HC_TUNING_CACHE", str(tmp_path / "tuning.json"))
+    w = W.source_sink_2d(2048, steps=1)
+    g = O.Grid(w.n, w.L)
+    prm = O.Params(c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, cg_rtol=1e-8, cg_maxit=2000, precond=1)
+    m_ref, p_ref, _ = O.step(g, prm, w.r, w.S, w.m0, np.zeros(g.shape))
+    with make_solver(hc, w, precision, rtol=1e-8, precond="kbar") as s:
+        s.step(1)
+        tuning = autotune(s, reps=5)
+        s.set_m(w.m0)
+        s.set_p(np.zeros(w.shape))
+        st = s.step(1)
+        assert st.status == 0 and st.rel_residual <= 1e-8
+        assert s.get_tuning() == tuning
+        em, ep = rel_l2(s.get_m(), m_ref), rel_l2(s.get_p(), p_ref)
+    assert em <= 1e-5 and ep <= 1e-6, (em, ep, tuning)
 
 
 @pytest.mark.parametrize("case", ["zero_source", "zero_m", "gamma_one", "gamma_gt_one", "no_activation",
