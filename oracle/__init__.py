@@ -379,9 +379,13 @@ def adjoint(grid: Grid, prm: Params, r, S, m0, p0, nsteps: int, lamT):
 def delta_m(m_new, m_old, dt: float) -> float:
     """Relative change of the conductivity per unit time (Section 2.5):
     ||m^k - m^{k-1}||_2 / (dt ||m^{k-1}||_2), discrete L2 norms (the cell
-    volume cancels in the ratio)."""
+    volume cancels in the ratio).  Reading R20: 0 when m^{k-1} = 0, a steady
+    state (every substep maps m = 0 to 0), where the ratio is 0/0."""
     m_new, m_old = _f64(m_new), _f64(m_old)
-    return float(np.sqrt(((m_new - m_old) ** 2).sum() / (m_old ** 2).sum()) / dt)
+    old2 = (m_old ** 2).sum()
+    if old2 == 0:
+        return 0.0
+    return float(np.sqrt(((m_new - m_old) ** 2).sum() / old2) / dt)
 
 
 @dataclass

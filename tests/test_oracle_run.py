@@ -88,7 +88,6 @@ def test_energy_rule_stops_after_the_increase_is_seen():
     assert np.allclose(res2.energies[:len(e)], e, rtol=1e-12)
 
 
-@pytest.mark.filterwarnings("ignore::RuntimeWarning")   # Delta m of m = 0 is 0/0
 def test_energy_rule_stops_on_equal_energies():
     """Section 2.5 stops the loop when E_h^k >= E_h^(k-1), equality included.
     With m0 = 0 the conductivity stays 0 (every substep maps 0 to 0) and the
@@ -101,6 +100,21 @@ def test_energy_rule_stops_on_equal_energies():
     assert res.reason == 2 and res.steps == 2 and res.energy_step == 0
     assert res.energies[1] == res.energies[0] > 0
     assert not res.m.any()
+
+
+def test_zero_conductivity_is_a_steady_state_for_the_delta_m_rule():
+    """Reading R20: Delta m of a step from m = 0 is 0 (m stays 0), so any
+    eps > 0 stops the loop after its first body; with eps = 0 the energy rule
+    stops it instead, one body later."""
+    g = O.Grid((16, 16))
+    w = W.source_sink_2d(16, steps=1)
+    prm = O.Params(c=3.0, D=0.05, gamma=0.75, dt=1e-3, cg_rtol=1e-12)
+    zero = np.zeros((2,) + g.shape)
+    assert O.delta_m(zero, zero, prm.dt) == 0.0
+    res = O.run(g, prm, w.r, w.S, zero, max_steps=10, eps=1e-4)
+    assert res.reason == 1 and res.steps == 1 and res.delta_ms == [0.0]
+    res = O.run(g, prm, w.r, w.S, zero, max_steps=10, eps=0.0)
+    assert res.reason == 2 and res.steps == 2
 
 
 def test_run_stops_on_a_failed_step_and_returns_its_state():

@@ -162,8 +162,9 @@ MUTANTS = [
 # and applying the energy rule before the Delta m rule (differs only when both fire
 # in the same step).
 PY_MUTANTS = [
-    ("delta_m_relative_to_new_m", "/ (m_old ** 2).sum()) / dt)", "/ (m_new ** 2).sum()) / dt)"),
-    ("delta_m_not_per_unit_time", "/ (m_old ** 2).sum()) / dt)", "/ (m_old ** 2).sum()))"),
+    ("delta_m_relative_to_new_m", "old2 = (m_old ** 2).sum()", "old2 = (m_new ** 2).sum()"),
+    ("delta_m_not_per_unit_time", "/ old2) / dt)", "/ old2))"),
+    ("delta_m_of_a_zero_state_undefined", "if old2 == 0:\n        return 0.0", "if old2 < 0:\n        return 0.0"),
     ("run_energy_of_the_new_m", "energies.append(energy(grid, prm, r, m, p))",
      "energies.append(energy(grid, prm, r, m_new, p))"),
     ("run_names_the_wrong_step", "reason, energy_step = 2, k - 1", "reason, energy_step = 2, k"),
