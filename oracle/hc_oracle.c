@@ -27,7 +27,9 @@
  *   R7  relaxation edge cases as printed: gamma == 1, |m| == 0, indicator b >= 0;
  *   R8  in 3D the perpendicular projector g_perp g_perp^T / |g|^2 is I - g g^T/|g|^2;
  *   R10 discrete L2 norms in the energy carry the quadrature weight h_x h_y [h_z];
- *   R11 Lie splitting, every substep with the full dt, order A -> R -> D.
+ *   R11 Lie splitting, every substep with the full dt, order A -> R -> D;
+ *   R21 at gamma = 0 the energy's relaxation term |m|^(2 gamma)/(2 gamma) is
+ *       undefined (1/0) and is left out; the scheme itself is defined there.
  *
  * What pins each function (tests/test_oracle_*.py). Every value there comes
  * from the mathematics or a library routine, not from this file. No function
@@ -624,8 +626,9 @@ double or_energy(const or_grid* g, const or_params* prm, const double* r, const 
   free(gp);
   free(gm);
   double c2 = prm->c * prm->c;
-  return h * (0.5 * prm->D * prm->D * e_diff + 0.5 * c2 * e_r + 0.5 * c2 * e_act +
-              e_rel / (2.0 * prm->gamma));
+  /* R21: at gamma = 0 the relaxation term |m|^(2 gamma) / (2 gamma) is undefined; it is left out */
+  const double rel = prm->gamma != 0.0 ? e_rel / (2.0 * prm->gamma) : 0.0;
+  return h * (0.5 * prm->D * prm->D * e_diff + 0.5 * c2 * e_r + 0.5 * c2 * e_act + rel);
 }
 
 /* ------------------------------------------------------------------ */
