@@ -106,6 +106,20 @@ MUTANTS = [
     ("diffusion_D_not_squared", "t[q] *= exp(-D * D * s * dt);", "t[q] *= exp(-D * s * dt);"),
     ("diffusion_drops_nyquist", "double x = or_xi(coord(g, q, a), g->n[a], g->L[a]);",
      "double x = or_xi_deriv(coord(g, q, a), g->n[a], g->L[a]);"),
+    # loops that stop at two dimensions
+    ("diffusion_wavenumber_2d_only", "      for (int a = 0; a < g->dim; ++a) {\n        double x = or_xi(",
+     "      for (int a = 0; a < 2; ++a) {\n        double x = or_xi("),
+    ("energy_grad_m_two_components",
+     "  for (int c = 0; c < dim; ++c) {\n    or_gradient(g, m + (size_t)c * npts, gm);",
+     "  for (int c = 0; c < 2; ++c) {\n    or_gradient(g, m + (size_t)c * npts, gm);"),
+    ("energy_pointwise_two_components",
+     "    for (int c = 0; c < dim; ++c) {\n      double gc = gp[(size_t)c * npts + q]",
+     "    for (int c = 0; c < 2; ++c) {\n      double gc = gp[(size_t)c * npts + q]"),
+    ("precond_symbol_two_axes",
+     "    for (int a = 0; a < g->dim; ++a)\n      for (int b = 0; b < g->dim; ++b) s += xi[a]",
+     "    for (int a = 0; a < 2; ++a)\n      for (int b = 0; b < 2; ++b) s += xi[a]"),
+    ("gradient_two_components", "  for (int c = 0; c < g->dim && !rc; ++c) {\n    /* d f / d x_c",
+     "  for (int c = 0; c < 2 && !rc; ++c) {\n    /* d f / d x_c"),
     # Algorithm 1's order
     ("step_relaxation_before_activation",
      "or_activation(dim, npts, m, grad, prm->c, prm->dt);\n    or_relaxation(dim, npts, m, prm->gamma, prm->dt);",
