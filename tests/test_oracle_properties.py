@@ -128,3 +128,21 @@ def test_energy_scales_term_by_term(g, seed, gamma, D, lam):
     want = lam ** 2 * E_diff + lam ** (2 * gamma) * E_relax
     assert np.isclose(got, want, rtol=1e-11)
     assert E_diff >= 0 and E_relax > 0
+
+
+@SETTINGS
+@given(grids(), seeds)
+def test_preconditioner_is_symmetric_positive_on_the_range(g, seed):
+    """M^-1 of reading R3 (both options) is symmetric, positive on the
+    complement of the null space, and zero on the null space."""
+    rng, m, r = fields(g, seed)
+    u = O.project(g, rng.standard_normal(g.shape))
+    v = O.project(g, rng.standard_normal(g.shape))
+    for kb in (O.kappa_default(g, m, r), O.kbar_default(g, m, r)):
+        Mu, Mv = O.precond(g, kb, u), O.precond(g, kb, v)
+        scale = np.abs(Mu).max() * np.abs(v).max() * g.npts
+        assert abs((v * Mu).sum() - (u * Mv).sum()) <= 1e-12 * scale
+        if np.abs(u).max() > 0:          # a grid of 2-point axes has only null modes
+            assert (u * Mu).sum() > 0
+        null = u - O.project(g, u) + (rng.standard_normal() * np.ones(g.shape))
+        assert np.abs(O.precond(g, kb, null)).max() <= 1e-12 * (1 + np.abs(null).max())
