@@ -453,7 +453,11 @@ int or_pcg(const or_grid* g, const double* m, const double* r, const double* b, 
     while (rnorm > rtol * bnorm && it < maxit) {
       rc = or_apply_A(g, m, r, d, q);
       if (rc) break;
-      double alpha = rho / dot(n, d, q);
+      const double dAd = dot(n, d, q);
+      /* <d, A d> = 0 only when d has no component in the range of A (R2), as on
+         a grid whose every mode is a null mode: nothing is left to solve */
+      if (!(dAd > 0)) break;
+      double alpha = rho / dAd;
       for (size_t i = 0; i < n; ++i) x[i] += alpha * d[i];
       for (size_t i = 0; i < n; ++i) res[i] -= alpha * q[i];
       rnorm = sqrt(dot(n, res, res));

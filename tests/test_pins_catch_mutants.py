@@ -87,8 +87,8 @@ MUTANTS = [
     ("cg_absolute_stop", "while (rnorm > rtol * bnorm && it < maxit) {",
      "while (rnorm > rtol && it < maxit) {"),
     ("cg_beta_inverted", "double beta = rho_new / rho;", "double beta = rho / rho_new;"),
-    ("cg_alpha_wrong_denominator", "double alpha = rho / dot(n, d, q);",
-     "double alpha = rho / dot(n, d, d);"),
+    ("cg_alpha_wrong_denominator", "const double dAd = dot(n, d, q);",
+     "const double dAd = dot(n, d, d);"),
     # splitting substeps
     ("activation_exponent_sign", "double e = exp(c * c * g2 * dt);", "double e = exp(-c * c * g2 * dt);"),
     ("activation_gperp_sign", "double gperp[2] = {-g[1], g[0]};", "double gperp[2] = {g[1], g[0]};"),
