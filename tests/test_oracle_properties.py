@@ -164,3 +164,31 @@ def test_step_keeps_p_in_the_range_and_repeats_exactly(g, seed, gamma):
     assert np.array_equal(m1, m2) and np.array_equal(p1, p2)
     E = O.energy(g, prm, r, m, p1)
     assert np.isfinite(E) and E >= 0
+
+
+@settings(max_examples=12, deadline=None, derandomize=True)
+@given(st.tuples(st.integers(3, 8), st.integers(3, 8)), seeds)
+def test_adjoint_directional_derivative_on_random_grids(n, seed):
+    """<dL/dm0, dm> equals the central difference of L = <w, m(T)> along a
+    random direction dm, on small odd and even grids (gamma = 1 keeps the
+    relaxation smooth; m stays away from 0)."""
+    g = O.Grid(n, (1.0, 0.8))
+    rng = np.random.default_rng(seed)
+    m0 = rng.uniform(0.3, 1.0, (2,) + g.shape)
+    r = rng.uniform(0.05, 0.3, g.shape)
+    S = rng.standard_normal(g.shape)
+    prm = O.Params(c=2.0, D=0.1, gamma=1.0, dt=2e-3, cg_rtol=1e-14, cg_maxit=2000)
+    w = rng.standard_normal(m0.shape)
+    dm = rng.standard_normal(m0.shape)
+    adj = O.adjoint(g, prm, r, S, m0, np.zeros(g.shape), 2, w)
+
+    def L(h):
+        m, p = m0 + h * dm, np.zeros(g.shape)
+        for _ in range(2):
+            m, p, _ = O.step(g, prm, r, S, m, p)
+        return float((w * m).sum())
+
+    h = 1e-6
+    fd = (L(h) - L(-h)) / (2 * h)
+    got = float((adj["dm0"] * dm).sum())
+    assert np.isfinite(got) and abs(got - fd) <= 1e-6 * (abs(fd) + np.abs(adj["dm0"]).sum())
