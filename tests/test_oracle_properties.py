@@ -192,3 +192,26 @@ def test_adjoint_directional_derivative_on_random_grids(n, seed):
     fd = (L(h) - L(-h)) / (2 * h)
     got = float((adj["dm0"] * dm).sum())
     assert np.isfinite(got) and abs(got - fd) <= 1e-6 * (abs(fd) + np.abs(adj["dm0"]).sum())
+
+
+@settings(max_examples=12, deadline=None, derandomize=True)
+@given(grids(dims=(2,)), seeds, st.floats(0.5, 1.5), st.sampled_from([0.0, 1e-3, 10.0]),
+       st.booleans())
+def test_run_reports_consistent_results(g, seed, gamma, eps, stop_on_energy):
+    """Algorithm 1's loop (Section 2.5): a stop reason from the list, at most
+    max_steps bodies, one energy and one Delta m per completed body, finite
+    values, and the energy rule naming the step before the one that saw it."""
+    rng, m, r = fields(g, seed)
+    S = rng.standard_normal(g.shape)
+    prm = O.Params(c=2.0, D=0.05, gamma=gamma, dt=1e-3, cg_rtol=1e-10)
+    res = O.run(g, prm, r, S, m, max_steps=5, eps=eps, stop_on_energy=stop_on_energy)
+    assert res.reason in (0, 1, 2) and 1 <= res.steps <= 5
+    assert len(res.energies) == len(res.delta_ms) == res.steps
+    assert all(np.isfinite(res.energies)) and all(np.isfinite(res.delta_ms))
+    if res.reason == 0:
+        assert res.steps == 5
+    if res.reason == 1:
+        assert eps > 0 and res.delta_ms[-1] <= eps
+    if res.reason == 2:
+        assert stop_on_energy and res.energies[-1] >= res.energies[-2]
+        assert res.energy_step == res.steps - 2
