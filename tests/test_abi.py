@@ -206,3 +206,38 @@ def test_error_codes_and_messages(lib):
     with pytest.raises(Bd.HuCaiError):
         Bd._check(Bd.HC_EINVAL, "x")
     Bd._check(Bd.HC_ENOCONV, "x", ok=(Bd.HC_OK, Bd.HC_ENOCONV))
+
+
+def test_grid_validation_matches_the_documented_rule(lib):
+    """hc_workspace_size accepts a grid exactly when include/hc.h says the
+    library supports it: 2D axes powers of two in [8, 4096]; 3D axes powers of
+    two in [8, 1024] with at most 2^28 points; lengths positive and finite."""
+    hyp = pytest.importorskip("hypothesis")
+    from hypothesis import given, settings, strategies as st
+    from paper_2606_06720_gb300 import _binding as Bd
+
+    def pow2_in(v, lo, hi):
+        return lo <= v <= hi and (v & (v - 1)) == 0
+
+    def supported(dim, n, L):
+        if not all(x > 0 and x != float("inf") for x in L[:dim]):
+            return False
+        if dim == 2:
+            return pow2_in(n[0], 8, 4096) and pow2_in(n[1], 8, 4096) and n[2] == 1
+        return all(pow2_in(v, 8, 1024) for v in n) and n[0] * n[1] * n[2] <= 1 << 28
+
+    axis = st.sampled_from([0, 1, 4, 6, 8, 12, 16, 64, 1000, 1024, 2048, 4096, 8192])
+    length = st.sampled_from([1.0, 0.25, 0.0, -1.0, float("inf")])
+
+    @settings(max_examples=300, deadline=None, derandomize=True)
+    @given(st.sampled_from([2, 3]), axis, axis, axis, length, length, length)
+    def check(dim, a, b, c, la, lb, lc):
+        n = (a, b, c if dim == 3 else 1)
+        L = (la, lb, lc if dim == 3 else 1.0)
+        g = Bd.hc_grid(dim, (C.c_int * 3)(*n), (C.c_double * 3)(*L))
+        p = Bd.hc_params(10.0, 0.05, 0.75, 1e-3, 1e-10, 100, 1, 0.0, 1e-4, 10, 0, None)
+        nb = C.c_size_t()
+        rc = Bd.hc_workspace_size(C.byref(g), C.byref(p), C.byref(nb))
+        assert (rc == 0) == supported(dim, n, L), (dim, n, L, rc)
+
+    check()
