@@ -241,3 +241,27 @@ def test_grid_validation_matches_the_documented_rule(lib):
         assert (rc == 0) == supported(dim, n, L), (dim, n, L, rc)
 
     check()
+
+
+def test_param_validation_matches_the_documented_rule(lib):
+    """hc_params is accepted exactly when precision is one of the three modes,
+    precond one of the two options, and c, D, gamma, dt are finite with dt >= 0."""
+    pytest.importorskip("hypothesis")
+    import math
+    from hypothesis import given, settings, strategies as st
+    from paper_2606_06720_gb300 import _binding as Bd
+    val = st.sampled_from([0.0, 1.0, -2.5, 1e-3, float("nan"), float("inf"), -float("inf")])
+
+    @settings(max_examples=300, deadline=None, derandomize=True)
+    @given(val, val, val, val, st.integers(-1, 3), st.integers(-1, 2))
+    def check(c, D, gamma, dt, precision, precond):
+        g = Bd.hc_grid(2, (C.c_int * 3)(64, 32, 1), (C.c_double * 3)(1.0, 1.0, 1.0))
+        p = Bd.hc_params(c, D, gamma, dt, 1e-10, 100, precision, 0.0, 1e-4, 10, 0, None,
+                         0, 0, 0, precond)
+        nb = C.c_size_t()
+        rc = Bd.hc_workspace_size(C.byref(g), C.byref(p), C.byref(nb))
+        ok = (precision in (0, 1, 2) and precond in (0, 1)
+              and all(math.isfinite(x) for x in (c, D, gamma, dt)) and dt >= 0)
+        assert (rc == 0) == ok, (c, D, gamma, dt, precision, precond, rc)
+
+    check()
