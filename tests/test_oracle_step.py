@@ -138,3 +138,22 @@ def test_step_reports_nonconvergence_but_advances():
     m2, p2, st = O.step(g, prm, r, S, m, np.zeros(g.shape))
     assert st.rc == O.ENOCONV and st.cg_iters == 2
     assert not np.array_equal(m2, m)
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """The oracle's parallel loops write disjoint entries and its sums run in a
+    fixed order, so a step gives bit-identical results on 1 and on 8 threads."""
+    import workloads as W
+    w = W.source_sink_2d(32, steps=1)
+    g = O.Grid(w.n, w.L)
+    prm = O.Params(c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, cg_rtol=1e-10)
+    before = O.get_threads()
+    try:
+        outs = []
+        for t in (1, 8):
+            O.set_threads(t)
+            outs.append(O.step(g, prm, w.r, w.S, w.m0, np.zeros(g.shape)))
+    finally:
+        O.set_threads(before)
+    (m1, p1, s1), (m8, p8, s8) = outs
+    assert np.array_equal(m1, m8) and np.array_equal(p1, p8) and s1.cg_iters == s8.cg_iters
