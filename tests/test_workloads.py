@@ -62,3 +62,25 @@ def test_seeded_inputs_repeat():
     assert np.array_equal(a.r, b.r) and np.array_equal(a.S, b.S) and np.array_equal(a.m0, b.m0)
     c = W.source_sink_2d(128, seed=1)
     assert not np.array_equal(a.m0, c.m0) and np.array_equal(a.r, c.r)
+
+
+def test_paper_inputs_at_chosen_nodes():
+    """Section 3's analytic inputs evaluated at nodes x = i/N, y = j/N, stored
+    at [j, i] (x along the last axis): m^A decays fast along y and slowly
+    along x (eq. m_ini_normal), m^B alike in both (eq. m_ini_symm), S_4 has
+    its source at the centre and sinks of weight 1/4 at the four (0.2|0.8,
+    0.2|0.8) points (eqs. S_4sinks*), S_int its constant sink pi/1000
+    (eq. SinternalSink)."""
+    import math
+    close = lambda a, b: abs(a - b) <= 1e-14 * abs(b)     # libm exp differs in the last bit
+    mA = W.paper_m_ini(64, "A")[0]
+    assert close(mA[32, 16], math.exp(-50 * 0.25 ** 2))       # x = 0.25, y = 0.5
+    assert close(mA[33, 32], math.exp(-1e4 * (1 / 64) ** 2))  # x = 0.5, y = 0.5 + 1/64
+    mB = W.paper_m_ini(64, "B")[0]
+    assert mB[32, 16] == mB[16, 32] and close(mB[32, 16], math.exp(-50 * 0.25 ** 2))
+    S4 = W.paper_S4(10)                                    # nodes at 0.2, 0.5 and 0.8
+    assert abs(S4[5, 5] - 1.0) < 1e-70
+    for j, i in ((2, 2), (2, 8), (8, 2), (8, 8)):
+        assert abs(S4[j, i] + 0.25) < 1e-70
+    Si = W.paper_Sint(10)
+    assert close(Si[5, 5], 1.0 - math.pi / 1000)
