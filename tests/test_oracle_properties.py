@@ -215,3 +215,24 @@ def test_run_reports_consistent_results(g, seed, gamma, eps, stop_on_energy):
     if res.reason == 2:
         assert stop_on_energy and res.energies[-1] >= res.energies[-2]
         assert res.energy_step == res.steps - 2
+
+
+@SETTINGS
+@given(grids(), seeds)
+def test_gradient_is_exact_below_the_nyquist_index(g, seed):
+    """Section 2.3.3's Fourier variables: for a trigonometric polynomial whose
+    modes all lie strictly below N/2 along every axis, the spectral gradient
+    equals the exact derivative, on odd and even grids alike."""
+    rng = np.random.default_rng(seed)
+    X = np.meshgrid(*[np.arange(N) * (L / N) for N, L in zip(g.n, g.L)][::-1], indexing="ij")[::-1]
+    f = np.zeros(g.shape)
+    df = np.zeros((g.dim,) + g.shape)
+    for _ in range(3):
+        k = [int(rng.integers(-((N - 1) // 2), (N - 1) // 2 + 1)) for N in g.n]
+        a, b = rng.standard_normal(2)
+        arg = sum(2 * np.pi * kk * Xa / L for kk, Xa, L in zip(k, X, g.L))
+        f += a * np.cos(arg) + b * np.sin(arg)
+        for ax in range(g.dim):
+            w = 2 * np.pi * k[ax] / g.L[ax]
+            df[ax] += w * (-a * np.sin(arg) + b * np.cos(arg))
+    assert np.allclose(O.gradient(g, f), df, atol=1e-11 * (1 + np.abs(df).max()))
