@@ -236,3 +236,19 @@ def test_gradient_is_exact_below_the_nyquist_index(g, seed):
             w = 2 * np.pi * k[ax] / g.L[ax]
             df[ax] += w * (-a * np.sin(arg) + b * np.cos(arg))
     assert np.allclose(O.gradient(g, f), df, atol=1e-11 * (1 + np.abs(df).max()))
+
+
+@settings(max_examples=10, deadline=None, derandomize=True)
+@given(grids(), seeds, st.integers(1, 4))
+def test_run_without_stops_equals_repeated_steps(g, seed, k):
+    """Algorithm 1's loop with both rules off is k loop bodies: the state it
+    returns is bit-identical to stepping by hand."""
+    rng, m, r = fields(g, seed)
+    S = rng.standard_normal(g.shape)
+    prm = O.Params(c=2.0, D=0.05, gamma=0.75, dt=1e-3, cg_rtol=1e-10)
+    res = O.run(g, prm, r, S, m, max_steps=k, eps=0.0, stop_on_energy=False)
+    mm, pp = m.copy(), np.zeros(g.shape)
+    for _ in range(k):
+        mm, pp, _ = O.step(g, prm, r, S, mm, pp)
+    assert res.reason == 0 and res.steps == k
+    assert np.array_equal(res.m, mm) and np.array_equal(res.p, pp)
