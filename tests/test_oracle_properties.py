@@ -252,3 +252,33 @@ def test_run_without_stops_equals_repeated_steps(g, seed, k):
         mm, pp, _ = O.step(g, prm, r, S, mm, pp)
     assert res.reason == 0 and res.steps == k
     assert np.array_equal(res.m, mm) and np.array_equal(res.p, pp)
+
+
+@settings(max_examples=8, deadline=None, derandomize=True)
+@given(st.tuples(st.integers(3, 5), st.integers(3, 5), st.integers(3, 5)), seeds)
+def test_adjoint_directional_derivative_on_random_3d_grids(n, seed):
+    """As the 2D case: <dL/dm0, dm> against a central difference along a random
+    dm, on small 3D grids, and <dL/dS, dS> along a random source direction."""
+    g = O.Grid(n, (1.0, 0.7, 1.3))
+    rng = np.random.default_rng(seed)
+    m0 = rng.uniform(0.3, 1.0, (3,) + g.shape)
+    r = rng.uniform(0.05, 0.3, g.shape)
+    S = rng.standard_normal(g.shape)
+    prm = O.Params(c=2.0, D=0.1, gamma=1.0, dt=2e-3, cg_rtol=1e-14, cg_maxit=2000)
+    w = rng.standard_normal(m0.shape)
+    dm, dS = rng.standard_normal(m0.shape), rng.standard_normal(g.shape)
+    adj = O.adjoint(g, prm, r, S, m0, np.zeros(g.shape), 2, w)
+
+    def L(hm, hs):
+        m, p = m0 + hm * dm, np.zeros(g.shape)
+        for _ in range(2):
+            m, p, _ = O.step(g, prm, r, S + hs * dS, m, p)
+        return float((w * m).sum())
+
+    h = 1e-6
+    fd_m = (L(h, 0) - L(-h, 0)) / (2 * h)
+    fd_s = (L(0, h) - L(0, -h)) / (2 * h)
+    got_m = float((adj["dm0"] * dm).sum())
+    got_s = float((adj["dS"] * dS).sum())
+    assert abs(got_m - fd_m) <= 1e-6 * (abs(fd_m) + np.abs(adj["dm0"]).sum())
+    assert abs(got_s - fd_s) <= 1e-6 * (abs(fd_s) + np.abs(adj["dS"]).sum())
