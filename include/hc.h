@@ -118,7 +118,10 @@ typedef struct {
    *   energy  = E_h(m) for the m the step started from, with that m's own pressure (the p the
    *             step solved): D^2/2 ||grad m||^2 + c^2/2 ||r^(1/2) grad p||^2
    *             + c^2/2 ||m . grad p||^2 + 1/(2 gamma) || |m|^gamma ||^2, gradients by the
-   *             spectral derivative of the scheme;
+   *             spectral derivative of the scheme.  At gamma = 0 the last term is
+   *             sum h ln|m|, its gradient-flow limit (the gamma = 0 relaxation term of
+   *             eq. 1.1b is the m-gradient of ln|m|), and -inf when some |m| = 0; the
+   *             energy rule then stops a run, as -inf < -inf is false;
    *   delta_m = ||m_new - m_old||_2 / (dt ||m_old||_2) of the step. */
   double energy;
   double delta_m;
@@ -357,7 +360,9 @@ void hc_batch_destroy(hc_batch* batch);
  *   nx, ny: powers of two in [8, 4096] with nx*ny <= HC_NOALLOC_MAX_POINTS;
  *           anything else (or a null pointer) returns HC_EINVAL.
  *   stream: cudaStream_t (NULL: legacy default stream); the call only enqueues
- *           work on it and returns.  CUDA failures return HC_ECUDA.
+ *           work on it and returns.  CUDA failures of its own launches return
+ *           HC_ECUDA; a non-sticky error left pending on the calling thread by
+ *           earlier work is cleared on entry (cudaGetLastError), not reported.
  * Scratch lives in one fixed 640 KiB static device array of the library
  * (present on every GPU the process uses, until the process exits); the call
  * allocates nothing and calls no allocating routine.  All calls share that

@@ -29,7 +29,10 @@
  *   R10 discrete L2 norms in the energy carry the quadrature weight h_x h_y [h_z];
  *   R11 Lie splitting, every substep with the full dt, order A -> R -> D;
  *   R21 at gamma = 0 the energy's relaxation term |m|^(2 gamma)/(2 gamma) is
- *       undefined (1/0) and is left out; the scheme itself is defined there.
+ *       1/0; the energy takes its gradient-flow limit there, sum h ln|m|
+ *       ((|m|^(2 gamma) - 1)/(2 gamma) -> ln|m|, whose m-gradient m/|m|^2 is the
+ *       gamma = 0 relaxation term of eq. (1.1b); the constant |Omega|/(2 gamma)
+ *       is dropped).  A point with m = 0 makes it -inf.
  *
  * What pins each function (tests/test_oracle_*.py). Every value there comes
  * from the mathematics or a library routine, not from this file. No function
@@ -625,13 +628,16 @@ double or_energy(const or_grid* g, const or_params* prm, const double* r, const 
     }
     e_r += r[q] * g2;
     e_act += mg * mg;
-    e_rel += pow(m2, prm->gamma); /* (|m|^gamma)^2 */
+    if (prm->gamma != 0.0)
+      e_rel += pow(m2, prm->gamma); /* (|m|^gamma)^2 */
+    else
+      e_rel += 0.5 * log(m2); /* ln|m| (R21); log(0) = -inf */
   }
   free(gp);
   free(gm);
   double c2 = prm->c * prm->c;
-  /* R21: at gamma = 0 the relaxation term |m|^(2 gamma) / (2 gamma) is undefined; it is left out */
-  const double rel = prm->gamma != 0.0 ? e_rel / (2.0 * prm->gamma) : 0.0;
+  /* R21: at gamma = 0 the relaxation term is sum ln|m| (its gradient-flow limit) */
+  const double rel = prm->gamma != 0.0 ? e_rel / (2.0 * prm->gamma) : e_rel;
   return h * (0.5 * prm->D * prm->D * e_diff + 0.5 * c2 * e_r + 0.5 * c2 * e_act + rel);
 }
 

@@ -604,7 +604,8 @@ int push_config(hc_ctx* c) {
   for (int a = 0; a < c->dim; ++a) h *= c->grid.L[a] / (double)c->grid.n[a];
   cfg.e_coef[0] = h * c->prm.D * c->prm.D / 2.0;
   cfg.e_coef[1] = h * c->prm.c * c->prm.c / 2.0;
-  cfg.e_coef[2] = c->prm.gamma != 0.0 ? h / (2.0 * c->prm.gamma) : 0.0;
+  // gamma = 0: the split step sums ln|m| in place of |m|^(2 gamma)
+  cfg.e_coef[2] = c->prm.gamma != 0.0 ? h / (2.0 * c->prm.gamma) : h;
   cfg.dt = c->prm.dt;
   // refined: FP32 first sweep when the warm start is off by more than 1e-5 ||S||
   cfg.first32_min2 = (c->refined && !c->prm.fp64_first_residual) ? 1e-10 : 0.0;

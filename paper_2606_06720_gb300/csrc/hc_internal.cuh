@@ -131,7 +131,7 @@ struct SolveState {
   unsigned int ticket[8];    // last-CTA tickets, one per reduction site
   // Diagnostics of Section 2.5, accumulated by the split step when diag != 0.
   // A step solves p[m^k] and so evaluates E_h(m^k) with its own pressure.
-  double dsum[3];            // running step: sum r|g|^2, sum (m.g)^2, sum |m|^(2 gamma); m = m^k, g = grad p[m^k]
+  double dsum[3];            // running step: sum r|g|^2, sum (m.g)^2, sum |m|^(2 gamma) (gamma = 0: sum ln|m|); m = m^k, g = grad p[m^k]
   double gm2;                // sum |grad m|^2 of the current m (derivative multipliers of reading R1)
   double gm2_next;           // the same for the m the running step produces
   double dm2;                // running step: sum |m^{k+1} - m^k|^2
@@ -139,7 +139,7 @@ struct SolveState {
   double energy;             // E_h(m^k) of the last completed step
   double energy_prev;        // the value before it
   double delta_m;            // Delta m of the last completed step
-  double e_coef[3];          // h D^2 / 2, h c^2 / 2, h / (2 gamma)  (h: cell volume)
+  double e_coef[3];          // h D^2 / 2, h c^2 / 2, h / (2 gamma) (h at gamma = 0)  (h: cell volume)
   double dt;
   double eps_dm;             // run mode: stop once delta_m <= eps_dm
   int dim;

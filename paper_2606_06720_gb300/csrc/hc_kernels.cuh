@@ -76,6 +76,8 @@ __device__ __forceinline__ float hc_expm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double hc_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float hc_pow(float x, float y) { return powf(x, y); }
 __device__ __forceinline__ double hc_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float hc_log(float x) { return logf(x); }
+__device__ __forceinline__ double hc_log(double x) { return log(x); }
 __device__ __forceinline__ float hc_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double hc_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ bool hc_finite(float x) { return isfinite(x); }
@@ -696,9 +698,16 @@ __device__ __forceinline__ void cg_alpha_from(SolveState* st, double gkg, double
   if (dq > 0 && isfinite(dq)) {
     st->alpha = st->rho / dq;
   } else {
+    // breakdown: <d, A d> is not positive (d without a component in the range
+    // of A) or not finite.  The plain solve then stops unconverged unless its
+    // residual already meets the tolerance; a refined inner solve leaves that
+    // verdict to the FP64 residual that follows it.
     st->alpha = 0;
     st->done = 1;
-    if (!isfinite(dq)) st->status = HC_ENONFINITE;
+    if (!isfinite(dq))
+      st->status = HC_ENONFINITE;
+    else if (!st->refined && st->rnorm2 > st->thresh2)
+      st->status = HC_ENOCONV;
   }
   st->first = 0;
 }
@@ -867,18 +876,28 @@ __global__ void __launch_bounds__(512) kp_row_apply(Geo<float> g, const cx<float
 }
 
 // Pointwise sums of the discrete energy (Section 2.5) at one point, from m^k
-// and g = grad p[m^k]: r |g|^2, (m.g)^2, |m|^(2 gamma).
+// and g = grad p[m^k]: r |g|^2, (m.g)^2, and |m|^(2 gamma), or at gamma = 0
+// ln|m|, the gradient-flow limit of (|m|^(2 gamma) - 1)/(2 gamma): the
+// gamma = 0 relaxation term m/|m|^2 is its m-gradient.  ln 0 = -inf is kept
+// out of the compensated float sums (inf - inf would give NaN there) and
+// applied to the thread's total instead, so the sum is -inf when any |m| = 0.
 template <typename T>
 struct EnergyAcc {
   DotAcc<T> er, ea, em;
+  bool zero = false;
   __device__ __forceinline__ void add(T r, T g2, T mg, T n2, T gamma) {
     er.add_prod(r, g2);
     ea.add_prod(mg, mg);
-    em.add_prod(n2 > (T)0 ? hc_pow(n2, gamma) : (T)0, (T)1);
+    if (gamma != (T)0)
+      em.add_prod(n2 > (T)0 ? hc_pow(n2, gamma) : (T)0, (T)1);
+    else if (n2 > (T)0)
+      em.add_prod(hc_log(n2), (T)0.5);
+    else
+      zero = true;
   }
   // every CTA calls this (the flag is grid-uniform); totals into st->dsum
   __device__ __forceinline__ void finish(double* partials, SolveState* st) {
-    double a[3] = {er.value(), ea.value(), em.value()}, t[3];
+    double a[3] = {er.value(), ea.value(), zero ? -HUGE_VAL : em.value()}, t[3];
     if (last_cta_sum<3>(a, partials, &st->ticket[TK_DIAG], t) && threadIdx.x == 0) {
       st->dsum[0] = t[0];
       st->dsum[1] = t[1];

@@ -61,6 +61,7 @@ int setup_device(int dev, void** addr) {
   if (!g_addr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return HC_ECUDA;
+    cudaGetLastError();  // a pending error of earlier work is not this set-up's
     hc::allow_smem(hc::k_row_r2c<double>);
     hc::allow_smem(hc::k_col_fwd<double, 1>);
     if (cudaGetLastError() != cudaSuccess) return HC_ECUDA;
@@ -82,6 +83,10 @@ extern "C" int hc_spectrum_noalloc(const double* f, double* out, int nx, int ny,
   int rc = setup_device(dev, &base);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  // A non-sticky error left pending on this thread by earlier work (the
+  // caller's or another library's) is consumed here, so that the check after
+  // the launches reports only this call's own launches.
+  cudaGetLastError();
   unsigned char* b = static_cast<unsigned char*>(base);
   cx<double>* inter = reinterpret_cast<cx<double>*>(b);
   cx<double>* twx = reinterpret_cast<cx<double>*>(b + kInterBytes);

@@ -25,13 +25,18 @@ def _factor(tok: str) -> float:
     return -v if neg else v
 
 
-def num(tok: str) -> float:
-    """A product or quotient of factors: decimals, pi, ln(k), sqrt(k)."""
+def _product(tok: str) -> float:
     parts = re.split(r"([*/])", tok.strip())
     v = _factor(parts[0])
     for op, f in zip(parts[1::2], parts[2::2]):
         v = v * _factor(f) if op == "*" else v / _factor(f)
     return v
+
+
+def num(tok: str) -> float:
+    """A sum of products or quotients of factors: decimals, pi, ln(k),
+    sqrt(k), inf."""
+    return sum(_product(t) for t in tok.strip().split("+"))
 
 
 def vec(tok: str) -> np.ndarray:

@@ -59,6 +59,38 @@ def test_energy_and_delta_m_per_step_match_oracle(hc, precision, dim):
             assert st.delta_m == pytest.approx(ref.delta_ms[k], rel=TOL_E[precision] * 10), k
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
+def test_gamma0_energy_is_the_log_term_like_the_oracle(hc, precision):
+    """Reading R21: at gamma = 0 the energy's relaxation term is h sum ln|m|.
+    With |m| kept away from 0 it is finite and matches the oracle step by step;
+    once the relaxation extinguishes points (|m|^2 < 2 dt) and diffusion leaves
+    a zero, it is -inf, and the energy rule stops the loop at the oracle's step."""
+    w = problem_2d()
+    w.gamma = 0.0
+    w.m0 = w.m0 + 0.5
+    g = O.Grid(w.n, w.L)
+    cast = (lambda a: a) if precision == "fp64" else (lambda a: a.astype(np.float32).astype(np.float64))
+    ref = O.run(g, oracle_prm(w), cast(w.r), w.S, cast(w.m0), max_steps=5, eps=0,
+                stop_on_energy=False)
+    assert all(np.isfinite(ref.energies))
+    with solver(hc, w, precision) as s:
+        for k in range(5):
+            st = s.step(1)
+            assert st.energy_valid == 1
+            assert st.energy == pytest.approx(ref.energies[k], rel=TOL_E[precision]), k
+    w = W.source_sink_2d(32, steps=10, gamma=0.0)
+    w.c, w.dt = 10.0, 0.05
+    g = O.Grid(w.n, w.L)
+    ref = O.run(g, oracle_prm(w), cast(w.r), w.S, cast(w.m0), max_steps=10, eps=0,
+                stop_on_energy=True)
+    assert ref.reason == 2 and np.isneginf(ref.energies[-1]) and np.isfinite(ref.energies[0])
+    with solver(hc, w, precision) as s:
+        st = s.run(10, eps=0, stop_on_energy=True)
+        assert st.stop_reason == hc.HC_STOP_ENERGY
+        assert st.steps == ref.steps and st.energy_step == ref.energy_step
+        assert np.isneginf(st.energy)
+
+
 def test_energy_validity_follows_the_diagnostics_switch(hc):
     """The energy of a state needs its gradient norm, computed by hc_set_m or
     by a step that ran with diagnostics on."""

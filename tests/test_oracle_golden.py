@@ -125,6 +125,8 @@ def test_number_and_field_grammar():
     assert num("pi*pi/3") == pytest.approx(math.pi ** 2 / 3)
     assert num("2/3") == pytest.approx(2 / 3)
     assert num("sqrt(0.5)") == pytest.approx(math.sqrt(0.5))
+    assert num("2*pi*pi+2*pi*pi*ln(2)") == pytest.approx(2 * math.pi ** 2 * (1 + math.log(2)))
+    assert num("-inf") == -math.inf
     f = field("0.5,2:cos:1:0,1:sin:0:1", (4, 4), (2 * math.pi, 2 * math.pi))
     assert f.shape == (4, 4)
     # x runs along the last axis: f[j, i] = 0.5 + 2 cos(x_i) + sin(y_j)

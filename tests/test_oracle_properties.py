@@ -131,6 +131,40 @@ def test_energy_scales_term_by_term(g, seed, gamma, D, lam):
 
 
 @SETTINGS
+@given(grids(), seeds, st.floats(1e-4, 0.3), st.floats(0.3, 3.0))
+def test_gamma0_energy_is_the_log_limit_and_relaxation_never_raises_it(g, seed, dt, lam):
+    """Reading R21: at gamma = 0 the relaxation term of the energy is
+    h sum ln|m|, the gamma -> 0 limit of h sum (|m|^(2 gamma) - 1)/(2 gamma).
+    (i) It is that limit: E_gamma(m) - |Omega|/(2 gamma) -> E_0(m), with an
+    O(gamma) gap. (ii) Scaling m by lam adds |Omega| ln lam. (iii) Pure
+    relaxation at gamma = 0 (the flow of that term) never raises it, and a
+    point it extinguishes makes it -inf."""
+    _, m, r = fields(g, seed)
+    p = np.zeros(g.shape)
+    vol = float(np.prod(g.L))
+
+    def E(gamma, mm):
+        return O.energy(g, O.Params(c=0.0, D=0.0, gamma=gamma, dt=dt), r, mm, p)
+
+    E0 = E(0.0, m)
+    assert np.isfinite(E0)
+    h = vol / g.npts
+    assert np.isclose(E0, h * np.log(np.linalg.norm(m, axis=0)).sum(), rtol=1e-12, atol=1e-12)
+    for gam in (1e-5, 1e-6):
+        gap = E(gam, m) - vol / (2 * gam) - E0
+        assert abs(gap) < 50 * gam * (vol + abs(E0) + 1)
+    assert np.isclose(E(0.0, lam * m), E0 + vol * np.log(lam), rtol=1e-11, atol=1e-11)
+    mk = m
+    for _ in range(4):
+        mn = O.relaxation(mk, 0.0, dt)
+        before, after = E(0.0, mk), E(0.0, mn)
+        assert after <= before or (np.isneginf(after) and np.isneginf(before))
+        if np.any(np.linalg.norm(mn, axis=0) == 0):
+            assert np.isneginf(after)
+        mk = mn
+
+
+@SETTINGS
 @given(grids(), seeds)
 def test_preconditioner_is_symmetric_positive_on_the_range(g, seed):
     """M^-1 of reading R3 (both options) is symmetric, positive on the

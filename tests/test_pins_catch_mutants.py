@@ -132,8 +132,10 @@ MUTANTS = [
     ("energy_one_derivative_direction", "q < (size_t)dim * npts; ++q) e_diff", "q < npts; ++q) e_diff"),
     ("energy_flow_term_factor", "0.5 * c2 * e_r +", "c2 * e_r +"),
     ("energy_flow_uses_m_squared", "mg += mc * gc;", "mg += mc * mc;"),
-    ("energy_divides_by_zero_gamma", "prm->gamma != 0.0 ? e_rel / (2.0 * prm->gamma) : 0.0",
-     "e_rel / (2.0 * prm->gamma)"),
+    ("energy_gamma0_drops_log_term", "prm->gamma != 0.0 ? e_rel / (2.0 * prm->gamma) : e_rel",
+     "prm->gamma != 0.0 ? e_rel / (2.0 * prm->gamma) : 0.0"),
+    ("energy_gamma0_log_of_m_squared", "e_rel += 0.5 * log(m2);", "e_rel += log(m2);"),
+    ("energy_gamma0_log_drops_zeros", "e_rel += 0.5 * log(m2);", "e_rel += m2 > 0 ? 0.5 * log(m2) : 0.0;"),
     ("energy_gamma_power", "e_rel += pow(m2, prm->gamma);", "e_rel += pow(m2, 2.0 * prm->gamma);"),
     # adjoint. Not listed, because they change nothing: dropping the projection of
     # lambda_p, a spectral divergence with no null-mode content; and dropping the final

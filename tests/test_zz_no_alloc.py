@@ -21,9 +21,11 @@ def test_noalloc_spectrum_matches_hc_spectrum_on_two_calls(hc):
     from paper_2606_06720_gb300 import _binding as Bd
     rng = np.random.default_rng(31)
     stream = torch.cuda.current_stream()
-    # the second call is smaller than the first: anything it read from the
-    # first call's scratch contents instead of its own would show up
-    for nx, ny in [(256, 256), (64, 32)]:
+    # each call is smaller than one before it: anything it read from an
+    # earlier call's scratch contents instead of its own would show up.  The
+    # extreme aspect ratios take the shared-memory opt-in of the row pass
+    # (4096 x 16) and a column tile clamped to one column (16 x 4096).
+    for nx, ny in [(256, 256), (4096, 16), (16, 4096), (64, 32), (8, 8)]:
         f = rng.standard_normal((ny, nx))
         with hc.Solver((nx, ny), (1.0, 1.0), c=1.0, D=0.1, gamma=1.0, dt=1e-3,
                        precision="fp64") as s:
