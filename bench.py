@@ -38,7 +38,9 @@ FP64_EQUAL_RTOL = 1e-4      # loosest plain-FP64 tolerance reaching m rel. L2 <=
 PRECOND = "kbar"
                             # (calibrated with --accuracy: rtol 1e-4 gives 5.9e-7, 1e-3 gives 2.2e-5)
 HBM_PEAK_FALLBACK = 6800.0  # GB/s, recipe fallback when MEASURED_PEAKS.json is absent
-FP64_PEAK_TFLOPS = 1.25     # nominal FP64 of GB300 (recipe table); a plain-ALU bound
+FP64_PEAK_NOMINAL = 1.25    # TFLOP/s, nominal FP64 of GB300 (recipe table): context only; the
+                            # FP64 kernels are reported against the measured FMA peak
+                            # (hc_fp64_fma_peak) taken in the same run
 
 # Algorithmic bytes moved per launch of each step kernel, in units of n = nx*ny
 # points (F4 = 4n bytes: one FP32 field, physical or packed spectral; F8 = 8n).
@@ -160,10 +162,11 @@ def fft_flops_per_point_3d(kernel: str, nx: int, ny: int, nz: int) -> float:
 
 
 def kernel_table(s, counts: dict, bytes_pp: dict, flops_pp, fp64_names: set, npts: int,
-                 reps: int, hbm_peak: float) -> dict:
+                 reps: int, hbm_peak: float, fp64_peak: float) -> dict:
     """Per-kernel CUDA-event durations (hc_time_kernel: back-to-back launches
     on the same data) with algorithmic GB/s and TFLOP/s and the fraction of
-    the kernel's roof: HBM for the FP32 kernels, nominal FP64 for the FP64 ones."""
+    the kernel's roof: HBM for the FP32 kernels, the measured FP64 FMA peak
+    for the FP64 ones."""
     kernels = {}
     for name, cnt in counts.items():
         kms = s.time_kernel(name, reps=reps)
@@ -174,7 +177,7 @@ def kernel_table(s, counts: dict, bytes_pp: dict, flops_pp, fp64_names: set, npt
         kernels[name] = {"ms": kms, "launches_per_step": cnt, "ms_per_step": kms * cnt,
                          "alg_GBs": gbs, "alg_TFLOPs": tfl,
                          "bound": "alu-df" if isdf else ("alu" if is64 else "hbm"),
-                         "frac": None if isdf else ((tfl / FP64_PEAK_TFLOPS) if is64
+                         "frac": None if isdf else ((tfl / fp64_peak) if is64
                                                     else (gbs / hbm_peak))}
     return kernels
 
@@ -253,7 +256,8 @@ class ClockSampler:
 def oracle_steps(n: int, steps: int, warm: int = 1):
     """Time `steps` oracle steps of the source/sink workload resampled at n^2,
     after `warm` untimed steps (so the timed steps are warm-started like the
-    GPU's).  Returns (seconds, threads, cg_iters)."""
+    GPU's), with the preconditioner the GPU legs use.  Returns (seconds,
+    threads, cg_iters)."""
     import numpy as np
     import oracle as O
     import workloads as W
@@ -261,7 +265,8 @@ def oracle_steps(n: int, steps: int, warm: int = 1):
     O.set_threads(threads)
     w = W.source_sink_2d(n)
     g = O.Grid(w.n, w.L)
-    prm = O.Params(c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, cg_rtol=CG_RTOL_REFINED, cg_maxit=2000)
+    prm = O.Params(c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, cg_rtol=CG_RTOL_REFINED, cg_maxit=2000,
+                   precond=1 if PRECOND == "kbar" else 0)
     m, p = w.m0.copy(), np.zeros(g.shape)
     for _ in range(warm):
         m, p, _ = O.step(g, prm, w.r, w.S, m, p)
@@ -293,23 +298,31 @@ def workload_config(extra: dict | None = None) -> dict:
 
 
 # ----------------------------------------------------------------- reference arm
+def reference_grid(steps: int) -> int:
+    """The reference arm's sample grid: the 2048^2 workload itself when its
+    oracle steps fit a few minutes (about 7 s per step on 16 cores), else the
+    same workload resampled at 1024^2 or 512^2."""
+    return N_GRID if steps <= 20 else (1024 if steps <= 80 else 512)
+
+
 def run_reference(args) -> None:
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    n = args.ref_n
+    n = args.ref_n or reference_grid(args.steps)
     K, Wm = args.steps, args.warmup
-    secs, threads, iters = oracle_steps(n, K, warm=max(Wm, 1))
+    secs, threads, iters = oracle_steps(n, K, warm=max(min(Wm, 3), 1))
     value = n * n * K / secs / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": K, "warmup": Wm, "ms_per_step": secs / K * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config({"preconditioner": "scalar kappa (-Laplacian), the oracle's "
-                                                        "default reading R3"}),
+        "config": workload_config({"precision": "FP64 (the CPU oracle)",
+                                   "sample_grid": [n, n]}),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"the same workload resampled at {n}x{n}; each timed step is one "
-                                   f"FP64 oracle step (warm-started, cg_rtol {CG_RTOL_REFINED})"},
+                         "sample": f"the same workload at {n}x{n}; each timed step is one FP64 "
+                                   f"oracle step (warm-started, cg_rtol {CG_RTOL_REFINED}, the "
+                                   f"Kbar preconditioner of the GPU legs)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "cg_iters_per_step": iters / K,
     }
@@ -318,42 +331,22 @@ def run_reference(args) -> None:
 
 # ----------------------------------------------------------------- accuracy calibration
 def run_accuracy(args) -> None:
-    import numpy as np
+    """The equal-accuracy calibration on its own, with more tolerances and
+    each leg's throughput."""
     import torch
     import workloads as W
+    import __graft_entry__
+    __graft_entry__._builder().build()
     import paper_2606_06720_gb300 as P
-    steps = args.acc_steps
-    w = W.source_sink_2d(N_GRID, steps=steps)
-
-    def run(precision, rtol):
-        with P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision=precision,
-                      cg_rtol=rtol, cg_maxit=5000, precond=PRECOND) as s:
-            s.set_r(w.r)
-            s.set_source(w.S)
-            s.set_m(w.m0)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st = s.step(steps)
-            dt = time.perf_counter() - t0
-            return s.get_m(), s.get_p(), st, dt
-
-    m_ref, p_ref, st_ref, _ = run("fp64", 1e-13)
-    out = {"steps": steps, "reference": "FP64 plain GPU, cg_rtol 1e-13", "runs": []}
-
-    def err(m):
-        return float(np.linalg.norm(m - m_ref) / np.linalg.norm(m_ref))
-
-    for precision, rtol in [("fp32_refined", CG_RTOL_REFINED), ("fp32_refined_df", CG_RTOL_REFINED),
-                            ("fp64", 1e-3), ("fp64", 1e-4), ("fp64", 1e-5), ("fp64", 1e-6)]:
-        m, p, st, secs = run(precision, rtol)
-        out["runs"].append({"precision": precision, "cg_rtol": rtol, "m_rel_l2": err(m),
-                            "mean_cg_iters": st.total_cg_iters / steps,
-                            "mpoint_steps_per_s": w.npts * steps / secs / 1e6})
+    out = equal_accuracy(P, W, torch.device("cuda", 0), args.acc_steps,
+                         [("fp32_refined", CG_RTOL_REFINED), ("fp32_refined_df", CG_RTOL_REFINED),
+                          ("fp64", 1e-3), ("fp64", 1e-4), ("fp64", 1e-5), ("fp64", 1e-6)],
+                         timed=True)
     print(json.dumps(out), flush=True)
 
 
 # ----------------------------------------------------------------- diagnostics leg
-def run_diagnostics(P, W, args, dev, barrier, max_over_ranks, world, headline) -> dict:
+def run_diagnostics(P, W, args, dev, barrier, job_rate, headline) -> dict:
     """(a) The headline 2048^2 workload with the energy and Delta m computed
     every step, run as Algorithm 1's loop (hc_run: eps 1e-4, energy rule on;
     neither fires within the steps timed): its throughput against the
@@ -377,9 +370,9 @@ def run_diagnostics(P, W, args, dev, barrier, max_over_ranks, world, headline) -
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st = s.run(K, eps=1e-4, stop_on_energy=True)
-    secs = max_over_ranks(time.perf_counter() - t0)
+    torch.cuda.synchronize()
+    _, v = job_rate((time.perf_counter() - t0) * 1e3, w.npts * st.steps)
     s.close()
-    v = world * w.npts * st.steps / secs / 1e6
     out["headline_with_diagnostics"] = {
         "value": v, "unit": UNIT, "steps": st.steps, "stop_reason": st.stop_reason,
         "cost_vs_headline": headline / v - 1.0, "energy": st.energy, "delta_m": st.delta_m,
@@ -397,9 +390,10 @@ def run_diagnostics(P, W, args, dev, barrier, max_over_ranks, world, headline) -
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         stp = sp.run(Kp, eps=1e-4, stop_on_energy=True)
-        secs = max_over_ranks(time.perf_counter() - t0)
+        torch.cuda.synchronize()
+        _, vp = job_rate((time.perf_counter() - t0) * 1e3, wp.npts * stp.steps)
         sp.close()
-        out[name] = {"value": world * wp.npts * stp.steps / secs / 1e6, "unit": UNIT,
+        out[name] = {"value": vp, "unit": UNIT,
                      "steps": stp.steps, "t_end": stp.steps * wp.dt,
                      "stop_reason": stp.stop_reason, "energy": stp.energy,
                      "delta_m": stp.delta_m, "cg_iters_last_step": stp.cg_iters}
@@ -407,7 +401,7 @@ def run_diagnostics(P, W, args, dev, barrier, max_over_ranks, world, headline) -
 
 
 # ----------------------------------------------------------------- 3D leg
-def run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src) -> dict:
+def run_3d(P, W, args, dev, barrier, job_rate, hbm_peak, hbm_src, fp64_peak) -> dict:
     """The 256^3 source/sink workload (r = 0.1, sigma 0.05 pair at
     (0.3,0.5,0.5)/(0.7,0.5,0.5), m0 ~ U[0,0.5], c = 25, D = 0.03,
     gamma = 0.75, dt = 5e-4), FP32 + FP64 refinement to 1e-8, graph mode."""
@@ -433,8 +427,8 @@ def run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src) -
     e1.record(s.stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    ms = max_over_ranks(e0.elapsed_time(e1))
     npts = w.npts
+    ms, value = job_rate(e0.elapsed_time(e1), npts * K3)
     it = st.total_cg_iters / K3
     sw = st.total_sweeps / K3
     r64 = st.total_refine_residuals / K3  # FP64 residuals per step
@@ -448,13 +442,13 @@ def run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src) -
     kernels = kernel_table(s, counts, BYTES_PER_POINT_3D,
                            lambda k: fft_flops_per_point_3d(k, *w.n),
                            FP64_KERNELS["fp32_refined"], npts, max(3, args.kernel_reps // 3),
-                           hbm_peak)
+                           hbm_peak, fp64_peak)
     s.close()
     # dominant FP32 kernel of the CG iteration against HBM
     fp32 = [k for k in kernels if kernels[k]["bound"] == "hbm"]
     dom = max(fp32, key=lambda k: kernels[k]["ms_per_step"])
     dk = kernels[dom]
-    return {"value": world * npts * K3 / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms / K3,
+    return {"value": value, "unit": UNIT, "ms_per_step": ms / K3,
             "steps": K3, "grid": list(w.n),
             "workload": "source_sink_3d_%d: r=0.1, S=+G(0.3,0.5,0.5)-G(0.7,0.5,0.5) sigma 0.05 "
                         "minus mean, m0~U[0,0.5] seed 0, c=25 D=0.03 gamma=0.75 dt=5e-4; "
@@ -467,6 +461,54 @@ def run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src) -
                               "peak_source": hbm_src,
                               "alg_bytes": BYTES_PER_POINT_3D[dom] * npts},
             "kernels": kernels}
+
+
+# ----------------------------------------------------------------- equal accuracy
+# Plain-FP64 tolerances tried for "equal accuracy", loosest first: the timed
+# FP64 leg uses the loosest one whose m error after ACC_STEPS steps is within
+# ACC_BOUND of the tight FP64 reference (calibrated: 1e-3 misses, 1e-4 meets).
+FP64_RTOL_CANDIDATES = (1e-3, 1e-4, 1e-5)
+ACC_STEPS = 100
+ACC_BOUND = 1e-5
+
+
+def equal_accuracy(P, W, dev, steps: int, legs, timed: bool = False) -> dict:
+    """m after `steps` steps of the 2048^2 workload from m0, for each
+    (precision, cg_rtol) leg, against a plain FP64 run at cg_rtol 1e-13 on the
+    GPU: the relative L2 error of each leg (and, with timed, its throughput)."""
+    import numpy as np
+    import torch
+    w = W.source_sink_2d(N_GRID, steps=steps)
+
+    def run(precision, rtol):
+        with P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision=precision,
+                      cg_rtol=rtol, cg_maxit=5000, precond=PRECOND, device=str(dev)) as s:
+            s.set_r(w.r)
+            s.set_source(w.S)
+            s.set_m(w.m0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = s.step(steps)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            return s.get_m(), st, secs
+
+    m_ref, st_ref, _ = run("fp64", 1e-13)
+    out = {"steps": steps, "bound": ACC_BOUND,
+           "reference": f"plain FP64 on the GPU, cg_rtol 1e-13, {steps} steps from m0 "
+                        f"({st_ref.total_cg_iters / steps:.1f} CG iterations per step)",
+           "legs": []}
+    nref = float(np.linalg.norm(m_ref))
+    for precision, rtol in legs:
+        m, st, secs = run(precision, rtol)
+        leg = {"precision": precision, "cg_rtol": rtol,
+               "m_rel_l2": float(np.linalg.norm(m - m_ref)) / nref,
+               "mean_cg_iters": st.total_cg_iters / steps,
+               "rel_residual_last_step": st.rel_residual}
+        if timed:
+            leg["mpoint_steps_per_s"] = w.npts * steps / secs / 1e6
+        out["legs"].append(leg)
+    return out
 
 
 # ----------------------------------------------------------------- GB300 arm
@@ -491,12 +533,25 @@ def run_gb300(args) -> None:
         if world > 1:
             torch.distributed.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
+    def reduce(x: float, op) -> float:
         t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t, op=op)
         return float(t.item())
+
+    def max_over_ranks(x: float) -> float:
+        return x if world == 1 else reduce(x, torch.distributed.ReduceOp.MAX)
+
+    def sum_over_ranks(x: float) -> float:
+        return x if world == 1 else reduce(x, torch.distributed.ReduceOp.SUM)
+
+    def job_rate(local_ms: float, local_units: float):
+        """(slowest rank's ms, whole-job Mpoint-steps/s): the units every rank
+        processed over the slowest rank's time (aggregate)."""
+        ms, _, per_s = aggregate(local_ms, local_units, world, max_over_ranks, sum_over_ranks)
+        return ms, per_s / 1e6
+
+    # the FP64 residual kernels' roof, measured here (independent FMA chains on every SM)
+    fp64_peak = P.fp64_fma_peak(reps=5)
 
     w = W.source_sink_2d(N_GRID)
     K, Wm = args.steps, args.warmup
@@ -538,9 +593,8 @@ def run_gb300(args) -> None:
         barrier()
     launches = s.launch_count() - launches0
     ms = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(ms)
     npts = w.npts
-    value = world * npts * K / (ms_max / 1e3) / 1e6
+    ms_max, value = job_rate(ms, npts * K)
     iters_per_step = st.total_cg_iters / K
     sweeps_per_step = st.total_sweeps / K
 
@@ -558,15 +612,17 @@ def run_gb300(args) -> None:
         counts.update({"mid_grad": mid_per_step, "mid_apply": mid_per_step, "mid_div": mid_per_step})
     kernels = kernel_table(s, counts, BYTES_PER_POINT["fp32_refined"],
                            lambda k: fft_flops_per_point(k, *w.n), FP64_KERNELS["fp32_refined"],
-                           npts, args.kernel_reps, hbm_peak)
+                           npts, args.kernel_reps, hbm_peak, fp64_peak)
     bytes_step = sum(BYTES_PER_POINT["fp32_refined"][k] * npts * c for k, c in counts.items())
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     dk = kernels[dom]
     traffic = NCU_TRAFFIC_2048.get(dom) if w.n == (2048, 2048) else None
     if dk["bound"] == "alu":
         roofline = {"bound": "alu", "kernel": dom, "achieved": dk["alg_TFLOPs"],
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": dk["frac"],
-                    "traffic": traffic, "peak_source": "nominal FP64 (recipe table)",
+                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": dk["frac"],
+                    "traffic": traffic,
+                    "peak_source": "measured: FP64 FMA throughput of this GPU in this run "
+                                   "(hc_fp64_fma_peak; FMA = 2 flops); nominal 1.25",
                     "alg_bytes": BYTES_PER_POINT["fp32_refined"][dom] * npts}
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["alg_GBs"], "peak": hbm_peak,
@@ -594,9 +650,9 @@ def run_gb300(args) -> None:
             s.get_m(out=hm)
             s.get_p(out=hp)
         torch.cuda.synchronize()
-        secs = max_over_ranks(time.perf_counter() - t0)
+        _, ve = job_rate((time.perf_counter() - t0) * 1e3, npts * Ke)
         barrier()
-        e2e = {"value": world * npts * Ke / secs / 1e6, "unit": UNIT,
+        e2e = {"value": ve, "unit": UNIT,
                "h2d_bytes_per_step": 3 * npts * 8, "d2h_bytes_per_step": 3 * npts * 8,
                "steps": Ke, "path": "hc_set_m + hc_set_p (pinned host FP64) -> hc_step(1) -> "
                                     "hc_get_m + hc_get_p (pinned host FP64)"}
@@ -625,7 +681,7 @@ def run_gb300(args) -> None:
         std = sdf.step(Kd)
         b1.record(sdf.stream)
         torch.cuda.synchronize()
-        msd = max_over_ranks(b0.elapsed_time(b1))
+        msd, vdf = job_rate(b0.elapsed_time(b1), npts * Kd)
         kdf = {}
         for name in ("res_grad", "res_apply", "res_div"):
             kms = sdf.time_kernel(name, reps=args.kernel_reps)
@@ -633,7 +689,7 @@ def run_gb300(args) -> None:
                          "alg_TFLOPs": fft_flops_per_point(name, *w.n) * npts / (kms / 1e3) / 1e12,
                          "alg_GBs": BYTES_PER_POINT["fp32_refined"][name] * npts / (kms / 1e3) / 1e9}
         sdf.close()
-        dfv = {"value": world * npts * Kd / (msd / 1e3) / 1e6, "unit": UNIT,
+        dfv = {"value": vdf, "unit": UNIT,
                "ms_per_step": msd / Kd, "steps": Kd,
                "cg_iters_per_step": std.total_cg_iters / Kd,
                "refine_sweeps_per_step": std.total_sweeps / Kd,
@@ -663,9 +719,9 @@ def run_gb300(args) -> None:
         stc = ss.step(Kc)
         c1.record(ss.stream)
         torch.cuda.synchronize()
-        msc = max_over_ranks(c0.elapsed_time(c1))
+        msc, vsc = job_rate(c0.elapsed_time(c1), npts * Kc)
         ss.close()
-        scal = {"value": world * npts * Kc / (msc / 1e3) / 1e6, "unit": UNIT,
+        scal = {"value": vsc, "unit": UNIT,
                 "ms_per_step": msc / Kc, "steps": Kc, "precond": "scalar kappa (-Laplacian)",
                 "cg_iters_per_step": stc.total_cg_iters / Kc,
                 "rel_residual_last_step": stc.rel_residual}
@@ -706,12 +762,12 @@ def run_gb300(args) -> None:
         sts = batch.step(Ks)
         c1.record(stream)
         torch.cuda.synchronize()
-        mss = max_over_ranks(c0.elapsed_time(c1))
-        pts = sum(wi.npts for wi in sws)
+        pts = sum(wi.npts for wi in sws)  # this rank's shard
+        mss, vsw = job_rate(c0.elapsed_time(c1), pts * Ks)
         batch.close()
         for si in solvers:
             si.close()
-        sweep = {"value": world * pts * Ks / (mss / 1e3) / 1e6, "unit": UNIT,
+        sweep = {"value": vsw, "unit": UNIT,
                  "ms_per_step": mss / Ks, "steps": Ks, "instances": 48,
                  "instances_per_rank": len(sws),
                  "workload": "48 instances: 16x128^2, 16x256^2, 16x512^2; (c,D,gamma) over "
@@ -726,7 +782,7 @@ def run_gb300(args) -> None:
     if not args.no_adjoint:
         wa = W.source_sink_2d(1024, gamma=0.75)
         wt = W.source_sink_2d(1024, gamma=0.75, seed=1)
-        Ka, every = args.adj_steps, max(1, args.adj_steps // 3)
+        Ka, every = args.adj_steps, max(1, min(args.adj_every, args.adj_steps))
         sa = P.Solver(wa.n, wa.L, c=wa.c, D=wa.D, gamma=wa.gamma, dt=wa.dt,
                       precision="fp32_refined", cg_rtol=CG_RTOL_REFINED, cg_maxit=2000,
                       precond=PRECOND, device=str(dev))
@@ -751,32 +807,45 @@ def run_gb300(args) -> None:
         t0 = time.perf_counter()
         grads = sa.adjoint(Ka, lamT, every=every)
         torch.cuda.synchronize()
-        secs = max_over_ranks(time.perf_counter() - t0)
+        msa, vadj = job_rate((time.perf_counter() - t0) * 1e3, wa.npts * Ka)
         sa.close()
-        adjv = {"value": world * wa.npts * Ka / secs / 1e6, "unit": UNIT,
-                "ms_per_step": secs / Ka * 1e3, "steps": Ka, "checkpoint_every": every,
-                "workload": "1024x1024 source/sink, gamma=0.75, FP32 + FP64 refinement; loss "
-                            "||m(T) - m_target||^2, m_target from the seed-1 m0; the time covers "
-                            "the checkpointed forward, the segment recomputation and the reverse "
-                            "sweep (gradients for c^2, D^2, r, S, m0)",
+        adjv = {"value": vadj, "unit": UNIT,
+                "ms_per_step": msa / Ka, "steps": Ka, "checkpoint_every": every,
+                "workload": "1024x1024 source/sink, gamma=0.75, c=25, D=0.02, dt=5e-4, FP32 + FP64 "
+                            "refinement; loss ||m(T) - m_target||^2, m_target from a forward run "
+                            "from the seed-1 m0; the time covers the checkpointed forward, the "
+                            "segment recomputation and the reverse sweep (gradients for c^2, D^2, "
+                            "r, S, m0)",
                 "dL_dc2": grads["dc2"], "dL_dD2": grads["dD2"]}
 
     # ---- diagnostics (Section 2.5) and Algorithm 1's loop with its stopping rules
     diag = None
     if not args.no_diag:
-        diag = run_diagnostics(P, W, args, dev, barrier, max_over_ranks, world, value)
+        diag = run_diagnostics(P, W, args, dev, barrier, job_rate, value)
 
     # ---- 3D: the 256^3 source/sink problem (d = 3), FP32 + FP64 refinement
     three_d = None
     if not args.no_3d:
-        three_d = run_3d(P, W, args, dev, barrier, max_over_ranks, world, hbm_peak, hbm_src)
+        three_d = run_3d(P, W, args, dev, barrier, job_rate, hbm_peak, hbm_src, fp64_peak)
+
+    # ---- equal accuracy (every rank runs its own replica): the refined path
+    # and the plain FP64 path at each candidate tolerance, 100 steps from m0,
+    # against a plain FP64 run at cg_rtol 1e-13
+    acc = None
+    fp64_rtol = FP64_EQUAL_RTOL
+    if not args.no_fp64:
+        acc = equal_accuracy(P, W, dev, ACC_STEPS,
+                             [("fp32_refined", CG_RTOL_REFINED)] +
+                             [("fp64", r) for r in FP64_RTOL_CANDIDATES])
+        ok = [leg["cg_rtol"] for leg in acc["legs"][1:] if leg["m_rel_l2"] <= ACC_BOUND]
+        fp64_rtol = max(ok) if ok else min(FP64_RTOL_CANDIDATES)
 
     # ---- plain FP64 path at equal accuracy
     fp64 = None
     if not args.no_fp64:
         K64 = max(3, K // 20)
         s64 = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp64",
-                       cg_rtol=FP64_EQUAL_RTOL, cg_maxit=5000, precond=PRECOND,
+                       cg_rtol=fp64_rtol, cg_maxit=5000, precond=PRECOND,
                        use_graph=True, device=str(dev))
         s64.set_r(w.r)
         s64.set_source(w.S)
@@ -795,15 +864,15 @@ def run_gb300(args) -> None:
         st64 = s64.step(K64)
         a1.record(s64.stream)
         torch.cuda.synchronize()
-        ms64 = max_over_ranks(a0.elapsed_time(a1))
+        ms64, v64 = job_rate(a0.elapsed_time(a1), npts * K64)
         k64 = {}
         for name in ("cg_apply", "cg_div", "cg_grad"):
             kms = s64.time_kernel(name, reps=max(3, args.kernel_reps // 5))
-            k64[name] = {"ms": kms, "alg_TFLOPs": fft_flops_per_point(name, *w.n) * npts / (kms / 1e3) / 1e12}
+            tfl = fft_flops_per_point(name, *w.n) * npts / (kms / 1e3) / 1e12
+            k64[name] = {"ms": kms, "alg_TFLOPs": tfl, "frac_of_fp64_peak": tfl / fp64_peak}
         s64.close()
-        v64 = world * npts * K64 / (ms64 / 1e3) / 1e6
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / K64, "steps": K64,
-                "cg_rtol": FP64_EQUAL_RTOL, "cg_iters_per_step": st64.total_cg_iters / K64,
+                "cg_rtol": fp64_rtol, "cg_iters_per_step": st64.total_cg_iters / K64,
                 "kernels": k64, "speedup_of_refined": value / v64}
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
@@ -825,11 +894,18 @@ def run_gb300(args) -> None:
                                        "tuning_us": tune_report.get("us")}),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
+            "fp64_fma_peak_tflops": fp64_peak,
             "hbm_gbs": bytes_step * K / (ms / 1e3) / 1e9,
             "cg_iters_per_step": iters_per_step, "refine_sweeps_per_step": sweeps_per_step,
             "fp64_residuals_per_step": res64, "df_mid_residuals_per_step": mid_per_step,
-            "cg_iterations_per_s": world * iters_per_step * K / (ms_max / 1e3),
+            "cg_iterations_per_s": sum_over_ranks(iters_per_step * K) / (ms_max / 1e3),
             "rel_residual_last_step": st.rel_residual,
+            "m_rel_l2_refined": acc["legs"][0]["m_rel_l2"] if acc else None,
+            "m_rel_l2_fp64_plain": next((leg["m_rel_l2"] for leg in acc["legs"][1:]
+                                         if leg["cg_rtol"] == fp64_rtol), None) if acc else None,
+            "fp64_plain_value": fp64["value"] if fp64 else None,
+            "speedup_vs_fp64_plain": fp64["speedup_of_refined"] if fp64 else None,
+            "equal_accuracy": acc,
             "fp64_plain": fp64, "refined_df": dfv, "scalar_kappa": scal, "sweep": sweep,
             "adjoint": adjv,
             "three_d": three_d, "diagnostics": diag, "kernels": kernels,
@@ -847,8 +923,9 @@ def run_only_3d(args) -> None:
     import paper_2606_06720_gb300 as P
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)
-    out = run_3d(P, W, args, torch.device("cuda", 0), lambda: None, lambda x: x, 1, hbm_peak,
-                 "measured" if "hbm_gbs" in peaks else "fallback")
+    out = run_3d(P, W, args, torch.device("cuda", 0), lambda: None,
+                 lambda ms, units: (ms, units / (ms / 1e3) / 1e6), hbm_peak,
+                 "measured" if "hbm_gbs" in peaks else "fallback", P.fp64_fma_peak(reps=5))
     print(json.dumps(out), flush=True)
 
 
@@ -858,7 +935,9 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--ref-n", type=int, default=512, help="reference arm: oracle sample grid")
+    ap.add_argument("--ref-n", type=int, default=0,
+                    help="reference arm: oracle sample grid (0: 2048 up to 20 steps, 1024 up to "
+                         "80, else 512)")
     ap.add_argument("--kernel-reps", type=int, default=30)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -868,7 +947,8 @@ def main() -> None:
                     help="skip the leg with the default scalar-kappa preconditioner")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched 48-instance sweep leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
-    ap.add_argument("--adj-steps", type=int, default=60, help="adjoint leg: steps (C4 uses 500)")
+    ap.add_argument("--adj-steps", type=int, default=500, help="adjoint leg: steps")
+    ap.add_argument("--adj-every", type=int, default=50, help="adjoint leg: checkpoint spacing")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D (256^3) leg")
     ap.add_argument("--no-diag", action="store_true",
                     help="skip the diagnostics / stopping-rule leg")

@@ -298,6 +298,14 @@ int hc_time_kernel(hc_ctx* ctx, int kernel, int reps, double* ms_per_launch);
  * (graph launches count every kernel node). */
 int hc_launch_count(const hc_ctx* ctx, long long* count);
 
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (an FMA counts
+ * two flops): the ALU roof against which the FP64 residual kernels are
+ * reported.  One warm-up and `reps` timed launches of a kernel of independent
+ * FMA chains filling every SM, between CUDA events on `stream` (NULL: legacy
+ * default stream); synchronises that stream.  No context needed; allocates
+ * nothing.  Errors: HC_EINVAL (reps < 1, NULL tflops), HC_ECUDA. */
+int hc_fp64_fma_peak(int reps, void* stream, double* tflops);
+
 /* --- Adjoint (gradients of a loss on m(T)) --- */
 
 /* Bytes of device memory hc_adjoint needs for nsteps steps with a checkpoint

@@ -12,5 +12,5 @@ from ._binding import (  # noqa: F401
     HC_EBOUNDS, CHECKED,
     HC_FP32_REFINED, HC_FP32_REFINED_DF, HC_FP64_PLAIN, HC_OK, HC_STOP_DELTA_M, HC_STOP_ENERGY,
     HC_STOP_NONE, HC_STOP_STATUS, HC_PRECOND_SCALAR, HC_PRECOND_KBAR, HuCaiError, Solver,
-    StepStats, Batch, hucai_steps, lib, library_path,
+    StepStats, Batch, hucai_steps, lib, library_path, fp64_fma_peak,
 )

@@ -99,6 +99,7 @@ def _load() -> C.CDLL:
         "hc_split_step": ([P], C.c_int),
         "hc_spectrum": ([P, dp, dp, C.c_size_t], C.c_int),
         "hc_launch_count": ([P, C.POINTER(C.c_longlong)], C.c_int),
+        "hc_fp64_fma_peak": ([C.c_int, P, dp], C.c_int),
         "hc_destroy": ([P], None),
         "hc_strerror": ([C.c_int], C.c_char_p),
         "hc_last_cuda_error": ([], C.c_char_p),
@@ -141,6 +142,7 @@ hc_apply_operator = lib.hc_apply_operator
 hc_split_step = lib.hc_split_step
 hc_spectrum = lib.hc_spectrum
 hc_launch_count = lib.hc_launch_count
+hc_fp64_fma_peak = lib.hc_fp64_fma_peak
 hc_destroy = lib.hc_destroy
 hc_time_kernel = lib.hc_time_kernel
 hc_get_tuning = lib.hc_get_tuning
@@ -428,6 +430,16 @@ class Solver:
         v = C.c_longlong()
         _check(hc_launch_count(self.ctx, C.byref(v)), "hc_launch_count")
         return v.value
+
+
+def fp64_fma_peak(reps: int = 5, stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device in TFLOP/s
+    (hc_fp64_fma_peak): the ALU roof of the FP64 residual kernels."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    v = C.c_double()
+    _check(hc_fp64_fma_peak(int(reps), C.c_void_p(s.cuda_stream), C.byref(v)), "hc_fp64_fma_peak")
+    return v.value
 
 
 class Batch:

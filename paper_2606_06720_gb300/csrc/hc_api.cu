@@ -2824,4 +2824,9 @@ int hc_launch_count(const hc_ctx* c, long long* count) {
   return HC_OK;
 }
 
+int hc_fp64_fma_peak(int reps, void* stream, double* tflops) {
+  if (!tflops || reps < 1) return HC_EINVAL;
+  return hc::fma_peak(reps, (cudaStream_t)stream, tflops);
+}
+
 }  // extern "C"

@@ -400,6 +400,8 @@ void set_smem_limits_3d_df();
 // Opt every kernel of one precision in to the full shared memory per block.
 void set_smem_limits_f32();
 void set_smem_limits_f64();
+// FP64 FMA throughput of the current device (TFLOP/s, FMA = 2 flops), reps timed launches on s.
+int fma_peak(int reps, cudaStream_t s, double* tflops);
 void set_smem_limits_df();
 // Solve bookkeeping (one thread): configuration, step start (counters, kappa,
 // thresholds), step end (stats and status accumulation), accumulator reset.

@@ -187,4 +187,50 @@ void set_run(SolveState* st, int run_mode, double eps_dm, int stop_energy, cudaS
 }
 void run_gate(SolveState* st, cudaStream_t s) { k_run_gate<<<1, 1, 0, s>>>(st); }
 
+// FP64 FMA throughput probe (the ALU roof of the FP64 residual kernels).  Each
+// thread runs 8 independent chains a = a b + c, enough independent work to
+// keep the FP64 pipe busy; the sink store never happens but keeps the chains
+// live.  b slightly below 1 keeps the values bounded and normal.
+__device__ double g_fma_sink;
+__global__ void __launch_bounds__(256) k_fma_peak(int iters, double b, double c) {
+  double a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = 1e-3 * (double)(threadIdx.x + i);
+#pragma unroll 4
+  for (int k = 0; k < iters; ++k)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = fma(a[i], b, c);
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t += a[i];
+  if (t == -1.0) g_fma_sink = t;
+}
+
+int fma_peak(int reps, cudaStream_t s, double* tflops) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HC_ECUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HC_ECUDA;
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return HC_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return HC_ECUDA;
+  }
+  k_fma_peak<<<blocks, threads, 0, s>>>(iters, 0.9999999, 1e-7);  // warm-up
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < reps; ++r) k_fma_peak<<<blocks, threads, 0, s>>>(iters, 0.9999999, 1e-7);
+  cudaEventRecord(e1, s);
+  float ms = 0.f;
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess || !(ms > 0.f)) return HC_ECUDA;
+  const double flops = 2.0 * 8.0 * iters * (double)blocks * threads * reps;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  return HC_OK;
+}
+
 }  // namespace hc
