@@ -752,6 +752,7 @@ def run_gb300(args) -> None:
             for si in solvers:
                 autotune(si, reps=5)
         batch = P.Batch(solvers, stream=stream)
+        ncls, nbat = batch.classes()
         batch.step(3)
         Ks = max(5, K // 15)
         barrier()
@@ -775,7 +776,11 @@ def run_gb300(args) -> None:
                              "Gaussian S, m0~U[0,1] seed i, dt=1e-3, FP32 + FP64 refinement",
                  "cg_iters_per_step_mean": sum(x.total_cg_iters for x in sts) / Ks / len(sts),
                  "max_rel_residual": max(x.rel_residual for x in sts),
-                 "one_graph_launch_per_step": True}
+                 "one_graph_launch_per_step": True,
+                 "size_classes": ncls, "batched_instances": nbat,
+                 "launch_structure": "one graph launch per step; inside it, one kernel launch "
+                                     "per pass of the step per size class over all its "
+                                     "instances (blockIdx.y = instance)"}
 
     # ---- adjoint: loss ||m(T) - m_target||^2 on the 1024^2 problem, checkpointed
     adjv = None

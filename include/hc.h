@@ -340,16 +340,29 @@ typedef struct hc_batch hc_batch; /* opaque; refers to (does not own) its contex
 
 /* Group `count` existing contexts (any mix of grids, parameters and precisions)
  * so that one CUDA graph launch on `stream` advances every one of them by a
- * step: the graph holds each context's step as an independent chain with its
- * own device-side CG/refinement loops, so small grids run side by side.  The
- * contexts must stay alive and keep their grids until hc_batch_destroy;
- * changing a context's parameters or tuning afterwards requires rebuilding the
- * batch.  Errors: HC_EINVAL (null/duplicate contexts, count < 1), HC_ECUDA. */
+ * step.  2D HC_FP32_REFINED contexts that share a grid size (with the default
+ * residual switches) form a size class: the class's step is one chain of
+ * batched launches, one launch per pass of the step over all its members
+ * (each member with its own parameters, fields, tables and device-side CG and
+ * refinement loops; a loop runs until its slowest member is done, finished
+ * members skip).  The class runs the first member's launch shapes, without
+ * the persistent passes.  Every other context (3D, FP64, double-float, a size
+ * with a single context) keeps its own step chain.  All chains sit side by
+ * side in one graph.  The contexts must stay alive and keep their grids until
+ * hc_batch_destroy; changing a context's parameters or tuning afterwards
+ * requires rebuilding the batch.  The batch allocates a little device memory
+ * of its own (the members' records).
+ * Errors: HC_EINVAL (null/duplicate contexts, count < 1), HC_ENOMEM, HC_ECUDA. */
 int hc_batch_create(hc_batch** out, hc_ctx* const* ctxs, int count, void* stream);
+
+/* How the batch runs: the number of size classes and of contexts in them
+ * (the rest run their own chains).  Errors: HC_EINVAL. */
+int hc_batch_classes(const hc_batch* batch, int* classes, int* batched_members);
 
 /* nsteps batched steps.  stats (may be NULL) receives count entries, the last
  * step of each context.  Returns HC_OK or the first non-OK step status of any
- * context (as hc_step does). */
+ * context (as hc_step does).  A size class's kernel launches are added to the
+ * launch count (hc_launch_count) of its first member. */
 int hc_batch_step(hc_batch* batch, int nsteps, hc_step_stats* stats);
 
 void hc_batch_destroy(hc_batch* batch);

@@ -112,6 +112,7 @@ def _load() -> C.CDLL:
         "hc_batch_create": ([C.POINTER(P), C.POINTER(P), C.c_int, P], C.c_int),
         "hc_batch_step": ([P, C.c_int, C.POINTER(hc_step_stats)], C.c_int),
         "hc_batch_destroy": ([P], None),
+        "hc_batch_classes": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "hc_check_redzones": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)],
                               C.c_int),
         "hc_check_poke": ([P, C.c_int], C.c_int),
@@ -153,6 +154,7 @@ hc_adjoint = lib.hc_adjoint
 hc_batch_create = lib.hc_batch_create
 hc_batch_step = lib.hc_batch_step
 hc_batch_destroy = lib.hc_batch_destroy
+hc_batch_classes = lib.hc_batch_classes
 hc_check_redzones = lib.hc_check_redzones
 hc_check_poke = lib.hc_check_poke
 
@@ -443,8 +445,9 @@ def fp64_fma_peak(reps: int = 5, stream=None) -> float:
 
 
 class Batch:
-    """Several Solvers advanced together: one CUDA graph launch per step runs
-    every solver's step as an independent chain (hc_batch_*)."""
+    """Several Solvers advanced together by one CUDA graph launch per step
+    (hc_batch_*): 2D refined solvers of one grid size as a size class of
+    batched launches, the others as chains of their own."""
 
     def __init__(self, solvers, stream=None):
         import torch
@@ -454,6 +457,12 @@ class Batch:
         self.b = C.c_void_p()
         _check(hc_batch_create(C.byref(self.b), arr, len(self.solvers),
                                C.c_void_p(self.stream.cuda_stream)), "hc_batch_create")
+
+    def classes(self) -> tuple:
+        """(size classes, contexts in them) of hc_batch_classes."""
+        a, m = C.c_int(), C.c_int()
+        _check(hc_batch_classes(self.b, C.byref(a), C.byref(m)), "hc_batch_classes")
+        return a.value, m.value
 
     def step(self, nsteps: int = 1, allow=(HC_OK, HC_ENOCONV)):
         st = (hc_step_stats * len(self.solvers))()

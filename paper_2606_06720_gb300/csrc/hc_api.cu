@@ -2278,14 +2278,174 @@ int hc_adjoint(hc_ctx* c, int nsteps, int every, const double* lamT, double* dc2
 
 }  // extern "C"
 
+// ===================================================================== batches
+// A batch groups contexts so that one graph launch advances all of them by a
+// step.  Contexts of the 2D HC_FP32_REFINED path that share a grid size form a
+// size class: the class's step is one chain of batched launches (hc_batch.cu),
+// one launch per pass over all its members.  Any other context (3D, FP64
+// plain, double-float, a size with one member) keeps its own step chain.  All
+// chains sit side by side in the batch's graph.
+struct BatchClass {
+  std::vector<int> members;  // indices into hc_batch::ctx
+  hc::BShape sh;
+  hc::BInst* d_inst = nullptr;      // device copy of the members' BInst records
+  long long* d_launches = nullptr;  // the class's kernel launches (device counter)
+  long long launches_seen = 0;
+};
+
 struct hc_batch {
   std::vector<hc_ctx*> ctx;
-  std::vector<Handles> h;
+  std::vector<Handles> h;     // per-context chains
+  std::vector<int> cls_of;    // class of each context, -1: its own chain
+  std::vector<BatchClass> cls;
+  void* dmem;                 // device memory of the classes
   cudaStream_t stream;
   cudaStream_t cap;
   cudaGraphExec_t exec;
   bool ready;
 };
+
+namespace {
+
+bool batchable(const hc_ctx* c) {
+  return c->dim == 2 && c->refined && !c->df && c->mid_df;
+}
+
+// A member's record: its own tables, state and buffers, with the class's
+// launch shapes (non-persistent kernels).
+template <typename T>
+hc::Geo<T> class_geo(const hc::Geo<T>& own, const hc::Geo<T>& rep) {
+  hc::Geo<T> g = own;
+  g.tc = rep.tc;
+  g.ltc = rep.ltc;
+  g.rpc = rep.rpc;
+  g.lrpc = rep.lrpc;
+  g.pipe = 0;
+  g.rpipe = 0;
+  return g;
+}
+
+hc::BInst member_record(const hc_ctx* c, const hc_ctx* rep) {
+  hc::BInst b{};
+  b.gf = class_geo(c->gf, rep->gf);
+  b.gd = class_geo(c->gd, rep->gd);
+  b.gq = class_geo(c->gq, rep->gq);
+  b.st = c->st;
+  b.p64 = c->p64;
+  b.b64 = c->b64;
+  b.r64 = c->r64;
+  b.bq = c->bq;
+  b.b32 = c->b32;
+  b.r32 = c->r32;
+  b.d32 = c->d32;
+  b.q32 = c->q32;
+  b.x32 = c->x32;
+  b.G32 = c->G32;
+  b.G64 = c->G64;
+  b.mx = (float*)c->m[0];
+  b.my = (float*)c->m[1];
+  b.rf = (const float*)c->rf;
+  b.ns = c->ns;
+  b.cf = split_coef(c->prm);
+  return b;
+}
+
+// Capture one size class's step into `target` as a chain with no dependencies
+// on what `target` already holds (the batched counterpart of build_chain):
+//   step_begin, FP32 residual, flags, WHILE(first){CG, flags},
+//   IF(mid){double-float residual, flags, WHILE(mid_inner){CG, flags}},
+//   WHILE(outer){FP64 residual, flags, WHILE(inner){CG, flags}}, split, step_end.
+// Every conditional handle is created before the kernels that set it are
+// captured; flags sets each to the OR over the members.
+int build_class_chain(const BatchClass& bc, cudaStream_t s, cudaGraph_t target) {
+  const hc::BInst* bi = bc.d_inst;
+  const hc::BShape& sh = bc.sh;
+  long long* cnt = bc.d_launches;
+  Handles hh;
+  auto handle = [&](cudaGraph_t g, cudaGraphConditionalHandle* hd) -> int {
+    CU(cudaGraphConditionalHandleCreate(hd, g, 0, cudaGraphCondAssignDefault));
+    return HC_OK;
+  };
+  auto begin = [&](cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd) -> int {
+    CU(cudaStreamBeginCaptureToGraph(s, g, deps, nullptr, nd, cudaStreamCaptureModeThreadLocal));
+    return HC_OK;
+  };
+  auto end = [&](cudaGraph_t g, std::vector<cudaGraphNode_t>* tail) -> int {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (tail) {
+      CU(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+      tail->assign(deps, deps + nd);
+    }
+    cudaGraph_t same = g;
+    CU(cudaStreamEndCapture(s, &same));
+    return HC_OK;
+  };
+  auto cond = [&](cudaGraph_t g, const std::vector<cudaGraphNode_t>& after,
+                  cudaGraphConditionalHandle hd, bool is_if, cudaGraphNode_t* node,
+                  cudaGraph_t* body) -> int {
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hd;
+    p.conditional.type = is_if ? cudaGraphCondTypeIf : cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    CU(cudaGraphAddNode(node, g, after.data(), nullptr, after.size(), &p));
+    *body = p.conditional.phGraph_out[0];
+    return HC_OK;
+  };
+  // the body of an inner CG loop driven by handle hd
+  auto iter_body = [&](cudaGraph_t body, cudaGraphConditionalHandle hd) -> int {
+    int rc = begin(body, nullptr, 0);
+    if (rc) return rc;
+    hc::batch_cg_iter(bi, sh, s);
+    hc::batch_flags(bi, sh, hc::BF_LOOP, hd, 0, cnt, 5, s);
+    return end(body, nullptr);
+  };
+  int rc = handle(target, &hh.outer);
+  if (!rc) rc = handle(target, &hh.first);
+  if (!rc) rc = handle(target, &hh.mid);
+  if (rc) return rc;
+  std::vector<cudaGraphNode_t> tail;
+  rc = begin(target, nullptr, 0);
+  if (rc) return rc;
+  hc::batch_step_begin(bi, sh, hh.outer, s);
+  hc::batch_first_resid(bi, sh, s);
+  hc::batch_flags(bi, sh, hc::BF_FIRST, hh.first, hh.mid, cnt, 5, s);
+  rc = end(target, &tail);
+  if (rc) return rc;
+  cudaGraphNode_t first_node, mid_node, outer_node, inode;
+  cudaGraph_t body = nullptr, mbody = nullptr, obody = nullptr;
+  rc = cond(target, tail, hh.first, false, &first_node, &body);
+  if (!rc) rc = iter_body(body, hh.first);
+  if (!rc) rc = cond(target, {first_node}, hh.mid, true, &mid_node, &mbody);
+  if (!rc) rc = handle(mbody, &hh.mid_inner);
+  if (!rc) rc = begin(mbody, nullptr, 0);
+  if (rc) return rc;
+  hc::batch_mid_resid(bi, sh, s);
+  hc::batch_flags(bi, sh, hc::BF_LOOP, hh.mid_inner, 0, cnt, 4, s);
+  std::vector<cudaGraphNode_t> mtail;
+  rc = end(mbody, &mtail);
+  if (!rc) rc = cond(mbody, mtail, hh.mid_inner, false, &inode, &body);
+  if (!rc) rc = iter_body(body, hh.mid_inner);
+  if (!rc) rc = cond(target, {mid_node}, hh.outer, false, &outer_node, &obody);
+  if (!rc) rc = handle(obody, &hh.inner);
+  if (!rc) rc = begin(obody, nullptr, 0);
+  if (rc) return rc;
+  hc::batch_refine_resid(bi, sh, s);
+  hc::batch_flags(bi, sh, hc::BF_REFINE, hh.inner, hh.outer, cnt, 4, s);
+  std::vector<cudaGraphNode_t> otail;
+  rc = end(obody, &otail);
+  if (!rc) rc = cond(obody, otail, hh.inner, false, &inode, &body);
+  if (!rc) rc = iter_body(body, hh.inner);
+  if (!rc) rc = begin(target, &outer_node, 1);
+  if (rc) return rc;
+  hc::batch_split(bi, sh, s);
+  hc::batch_step_end(bi, sh, cnt, s);
+  return end(target, nullptr);
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -2301,6 +2461,8 @@ int hc_batch_create(hc_batch** out, hc_ctx* const* ctxs, int count, void* stream
   if (!b) return HC_ENOMEM;
   b->ctx.assign(ctxs, ctxs + count);
   b->h.assign(count, Handles{});
+  b->cls_of.assign(count, -1);
+  b->dmem = nullptr;
   b->stream = (cudaStream_t)stream;
   b->cap = nullptr;
   b->ready = false;
@@ -2309,13 +2471,68 @@ int hc_batch_create(hc_batch** out, hc_ctx* const* ctxs, int count, void* stream
       abort_capture(b->cap);
       cudaStreamDestroy(b->cap);
     }
+    if (b->dmem) cudaFree(b->dmem);
     delete b;
     return rc;
   };
+  // size classes: batchable contexts by grid size, two members at least
+  for (int i = 0; i < count; ++i) {
+    const hc_ctx* c = b->ctx[i];
+    if (!batchable(c) || b->cls_of[i] >= 0) continue;
+    BatchClass bc;
+    for (int k = i; k < count; ++k) {
+      const hc_ctx* o = b->ctx[k];
+      if (batchable(o) && b->cls_of[k] < 0 && o->nx == c->nx && o->ny == c->ny)
+        bc.members.push_back(k);
+    }
+    if (bc.members.size() < 2) continue;
+    for (int k : bc.members) b->cls_of[k] = (int)b->cls.size();
+    b->cls.push_back(bc);
+  }
+  if (!b->cls.empty()) {
+    size_t bytes = 0;
+    for (auto& bc : b->cls) bytes += 256 + bc.members.size() * sizeof(hc::BInst);
+    if (cudaMalloc(&b->dmem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HC_ENOMEM);
+    }
+    if (cudaMemset(b->dmem, 0, bytes) != cudaSuccess) return fail(HC_ECUDA);
+    char* p = static_cast<char*>(b->dmem);
+    hc::set_smem_limits_batch();
+    for (auto& bc : b->cls) {
+      const hc_ctx* rep = b->ctx[bc.members[0]];
+      bc.d_launches = reinterpret_cast<long long*>(p);
+      bc.d_inst = reinterpret_cast<hc::BInst*>(p + 256);
+      p += 256 + bc.members.size() * sizeof(hc::BInst);
+      std::vector<hc::BInst> recs;
+      for (int k : bc.members) recs.push_back(member_record(b->ctx[k], rep));
+      if (cudaMemcpy(bc.d_inst, recs.data(), recs.size() * sizeof(hc::BInst),
+                     cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(HC_ECUDA);
+      bc.sh.gf = recs[0].gf;
+      bc.sh.gd = recs[0].gd;
+      bc.sh.gq = recs[0].gq;
+      bc.sh.nb = (int)bc.members.size();
+    }
+    if (cudaGetLastError() != cudaSuccess) return fail(HC_ECUDA);
+  }
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(HC_ECUDA);
   cudaGraph_t graph;
   if (cudaGraphCreate(&graph, 0) != cudaSuccess) return fail(HC_ECUDA);
+  for (auto& bc : b->cls) {
+    for (int k : bc.members)
+      if (cudaStreamSynchronize(b->ctx[k]->stream) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(HC_ECUDA);
+      }
+    int rc = build_class_chain(bc, b->cap, graph);
+    if (rc) {
+      cudaGraphDestroy(graph);
+      return fail(rc);
+    }
+  }
   for (int i = 0; i < count; ++i) {
+    if (b->cls_of[i] >= 0) continue;
     hc_ctx* c = b->ctx[i];
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
       cudaGraphDestroy(graph);
@@ -2350,11 +2567,17 @@ int hc_batch_step(hc_batch* b, int nsteps, hc_step_stats* stats) {
   for (int i = 0; i < n; ++i) {
     hc_ctx* c = b->ctx[i];
     CU(cudaStreamSynchronize(c->stream));
-    int rc = use_handles(c, b->h[i]);
-    if (rc) return rc;
-    c->batch_handles = 1;
-    rc = set_graph_mode(c, 1);
-    if (rc) return rc;
+    if (b->cls_of[i] < 0) {
+      int rc = use_handles(c, b->h[i]);
+      if (rc) return rc;
+      c->batch_handles = 1;
+      rc = set_graph_mode(c, 1);
+      if (rc) return rc;
+    } else {
+      // a class member's own kernels leave the graph conditions alone
+      int rc = set_graph_mode(c, 0);
+      if (rc) return rc;
+    }
     hc::reset_accum(c->st, b->stream);
     c->launches += 1;
   }
@@ -2362,12 +2585,22 @@ int hc_batch_step(hc_batch* b, int nsteps, hc_step_stats* stats) {
   for (int i = 0; i < n; ++i)
     CU(cudaMemcpyAsync(b->ctx[i]->st_host, b->ctx[i]->st, sizeof(hc::SolveState),
                        cudaMemcpyDeviceToHost, b->stream));
+  std::vector<long long> cls_launches(b->cls.size(), 0);
+  for (size_t k = 0; k < b->cls.size(); ++k)
+    CU(cudaMemcpyAsync(&cls_launches[k], b->cls[k].d_launches, sizeof(long long),
+                       cudaMemcpyDeviceToHost, b->stream));
   CU(cudaStreamSynchronize(b->stream));
+  // a class's launches are counted once, on its first member
+  for (size_t k = 0; k < b->cls.size(); ++k) {
+    BatchClass& bc = b->cls[k];
+    b->ctx[bc.members[0]]->launches += cls_launches[k] - bc.launches_seen;
+    bc.launches_seen = cls_launches[k];
+  }
   int first_bad = HC_OK;
   for (int i = 0; i < n; ++i) {
     hc_ctx* c = b->ctx[i];
     const hc::SolveState& h = *c->st_host;
-    c->launches += graph_kernel_count(c, h);
+    if (b->cls_of[i] < 0) c->launches += graph_kernel_count(c, h);
     if (stats) fill_stats(c, &stats[i]);
     if (!first_bad && h.first_bad) first_bad = h.first_bad;
     int rc = set_graph_mode(c, 0);
@@ -2382,7 +2615,17 @@ void hc_batch_destroy(hc_batch* b) {
   else cudaDeviceSynchronize();
   if (b->ready) cudaGraphExecDestroy(b->exec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->dmem) cudaFree(b->dmem);
   delete b;
+}
+
+int hc_batch_classes(const hc_batch* b, int* classes, int* batched_members) {
+  if (!b || !classes || !batched_members) return HC_EINVAL;
+  *classes = (int)b->cls.size();
+  int m = 0;
+  for (auto& bc : b->cls) m += (int)bc.members.size();
+  *batched_members = m;
+  return HC_OK;
 }
 
 int hc_get_tuning(const hc_ctx* c, hc_tuning* t) {

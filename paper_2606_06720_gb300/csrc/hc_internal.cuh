@@ -245,6 +245,42 @@ struct SplitCoef {
   int gamma_is_one;
 };
 
+// One member of a batched size class of the parameter sweep (2D grids of one
+// size, HC_FP32_REFINED): everything a batched launch takes per instance.
+// A batched kernel runs one pass of the step for every member at once, member
+// blockIdx.y, with the member's own geometry tables, solve state and buffers.
+struct BInst {
+  Geo<float> gf;
+  Geo<double> gd;
+  Geo<df64> gq;
+  SolveState* st;
+  cx<double>* p64;        // pressure spectrum (FP64)
+  const cx<double>* b64;  // projected source spectrum (FP64)
+  cx<double>* r64;        // FP64 residual
+  const cx<df64>* bq;     // double-float copy of the source (mid-step residual)
+  const cx<float>* b32;   // FP32 copy of the source (column-major)
+  cx<float>* r32;         // inner CG vectors (column-major)
+  cx<float>* d32;
+  cx<float>* q32;
+  cx<float>* x32;
+  cx<float>* G32;         // FP32 gradient / flux scratch, two fields ns apart
+  cx<double>* G64;        // FP64 / double-float scratch, two fields ns apart
+  float* mx;
+  float* my;
+  const float* rf;
+  size_t ns;              // ny * H packed spectral values per field
+  SplitCoef cf;
+};
+
+// Launch geometry of a batched size class (every member has the same grid
+// and launch shapes): the host copies of one member's three geometries.
+struct BShape {
+  Geo<float> gf;
+  Geo<double> gd;
+  Geo<df64> gq;
+  int nb;                 // members
+};
+
 // Column-kernel modes.
 enum ColGradMode { CG_PLAIN = 0, CG_DUPDATE = 1, CG_ADDDELTA = 2 };
 enum ColDivMode { CD_PLAIN = 0, CD_CG = 1, CD_RESID = 2, CD_RESID_REFINE = 3, CD_RESID_FIRST = 4 };
@@ -409,6 +445,22 @@ void set_config(SolveState* st, SolveConfig cfg, cudaStream_t s);
 void step_begin(SolveState* st, int npts, cudaStream_t s);
 void step_end(SolveState* st, int refined, cudaStream_t s);
 void reset_accum(SolveState* st, cudaStream_t s);
+// Batched step of a size class (hc_batch.cu).  Each launches one kernel per
+// pass over all members (bi: device array of sh.nb members).  The members'
+// own kernels leave the graph conditions alone (graph_mode 0); batch_flags
+// sets them to the OR over members and counts the class's launches.
+void batch_step_begin(const BInst* bi, const BShape& sh, cudaGraphConditionalHandle h_outer,
+                      cudaStream_t s);
+void batch_first_resid(const BInst* bi, const BShape& sh, cudaStream_t s);
+void batch_cg_iter(const BInst* bi, const BShape& sh, cudaStream_t s);
+void batch_mid_resid(const BInst* bi, const BShape& sh, cudaStream_t s);
+void batch_refine_resid(const BInst* bi, const BShape& sh, cudaStream_t s);
+void batch_split(const BInst* bi, const BShape& sh, cudaStream_t s);
+void batch_step_end(const BInst* bi, const BShape& sh, long long* launches, cudaStream_t s);
+enum { BF_FIRST = 0, BF_LOOP = 1, BF_REFINE = 2 };
+void batch_flags(const BInst* bi, const BShape& sh, int kind, cudaGraphConditionalHandle h1,
+                 cudaGraphConditionalHandle h2, long long* launches, int kernels, cudaStream_t s);
+void set_smem_limits_batch();
 // Run mode of Algorithm 1's loop: stopping rules on/off, thresholds; clears halt.
 void set_run(SolveState* st, int run_mode, double eps_dm, int stop_energy, cudaStream_t s);
 // Sets st->h_gate to 1 unless a stopping rule fired (the gated step of hc_run).

@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(512) k_row_r2c(Geo<T> g, const T* __restrict__
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const cx<T>* B, T* a,
+__device__ __forceinline__ void row_c2r_body(Geo<T> g, const cx<T>* A, const cx<T>* B, T* a,
                                                  T* b, SolveState* st,
                                                  int kappa_update) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -686,6 +686,12 @@ __global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const
     }
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(512) k_row_c2r(Geo<T> g, const cx<T>* A, const cx<T>* B, T* a,
+                                                 T* b, SolveState* st,
+                                                 int kappa_update) {
+  row_c2r_body<T>(g, A, B, a, b, st, kappa_update);
+}
 
 // CG step length from the row pass.  With g = grad d (the physical gradient
 // this pass receives) and K = m m^T + r I, the spectral <d, A d> equals
@@ -719,7 +725,7 @@ __device__ __forceinline__ void cg_alpha_from(SolveState* st, double gkg, double
 // sharing twiddles, slot addresses and barriers (the CTA's rpc rows form
 // rpc / NV groups).
 template <typename T, typename Tm, bool DOT, int NV>
-__global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
+__device__ __forceinline__ void row_apply_body(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
                                                    const Tm* __restrict__ mx,
                                                    const Tm* __restrict__ my,
                                                    const Tm* __restrict__ rr, cx<T>* Qx, cx<T>* Qy,
@@ -796,6 +802,14 @@ __global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, co
     }
     if (last && threadIdx.x == 0) cg_alpha_from(st, t1[0], (double)g.nx * (double)g.ny);
   }
+}
+template <typename T, typename Tm, bool DOT, int NV>
+__global__ void __launch_bounds__(512) k_row_apply(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
+                                                   const Tm* __restrict__ mx,
+                                                   const Tm* __restrict__ my,
+                                                   const Tm* __restrict__ rr, cx<T>* Qx, cx<T>* Qy,
+                                                   SolveState* st) {
+  row_apply_body<T, Tm, DOT, NV>(g, Gx, Gy, mx, my, rr, Qx, Qy, st);
 }
 
 // Persistent FP32 row pass of the operator apply (g.rpipe): CTA b walks the
@@ -907,7 +921,7 @@ struct EnergyAcc {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_row_split(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
+__device__ __forceinline__ void row_split_body(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
                                                    const T* __restrict__ mx,
                                                    const T* __restrict__ my,
                                                    const T* __restrict__ rr, cx<T>* Mx, cx<T>* My,
@@ -969,6 +983,15 @@ __global__ void __launch_bounds__(512) k_row_split(Geo<T> g, const cx<T>* Gx, co
   if (diag) en.finish(g.partials, st);
   fft_canon<-1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   store_pair_r2c(v, slab, j, N, H, Mx + (size_t)y * H, My + (size_t)y * H);
+}
+template <typename T>
+__global__ void __launch_bounds__(512) k_row_split(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
+                                                   const T* __restrict__ mx,
+                                                   const T* __restrict__ my,
+                                                   const T* __restrict__ rr, cx<T>* Mx, cx<T>* My,
+                                                   SplitCoef cf,
+                                                   SolveState* st) {
+  row_split_body<T>(g, Gx, Gy, mx, my, rr, Mx, My, cf, st);
 }
 
 // ------------------------------------------------------------------ solve-state finalizers
@@ -1117,6 +1140,88 @@ __device__ __forceinline__ cx<T> add_delta_at(cx<Tin>* in, size_t idx, cx<float>
   }
 }
 
+// ------------------------------------------------------------------ step bookkeeping (one thread)
+// Step start: the preconditioner constants, counters and thresholds.
+__device__ __forceinline__ void step_begin_body(SolveState* st, int npts) {
+  // reading R3: Kbar = kappa I with kappa = mean(r) + mean(|m|^2) / d, or
+  // the caller's kappa; option HC_PRECOND_KBAR: Kbar = mean(m m^T) + mean(r) I.
+  // kappa = trace(Kbar) / d is reported.
+  const double kiso = st->user_kappa > 0 ? st->user_kappa
+                                         : st->mean_r + st->msum / (double)npts / (double)st->dim;
+  const bool aniso = st->user_kappa <= 0 && st->precond == HC_PRECOND_KBAR;
+  for (int e = 0; e < 6; ++e) {
+    const bool diag = e < 3, used = st->dim == 3 || e == 0 || e == 1 || e == 3;
+    double v = 0.0;
+    if (used) v = aniso ? st->mm[e] / (double)npts + (diag ? st->mean_r : 0.0) : (diag ? kiso : 0.0);
+    st->kbar[e] = v;
+  }
+  st->kappa = 0.0;
+  for (int a = 0; a < st->dim; ++a) st->kappa += st->kbar[a] / (double)st->dim;
+  st->msum_old = st->msum;
+  st->gm2_next_valid = 0;
+  st->first_used = 0;
+  st->mid_phase = 0;
+  st->mid_used = 0;
+  st->res_full = 0;
+  st->outer_thresh2 = st->outer_rtol2 * st->outer_b2;
+  st->it = 0;
+  st->total_it = 0;
+  st->sweeps = 0;
+  st->done = 0;
+  st->status = 0;
+  st->nonfinite = 0;
+  st->outer_done = 0;
+  st->first = 1;
+  if (!st->refined) st->thresh2 = st->outer_thresh2;
+  if (st->graph_mode && st->refined) cudaGraphSetConditional(st->h_outer, 1u);
+}
+
+// Diagnostics of Section 2.5 for the step that just ran from m^k: the energy
+// E_h(m^k) (with p[m^k], the pressure this step solved) and Delta m^{k+1}.
+// In run mode, the stopping rules of Algorithm 1's loop.
+__device__ __forceinline__ void step_end_body(SolveState* st, int refined) {
+  const int status = st->nonfinite ? HC_ENONFINITE : st->status;
+  st->step_status = status;
+  if (!st->first_bad && status) st->first_bad = status;
+  st->acc_iters += st->total_it;
+  st->acc_sweeps += st->sweeps;
+  st->acc_steps += 1;
+  if (st->diag) {
+    if (st->gm2_valid) {
+      st->energy_prev = st->energy;
+      st->energy = st->e_coef[0] * st->gm2 + st->e_coef[1] * (st->dsum[0] + st->dsum[1]) +
+                   st->e_coef[2] * st->dsum[2];
+      st->energy_valid = 1;
+      st->n_energy += 1;
+    } else {
+      st->energy_valid = 0;
+    }
+    st->delta_m = st->msum_old > 0 ? sqrt(st->dm2 / st->msum_old) / st->dt : 0.0;
+    st->gm2 = st->gm2_next;
+    st->gm2_valid = st->gm2_next_valid;
+  } else {
+    st->energy_valid = 0;
+    st->gm2_valid = 0;
+  }
+  if (st->run_mode && !st->halt) {
+    int reason = HC_STOP_NONE;
+    if (status == HC_ENONFINITE) {
+      reason = HC_STOP_STATUS;
+    } else if (st->diag && st->eps_dm > 0 && st->delta_m <= st->eps_dm) {
+      reason = HC_STOP_DELTA_M;
+    } else if (st->stop_energy && st->energy_valid && st->n_energy >= 2 &&
+               !(st->energy < st->energy_prev)) {
+      // this step evaluated E(m^k) >= E(m^{k-1}); the previous step made m^k
+      reason = HC_STOP_ENERGY;
+      st->energy_step = st->acc_steps - 2;
+    }
+    if (reason != HC_STOP_NONE) {
+      st->halt = 1;
+      st->stop_reason = reason;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ column kernels
 // Thread layout of a column CTA: b = packed column within the tile (fastest),
 // j = FFT thread index; slab q at sm + q * slab_elems + b with stride tc.
@@ -1145,7 +1250,7 @@ __device__ __forceinline__ int slab_elems(const Geo<T>& g) {
 }
 
 template <typename T, typename Tin, int MODE>
-__global__ void __launch_bounds__(512) k_col_grad(Geo<T> g, cx<Tin>* in, const cx<T>* __restrict__ rvec,
+__device__ __forceinline__ void col_grad_body(Geo<T> g, cx<Tin>* in, const cx<T>* __restrict__ rvec,
                                                   cx<T>* dio, const cx<float>* __restrict__ delta,
                                                   cx<T>* __restrict__ Gx, cx<T>* __restrict__ Gy,
                                                   SolveState* st, int check_done) {
@@ -1198,9 +1303,16 @@ __global__ void __launch_bounds__(512) k_col_grad(Geo<T> g, cx<Tin>* in, const c
     Gy[idx] = v[1][s];
   }
 }
+template <typename T, typename Tin, int MODE>
+__global__ void __launch_bounds__(512) k_col_grad(Geo<T> g, cx<Tin>* in, const cx<T>* __restrict__ rvec,
+                                                  cx<T>* dio, const cx<float>* __restrict__ delta,
+                                                  cx<T>* __restrict__ Gx, cx<T>* __restrict__ Gy,
+                                                  SolveState* st, int check_done) {
+  col_grad_body<T, Tin, MODE>(g, in, rvec, dio, delta, Gx, Gy, st, check_done);
+}
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restrict__ Qx,
+__device__ __forceinline__ void col_div_body(Geo<T> g, const cx<T>* __restrict__ Qx,
                                                  const cx<T>* __restrict__ Qy,
                                                  const cx<T>* __restrict__ d,
                                                  const cx<T>* __restrict__ bvec,
@@ -1294,6 +1406,15 @@ __global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restri
       resid_sweep_init(st, tot[0], tot[1], tot[2]);
   }
 }
+template <typename T, int MODE>
+__global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restrict__ Qx,
+                                                 const cx<T>* __restrict__ Qy,
+                                                 const cx<T>* __restrict__ d,
+                                                 const cx<T>* __restrict__ bvec,
+                                                 cx<T>* __restrict__ out, cx<float>* __restrict__ r32,
+                                                 cx<float>* __restrict__ delta32, SolveState* st) {
+  col_div_body<T, MODE>(g, Qx, Qy, d, bvec, out, r32, delta32, st);
+}
 
 // sum over one thread's spectral values of w |xi~|^2 (|v0|^2 + |v1|^2) (w the
 // Parseval weight of the packed column kx, xi~ the R1 derivative multipliers;
@@ -1325,7 +1446,7 @@ __device__ __forceinline__ void gradnorm_finish(double part, double scale, doubl
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My, SolveState* st) {  // in place
+__device__ __forceinline__ void col_heat_body(Geo<T> g, cx<T>* Mx, cx<T>* My, SolveState* st) {  // in place
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const ColIdx c = col_idx(g);
@@ -1389,6 +1510,10 @@ __global__ void __launch_bounds__(512) k_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My
     Mx[idx] = v[0][s];
     My[idx] = v[1][s];
   }
+}
+template <typename T>
+__global__ void __launch_bounds__(512) k_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My, SolveState* st) {
+  col_heat_body<T>(g, Mx, My, st);
 }
 
 template <typename T, int NV>
@@ -1799,7 +1924,7 @@ __global__ void __launch_bounds__(512) k_col_gradnorm(Geo<T> g, const cx<T>* __r
 
 // ------------------------------------------------------------------ CG update
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_cg_update(Geo<T> g, cx<T>* __restrict__ x,
+__device__ __forceinline__ void cg_update_body(Geo<T> g, cx<T>* __restrict__ x,
                                                    cx<T>* __restrict__ r,
                                                    const cx<T>* __restrict__ d,
                                                    const cx<T>* __restrict__ q, SolveState* st) {
@@ -1854,6 +1979,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_cg_update(Geo<T
     last = last_cta_sum<2>(acc, g.partials, &st->ticket[TK_UPDATE], tot);
   }
   if (last && threadIdx.x == 0) cg_step_finish(st, tot[0], tot[1]);
+}
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_cg_update(Geo<T> g, cx<T>* __restrict__ x,
+                                                   cx<T>* __restrict__ r,
+                                                   const cx<T>* __restrict__ d,
+                                                   const cx<T>* __restrict__ q, SolveState* st) {
+  cg_update_body<T>(g, x, r, d, q, st);
 }
 
 // ------------------------------------------------------------------ elementwise

@@ -74,85 +74,9 @@ __global__ void k_set_config(SolveState* st, SolveConfig c) {
   st->refined = c.refined;
 }
 
-__global__ void k_step_begin(SolveState* st, int npts) {
-  // reading R3: Kbar = kappa I with kappa = mean(r) + mean(|m|^2) / d, or
-  // the caller's kappa; option HC_PRECOND_KBAR: Kbar = mean(m m^T) + mean(r) I.
-  // kappa = trace(Kbar) / d is reported.
-  const double kiso = st->user_kappa > 0 ? st->user_kappa
-                                         : st->mean_r + st->msum / (double)npts / (double)st->dim;
-  const bool aniso = st->user_kappa <= 0 && st->precond == HC_PRECOND_KBAR;
-  for (int e = 0; e < 6; ++e) {
-    const bool diag = e < 3, used = st->dim == 3 || e == 0 || e == 1 || e == 3;
-    double v = 0.0;
-    if (used) v = aniso ? st->mm[e] / (double)npts + (diag ? st->mean_r : 0.0) : (diag ? kiso : 0.0);
-    st->kbar[e] = v;
-  }
-  st->kappa = 0.0;
-  for (int a = 0; a < st->dim; ++a) st->kappa += st->kbar[a] / (double)st->dim;
-  st->msum_old = st->msum;
-  st->gm2_next_valid = 0;
-  st->first_used = 0;
-  st->mid_phase = 0;
-  st->mid_used = 0;
-  st->res_full = 0;
-  st->outer_thresh2 = st->outer_rtol2 * st->outer_b2;
-  st->it = 0;
-  st->total_it = 0;
-  st->sweeps = 0;
-  st->done = 0;
-  st->status = 0;
-  st->nonfinite = 0;
-  st->outer_done = 0;
-  st->first = 1;
-  if (!st->refined) st->thresh2 = st->outer_thresh2;
-  if (st->graph_mode && st->refined) cudaGraphSetConditional(st->h_outer, 1u);
-}
+__global__ void k_step_begin(SolveState* st, int npts) { step_begin_body(st, npts); }
 
-// Diagnostics of Section 2.5 for the step that just ran from m^k: the energy
-// E_h(m^k) (with p[m^k], the pressure this step solved) and Delta m^{k+1}.
-// In run mode, the stopping rules of Algorithm 1's loop.
-__global__ void k_step_end(SolveState* st, int refined) {
-  const int status = st->nonfinite ? HC_ENONFINITE : st->status;
-  st->step_status = status;
-  if (!st->first_bad && status) st->first_bad = status;
-  st->acc_iters += st->total_it;
-  st->acc_sweeps += st->sweeps;
-  st->acc_steps += 1;
-  if (st->diag) {
-    if (st->gm2_valid) {
-      st->energy_prev = st->energy;
-      st->energy = st->e_coef[0] * st->gm2 + st->e_coef[1] * (st->dsum[0] + st->dsum[1]) +
-                   st->e_coef[2] * st->dsum[2];
-      st->energy_valid = 1;
-      st->n_energy += 1;
-    } else {
-      st->energy_valid = 0;
-    }
-    st->delta_m = st->msum_old > 0 ? sqrt(st->dm2 / st->msum_old) / st->dt : 0.0;
-    st->gm2 = st->gm2_next;
-    st->gm2_valid = st->gm2_next_valid;
-  } else {
-    st->energy_valid = 0;
-    st->gm2_valid = 0;
-  }
-  if (st->run_mode && !st->halt) {
-    int reason = HC_STOP_NONE;
-    if (status == HC_ENONFINITE) {
-      reason = HC_STOP_STATUS;
-    } else if (st->diag && st->eps_dm > 0 && st->delta_m <= st->eps_dm) {
-      reason = HC_STOP_DELTA_M;
-    } else if (st->stop_energy && st->energy_valid && st->n_energy >= 2 &&
-               !(st->energy < st->energy_prev)) {
-      // this step evaluated E(m^k) >= E(m^{k-1}); the previous step made m^k
-      reason = HC_STOP_ENERGY;
-      st->energy_step = st->acc_steps - 2;
-    }
-    if (reason != HC_STOP_NONE) {
-      st->halt = 1;
-      st->stop_reason = reason;
-    }
-  }
-}
+__global__ void k_step_end(SolveState* st, int refined) { step_end_body(st, refined); }
 
 __global__ void k_set_run(SolveState* st, int run_mode, double eps_dm, int stop_energy) {
   st->run_mode = run_mode;
