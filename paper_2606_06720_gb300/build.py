@@ -2,8 +2,9 @@
 
 libhc_gb300.so is the product. Its translation units compile in parallel and
 link into one shared object next to this file: the 2D and 3D kernels per
-precision, the batched sweep kernels, the host orchestration with the C ABI,
-and the allocation-free transform.
+precision, the batched sweep kernels, the mixed-radix kernels of grids that
+are not powers of two, the host orchestration with the C ABI, and the
+allocation-free transform.
 
 libhc_gb300_check.so is the bounds-checked build. HC_CHECK=1 changes only the
 host orchestration (hc_api.cu: guard zones after every workspace buffer, and
@@ -25,7 +26,8 @@ BUILD_DIR = os.path.join(HERE, "_build")
 CHECK_SOURCE = "hc_api.cu"   # the only unit HC_CHECK changes
 
 SOURCES = ["hc_kernels_f32.cu", "hc_kernels_f64.cu", "hc_kernels_df.cu", "hc_kernels3d_f32.cu",
-           "hc_kernels3d_f64.cu", "hc_kernels3d_df.cu", "hc_batch.cu", "hc_api.cu", "hc_noalloc.cu"]
+           "hc_kernels3d_f64.cu", "hc_kernels3d_df.cu", "hc_batch.cu", "hc_generic.cu", "hc_api.cu",
+           "hc_noalloc.cu"]
 HEADERS = ["hc_internal.cuh", "hc_kernels.cuh", "hc_kernels3d.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE] + ARCH

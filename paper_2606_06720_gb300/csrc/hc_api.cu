@@ -79,6 +79,27 @@ struct Layout {
 };
 
 bool is_pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+// Sizes of the generic 2D path: 4 .. 4096 points with no prime factor above 5.
+bool is_235_in(int v, int lo, int hi) {
+  if (v < lo || v > hi) return false;
+  for (int p : {2, 3, 5})
+    while (v % p == 0) v /= p;
+  return v == 1;
+}
+// A 2D grid that the power-of-two kernels do not take.
+bool generic_grid(const hc_grid* g) {
+  return g && g->dim == 2 && !(is_pow2_in(g->n[0], 8, 4096) && is_pow2_in(g->n[1], 8, 4096));
+}
+// Radix passes (4, 2, 3, 5) of a generic transform length; returns their count.
+int radices(int N, int* r) {
+  int np = 0;
+  while (N % 4 == 0) { r[np++] = 4; N /= 4; }
+  while (N % 2 == 0) { r[np++] = 2; N /= 2; }
+  while (N % 3 == 0) { r[np++] = 3; N /= 3; }
+  while (N % 5 == 0) { r[np++] = 5; N /= 5; }
+  return np;
+}
 int ilog2(int v) {
   int l = 0;
   while ((1 << l) < v) ++l;
@@ -99,7 +120,8 @@ struct hc_ctx {
   hc_params prm;
   Zones zones;  // guard zones of the workspace (bounds-checked build only)
   int dim;   // 2 or 3
-  int nx, ny, nz, H;  // nz = 1 in 2D
+  int gen;   // 1: a 2D grid whose sizes are not both powers of two (hc_generic.cu, FP64)
+  int nx, ny, nz, H;  // nz = 1 in 2D; H = spectral columns (nx/2 packed, nx/2 + 1 generic)
   size_t n;  // points
   size_t ns; // packed spectral values: nz * ny * H
   int refined;
@@ -150,6 +172,7 @@ struct hc_ctx {
   hc::Geo<float> gf;
   hc::Geo<double> gd;
   hc::Geo<df64> gq;  // double-float kernels (HC_FP32_REFINED_DF)
+  hc::GenGeo gg;     // generic sizes: geometry and tables of the mixed-radix kernels
   // The same geometry seen as ny*nz rows of length nx: the 2D row kernels
   // (R2C/C2R of single fields) run the x pass of a 3D grid through these.
   hc::Geo<float> rowf;
@@ -221,7 +244,36 @@ size_t max_reducing_ctas(const hc_ctx* c) {
   return m;
 }
 
+// Generic sizes (FP64 plain only): the solve state, the FP64 spectral vectors
+// of the unpacked half spectrum, the fields and the mixed-radix tables.
+void layout_generic(hc_ctx* c, Layout& L) {
+  const size_t n = c->n;
+  const size_t S64 = c->ns * sizeof(cx<double>);
+  c->st = L.take<hc::SolveState>(sizeof(hc::SolveState));
+  c->st_time = L.take<hc::SolveState>(sizeof(hc::SolveState));
+  c->partials = L.take<double>(sizeof(double) * hc::kPartialStride * max_reducing_ctas(c));
+  c->stage = L.take<double>(sizeof(double) * 2 * n);
+  c->p64 = L.take<cx<double>>(S64);
+  c->b64 = L.take<cx<double>>(S64);
+  c->r64 = L.take<cx<double>>(S64);
+  c->d64 = L.take<cx<double>>(S64);
+  c->q64 = L.take<cx<double>>(S64);
+  c->G64 = L.take<cx<double>>(2 * S64);
+  for (int k = 0; k < 2; ++k) c->m[k] = L.take<double>(sizeof(double) * n);
+  c->rf = L.take<double>(sizeof(double) * n);
+  c->twx_d = L.take<cx<double>>(sizeof(cx<double>) * c->nx);
+  c->twy_d = L.take<cx<double>>(sizeof(cx<double>) * c->ny);
+  c->kxd_d = L.take<double>(sizeof(double) * c->H);
+  c->kyd_d = L.take<double>(sizeof(double) * c->ny);
+  c->hx_d = L.take<double>(sizeof(double) * c->H);
+  c->hy_d = L.take<double>(sizeof(double) * c->ny);
+}
+
 void layout(hc_ctx* c, Layout& L) {
+  if (c->gen) {
+    layout_generic(c, L);
+    return;
+  }
   const size_t n = c->n;
   const int d = c->dim;
   const size_t S64 = c->ns * sizeof(cx<double>);
@@ -288,7 +340,7 @@ void layout(hc_ctx* c, Layout& L) {
 int check_grid(const hc_grid* g) {
   if (!g || (g->dim != 2 && g->dim != 3)) return HC_EINVAL;
   if (g->dim == 2) {
-    if (!is_pow2_in(g->n[0], 8, 4096) || !is_pow2_in(g->n[1], 8, 4096) || g->n[2] != 1)
+    if (!is_235_in(g->n[0], 4, 4096) || !is_235_in(g->n[1], 4, 4096) || g->n[2] != 1)
       return HC_EINVAL;
   } else {
     if (!is_pow2_in(g->n[0], 8, 1024) || !is_pow2_in(g->n[1], 8, 1024) ||
@@ -475,7 +527,57 @@ int scan_zones(cudaStream_t s, const char* base, const Zones& z, int* bad) {
   return HC_OK;
 }
 
+// Tables of the generic path: twiddles of both lengths, first-derivative
+// multipliers (Nyquist entry 0, reading R1) of the Hh = nx/2 + 1 columns and
+// the ny rows.
+int upload_tables_generic(hc_ctx* c) {
+  std::vector<double> re, im;
+  auto put_tw = [&](int N, cx<double>* dd) -> int {
+    twiddles(N, re, im);
+    std::vector<cx<double>> hd(N);
+    for (int m = 0; m < N; ++m) {
+      hd[m].x = re[m];
+      hd[m].y = im[m];
+    }
+    CU(cudaMemcpy(dd, hd.data(), sizeof(cx<double>) * N, cudaMemcpyHostToDevice));
+    return HC_OK;
+  };
+  int rc = put_tw(c->nx, c->twx_d);
+  if (!rc) rc = put_tw(c->ny, c->twy_d);
+  if (rc) return rc;
+  std::vector<double> kx(c->H), ky(c->ny);
+  for (int k = 0; k < c->H; ++k) kx[k] = xid(k, c->nx, c->grid.L[0]);
+  for (int k = 0; k < c->ny; ++k) ky[k] = xid(k, c->ny, c->grid.L[1]);
+  CU(cudaMemcpy(c->kxd_d, kx.data(), sizeof(double) * c->H, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->kyd_d, ky.data(), sizeof(double) * c->ny, cudaMemcpyHostToDevice));
+  return HC_OK;
+}
+
+void fill_generic_geo(hc_ctx* c) {
+  hc::GenGeo& g = c->gg;
+  g = hc::GenGeo{};
+  g.nx = c->nx;
+  g.ny = c->ny;
+  g.Hh = c->H;
+  g.nrx = radices(c->nx, g.rx);
+  g.nry = radices(c->ny, g.ry);
+  g.twx = c->twx_d;
+  g.twy = c->twy_d;
+  g.kxd = c->kxd_d;
+  g.kyd = c->kyd_d;
+  g.hx = c->hx_d;
+  g.hy = c->hy_d;
+  g.partials = c->partials;
+  // the grid-wide sums (hc::msum) take only nx, ny and the partials
+  c->gd = hc::Geo<double>{};
+  c->gd.nx = c->nx;
+  c->gd.ny = c->ny;
+  c->gd.partials = c->partials;
+  c->gd.npartials = (int)max_reducing_ctas(c);
+}
+
 int upload_tables(hc_ctx* c) {
+  if (c->gen) return upload_tables_generic(c);
   std::vector<double> re, im;
   auto put_tw = [&](int N, cx<float>* df, cx<double>* dd, cx<df64>* dq) -> int {
     twiddles(N, re, im);
@@ -536,6 +638,23 @@ int upload_tables(hc_ctx* c) {
 // 2D factor is their product.
 int upload_heat(hc_ctx* c) {
   const double D2dt = c->prm.D * c->prm.D * c->prm.dt;
+  if (c->gen) {  // FP64 only, kx = 0 .. nx/2 (H entries)
+    std::vector<double> hx(c->H), hy(c->ny);
+    for (int k = 0; k < c->H; ++k) {
+      const double x = xi(k, c->nx, c->grid.L[0]);
+      hx[k] = std::exp(-D2dt * x * x);
+    }
+    for (int k = 0; k < c->ny; ++k) {
+      const double y = xi(k, c->ny, c->grid.L[1]);
+      hy[k] = std::exp(-D2dt * y * y);
+    }
+    CU(cudaMemcpyAsync(c->hx_d, hx.data(), sizeof(double) * c->H, cudaMemcpyHostToDevice,
+                       c->stream));
+    CU(cudaMemcpyAsync(c->hy_d, hy.data(), sizeof(double) * c->ny, cudaMemcpyHostToDevice,
+                       c->stream));
+    CU(cudaStreamSynchronize(c->stream));  // host vectors die here
+    return HC_OK;
+  }
   std::vector<double> hx(c->H + 1), hy(c->ny);
   for (int k = 0; k <= c->H; ++k) {
     const double x = xi(k, c->nx, c->grid.L[0]);
@@ -657,6 +776,16 @@ void apply3_open(hc_ctx* c, hc::Geo<T>& g, int mode, cx<Tin>* in, const cx<T>* r
 
 // r = b - A x0 in FP64 plain mode; initialises the CG state.
 void plain_init(hc_ctx* c) {
+  if (c->gen) {
+    cx<double>* Gx = c->G64;
+    cx<double>* Gy = c->G64 + c->ns;
+    hc::gen_col_grad(c->gg, hc::CG_PLAIN, c->p64, nullptr, nullptr, Gx, Gy, c->st, 0, c->stream);
+    hc::gen_row_apply(c->gg, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1],
+                      (const double*)c->rf, Gx, Gy, nullptr, c->stream);
+    hc::gen_col_div(c->gg, hc::CD_RESID, Gx, Gy, c->b64, c->r64, c->st, c->stream);
+    c->launches += 3;
+    return;
+  }
   if (c->dim == 3) {
     apply3_open<double, double, double>(c, c->gd, hc::CG_PLAIN, c->p64, nullptr, nullptr, c->G64, 0);
     hc::z_div<double>(c->gd, hc::CD_RESID, tri(c->G64, c->ns), nullptr, c->b64, c->r64, nullptr,
@@ -677,6 +806,17 @@ void plain_init(hc_ctx* c) {
 }
 
 void plain_iter(hc_ctx* c) {
+  if (c->gen) {
+    cx<double>* Gx = c->G64;
+    cx<double>* Gy = c->G64 + c->ns;
+    hc::gen_col_grad(c->gg, hc::CG_DUPDATE, nullptr, c->r64, c->d64, Gx, Gy, c->st, 1, c->stream);
+    hc::gen_row_apply(c->gg, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1],
+                      (const double*)c->rf, Gx, Gy, c->st, c->stream);
+    hc::gen_col_div(c->gg, hc::CD_CG, Gx, Gy, nullptr, c->q64, c->st, c->stream);
+    hc::gen_cg_update(c->gg, c->p64, c->r64, c->d64, c->q64, c->st, c->stream);
+    c->launches += 4;
+    return;
+  }
   if (c->dim == 3) {
     apply3_open<double, double, double>(c, c->gd, hc::CG_DUPDATE, (cx<double>*)nullptr, c->r64,
                                         c->d64, c->G64, 1);
@@ -890,6 +1030,13 @@ void gradnorm3(hc_ctx* c, hc::Geo<T>& g, cx<T>* G, int into_next) {
 
 // sum |grad m|^2 of the current m into st->gm2 (after hc_set_m).
 void gradnorm_current(hc_ctx* c) {
+  if (c->gen) {
+    hc::gen_row_fwd(c->gg, (const double*)c->m[0], (const double*)c->m[1], c->G64,
+                    c->G64 + c->ns, c->stream);
+    hc::gen_col_fwd(c->gg, c->G64, c->G64 + c->ns, nullptr, nullptr, 0, 1, c->st, c->stream);
+    c->launches += 2;
+    return;
+  }
   if (c->dim == 3) {
     if (c->refined)
       gradnorm3<float>(c, c->gf, c->G32, 0);
@@ -940,6 +1087,17 @@ void split_step3(hc_ctx* c, hc::Geo<T>& g, cx<T>* G) {
 }
 
 void split_step(hc_ctx* c) {
+  if (c->gen) {
+    cx<double>* Gx = c->G64;
+    cx<double>* Gy = c->G64 + c->ns;
+    hc::gen_col_grad(c->gg, hc::CG_PLAIN, c->p64, nullptr, nullptr, Gx, Gy, c->st, 0, c->stream);
+    hc::gen_row_split(c->gg, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1],
+                      (const double*)c->rf, split_coef(c->prm), c->st, c->stream);
+    hc::gen_col_heat(c->gg, Gx, Gy, c->st, c->stream);
+    hc::gen_row_c2r(c->gg, Gx, Gy, (double*)c->m[0], (double*)c->m[1], c->st, 1, c->stream);
+    c->launches += 4;
+    return;
+  }
   if (c->dim == 3) {
     if (c->refined)
       split_step3<float>(c, c->gf, c->G32);
@@ -1325,13 +1483,15 @@ const char* hc_strerror(int code) {
 
 int hc_workspace_size(const hc_grid* grid, const hc_params* params, size_t* bytes) {
   if (check_grid(grid) || check_params(params) || !bytes) return HC_EINVAL;
+  if (generic_grid(grid) && params->precision != HC_FP64_PLAIN) return HC_ENOTSUP;
   hc_ctx tmp{};  // every member zero (or its default)
   tmp.grid = *grid;
   tmp.dim = grid->dim;
+  tmp.gen = generic_grid(grid) ? 1 : 0;
   tmp.nx = grid->n[0];
   tmp.ny = grid->n[1];
   tmp.nz = grid->dim == 3 ? grid->n[2] : 1;
-  tmp.H = tmp.nx / 2;
+  tmp.H = tmp.gen ? tmp.nx / 2 + 1 : tmp.nx / 2;
   tmp.n = (size_t)tmp.nx * tmp.ny * tmp.nz;
   tmp.ns = (size_t)tmp.nz * tmp.ny * tmp.H;
   tmp.refined = params->precision != HC_FP64_PLAIN;
@@ -1347,6 +1507,7 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   if (!out) return HC_EINVAL;
   *out = nullptr;
   if (check_grid(grid) || check_params(params)) return HC_EINVAL;
+  if (generic_grid(grid) && params->precision != HC_FP64_PLAIN) return HC_ENOTSUP;
   if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return HC_EINVAL;
   size_t need = 0;
   hc_workspace_size(grid, params, &need);
@@ -1357,10 +1518,11 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   c->prm = *params;
   apply_defaults(c->prm);
   c->dim = grid->dim;
+  c->gen = generic_grid(grid) ? 1 : 0;
   c->nx = grid->n[0];
   c->ny = grid->n[1];
   c->nz = grid->dim == 3 ? grid->n[2] : 1;
-  c->H = c->nx / 2;
+  c->H = c->gen ? c->nx / 2 + 1 : c->nx / 2;
   c->n = (size_t)c->nx * c->ny * c->nz;
   c->ns = (size_t)c->nz * c->ny * c->H;
   c->refined = params->precision != HC_FP64_PLAIN;
@@ -1390,27 +1552,32 @@ int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* 
   L.base = static_cast<char*>(c->ws);
   L.zones = &c->zones;
   layout(c, L);
-  fill_geo<float>(c, c->gf, c->twx_f, c->twy_f, c->kxd_f, c->kyd_f, c->hx_f, c->hy_f);
-  fill_geo<double>(c, c->gd, c->twx_d, c->twy_d, c->kxd_d, c->kyd_d, c->hx_d, c->hy_d);
-  c->gf.x2x = c->x2x_f;
-  c->gf.x2y = c->x2y_f;
-  c->gd.x2x = c->x2x_d;
-  c->gd.x2y = c->x2y_d;
-  fill_geo<df64>(c, c->gq, c->twx_q, c->twy_q, c->kxd_q, c->kyd_q, nullptr, nullptr);
-  c->gq.tc = c->gd.tc;
-  c->gq.ltc = c->gd.ltc;
-  if (c->dim == 3) {
-    fill_geo3<float>(c, c->gf, c->rowf, c->twz_f, c->kzd_f, c->hz_f);
-    fill_geo3<double>(c, c->gd, c->rowd, c->twz_d, c->kzd_d, c->hz_d);
-    fill_geo3<df64>(c, c->gq, c->rowq, c->twz_q, c->kzd_q, nullptr);
-  }
-  hc::set_smem_limits_f32();
-  hc::set_smem_limits_f64();
-  hc::set_smem_limits_df();
-  if (c->dim == 3) {
-    hc::set_smem_limits_3d_f32();
-    hc::set_smem_limits_3d_f64();
-    hc::set_smem_limits_3d_df();
+  if (c->gen) {
+    fill_generic_geo(c);
+    hc::set_smem_limits_gen();
+  } else {
+    fill_geo<float>(c, c->gf, c->twx_f, c->twy_f, c->kxd_f, c->kyd_f, c->hx_f, c->hy_f);
+    fill_geo<double>(c, c->gd, c->twx_d, c->twy_d, c->kxd_d, c->kyd_d, c->hx_d, c->hy_d);
+    c->gf.x2x = c->x2x_f;
+    c->gf.x2y = c->x2y_f;
+    c->gd.x2x = c->x2x_d;
+    c->gd.x2y = c->x2y_d;
+    fill_geo<df64>(c, c->gq, c->twx_q, c->twy_q, c->kxd_q, c->kyd_q, nullptr, nullptr);
+    c->gq.tc = c->gd.tc;
+    c->gq.ltc = c->gd.ltc;
+    if (c->dim == 3) {
+      fill_geo3<float>(c, c->gf, c->rowf, c->twz_f, c->kzd_f, c->hz_f);
+      fill_geo3<double>(c, c->gd, c->rowd, c->twz_d, c->kzd_d, c->hz_d);
+      fill_geo3<df64>(c, c->gq, c->rowq, c->twz_q, c->kzd_q, nullptr);
+    }
+    hc::set_smem_limits_f32();
+    hc::set_smem_limits_f64();
+    hc::set_smem_limits_df();
+    if (c->dim == 3) {
+      hc::set_smem_limits_3d_f32();
+      hc::set_smem_limits_3d_f64();
+      hc::set_smem_limits_3d_df();
+    }
   }
   int rc = HC_OK;
   if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess) rc = HC_ECUDA;
@@ -1526,6 +1693,13 @@ static int forward64_3d(hc_ctx* c, cx<double>* out, hc::SolveState* norm_into) {
 // Forward 2D transform of the FP64 field in stage -> projected FP64 spectrum.
 static int forward64(hc_ctx* c, cx<double>* out, hc::SolveState* norm_into) {
   if (c->dim == 3) return forward64_3d(c, out, norm_into);
+  if (c->gen) {
+    hc::gen_row_fwd(c->gg, c->stage, nullptr, c->G64, nullptr, c->stream);
+    hc::gen_col_fwd(c->gg, c->G64, nullptr, out, nullptr, 1, 0, norm_into, c->stream);
+    c->launches += 2;
+    CU(cudaGetLastError());
+    return HC_OK;
+  }
   if (c->df) {
     df64* phys = reinterpret_cast<df64*>(c->stage + c->n);
     cx<df64>* rows = reinterpret_cast<cx<df64>*>(c->G64);
@@ -1651,6 +1825,15 @@ int hc_get_m(hc_ctx* c, double* out, size_t count) {
 
 int hc_get_p(hc_ctx* c, double* out, size_t count) {
   if (!c || !out || count != c->n) return HC_EINVAL;
+  if (c->gen) {
+    hc::gen_col_inv(c->gg, c->p64, c->G64, 1.0 / (double)c->n, c->stream);
+    hc::gen_row_c2r(c->gg, c->G64, nullptr, c->stage, nullptr, nullptr, 0, c->stream);
+    c->launches += 2;
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(out, c->stage, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return HC_OK;
+  }
   if (c->dim == 3) {
     if (c->df) {
       auto* p = reinterpret_cast<cx<df64>*>(c->p64);
@@ -1835,7 +2018,13 @@ int hc_run(hc_ctx* c, int max_steps, double eps, int stop_on_energy, int* steps_
 
 int hc_gradient(hc_ctx* c, double* out, size_t count) {
   if (!c || !out || count != (size_t)c->dim * c->n) return HC_EINVAL;
-  if (c->dim == 3) {
+  if (c->gen) {
+    cx<double>* Gx = c->G64;
+    cx<double>* Gy = c->G64 + c->ns;
+    hc::gen_col_grad(c->gg, hc::CG_PLAIN, c->p64, nullptr, nullptr, Gx, Gy, c->st, 0, c->stream);
+    hc::gen_row_c2r(c->gg, Gx, Gy, c->stage, c->stage + c->n, nullptr, 0, c->stream);
+    c->launches += 2;
+  } else if (c->dim == 3) {
     gradient3(c);
   } else if (c->refined) {
     cx<float>* Gx = c->G32;
@@ -1867,7 +2056,19 @@ int hc_gradient(hc_ctx* c, double* out, size_t count) {
 int hc_apply_operator(hc_ctx* c, const double* f, double* out, size_t count) {
   if (!c || !f || !out || count != c->n) return HC_EINVAL;
   CU(cudaMemcpyAsync(c->stage, f, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
-  if (c->dim == 3) {
+  if (c->gen) {
+    cx<double>* Gx = c->G64;
+    cx<double>* Gy = c->G64 + c->ns;
+    hc::gen_row_fwd(c->gg, c->stage, nullptr, Gx, nullptr, c->stream);
+    hc::gen_col_fwd(c->gg, Gx, nullptr, c->d64, nullptr, 1, 0, nullptr, c->stream);
+    hc::gen_col_grad(c->gg, hc::CG_PLAIN, c->d64, nullptr, nullptr, Gx, Gy, c->st, 0, c->stream);
+    hc::gen_row_apply(c->gg, Gx, Gy, (const double*)c->m[0], (const double*)c->m[1],
+                      (const double*)c->rf, Gx, Gy, nullptr, c->stream);
+    hc::gen_col_div(c->gg, hc::CD_PLAIN, Gx, Gy, nullptr, c->q64, nullptr, c->stream);
+    hc::gen_col_inv(c->gg, c->q64, Gx, 1.0 / (double)c->n, c->stream);
+    hc::gen_row_c2r(c->gg, Gx, nullptr, c->stage, nullptr, nullptr, 0, c->stream);
+    c->launches += 7;
+  } else if (c->dim == 3) {
     if (c->refined) {
       float* fp = reinterpret_cast<float*>(c->q32);
       hc::convert<float, double>(c->stage, fp, c->n, c->stream);
@@ -1929,7 +2130,12 @@ int hc_spectrum(hc_ctx* c, const double* f, double* out, size_t count) {
   if (!c || !f || !out || count != c->n) return HC_EINVAL;
   CU(cudaMemcpyAsync(c->stage, f, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
   const size_t ns = c->ns;
-  if (c->dim == 3) {
+  if (c->gen) {
+    hc::gen_row_fwd(c->gg, c->stage, nullptr, c->G64, nullptr, c->stream);
+    hc::gen_col_fwd(c->gg, c->G64, nullptr, reinterpret_cast<cx<double>*>(c->stage), nullptr, 0, 0,
+                    nullptr, c->stream);
+    c->launches += 2;
+  } else if (c->dim == 3) {
     if (c->refined) {
       float* fp = reinterpret_cast<float*>(c->q32);
       auto Gt = tri(c->G32, ns);
@@ -2219,7 +2425,7 @@ extern "C" {
 
 int hc_adjoint_workspace_size(const hc_ctx* c, int nsteps, int every, size_t* bytes) {
   if (!c || !bytes || nsteps < 0 || every < 1) return HC_EINVAL;
-  if (c->df || c->dim != 2) return HC_ENOTSUP;
+  if (c->df || c->dim != 2 || c->gen) return HC_ENOTSUP;
   if (c->refined) {
     AdjLayout<float> a;
     adj_layout<float>(c, nsteps, every, nullptr, a);
@@ -2235,7 +2441,7 @@ int hc_adjoint_workspace_size(const hc_ctx* c, int nsteps, int every, size_t* by
 int hc_adjoint(hc_ctx* c, int nsteps, int every, const double* lamT, double* dc2, double* dD2,
                double* dr, double* dS, double* dm0, void* workspace, size_t workspace_bytes) {
   if (!c || !lamT || nsteps < 0 || every < 1) return HC_EINVAL;
-  if (c->df || c->dim != 2) return HC_ENOTSUP;
+  if (c->df || c->dim != 2 || c->gen) return HC_ENOTSUP;
   if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return HC_EINVAL;
   size_t need = 0;
   int rc = hc_adjoint_workspace_size(c, nsteps, every, &need);
@@ -2643,7 +2849,7 @@ int hc_get_tuning(const hc_ctx* c, hc_tuning* t) {
 
 int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
   if (!c || !t) return HC_EINVAL;
-  if (c->dim != 2) return HC_ENOTSUP;  // 3D launch shapes are fixed at creation
+  if (c->dim != 2 || c->gen) return HC_ENOTSUP;  // 3D and generic-size launch shapes are fixed
   int dev = 0, optin = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -2705,6 +2911,7 @@ int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
 
 int hc_time_kernel(hc_ctx* c, int kernel, int reps, double* ms_per_launch) {
   if (!c || !ms_per_launch || reps < 1 || kernel < 0 || kernel >= HC_K_COUNT) return HC_EINVAL;
+  if (c->gen) return HC_ENOTSUP;
   // scratch state: loop open, nothing converges, zero step lengths so the
   // repeated launches leave their inputs unchanged
   hc::SolveState init;

@@ -245,6 +245,22 @@ struct SplitCoef {
   int gamma_is_one;
 };
 
+// 2D grids whose sizes are not powers of two (hc_generic.cu): N = 2^a 3^b 5^c
+// per axis, FP64, unpacked half spectrum of Hh = nx/2 + 1 columns.
+constexpr int kGenMaxPasses = 24;
+struct GenGeo {
+  int nx, ny, Hh;
+  int rx[kGenMaxPasses], nrx;  // radices (2, 3, 4, 5) of the x transform, product nx
+  int ry[kGenMaxPasses], nry;  // the same along y
+  const cx<double>* twx;       // exp(-2 pi i m / nx), m < nx
+  const cx<double>* twy;       // exp(-2 pi i m / ny), m < ny
+  const double* kxd;           // first-derivative multipliers, kx < Hh (0 at the Nyquist index)
+  const double* kyd;           // the same, ky < ny
+  const double* hx;            // heat factor exp(-D^2 xi_x^2 dt), kx < Hh
+  const double* hy;            // exp(-D^2 xi_y^2 dt), ky < ny
+  double* partials;            // per-CTA FP64 partial sums
+};
+
 // One member of a batched size class of the parameter sweep (2D grids of one
 // size, HC_FP32_REFINED): everything a batched launch takes per instance.
 // A batched kernel runs one pass of the step for every member at once, member
@@ -461,6 +477,34 @@ enum { BF_FIRST = 0, BF_LOOP = 1, BF_REFINE = 2 };
 void batch_flags(const BInst* bi, const BShape& sh, int kind, cudaGraphConditionalHandle h1,
                  cudaGraphConditionalHandle h2, long long* launches, int kernels, cudaStream_t s);
 void set_smem_limits_batch();
+// The generic-size kernels (hc_generic.cu), FP64: column gradient (mode
+// CG_PLAIN from `in`, CG_DUPDATE the CG direction update), row apply (st: the
+// CG variant with alpha), column divergence (CD_PLAIN, CD_CG, CD_RESID), CG
+// update, the split step's row, heat and back-transform passes, and the plain
+// transforms of the boundary (row forward, column forward with projection or
+// gradient norm, column inverse).
+void gen_col_grad(const GenGeo& g, int mode, const cx<double>* in, const cx<double>* rvec,
+                  cx<double>* dio, cx<double>* Gx, cx<double>* Gy, SolveState* st, int check_done,
+                  cudaStream_t s);
+void gen_row_apply(const GenGeo& g, const cx<double>* Gx, const cx<double>* Gy, const double* mx,
+                   const double* my, const double* r, cx<double>* Qx, cx<double>* Qy,
+                   SolveState* st, cudaStream_t s);
+void gen_col_div(const GenGeo& g, int mode, const cx<double>* Qx, const cx<double>* Qy,
+                 const cx<double>* b, cx<double>* out, SolveState* st, cudaStream_t s);
+void gen_cg_update(const GenGeo& g, cx<double>* x, cx<double>* r, const cx<double>* d,
+                   const cx<double>* q, SolveState* st, cudaStream_t s);
+void gen_row_split(const GenGeo& g, cx<double>* Gx, cx<double>* Gy, const double* mx,
+                   const double* my, const double* r, SplitCoef cf, SolveState* st, cudaStream_t s);
+void gen_col_heat(const GenGeo& g, cx<double>* Mx, cx<double>* My, SolveState* st, cudaStream_t s);
+void gen_row_c2r(const GenGeo& g, const cx<double>* A, const cx<double>* B, double* a, double* b,
+                 SolveState* st, int kappa_update, cudaStream_t s);
+void gen_row_fwd(const GenGeo& g, const double* a, const double* b, cx<double>* A, cx<double>* B,
+                 cudaStream_t s);
+void gen_col_fwd(const GenGeo& g, const cx<double>* in0, const cx<double>* in1, cx<double>* out0,
+                 cx<double>* out1, int project, int gradnorm, SolveState* st, cudaStream_t s);
+void gen_col_inv(const GenGeo& g, const cx<double>* in, cx<double>* out, double scale,
+                 cudaStream_t s);
+void set_smem_limits_gen();
 // Run mode of Algorithm 1's loop: stopping rules on/off, thresholds; clears halt.
 void set_run(SolveState* st, int run_mode, double eps_dm, int stop_energy, cudaStream_t s);
 // Sets st->h_gate to 1 unless a stopping rule fired (the gated step of hc_run).

@@ -920,6 +920,36 @@ struct EnergyAcc {
   }
 };
 
+// Activation then relaxation of one point's m = (ax, ay) with g = grad p.
+// Activation, exact solution of dm/dt = c^2 (g g^T) m over dt written as
+// m + c^2 dt phi1(c^2 |g|^2 dt) (m.g) g with phi1(z) = expm1(z)/z: the
+// same value as eq. (m_activation_discrete) without forming exp(z) - 1.
+// Relaxation, eq. (m_relaxation_discrete).
+template <typename T>
+__device__ __forceinline__ void split_point(T& ax, T& ay, T gx, T gy, T c2dt, const SplitCoef& cf) {
+  const T mg = ax * gx + ay * gy;
+  if (mg != (T)0) {
+    const T z = c2dt * (gx * gx + gy * gy);
+    const T coef = z > (T)0 ? c2dt * (hc_expm1(z) / z) : c2dt;
+    const T t = coef * mg;
+    ax += t * gx;
+    ay += t * gy;
+  }
+  if (cf.gamma_is_one) {
+    ax *= (T)cf.exp_mdt;
+    ay *= (T)cf.exp_mdt;
+  } else {
+    const T n2 = ax * ax + ay * ay;
+    if (n2 > (T)0) {
+      const T nm = hc_sqrt(n2);
+      const T bb = hc_pow(nm, (T)cf.pow_a) - (T)cf.two1mg_dt;
+      const T sc = bb >= (T)0 ? hc_pow(bb, (T)cf.pow_b) / nm : (T)0;
+      ax *= sc;
+      ay *= sc;
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void row_split_body(Geo<T> g, const cx<T>* Gx, const cx<T>* Gy,
                                                    const T* __restrict__ mx,
@@ -951,31 +981,7 @@ __device__ __forceinline__ void row_split_body(Geo<T> g, const cx<T>* Gx, const 
     T ax = mx[ro + x], ay = my[ro + x];
     if (diag)
       en.add(rr[ro + x], gx * gx + gy * gy, ax * gx + ay * gy, ax * ax + ay * ay, (T)cf.gamma);
-    // Activation, exact solution of dm/dt = c^2 (g g^T) m over dt written as
-    // m + c^2 dt phi1(c^2 |g|^2 dt) (m.g) g with phi1(z) = expm1(z)/z: the
-    // same value as eq. (m_activation_discrete) without forming exp(z) - 1.
-    const T mg = ax * gx + ay * gy;
-    if (mg != (T)0) {
-      const T z = c2dt * (gx * gx + gy * gy);
-      const T coef = z > (T)0 ? c2dt * (hc_expm1(z) / z) : c2dt;
-      const T t = coef * mg;
-      ax += t * gx;
-      ay += t * gy;
-    }
-    // Relaxation, eq. (m_relaxation_discrete).
-    if (cf.gamma_is_one) {
-      ax *= (T)cf.exp_mdt;
-      ay *= (T)cf.exp_mdt;
-    } else {
-      const T n2 = ax * ax + ay * ay;
-      if (n2 > (T)0) {
-        const T nm = hc_sqrt(n2);
-        const T bb = hc_pow(nm, (T)cf.pow_a) - (T)cf.two1mg_dt;
-        const T sc = bb >= (T)0 ? hc_pow(bb, (T)cf.pow_b) / nm : (T)0;
-        ax *= sc;
-        ay *= sc;
-      }
-    }
+    split_point<T>(ax, ay, gx, gy, c2dt, cf);
     finite = finite && hc_finite(ax) && hc_finite(ay);
     v[0][s] = cmk<T>(ax, ay);
   }
