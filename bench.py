@@ -400,6 +400,60 @@ def run_diagnostics(P, W, args, dev, barrier, job_rate, headline) -> dict:
     return out
 
 
+# ----------------------------------------------------------------- paper's convergence grids
+# Section 4's first grid-convergence table at t = 5 (context only: these are
+# the paper's long-run CPU figures, parity unpinned).
+PAPER_Q_T5 = {"50-100-200": {"q_m": 6.6747, "q_grad_p": 5.0983, "q_p": 5.6516},
+              "100-200-400": {"q_m": 3.9922, "q_grad_p": 3.8377, "q_p": 3.2919},
+              "200-400-800": {"q_m": 3.4010, "q_grad_p": 4.5286, "q_p": 5.6811}}
+
+
+def run_convergence(P, W, args, dev, job_rate) -> dict:
+    """The paper's grid-convergence setup (S_int, m^A, c = 100, gamma = 0.75,
+    D = 0.01, dt = 0.05, CG threshold 1e-7) on N = 50, 100, 200, 400, 800, the
+    mixed-radix FP64 path, to t = 5 (100 steps).  The observed orders
+    q = ln(|u_h - u_h/2| / |u_h/2 - u_h/4|) / ln 2 of Section 4 for u = |m|,
+    |grad p| and p, with the finer solutions sampled at the coarse nodes
+    (every second node), beside the paper's values; and each run's throughput."""
+    import numpy as np
+    import torch
+    sizes = (50, 100, 200, 400, 800)
+    K = args.conv_steps
+    sol, rate, iters = {}, {}, {}
+    for n in sizes:
+        w = W.paper_convergence(n, steps=K)
+        with P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp64",
+                      cg_rtol=w.cg_rtol, cg_maxit=5000, precond=PRECOND, device=str(dev)) as s:
+            s.set_r(w.r)
+            s.set_source(w.S)
+            s.set_m(w.m0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = s.step(K)
+            torch.cuda.synchronize()
+            _, rate[n] = job_rate((time.perf_counter() - t0) * 1e3, w.npts * K)
+            iters[n] = st.total_cg_iters / K
+            m, p, gp = s.get_m(), s.get_p(), s.gradient().reshape((2,) + w.shape)
+        sol[n] = {"m": np.sqrt((m.reshape((2,) + w.shape) ** 2).sum(0)), "grad_p": np.sqrt((gp ** 2).sum(0)),
+                  "p": p}
+
+    def diff(a, b):  # b on the grid twice as fine, sampled at a's nodes
+        return float(np.linalg.norm(a - b[::2, ::2]))
+
+    orders = {}
+    for n in sizes[:-2]:
+        key = f"{n}-{2 * n}-{4 * n}"
+        orders[key] = {
+            "q_" + f: math.log(diff(sol[n][f], sol[2 * n][f]) / diff(sol[2 * n][f], sol[4 * n][f]))
+            / math.log(2.0) for f in ("m", "grad_p", "p")}
+    return {"t": K * 0.05, "steps": K, "grids": list(sizes), "orders": orders,
+            "paper_orders_t5": PAPER_Q_T5 if K == 100 else None,
+            "mpoint_steps_per_s": {str(n): rate[n] for n in sizes},
+            "cg_iters_per_step": {str(n): iters[n] for n in sizes},
+            "path": "mixed-radix FP64 kernels (radix 4, 2, 5 passes); Kbar preconditioner; "
+                    "context only, parity unpinned (the paper's long-run figures)"}
+
+
 # ----------------------------------------------------------------- 3D leg
 def run_3d(P, W, args, dev, barrier, job_rate, hbm_peak, hbm_src, fp64_peak) -> dict:
     """The 256^3 source/sink workload (r = 0.1, sigma 0.05 pair at
@@ -828,6 +882,11 @@ def run_gb300(args) -> None:
     if not args.no_diag:
         diag = run_diagnostics(P, W, args, dev, barrier, job_rate, value)
 
+    # ---- the paper's grid-convergence setup on its N = 50 2^k grids (mixed radix)
+    conv = None
+    if not args.no_conv:
+        conv = run_convergence(P, W, args, dev, job_rate)
+
     # ---- 3D: the 256^3 source/sink problem (d = 3), FP32 + FP64 refinement
     three_d = None
     if not args.no_3d:
@@ -913,7 +972,8 @@ def run_gb300(args) -> None:
             "equal_accuracy": acc,
             "fp64_plain": fp64, "refined_df": dfv, "scalar_kappa": scal, "sweep": sweep,
             "adjoint": adjv,
-            "three_d": three_d, "diagnostics": diag, "kernels": kernels,
+            "three_d": three_d, "diagnostics": diag, "paper_convergence": conv,
+            "kernels": kernels,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -958,6 +1018,10 @@ def main() -> None:
     ap.add_argument("--no-diag", action="store_true",
                     help="skip the diagnostics / stopping-rule leg")
     ap.add_argument("--n3d", type=int, default=256, help="3D leg: grid points per axis")
+    ap.add_argument("--no-conv", action="store_true",
+                    help="skip the paper's grid-convergence leg (N = 50 .. 800, mixed radix)")
+    ap.add_argument("--conv-steps", type=int, default=100,
+                    help="convergence leg: steps (100 reach the paper's t = 5)")
     ap.add_argument("--only-3d", action="store_true",
                     help="run only the 3D leg, --steps/--warmup steps (for profiling)")
     ap.add_argument("--inner-rtol", type=float, default=0.0,

@@ -68,6 +68,13 @@ extern "C" {
 
 typedef struct hc_ctx hc_ctx; /* opaque; owns (or borrows) all device memory of one problem */
 
+/* Supported grids.  2D: each axis 4 .. 4096 nodes with no prime factor above 5.
+ * When both axes are powers of two in [8, 4096] the step runs the fused
+ * radix-8 kernels in any precision; otherwise (e.g. the paper's N = 50 2^k
+ * convergence grids, Section 4) it runs mixed-radix FP64 kernels, in
+ * HC_FP64_PLAIN only (other precisions: HC_ENOTSUP), without the adjoint,
+ * tuning or kernel timing (HC_ENOTSUP).  3D: each axis a power of two in
+ * [8, 1024], at most 2^28 points. */
 typedef struct {
   int dim;      /* 2 or 3 */
   int n[3];     /* nodes per axis (x, y, z) */
@@ -139,14 +146,16 @@ typedef struct {
 
 /* Bytes of device workspace hc_create needs for this grid and precision
  * (host arithmetic only, no GPU work).  Errors: HC_EINVAL for an unsupported
- * grid, invalid params or a NULL bytes. */
+ * grid, invalid params or a NULL bytes; HC_ENOTSUP for a mixed-radix grid in a
+ * precision other than HC_FP64_PLAIN. */
 int hc_workspace_size(const hc_grid* grid, const hc_params* params, size_t* bytes);
 
 /* Create a context.  If workspace is non-NULL it must be a device pointer to at
  * least hc_workspace_size() bytes, 256-byte aligned; the context borrows it
  * (the caller frees it after hc_destroy).  If NULL the context allocates its
  * own with cudaMalloc.  Initial state: r = 1, S = 0, m = 0, p = 0.
- * Errors: HC_EINVAL (grid/params), HC_ENOMEM, HC_ECUDA. */
+ * Errors: HC_EINVAL (grid/params), HC_ENOTSUP (as hc_workspace_size),
+ * HC_ENOMEM, HC_ECUDA. */
 int hc_create(hc_ctx** out, const hc_grid* grid, const hc_params* params, void* workspace,
               size_t workspace_bytes);
 
@@ -226,7 +235,9 @@ int hc_split_step(hc_ctx* ctx);
 /* Forward DFT of a real field (count = npts) in the packed half-spectrum
  * layout: out has nz*ny*(nx/2) complex values (npts doubles, re/im
  * interleaved); entry (kz, ky, kx) for 1 <= kx < nx/2 is F[kz][ky][kx] and
- * entry (kz, ky, 0) is F[kz][ky][0] + i F[kz][ky][nx/2] (kz = 0 in 2D). */
+ * entry (kz, ky, 0) is F[kz][ky][0] + i F[kz][ky][nx/2] (kz = 0 in 2D).
+ * On a mixed-radix grid: the unpacked half spectrum, ny*(nx/2 + 1) complex
+ * values, entry (ky, kx) = F[ky][kx] for kx = 0 .. nx/2. */
 int hc_spectrum(hc_ctx* ctx, const double* f, double* out, size_t count);
 
 /* Launch shapes of the FFT passes, per arithmetic precision ([0] FP32

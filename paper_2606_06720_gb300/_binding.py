@@ -370,10 +370,20 @@ class Solver:
     def split_step(self):
         _check(hc_split_step(self.ctx), "hc_split_step")
 
+    @property
+    def generic(self) -> bool:
+        """A 2D grid whose sizes are not both powers of two in [8, 4096]: the
+        mixed-radix FP64 path, with the unpacked half spectrum."""
+        def pow2(v):
+            return 8 <= v <= 4096 and (v & (v - 1)) == 0
+        return len(self.n) == 2 and not (pow2(self.n[0]) and pow2(self.n[1]))
+
     def spectrum(self, f):
-        """Packed half spectrum, complex array of shape (ny, nx/2) or (nz, ny, nx/2)."""
+        """Packed half spectrum, complex array of shape (ny, nx/2) or (nz, ny, nx/2);
+        on a generic-size grid the unpacked half spectrum (ny, nx/2 + 1)."""
         fp, keep = _host_f64(f, self.npts)
-        out = np.empty(self.shape[:-1] + (self.n[0] // 2,), dtype=np.complex128)
+        cols = self.n[0] // 2 + 1 if self.generic else self.n[0] // 2
+        out = np.empty(self.shape[:-1] + (cols,), dtype=np.complex128)
         op = out.view(np.float64).ctypes.data_as(C.POINTER(C.c_double))
         _check(hc_spectrum(self.ctx, fp, op, self.npts), "hc_spectrum")
         return out

@@ -47,7 +47,7 @@ def test_strerror_and_workspace_size_without_gpu(lib):
         assert nb.value > 64 * 32 * 8 * 6
 
 
-@pytest.mark.parametrize("n", [(12, 8), (4, 8), (8, 8192), (64, 0), (3, 3)])
+@pytest.mark.parametrize("n", [(14, 8), (2, 8), (8, 8192), (64, 0), (3, 3), (49, 50), (5000, 50)])
 def test_invalid_grids_are_rejected_on_the_host(lib, n):
     from paper_2606_06720_gb300 import _binding as Bd
     g = Bd.hc_grid(2, (C.c_int * 3)(n[0], n[1], 1), (C.c_double * 3)(1.0, 1.0, 1.0))
@@ -210,7 +210,8 @@ def test_error_codes_and_messages(lib):
 
 def test_grid_validation_matches_the_documented_rule(lib):
     """hc_workspace_size accepts a grid exactly when include/hc.h says the
-    library supports it: 2D axes powers of two in [8, 4096]; 3D axes powers of
+    library supports it: 2D axes in [4, 4096] with no prime factor above 5
+    (FP64 plain unless both are powers of two in [8, 4096]); 3D axes powers of
     two in [8, 1024] with at most 2^28 points; lengths positive and finite."""
     hyp = pytest.importorskip("hypothesis")
     from hypothesis import given, settings, strategies as st
@@ -219,26 +220,38 @@ def test_grid_validation_matches_the_documented_rule(lib):
     def pow2_in(v, lo, hi):
         return lo <= v <= hi and (v & (v - 1)) == 0
 
-    def supported(dim, n, L):
+    def smooth_in(v, lo, hi):  # no prime factor above 5
+        if not lo <= v <= hi:
+            return False
+        for p in (2, 3, 5):
+            while v % p == 0:
+                v //= p
+        return v == 1
+
+    def supported(dim, n, L, precision):
         if not all(x > 0 and x != float("inf") for x in L[:dim]):
             return False
         if dim == 2:
-            return pow2_in(n[0], 8, 4096) and pow2_in(n[1], 8, 4096) and n[2] == 1
+            if not (smooth_in(n[0], 4, 4096) and smooth_in(n[1], 4, 4096) and n[2] == 1):
+                return False
+            return precision == 0 or (pow2_in(n[0], 8, 4096) and pow2_in(n[1], 8, 4096))
         return all(pow2_in(v, 8, 1024) for v in n) and n[0] * n[1] * n[2] <= 1 << 28
 
-    axis = st.sampled_from([0, 1, 4, 6, 8, 12, 16, 64, 1000, 1024, 2048, 4096, 8192])
+    axis = st.sampled_from([0, 1, 4, 6, 7, 8, 12, 14, 16, 50, 64, 1000, 1024, 2048, 4096, 8192])
     length = st.sampled_from([1.0, 0.25, 0.0, -1.0, float("inf")])
 
-    @settings(max_examples=300, deadline=None, derandomize=True)
-    @given(st.sampled_from([2, 3]), axis, axis, axis, length, length, length)
-    def check(dim, a, b, c, la, lb, lc):
+    @settings(max_examples=400, deadline=None, derandomize=True)
+    @given(st.sampled_from([2, 3]), axis, axis, axis, length, length, length, st.sampled_from([0, 1]))
+    def check(dim, a, b, c, la, lb, lc, precision):
         n = (a, b, c if dim == 3 else 1)
         L = (la, lb, lc if dim == 3 else 1.0)
         g = Bd.hc_grid(dim, (C.c_int * 3)(*n), (C.c_double * 3)(*L))
-        p = Bd.hc_params(10.0, 0.05, 0.75, 1e-3, 1e-10, 100, 1, 0.0, 1e-4, 10, 0, None)
+        p = Bd.hc_params(10.0, 0.05, 0.75, 1e-3, 1e-10, 100, precision, 0.0, 1e-4, 10, 0, None)
         nb = C.c_size_t()
         rc = Bd.hc_workspace_size(C.byref(g), C.byref(p), C.byref(nb))
-        assert (rc == 0) == supported(dim, n, L), (dim, n, L, rc)
+        assert (rc == 0) == supported(dim, n, L, precision), (dim, n, L, precision, rc)
+        if rc != 0:
+            assert rc in (Bd.HC_EINVAL, Bd.HC_ENOTSUP)
 
     check()
 

@@ -244,3 +244,12 @@ def paper_internal_sink(n: int, gamma: float = 0.75, kind: str = "const",
     return Workload("paper_internal_sink_%d_%s" % (n, kind), (n, n), (1.0, 1.0), 200.0, 0.0025,
                     gamma, 0.005, steps, 1e-7, np.full((n, n), 0.1), paper_Sint(n),
                     paper_m_ini(n, kind))
+
+
+def paper_convergence(n: int, steps: int = 100) -> Workload:
+    """Section 4's grid-convergence setup of its first table: Omega = [0,1]^2,
+    N x N with N in {50, 100, 200, 400}, r = 0.1, S_int, m^A, c = 100,
+    gamma = 0.75, D = 0.01, dt = 0.05 (steps = 100 reaches t = 5), CG threshold
+    1e-7 (the paper's default, Section 3.1)."""
+    return Workload("paper_convergence_%d" % n, (n, n), (1.0, 1.0), 100.0, 0.01, 0.75, 0.05, steps,
+                    1e-7, np.full((n, n), 0.1), paper_Sint(n), paper_m_ini(n, "A"))
