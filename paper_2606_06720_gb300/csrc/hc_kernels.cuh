@@ -1310,7 +1310,7 @@ __device__ __forceinline__ void col_grad_body(Geo<T> g, cx<Tin>* in, const cx<T>
   }
 }
 template <typename T, typename Tin, int MODE>
-__global__ void __launch_bounds__(512) k_col_grad(Geo<T> g, cx<Tin>* in, const cx<T>* __restrict__ rvec,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_col_grad(Geo<T> g, cx<Tin>* in, const cx<T>* __restrict__ rvec,
                                                   cx<T>* dio, const cx<float>* __restrict__ delta,
                                                   cx<T>* __restrict__ Gx, cx<T>* __restrict__ Gy,
                                                   SolveState* st, int check_done) {
@@ -1413,7 +1413,7 @@ __device__ __forceinline__ void col_div_body(Geo<T> g, const cx<T>* __restrict__
   }
 }
 template <typename T, int MODE>
-__global__ void __launch_bounds__(512) k_col_div(Geo<T> g, const cx<T>* __restrict__ Qx,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_col_div(Geo<T> g, const cx<T>* __restrict__ Qx,
                                                  const cx<T>* __restrict__ Qy,
                                                  const cx<T>* __restrict__ d,
                                                  const cx<T>* __restrict__ bvec,
