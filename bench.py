@@ -611,7 +611,7 @@ def run_gb300(args) -> None:
     K, Wm = args.steps, args.warmup
     s = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision="fp32_refined",
                  cg_rtol=CG_RTOL_REFINED, cg_maxit=2000, precond=PRECOND,
-                 use_graph=not args.host_loop,
+                 use_graph=not args.host_loop, sync_cert=args.sync_cert,
                  device=str(dev))
     s.set_r(w.r)
     s.set_source(w.S)
@@ -1027,6 +1027,8 @@ def main() -> None:
     ap.add_argument("--inner-rtol", type=float, default=0.0,
                     help="inner FP32 CG reduction factor (0: library default)")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--sync-cert", action="store_true",
+                    help="headline leg: certify each step before the next (hc_params.sync_cert)")
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven CG loop instead of graphs (ncu cannot profile kernel "
                          "nodes of graphs with conditional nodes)")

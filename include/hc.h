@@ -109,6 +109,18 @@ typedef struct {
                               kappa = mean(r) + mean(|m|^2)/dim; HC_PRECOND_KBAR (1) -div(Kbar grad)
                               with Kbar = mean(m m^T) + mean(r) I, the whole mean of the coefficient
                               tensor (fewer CG iterations when m is anisotropic on average) */
+  int sync_cert;           /* 2D HC_FP32_REFINED steps in graph mode with diagnostics off.
+                              0 (default): lagged certification.  A step's FP32 inner solves end
+                              with the double-float residual's solve; the FP64 residual that
+                              certifies its pressure (||S - A p|| <= cg_rtol ||S||, as always) runs
+                              beside the next step's solve, on the spare FP64 pipes, and the last
+                              step's after the loop.  If a certification fails (rare), hc_step
+                              goes back to that step's start, redoes it with the refinement loop
+                              and runs the call's remaining steps certifying each before the
+                              next, so every step hc_step returns is certified.
+                              When every certification passes, the results are bit-identical to
+                              sync_cert = 1.  1: each step certifies (and, if needed, refines)
+                              before the next one starts. */
 } hc_params;
 
 enum { HC_PRECOND_SCALAR = 0, HC_PRECOND_KBAR = 1 };

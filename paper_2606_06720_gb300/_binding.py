@@ -51,7 +51,7 @@ class hc_params(C.Structure):
                 ("kappa", C.c_double), ("inner_rtol", C.c_double), ("max_sweeps", C.c_int),
                 ("use_graph", C.c_int), ("stream", C.c_void_p), ("diagnostics", C.c_int),
                 ("fp64_first_residual", C.c_int), ("fp64_mid_residual", C.c_int),
-                ("precond", C.c_int)]
+                ("precond", C.c_int), ("sync_cert", C.c_int)]
 
 
 class hc_tuning(C.Structure):
@@ -242,7 +242,8 @@ class Solver:
                  kappa: float = 0.0, inner_rtol: float = 1e-4, max_sweeps: int = 10,
                  use_graph: bool = True, device: str = "cuda:0", stream=None,
                  diagnostics: bool = False, fp64_first_residual: bool = False,
-                 fp64_mid_residual: bool = False, precond: str = "scalar"):
+                 fp64_mid_residual: bool = False, precond: str = "scalar",
+                 sync_cert: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -266,7 +267,8 @@ class Solver:
         self.params = hc_params(c, D, gamma, dt, cg_rtol, int(cg_maxit), prec, kappa, inner_rtol,
                                 int(max_sweeps), int(bool(use_graph)), self.stream.cuda_stream,
                                 int(bool(diagnostics)), int(bool(fp64_first_residual)),
-                                int(bool(fp64_mid_residual)), _PRECOND[precond])
+                                int(bool(fp64_mid_residual)), _PRECOND[precond],
+                                int(bool(sync_cert)))
         nbytes = C.c_size_t()
         _check(hc_workspace_size(C.byref(self.grid), C.byref(self.params), C.byref(nbytes)),
                "hc_workspace_size")
@@ -300,7 +302,8 @@ class Solver:
     # parameters and fields ----------------------------------------------
     def set_params(self, **kw):
         for k, v in kw.items():
-            if k in ("use_graph", "diagnostics", "fp64_first_residual", "fp64_mid_residual"):
+            if k in ("use_graph", "diagnostics", "fp64_first_residual", "fp64_mid_residual",
+                     "sync_cert"):
                 v = int(bool(v))
             if k == "precond":
                 v = _PRECOND[v] if isinstance(v, str) else int(v)

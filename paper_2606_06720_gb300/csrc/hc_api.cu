@@ -193,6 +193,20 @@ struct hc_ctx {
   cudaGraphConditionalHandle h_gate;
   bool run_graph_ready;
   int force_diag;                       // 1 while hc_run runs (diagnostics forced on)
+  // Lagged certification (2D HC_FP32_REFINED; see hc_params.sync_cert): the
+  // previous step's input m and its pressure await their FP64 certification
+  // (m_prev, p_saved) while the next step runs; the split step writes m_tmp.
+  float* m_prev[2];
+  float* m_tmp[2];
+  cx<double>* p_saved;
+  cx<double>* G64c;                     // the certifying residual's FP64 scratch (two fields)
+  double* partials_c;                   // its per-CTA partial sums
+  hc::SolveState* st_c;                 // its state (cert_pending, cert_r2, done = nothing pending)
+  cudaGraphExec_t gexec_pipe;
+  bool pipe_ready;
+  Handles h_pipe;
+  cudaGraphConditionalHandle h_pipe_gate;
+  cudaStream_t cap_hi, cap_lo;          // capture streams of the lagged graph's two branches
   int graph_nodes_fixed, graph_nodes_body, graph_nodes_outer;
 };
 
@@ -304,6 +318,14 @@ void layout(hc_ctx* c, Layout& L) {
     c->G32 = L.take<cx<float>>(d * S32);
     for (int k = 0; k < d; ++k) c->m[k] = L.take<float>(sizeof(float) * n);
     c->rf = L.take<float>(sizeof(float) * n);
+    if (d == 2 && !c->df) {  // lagged certification
+      for (int k = 0; k < 2; ++k) c->m_prev[k] = L.take<float>(sizeof(float) * n);
+      for (int k = 0; k < 2; ++k) c->m_tmp[k] = L.take<float>(sizeof(float) * n);
+      c->p_saved = L.take<cx<double>>(S64);
+      c->G64c = L.take<cx<double>>(2 * S64);
+      c->partials_c = L.take<double>(sizeof(double) * hc::kPartialStride * max_reducing_ctas(c));
+      c->st_c = L.take<hc::SolveState>(sizeof(hc::SolveState));
+    }
   }
   c->twx_f = L.take<cx<float>>(sizeof(cx<float>) * c->nx);
   c->twy_f = L.take<cx<float>>(sizeof(cx<float>) * c->ny);
@@ -1417,14 +1439,301 @@ int build_run_graph(hc_ctx* c) {
 void drop_graphs(hc_ctx* c) {
   if (c->graph_ready) cudaGraphExecDestroy(c->gexec);
   if (c->run_graph_ready) cudaGraphExecDestroy(c->gexec_run);
+  if (c->pipe_ready) cudaGraphExecDestroy(c->gexec_pipe);
   c->graph_ready = false;
   c->run_graph_ready = false;
+  c->pipe_ready = false;
+}
+
+// ---------------------------------------------------------------- lagged certification
+// hc_step with lagged certification: 2D HC_FP32_REFINED (the double-float
+// mid-step residual on), graph mode, diagnostics off, sync_cert off.
+bool pipe_on(const hc_ctx* c) {
+  return c->dim == 2 && c->refined && !c->df && c->mid_df && !c->gen && c->prm.use_graph &&
+         !diag_on(c) && !c->prm.sync_cert && c->m_prev[0] != nullptr;
+}
+
+// The split step of a lagged step: its gradient pass adds the last inner
+// solve's correction to p64 (as the refinement residual's pass would), and
+// the new m goes to m_tmp (m stays the step's input until the commit).
+void split_step_lagged(hc_ctx* c) {
+  auto& g = c->gf;
+  cx<float>* Gx = c->G32;
+  cx<float>* Gy = c->G32 + c->ns;
+  hc::col_grad<float, double>(g, hc::CG_ADDDELTA, c->p64, nullptr, nullptr, c->x32, Gx, Gy, c->st, 0,
+                              c->stream);
+  hc::row_split<float>(g, Gx, Gy, (const float*)c->m[0], (const float*)c->m[1], (const float*)c->rf,
+                       Gx, Gy, split_coef(c->prm), c->st, c->stream);
+  hc::col_heat<float>(g, Gx, Gy, c->st, c->stream);
+  hc::row_c2r<float>(g, Gx, Gy, c->m_tmp[0], c->m_tmp[1], c->st, 1, c->stream);
+  c->launches += 4;
+}
+
+// The certifying FP64 residual of the pressure awaiting certification
+// (p_saved, solved with m_prev), on stream s, with its own partial sums.
+void cert_resid_launch(hc_ctx* c, cudaStream_t s) {
+  hc::Geo<double> g = c->gd;
+  g.partials = c->partials_c;
+  hc::cert_resid(g, c->p_saved, c->m_prev[0], c->m_prev[1], (const float*)c->rf, c->b64, c->G64c,
+                 c->st_c, s);
+  c->launches += 3;
+}
+
+// Kernels of one lagged step graph launch (gate, step_begin, FP32 residual,
+// split, step_end, certification, commit) besides its loops.
+constexpr int kPipeFixedKernels = 1 + 1 + 3 + 4 + 1 + 3 + 2;
+
+// The lagged step graph: a gate, then IF(not halted) { A ; B ; commit } with
+//   A (high priority): step_begin, FP32 residual, WHILE(first){CG},
+//     IF(mid){double-float residual, WHILE(mid_inner){CG}}, split (-> m_tmp), step_end;
+//   B (low priority, beside A): the FP64 residual certifying the previous step;
+//   commit after both: accept the step (m_tmp -> m, keeping m and p for its own
+//   certification) or, if the previous step's certification failed, halt.
+// A's kernels get the device's highest stream priority and B's the lowest, so
+// the block scheduler fills the SMs with A's CTAs first and B's FP64-pipe work
+// runs in what is left.
+int build_pipe_graph(hc_ctx* c) {
+  int lo = 0, hi = 0;
+  CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  if (!c->cap_hi) CU(cudaStreamCreateWithPriority(&c->cap_hi, cudaStreamNonBlocking, hi));
+  if (!c->cap_lo) CU(cudaStreamCreateWithPriority(&c->cap_lo, cudaStreamNonBlocking, lo));
+  CU(cudaStreamSynchronize(c->stream));
+  cudaGraph_t graph;
+  CU(cudaGraphCreate(&graph, 0));
+  cudaStream_t keep = c->stream;
+  const long long before = c->launches;
+  c->stream = c->cap_hi;
+  Handles hh;
+  cudaGraphConditionalHandle hgate = 0;
+  std::vector<cudaGraph_t> graphs_a;     // graphs holding A's (and the commit's) kernels
+  std::vector<cudaGraphNode_t> nodes_b;  // B's kernel nodes
+  auto run = [&]() -> int {
+    cudaStream_t s = c->stream;
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    auto end_capture = [&](cudaStream_t es, cudaGraph_t g, std::vector<cudaGraphNode_t>* tail) -> int {
+      if (tail) {
+        CU(cudaStreamGetCaptureInfo(es, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+        tail->assign(deps, deps + ndeps);
+      }
+      cudaGraph_t same = g;
+      CU(cudaStreamEndCapture(es, &same));
+      return HC_OK;
+    };
+    auto add_cond = [&](cudaGraph_t g, const std::vector<cudaGraphNode_t>& after,
+                        cudaGraphConditionalHandle* hd, bool is_if, cudaGraphNode_t* node,
+                        cudaGraph_t* body) -> int {
+      CU(cudaGraphConditionalHandleCreate(hd, g, 0, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams p = {};
+      p.type = cudaGraphNodeTypeConditional;
+      p.conditional.handle = *hd;
+      p.conditional.type = is_if ? cudaGraphCondTypeIf : cudaGraphCondTypeWhile;
+      p.conditional.size = 1;
+      CU(cudaGraphAddNode(node, g, after.data(), nullptr, after.size(), &p));
+      *body = p.conditional.phGraph_out[0];
+      graphs_a.push_back(*body);
+      return HC_OK;
+    };
+    auto capture_iter = [&](cudaGraph_t body) -> int {
+      CU(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      refined_iter(c);
+      return end_capture(s, body, nullptr);
+    };
+    // gate, IF(not halted)
+    graphs_a.push_back(graph);
+    CU(cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    hc::run_gate(c->st, s);
+    std::vector<cudaGraphNode_t> tail;
+    int rc = end_capture(s, graph, &tail);
+    cudaGraphNode_t gate_node;
+    cudaGraph_t target = nullptr;
+    if (!rc) rc = add_cond(graph, tail, &hgate, true, &gate_node, &target);
+    if (rc) return rc;
+    // A
+    CU(cudaStreamBeginCaptureToGraph(s, target, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    hc::step_begin(c->st, (int)c->n, s);
+    first_resid32(c);
+    rc = end_capture(s, target, &tail);
+    cudaGraphNode_t first_node, mid_node, mi_node;
+    cudaGraph_t body = nullptr, mbody = nullptr;
+    if (!rc) rc = add_cond(target, tail, &hh.first, false, &first_node, &body);
+    if (!rc) rc = capture_iter(body);
+    if (!rc) rc = add_cond(target, {first_node}, &hh.mid, true, &mid_node, &mbody);
+    if (rc) return rc;
+    CU(cudaStreamBeginCaptureToGraph(s, mbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    mid_resid(c);
+    std::vector<cudaGraphNode_t> mtail;
+    rc = end_capture(s, mbody, &mtail);
+    if (!rc) rc = add_cond(mbody, mtail, &hh.mid_inner, false, &mi_node, &body);
+    if (!rc) rc = capture_iter(body);
+    if (rc) return rc;
+    CU(cudaStreamBeginCaptureToGraph(s, target, &mid_node, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    split_step_lagged(c);
+    hc::step_end(c->st, 1, s);
+    std::vector<cudaGraphNode_t> atail;
+    rc = end_capture(s, target, &atail);
+    if (rc) return rc;
+    // B, beside A; its nodes are the ones its capture adds
+    size_t nb0 = 0, nb1 = 0;
+    CU(cudaGraphGetNodes(target, nullptr, &nb0));
+    std::vector<cudaGraphNode_t> pre(nb0);
+    CU(cudaGraphGetNodes(target, pre.data(), &nb0));
+    // B waits for A's first residual, so A's first inner loop starts on SMs
+    // that B's long FP64 CTAs have not taken yet
+    CU(cudaStreamBeginCaptureToGraph(c->cap_lo, target, tail.data(), nullptr, tail.size(),
+                                     cudaStreamCaptureModeThreadLocal));
+    cert_resid_launch(c, c->cap_lo);
+    std::vector<cudaGraphNode_t> btail;
+    rc = end_capture(c->cap_lo, target, &btail);
+    if (rc) return rc;
+    CU(cudaGraphGetNodes(target, nullptr, &nb1));
+    std::vector<cudaGraphNode_t> all(nb1);
+    CU(cudaGraphGetNodes(target, all.data(), &nb1));
+    for (cudaGraphNode_t nd : all)
+      if (std::find(pre.begin(), pre.end(), nd) == pre.end()) nodes_b.push_back(nd);
+    // commit after A and B
+    std::vector<cudaGraphNode_t> join(atail);
+    join.insert(join.end(), btail.begin(), btail.end());
+    CU(cudaStreamBeginCaptureToGraph(s, target, join.data(), nullptr, join.size(),
+                                     cudaStreamCaptureModeThreadLocal));
+    float* mp[2] = {c->m_prev[0], c->m_prev[1]};
+    float* mm[2] = {(float*)c->m[0], (float*)c->m[1]};
+    const float* mt[2] = {c->m_tmp[0], c->m_tmp[1]};
+    hc::commit_copy(c->st, c->st_c, mm, mp, mt, c->p64, c->p_saved, c->n, c->ns, s);
+    hc::commit_flags(c->st, c->st_c, 0, s);
+    c->launches += 2;
+    return end_capture(s, target, nullptr);
+  };
+  int rc = run();
+  c->stream = keep;
+  c->launches = before;
+  if (rc) {
+    abort_capture(c->cap_hi);
+    abort_capture(c->cap_lo);
+    cudaGraphDestroy(graph);
+    return rc;
+  }
+  // priorities: every kernel node high, then B's low
+  cudaKernelNodeAttrValue vhi = {}, vlo = {};
+  vhi.priority = hi;
+  vlo.priority = lo;
+  for (cudaGraph_t g : graphs_a) {
+    size_t nn = 0;
+    CU(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CU(cudaGraphGetNodes(g, nodes.data(), &nn));
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType t;
+      CU(cudaGraphNodeGetType(nd, &t));
+      if (t == cudaGraphNodeTypeKernel)
+        CU(cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &vhi));
+    }
+  }
+  for (cudaGraphNode_t nd : nodes_b) {
+    cudaGraphNodeType t;
+    CU(cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel)
+      CU(cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &vlo));
+  }
+  cudaError_t e = cudaGraphInstantiate(&c->gexec_pipe, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __LINE__);
+  c->h_pipe = hh;
+  c->h_pipe_gate = hgate;
+  c->pipe_ready = true;
+  return HC_OK;
 }
 
 int set_graph_mode(hc_ctx* c, int on) {
   int v = on ? 1 : 0;
   CU(cudaMemcpyAsync(&c->st->graph_mode, &v, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+// One int field of a device SolveState, from the host (stream-ordered).
+int put_state_int(hc_ctx* c, hc::SolveState* st, int hc::SolveState::*field, int v) {
+  int* dst = &(st->*field);
+  CU(cudaMemcpyAsync(dst, &v, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+// hc_step with lagged certification.  A pass launches the lagged graph once
+// per step, then certifies the last step.  A failed certification halts the
+// pass's later launches; hc_step then goes back to the failed step's start
+// (its input m, its pressure as warm start), redoes it with the context's own
+// certifying graph, and runs the call's remaining steps with that graph too
+// (a tolerance that two sweeps miss would otherwise cost a repair per step).
+// So every step returned is certified.
+int step_lagged(hc_ctx* c, int nsteps) {
+  if (!c->pipe_ready) {
+    int rc = build_pipe_graph(c);
+    if (rc) return rc;
+  }
+  int done = 0;
+  while (done < nsteps) {
+    const int todo = nsteps - done;
+    int rc = read_state(c);
+    if (rc) return rc;
+    const hc::SolveState before = *c->st_host;
+    // nothing awaits certification at the start of a pass
+    rc = put_state_int(c, c->st_c, &hc::SolveState::cert_pending, 0);
+    if (!rc) rc = put_state_int(c, c->st_c, &hc::SolveState::done, 1);
+    if (!rc) rc = put_state_int(c, c->st, &hc::SolveState::halt, 0);
+    if (!rc) rc = put_state_int(c, c->st, &hc::SolveState::cert_failed, 0);
+    if (!rc) rc = put_state_int(c, c->st, &hc::SolveState::cert_steps, 0);
+    if (!rc) rc = put_state_int(c, c->st, &hc::SolveState::pipelined, 1);
+    if (!rc) rc = use_handles(c, c->h_pipe, c->h_pipe_gate);
+    if (!rc) rc = set_graph_mode(c, 1);
+    if (rc) return rc;
+    c->batch_handles = 0;
+    for (int k = 0; k < todo; ++k) CU(cudaGraphLaunch(c->gexec_pipe, c->stream));
+    cert_resid_launch(c, c->stream);  // the last step's certification
+    hc::commit_flags(c->st, c->st_c, 1, c->stream);
+    c->launches += 1;
+    CU(cudaGetLastError());
+    rc = read_state(c);
+    if (!rc) rc = put_state_int(c, c->st, &hc::SolveState::pipelined, 0);
+    if (!rc) rc = set_graph_mode(c, 0);
+    if (rc) return rc;
+    const hc::SolveState& h = *c->st_host;
+    const long long steps_a = h.acc_steps - before.acc_steps;
+    c->launches += kPipeFixedKernels * steps_a + (long long)(todo - steps_a) +
+                   (long long)c->graph_nodes_body * (h.acc_iters - before.acc_iters) +
+                   (long long)c->graph_nodes_outer * (h.acc_mid - before.acc_mid);
+    if (!h.cert_failed) return HC_OK;
+    // back to the start of the step that failed its certification
+    done += h.cert_steps - 1;
+    for (int k = 0; k < 2; ++k)
+      CU(cudaMemcpyAsync(c->m[k], c->m_prev[k], sizeof(float) * c->n, cudaMemcpyDeviceToDevice,
+                         c->stream));
+    CU(cudaMemcpyAsync(c->p64, c->p_saved, sizeof(cx<double>) * c->ns, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    hc::msum<float>(c->gf, (const float*)c->m[0], (const float*)c->m[1], c->st, c->stream);
+    c->launches += 1;
+    if (!c->graph_ready) {
+      rc = build_graph(c);
+      if (rc) return rc;
+    }
+    rc = read_state(c);
+    if (rc) return rc;
+    const hc::SolveState b2 = *c->st_host;
+    rc = use_handles(c, c->h_own);
+    if (!rc) rc = set_graph_mode(c, 1);
+    if (rc) return rc;
+    for (int k = done; k < nsteps; ++k) CU(cudaGraphLaunch(c->gexec, c->stream));
+    rc = read_state(c);
+    if (!rc) rc = set_graph_mode(c, 0);
+    if (rc) return rc;
+    const hc::SolveState& h2 = *c->st_host;
+    c->launches += (long long)c->graph_nodes_fixed * (h2.acc_steps - b2.acc_steps) +
+                   (long long)c->graph_nodes_body * (h2.acc_iters - b2.acc_iters) +
+                   (long long)c->graph_nodes_outer *
+                       ((h2.acc_res_full - b2.acc_res_full) + (h2.acc_mid - b2.acc_mid));
+    done = nsteps;
+  }
   return HC_OK;
 }
 
@@ -1629,6 +1938,8 @@ void hc_destroy(hc_ctx* c) {
   else cudaDeviceSynchronize();
   drop_graphs(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->cap_hi) cudaStreamDestroy(c->cap_hi);
+  if (c->cap_lo) cudaStreamDestroy(c->cap_lo);
   if (c->owns_ws && c->ws) cudaFree(c->ws);
   if (c->st_host) cudaFreeHost(c->st_host);
   delete c;
@@ -1883,7 +2194,10 @@ int hc_step(hc_ctx* c, int nsteps, hc_step_stats* last) {
   if (nsteps == 0) return HC_OK;
   hc::reset_accum(c->st, c->stream);
   c->launches += 1;
-  if (c->prm.use_graph) {
+  if (pipe_on(c)) {
+    int rc = step_lagged(c, nsteps);
+    if (rc) return rc;
+  } else if (c->prm.use_graph) {
     if (!c->graph_ready) {
       int rc = build_graph(c);
       if (rc) return rc;

@@ -153,7 +153,13 @@ struct SolveState {
   int halt;                  // run mode: a stopping rule fired
   int stop_reason;           // HC_STOP_* of the rule that fired
   int energy_step;           // run mode: steps completed when the energy increase was seen
-  int pad1_;
+  // Lagged certification (2D HC_FP32_REFINED steps in graph mode, diagnostics off): the FP64
+  // residual that certifies step k runs beside step k+1's FP32 solve (see hc_step).
+  int pipelined;             // 1 while such steps run: the mid-step residual always opens
+  int cert_pending;          // (certifying state) a step awaits its FP64 certification
+  int cert_failed;           // a certification found ||S - A p|| above the tolerance
+  int cert_steps;            // steps whose certification passed (or that were accepted) in this call
+  double cert_r2;            // (certifying state) ||S - A p||^2 of the last certification
 };
 
 // Values the host changes between steps (tolerances, caps, r statistics).
@@ -179,7 +185,8 @@ struct SolveConfig {
 constexpr int kPartialStride = 8;
 
 // Reduction sites (ticket indices).
-enum { TK_DIV = 0, TK_UPDATE = 1, TK_RESID = 2, TK_MSUM = 3, TK_PROJ = 4, TK_DIAG = 5, TK_GRADM = 6 };
+enum { TK_DIV = 0, TK_UPDATE = 1, TK_RESID = 2, TK_MSUM = 3, TK_PROJ = 4, TK_DIAG = 5, TK_GRADM = 6,
+       TK_CERT = 7 };
 
 // One batched column pass of a 3D grid: transforms of length 2^lL whose
 // consecutive elements are `stride` apart, over tiles of 2^ltc adjacent
@@ -299,7 +306,8 @@ struct BShape {
 
 // Column-kernel modes.
 enum ColGradMode { CG_PLAIN = 0, CG_DUPDATE = 1, CG_ADDDELTA = 2 };
-enum ColDivMode { CD_PLAIN = 0, CD_CG = 1, CD_RESID = 2, CD_RESID_REFINE = 3, CD_RESID_FIRST = 4 };
+enum ColDivMode { CD_PLAIN = 0, CD_CG = 1, CD_RESID = 2, CD_RESID_REFINE = 3, CD_RESID_FIRST = 4,
+                  CD_CERT = 5 };
 
 // ---------------- launchers (defined per precision) ----------------
 // Row pass, forward: physical pair (a, b) -> packed row spectra (A, B). b/B may be null.
@@ -452,6 +460,16 @@ void set_smem_limits_3d_df();
 // Opt every kernel of one precision in to the full shared memory per block.
 void set_smem_limits_f32();
 void set_smem_limits_f64();
+// Lagged certification (2D refined steps): the FP64 certifying residual of
+// pressure p with the FP32 m, r it was solved with (sc: the certifying state,
+// skipped when nothing is pending); the commit after a lagged step (copies
+// guarded by the certification's outcome); the flag update after it.
+void cert_resid(const Geo<double>& g, const cx<double>* p, const float* mx, const float* my,
+                const float* r, const cx<double>* b, cx<double>* G, SolveState* sc, cudaStream_t s);
+void commit_copy(const SolveState* st, const SolveState* sc, float* const* m, float* const* mp,
+                 const float* const* mt, const cx<double>* p64, cx<double>* ps, size_t n, size_t ns,
+                 cudaStream_t s);
+void commit_flags(SolveState* st, SolveState* sc, int final_cert, cudaStream_t s);
 // FP64 FMA throughput of the current device (TFLOP/s, FMA = 2 flops), reps timed launches on s.
 int fma_peak(int reps, cudaStream_t s, double* tflops);
 void set_smem_limits_df();

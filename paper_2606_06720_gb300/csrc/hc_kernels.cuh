@@ -1038,7 +1038,9 @@ __device__ __forceinline__ void resid_first_init(SolveState* st, double r32, dou
     st->sweeps = 1;  // the next FP64 residual adds this sweep's correction
     st->acc_first += 1;
   }
-  st->mid_phase = (use && st->mid_df) ? 1 : 0;
+  // with lagged certification the double-float residual always follows, as the
+  // right-hand side of the step's last inner solve
+  st->mid_phase = ((use || st->pipelined) && st->mid_df) ? 1 : 0;
   st->h_cur = st->h_first;
   if (st->graph_mode) {
     cudaGraphSetConditional(st->h_first, use ? 1u : 0u);
@@ -1179,7 +1181,7 @@ __device__ __forceinline__ void step_begin_body(SolveState* st, int npts) {
   st->outer_done = 0;
   st->first = 1;
   if (!st->refined) st->thresh2 = st->outer_thresh2;
-  if (st->graph_mode && st->refined) cudaGraphSetConditional(st->h_outer, 1u);
+  if (st->graph_mode && st->refined && st->h_outer) cudaGraphSetConditional(st->h_outer, 1u);
 }
 
 // Diagnostics of Section 2.5 for the step that just ran from m^k: the energy
@@ -1324,7 +1326,7 @@ __device__ __forceinline__ void col_div_body(Geo<T> g, const cx<T>* __restrict__
                                                  const cx<T>* __restrict__ bvec,
                                                  cx<T>* __restrict__ out, cx<float>* __restrict__ r32,
                                                  cx<float>* __restrict__ delta32, SolveState* st) {
-  if (MODE == CD_CG && st->done) return;
+  if ((MODE == CD_CG || MODE == CD_CERT) && st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const ColIdx c = col_idx(g);
@@ -1367,6 +1369,10 @@ __device__ __forceinline__ void col_div_body(Geo<T> g, const cx<T>* __restrict__
       const double r2 = (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
       acc[0] += w * r2;
       acc[1] += w * r2 * (double)pinv_sym(g, c.kx, ky, pc);
+    } else if constexpr (MODE == CD_CERT) {
+      // certification only: ||S - A p||^2 in the column's precision, nothing written
+      const cx<T> rv = csub(bvec[idx], q);
+      acc[0] += w * ((double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y);
     } else if constexpr (MODE == CD_RESID_FIRST) {
       const size_t ci = cmi(g, ky, c.kx);  // b32, r32 and delta32 are column-major
       const cx<float> rf = ccast<float>(csub(bvec[ci], q));
@@ -1396,7 +1402,11 @@ __device__ __forceinline__ void col_div_body(Geo<T> g, const cx<T>* __restrict__
   }
   if constexpr (MODE == CD_PLAIN || MODE == CD_CG) return;
   double tot[3];
-  if constexpr (MODE == CD_RESID) {
+  if constexpr (MODE == CD_CERT) {
+    double a1[1] = {acc[0]}, t1[1];
+    if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_CERT], t1) && threadIdx.x == 0)
+      st->cert_r2 = t1[0];
+  } else if constexpr (MODE == CD_RESID) {
     double a2[2] = {acc[0], acc[1]}, t2[2];
     if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
       resid_init(st, t2[0], t2[1]);

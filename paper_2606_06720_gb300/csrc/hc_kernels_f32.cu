@@ -53,6 +53,68 @@ int row_pipe_ctas_per_sm(int threads, size_t smem) {
   return n;
 }
 
+// ------------------------------------------------------------------ lagged certification
+// The certification of the previous step passed, or nothing awaited one.
+__device__ __forceinline__ bool cert_ok(const SolveState* st, const SolveState* sc) {
+  return !sc->cert_pending || (isfinite(sc->cert_r2) && sc->cert_r2 <= st->outer_thresh2);
+}
+
+// After both branches of a lagged step: unless the previous step's
+// certification failed, keep its input m and its pressure for the
+// certification of the step just made (m -> m_prev, p -> p_saved) and accept
+// that step's m (m_tmp -> m).  Every CTA reads the decision from states this
+// kernel does not change; k_commit_flags updates them afterwards.
+__global__ void __launch_bounds__(256) k_commit_copy(const SolveState* st, const SolveState* sc,
+                                                     float* __restrict__ m0, float* __restrict__ m1,
+                                                     float* __restrict__ mp0, float* __restrict__ mp1,
+                                                     const float* __restrict__ mt0,
+                                                     const float* __restrict__ mt1,
+                                                     const cx<double>* __restrict__ p64,
+                                                     cx<double>* __restrict__ ps, size_t n,
+                                                     size_t ns) {
+  if (!cert_ok(st, sc)) return;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    mp0[i] = m0[i];
+    mp1[i] = m1[i];
+    m0[i] = mt0[i];
+    m1[i] = mt1[i];
+  }
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += stride) ps[i] = p64[i];
+}
+
+// One thread.  A passed (or absent) certification: the step just made now
+// awaits its own.  A failed one: halt the remaining lagged steps (the host
+// redoes the failed step); the state still holds that step's input m and its
+// pressure.  With final = 1 (after the last step, no new step made) nothing
+// awaits a certification afterwards.
+__global__ void k_commit_flags(SolveState* st, SolveState* sc, int final_cert) {
+  const bool ok = cert_ok(st, sc);
+  if (sc->cert_pending) {
+    st->outer_r2 = sc->cert_r2;  // the certified residual of the step it certified
+    st->res_full = 1;
+    st->acc_res_full += 1;
+  }
+  if (ok) {
+    if (!final_cert) st->cert_steps += 1;
+    sc->cert_pending = final_cert ? 0 : 1;
+    sc->done = final_cert ? 1 : 0;
+  } else {
+    st->cert_failed = 1;
+    st->halt = 1;
+  }
+}
+
+void commit_copy(const SolveState* st, const SolveState* sc, float* const* m, float* const* mp,
+                 const float* const* mt, const cx<double>* p64, cx<double>* ps, size_t n, size_t ns,
+                 cudaStream_t s) {
+  k_commit_copy<<<upd_blocks(n), 256, 0, s>>>(st, sc, m[0], m[1], mp[0], mp[1], mt[0], mt[1], p64, ps,
+                                              n, ns);
+}
+void commit_flags(SolveState* st, SolveState* sc, int final_cert, cudaStream_t s) {
+  k_commit_flags<<<1, 1, 0, s>>>(st, sc, final_cert);
+}
+
 void set_smem_limits_f32() {
   allow_smem(kp_row_apply<true>);
   allow_smem(kp_row_apply<false>);

@@ -47,7 +47,27 @@ template void col_lap_dot<double>(const Geo<double>&, const cx<double>*, const c
 template void spec_accum<double>(const Geo<double>&, double*, const cx<double>*, cudaStream_t);
 template void spec_norm2<double>(const Geo<double>&, const cx<double>*, SolveState*, cudaStream_t);
 
+// FP64 residual S - A p of a certification (lagged certification): the
+// pressure p and the m it was solved with are the caller's; the state sc
+// skips it when nothing awaits certification (sc->done) and receives
+// ||S - A p||^2 in sc->cert_r2.  Non-persistent passes, nothing else written.
+void cert_resid(const Geo<double>& g, const cx<double>* p, const float* mx, const float* my,
+                const float* r, const cx<double>* b, cx<double>* G, SolveState* sc, cudaStream_t s) {
+  const int nb = g.H >> g.ltc, nt = col_threads(g);
+  const size_t ns = (size_t)g.ny * g.H;
+  cx<double>* Gx = G;
+  cx<double>* Gy = G + ns;
+  k_col_grad<double, double, CG_PLAIN><<<nb, nt, col_smem(g, 2), s>>>(
+      g, const_cast<cx<double>*>(p), nullptr, nullptr, nullptr, Gx, Gy, sc, 1);
+  const size_t sm = row_smem(g) + (size_t)3 * g.rpc * g.nx * sizeof(float);
+  k_row_apply<double, float, false, 1><<<g.ny >> g.lrpc, row_threads(g), sm, s>>>(g, Gx, Gy, mx, my, r,
+                                                                                 Gx, Gy, sc);
+  k_col_div<double, CD_CERT><<<nb, nt, col_smem(g, 2), s>>>(g, Gx, Gy, nullptr, b, nullptr, nullptr,
+                                                             nullptr, sc);
+}
+
 void set_smem_limits_f64() {
+  allow_smem(k_col_div<double, CD_CERT>);
   set_smem_limits_t<double>();
   set_smem_limits_grad<double, double>();
   allow_smem(k_row_apply<double, float, false, 1>);

@@ -17,8 +17,10 @@ pytestmark = pytest.mark.gpu
 
 
 def solver_for(hc, w, precision="fp32_refined"):
+    # batches run the synchronous step (each step certified before the next), so
+    # the solo runs they are compared with do too
     s = hc.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision=precision,
-                  cg_rtol=w.cg_rtol, cg_maxit=2000)
+                  cg_rtol=w.cg_rtol, cg_maxit=2000, sync_cert=True)
     s.set_r(w.r)
     s.set_source(w.S)
     s.set_m(w.m0)

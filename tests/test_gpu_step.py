@@ -72,7 +72,8 @@ def test_graph_and_host_loop_agree_bitwise(hc, precision):
     w = W.source_sink_2d(128, steps=3)
     outs = []
     for use_graph in (True, False):
-        with make_solver(hc, w, precision, use_graph=use_graph) as s:
+        # the host loop certifies each step before the next: so does the graph here
+        with make_solver(hc, w, precision, use_graph=use_graph, sync_cert=True) as s:
             st = s.step(3)
             outs.append((s.get_m(), s.get_p(), st.cg_iters, st.refine_sweeps))
     assert np.array_equal(outs[0][0], outs[1][0])
@@ -473,3 +474,69 @@ def test_largest_2d_grid_one_step(hc, precision):
     gp = O.gradient(g, p)
     ref = O.diffusion(g, O.relaxation(O.activation(m0, gp, w.c, w.dt), w.gamma, w.dt), w.D, w.dt)
     assert rel_l2(m1, ref) < 2e-6
+
+
+@pytest.mark.parametrize("precond", ["scalar", "kbar"])
+def test_lagged_certification_matches_synchronous_bitwise(hc, precond):
+    """Lagged certification (the FP64 residual certifying step k runs beside
+    step k+1's FP32 solve) against certifying every step before the next: when
+    every certification passes at its first FP64 residual (cg_rtol 1e-7 leaves
+    two sweeps a margin; the synchronous run confirms one FP64 residual per
+    step), m, p and the iteration counts are bit-identical."""
+    w = W.source_sink_2d(256, steps=12)
+    out = []
+    for sync in (True, False):
+        with make_solver(hc, w, "fp32_refined", rtol=1e-7, precond=precond, sync_cert=sync) as s:
+            sts = [s.step(4) for _ in range(3)]
+            out.append((s.get_m(), s.get_p(), sts))
+    (m_s, p_s, st_s), (m_l, p_l, st_l) = out
+    assert all(b.total_refine_residuals == 4 for b in st_s)
+    assert np.array_equal(m_l, m_s) and np.array_equal(p_l, p_s)
+    for a, b in zip(st_l, st_s):
+        assert a.status == b.status == 0
+        assert a.total_cg_iters == b.total_cg_iters and a.total_sweeps == b.total_sweeps
+        assert a.total_refine_residuals == 4
+        assert a.rel_residual <= 1e-7 and a.rel_residual == pytest.approx(b.rel_residual, rel=1e-9)
+
+
+def test_lagged_certification_at_the_bench_tolerance(hc):
+    """At cg_rtol 1e-8 two sweeps are marginal on a 256^2 grid: some steps need
+    a third, which the lagged path gets by going back to the step (the
+    synchronous one by one more sweep).  Both certify every step, and their m
+    agree to the tolerance of the solves."""
+    w = W.source_sink_2d(256, steps=12)
+    out = {}
+    for sync in (True, False):
+        with make_solver(hc, w, "fp32_refined", sync_cert=sync) as s:
+            for _ in range(12):
+                st = s.step(1)
+                assert st.status == 0 and st.rel_residual <= 1e-8
+            out[sync] = s.get_m()
+    assert rel_l2(out[False], out[True]) < 1e-6
+
+
+def test_lagged_certification_repairs_failed_certifications(hc):
+    """With inner solves that reduce their residual only 20-fold, the two FP32
+    solves of a lagged step leave ||S - A p|| far above 1e-8, so every lagged
+    certification fails: each step is sent back to its start and redone with the
+    refinement loop.  Every step hc_step returns is still certified (the
+    residual recomputed with the oracle's operator), and m agrees with the
+    synchronous path to the tolerance of the solves."""
+    w = W.source_sink_2d(128, steps=5)
+    g = O.Grid(w.n, w.L)
+    res = {}
+    for sync in (False, True):
+        with make_solver(hc, w, "fp32_refined", inner_rtol=0.05, max_sweeps=20,
+                         sync_cert=sync) as s:
+            for _ in range(5):
+                m_in = s.get_m()
+                st = s.step(1)
+                assert st.status == 0 and st.rel_residual <= 1e-8
+                assert st.refine_residuals >= 1
+                p = s.get_p()
+                f32 = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+                b = O.project(g, w.S)
+                r = np.linalg.norm(b - O.apply_A(g, f32(m_in), f32(w.r), p)) / np.linalg.norm(b)
+                assert r <= 1.2e-8, r
+            res[sync] = s.get_m()
+    assert rel_l2(res[False], res[True]) < 1e-6
