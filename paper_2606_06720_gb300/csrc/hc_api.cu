@@ -1448,9 +1448,9 @@ void drop_graphs(hc_ctx* c) {
 // ---------------------------------------------------------------- lagged certification
 // hc_step with lagged certification: 2D HC_FP32_REFINED (the double-float
 // mid-step residual on), graph mode, diagnostics off, sync_cert off.
-bool pipe_on(const hc_ctx* c) {
-  return c->dim == 2 && c->refined && !c->df && c->mid_df && !c->gen && c->prm.use_graph &&
-         !diag_on(c) && !c->prm.sync_cert && c->m_prev[0] != nullptr;
+bool pipe_on(const hc_ctx* c, int nsteps) {
+  return nsteps >= 2 && c->dim == 2 && c->refined && !c->df && c->mid_df && !c->gen &&
+         c->prm.use_graph && !diag_on(c) && !c->prm.sync_cert && c->m_prev[0] != nullptr;
 }
 
 // The split step of a lagged step: its gradient pass adds the last inner
@@ -1652,88 +1652,64 @@ int set_graph_mode(hc_ctx* c, int on) {
   return HC_OK;
 }
 
-// One int field of a device SolveState, from the host (stream-ordered).
-int put_state_int(hc_ctx* c, hc::SolveState* st, int hc::SolveState::*field, int v) {
-  int* dst = &(st->*field);
-  CU(cudaMemcpyAsync(dst, &v, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-  CU(cudaStreamSynchronize(c->stream));
-  return HC_OK;
-}
-
-// hc_step with lagged certification.  A pass launches the lagged graph once
-// per step, then certifies the last step.  A failed certification halts the
-// pass's later launches; hc_step then goes back to the failed step's start
-// (its input m, its pressure as warm start), redoes it with the context's own
-// certifying graph, and runs the call's remaining steps with that graph too
-// (a tolerance that two sweeps miss would otherwise cost a repair per step).
-// So every step returned is certified.
+// hc_step with lagged certification: the lagged graph once per step, then
+// the last step's certification.  A failed certification halts the later
+// launches; hc_step then goes back to the failed step's start (its input m,
+// its pressure as warm start), redoes it with the context's own certifying
+// graph and runs the call's remaining steps with that graph too (a tolerance
+// that two sweeps miss would otherwise cost a repair per step).  So every
+// step returned is certified.
 int step_lagged(hc_ctx* c, int nsteps) {
   if (!c->pipe_ready) {
     int rc = build_pipe_graph(c);
     if (rc) return rc;
   }
-  int done = 0;
-  while (done < nsteps) {
-    const int todo = nsteps - done;
-    int rc = read_state(c);
-    if (rc) return rc;
-    const hc::SolveState before = *c->st_host;
-    // nothing awaits certification at the start of a pass
-    rc = put_state_int(c, c->st_c, &hc::SolveState::cert_pending, 0);
-    if (!rc) rc = put_state_int(c, c->st_c, &hc::SolveState::done, 1);
-    if (!rc) rc = put_state_int(c, c->st, &hc::SolveState::halt, 0);
-    if (!rc) rc = put_state_int(c, c->st, &hc::SolveState::cert_failed, 0);
-    if (!rc) rc = put_state_int(c, c->st, &hc::SolveState::cert_steps, 0);
-    if (!rc) rc = put_state_int(c, c->st, &hc::SolveState::pipelined, 1);
-    if (!rc) rc = use_handles(c, c->h_pipe, c->h_pipe_gate);
-    if (!rc) rc = set_graph_mode(c, 1);
-    if (rc) return rc;
-    c->batch_handles = 0;
-    for (int k = 0; k < todo; ++k) CU(cudaGraphLaunch(c->gexec_pipe, c->stream));
-    cert_resid_launch(c, c->stream);  // the last step's certification
-    hc::commit_flags(c->st, c->st_c, 1, c->stream);
-    c->launches += 1;
-    CU(cudaGetLastError());
-    rc = read_state(c);
-    if (!rc) rc = put_state_int(c, c->st, &hc::SolveState::pipelined, 0);
-    if (!rc) rc = set_graph_mode(c, 0);
-    if (rc) return rc;
-    const hc::SolveState& h = *c->st_host;
-    const long long steps_a = h.acc_steps - before.acc_steps;
-    c->launches += kPipeFixedKernels * steps_a + (long long)(todo - steps_a) +
-                   (long long)c->graph_nodes_body * (h.acc_iters - before.acc_iters) +
-                   (long long)c->graph_nodes_outer * (h.acc_mid - before.acc_mid);
-    if (!h.cert_failed) return HC_OK;
-    // back to the start of the step that failed its certification
-    done += h.cert_steps - 1;
-    for (int k = 0; k < 2; ++k)
-      CU(cudaMemcpyAsync(c->m[k], c->m_prev[k], sizeof(float) * c->n, cudaMemcpyDeviceToDevice,
-                         c->stream));
-    CU(cudaMemcpyAsync(c->p64, c->p_saved, sizeof(cx<double>) * c->ns, cudaMemcpyDeviceToDevice,
+  int rc = use_handles(c, c->h_pipe, c->h_pipe_gate);
+  if (!rc) rc = set_graph_mode(c, 1);
+  if (rc) return rc;
+  c->batch_handles = 0;
+  hc::lag_mark(c->st, c->st_c, 1, c->stream);
+  for (int k = 0; k < nsteps; ++k) CU(cudaGraphLaunch(c->gexec_pipe, c->stream));
+  cert_resid_launch(c, c->stream);  // the last step's certification
+  hc::commit_flags(c->st, c->st_c, 1, c->stream);
+  hc::lag_mark(c->st, c->st_c, 0, c->stream);
+  c->launches += 3;
+  CU(cudaGetLastError());
+  rc = read_state(c);
+  if (!rc) rc = set_graph_mode(c, 0);
+  if (rc) return rc;
+  const hc::SolveState& h = *c->st_host;  // counters were reset at the call's start
+  c->launches += kPipeFixedKernels * (long long)h.acc_steps + (long long)(nsteps - h.acc_steps) +
+                 (long long)c->graph_nodes_body * h.acc_iters +
+                 (long long)c->graph_nodes_outer * h.acc_mid;
+  if (!h.cert_failed) return HC_OK;
+  // back to the start of the step that failed its certification, then the
+  // rest of the call with the certifying graph
+  const int done = h.cert_steps - 1;
+  for (int k = 0; k < 2; ++k)
+    CU(cudaMemcpyAsync(c->m[k], c->m_prev[k], sizeof(float) * c->n, cudaMemcpyDeviceToDevice,
                        c->stream));
-    hc::msum<float>(c->gf, (const float*)c->m[0], (const float*)c->m[1], c->st, c->stream);
-    c->launches += 1;
-    if (!c->graph_ready) {
-      rc = build_graph(c);
-      if (rc) return rc;
-    }
-    rc = read_state(c);
+  CU(cudaMemcpyAsync(c->p64, c->p_saved, sizeof(cx<double>) * c->ns, cudaMemcpyDeviceToDevice,
+                     c->stream));
+  hc::msum<float>(c->gf, (const float*)c->m[0], (const float*)c->m[1], c->st, c->stream);
+  c->launches += 1;
+  if (!c->graph_ready) {
+    rc = build_graph(c);
     if (rc) return rc;
-    const hc::SolveState b2 = *c->st_host;
-    rc = use_handles(c, c->h_own);
-    if (!rc) rc = set_graph_mode(c, 1);
-    if (rc) return rc;
-    for (int k = done; k < nsteps; ++k) CU(cudaGraphLaunch(c->gexec, c->stream));
-    rc = read_state(c);
-    if (!rc) rc = set_graph_mode(c, 0);
-    if (rc) return rc;
-    const hc::SolveState& h2 = *c->st_host;
-    c->launches += (long long)c->graph_nodes_fixed * (h2.acc_steps - b2.acc_steps) +
-                   (long long)c->graph_nodes_body * (h2.acc_iters - b2.acc_iters) +
-                   (long long)c->graph_nodes_outer *
-                       ((h2.acc_res_full - b2.acc_res_full) + (h2.acc_mid - b2.acc_mid));
-    done = nsteps;
   }
+  const hc::SolveState b2 = h;
+  rc = use_handles(c, c->h_own);
+  if (!rc) rc = set_graph_mode(c, 1);
+  if (rc) return rc;
+  for (int k = done; k < nsteps; ++k) CU(cudaGraphLaunch(c->gexec, c->stream));
+  rc = read_state(c);
+  if (!rc) rc = set_graph_mode(c, 0);
+  if (rc) return rc;
+  const hc::SolveState& h2 = *c->st_host;
+  c->launches += (long long)c->graph_nodes_fixed * (h2.acc_steps - b2.acc_steps) +
+                 (long long)c->graph_nodes_body * (h2.acc_iters - b2.acc_iters) +
+                 (long long)c->graph_nodes_outer *
+                     ((h2.acc_res_full - b2.acc_res_full) + (h2.acc_mid - b2.acc_mid));
   return HC_OK;
 }
 
@@ -2194,7 +2170,7 @@ int hc_step(hc_ctx* c, int nsteps, hc_step_stats* last) {
   if (nsteps == 0) return HC_OK;
   hc::reset_accum(c->st, c->stream);
   c->launches += 1;
-  if (pipe_on(c)) {
+  if (pipe_on(c, nsteps)) {
     int rc = step_lagged(c, nsteps);
     if (rc) return rc;
   } else if (c->prm.use_graph) {

@@ -470,6 +470,7 @@ void commit_copy(const SolveState* st, const SolveState* sc, float* const* m, fl
                  const float* const* mt, const cx<double>* p64, cx<double>* ps, size_t n, size_t ns,
                  cudaStream_t s);
 void commit_flags(SolveState* st, SolveState* sc, int final_cert, cudaStream_t s);
+void lag_mark(SolveState* st, SolveState* sc, int on, cudaStream_t s);
 // FP64 FMA throughput of the current device (TFLOP/s, FMA = 2 flops), reps timed launches on s.
 int fma_peak(int reps, cudaStream_t s, double* tflops);
 void set_smem_limits_df();

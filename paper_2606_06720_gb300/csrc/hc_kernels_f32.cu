@@ -105,6 +105,22 @@ __global__ void k_commit_flags(SolveState* st, SolveState* sc, int final_cert) {
   }
 }
 
+// Start (on = 1) or end (on = 0) of a pass of lagged steps: nothing awaits
+// certification at its start, and no halt or failure is pending.
+__global__ void k_lag_mark(SolveState* st, SolveState* sc, int on) {
+  st->pipelined = on;
+  if (on) {
+    sc->cert_pending = 0;
+    sc->done = 1;
+    st->halt = 0;
+    st->cert_failed = 0;
+    st->cert_steps = 0;
+  }
+}
+void lag_mark(SolveState* st, SolveState* sc, int on, cudaStream_t s) {
+  k_lag_mark<<<1, 1, 0, s>>>(st, sc, on);
+}
+
 void commit_copy(const SolveState* st, const SolveState* sc, float* const* m, float* const* mp,
                  const float* const* mt, const cx<double>* p64, cx<double>* ps, size_t n, size_t ns,
                  cudaStream_t s) {
