@@ -78,8 +78,12 @@ def test_invalid_params_are_rejected_on_the_host(lib):
 
 def test_precond_and_refinement_options_on_the_host(lib):
     """The preconditioner option takes the two values of reading R3 only, and
-    the FP64-refined mode's workspace holds the double-float copy of S that
-    its mid-step residual reads (n/2 packed values of 16 bytes)."""
+    the FP64-refined mode's workspace holds, beyond the double-float mode's,
+    the double-float copy of S that its mid-step residual reads and the
+    buffers of the lagged certification: m of the step awaiting it and of the
+    step in flight (4 FP32 fields), its pressure and its two FP64 gradient
+    fields (3 FP64 spectra), and its own partial sums (8 doubles per CTA of the
+    largest reducing grid, at least 1216) and solve state."""
     from paper_2606_06720_gb300 import _binding as Bd
     n = (64, 32)
     g = Bd.hc_grid(2, (C.c_int * 3)(n[0], n[1], 1), (C.c_double * 3)(1.0, 1.0, 1.0))
@@ -103,7 +107,9 @@ def test_precond_and_refinement_options_on_the_host(lib):
         assert Bd.hc_workspace_size(C.byref(g), C.byref(params(precision=prec)), C.byref(nb)) == 0
         sizes[prec] = nb.value
     extra = sizes[Bd.HC_FP32_REFINED] - sizes[Bd.HC_FP32_REFINED_DF]
-    assert n[0] // 2 * n[1] * 16 <= extra <= n[0] // 2 * n[1] * 16 + 256
+    spec16 = n[0] // 2 * n[1] * 16                       # one packed spectrum of 16-byte values
+    fixed = spec16 + 4 * n[0] * n[1] * 4 + 3 * spec16 + 8 * 8 * max(n[0] // 2, n[1], 1216)
+    assert fixed < extra <= fixed + 4096 + 8 * 256       # + the solve state, alignment
 
 
 # --- the bounds-checked build (libhc_gb300_check.so, HC_CHECK=1) -------------------------------
