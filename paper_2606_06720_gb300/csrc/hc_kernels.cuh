@@ -460,17 +460,44 @@ struct DotAcc<float> {
 // exact TwoSum of the high parts (about 48 significant bits): on this part
 // the FP64 pipe is narrow, and this keeps the per-thread shuffle reduction of
 // FP32 kernels off it.
-__device__ __forceinline__ double warp_sum_pair(float hi, float lo) {
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float h2, float l2) {
+  const float t = hi + h2;
+  const float bp = t - hi;
+  lo = lo + l2 + ((hi - (t - bp)) + (h2 - bp));
+  hi = t;
+}
+__device__ __forceinline__ void warp_pair(float& hi, float& lo) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     const float h2 = __shfl_down_sync(0xffffffffu, hi, off);
     const float l2 = __shfl_down_sync(0xffffffffu, lo, off);
-    const float t = hi + h2;
-    const float bp = t - hi;
-    lo = lo + l2 + ((hi - (t - bp)) + (h2 - bp));
-    hi = t;
+    pair_add(hi, lo, h2, l2);
   }
+}
+__device__ __forceinline__ double warp_sum_pair(float hi, float lo) {
+  warp_pair(hi, lo);
   return (double)hi + (double)lo;
+}
+
+// This CTA's float-pair partial (hi + lo of every thread), reduced in fixed
+// order and stored as one double in partials[bx] with a plain store: no fence
+// and no ticket.  Its reader is a later kernel (kernel boundaries order it).
+// Only the block total reaches the FP64 pipe, which on this part is narrow.
+__device__ __forceinline__ void cta_pair_partial(float hi, float lo, double* partials, int bx) {
+  __shared__ float s_pair[64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  warp_pair(hi, lo);
+  if (lane == 0) {
+    s_pair[2 * warp] = hi;
+    s_pair[2 * warp + 1] = lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float h = s_pair[0], l = s_pair[1];
+    for (int w = 1; w < nw; ++w) pair_add(h, l, s_pair[2 * w], s_pair[2 * w + 1]);
+    partials[(size_t)bx * kPartialStride] = (double)h + (double)l;
+  }
 }
 
 template <>
@@ -718,6 +745,19 @@ __device__ __forceinline__ void cg_alpha_from(SolveState* st, double gkg, double
   st->first = 0;
 }
 
+// Step length of an FP32 CG iteration from the row pass's per-CTA partials of
+// <d, A d> (cta_pair_partial): run by one CTA of the divergence pass that
+// follows it, which sums them in fixed order and calls cg_alpha_from.  The
+// update kernel after that pass reads alpha.
+__device__ __forceinline__ void cg_alpha_finish(const Geo<float>& g, SolveState* st) {
+  const int np = g.rpipe ? g.rgrid : (g.ny >> g.lrpc);  // CTAs of the row pass
+  double a[1] = {0.0};
+  for (int i = threadIdx.x; i < np; i += blockDim.x) a[0] += g.partials[(size_t)i * kPartialStride];
+  block_sum<1>(a);
+  if (threadIdx.x == 0) cg_alpha_from(st, a[0], (double)g.nx * (double)g.ny);
+  __syncthreads();  // the block_sum scratch is reused by the caller
+}
+
 // Row pass of the operator apply.  The CTA's rows of m and r are staged into
 // shared memory with cp.async at the start, so their latency overlaps the
 // inverse transform.  DOT: the CG variant (alpha, see cg_alpha_from).  NV
@@ -791,16 +831,15 @@ __device__ __forceinline__ void row_apply_body(Geo<T> g, const cx<T>* Gx, const 
   fft_canon<-1, NV, true>(v, sl, 1, j, g.lnx, g.twx);
   store_rows_r2c<NV>(v, sl, j, N, H, Qa, Qb);
   if (DOT) {
-    double t1[1];
-    bool last;
     if constexpr (std::is_same<T, float>::value) {
-      double a1[1] = {warp_sum_pair(gkg, 0.0f)};
-      last = last_cta_sum<1, true>(a1, g.partials, &st->ticket[TK_DIV], t1);
+      // FP32: the CTA's partial only; the divergence pass forms alpha
+      // (cg_alpha_finish), so this pass ends without a fence or ticket
+      cta_pair_partial(gkg, 0.0f, g.partials, blockIdx.x);
     } else {
-      double a1[1] = {(double)gkg};
-      last = last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1);
+      double a1[1] = {(double)gkg}, t1[1];
+      if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0)
+        cg_alpha_from(st, t1[0], (double)g.nx * (double)g.ny);
     }
-    if (last && threadIdx.x == 0) cg_alpha_from(st, t1[0], (double)g.nx * (double)g.ny);
   }
 }
 template <typename T, typename Tm, bool DOT, int NV>
@@ -882,11 +921,7 @@ __global__ void __launch_bounds__(512) kp_row_apply(Geo<float> g, const cx<float
     buf ^= 1;
   }
   cp_async_wait_all();
-  if (DOT) {
-    double a1[1] = {gkg.value()}, t1[1];
-    if (last_cta_sum<1>(a1, g.partials, &st->ticket[TK_DIV], t1) && threadIdx.x == 0)
-      cg_alpha_from(st, t1[0], (double)g.nx * (double)g.ny);
-  }
+  if (DOT) cta_pair_partial(gkg.hi, gkg.lo, g.partials, blockIdx.x);  // alpha: cg_alpha_finish
 }
 
 // Pointwise sums of the discrete energy (Section 2.5) at one point, from m^k
@@ -1327,6 +1362,8 @@ __device__ __forceinline__ void col_div_body(Geo<T> g, const cx<T>* __restrict__
                                                  cx<T>* __restrict__ out, cx<float>* __restrict__ r32,
                                                  cx<float>* __restrict__ delta32, SolveState* st) {
   if ((MODE == CD_CG || MODE == CD_CERT) && st->done) return;
+  if constexpr (MODE == CD_CG && std::is_same<T, float>::value)
+    if (blockIdx.x == 0) cg_alpha_finish(g, st);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const ColIdx c = col_idx(g);
@@ -1723,6 +1760,8 @@ __global__ void __launch_bounds__(512) kp_col_div(Geo<T> g, const cx<T>* __restr
                                                   cx<T>* __restrict__ out, cx<float>* __restrict__ r32,
                                                   cx<float>* __restrict__ delta32, SolveState* st) {
   if (MODE == CD_CG && st->done) return;
+  if constexpr (MODE == CD_CG && std::is_same<T, float>::value)
+    if (blockIdx.x == 0) cg_alpha_finish(g, st);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const int H = g.H, se = slab_elems(g), ntiles = g.H >> g.ltc;
