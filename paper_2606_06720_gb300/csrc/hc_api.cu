@@ -721,6 +721,13 @@ hc::SplitCoef split_coef(const hc_params& p) {
   s.two1mg_dt = 2.0 * (1.0 - p.gamma) * p.dt;
   s.pow_a = 2.0 * (1.0 - p.gamma);
   s.pow_b = s.gamma_is_one ? 0.0 : 1.0 / (2.0 * (1.0 - p.gamma));
+  s.f_c2dt = (float)s.c2dt;
+  s.f_gamma = (float)s.gamma;
+  s.f_dt = (float)s.dt;
+  s.f_exp_mdt = (float)s.exp_mdt;
+  s.f_two1mg_dt = (float)s.two1mg_dt;
+  s.f_pow_a = (float)s.pow_a;
+  s.f_pow_b = (float)s.pow_b;
   return s;
 }
 

@@ -84,6 +84,11 @@ struct SolveState {
   double thresh2;            // CG stops when rnorm2 <= thresh2
   double kappa;              // trace(Kbar) / dim of this step's preconditioner (reported)
   double kbar[6];            // preconditioner matrix Kbar (xx, yy, zz, xy, xz, yz), reading R3
+  // FP32 copies of kbar, alpha and beta, written with them by the one thread
+  // that sets them: the FP32 kernels read these, so their threads do no
+  // double-to-float conversions (the FP64 pipe of this part is narrow)
+  float kbar_f[6];
+  float alpha_f, beta_f;
   double mean_r;             // mean of r (set with r)
   double msum;               // sum |m|^2 of the current m
   double mm[6];              // sum m_a m_b of the current m (xx, yy, zz, xy, xz, yz); follows msum
@@ -250,6 +255,8 @@ struct SplitCoef {
   double pow_a;      // 2 (1 - gamma)
   double pow_b;      // 1 / (2 (1 - gamma))
   int gamma_is_one;
+  // the same rounded to FP32 on the host, for the FP32 kernels (cfv)
+  float f_c2dt, f_gamma, f_dt, f_exp_mdt, f_two1mg_dt, f_pow_a, f_pow_b;
 };
 
 // 2D grids whose sizes are not powers of two (hc_generic.cu): N = 2^a 3^b 5^c

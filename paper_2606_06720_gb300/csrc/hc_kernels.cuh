@@ -365,7 +365,7 @@ __device__ __forceinline__ void fft_canon(cx<T> (&v)[NV][8], cx<T>* const* sl, i
 
 // ------------------------------------------------------------------ reductions
 // Block-reduce K doubles; thread 0 gets the block total.
-// WARP_DONE: the values are already warp sums held by lane 0 (warp_sum_pair).
+// WARP_DONE: the values are already warp sums held by lane 0.
 template <int K, bool WARP_DONE = false>
 __device__ __forceinline__ void block_sum(double (&v)[K]) {
   __shared__ double red[32 * K];
@@ -395,11 +395,13 @@ __device__ __forceinline__ void block_sum(double (&v)[K]) {
 // Write this CTA's K partial sums; returns true (in every thread) in the CTA
 // that arrived last, which then holds the grand totals in tot (fixed order:
 // CTA 0, 1, 2, ...), and re-arms the ticket.
-template <int K, bool WARP_DONE = false>
+// PRE: 0 per-thread values, 1 warp sums in lane 0, 2 the CTA's
+// totals already in thread 0 (cta_pair_sums).
+template <int K, int PRE = 0>
 __device__ __forceinline__ bool last_cta_sum(double (&v)[K], double* partials,
                                              unsigned int* ticket, double (&tot)[K]) {
   __shared__ unsigned int s_last;
-  block_sum<K, WARP_DONE>(v);
+  if constexpr (PRE < 2) block_sum<K, PRE == 1>(v);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) partials[blockIdx.x * kPartialStride + k] = v[k];
@@ -456,10 +458,10 @@ struct DotAcc<float> {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-// Warp sum of float pairs hi + lo into lane 0, in fixed order, each step an
-// exact TwoSum of the high parts (about 48 significant bits): on this part
-// the FP64 pipe is narrow, and this keeps the per-thread shuffle reduction of
-// FP32 kernels off it.
+// Float-pair sums (about 48 significant bits): each addition an exact TwoSum
+// of the high parts.  warp_pair sums a warp's pairs into lane 0 in fixed
+// order.  On this part the FP64 pipe is narrow, and these keep the shuffle
+// reductions of FP32 kernels off it.
 __device__ __forceinline__ void pair_add(float& hi, float& lo, float h2, float l2) {
   const float t = hi + h2;
   const float bp = t - hi;
@@ -474,30 +476,40 @@ __device__ __forceinline__ void warp_pair(float& hi, float& lo) {
     pair_add(hi, lo, h2, l2);
   }
 }
-__device__ __forceinline__ double warp_sum_pair(float hi, float lo) {
-  warp_pair(hi, lo);
-  return (double)hi + (double)lo;
-}
 
-// This CTA's float-pair partial (hi + lo of every thread), reduced in fixed
-// order and stored as one double in partials[bx] with a plain store: no fence
-// and no ticket.  Its reader is a later kernel (kernel boundaries order it).
-// Only the block total reaches the FP64 pipe, which on this part is narrow.
-__device__ __forceinline__ void cta_pair_partial(float hi, float lo, double* partials, int bx) {
-  __shared__ float s_pair[64];
+// The CTA's sums of K float pairs (hi[k] + lo[k] of every thread), in fixed
+// order, as doubles in thread 0: only those K conversions reach the FP64
+// pipe, which on this part is narrow.
+template <int K>
+__device__ __forceinline__ void cta_pair_sums(float (&hi)[K], float (&lo)[K], double (&tot)[K]) {
+  __shared__ float s_pair[64 * K];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
-  warp_pair(hi, lo);
-  if (lane == 0) {
-    s_pair[2 * warp] = hi;
-    s_pair[2 * warp + 1] = lo;
-  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) warp_pair(hi[k], lo[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      s_pair[2 * (warp * K + k)] = hi[k];
+      s_pair[2 * (warp * K + k) + 1] = lo[k];
+    }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float h = s_pair[0], l = s_pair[1];
-    for (int w = 1; w < nw; ++w) pair_add(h, l, s_pair[2 * w], s_pair[2 * w + 1]);
-    partials[(size_t)bx * kPartialStride] = (double)h + (double)l;
-  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float h = s_pair[2 * k], l = s_pair[2 * k + 1];
+      for (int w = 1; w < nw; ++w) pair_add(h, l, s_pair[2 * (w * K + k)], s_pair[2 * (w * K + k) + 1]);
+      tot[k] = (double)h + (double)l;
+    }
+}
+// This CTA's float-pair partial stored as one double in partials[bx] with a
+// plain store: no fence and no ticket.  Its reader is a later kernel (kernel
+// boundaries order it).
+__device__ __forceinline__ void cta_pair_partial(float hi, float lo, double* partials, int bx) {
+  float h[1] = {hi}, l[1] = {lo};
+  double t[1];
+  cta_pair_sums<1>(h, l, t);
+  if (threadIdx.x == 0) partials[(size_t)bx * kPartialStride] = t[0];
 }
 
 template <>
@@ -527,8 +539,38 @@ struct Pc {
 };
 template <typename T>
 __device__ __forceinline__ Pc<T> pc_of(const SolveState* st) {
-  return Pc<T>{(T)st->kbar[0], (T)st->kbar[1], (T)st->kbar[2],
-               (T)st->kbar[3], (T)st->kbar[4], (T)st->kbar[5]};
+  if constexpr (std::is_same<T, float>::value)
+    return Pc<float>{st->kbar_f[0], st->kbar_f[1], st->kbar_f[2],
+                     st->kbar_f[3], st->kbar_f[4], st->kbar_f[5]};
+  else
+    return Pc<T>{(T)st->kbar[0], (T)st->kbar[1], (T)st->kbar[2],
+                 (T)st->kbar[3], (T)st->kbar[4], (T)st->kbar[5]};
+}
+// The CG scalars in the kernel's type (FP32: the copies kept beside them).
+template <typename T>
+__device__ __forceinline__ T st_alpha(const SolveState* st) {
+  if constexpr (std::is_same<T, float>::value) return st->alpha_f;
+  else return (T)st->alpha;
+}
+template <typename T>
+__device__ __forceinline__ T st_beta(const SolveState* st) {
+  if constexpr (std::is_same<T, float>::value) return st->beta_f;
+  else return (T)st->beta;
+}
+// A split-step coefficient in the kernel's type: FP32 kernels take the copy
+// rounded on the host.
+template <typename T>
+__device__ __forceinline__ T cfv(double d, float f) {
+  if constexpr (std::is_same<T, float>::value) return f;
+  else return (T)d;
+}
+// 2^-e in T, exactly (0 <= e < 126), from the exponent bits: the reciprocal
+// of a power-of-two point count without a division.
+template <typename T>
+__device__ __forceinline__ T exp2_neg(int e) {
+  const float f = __int_as_float((127 - e) << 23);
+  if constexpr (std::is_same<T, float>::value) return f;
+  else return T((double)f);
 }
 
 // Preconditioner symbol 1 / (xi~^T Kbar xi~) of the constant-coefficient
@@ -704,10 +746,21 @@ __device__ __forceinline__ void row_c2r_body(Geo<T> g, const cx<T>* A, const cx<
     }
   }
   if (kappa_update) {
-    double acc[4] = {(double)mxx, (double)myy, (double)mxy, d2.value()};
     if (!finite) st->nonfinite = 1;
-    double tot[4];
-    if (last_cta_sum<4>(acc, g.partials, &st->ticket[TK_MSUM], tot) && threadIdx.x == 0) {
+    double acc[4], tot[4];
+    bool last;
+    if constexpr (std::is_same<T, float>::value) {  // float pairs up to the CTA total
+      float h[4] = {mxx, myy, mxy, d2.hi}, l[4] = {0.0f, 0.0f, 0.0f, d2.lo};
+      cta_pair_sums<4>(h, l, acc);
+      last = last_cta_sum<4, 2>(acc, g.partials, &st->ticket[TK_MSUM], tot);
+    } else {
+      acc[0] = (double)mxx;
+      acc[1] = (double)myy;
+      acc[2] = (double)mxy;
+      acc[3] = d2.value();
+      last = last_cta_sum<4>(acc, g.partials, &st->ticket[TK_MSUM], tot);
+    }
+    if (last && threadIdx.x == 0) {
       set_mm2(st, tot[0], tot[1], tot[2]);
       if (diag) st->dm2 = tot[3];
     }
@@ -730,12 +783,14 @@ __device__ __forceinline__ void cg_alpha_from(SolveState* st, double gkg, double
   const double dq = gkg * n;
   if (dq > 0 && isfinite(dq)) {
     st->alpha = st->rho / dq;
+    st->alpha_f = (float)st->alpha;
   } else {
     // breakdown: <d, A d> is not positive (d without a component in the range
     // of A) or not finite.  The plain solve then stops unconverged unless its
     // residual already meets the tolerance; a refined inner solve leaves that
     // verdict to the FP64 residual that follows it.
     st->alpha = 0;
+    st->alpha_f = 0.0f;
     st->done = 1;
     if (!isfinite(dq))
       st->status = HC_ENONFINITE;
@@ -971,14 +1026,14 @@ __device__ __forceinline__ void split_point(T& ax, T& ay, T gx, T gy, T c2dt, co
     ay += t * gy;
   }
   if (cf.gamma_is_one) {
-    ax *= (T)cf.exp_mdt;
-    ay *= (T)cf.exp_mdt;
+    ax *= cfv<T>(cf.exp_mdt, cf.f_exp_mdt);
+    ay *= cfv<T>(cf.exp_mdt, cf.f_exp_mdt);
   } else {
     const T n2 = ax * ax + ay * ay;
     if (n2 > (T)0) {
       const T nm = hc_sqrt(n2);
-      const T bb = hc_pow(nm, (T)cf.pow_a) - (T)cf.two1mg_dt;
-      const T sc = bb >= (T)0 ? hc_pow(bb, (T)cf.pow_b) / nm : (T)0;
+      const T bb = hc_pow(nm, cfv<T>(cf.pow_a, cf.f_pow_a)) - cfv<T>(cf.two1mg_dt, cf.f_two1mg_dt);
+      const T sc = bb >= (T)0 ? hc_pow(bb, cfv<T>(cf.pow_b, cf.f_pow_b)) / nm : (T)0;
       ax *= sc;
       ay *= sc;
     }
@@ -1005,7 +1060,7 @@ __device__ __forceinline__ void row_split_body(Geo<T> g, const cx<T>* Gx, const 
   load_rows_c2r<1>(v, Ar, Br, j, N8);
   fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
   const size_t ro = (size_t)y * N;
-  const T c2dt = (T)cf.c2dt;
+  const T c2dt = cfv<T>(cf.c2dt, cf.f_c2dt);
   bool finite = true;
   const bool diag = st->diag != 0;
   EnergyAcc<T> en;
@@ -1015,7 +1070,7 @@ __device__ __forceinline__ void row_split_body(Geo<T> g, const cx<T>* Gx, const 
     const T gx = v[0][s].x, gy = v[0][s].y;
     T ax = mx[ro + x], ay = my[ro + x];
     if (diag)
-      en.add(rr[ro + x], gx * gx + gy * gy, ax * gx + ay * gy, ax * ax + ay * ay, (T)cf.gamma);
+      en.add(rr[ro + x], gx * gx + gy * gy, ax * gx + ay * gy, ax * ax + ay * ay, cfv<T>(cf.gamma, cf.f_gamma));
     split_point<T>(ax, ay, gx, gy, c2dt, cf);
     finite = finite && hc_finite(ax) && hc_finite(ay);
     v[0][s] = cmk<T>(ax, ay);
@@ -1142,6 +1197,7 @@ __device__ __forceinline__ void resid_refine_init(SolveState* st, double r64, do
 __device__ __forceinline__ void cg_step_finish(SolveState* st, double rr, double rz) {
   st->rnorm2 = rr;
   st->beta = st->rho > 0 ? rz / st->rho : 0.0;
+  st->beta_f = (float)st->beta;
   st->rho = rz;
   st->it += 1;
   st->total_it += 1;
@@ -1197,6 +1253,7 @@ __device__ __forceinline__ void step_begin_body(SolveState* st, int npts) {
     double v = 0.0;
     if (used) v = aniso ? st->mm[e] / (double)npts + (diag ? st->mean_r : 0.0) : (diag ? kiso : 0.0);
     st->kbar[e] = v;
+    st->kbar_f[e] = (float)v;
   }
   st->kappa = 0.0;
   for (int a = 0; a < st->dim; ++a) st->kappa += st->kbar[a] / (double)st->dim;
@@ -1304,14 +1361,14 @@ __device__ __forceinline__ void col_grad_body(Geo<T> g, cx<Tin>* in, const cx<T>
   const int H = g.H;
   const int se = slab_elems(g);
   cx<T>* const sl[2] = {sm + c.b, sm + se + c.b};
-  const T invn = (T)(1.0 / ((double)g.nx * (double)g.ny));
+  const T invn = exp2_neg<T>(g.lnx + g.lny);  // 1 / (nx ny)
   const T ax = g.kxd[c.kx] * invn;
   bool first = false, add_delta = false;
   T beta = 0;
   Pc<T> pc{};
   if (MODE == CG_DUPDATE) {
     first = st->first != 0;
-    beta = (T)st->beta;
+    beta = st_beta<T>(st);
     pc = pc_of<T>(st);
   }
   if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
@@ -1448,15 +1505,24 @@ __device__ __forceinline__ void col_div_body(Geo<T> g, const cx<T>* __restrict__
     if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
       resid_init(st, t2[0], t2[1]);
   } else if constexpr (MODE == CD_RESID_FIRST) {
-    double a2[2] = {r32acc.value(), rzacc.value()}, t2[2];
-    if (last_cta_sum<2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
+    float h[2] = {r32acc.hi, rzacc.hi}, l[2] = {r32acc.lo, rzacc.lo};
+    double a2[2], t2[2];
+    cta_pair_sums<2>(h, l, a2);  // float pairs up to the CTA total
+    if (last_cta_sum<2, 2>(a2, g.partials, &st->ticket[TK_RESID], t2) && threadIdx.x == 0)
       resid_first_init(st, t2[0], t2[1]);
   } else {
-    acc[0] = r64acc.value();
-    acc[1] = r32acc.value();
-    acc[2] = rzacc.value();
-    if (last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot) && threadIdx.x == 0)
-      resid_sweep_init(st, tot[0], tot[1], tot[2]);
+    bool last;
+    if constexpr (std::is_same<T, df64>::value) {  // all three sums are float pairs
+      float h[3] = {r64acc.s.hi, r32acc.hi, rzacc.hi}, l[3] = {r64acc.s.lo, r32acc.lo, rzacc.lo};
+      cta_pair_sums<3>(h, l, acc);
+      last = last_cta_sum<3, 2>(acc, g.partials, &st->ticket[TK_RESID], tot);
+    } else {
+      acc[0] = r64acc.value();
+      acc[1] = r32acc.value();
+      acc[2] = rzacc.value();
+      last = last_cta_sum<3>(acc, g.partials, &st->ticket[TK_RESID], tot);
+    }
+    if (last && threadIdx.x == 0) resid_sweep_init(st, tot[0], tot[1], tot[2]);
   }
 }
 template <typename T, int MODE>
@@ -1514,7 +1580,7 @@ __device__ __forceinline__ void col_heat_body(Geo<T> g, cx<T>* Mx, cx<T>* My, So
     v[1][s] = My[idx];
   }
   fft_canon<-1, 2>(v, sl, g.tc, c.j, g.lny, g.twy);
-  const T invn = (T)(1.0 / ((double)g.nx * (double)ny));
+  const T invn = exp2_neg<T>(g.lnx + g.lny);  // 1 / (nx ny)
   if (blockIdx.x == 0) {
     // The packed column holds kx = 0 (A) and kx = nx/2 (B) as A + iB; their heat
     // factors differ, so separate with the ky <-> -ky symmetry:
@@ -1676,13 +1742,13 @@ __global__ void __launch_bounds__(512) kp_col_grad(Geo<T> g, cx<T>* in, const cx
   constexpr int NS = MODE == CG_DUPDATE ? 2 : 1;
   const int H = g.H, se = slab_elems(g), ntiles = g.H >> g.ltc;
   const int b = threadIdx.x & (g.tc - 1), j = threadIdx.x >> g.ltc, NY8 = 1 << (g.lny - 3);
-  const T invn = (T)(1.0 / ((double)g.nx * (double)g.ny));
+  const T invn = exp2_neg<T>(g.lnx + g.lny);  // 1 / (nx ny)
   bool first = false, add_delta = false;
   T beta = 0;
   Pc<T> pc{};
   if (MODE == CG_DUPDATE) {
     first = st->first != 0;
-    beta = (T)st->beta;
+    beta = st_beta<T>(st);
     pc = pc_of<T>(st);
   }
   if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
@@ -1878,7 +1944,7 @@ __global__ void __launch_bounds__(512) kp_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* M
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const int H = g.H, ny = g.ny, se = slab_elems(g), ntiles = g.H >> g.ltc;
   const int b = threadIdx.x & (g.tc - 1), j = threadIdx.x >> g.ltc, NY8 = 1 << (g.lny - 3);
-  const T invn = (T)(1.0 / ((double)g.nx * (double)ny));
+  const T invn = exp2_neg<T>(g.lnx + g.lny);  // 1 / (nx ny)
   const bool diag = st && st->diag;
   DotAcc<T> ga;
   int half = 0;
@@ -1988,7 +2054,7 @@ __device__ __forceinline__ void cg_update_body(Geo<T> g, cx<T>* __restrict__ x,
       cudaGraphSetConditional(st->h_cur, 0u);
     return;
   }
-  const T alpha = (T)st->alpha;
+  const T alpha = st_alpha<T>(st);
   const Pc<T> pc = pc_of<T>(st);
   const size_t total = (size_t)g.ny * g.H;
   DotAcc<T> rr, rz;
@@ -2027,8 +2093,10 @@ __device__ __forceinline__ void cg_update_body(Geo<T> g, cx<T>* __restrict__ x,
   double tot[2];
   bool last;
   if constexpr (std::is_same<T, float>::value) {
-    double acc[2] = {warp_sum_pair(rr.hi, rr.lo), warp_sum_pair(rz.hi, rz.lo)};
-    last = last_cta_sum<2, true>(acc, g.partials, &st->ticket[TK_UPDATE], tot);
+    float h[2] = {rr.hi, rz.hi}, l[2] = {rr.lo, rz.lo};
+    double acc[2];
+    cta_pair_sums<2>(h, l, acc);
+    last = last_cta_sum<2, 2>(acc, g.partials, &st->ticket[TK_UPDATE], tot);
   } else {
     double acc[2] = {rr.value(), rz.value()};
     last = last_cta_sum<2>(acc, g.partials, &st->ticket[TK_UPDATE], tot);
@@ -2110,7 +2178,7 @@ template <typename T>
 __device__ __forceinline__ void relax_jac(T ax, T ay, const SplitCoef& cf, T& c1, T& c2) {
   c2 = (T)0;
   if (cf.gamma_is_one) {
-    c1 = (T)cf.exp_mdt;
+    c1 = cfv<T>(cf.exp_mdt, cf.f_exp_mdt);
     return;
   }
   const T n2 = ax * ax + ay * ay;
@@ -2119,14 +2187,14 @@ __device__ __forceinline__ void relax_jac(T ax, T ay, const SplitCoef& cf, T& c1
     return;
   }
   const T rho = hc_sqrt(n2);
-  const T e = (T)cf.pow_a;  // 2 (1 - gamma)
-  const T beta = hc_pow(rho, e) - (T)cf.two1mg_dt;
+  const T e = cfv<T>(cf.pow_a, cf.f_pow_a);  // 2 (1 - gamma)
+  const T beta = hc_pow(rho, e) - cfv<T>(cf.two1mg_dt, cf.f_two1mg_dt);
   if (!(beta > (T)0)) {
     c1 = (T)0;
     return;
   }
-  const T f = hc_pow(beta, (T)cf.pow_b);                         // new modulus
-  const T fp = hc_pow(beta, (T)cf.pow_b - (T)1) * hc_pow(rho, e - (T)1);  // d f / d rho
+  const T f = hc_pow(beta, cfv<T>(cf.pow_b, cf.f_pow_b));                         // new modulus
+  const T fp = hc_pow(beta, cfv<T>(cf.pow_b, cf.f_pow_b) - (T)1) * hc_pow(rho, e - (T)1);  // d f / d rho
   const T sv = f / rho;
   c1 = sv;
   c2 = (fp - sv) / n2;
@@ -2154,7 +2222,7 @@ __global__ void __launch_bounds__(512) k_row_adj_point(Geo<T> g, cx<T>* G0, cx<T
   }
   fft_canon<+1, 2, true>(v, sl, 1, j, g.lnx, g.twx);
   const size_t ro = (size_t)y * N;
-  const T c2dt = (T)cf.c2dt, dt = (T)cf.dt;
+  const T c2dt = cfv<T>(cf.c2dt, cf.f_c2dt), dt = cfv<T>(cf.dt, cf.f_dt);
   DotAcc<T> dc;
   cx<T> w[1][8];
 #pragma unroll

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) k3_zgrad(Geo<T> g, cx<Tin>* in, const cx<
   const CIdx3 c = cidx3(p);
   const int se = slab3(p);
   cx<T>* const sl[3] = {sm + c.b, sm + se + c.b, sm + 2 * se + c.b};
-  const T invn = (T)(1.0 / ((double)g.nx * (double)g.ny * (double)g.nz));
+  const T invn = exp2_neg<T>(g.lnx + g.lny + g.lnz);  // 1 / (nx ny nz)
   const int kx = c.col & (g.H - 1), ky = c.col >> g.lH;
   const T ax = g.kxd[kx] * invn, ay = g.kyd[ky] * invn;
   bool first = false, add_delta = false;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k3_zgrad(Geo<T> g, cx<Tin>* in, const cx<
   Pc<T> pc{};
   if (MODE == CG_DUPDATE) {
     first = st->first != 0;
-    beta = (T)st->beta;
+    beta = st_beta<T>(st);
     pc = pc_of<T>(st);
   }
   if (MODE == CG_ADDDELTA) add_delta = st->sweeps > 0;
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(256) k3_row_apply(Geo<T> g, Tri<cx<T>*> G, Tri
 template <typename T>
 __device__ __forceinline__ void act_relax3(T& ax, T& ay, T& az, T gx, T gy, T gz,
                                            const SplitCoef& cf) {
-  const T c2dt = (T)cf.c2dt;
+  const T c2dt = cfv<T>(cf.c2dt, cf.f_c2dt);
   const T mg = ax * gx + ay * gy + az * gz;
   if (mg != (T)0) {
     const T z = c2dt * (gx * gx + gy * gy + gz * gz);
@@ -414,15 +414,15 @@ __device__ __forceinline__ void act_relax3(T& ax, T& ay, T& az, T gx, T gy, T gz
     az += t * gz;
   }
   if (cf.gamma_is_one) {
-    ax *= (T)cf.exp_mdt;
-    ay *= (T)cf.exp_mdt;
-    az *= (T)cf.exp_mdt;
+    ax *= cfv<T>(cf.exp_mdt, cf.f_exp_mdt);
+    ay *= cfv<T>(cf.exp_mdt, cf.f_exp_mdt);
+    az *= cfv<T>(cf.exp_mdt, cf.f_exp_mdt);
   } else {
     const T n2 = ax * ax + ay * ay + az * az;
     if (n2 > (T)0) {
       const T nm = hc_sqrt(n2);
-      const T bb = hc_pow(nm, (T)cf.pow_a) - (T)cf.two1mg_dt;
-      const T sc = bb >= (T)0 ? hc_pow(bb, (T)cf.pow_b) / nm : (T)0;
+      const T bb = hc_pow(nm, cfv<T>(cf.pow_a, cf.f_pow_a)) - cfv<T>(cf.two1mg_dt, cf.f_two1mg_dt);
+      const T sc = bb >= (T)0 ? hc_pow(bb, cfv<T>(cf.pow_b, cf.f_pow_b)) / nm : (T)0;
       ax *= sc;
       ay *= sc;
       az *= sc;
@@ -457,9 +457,9 @@ __global__ void __launch_bounds__(256) k3_row_split(Geo<T> g, Tri<cx<T>*> G, Tri
       const T g0x = v[0][s].x, g0y = v[0][s].y, g0z = v[2][s].x;
       const T g1x = v[1][s].x, g1y = v[1][s].y, g1z = v[2][s].y;
       en.add(rr[o0 + x], g0x * g0x + g0y * g0y + g0z * g0z, ax * g0x + ay * g0y + az * g0z,
-             ax * ax + ay * ay + az * az, (T)cf.gamma);
+             ax * ax + ay * ay + az * az, cfv<T>(cf.gamma, cf.f_gamma));
       en.add(rr[o1 + x], g1x * g1x + g1y * g1y + g1z * g1z, bx * g1x + by * g1y + bz * g1z,
-             bx * bx + by * by + bz * bz, (T)cf.gamma);
+             bx * bx + by * by + bz * bz, cfv<T>(cf.gamma, cf.f_gamma));
     }
     act_relax3(ax, ay, az, v[0][s].x, v[0][s].y, v[2][s].x, cf);
     act_relax3(bx, by, bz, v[1][s].x, v[1][s].y, v[2][s].y, cf);
@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(256) k3_row_split(Geo<T> g, Tri<cx<T>*> G, Tri
   if (diag) en.finish(g.partials, st);
   // diffusion along x: a real, even multiplier on complex rows
   fft_canon<-1, 3, true>(v, sl, 1, r.j, g.lnx, g.twx);
-  const T invN = (T)(1.0 / (double)N);
+  const T invN = exp2_neg<T>(g.lnx);  // 1 / N, N = nx
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int k = r.j + s * r.N8;
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(256) k3_heat(Geo<T> g, int axis, Tri<cx<T>*> M
     for (int q = 0; q < 3; ++q) v[q][s] = M.v[q][idx];
   }
   fft_canon<-1, 3>(v, sl, 1 << p.ltc, c.j, p.lL, tw);
-  const T invL = (T)(1.0 / (double)(1 << p.lL));
+  const T invL = exp2_neg<T>(p.lL);
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const T f = h[c.j + s * c.L8] * invL;
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k3_cg_update(Geo<
       cudaGraphSetConditional(st->h_cur, 0u);
     return;
   }
-  const T alpha = (T)st->alpha;
+  const T alpha = st_alpha<T>(st);
   const Pc<T> pc = pc_of<T>(st);
   const size_t total = (size_t)g.nz * g.ny * g.H;
   DotAcc<T> rr, rz;
@@ -649,6 +649,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k3_cg_update(Geo<
     const double rho_new = tot[1];
     st->rnorm2 = tot[0];
     st->beta = st->rho > 0 ? rho_new / st->rho : 0.0;
+    st->beta_f = (float)st->beta;
     st->rho = rho_new;
     st->it += 1;
     st->total_it += 1;
