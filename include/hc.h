@@ -254,7 +254,8 @@ int hc_spectrum(hc_ctx* ctx, const double* f, double* out, size_t count);
 
 /* Launch shapes of the FFT passes, per arithmetic precision ([0] FP32
  * kernels, [1] FP64 kernels).  col_tile: packed columns per column-pass CTA
- * (power of two, col_tile*ny/8 <= 512 threads, col_tile <= nx/2, <= 32);
+ * (power of two, col_tile*ny/8 <= 1024 threads for [0] and <= 512 for [1],
+ * col_tile <= nx/2, <= 32);
  * row_rows: rows per row-pass CTA (power of two, row_rows*nx/8 <= 512,
  * row_rows <= ny), col_pipe (see below).  Results do not depend on them
  * beyond the order of floating-point sums. */

@@ -38,7 +38,7 @@ _WEIGHT = {"cg_grad": 20, "cg_apply": 20, "cg_div": 20}
 
 # Bumped whenever the kernels' launch-shape trade-offs change, so cached
 # choices made for older kernels are not reused.
-_KERNELS_VERSION = 6
+_KERNELS_VERSION = 7
 
 
 def _key(solver) -> str:
@@ -47,13 +47,15 @@ def _key(solver) -> str:
     return f"{name}|{solver.n[0]}x{solver.n[1]}|{solver.precision}|k{_KERNELS_VERSION}"
 
 
-def _candidates(solver, knob: str):
+def _candidates(solver, knob: str, idx: int = 1):
+    """Admissible values of a launch-shape knob: FP32 column passes ([0]) take
+    CTAs of up to 1024 threads, the FP64 ones and the row passes up to 512."""
     nx, ny = solver.n
     out = []
     v = 1
     while v <= 32:
         if knob == "col_tile":
-            ok = v <= nx // 2 and v * (ny // 8) <= 512
+            ok = v <= nx // 2 and v * (ny // 8) <= (1024 if idx == 0 else 512)
         else:
             ok = v <= ny and v * (nx // 8) <= 512
         if ok:
@@ -98,7 +100,7 @@ def autotune(solver, reps: int = 20, use_cache: bool = True, verbose: bool = Fal
     measured = {}
     for (knob, idx), kernels in _FAMILIES[prec].items():
         times = {}
-        for v in _candidates(solver, knob):
+        for v in _candidates(solver, knob, idx):
             # the knob's pipelined variants: col_pipe 0/1 for the column
             # passes, row_pipe 0/1 for the FP32 apply row pass
             if knob == "col_tile":

@@ -397,8 +397,9 @@ void fill_geo(hc_ctx* c, hc::Geo<T>& g, const cx<T>* twx, const cx<T>* twy, cons
   g.lnx = ilog2(c->nx);
   g.lny = ilog2(c->ny);
   g.lH = ilog2(c->H);
-  // column CTA: tc packed columns x ny/8 threads, at most 512 threads
-  int tc = 512 >> (g.lny - 3);
+  // column CTA: tc packed columns x ny/8 threads, at most 1024 threads (FP32)
+  // or 512 (FP64, double-float)
+  int tc = hc::col_cta_max<T, true>() >> (g.lny - 3);
   if (tc < 1) tc = 1;
   if (tc > 32) tc = 32;
   if (tc > c->H) tc = c->H;
@@ -2831,6 +2832,7 @@ hc::Geo<T> class_geo(const hc::Geo<T>& own, const hc::Geo<T>& rep) {
 hc::BInst member_record(const hc_ctx* c, const hc_ctx* rep) {
   hc::BInst b{};
   b.gf = class_geo(c->gf, rep->gf);
+  b.gfn = hc::col_narrow(b.gf);
   b.gd = class_geo(c->gd, rep->gd);
   b.gq = class_geo(c->gq, rep->gq);
   b.st = c->st;
@@ -3013,6 +3015,7 @@ int hc_batch_create(hc_batch** out, hc_ctx* const* ctxs, int count, void* stream
                      cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(HC_ECUDA);
       bc.sh.gf = recs[0].gf;
+      bc.sh.gfn = recs[0].gfn;
       bc.sh.gd = recs[0].gd;
       bc.sh.gq = recs[0].gq;
       bc.sh.nb = (int)bc.members.size();
@@ -3154,7 +3157,9 @@ int hc_set_tuning(hc_ctx* c, const hc_tuning* t) {
   for (int p = 0; p < 2; ++p) {
     const int tc = t->col_tile[p], rpc = t->row_rows[p];
     const size_t esz = p == 0 ? sizeof(cx<float>) : sizeof(cx<double>);
-    if (tc < 1 || (tc & (tc - 1)) || tc > 32 || tc > c->H || (tc << (lny - 3)) > 512) return HC_EINVAL;
+    const int max_threads = p == 0 ? hc::col_cta_max<float, true>() : hc::col_cta_max<double, true>();
+    if (tc < 1 || (tc & (tc - 1)) || tc > 32 || tc > c->H || (tc << (lny - 3)) > max_threads)
+      return HC_EINVAL;
     if (rpc < 1 || (rpc & (rpc - 1)) || rpc > c->ny || (rpc << (lnx - 3)) > 512) return HC_EINVAL;
     const size_t col_sm = 2 * (size_t)(c->ny + (c->ny >> 3)) * tc * esz + 1024;
     // the apply row pass also stages m and r (FP32 unless plain FP64)

@@ -16,8 +16,11 @@ namespace hc {
 
 namespace {
 
+// The FP32 gradient and divergence passes take the class tile (CTAs of up to
+// 1024 threads), the heat pass at most 512 threads (gfn, col_narrow).
+
 // ------------------------------------------------------------------ FP32 first residual
-__global__ void __launch_bounds__(512) kb_first_grad(const BInst* bi) {
+__global__ void __launch_bounds__(1024, 1) kb_first_grad(const BInst* bi) {
   const BInst& c = bi[blockIdx.y];
   col_grad_body<float, double, CG_PLAIN>(c.gf, c.p64, nullptr, nullptr, nullptr, c.G32,
                                          c.G32 + c.ns, c.st, 0);
@@ -28,14 +31,14 @@ __global__ void __launch_bounds__(512) kb_first_apply(const BInst* bi) {
   row_apply_body<float, float, false, NV>(c.gf, c.G32, c.G32 + c.ns, c.mx, c.my, c.rf, c.G32,
                                           c.G32 + c.ns, nullptr);
 }
-__global__ void __launch_bounds__(512) kb_first_div(const BInst* bi) {
+__global__ void __launch_bounds__(1024, 1) kb_first_div(const BInst* bi) {
   const BInst& c = bi[blockIdx.y];
   col_div_body<float, CD_RESID_FIRST>(c.gf, c.G32, c.G32 + c.ns, nullptr, c.b32, nullptr, c.r32,
                                       c.x32, c.st);
 }
 
 // ------------------------------------------------------------------ inner FP32 CG iteration
-__global__ void __launch_bounds__(512) kb_cg_grad(const BInst* bi) {
+__global__ void __launch_bounds__(1024, 1) kb_cg_grad(const BInst* bi) {
   const BInst& c = bi[blockIdx.y];
   col_grad_body<float, float, CG_DUPDATE>(c.gf, (cx<float>*)nullptr, c.r32, c.d32, nullptr, c.G32,
                                           c.G32 + c.ns, c.st, 1);
@@ -46,7 +49,7 @@ __global__ void __launch_bounds__(512) kb_cg_apply(const BInst* bi) {
   row_apply_body<float, float, true, NV>(c.gf, c.G32, c.G32 + c.ns, c.mx, c.my, c.rf, c.G32,
                                          c.G32 + c.ns, c.st);
 }
-__global__ void __launch_bounds__(512) kb_cg_div(const BInst* bi) {
+__global__ void __launch_bounds__(1024, 1) kb_cg_div(const BInst* bi) {
   const BInst& c = bi[blockIdx.y];
   col_div_body<float, CD_CG>(c.gf, c.G32, c.G32 + c.ns, c.d32, nullptr, c.q32, nullptr, nullptr,
                              c.st);
@@ -103,7 +106,7 @@ __global__ void __launch_bounds__(512) kb_res_div(const BInst* bi) {
 }
 
 // ------------------------------------------------------------------ split step
-__global__ void __launch_bounds__(512) kb_split_grad(const BInst* bi) {
+__global__ void __launch_bounds__(1024, 1) kb_split_grad(const BInst* bi) {
   const BInst& c = bi[blockIdx.y];
   col_grad_body<float, double, CG_PLAIN>(c.gf, c.p64, nullptr, nullptr, nullptr, c.G32,
                                          c.G32 + c.ns, c.st, 0);
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(512) kb_split_row(const BInst* bi) {
 }
 __global__ void __launch_bounds__(512) kb_split_heat(const BInst* bi) {
   const BInst& c = bi[blockIdx.y];
-  col_heat_body<float>(c.gf, c.G32, c.G32 + c.ns, c.st);
+  col_heat_body<float>(c.gfn, c.G32, c.G32 + c.ns, c.st);
 }
 __global__ void __launch_bounds__(512) kb_split_c2r(const BInst* bi) {
   const BInst& c = bi[blockIdx.y];
@@ -215,9 +218,10 @@ void batch_refine_resid(const BInst* bi, const BShape& sh, cudaStream_t s) {
 
 void batch_split(const BInst* bi, const BShape& sh, cudaStream_t s) {
   const Geo<float>& g = sh.gf;
+  const Geo<float>& gn = sh.gfn;
   kb_split_grad<<<col_grid(g, sh.nb), col_threads(g), col_smem(g, 2), s>>>(bi);
   kb_split_row<<<row_grid(g, sh.nb), row_threads(g), row_smem(g), s>>>(bi);
-  kb_split_heat<<<col_grid(g, sh.nb), col_threads(g), col_smem(g, 2), s>>>(bi);
+  kb_split_heat<<<col_grid(gn, sh.nb), col_threads(gn), col_smem(gn, 2), s>>>(bi);
   kb_split_c2r<<<row_grid(g, sh.nb), row_threads(g), row_smem(g), s>>>(bi);
 }
 

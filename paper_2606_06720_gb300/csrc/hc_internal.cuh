@@ -281,6 +281,7 @@ struct GenGeo {
 // blockIdx.y, with the member's own geometry tables, solve state and buffers.
 struct BInst {
   Geo<float> gf;
+  Geo<float> gfn;         // gf limited to 512-thread column CTAs (col_narrow)
   Geo<double> gd;
   Geo<df64> gq;
   SolveState* st;
@@ -306,10 +307,33 @@ struct BInst {
 // and launch shapes): the host copies of one member's three geometries.
 struct BShape {
   Geo<float> gf;
+  Geo<float> gfn;         // gf limited to 512-thread column CTAs (col_narrow)
   Geo<double> gd;
   Geo<df64> gq;
   int nb;                 // members
 };
+
+// Threads of a column-pass CTA at most.  The FP32 gradient and divergence
+// passes (WIDE) take up to 1024 at 64 registers a thread: a tile of four
+// packed columns of 2048 values reads and writes 32 contiguous bytes per row,
+// whole DRAM sectors.  The other column passes (heat, transforms, adjoint,
+// the persistent ones) and every FP64 and double-float pass take up to 512,
+// with up to 128 registers.
+template <typename T, bool WIDE>
+constexpr int col_cta_max() {
+  return sizeof(T) == 4 && WIDE ? 1024 : 512;
+}
+// The geometry a column pass of at most 512 threads runs with: the tile
+// halved while tc ny/8 is above 512 (a tile is any power of two of columns;
+// the passes share no state through it).
+template <typename T>
+inline Geo<T> col_narrow(Geo<T> g) {
+  while (g.tc > 1 && (g.tc << (g.lny - 3)) > 512) {
+    g.tc >>= 1;
+    g.ltc -= 1;
+  }
+  return g;
+}
 
 // Column-kernel modes.
 enum ColGradMode { CG_PLAIN = 0, CG_DUPDATE = 1, CG_ADDDELTA = 2 };

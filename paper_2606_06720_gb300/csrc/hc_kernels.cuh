@@ -1404,7 +1404,7 @@ __device__ __forceinline__ void col_grad_body(Geo<T> g, cx<Tin>* in, const cx<T>
   }
 }
 template <typename T, typename Tin, int MODE>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_col_grad(Geo<T> g, cx<Tin>* in, const cx<T>* __restrict__ rvec,
+__global__ void __launch_bounds__(col_cta_max<T, true>(), 1) k_col_grad(Geo<T> g, cx<Tin>* in, const cx<T>* __restrict__ rvec,
                                                   cx<T>* dio, const cx<float>* __restrict__ delta,
                                                   cx<T>* __restrict__ Gx, cx<T>* __restrict__ Gy,
                                                   SolveState* st, int check_done) {
@@ -1526,7 +1526,7 @@ __device__ __forceinline__ void col_div_body(Geo<T> g, const cx<T>* __restrict__
   }
 }
 template <typename T, int MODE>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_col_div(Geo<T> g, const cx<T>* __restrict__ Qx,
+__global__ void __launch_bounds__(col_cta_max<T, true>(), 1) k_col_div(Geo<T> g, const cx<T>* __restrict__ Qx,
                                                  const cx<T>* __restrict__ Qy,
                                                  const cx<T>* __restrict__ d,
                                                  const cx<T>* __restrict__ bvec,
@@ -2449,8 +2449,9 @@ void row_split(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const T* mx, c
                                                                      cf, st);
 }
 template <typename T>
-void col_fwd(const Geo<T>& g, const cx<T>* in0, const cx<T>* in1, cx<T>* out0, cx<T>* out1, int nv,
+void col_fwd(const Geo<T>& g0, const cx<T>* in0, const cx<T>* in1, cx<T>* out0, cx<T>* out1, int nv,
              int project, SolveState* st, cudaStream_t s) {
+  const Geo<T> g = col_narrow(g0);
   if (nv == 1)
     k_col_fwd<T, 1><<<g.H >> g.ltc, col_threads(g), col_smem(g, 1), s>>>(g, in0, in1, out0, out1,
                                                                           project, st);
@@ -2459,7 +2460,8 @@ void col_fwd(const Geo<T>& g, const cx<T>* in0, const cx<T>* in1, cx<T>* out0, c
                                                                           project, st);
 }
 template <typename T>
-void col_inv(const Geo<T>& g, const cx<T>* in, cx<T>* out, T scale, cudaStream_t s) {
+void col_inv(const Geo<T>& g0, const cx<T>* in, cx<T>* out, T scale, cudaStream_t s) {
+  const Geo<T> g = col_narrow(g0);
   k_col_inv<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 1), s>>>(g, in, out, scale);
 }
 template <typename T>
@@ -2468,9 +2470,11 @@ static inline size_t pipe_smem(const Geo<T>& g) {
 }
 
 template <typename T, typename Tin>
-void col_grad(const Geo<T>& g, int mode, cx<Tin>* in, const cx<T>* rvec, cx<T>* dio,
+void col_grad(const Geo<T>& g0, int mode, cx<Tin>* in, const cx<T>* rvec, cx<T>* dio,
               const cx<float>* delta, cx<T>* Gx, cx<T>* Gy, SolveState* st, int check_done,
               cudaStream_t s) {
+  // the whole tile; the persistent passes at most 512 threads
+  const Geo<T> g = g0.pipe ? col_narrow(g0) : g0;
   const int nb = g.H >> g.ltc, nt = col_threads(g);
   const size_t sm = col_smem(g, 2);
   if constexpr (std::is_same<T, Tin>::value) {
@@ -2497,9 +2501,11 @@ void col_grad(const Geo<T>& g, int mode, cx<Tin>* in, const cx<T>* rvec, cx<T>* 
                                                        check_done);
 }
 template <typename T>
-void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const cx<T>* d,
+void col_div(const Geo<T>& g0, int mode, const cx<T>* Qx, const cx<T>* Qy, const cx<T>* d,
              const cx<T>* b, cx<T>* out, cx<float>* r32, cx<float>* delta32, SolveState* st,
              cudaStream_t s) {
+  // the whole tile; the persistent passes at most 512 threads
+  const Geo<T> g = g0.pipe ? col_narrow(g0) : g0;
   const int nb = g.H >> g.ltc, nt = col_threads(g);
   const size_t sm = col_smem(g, 2);
   if (g.pipe) {
@@ -2546,7 +2552,8 @@ void col_div(const Geo<T>& g, int mode, const cx<T>* Qx, const cx<T>* Qy, const 
   }
 }
 template <typename T>
-void col_heat(const Geo<T>& g, cx<T>* Mx, cx<T>* My, SolveState* st, cudaStream_t s) {
+void col_heat(const Geo<T>& g0, cx<T>* Mx, cx<T>* My, SolveState* st, cudaStream_t s) {
+  const Geo<T> g = col_narrow(g0);
   if (g.pipe) {
     kp_col_heat<T><<<g.pgrid, col_threads(g), pipe_smem(g), s>>>(g, Mx, My, st);
     return;
@@ -2554,8 +2561,9 @@ void col_heat(const Geo<T>& g, cx<T>* Mx, cx<T>* My, SolveState* st, cudaStream_
   k_col_heat<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 2), s>>>(g, Mx, My, st);
 }
 template <typename T>
-void col_gradnorm(const Geo<T>& g, const cx<T>* Mx, const cx<T>* My, SolveState* st, int into_next,
+void col_gradnorm(const Geo<T>& g0, const cx<T>* Mx, const cx<T>* My, SolveState* st, int into_next,
                   cudaStream_t s) {
+  const Geo<T> g = col_narrow(g0);
   k_col_gradnorm<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 2), s>>>(g, Mx, My, st, into_next);
 }
 template <typename T>
@@ -2590,8 +2598,9 @@ void row_adj_press(const Geo<T>& g, const cx<T>* GM0, const cx<T>* GM1, const cx
       g, GM0, GM1, GP0, GP1, mx, my, lmx, lmy, lx, ly, dr);
 }
 template <typename T>
-void col_lap_dot(const Geo<T>& g, const cx<T>* A, const cx<T>* B, double dt, AdjState* as,
+void col_lap_dot(const Geo<T>& g0, const cx<T>* A, const cx<T>* B, double dt, AdjState* as,
                  cudaStream_t s) {
+  const Geo<T> g = col_narrow(g0);
   k_col_lap_dot<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 2), s>>>(g, A, B, dt, as);
 }
 template <typename T>

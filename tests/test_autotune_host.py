@@ -70,6 +70,7 @@ def test_candidates_respect_the_thread_limits(tuner):
     assert tuner._candidates(s, "row_rows") == [1, 2, 4, 8, 16]       # v <= ny, v*nx/8 <= 512
     s = Stand(n=(2048, 2048))
     assert tuner._candidates(s, "col_tile") == [1, 2]
+    assert tuner._candidates(s, "col_tile", 0) == [1, 2, 4]            # FP32: v*ny/8 <= 1024
     assert tuner._candidates(s, "row_rows") == [1, 2]
     s = Stand(n=(4096, 8))
     assert tuner._candidates(s, "col_tile") == [1, 2, 4, 8, 16, 32]

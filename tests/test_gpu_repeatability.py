@@ -26,7 +26,10 @@ def run(hc, w, precision, nsteps, tuning=None):
                    precond="kbar") as s:
         if tuning is not None:
             t = s.get_tuning()
-            s.set_tuning(t["col_tile"], t["row_rows"], *tuning)
+            col = list(t["col_tile"])
+            if tuning[0][0]:  # the persistent passes double-buffer tiles of at most 512 threads
+                col[0] = min(col[0], 512 // (w.n[1] // 8))
+            s.set_tuning(col, t["row_rows"], *tuning)
         s.set_r(w.r)
         s.set_source(w.S)
         s.set_m(w.m0)
