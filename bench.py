@@ -106,10 +106,11 @@ BYTES_PER_POINT_3D = {
 # DRAM bytes (read + write) per launch measured by ncu for the 2048^2 refined
 # workload with the current kernels (from the committed ncu summaries).
 # Set an entry to None when its kernel changes.
-NCU_TRAFFIC_2048 = {"res_grad": 104.5e6, "res_apply": 128.2e6, "res_div": 133.2e6,
-                    "cg_grad": 36.2e6, "cg_apply": 84.8e6, "cg_div": 33.6e6, "cg_update": 67.3e6,
-                    "mid_grad": 100.9e6, "mid_apply": 130.8e6, "mid_div": 114.2e6,
-                    "split_row": 67.2e6, "split_c2r": 33.7e6}
+NCU_TRAFFIC_2048 = {"res_grad": 104.6e6, "res_apply": 132.7e6, "res_div": 132.7e6,
+                    "cg_grad": 19.4e6, "cg_apply": 86.8e6, "cg_div": 34.1e6, "cg_update": 67.8e6,
+                    "split_grad": 37.2e6, "split_heat": 33.7e6, "split_c2r": 34.1e6,
+                    "first_grad": 37.2e6, "first_div": 52.4e6,
+                    "mid_grad": None, "mid_apply": None, "mid_div": None, "split_row": None}
 
 
 def shard(items: int, rank: int, world: int) -> list:
