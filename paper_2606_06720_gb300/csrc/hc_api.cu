@@ -729,6 +729,9 @@ hc::SplitCoef split_coef(const hc_params& p) {
   s.f_two1mg_dt = (float)s.two1mg_dt;
   s.f_pow_a = (float)s.pow_a;
   s.f_pow_b = (float)s.pow_b;
+  auto kind = [](double e) { return e == 1.0 ? 1 : e == 2.0 ? 2 : e == 0.5 ? 3 : 0; };
+  s.pow_a_kind = kind(s.pow_a);
+  s.pow_b_kind = s.gamma_is_one ? 0 : kind(s.pow_b);
   return s;
 }
 

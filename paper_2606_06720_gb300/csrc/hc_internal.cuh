@@ -257,6 +257,9 @@ struct SplitCoef {
   int gamma_is_one;
   // the same rounded to FP32 on the host, for the FP32 kernels (cfv)
   float f_c2dt, f_gamma, f_dt, f_exp_mdt, f_two1mg_dt, f_pow_a, f_pow_b;
+  // pow_a, pow_b when they are 1, 2 or 1/2 (1, 2, 3; else 0): the power is
+  // then x, x x or sqrt x (pow_k), e.g. both are 1 at gamma = 1/2
+  int pow_a_kind, pow_b_kind;
 };
 
 // 2D grids whose sizes are not powers of two (hc_generic.cu): N = 2^a 3^b 5^c

@@ -557,6 +557,18 @@ __device__ __forceinline__ T st_beta(const SolveState* st) {
   if constexpr (std::is_same<T, float>::value) return st->beta_f;
   else return (T)st->beta;
 }
+// x^y for a relaxation exponent y of kind 1, 2, 3 (y = 1, 2, 1/2: x, x x,
+// sqrt x; x >= 0 here) or 0 (the general power).  The kind is uniform.
+template <typename T>
+__device__ __forceinline__ T pow_k(T x, T y, int kind) {
+  switch (kind) {
+    case 1: return x;
+    case 2: return x * x;
+    case 3: return hc_sqrt(x);
+    default: return hc_pow(x, y);
+  }
+}
+
 // A split-step coefficient in the kernel's type: FP32 kernels take the copy
 // rounded on the host.
 template <typename T>
@@ -1032,8 +1044,9 @@ __device__ __forceinline__ void split_point(T& ax, T& ay, T gx, T gy, T c2dt, co
     const T n2 = ax * ax + ay * ay;
     if (n2 > (T)0) {
       const T nm = hc_sqrt(n2);
-      const T bb = hc_pow(nm, cfv<T>(cf.pow_a, cf.f_pow_a)) - cfv<T>(cf.two1mg_dt, cf.f_two1mg_dt);
-      const T sc = bb >= (T)0 ? hc_pow(bb, cfv<T>(cf.pow_b, cf.f_pow_b)) / nm : (T)0;
+      const T bb = pow_k(nm, cfv<T>(cf.pow_a, cf.f_pow_a), cf.pow_a_kind) -
+                   cfv<T>(cf.two1mg_dt, cf.f_two1mg_dt);
+      const T sc = bb >= (T)0 ? pow_k(bb, cfv<T>(cf.pow_b, cf.f_pow_b), cf.pow_b_kind) / nm : (T)0;
       ax *= sc;
       ay *= sc;
     }
