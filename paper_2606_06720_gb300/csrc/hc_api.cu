@@ -397,9 +397,11 @@ void fill_geo(hc_ctx* c, hc::Geo<T>& g, const cx<T>* twx, const cx<T>* twy, cons
   g.lnx = ilog2(c->nx);
   g.lny = ilog2(c->ny);
   g.lH = ilog2(c->H);
-  // column CTA: tc packed columns x ny/8 threads, at most 1024 threads (FP32)
-  // or 512 (FP64, double-float)
-  int tc = hc::col_cta_max<T, true>() >> (g.lny - 3);
+  // column CTA: tc packed columns x ny/8 threads: 1024 threads (FP32), 256
+  // (FP64, double-float: at 128 registers two CTAs per SM, the same warps as
+  // one of 512 in finer pieces; measured at 2048^2, the FP64 gradient and
+  // divergence passes take 674 us per step at 256 threads, 801 at 512)
+  int tc = (sizeof(T) == 4 ? hc::col_cta_max<T, true>() : 256) >> (g.lny - 3);
   if (tc < 1) tc = 1;
   if (tc > 32) tc = 32;
   if (tc > c->H) tc = c->H;
