@@ -503,6 +503,7 @@ def run_3d(P, W, args, dev, barrier, job_rate, hbm_peak, hbm_src, fp64_peak) -> 
     fp32 = [k for k in kernels if kernels[k]["bound"] == "hbm"]
     dom = max(fp32, key=lambda k: kernels[k]["ms_per_step"])
     dk = kernels[dom]
+    plain = None if args.no_fp64 else run_3d_fp64_plain(P, W, args, dev, barrier, job_rate, K3, value)
     return {"value": value, "unit": UNIT, "ms_per_step": ms / K3,
             "steps": K3, "grid": list(w.n),
             "workload": "source_sink_3d_%d: r=0.1, S=+G(0.3,0.5,0.5)-G(0.7,0.5,0.5) sigma 0.05 "
@@ -515,7 +516,71 @@ def run_3d(P, W, args, dev, barrier, job_rate, hbm_peak, hbm_src, fp64_peak) -> 
                               "peak": hbm_peak, "unit": "GB/s", "frac": dk["frac"],
                               "peak_source": hbm_src,
                               "alg_bytes": BYTES_PER_POINT_3D[dom] * npts},
+            "fp64_plain": plain,
             "kernels": kernels}
+
+
+# Plain-FP64 tolerances tried for the 3D comparison, loosest first.
+FP64_RTOL_CANDIDATES_3D = (1e-3, 1e-4, 1e-5, 1e-6)
+
+
+def run_3d_fp64_plain(P, W, args, dev, barrier, job_rate, K3: int, refined_value: float) -> dict:
+    """The 3D comparison of the refined path with plain FP64 at equal accuracy.
+    From m0, `acc3d_steps` steps of the 3D workload on each leg: a plain FP64
+    run at cg_rtol 1e-13 is the reference, and the relative L2 error of m is
+    measured for the refined path (cg_rtol 1e-8) and for plain FP64 at each
+    candidate tolerance.  The plain leg is then timed, like the refined one,
+    over K3 steps after 3 warm-up steps at the loosest tolerance whose error
+    is within ACC_BOUND."""
+    import numpy as np
+    import torch
+    steps = args.acc3d_steps
+    w = W.source_sink_3d(args.n3d)
+
+    def make(precision, rtol):
+        s = P.Solver(w.n, w.L, c=w.c, D=w.D, gamma=w.gamma, dt=w.dt, precision=precision,
+                     cg_rtol=rtol, cg_maxit=5000, precond=PRECOND,
+                     use_graph=not args.host_loop, device=str(dev))
+        s.set_r(w.r)
+        s.set_source(w.S)
+        s.set_m(w.m0)
+        return s
+
+    def run(precision, rtol):
+        with make(precision, rtol) as s:
+            st = s.step(steps)
+            return s.get_m(), st
+
+    m_ref, st_ref = run("fp64", 1e-13)
+    nref = float(np.linalg.norm(m_ref))
+    legs = []
+    for precision, rtol in [("fp32_refined", CG_RTOL_REFINED)] + \
+            [("fp64", r) for r in FP64_RTOL_CANDIDATES_3D]:
+        m, st = run(precision, rtol)
+        legs.append({"precision": precision, "cg_rtol": rtol,
+                     "m_rel_l2": float(np.linalg.norm(m - m_ref)) / nref,
+                     "mean_cg_iters": st.total_cg_iters / steps})
+    ok = [leg["cg_rtol"] for leg in legs[1:] if leg["m_rel_l2"] <= ACC_BOUND]
+    rtol = max(ok) if ok else min(FP64_RTOL_CANDIDATES_3D)
+    with make("fp64", rtol) as s:
+        s.step(3)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        st = s.step(K3)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+    ms, v64 = job_rate(e0.elapsed_time(e1), w.npts * K3)
+    return {"value": v64, "unit": UNIT, "ms_per_step": ms / K3, "steps": K3, "cg_rtol": rtol,
+            "cg_iters_per_step": st.total_cg_iters / K3,
+            "speedup_of_refined": refined_value / v64,
+            "equal_accuracy": {"steps": steps, "bound": ACC_BOUND,
+                               "reference": f"plain FP64 on the GPU, cg_rtol 1e-13, {steps} steps "
+                                            f"from m0 ({st_ref.total_cg_iters / steps:.1f} CG "
+                                            f"iterations per step)",
+                               "legs": legs}}
 
 
 # ----------------------------------------------------------------- equal accuracy
@@ -1019,6 +1084,8 @@ def main() -> None:
     ap.add_argument("--no-diag", action="store_true",
                     help="skip the diagnostics / stopping-rule leg")
     ap.add_argument("--n3d", type=int, default=256, help="3D leg: grid points per axis")
+    ap.add_argument("--acc3d-steps", type=int, default=5,
+                    help="3D leg: steps from m0 of the equal-accuracy comparison with plain FP64")
     ap.add_argument("--no-conv", action="store_true",
                     help="skip the paper's grid-convergence leg (N = 50 .. 800, mixed radix)")
     ap.add_argument("--conv-steps", type=int, default=100,
