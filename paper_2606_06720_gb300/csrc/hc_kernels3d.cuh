@@ -420,10 +420,7 @@ __device__ __forceinline__ void act_relax3(T& ax, T& ay, T& az, T gx, T gy, T gz
   } else {
     const T n2 = ax * ax + ay * ay + az * az;
     if (n2 > (T)0) {
-      const T nm = hc_sqrt(n2);
-      const T bb = pow_k(nm, cfv<T>(cf.pow_a, cf.f_pow_a), cf.pow_a_kind) -
-                   cfv<T>(cf.two1mg_dt, cf.f_two1mg_dt);
-      const T sc = bb >= (T)0 ? pow_k(bb, cfv<T>(cf.pow_b, cf.f_pow_b), cf.pow_b_kind) / nm : (T)0;
+      const T sc = relax_factor(hc_sqrt(n2), cf);
       ax *= sc;
       ay *= sc;
       az *= sc;
