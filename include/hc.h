@@ -227,6 +227,20 @@ int hc_run(hc_ctx* ctx, int max_steps, double eps, int stop_on_energy, int* step
 int hc_get_p(hc_ctx* ctx, double* out, size_t count);
 int hc_get_m(hc_ctx* ctx, double* out, size_t count);
 
+/* The whole state of Algorithm 1 in one call: m (m_count = dim*npts) and p
+ * (p_count = npts), host FP64 in the layouts above, with the effect of
+ * hc_set_m followed by hc_set_p (hc_set_state) or of hc_get_m and hc_get_p
+ * (hc_get_state), bit for bit; both wait for their copies.  A caller that
+ * hands the state over every step moves m and p (3 npts doubles each way)
+ * across the host link per step, and p needs an FP64 2D transform each way.
+ * In the 2D FP32-refined mode the copy of m runs on a second stream of the
+ * context while p is transformed, and p is staged in the FP64 scratch of the
+ * step's certification (free between hc_step calls); the other modes call the
+ * single-field entry points in turn.  Page-locked host buffers give the full
+ * link bandwidth.  Errors: HC_EINVAL (NULL, wrong counts), HC_ECUDA. */
+int hc_set_state(hc_ctx* ctx, const double* m, size_t m_count, const double* p, size_t p_count);
+int hc_get_state(hc_ctx* ctx, double* m_out, size_t m_count, double* p_out, size_t p_count);
+
 /* --- Component entry points (each runs one part of the step on the GPU) --- */
 
 /* Spectral gradient of the current p (Section 2.4 and Algorithm 1 "compute
@@ -324,10 +338,11 @@ int hc_launch_count(const hc_ctx* ctx, long long* count);
 
 /* Measured FP64 FMA throughput of the current device in TFLOP/s (an FMA counts
  * two flops): the ALU roof against which the FP64 residual kernels are
- * reported.  One warm-up and `reps` timed launches of a kernel of independent
- * FMA chains filling every SM, between CUDA events on `stream` (NULL: legacy
- * default stream); synchronises that stream.  No context needed; allocates
- * nothing.  Errors: HC_EINVAL (reps < 1, NULL tflops), HC_ECUDA. */
+ * reported.  Two warm-up launches, then `reps` launches of a kernel of
+ * independent FMA chains filling every SM, each timed between CUDA events on
+ * `stream` (NULL: legacy default stream); the fastest gives the figure.
+ * Synchronises that stream.  No context needed; allocates nothing.
+ * Errors: HC_EINVAL (reps < 1, NULL tflops), HC_ECUDA. */
 int hc_fp64_fma_peak(int reps, void* stream, double* tflops);
 
 /* --- Adjoint (gradients of a loss on m(T)) --- */

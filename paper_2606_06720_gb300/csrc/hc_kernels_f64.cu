@@ -161,19 +161,27 @@ int fma_peak(int reps, cudaStream_t s, double* tflops) {
     cudaEventDestroy(e0);
     return HC_ECUDA;
   }
-  k_fma_peak<<<blocks, threads, 0, s>>>(iters, 0.9999999, 1e-7);  // warm-up
-  cudaEventRecord(e0, s);
-  for (int r = 0; r < reps; ++r) k_fma_peak<<<blocks, threads, 0, s>>>(iters, 0.9999999, 1e-7);
-  cudaEventRecord(e1, s);
-  float ms = 0.f;
-  cudaError_t e = cudaEventSynchronize(e1);
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  // the fastest of `reps` timed launches after two warm-up launches: a peak,
+  // so a launch slowed while the clocks ramp up does not lower it
+  k_fma_peak<<<blocks, threads, 0, s>>>(iters, 0.9999999, 1e-7);
+  k_fma_peak<<<blocks, threads, 0, s>>>(iters, 0.9999999, 1e-7);
+  float best = 0.f;
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    cudaEventRecord(e0, s);
+    k_fma_peak<<<blocks, threads, 0, s>>>(iters, 0.9999999, 1e-7);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && ms > 0.f && (best == 0.f || ms < best)) best = ms;
+  }
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (e != cudaSuccess || !(ms > 0.f)) return HC_ECUDA;
-  const double flops = 2.0 * 8.0 * iters * (double)blocks * threads * reps;
-  *tflops = flops / (ms * 1e-3) / 1e12;
+  if (e != cudaSuccess || !(best > 0.f)) return HC_ECUDA;
+  const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+  *tflops = flops / (best * 1e-3) / 1e12;
   return HC_OK;
 }
 
