@@ -671,7 +671,7 @@ def run_gb300(args) -> None:
         return ms, per_s / 1e6
 
     # the FP64 residual kernels' roof, measured here (independent FMA chains on every SM)
-    fp64_peak = P.fp64_fma_peak(reps=5)
+    fp64_peak = P.fp64_fma_peak(reps=10)
 
     w = W.source_sink_2d(N_GRID)
     K, Wm = args.steps, args.warmup
@@ -742,7 +742,8 @@ def run_gb300(args) -> None:
                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": dk["frac"],
                     "traffic": traffic,
                     "peak_source": "measured: FP64 FMA throughput of this GPU in this run "
-                                   "(hc_fp64_fma_peak; FMA = 2 flops); nominal 1.25",
+                                   "(hc_fp64_fma_peak: fastest of 10 launches; FMA = 2 flops); "
+                                   "nominal 1.25",
                     "alg_bytes": BYTES_PER_POINT["fp32_refined"][dom] * npts}
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["alg_GBs"], "peak": hbm_peak,
@@ -758,24 +759,21 @@ def run_gb300(args) -> None:
         Ke = max(5, K // 10)
         hm = torch.empty(2 * npts, dtype=torch.float64, pin_memory=True)
         hp = torch.empty(npts, dtype=torch.float64, pin_memory=True)
-        s.get_m(out=hm)
-        s.get_p(out=hp)
+        s.get_state(hm, hp)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(Ke):
-            s.set_m(hm)
-            s.set_p(hp)
+            s.set_state(hm, hp)
             s.step(1)
-            s.get_m(out=hm)
-            s.get_p(out=hp)
+            s.get_state(hm, hp)
         torch.cuda.synchronize()
         _, ve = job_rate((time.perf_counter() - t0) * 1e3, npts * Ke)
         barrier()
         e2e = {"value": ve, "unit": UNIT,
                "h2d_bytes_per_step": 3 * npts * 8, "d2h_bytes_per_step": 3 * npts * 8,
-               "steps": Ke, "path": "hc_set_m + hc_set_p (pinned host FP64) -> hc_step(1) -> "
-                                    "hc_get_m + hc_get_p (pinned host FP64)"}
+               "steps": Ke, "path": "hc_set_state (m, p from pinned host FP64) -> hc_step(1) -> "
+                                    "hc_get_state (m, p to pinned host FP64)"}
 
     # ---- the same refined path with the refinement in double-float (FP32 pipes)
     dfv = None

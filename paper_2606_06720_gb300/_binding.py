@@ -94,6 +94,8 @@ def _load() -> C.CDLL:
                    C.c_int),
         "hc_get_p": ([P, dp, C.c_size_t], C.c_int),
         "hc_get_m": ([P, dp, C.c_size_t], C.c_int),
+        "hc_set_state": ([P, dp, C.c_size_t, dp, C.c_size_t], C.c_int),
+        "hc_get_state": ([P, dp, C.c_size_t, dp, C.c_size_t], C.c_int),
         "hc_gradient": ([P, dp, C.c_size_t], C.c_int),
         "hc_apply_operator": ([P, dp, dp, C.c_size_t], C.c_int),
         "hc_split_step": ([P], C.c_int),
@@ -138,6 +140,8 @@ hc_step = lib.hc_step
 hc_run = lib.hc_run
 hc_get_p = lib.hc_get_p
 hc_get_m = lib.hc_get_m
+hc_set_state = lib.hc_set_state
+hc_get_state = lib.hc_get_state
 hc_gradient = lib.hc_gradient
 hc_apply_operator = lib.hc_apply_operator
 hc_split_step = lib.hc_split_step
@@ -337,6 +341,21 @@ class Solver:
         p, keep = _host_f64(out, self.dim * self.npts, writable=True)
         _check(hc_get_m(self.ctx, p, self.dim * self.npts), "hc_get_m")
         return out
+
+    def set_state(self, m, p_):
+        """m and p in one call (hc_set_state)."""
+        pm, keep_m = _host_f64(m, self.dim * self.npts)
+        pp, keep_p = _host_f64(p_, self.npts)
+        _check(hc_set_state(self.ctx, pm, self.dim * self.npts, pp, self.npts), "hc_set_state")
+
+    def get_state(self, m_out=None, p_out=None):
+        """(m, p) in one call (hc_get_state); returns the two buffers."""
+        m_out = np.empty((self.dim,) + self.shape) if m_out is None else m_out
+        p_out = np.empty(self.shape) if p_out is None else p_out
+        pm, keep_m = _host_f64(m_out, self.dim * self.npts, writable=True)
+        pp, keep_p = _host_f64(p_out, self.npts, writable=True)
+        _check(hc_get_state(self.ctx, pm, self.dim * self.npts, pp, self.npts), "hc_get_state")
+        return m_out, p_out
 
     # the step -------------------------------------------------------------
     def step(self, nsteps: int = 1, allow=(HC_OK, HC_ENOCONV)) -> StepStats:

@@ -207,6 +207,8 @@ struct hc_ctx {
   Handles h_pipe;
   cudaGraphConditionalHandle h_pipe_gate;
   cudaStream_t cap_hi, cap_lo;          // capture streams of the lagged graph's two branches
+  cudaStream_t io_stream;               // hc_set_state / hc_get_state: m's copy beside p's transform
+  cudaEvent_t io_ev[2];
   int graph_nodes_fixed, graph_nodes_body, graph_nodes_outer;
 };
 
@@ -1929,6 +1931,9 @@ void hc_destroy(hc_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->cap_hi) cudaStreamDestroy(c->cap_hi);
   if (c->cap_lo) cudaStreamDestroy(c->cap_lo);
+  if (c->io_stream) cudaStreamDestroy(c->io_stream);
+  for (int k = 0; k < 2; ++k)
+    if (c->io_ev[k]) cudaEventDestroy(c->io_ev[k]);
   if (c->owns_ws && c->ws) cudaFree(c->ws);
   if (c->st_host) cudaFreeHost(c->st_host);
   delete c;
@@ -2174,6 +2179,78 @@ int hc_get_p(hc_ctx* c, double* out, size_t count) {
   }
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(out, c->stage, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+// The whole state in one call.  In the 2D FP32-refined mode the host link
+// carries m on a second stream (io_stream, copy engine) while the SMs run p's
+// FP64 transform; p is staged in the lagged certification's FP64 scratch
+// (G64c, 2 half spectra), which no step keeps between hc_step calls.  Other
+// modes run the single-field calls one after the other.
+static bool state_overlap(const hc_ctx* c) {
+  return c->dim == 2 && !c->gen && c->refined && !c->df && c->G64c != nullptr;
+}
+static int io_setup(hc_ctx* c) {
+  if (!c->io_stream) CU(cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking));
+  for (int k = 0; k < 2; ++k)
+    if (!c->io_ev[k]) CU(cudaEventCreateWithFlags(&c->io_ev[k], cudaEventDisableTiming));
+  return HC_OK;
+}
+
+int hc_set_state(hc_ctx* c, const double* m, size_t m_count, const double* p, size_t p_count) {
+  if (!c || !m || !p || m_count != (size_t)c->dim * c->n || p_count != c->n) return HC_EINVAL;
+  if (!state_overlap(c)) {
+    int rc = hc_set_m(c, m, m_count);
+    return rc ? rc : hc_set_p(c, p, p_count);
+  }
+  int rc = io_setup(c);
+  if (rc) return rc;
+  double* pst = reinterpret_cast<double*>(c->G64c);  // n doubles fit in 2 half spectra
+  // earlier work on the context's stream (it may still read m or the stage)
+  CU(cudaEventRecord(c->io_ev[0], c->stream));
+  CU(cudaStreamWaitEvent(c->io_stream, c->io_ev[0], 0));
+  // p first: its transform starts while m is still on the link
+  CU(cudaMemcpyAsync(pst, p, sizeof(double) * p_count, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->stage, m, sizeof(double) * m_count, cudaMemcpyHostToDevice, c->io_stream));
+  hc::convert<float, double>(c->stage, (float*)c->m[0], c->n, c->io_stream);
+  hc::convert<float, double>(c->stage + c->n, (float*)c->m[1], c->n, c->io_stream);
+  CU(cudaEventRecord(c->io_ev[1], c->io_stream));
+  hc::row_r2c<double>(c->gd, pst, nullptr, c->G64, nullptr, c->stream);
+  hc::col_fwd<double>(c->gd, c->G64, nullptr, c->p64, nullptr, 1, 1, nullptr, c->stream);
+  CU(cudaStreamWaitEvent(c->stream, c->io_ev[1], 0));
+  hc::msum<float>(c->gf, (const float*)c->m[0], (const float*)c->m[1], c->st, c->stream);
+  c->launches += 5;
+  rc = gm2_for_new_m(c);
+  if (rc) return rc;
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(c->stream));
+  return HC_OK;
+}
+
+int hc_get_state(hc_ctx* c, double* m_out, size_t m_count, double* p_out, size_t p_count) {
+  if (!c || !m_out || !p_out || m_count != (size_t)c->dim * c->n || p_count != c->n)
+    return HC_EINVAL;
+  if (!state_overlap(c)) {
+    int rc = hc_get_m(c, m_out, m_count);
+    return rc ? rc : hc_get_p(c, p_out, p_count);
+  }
+  int rc = io_setup(c);
+  if (rc) return rc;
+  double* pst = reinterpret_cast<double*>(c->G64c);
+  CU(cudaEventRecord(c->io_ev[0], c->stream));
+  CU(cudaStreamWaitEvent(c->io_stream, c->io_ev[0], 0));
+  hc::convert<double, float>((const float*)c->m[0], c->stage, c->n, c->io_stream);
+  hc::convert<double, float>((const float*)c->m[1], c->stage + c->n, c->n, c->io_stream);
+  CU(cudaMemcpyAsync(m_out, c->stage, sizeof(double) * m_count, cudaMemcpyDeviceToHost,
+                     c->io_stream));
+  CU(cudaEventRecord(c->io_ev[1], c->io_stream));
+  hc::col_inv<double>(c->gd, c->p64, c->G64, 1.0 / (double)c->n, c->stream);
+  hc::row_c2r<double>(c->gd, c->G64, nullptr, pst, nullptr, nullptr, 0, c->stream);
+  c->launches += 4;
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(p_out, pst, sizeof(double) * p_count, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamWaitEvent(c->stream, c->io_ev[1], 0));
   CU(cudaStreamSynchronize(c->stream));
   return HC_OK;
 }
