@@ -872,7 +872,7 @@ def run_gb300(args) -> None:
         batch = P.Batch(solvers, stream=stream)
         ncls, nbat = batch.classes()
         batch.step(3)
-        Ks = max(5, K // 15)
+        Ks = max(20, K // 15)  # a 20-step window at least of the 1000-step sweep
         barrier()
         torch.cuda.synchronize()
         c0 = torch.cuda.Event(enable_timing=True)

@@ -185,6 +185,51 @@ def test_refined_adjoint_matches_fp64_gpu_adjoint_256(hc):
         assert rel_l2(got[k], ref[k]) < 2e-3, k
 
 
+def test_adjoint_at_1024_against_differences_and_fp64(hc):
+    """The 1024^2 adjoint configuration (smooth r, source/sink S, c = 25,
+    D = 0.02, gamma = 0.75, dt = 5e-4) at its full grid, over 4 steps with a
+    checkpoint every 2: the plain FP64 GPU adjoint against central differences
+    of the FP64 forward (rtol 1e-13) for dL/dc^2, dL/dD^2 and the directional
+    derivative of L along a smooth perturbation of r, within 1e-4; and the
+    refined path's gradients against that FP64 adjoint within 2e-3 (the bound
+    of the 256^2 comparison above)."""
+    w = W.source_sink_2d(1024, steps=4, gamma=0.75)
+    nsteps = 4
+    lam = np.random.default_rng(11).standard_normal((2,) + w.shape)
+    dr = 0.01 * W.smooth_field(w.n, 3, 8, w.L)
+
+    def L_of(c2=None, D2=None, r=None):
+        c = w.c if c2 is None else np.sqrt(c2)
+        D = w.D if D2 is None else np.sqrt(D2)
+        with hc.Solver(w.n, w.L, c=c, D=D, gamma=w.gamma, dt=w.dt, precision="fp64",
+                       cg_rtol=1e-13, cg_maxit=5000) as s:
+            s.set_r(w.r if r is None else r)
+            s.set_source(w.S)
+            s.set_m(w.m0)
+            s.step(nsteps)
+            return float((lam * s.get_m()).sum())
+
+    with make(hc, w, "fp64", rtol=1e-13) as s:
+        ref = s.adjoint(nsteps, lam, every=2)
+    c2, D2 = w.c ** 2, w.D ** 2
+    h = 1e-4 * c2
+    fd = (L_of(c2=c2 + h) - L_of(c2=c2 - h)) / (2 * h)
+    assert abs(ref["dc2"] - fd) <= 1e-4 * abs(fd), (ref["dc2"], fd)
+    h = 1e-3 * D2
+    fd = (L_of(D2=D2 + h) - L_of(D2=D2 - h)) / (2 * h)
+    assert abs(ref["dD2"] - fd) <= 1e-4 * abs(fd), (ref["dD2"], fd)
+    h = 1e-2
+    fd = (L_of(r=w.r + h * dr) - L_of(r=w.r - h * dr)) / (2 * h)
+    dd = float((ref["dr"] * dr).sum())
+    assert abs(dd - fd) <= 1e-4 * abs(fd), (dd, fd)
+    with make(hc, w, "fp32_refined", rtol=1e-9) as s:
+        got = s.adjoint(nsteps, lam, every=2)
+    assert np.isclose(got["dc2"], ref["dc2"], rtol=2e-3), (got["dc2"], ref["dc2"])
+    assert np.isclose(got["dD2"], ref["dD2"], rtol=2e-3), (got["dD2"], ref["dD2"])
+    for k in ("dr", "dS", "dm0"):
+        assert rel_l2(got[k], ref[k]) < 2e-3, k
+
+
 def test_autograd_function(hc):
     import torch
     w = problem(64)
