@@ -207,8 +207,8 @@ struct hc_ctx {
   Handles h_pipe;
   cudaGraphConditionalHandle h_pipe_gate;
   cudaStream_t cap_hi, cap_lo;          // capture streams of the lagged graph's two branches
-  cudaStream_t io_stream;               // hc_set_state / hc_get_state: m's copy beside p's transform
-  cudaEvent_t io_ev[2];
+  cudaStream_t io_stream;               // hc_set_state / hc_get_state: copies beside p's transform
+  cudaEvent_t io_ev[2 + 4];             // entry, copies done, and one per row chunk of p
   int graph_nodes_fixed, graph_nodes_body, graph_nodes_outer;
 };
 
@@ -1932,8 +1932,8 @@ void hc_destroy(hc_ctx* c) {
   if (c->cap_hi) cudaStreamDestroy(c->cap_hi);
   if (c->cap_lo) cudaStreamDestroy(c->cap_lo);
   if (c->io_stream) cudaStreamDestroy(c->io_stream);
-  for (int k = 0; k < 2; ++k)
-    if (c->io_ev[k]) cudaEventDestroy(c->io_ev[k]);
+  for (cudaEvent_t e : c->io_ev)
+    if (e) cudaEventDestroy(e);
   if (c->owns_ws && c->ws) cudaFree(c->ws);
   if (c->st_host) cudaFreeHost(c->st_host);
   delete c;
@@ -2184,18 +2184,28 @@ int hc_get_p(hc_ctx* c, double* out, size_t count) {
 }
 
 // The whole state in one call.  In the 2D FP32-refined mode the host link
-// carries m on a second stream (io_stream, copy engine) while the SMs run p's
-// FP64 transform; p is staged in the lagged certification's FP64 scratch
-// (G64c, 2 half spectra), which no step keeps between hc_step calls.  Other
-// modes run the single-field calls one after the other.
+// and the SMs work side by side: a second stream of the context (io_stream)
+// carries the copies, p's rows cross in kStateChunks pieces so that its FP64
+// row transform starts on the first piece (set) and its last row transform
+// overlaps the first pieces' copies (get), and m's copy and conversion run
+// beside p's column transform.  p is staged in the lagged certification's
+// FP64 scratch (G64c, 2 half spectra), which no step keeps between hc_step
+// calls.  Other modes run the single-field calls one after the other.
+constexpr int kStateChunks = 4;
 static bool state_overlap(const hc_ctx* c) {
   return c->dim == 2 && !c->gen && c->refined && !c->df && c->G64c != nullptr;
 }
 static int io_setup(hc_ctx* c) {
   if (!c->io_stream) CU(cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking));
-  for (int k = 0; k < 2; ++k)
-    if (!c->io_ev[k]) CU(cudaEventCreateWithFlags(&c->io_ev[k], cudaEventDisableTiming));
+  for (cudaEvent_t& e : c->io_ev)
+    if (!e) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   return HC_OK;
+}
+// Row pieces of p: kStateChunks when each is a whole number of the row
+// passes' CTAs, else one.
+static int state_chunks(const hc_ctx* c) {
+  const int rows = c->ny / kStateChunks;
+  return (c->ny % kStateChunks == 0 && rows % c->gd.rpc == 0 && rows >= 64) ? kStateChunks : 1;
 }
 
 int hc_set_state(hc_ctx* c, const double* m, size_t m_count, const double* p, size_t p_count) {
@@ -2207,20 +2217,32 @@ int hc_set_state(hc_ctx* c, const double* m, size_t m_count, const double* p, si
   int rc = io_setup(c);
   if (rc) return rc;
   double* pst = reinterpret_cast<double*>(c->G64c);  // n doubles fit in 2 half spectra
+  const int nch = state_chunks(c), rows = c->ny / nch;
+  const size_t prow = (size_t)rows * c->nx;           // values of one piece
+  hc::Geo<double> gch = c->gd;
+  gch.ny = rows;                                      // a row pass over one piece
   // earlier work on the context's stream (it may still read m or the stage)
   CU(cudaEventRecord(c->io_ev[0], c->stream));
   CU(cudaStreamWaitEvent(c->io_stream, c->io_ev[0], 0));
-  // p first: its transform starts while m is still on the link
-  CU(cudaMemcpyAsync(pst, p, sizeof(double) * p_count, cudaMemcpyHostToDevice, c->stream));
+  // p first, piece by piece: each piece's row transform starts once it is on the device
+  for (int k = 0; k < nch; ++k) {
+    CU(cudaMemcpyAsync(pst + k * prow, p + k * prow, sizeof(double) * prow, cudaMemcpyHostToDevice,
+                       c->io_stream));
+    CU(cudaEventRecord(c->io_ev[2 + k], c->io_stream));
+  }
   CU(cudaMemcpyAsync(c->stage, m, sizeof(double) * m_count, cudaMemcpyHostToDevice, c->io_stream));
   hc::convert<float, double>(c->stage, (float*)c->m[0], c->n, c->io_stream);
   hc::convert<float, double>(c->stage + c->n, (float*)c->m[1], c->n, c->io_stream);
   CU(cudaEventRecord(c->io_ev[1], c->io_stream));
-  hc::row_r2c<double>(c->gd, pst, nullptr, c->G64, nullptr, c->stream);
+  for (int k = 0; k < nch; ++k) {
+    CU(cudaStreamWaitEvent(c->stream, c->io_ev[2 + k], 0));
+    hc::row_r2c<double>(gch, pst + k * prow, nullptr, c->G64 + (size_t)k * rows * c->H, nullptr,
+                        c->stream);
+  }
   hc::col_fwd<double>(c->gd, c->G64, nullptr, c->p64, nullptr, 1, 1, nullptr, c->stream);
   CU(cudaStreamWaitEvent(c->stream, c->io_ev[1], 0));
   hc::msum<float>(c->gf, (const float*)c->m[0], (const float*)c->m[1], c->st, c->stream);
-  c->launches += 5;
+  c->launches += 4 + nch;
   rc = gm2_for_new_m(c);
   if (rc) return rc;
   CU(cudaGetLastError());
@@ -2238,18 +2260,31 @@ int hc_get_state(hc_ctx* c, double* m_out, size_t m_count, double* p_out, size_t
   int rc = io_setup(c);
   if (rc) return rc;
   double* pst = reinterpret_cast<double*>(c->G64c);
+  const int nch = state_chunks(c), rows = c->ny / nch;
+  const size_t prow = (size_t)rows * c->nx;
+  hc::Geo<double> gch = c->gd;
+  gch.ny = rows;
   CU(cudaEventRecord(c->io_ev[0], c->stream));
   CU(cudaStreamWaitEvent(c->io_stream, c->io_ev[0], 0));
+  // m: conversion and copy on the second stream
   hc::convert<double, float>((const float*)c->m[0], c->stage, c->n, c->io_stream);
   hc::convert<double, float>((const float*)c->m[1], c->stage + c->n, c->n, c->io_stream);
   CU(cudaMemcpyAsync(m_out, c->stage, sizeof(double) * m_count, cudaMemcpyDeviceToHost,
                      c->io_stream));
-  CU(cudaEventRecord(c->io_ev[1], c->io_stream));
+  // p: column transform, then row transforms piece by piece, each piece's copy
+  // queued behind m's on the second stream
   hc::col_inv<double>(c->gd, c->p64, c->G64, 1.0 / (double)c->n, c->stream);
-  hc::row_c2r<double>(c->gd, c->G64, nullptr, pst, nullptr, nullptr, 0, c->stream);
-  c->launches += 4;
+  for (int k = 0; k < nch; ++k) {
+    hc::row_c2r<double>(gch, c->G64 + (size_t)k * rows * c->H, nullptr, pst + k * prow, nullptr,
+                        nullptr, 0, c->stream);
+    CU(cudaEventRecord(c->io_ev[2 + k], c->stream));
+    CU(cudaStreamWaitEvent(c->io_stream, c->io_ev[2 + k], 0));
+    CU(cudaMemcpyAsync(p_out + k * prow, pst + k * prow, sizeof(double) * prow,
+                       cudaMemcpyDeviceToHost, c->io_stream));
+  }
+  c->launches += 3 + nch;
   CU(cudaGetLastError());
-  CU(cudaMemcpyAsync(p_out, pst, sizeof(double) * p_count, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaEventRecord(c->io_ev[1], c->io_stream));
   CU(cudaStreamWaitEvent(c->stream, c->io_ev[1], 0));
   CU(cudaStreamSynchronize(c->stream));
   return HC_OK;

@@ -13,7 +13,9 @@ from gpu_common import hc  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
-CASES = [((64, 32), "fp32_refined"), ((64, 32), "fp64"), ((64, 32), "fp32_refined_df"),
+# (64, 256) and (512, 512) refined: p crosses in four row pieces; the others in one
+CASES = [((64, 256), "fp32_refined"), ((512, 512), "fp32_refined"),
+         ((64, 32), "fp32_refined"), ((64, 32), "fp64"), ((64, 32), "fp32_refined_df"),
          ((2048, 16), "fp32_refined"), ((48, 40), "fp64"), ((16, 16, 16), "fp32_refined"),
          ((16, 8, 16), "fp64")]
 
@@ -58,7 +60,7 @@ def test_state_calls_match_single_field_calls(hc, n, precision):
 def test_state_calls_with_page_locked_buffers(hc):
     """The e2e pattern: page-locked torch buffers in and out every step, two
     steps in a row, against numpy buffers on a second context."""
-    n = (256, 128)
+    n = (256, 512)
     with make(hc, n, "fp32_refined") as a, make(hc, n, "fp32_refined") as b:
         a.step(1)
         b.step(1)
