@@ -2224,22 +2224,22 @@ int hc_set_state(hc_ctx* c, const double* m, size_t m_count, const double* p, si
   // earlier work on the context's stream (it may still read m or the stage)
   CU(cudaEventRecord(c->io_ev[0], c->stream));
   CU(cudaStreamWaitEvent(c->io_stream, c->io_ev[0], 0));
-  // p first, piece by piece: each piece's row transform starts once it is on the device
+  // p first, piece by piece: each piece's row transform starts once it is on the device.
+  // (Each launch is queued right after its piece's copy: from pageable memory a copy
+  // returns only once the data is staged, and the work queued before it then already runs.)
   for (int k = 0; k < nch; ++k) {
     CU(cudaMemcpyAsync(pst + k * prow, p + k * prow, sizeof(double) * prow, cudaMemcpyHostToDevice,
                        c->io_stream));
     CU(cudaEventRecord(c->io_ev[2 + k], c->io_stream));
-  }
-  CU(cudaMemcpyAsync(c->stage, m, sizeof(double) * m_count, cudaMemcpyHostToDevice, c->io_stream));
-  hc::convert<float, double>(c->stage, (float*)c->m[0], c->n, c->io_stream);
-  hc::convert<float, double>(c->stage + c->n, (float*)c->m[1], c->n, c->io_stream);
-  CU(cudaEventRecord(c->io_ev[1], c->io_stream));
-  for (int k = 0; k < nch; ++k) {
     CU(cudaStreamWaitEvent(c->stream, c->io_ev[2 + k], 0));
     hc::row_r2c<double>(gch, pst + k * prow, nullptr, c->G64 + (size_t)k * rows * c->H, nullptr,
                         c->stream);
   }
   hc::col_fwd<double>(c->gd, c->G64, nullptr, c->p64, nullptr, 1, 1, nullptr, c->stream);
+  CU(cudaMemcpyAsync(c->stage, m, sizeof(double) * m_count, cudaMemcpyHostToDevice, c->io_stream));
+  hc::convert<float, double>(c->stage, (float*)c->m[0], c->n, c->io_stream);
+  hc::convert<float, double>(c->stage + c->n, (float*)c->m[1], c->n, c->io_stream);
+  CU(cudaEventRecord(c->io_ev[1], c->io_stream));
   CU(cudaStreamWaitEvent(c->stream, c->io_ev[1], 0));
   hc::msum<float>(c->gf, (const float*)c->m[0], (const float*)c->m[1], c->st, c->stream);
   c->launches += 4 + nch;
@@ -2266,14 +2266,16 @@ int hc_get_state(hc_ctx* c, double* m_out, size_t m_count, double* p_out, size_t
   gch.ny = rows;
   CU(cudaEventRecord(c->io_ev[0], c->stream));
   CU(cudaStreamWaitEvent(c->io_stream, c->io_ev[0], 0));
+  // p's column transform is queued first: a copy to pageable memory returns only
+  // when it is done, and the transform then already runs
+  hc::col_inv<double>(c->gd, c->p64, c->G64, 1.0 / (double)c->n, c->stream);
   // m: conversion and copy on the second stream
   hc::convert<double, float>((const float*)c->m[0], c->stage, c->n, c->io_stream);
   hc::convert<double, float>((const float*)c->m[1], c->stage + c->n, c->n, c->io_stream);
   CU(cudaMemcpyAsync(m_out, c->stage, sizeof(double) * m_count, cudaMemcpyDeviceToHost,
                      c->io_stream));
-  // p: column transform, then row transforms piece by piece, each piece's copy
-  // queued behind m's on the second stream
-  hc::col_inv<double>(c->gd, c->p64, c->G64, 1.0 / (double)c->n, c->stream);
+  // p's row transforms piece by piece, each piece's copy queued behind m's on
+  // the second stream
   for (int k = 0; k < nch; ++k) {
     hc::row_c2r<double>(gch, c->G64 + (size_t)k * rows * c->H, nullptr, pst + k * prow, nullptr,
                         nullptr, 0, c->stream);
