@@ -2266,12 +2266,12 @@ int hc_get_state(hc_ctx* c, double* m_out, size_t m_count, double* p_out, size_t
   gch.ny = rows;
   CU(cudaEventRecord(c->io_ev[0], c->stream));
   CU(cudaStreamWaitEvent(c->io_stream, c->io_ev[0], 0));
-  // p's column transform is queued first: a copy to pageable memory returns only
-  // when it is done, and the transform then already runs
-  hc::col_inv<double>(c->gd, c->p64, c->G64, 1.0 / (double)c->n, c->stream);
-  // m: conversion and copy on the second stream
+  // m's conversion is queued before p's column transform so that it gets the SMs
+  // first; m's copy after the transform, because a copy to pageable memory
+  // returns only when it is done
   hc::convert<double, float>((const float*)c->m[0], c->stage, c->n, c->io_stream);
   hc::convert<double, float>((const float*)c->m[1], c->stage + c->n, c->n, c->io_stream);
+  hc::col_inv<double>(c->gd, c->p64, c->G64, 1.0 / (double)c->n, c->stream);
   CU(cudaMemcpyAsync(m_out, c->stage, sizeof(double) * m_count, cudaMemcpyDeviceToHost,
                      c->io_stream));
   // p's row transforms piece by piece, each piece's copy queued behind m's on
