@@ -81,7 +81,7 @@ def test_operator_3d_matches_oracle(hc, precision, n, L):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
-@pytest.mark.parametrize("gamma", [0.5, 0.75, 1.0, 1.5])
+@pytest.mark.parametrize("gamma", [0.25, 0.5, 0.75, 0.999, 1.0, 1.001, 1.5])
 def test_split_step_3d_matches_oracle(hc, precision, gamma):
     """Step 2 of Algorithm 1 with p given, including |m| = 0 planes and
     points that relaxation extinguishes; the GPU applies the diffusion as
