@@ -1598,74 +1598,67 @@ __device__ __forceinline__ void gradnorm_finish(double part, double scale, doubl
   }
 }
 
+// Diffusion of one step along y for both components, one after the other
+// through one slab (forward transform, heat factor, inverse), so that only one
+// column's 8 values per thread are live: the FP32 pass then fits 64 registers
+// and the wide tiles of the gradient and divergence passes.  The arithmetic
+// per component is that of a joint two-component transform.
 template <typename T>
 __device__ __forceinline__ void col_heat_body(Geo<T> g, cx<T>* Mx, cx<T>* My, SolveState* st) {  // in place
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const ColIdx c = col_idx(g);
   const int H = g.H, ny = g.ny;
-  const int se = slab_elems(g);
-  cx<T>* const sl[2] = {sm + c.b, sm + se + c.b};
-  cx<T> v[2][8];
-#pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const size_t idx = (size_t)(c.j + s * c.NY8) * H + c.kx;
-    v[0][s] = Mx[idx];
-    v[1][s] = My[idx];
-  }
-  fft_canon<-1, 2>(v, sl, g.tc, c.j, g.lny, g.twy);
+  cx<T>* const sl[1] = {sm + c.b};
   const T invn = exp2_neg<T>(g.lnx + g.lny);  // 1 / (nx ny)
-  if (blockIdx.x == 0) {
-    // The packed column holds kx = 0 (A) and kx = nx/2 (B) as A + iB; their heat
-    // factors differ, so separate with the ky <-> -ky symmetry:
-    // new = (h0 + hN)/2 P[ky] + (h0 - hN)/2 conj(P[-ky]).
-    __syncthreads();
+  const bool diag = st && st->diag;
+  DotAcc<T> ga;
+#pragma unroll 1
+  for (int q = 0; q < 2; ++q) {
+    cx<T>* M = q == 0 ? Mx : My;
+    cx<T> v[1][8];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const int e = padk(c.j + s * c.NY8) * g.tc;
-      sl[0][e] = v[0][s];
-      sl[1][e] = v[1][s];
-    }
-    __syncthreads();
-    if (c.b == 0) {
+    for (int s = 0; s < 8; ++s) v[0][s] = M[(size_t)(c.j + s * c.NY8) * H + c.kx];
+    fft_canon<-1, 1>(v, sl, g.tc, c.j, g.lny, g.twy);
+    if (blockIdx.x == 0) {
+      // The packed column holds kx = 0 (A) and kx = nx/2 (B) as A + iB; their heat
+      // factors differ, so separate with the ky <-> -ky symmetry:
+      // new = (h0 + hN)/2 P[ky] + (h0 - hN)/2 conj(P[-ky]).
+      __syncthreads();
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const int ky = c.j + s * c.NY8;
-        const int kn = (ny - ky) & (ny - 1);
-        const T h0 = g.hx[0] * g.hy[ky] * invn, hN = g.hx[H] * g.hy[ky] * invn;
-        const T hp = (T)0.5 * (h0 + hN), hm = (T)0.5 * (h0 - hN);
+      for (int s = 0; s < 8; ++s) sl[0][padk(c.j + s * c.NY8) * g.tc] = v[0][s];
+      __syncthreads();
+      if (c.b == 0) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const cx<T> pn = sl[q][padk(kn) * g.tc];
-          v[q][s] = cmk<T>(hp * v[q][s].x + hm * pn.x, hp * v[q][s].y - hm * pn.y);
+        for (int s = 0; s < 8; ++s) {
+          const int ky = c.j + s * c.NY8;
+          const int kn = (ny - ky) & (ny - 1);
+          const T h0 = g.hx[0] * g.hy[ky] * invn, hN = g.hx[H] * g.hy[ky] * invn;
+          const T hp = (T)0.5 * (h0 + hN), hm = (T)0.5 * (h0 - hN);
+          const cx<T> pn = sl[0][padk(kn) * g.tc];
+          v[0][s] = cmk<T>(hp * v[0][s].x + hm * pn.x, hp * v[0][s].y - hm * pn.y);
         }
       }
     }
-  }
-  if (c.kx != 0) {
+    if (c.kx != 0) {
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const T h = g.hx[c.kx] * g.hy[c.j + s * c.NY8] * invn;
-      v[0][s] = cscale(v[0][s], h);
-      v[1][s] = cscale(v[1][s], h);
+      for (int s = 0; s < 8; ++s)
+        v[0][s] = cscale(v[0][s], g.hx[c.kx] * g.hy[c.j + s * c.NY8] * invn);
     }
-  }
-  if (st && st->diag) {  // v = F(m_new) / n: sum |grad m_new|^2 = n sum w |xi~|^2 |v|^2
-    DotAcc<T> ga;
+    if (diag) {  // v = F(m_new) / n: sum |grad m_new|^2 = n sum w |xi~|^2 |v|^2
 #pragma unroll
-    for (int s = 0; s < 8; ++s) gradnorm_acc(g, ga, c.kx, c.j + s * c.NY8, v[0][s], v[1][s]);
-    gradnorm_finish(ga.value(), (double)g.nx * (double)ny, g.partials, st, 1);
-  }
-  fft_canon<+1, 2>(v, sl, g.tc, c.j, g.lny, g.twy);
+      for (int s = 0; s < 8; ++s) gradnorm_acc(g, ga, c.kx, c.j + s * c.NY8, v[0][s], czero<T>());
+    }
+    fft_canon<+1, 1>(v, sl, g.tc, c.j, g.lny, g.twy);
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const size_t idx = (size_t)(c.j + s * c.NY8) * H + c.kx;
-    Mx[idx] = v[0][s];
-    My[idx] = v[1][s];
+    for (int s = 0; s < 8; ++s) M[(size_t)(c.j + s * c.NY8) * H + c.kx] = v[0][s];
+    __syncthreads();  // the slab is the next component's
   }
+  if (diag) gradnorm_finish(ga.value(), (double)g.nx * (double)ny, g.partials, st, 1);
 }
 template <typename T>
-__global__ void __launch_bounds__(512) k_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My, SolveState* st) {
+__global__ void __launch_bounds__(col_cta_max<T, true>(), 1) k_col_heat(Geo<T> g, cx<T>* Mx, cx<T>* My,
+                                                                        SolveState* st) {
   col_heat_body<T>(g, Mx, My, st);
 }
 
@@ -2587,12 +2580,13 @@ void col_div(const Geo<T>& g0, int mode, const cx<T>* Qx, const cx<T>* Qy, const
 }
 template <typename T>
 void col_heat(const Geo<T>& g0, cx<T>* Mx, cx<T>* My, SolveState* st, cudaStream_t s) {
-  const Geo<T> g = col_narrow(g0);
+  // the whole tile (one slab); the persistent pass at most 512 threads
+  const Geo<T> g = g0.pipe ? col_narrow(g0) : g0;
   if (g.pipe) {
     kp_col_heat<T><<<g.pgrid, col_threads(g), pipe_smem(g), s>>>(g, Mx, My, st);
     return;
   }
-  k_col_heat<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 2), s>>>(g, Mx, My, st);
+  k_col_heat<T><<<g.H >> g.ltc, col_threads(g), col_smem(g, 1), s>>>(g, Mx, My, st);
 }
 template <typename T>
 void col_gradnorm(const Geo<T>& g0, const cx<T>* Mx, const cx<T>* My, SolveState* st, int into_next,
