@@ -220,7 +220,7 @@ void batch_split(const BInst* bi, const BShape& sh, cudaStream_t s) {
   const Geo<float>& g = sh.gf;
   const Geo<float>& gn = sh.gfn;
   kb_split_grad<<<col_grid(g, sh.nb), col_threads(g), col_smem(g, 2), s>>>(bi);
-  kb_split_row<<<row_grid(g, sh.nb), row_threads(g), row_smem(g), s>>>(bi);
+  kb_split_row<<<row_grid(g, sh.nb), row_threads(g), row_split_smem(g), s>>>(bi);
   kb_split_heat<<<col_grid(gn, sh.nb), col_threads(gn), col_smem(gn, 2), s>>>(bi);
   kb_split_c2r<<<row_grid(g, sh.nb), row_threads(g), row_smem(g), s>>>(bi);
 }

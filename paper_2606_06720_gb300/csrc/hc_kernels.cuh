@@ -1090,21 +1090,39 @@ __device__ __forceinline__ void row_split_body(Geo<T> g, const cx<T>* Gx, const 
   cx<T>* const sl[1] = {slab};
   const cx<T>* Ar[1] = {Gx + (size_t)y * H};
   const cx<T>* Br[1] = {Gy + (size_t)y * H};
+  const bool diag = st->diag != 0;
+  // stage the CTA's rows of mx, my (and r for the diagnostics) behind the
+  // slabs with cp.async, so that their latency overlaps the inverse transform
+  T* sf = reinterpret_cast<T*>(sm + ((size_t)g.rpc << g.lnx));
+  {
+    const size_t row0 = ((size_t)blockIdx.x << g.lrpc) * N;
+    const int per = (int)(((size_t)g.rpc * N * sizeof(T)) >> 4);  // 16-byte chunks per field
+    const T* const src[3] = {mx + row0, my + row0, rr + row0};
+    for (int q = 0; q < (diag ? 3 : 2); ++q) {
+      char* dst = reinterpret_cast<char*>(sf + (size_t)q * g.rpc * N);
+      const char* from = reinterpret_cast<const char*>(src[q]);
+      for (int c = threadIdx.x; c < per; c += blockDim.x) cp_async16(dst + 16 * c, from + 16 * c);
+    }
+    cp_async_commit();
+  }
   cx<T> v[1][8];
   load_rows_c2r<1>(v, Ar, Br, j, N8);
   fft_canon<+1, 1, true>(v, sl, 1, j, g.lnx, g.twx);
-  const size_t ro = (size_t)y * N;
+  cp_async_wait_all();
+  __syncthreads();
+  const T* smx = sf + (size_t)rb * N;
+  const T* smy = smx + (size_t)g.rpc * N;
+  const T* srr = smy + (size_t)g.rpc * N;
   const T c2dt = cfv<T>(cf.c2dt, cf.f_c2dt);
   bool finite = true;
-  const bool diag = st->diag != 0;
   EnergyAcc<T> en;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = j + s * N8;
     const T gx = v[0][s].x, gy = v[0][s].y;
-    T ax = mx[ro + x], ay = my[ro + x];
+    T ax = smx[x], ay = smy[x];
     if (diag)
-      en.add(rr[ro + x], gx * gx + gy * gy, ax * gx + ay * gy, ax * ax + ay * ay, cfv<T>(cf.gamma, cf.f_gamma));
+      en.add(srr[x], gx * gx + gy * gy, ax * gx + ay * gy, ax * ax + ay * ay, cfv<T>(cf.gamma, cf.f_gamma));
     split_point<T>(ax, ay, gx, gy, c2dt, cf);
     finite = finite && hc_finite(ax) && hc_finite(ay);
     v[0][s] = cmk<T>(ax, ay);
@@ -2418,6 +2436,11 @@ template <typename T>
 static inline size_t row_smem(const Geo<T>& g) {
   return (size_t)g.rpc * g.nx * sizeof(cx<T>);
 }
+// the split row pass: its slabs plus the staged rows of mx, my and r
+template <typename T>
+static inline size_t row_split_smem(const Geo<T>& g) {
+  return row_smem(g) + (size_t)3 * g.rpc * g.nx * sizeof(T);
+}
 template <typename T>
 static inline int col_threads(const Geo<T>& g) { return g.tc << (g.lny - 3); }
 template <typename T>
@@ -2472,8 +2495,8 @@ void row_apply(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const Tm* mx, 
 template <typename T>
 void row_split(const Geo<T>& g, const cx<T>* Gx, const cx<T>* Gy, const T* mx, const T* my,
                const T* r, cx<T>* Mx, cx<T>* My, SplitCoef cf, SolveState* st, cudaStream_t s) {
-  k_row_split<T><<<g.ny >> g.lrpc, row_threads(g), row_smem(g), s>>>(g, Gx, Gy, mx, my, r, Mx, My,
-                                                                     cf, st);
+  k_row_split<T><<<g.ny >> g.lrpc, row_threads(g), row_split_smem(g), s>>>(g, Gx, Gy, mx, my, r, Mx,
+                                                                           My, cf, st);
 }
 template <typename T>
 void col_fwd(const Geo<T>& g0, const cx<T>* in0, const cx<T>* in1, cx<T>* out0, cx<T>* out1, int nv,
