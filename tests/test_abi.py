@@ -284,3 +284,16 @@ def test_param_validation_matches_the_documented_rule(lib):
         assert (rc == 0) == ok, (c, D, gamma, dt, precision, precond, rc)
 
     check()
+
+
+def test_state_calls_reject_a_null_context(lib):
+    """hc_set_state / hc_get_state check their arguments before any copy: a
+    NULL context (or NULL buffers) is HC_EINVAL on the host."""
+    from paper_2606_06720_gb300 import _binding as Bd
+    import numpy as np
+    m, p = np.zeros(2 * 64), np.zeros(64)
+    dp = C.POINTER(C.c_double)
+    pm, pp = m.ctypes.data_as(dp), p.ctypes.data_as(dp)
+    assert Bd.hc_set_state(None, pm, m.size, pp, p.size) == Bd.HC_EINVAL
+    assert Bd.hc_get_state(None, pm, m.size, pp, p.size) == Bd.HC_EINVAL
+    assert Bd.hc_set_state(None, dp(), m.size, dp(), p.size) == Bd.HC_EINVAL
